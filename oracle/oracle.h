@@ -1,0 +1,146 @@
+/*
+ * oracle.h -- plain FP64 CPU oracle for one IMEX monodomain time step of
+ * lifex-ep (Africa et al., arXiv 2308.01651).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the CUDA path: only the
+ * test suite, the smoke check and the CPU-baseline leg of the benchmark may
+ * load it.  It shares no source, header, table or helper with the CUDA
+ * library, and the CUDA library never calls it.
+ *
+ * What it computes (paper Sec. 1.2, "numerical discretization"):
+ *   - Eq. (4): the ionic ODEs, one BDF step per DoF, with states whose right
+ *     hand side is affine in themselves taken implicitly and the rest
+ *     explicitly, so the update is a direct division.
+ *   - Eq. (6): (alpha/dt M + K) u_{n+1} = M u_BDF/dt - M I_ion + M I_app,
+ *     with M, K assembled on Q1 hexahedra by 2x2x2 Gauss-Legendre quadrature
+ *     (the minimum rule that integrates the mass matrix exactly), the ionic
+ *     current and the applied current interpolated from the nodes (ICI).
+ *   - Eq. (3): D = sigma_l f0 f0^T + sigma_t s0 s0^T + sigma_n n0 n0^T,
+ *     written as sigma_n I + (sigma_l - sigma_n) f f^T + (sigma_t - sigma_n) s s^T
+ *     with f, s the Q1 interpolants of the nodal fibre vectors at each
+ *     quadrature point (not renormalised).
+ *   - Jacobi-preconditioned CG to ||r||_2 <= tol ||b||_2, initial guess u_EXT.
+ *   - Activation time (Sec. 3.2.1): time of the largest forward difference
+ *     u_{n+1} - u_n at each node (first maximum wins).
+ *
+ * Units: ms, mV (Bueno-Orovio: dimensionless u), cm, mM.
+ */
+#ifndef GB300_EP_ORACLE_H
+#define GB300_EP_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_MODEL_BO = 0, OR_MODEL_TTP06 = 1, OR_MODEL_PASSIVE = 2 };
+enum { OR_CELL_ENDO = 0, OR_CELL_MID = 1, OR_CELL_EPI = 2 };
+#define OR_MAX_STATES 18
+#define OR_MAX_PULSES 8
+
+/* ---- single-cell ionic models (Sec. 1.1.1, Eq. (1)) ------------------- */
+
+/* Number of ionic state variables w (not counting u). */
+int or_model_nstates(int model);
+/* Resting / initial state.  TTP06 uses the epicardial initial conditions the
+ * paper prints for the N-version benchmark (Sec. 3.2.1) for every cell type. */
+void or_model_initial(int model, int cell, double* u0, double* w0);
+/* Right-hand side of dw/dt written as a - b*w for every state.  States whose
+ * rate is affine in themselves (gates, BO v/w/s, TTP06 R) return b > 0;
+ * concentrations return their full rate in a and b = 0. */
+void or_model_rates(int model, int cell, double g_passive, double u,
+                    const double* w, double* a, double* b);
+/* Ionic current I_ion(u, w) in model units per ms. */
+double or_model_iion(int model, int cell, double g_passive, double u,
+                     const double* w);
+
+/* One semi-implicit single-cell step (Eq. (4) with the potential equation of
+ * Eq. (1) treated like Eq. (5) without diffusion).  order 1 or 2; hist holds
+ * u_{n-1}, w_{n-1} when order == 2.  Returns the new u and writes w_new. */
+double or_cell_step(int model, int cell, double g_passive, int order, double dt,
+                    double u_n, const double* w_n, double u_nm1,
+                    const double* w_nm1, double iapp, double* w_new);
+
+/* ---- Q1 finite elements (Sec. 1.2, Eq. (6)) ---------------------------- */
+
+/* Element mass and stiffness matrices (8x8, row-major, local node index
+ * a = ia + 2 ib + 4 ic) of a trilinear hexahedron with vertex coordinates X,
+ * nodal fibre vectors f, s and diffusivities dl, dt_, dn (cm^2/ms). */
+void or_element_matrices(const double* X, const double* f, const double* s,
+                         double dl, double dt_, double dn, double* Me,
+                         double* Ke);
+
+typedef struct {
+    int64_t n;        /* rows */
+    int64_t nnz;
+    int64_t* rowptr;  /* n + 1 */
+    int64_t* col;     /* nnz, sorted within each row */
+    double* mval;     /* mass matrix values */
+    double* kval;     /* stiffness matrix values */
+} or_csr;
+
+/* Assemble M and K on the same sparsity pattern.  Returns 0 on success. */
+int or_assemble(int64_t nn, int64_t ne, const double* xyz, const int32_t* hex,
+                const double* f0, const double* s0, double dl, double dt_,
+                double dn, or_csr* A);
+void or_csr_free(or_csr* A);
+/* y = (cm*M + ck*K) x */
+void or_csr_apply(const or_csr* A, double cm, double ck, const double* x,
+                  double* y);
+
+/* Jacobi-PCG on (cm M + ck K) x = b; x holds the initial guess.  Returns the
+ * iteration count, or -1 when maxit is reached. */
+int or_pcg(const or_csr* A, double cm, double ck, const double* b, double* x,
+           double tol, int maxit, double* relres_out);
+
+/* ---- monodomain simulation ---------------------------------------------- */
+
+typedef struct or_sim or_sim;
+
+typedef struct {
+    double amp;     /* model units per ms */
+    double t0;      /* ms */
+    double dur;     /* ms */
+    double period;  /* ms; <= 0 means a single pulse */
+} or_pulse;
+
+/* Creates a simulation.  cell may be NULL (all epicardial).  masks holds
+ * npulses x nn bytes (1 = node receives the pulse).  act_thr is the slope
+ * (model units per ms) a node's largest forward difference must exceed to
+ * count as activated. */
+or_sim* or_sim_create(int64_t nn, int64_t ne, const double* xyz,
+                      const int32_t* hex, const double* f0, const double* s0,
+                      double dl, double dt_, double dn, int model,
+                      const uint8_t* cell, double g_passive, double dt,
+                      int bdf_order, double tol, int maxit, int npulses,
+                      const or_pulse* pulses, const uint8_t* masks,
+                      double act_thr);
+void or_sim_destroy(or_sim* S);
+/* Advances nsteps steps; returns 0, or -1 on CG failure, -2 on non-finite. */
+int or_sim_step(or_sim* S, int64_t nsteps);
+/* Extra nodal applied current for the next step only (manufactured
+ * solutions).  NULL clears it. */
+void or_sim_set_iapp_extra(or_sim* S, const double* iapp);
+int64_t or_sim_nodes(const or_sim* S);
+int or_sim_nstates(const or_sim* S);
+int64_t or_sim_stepindex(const or_sim* S);
+int or_sim_last_iters(const or_sim* S);
+double or_sim_last_relres(const or_sim* S);
+/* Copies out / in u_n, u_{n-1}, w_n, w_{n-1} (state-major, ns x nn). */
+void or_sim_get_state(const or_sim* S, double* u_n, double* u_nm1, double* w_n,
+                      double* w_nm1);
+void or_sim_set_state(or_sim* S, const double* u_n, const double* u_nm1,
+                      const double* w_n, const double* w_nm1, int64_t step);
+/* Activation times in ms (NaN where never activated) and the largest
+ * forward difference seen so far. */
+void or_sim_get_activation(const or_sim* S, double* at, double* best);
+void or_sim_set_activation(or_sim* S, const double* at, const double* best);
+/* Ionic current at the last step, nodal. */
+void or_sim_get_iion(const or_sim* S, double* iion);
+const or_csr* or_sim_matrix(const or_sim* S);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,82 @@
+"""Pins of the oracle's monodomain time discretisation (paper Sec. 1.2,
+Eqs. (5)-(6)), of the stimulus window and of the activation-time rule.
+
+  * BDF order on a manufactured solution: a passive membrane I_ion = g u,
+    u = e^{-t} cos(pi x/Lx) cos(pi y/Ly) cos(pi z/Lz) (homogeneous Neumann,
+    Eq. (2)), isotropic D, forcing I_app = (g - 1 + D pi^2 sum 1/L^2) u at the
+    nodes.  Errors against a dt/64 run on the same mesh fall with slope 1 for
+    BDF1 and 2 for BDF2 (the IMEX extrapolation keeps the order).
+  * A spatially uniform pulse with g = 0 leaves u uniform (K 1 = 0), so each
+    active step adds dt * amp: the pulse is active for exactly round(dur/dt)
+    steps starting at step round(t0/dt) + 1.
+  * A second one-step pulse inside the first makes one step's slope the
+    largest, which fixes the activation time.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle.oracle as O
+from paper_2308_01651_gb300 import inputs as I
+
+
+def manufactured_run(bdf, dt, T=1.0, n=(6, 4, 3), L=(0.6, 0.4, 0.3), D=1e-2, g=0.5):
+    m = I.slab_mesh(*n, L)
+    xyz = m["xyz"]
+    f0, s0 = I.uniform_fibres(xyz.shape[0])
+    S = O.Sim(xyz, m["hex"], f0, s0, (D, D, D), O.PASSIVE, dt, bdf, g=g, tol=1e-13)
+    shape = np.cos(math.pi * xyz[:, 0] / L[0]) * np.cos(math.pi * xyz[:, 1] / L[1]) * np.cos(math.pi * xyz[:, 2] / L[2])
+    lam = math.pi ** 2 * sum(1.0 / l ** 2 for l in L)
+    S.set_state(shape, shape * math.exp(dt), np.zeros((0, xyz.shape[0])), np.zeros((0, xyz.shape[0])), 0)
+    for k in range(int(round(T / dt))):
+        t1 = (k + 1) * dt
+        S.set_iapp_extra((g - 1.0 + D * lam) * math.exp(-t1) * shape)
+        S.step(1)
+    return S.potential()
+
+
+@pytest.mark.parametrize("bdf,lo,hi", [(1, 0.85, 1.15), (2, 1.85, 2.2)])
+def test_bdf_order_manufactured(bdf, lo, hi):
+    dts = [0.1, 0.05, 0.025]
+    ref = manufactured_run(bdf, dts[-1] / 64)
+    errs = [np.abs(manufactured_run(bdf, dt) - ref).max() for dt in dts]
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert all(lo < s < hi for s in slopes), (errs, slopes)
+
+
+@pytest.mark.parametrize("t0,dur,dt", [(0.0, 1.0, 0.05), (0.3, 0.2, 0.1), (1.0, 2.0, 0.05)])
+def test_stimulus_window_and_activation(t0, dur, dt):
+    """Pulse 1 (amplitude 2) covers the window; pulse 2 (amplitude 1) adds one
+    step inside it, so the slope peaks on exactly that step."""
+    m = I.slab_mesh(3, 2, 2, (0.3, 0.2, 0.2))
+    n = m["xyz"].shape[0]
+    f0, s0 = I.uniform_fibres(n)
+    k0, kd = round(t0 / dt), round(dur / dt)
+    j = kd // 2
+    S = O.Sim(m["xyz"], m["hex"], f0, s0, (1e-3, 1e-3, 1e-3), O.PASSIVE, dt, 1, g=0.0,
+              pulses=[dict(amp=2.0, t0=t0, dur=dur), dict(amp=1.0, t0=t0 + j * dt, dur=dt)],
+              masks=np.ones((2, n), dtype=np.uint8), act_thr=1.0)
+    S.step(k0 + kd + 5)
+    u = S.potential()
+    assert np.allclose(u, (2.0 * kd + 1.0) * dt, rtol=1e-10, atol=0)
+    at, best = S.activation()
+    assert np.allclose(at, (k0 + j + 1) * dt, rtol=0, atol=1e-12)
+    assert np.allclose(best, 3.0 * dt, rtol=1e-10)
+
+
+def test_manufactured_solution_converges_in_space():
+    """With a small time step the discrete solution approaches the exact
+    e^{-T} cos cos cos at second order in h; a wrong sign or factor on the
+    ionic, applied-current or history term of Eq. (6) would leave an O(1) gap."""
+    T, L = 0.5, (0.6, 0.4, 0.3)
+    errs = []
+    for n in [(6, 4, 3), (12, 8, 6)]:
+        u = manufactured_run(2, 0.005, T=T, n=n, L=L)
+        m = I.slab_mesh(*n, L)
+        xyz = m["xyz"]
+        exact = math.exp(-T) * np.cos(math.pi * xyz[:, 0] / L[0]) * np.cos(math.pi * xyz[:, 1] / L[1]) \
+            * np.cos(math.pi * xyz[:, 2] / L[2])
+        errs.append(np.abs(u - exact).max() / np.abs(exact).max())
+    assert errs[0] < 0.1
+    assert 3.0 < errs[0] / errs[1] < 5.0, errs

@@ -1,0 +1,422 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 monodomain IMEX step (lifex-ep, arXiv 2308.01651).
+
+Workload: the 200 x 70 x 30 Q1 slab (442,401 nodes), ten Tusscher-Panfilov
+2006 epicardial cells, fibres rotating +60 -> -60 deg through z, BDF2,
+dt = 0.05 ms, stimulus on the x = 0 face, FP32 inner CG inside FP64
+refinement.  A step is one IMEX time step (ionic update, right-hand side,
+refined linear solve, activation update) of the whole slab.
+
+Prints one JSON line (rank 0): DoF-steps/s over the timed steps with the L2
+flushed before every step (each step bracketed by CUDA events on the
+instance's stream), step-latency p50/p99, the dominant kernel's roofline
+position, the plain FP64 GPU path and the oracle (CPU) for reference, the
+activation-time error of the refined path against the FP64 GPU path, an
+end-to-end figure through the public API with host buffers, and the SM
+clocks sampled during the timed region.
+
+--impl reference times the FP64 CPU oracle (the reference of this build) on
+the same workload, a bounded number of steps, on the host cores.
+Multi-GPU (torchrun): every rank runs its own replica (the path has no
+cross-instance exchange), value = all ranks' DoF-steps / the slowest rank.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DoF-steps/s per monodomain step at <=0.5 ms activation error; p50/p99 latency"
+UNIT = "DoF-steps/s"
+WORKLOAD = ("slab_ttp06: 2 x 0.7 x 0.3 cm Q1 slab, 200x70x30 elements (442,401 nodes), TTP06 epi, "
+            "fibres +60->-60 deg in z, sigma 1.4/0.5/0.25 mS/cm, chi_m 1400/cm, C_m 1 uF/cm^2, BDF2, "
+            "dt 0.05 ms, x=0 face stimulus 35.714 mV/ms x 2 ms")
+# FP32 pipe peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# FP64 pipe peak (GB300 nominal dense FP64)
+FP64_PEAK_TFLOPS = 1.25
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_model(name, N, n_elems):
+    """Algorithmic bytes and flops per launch of each kernel (what the method
+    must move / compute, not what the hardware did)."""
+    B = {
+        # read z, p_old, 6 fibre components; write p_new, q
+        "apply32_mf": (40 * N, 910 * n_elems + 12 * N),
+        # read z, p_old at the row; 14 FP32 coefficients; write p_new, q
+        "apply32_stencil": (4 * 14 + 16, 2 * 27 * 2 + 4),
+        # read p, q, d, r, D^-1; write d, r, z
+        "update32": (32 * N, 8 * N),
+        # read d, u; write u
+        "correct": (20 * N, 1 * N),
+        # FP64 residual: A64 (14 doubles), u, b; write r, r32, z32, d32
+        "resid": (112 * N + 16 * N + 20 * N, 54 * N),
+        # FP64 rhs: M64, A64, v, u; write b, r, r32, z32, d32
+        "rhs": (224 * N + 16 * N + 28 * N, 108 * N),
+        # TTP06 refined: u_n, u_nm1, 2 x (13 f32 gates + 5 f64 conc), cell, mask;
+        # write gates, conc, v, u_new
+        "ionic": ((16 + 2 * (52 + 40) + 2 + 52 + 40 + 16) * N, None),
+        "finish": (40 * N, 2 * N),
+    }
+    v = B.get(name)
+    if v is None:
+        return None, None
+    if name == "apply32_stencil":
+        return v[0] * N, v[1] * N
+    return v
+
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {
+    "apply32_mf": ["paper_2308_01651_gb300/csrc/k_mf.cu", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
+    "resid": ["paper_2308_01651_gb300/csrc/k_stencil.cu", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
+    "update32": ["paper_2308_01651_gb300/csrc/k_cg.cu", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
+    "ionic": ["paper_2308_01651_gb300/csrc/k_ionic.cu", "paper_2308_01651_gb300/csrc/ionic_models.cuh"],
+}
+
+
+def committed_traffic(name):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if the
+    kernel's sources are unchanged since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p) or name not in KERNEL_SOURCES:
+        return None
+    with open(p) as f:
+        d = json.load(f).get(name)
+    if not d or d.get("source_hash") != source_hash(KERNEL_SOURCES[name]):
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ CPU leg --
+
+def oracle_leg(prob, budget_s=20.0, max_steps=50):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    CSR assembly untimed, then as many steps from rest as fit ~budget_s."""
+    import oracle.oracle as O
+
+    sim = O.sim_from_problem(prob)
+    N = sim.nn
+    t = time.perf_counter()
+    sim.step(1)
+    t1 = time.perf_counter() - t
+    k = int(max(1, min(max_steps - 1, budget_s / max(t1, 1e-6) - 1)))
+    t = time.perf_counter()
+    sim.step(k)
+    tk = time.perf_counter() - t
+    steps = k + 1
+    total = t1 + tk
+    return {"value": N * steps / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"steps 1..{steps} from rest (stimulus on) of the full {N}-node slab, "
+                      f"CSR assembly untimed, single thread, {total:.1f} s",
+            "ms_per_step": 1e3 * total / steps, "steps": steps}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2308_01651_gb300 import inputs as I
+    prob = I.slab_ttp06()
+    leg = oracle_leg(prob, budget_s=min(120.0, 10.0 + 2.0 * args.steps), max_steps=max(2, args.steps))
+    line = {"metric": METRIC, "value": leg["value"], "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": leg["steps"], "warmup": 0, "ms_per_step": leg["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": prob["mesh"]["xyz"].shape[0],
+                       "l2": "n/a (CPU)", "note": "bounded sample; see cpu_baseline.sample"},
+            "cpu_baseline": {k: leg[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": leg["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg --
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    import __graft_entry__
+    if local == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    from paper_2308_01651_gb300 import ep
+    from paper_2308_01651_gb300 import inputs as I
+
+    prob = I.slab_ttp06()
+    N = prob["mesh"]["xyz"].shape[0]
+    n_elems = prob["mesh"]["hex"].shape[0]
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    REF, FP64 = ep.EP_PREC_FP32_REFINED, ep.EP_PREC_FP64
+
+    inst = ep.Instance(prob, precision=REF, cuda_stream=sp)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    W, K = max(3, args.warmup), args.steps
+    inst.step(W)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    launches = 0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            inst.step_async(1)
+            ev[k][1].record(stream)
+            st = inst.stats()  # synchronises; outside the events
+            launches += 3 + 2 * st["cg_iters"] + 2 * st["sweeps"]
+        inst.sync()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    times = [a.elapsed_time(b) for a, b in ev]  # ms
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = N * K * world / (total_ms / 1e3)
+    lat = sorted(times)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+    t_end = (W + K) * prob["dt"]
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---- kernel attribution (events around every kernel, host-driven loops)
+    P = args.profile_steps
+    kernels, roof = {}, None
+    if P > 0:
+        ep.ep_profile_enable(inst.h, True)
+        ep.ep_profile_read(inst.h, reset=True)
+        inst.step(P)
+        prof = ep.ep_profile_read(inst.h, reset=True)
+        ep.ep_profile_enable(inst.h, False)
+        tot_prof = sum(v[1] for v in prof.values())
+        for name, (n_l, ms) in prof.items():
+            b, f = kernel_model(name, N, n_elems)
+            avg_s = ms / 1e3 / n_l
+            kernels[name] = {"launches": n_l, "avg_us": 1e6 * avg_s, "share": ms / tot_prof,
+                             "gbs": (b / avg_s / 1e9) if b else None,
+                             "tflops": (f / avg_s / 1e12) if f else None}
+        dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
+        hbm_peak, peak_kind = measured_peaks()
+        d = kernels[dom]
+        hbm_frac = d["gbs"] / hbm_peak if d["gbs"] else 0.0
+        fp64 = dom in ("resid", "rhs", "apply64")
+        alu_peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+        alu_frac = d["tflops"] / alu_peak if d["tflops"] else 0.0
+        if alu_frac > hbm_frac:
+            roof = {"bound": "alu", "achieved": d["tflops"], "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": alu_frac,
+                    "peak_source": "GB300 nominal FP64" if fp64 else "FP32 lanes x 2 x max SM clock (derived)"}
+        else:
+            roof = {"bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_frac, "peak_source": f"{peak_kind} HBM copy bandwidth"}
+        roof.update(kernel=dom, hbm_frac=hbm_frac, alu_frac=alu_frac, traffic=committed_traffic(dom))
+
+    # ---- refined vs plain FP64 on the GPU: accuracy and the FP64 throughput
+    steps_done = W + K + P
+    at_ref32 = inst.activation_times()
+    u32 = inst.potential()
+    inst.close()
+    acc, fp64 = None, None
+    if not args.no_accuracy:
+        i64 = ep.Instance(prob, precision=FP64, cuda_stream=sp)
+        i64.step(W)
+        e64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(min(K, args.fp64_steps))]
+        for a, b in e64:
+            flush.zero_()
+            a.record(stream)
+            i64.step_async(1)
+            b.record(stream)
+        i64.sync()
+        torch.cuda.synchronize()
+        t64 = sum(a.elapsed_time(b) for a, b in e64)
+        i64.step(steps_done - W - len(e64))
+        at64 = i64.activation_times()
+        u64 = i64.potential()
+        i64.close()
+        both = ~np.isnan(at64) & ~np.isnan(at_ref32)
+        acc = {"at_max_abs_err_ms": float(np.abs(at64 - at_ref32)[both].max()) if both.any() else None,
+               "activated_nodes": int(both.sum()), "activation_sets_equal": bool(
+                   np.array_equal(np.isnan(at64), np.isnan(at_ref32))),
+               "u_linf_mV_at_end": float(np.abs(u64 - u32).max()), "t_end_ms": steps_done * prob["dt"],
+               "vs": "plain FP64 GPU path, same workload and steps"}
+        fp64 = {"value": N * len(e64) / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / len(e64),
+                "steps": len(e64)}
+
+    # ---- end to end through the public API, host buffers in and out
+    e2e = None
+    torch.cuda.synchronize()
+    if args.no_e2e:
+        K_e2e = 0
+    else:
+        K_e2e = K
+    t0 = time.perf_counter()
+    if K_e2e:
+        ie = ep.Instance(prob, precision=REF, cuda_stream=sp)
+        ie.step_async(K_e2e)
+        at_h = ie.activation_times()
+        u_h = ie.potential()
+        e2e_s = time.perf_counter() - t0
+        ie.close()
+        h2d = (prob["f0"].nbytes + prob["s0"].nbytes + prob["masks"].nbytes + prob["cell"].nbytes)
+        d2h = at_h.nbytes + u_h.nbytes
+        e2e = {"value": N * K_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / K_e2e,
+               "d2h_bytes_per_step": d2h / K_e2e,
+               "includes": "ep_create from host arrays (upload + operator assembly + graph build), "
+                           f"{K_e2e} steps, activation times and potential read back to host"}
+
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        leg = oracle_leg(prob, budget_s=args.cpu_budget)
+        cpu = {k: leg[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": N, "elements": n_elems, "precision": "FP32 inner CG, FP64 refinement",
+                   "t_window_ms": [W * prob["dt"], (W + K) * prob["dt"]],
+                   "l2": "flushed before every step (256 MiB write), per-step CUDA events on the instance stream",
+                   "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": p50, "p99": p99, "what": "one IMEX step of the whole slab"},
+        "roofline": roof, "kernels": kernels, "profile_steps": P,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+        "accuracy": acc, "fp64_gpu": fp64,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile-steps", type=int, default=200)
+    ap.add_argument("--fp64-steps", type=int, default=400)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * ep.h -- C ABI of the GB300 (sm_103a) monodomain IMEX step.
+ *
+ * One time step of the cardiac monodomain model as discretised in lifex-ep
+ * (Africa et al., arXiv 2308.01651, Sec. 1.2):
+ *   1. the ionic model at every mesh node, Eq. (4): states whose rate is
+ *      affine in themselves are taken implicitly, the others explicitly, so
+ *      the update is a direct division; then I_ion(u_EXT, w_{n+1}) at the
+ *      nodes (ionic current interpolation);
+ *   2. the linear system Eq. (6), (alpha_BDF/dt M + K) u_{n+1} =
+ *      M (u_BDF/dt - I_ion + I_app), with Q1 hexahedral mass and stiffness
+ *      matrices, K from the orthotropic tensor of Eq. (3).
+ * Everything runs in this library's CUDA kernels on one GPU; the library
+ * owns all device memory of an instance.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an ep_status; nothing aborts the process.  On any
+ *     status other than EP_OK, ep_last_error() returns a message (per host
+ *     thread) describing the failure.
+ *   - Input arrays are read during the call and copied; the caller keeps
+ *     ownership.  Output arrays are caller-owned host buffers.
+ *   - Units: ms, cm, mV (the Bueno-Orovio model's dimensionless potential u
+ *     is reported as 85.7 u - 84 mV, Sec. 3.2.3), mS/cm, 1/cm, uF/cm^2.
+ *   - An instance is used by one host thread at a time; its work is ordered
+ *     on its CUDA stream.
+ *
+ * Node numbering of the structured meshes: node (i, j, k) has index
+ * i + (nx+1) * (j + NY * k), with NY = ny + 1 for a slab and NY = ny for a
+ * shell (periodic in j).  Element (i, j, k) has local nodes a = ia + 2 ib +
+ * 4 ic at (i+ia, j+ib, k+ic).
+ */
+#ifndef EP_GB300_H
+#define EP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ep_instance ep_instance;
+
+typedef enum {
+    EP_OK = 0,
+    EP_EINVAL = 1,       /* an argument is invalid (message says which) */
+    EP_ENOMEM = 2,       /* device or host allocation failed */
+    EP_ENOCONV = 3,      /* the linear solver did not reach its tolerance */
+    EP_ENAN = 4,         /* a potential became non-finite */
+    EP_ETIMEOUT = 5,     /* a bounded device wait gave up */
+    EP_ECUDA = 6,        /* a CUDA runtime call failed */
+    EP_EUNSUPPORTED = 7  /* a valid request this build does not implement */
+} ep_status;
+
+enum { EP_MESH_SLAB = 0, EP_MESH_SHELL = 1 };
+enum { EP_MODEL_BO = 0, EP_MODEL_TTP06 = 1 };
+enum { EP_CELL_ENDO = 0, EP_CELL_MID = 1, EP_CELL_EPI = 2 };
+/* Arithmetic of the step.  FP64: every quantity in double, CG on the FP64
+ * operator.  FP32_REFINED: ionic gates, ionic current and the CG inner solve
+ * in float, inside FP64 iterative refinement (FP64 residual, dot products,
+ * solution update) with FP64 ionic concentrations. */
+enum { EP_PREC_FP64 = 0, EP_PREC_FP32_REFINED = 1 };
+/* FP32 inner operator of the refined solver. */
+enum { EP_OP_AUTO = 0, EP_OP_MATRIX_FREE = 1, EP_OP_STENCIL = 2 };
+
+/* Mesh (Sec. 1.2: Q1 hexahedra).
+ *   SLAB : the box [0,L0]x[0,L1]x[0,L2] split into nx x ny x nz equal
+ *          hexahedra; xyz is ignored.
+ *   SHELL: a structured hexahedral shell, nx elements across the wall, ny
+ *          around (periodic, ny >= 3), nz along; xyz holds the
+ *          n_nodes x 3 node coordinates (cm) in the numbering above.
+ * n_nodes must match the count implied by kind and sizes. */
+typedef struct {
+    int32_t kind;
+    int32_t nx, ny, nz;
+    double L[3];
+    const double* xyz;
+    int64_t n_nodes;
+} ep_mesh;
+
+/* Nodal fibre (f0) and sheet (s0) directions, n_nodes x 3 each (Eq. (3)).
+ * n0 is implied (orthonormal frame); the diffusion tensor at a quadrature
+ * point is dn I + (dl - dn) f f^T + (dt - dn) s s^T with f, s the Q1
+ * interpolants of f0, s0 (not renormalised). */
+typedef struct {
+    const double* f0;
+    const double* s0;
+} ep_fibers;
+
+/* Conductivities (Eq. (3)).  If is_D != 0, sigma_* are diffusivities in
+ * cm^2/ms; otherwise they are conductivities in mS/cm and the library
+ * rescales D = sigma / (chi_m C_m) (Sec. 1.1.2) with chi_m in 1/cm and C_m in
+ * uF/cm^2.  All must be positive and finite. */
+typedef struct {
+    double sigma_l, sigma_t, sigma_n;
+    double chi_m, Cm;
+    int32_t is_D;
+} ep_conductivities;
+
+/* Ionic model (Sec. 1.1.1): Bueno-Orovio minimal model (epicardial
+ * parameters) or ten Tusscher-Panfilov 2006.  cell_type is per node
+ * (EP_CELL_*), used by TTP06 only; NULL means all epicardial.  Initial state:
+ * BO rest (u = 0, v = w = 1, s = 0); TTP06 the epicardial values printed for
+ * the N-version benchmark (Sec. 3.2.1) for every cell type. */
+typedef struct {
+    int32_t model;
+    const uint8_t* cell_type;
+} ep_ionic_model;
+
+/* Applied current I_app (Sec. 1.1.2): pulse p adds amp (model units per ms:
+ * mV/ms for TTP06, 1/ms for BO) at the nodes where mask[node] != 0, on step
+ * n+1 when k0 < n+1 <= k0 + kd with k0 = round(t0/dt), kd = round(dur/dt),
+ * repeating every round(period/dt) steps when period > 0.  At most
+ * EP_MAX_PULSES pulses; each mask has n_nodes bytes. */
+#define EP_MAX_PULSES 4
+typedef struct {
+    double amp, t0, dur, period;
+    const uint8_t* mask;
+} ep_pulse;
+
+typedef struct {
+    int32_t n_pulses;
+    const ep_pulse* pulses;
+} ep_stimulus;
+
+/* Solver options.  dt > 0 (ms); bdf_order 1 or 2 (order 2 takes a BDF1 first
+ * step); tol: relative FP64 residual ||b - A u||_2 <= tol ||b||_2 (0 ->
+ * 1e-12 for FP64, 1e-10 for FP32_REFINED); max_iter: CG iterations (FP64) or
+ * inner iterations per refinement sweep (0 -> 1000 / 200); inner_tol:
+ * relative FP32 inner residual (0 -> 1e-4); max_sweeps: refinement sweeps
+ * (0 -> 8); op32: FP32 inner operator; cuda_stream: a cudaStream_t to order
+ * the instance's work on, or NULL for a stream the library creates. */
+typedef struct {
+    double dt;
+    int32_t bdf_order;
+    int32_t precision;
+    double tol;
+    int32_t max_iter;
+    double inner_tol;
+    int32_t max_sweeps;
+    int32_t op32;
+    void* cuda_stream;
+} ep_options;
+
+/* Per-step counters of the last completed step. */
+typedef struct {
+    int64_t step;           /* time level reached (t = step * dt) */
+    int32_t cg_iters;       /* FP64 CG iterations or total FP32 inner iterations */
+    int32_t sweeps;         /* refinement sweeps (0 for FP64) */
+    double relres;          /* final ||b - A u|| / ||b|| (FP64) */
+    int32_t op32;           /* FP32 operator in use (EP_OP_*) */
+    int32_t reserved;
+    size_t device_bytes;    /* device memory held by the instance */
+} ep_stats;
+
+/* Creates an instance: validates the inputs, copies them to the device,
+ * builds the FP64 mass and system stencils (2x2x2 Gauss-Legendre, Eq. (6)),
+ * the Jacobi diagonal and, for FP32_REFINED, the FP32 operator data.
+ * On success *out owns all device memory of the instance. */
+ep_status ep_create(const ep_mesh* mesh, const ep_fibers* fibers,
+                    const ep_conductivities* cond, const ep_ionic_model* ionic,
+                    const ep_stimulus* stim, const ep_options* opts,
+                    ep_instance** out);
+
+/* Advances n_steps >= 0 time steps and waits for them; returns EP_ENAN,
+ * EP_ENOCONV or EP_ETIMEOUT when a step failed (the instance then holds the
+ * state of the failing step and further steps are refused with the same
+ * status). */
+ep_status ep_step(ep_instance* inst, int64_t n_steps);
+/* Enqueues n_steps steps on the instance's stream without waiting. */
+ep_status ep_step_async(ep_instance* inst, int64_t n_steps);
+/* Waits for the enqueued steps and returns their status (as ep_step). */
+ep_status ep_sync(ep_instance* inst);
+
+/* Advances several instances by n_steps each, all enqueued before any wait;
+ * returns the first failing status (inst[k] order). */
+ep_status ep_step_batch(ep_instance* const* insts, int32_t n, int64_t n_steps);
+
+/* Copies u_n (mV) into out[0..n), n == n_nodes. */
+ep_status ep_read_potential(const ep_instance* inst, double* out_mV, int64_t n);
+/* Activation times (ms): time of the largest forward difference u_{n+1}-u_n
+ * seen so far (first maximum wins; Sec. 3.2.1), NaN where that largest slope
+ * never exceeded 1 mV/ms.  n == n_nodes. */
+ep_status ep_activation_times(const ep_instance* inst, double* out_ms, int64_t n);
+
+/* Checkpoint.  Layout of the buffer (all little-endian, doubles unaligned
+ * after the 64-byte header):
+ *   header: char magic[8] = "EPSTATE1"; int32 version (1); int32 model;
+ *           int64 n_nodes; int32 n_states; int32 bdf_order; int64 step;
+ *           double dt; int64 reserved[2];
+ *   double u_n[N], u_{n-1}[N]          (model units)
+ *   double w_n[S][N], w_{n-1}[S][N]    (state-major; S = 3 BO, 18 TTP06)
+ *   double at[N]                       (time of the largest slope, ms)
+ *   double best[N]                     (largest u_{n+1} - u_n, model units)
+ * ep_state_bytes gives the size.  ep_load_state requires the same model and
+ * n_nodes; it also resets the stimulus clock to the loaded step. */
+size_t ep_state_bytes(const ep_instance* inst);
+ep_status ep_save_state(const ep_instance* inst, void* buf, size_t bytes);
+ep_status ep_load_state(ep_instance* inst, const void* buf, size_t bytes);
+
+/* Device bytes an instance of this mesh, model and options would hold;
+ * 0 if the arguments are invalid. */
+size_t ep_footprint_bytes(const ep_mesh* mesh, const ep_ionic_model* ionic,
+                          const ep_options* opts);
+
+ep_status ep_get_stats(const ep_instance* inst, ep_stats* out);
+/* Device pointer to u_n (double, model units, n_nodes), valid until the
+ * next ep_step* call on the instance. */
+ep_status ep_potential_device(const ep_instance* inst, const double** out);
+
+/* Per-kernel timing.  While profiling is on, ep_step runs its loops from the
+ * host (no CUDA graph) and brackets every kernel launch with a pair of CUDA
+ * events on the instance's stream; the totals accumulate until reset.  The
+ * step time is then not representative, the kernel times are.  Kernel names:
+ * "ionic", "rhs", "resid", "p64", "apply64", "update64", "apply32_mf",
+ * "apply32_stencil", "update32", "correct", "finish", "realpha". */
+typedef struct {
+    char name[24];
+    int64_t launches;
+    double ms_total;
+} ep_kernel_time;
+ep_status ep_profile_enable(ep_instance* inst, int32_t on);
+/* Writes up to cap entries (kernels launched at least once) and their count
+ * to *n; reset != 0 clears the totals afterwards. */
+ep_status ep_profile_read(ep_instance* inst, ep_kernel_time* out, int32_t cap,
+                          int32_t* n, int32_t reset);
+
+/* Frees every resource of the instance (NULL is accepted). */
+ep_status ep_destroy(ep_instance* inst);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* ep_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

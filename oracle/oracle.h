@@ -135,6 +135,8 @@ void or_sim_set_state(or_sim* S, const double* u_n, const double* u_nm1,
 /* Activation times in ms (NaN where never activated) and the largest
  * forward difference seen so far. */
 void or_sim_get_activation(const or_sim* S, double* at, double* best);
+/* Same without the threshold: the time of the largest difference so far. */
+void or_sim_get_activation_raw(const or_sim* S, double* at, double* best);
 void or_sim_set_activation(or_sim* S, const double* at, const double* best);
 /* Ionic current at the last step, nodal. */
 void or_sim_get_iion(const or_sim* S, double* iion);

@@ -51,6 +51,7 @@ def lib():
         L.or_sim_set_state.argtypes = [vp, vp, vp, vp, vp, i64]
         L.or_sim_get_activation.argtypes = [vp, vp, vp]
         L.or_sim_set_activation.argtypes = [vp, vp, vp]
+        L.or_sim_get_activation_raw.argtypes = [vp, vp, vp]
         L.or_sim_get_iion.argtypes = [vp, vp]
         L.or_sim_matrix.argtypes = [vp]
         L.or_sim_matrix.restype = vp
@@ -189,6 +190,11 @@ class Sim:
     def activation(self):
         at, best = np.zeros(self.nn), np.zeros(self.nn)
         lib().or_sim_get_activation(self.h, _p(at), _p(best))
+        return at, best
+
+    def activation_raw(self):
+        at, best = np.zeros(self.nn), np.zeros(self.nn)
+        lib().or_sim_get_activation_raw(self.h, _p(at), _p(best))
         return at, best
 
     def set_activation(self, at, best):

@@ -242,6 +242,11 @@ void or_sim_get_activation(const or_sim* S, double* at, double* best) {
     }
 }
 
+void or_sim_get_activation_raw(const or_sim* S, double* at, double* best) {
+    memcpy(at, S->at, sizeof(double) * (size_t)S->nn);
+    memcpy(best, S->best, sizeof(double) * (size_t)S->nn);
+}
+
 void or_sim_set_activation(or_sim* S, const double* at, const double* best) {
     for (int64_t i = 0; i < S->nn; ++i) {
         S->at[i] = at[i];

@@ -1,0 +1,927 @@
+// ep_api.cu -- host side of the C ABI declared in include/ep.h.
+//
+// An instance owns its device memory and one CUDA graph holding a whole time
+// step: the fused ionic kernel, the FP64 right-hand side, the linear solve
+// with its loops as conditional WHILE nodes (loop control stays on the
+// device), and the activation/rotation kernel.  ep_step replays the graph.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ep_dev.cuh"
+#include "ionic_models.cuh"
+
+namespace epk {
+void launch_ionic(Dev* d, const Dev& h, int grid, cudaStream_t s);
+void launch_assemble(Dev* d, const Dev& h, const AsmParams& P, cudaStream_t s);
+void launch_realpha(Dev* d, const Dev& h, double delta, double alpha_dt, float cmass, cudaStream_t s);
+void launch_rhs(Dev* d, const Dev& h, int first, cudaStream_t s);
+void launch_p64(Dev* d, const Dev& h, int grid, cudaStream_t s);
+void launch_apply64(Dev* d, const Dev& h, cudaStream_t s);
+void launch_update64(Dev* d, const Dev& h, int grid, cudaStream_t s);
+void launch_apply32_stencil(Dev* d, const Dev& h, cudaStream_t s);
+void launch_apply32_mf(Dev* d, const Dev& h, cudaStream_t s);
+void launch_update32(Dev* d, const Dev& h, int grid, cudaStream_t s);
+void launch_correct(Dev* d, const Dev& h, int grid, cudaStream_t s);
+void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s);
+int mf_tiles(const Dev& h);
+cudaError_t mf_prepare();
+}  // namespace epk
+
+using epk::Dev;
+
+static thread_local std::string g_err;
+
+static ep_status fail(ep_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CUDA_TRY(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(e_ == cudaErrorMemoryAllocation ? EP_ENOMEM : EP_ECUDA,             \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                \
+    } while (0)
+
+struct ep_instance {
+    Dev h{};                   // host mirror of the device descriptor
+    Dev* d = nullptr;          // device descriptor
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    long long host_step = 0;   // step index of the next enqueued step
+    double alpha_dt_dev = 0;   // alpha/dt the device operators hold
+    int grid_nodes = 0;        // grid of the grid-stride node kernels
+    int grid_ionic = 0;
+    ep_status sticky = EP_OK;
+    int* bad = nullptr;        // device flag of the assembly
+    bool graph_mode = true;    // false: host-driven loops (EP_GRAPH=0), for debugging
+    // per-kernel event timing (ep_profile_enable)
+    bool profiling = false;
+    struct Pending { int id; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> free_events;
+    double prof_ms[16] = {0};
+    long long prof_n[16] = {0};
+};
+
+static const char* kKernelNames[] = {"ionic", "rhs", "resid", "p64", "apply64", "update64",
+                                     "apply32_mf", "apply32_stencil", "update32", "correct",
+                                     "finish", "realpha"};
+enum { K_IONIC, K_RHS, K_RESID, K_P64, K_APPLY64, K_UPDATE64, K_APPLY32MF, K_APPLY32ST, K_UPDATE32,
+       K_CORRECT, K_FINISH, K_REALPHA, K_COUNT };
+
+static cudaEvent_t prof_event(ep_instance* I) {
+    if (!I->free_events.empty()) {
+        cudaEvent_t e = I->free_events.back();
+        I->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launches f() bracketed by events when profiling.
+template <class F>
+static void timed(ep_instance* I, int id, F f) {
+    if (!I->profiling) {
+        f();
+        return;
+    }
+    ep_instance::Pending p{id, prof_event(I), prof_event(I)};
+    cudaEventRecord(p.a, I->stream);
+    f();
+    cudaEventRecord(p.b, I->stream);
+    I->pending.push_back(p);
+}
+
+// Folds completed event pairs into the totals (call after a stream sync).
+static void prof_resolve(ep_instance* I) {
+    for (auto& p : I->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            I->prof_ms[p.id] += ms;
+            I->prof_n[p.id] += 1;
+        }
+        I->free_events.push_back(p.a);
+        I->free_events.push_back(p.b);
+    }
+    I->pending.clear();
+}
+
+namespace {
+
+constexpr double kBOmV = 85.7, kBOoff = -84.0;
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+int64_t expected_nodes(const ep_mesh* m) {
+    if (m->kind == EP_MESH_SLAB) return (int64_t)(m->nx + 1) * (m->ny + 1) * (m->nz + 1);
+    return (int64_t)(m->nx + 1) * m->ny * (m->nz + 1);
+}
+
+template <class T>
+ep_status dalloc(ep_instance* I, T** p, size_t count) {
+    void* v = nullptr;
+    const size_t b = ((count * sizeof(T) + 255) / 256) * 256;
+    cudaError_t e = cudaMalloc(&v, b > 0 ? b : 256);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(EP_ENOMEM, "cudaMalloc of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    I->allocs.push_back(v);
+    I->bytes += b;
+    *p = static_cast<T*>(v);
+    return EP_OK;
+}
+
+struct Sizes {
+    int N, ns, ng32, ns64, prec, op32;
+    bool slab;
+};
+
+// Device bytes per instance; mirrors the allocations in ep_create.
+size_t footprint(const Sizes& z) {
+    auto al = [](size_t b) { return ((b + 255) / 256) * 256; };
+    const size_t N = (size_t)z.N;
+    size_t b = 0;
+    b += 3 * al(N * 8);                   // u_n, u_nm1, u_new
+    b += 2 * al(z.ng32 * N * 4);          // gates (refined)
+    b += 2 * al(z.ns64 * N * 8);          // FP64 states
+    b += al(N);                           // cell types
+    b += 3 * al(N * 8);                   // v, b, r
+    b += 2 * al(N * 8);                   // at, best
+    b += 2 * al(epk::kSlots * N * 8);     // M64, A64
+    b += al(N * 8);                       // dinv64
+    if (z.prec == EP_PREC_FP32_REFINED) {
+        b += al(N * 4);                   // dinv32
+        if (z.op32 == EP_OP_STENCIL) b += al(epk::kSlots * N * 4);
+        else b += al(6 * N * 4);          // fibres
+        b += 6 * al(N * 4);               // r32 z32 q32 d32 pa32 pb32
+    } else {
+        b += 4 * al(N * 8);               // z64 q64 pa64 pb64
+    }
+    const size_t blocks = (N + 255) / 256 + 1;
+    b += al(blocks * 4 * 8);              // partials
+    b += al(epk::CNT_N * 4);
+    b += al(sizeof(Dev)) + 256;
+    return b;
+}
+
+ep_status validate(const ep_mesh* mesh, const ep_fibers* fib, const ep_conductivities* cond,
+                   const ep_ionic_model* ionic, const ep_stimulus* stim, const ep_options* opts) {
+    if (!mesh || !fib || !cond || !ionic || !opts) return fail(EP_EINVAL, "NULL argument");
+    if (mesh->kind != EP_MESH_SLAB && mesh->kind != EP_MESH_SHELL) return fail(EP_EINVAL, "mesh.kind");
+    if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1) return fail(EP_EINVAL, "mesh sizes must be >= 1");
+    if (mesh->kind == EP_MESH_SHELL && mesh->ny < 3) return fail(EP_EINVAL, "shell needs ny >= 3");
+    const int64_t nn = expected_nodes(mesh);
+    if (nn > (int64_t)1 << 30) return fail(EP_EINVAL, "mesh too large for one instance (> 2^30 nodes)");
+    if (mesh->n_nodes != nn) return fail(EP_EINVAL, "mesh.n_nodes does not match the structured sizes");
+    if (mesh->kind == EP_MESH_SLAB) {
+        for (int d = 0; d < 3; ++d)
+            if (!finite_pos(mesh->L[d])) return fail(EP_EINVAL, "slab lengths must be positive");
+    } else if (!mesh->xyz) {
+        return fail(EP_EINVAL, "shell needs xyz");
+    }
+    if (!fib->f0 || !fib->s0) return fail(EP_EINVAL, "fibers.f0/s0 must be given");
+    if (!finite_pos(cond->sigma_l) || !finite_pos(cond->sigma_t) || !finite_pos(cond->sigma_n))
+        return fail(EP_EINVAL, "conductivities must be positive and finite");
+    if (!cond->is_D && (!finite_pos(cond->chi_m) || !finite_pos(cond->Cm)))
+        return fail(EP_EINVAL, "chi_m and Cm must be positive and finite");
+    if (ionic->model != EP_MODEL_BO && ionic->model != EP_MODEL_TTP06) return fail(EP_EINVAL, "ionic.model");
+    if (ionic->cell_type)
+        for (int64_t i = 0; i < nn; ++i)
+            if (ionic->cell_type[i] > EP_CELL_EPI) return fail(EP_EINVAL, "cell_type out of range");
+    if (stim) {
+        if (stim->n_pulses < 0 || stim->n_pulses > EP_MAX_PULSES)
+            return fail(EP_EINVAL, "stimulus.n_pulses must be in 0..4");
+        if (stim->n_pulses > 0 && !stim->pulses) return fail(EP_EINVAL, "stimulus.pulses is NULL");
+        for (int p = 0; p < stim->n_pulses; ++p) {
+            const ep_pulse& P = stim->pulses[p];
+            if (!P.mask) return fail(EP_EINVAL, "pulse mask is NULL");
+            if (!std::isfinite(P.amp) || !std::isfinite(P.t0) || !(P.dur >= 0) || !std::isfinite(P.period))
+                return fail(EP_EINVAL, "pulse parameters must be finite, dur >= 0");
+        }
+    }
+    if (!finite_pos(opts->dt)) return fail(EP_EINVAL, "options.dt must be positive");
+    if (opts->bdf_order != 1 && opts->bdf_order != 2) return fail(EP_EINVAL, "options.bdf_order must be 1 or 2");
+    if (opts->precision != EP_PREC_FP64 && opts->precision != EP_PREC_FP32_REFINED)
+        return fail(EP_EINVAL, "options.precision");
+    if (opts->op32 < EP_OP_AUTO || opts->op32 > EP_OP_STENCIL) return fail(EP_EINVAL, "options.op32");
+    if (opts->op32 == EP_OP_MATRIX_FREE && mesh->kind != EP_MESH_SLAB)
+        return fail(EP_EUNSUPPORTED, "the matrix-free FP32 operator needs a slab mesh");
+    if (opts->tol < 0 || opts->inner_tol < 0 || opts->max_iter < 0 || opts->max_sweeps < 0)
+        return fail(EP_EINVAL, "negative solver option");
+    return EP_OK;
+}
+
+Sizes sizes_of(const ep_mesh* mesh, const ep_ionic_model* ionic, const ep_options* opts) {
+    Sizes z{};
+    z.N = (int)expected_nodes(mesh);
+    z.ns = ionic->model == EP_MODEL_BO ? epk::kBOStates : epk::kTTGates + epk::kTTConc;
+    z.prec = opts->precision;
+    z.slab = mesh->kind == EP_MESH_SLAB;
+    z.op32 = opts->op32 == EP_OP_AUTO ? (z.slab ? EP_OP_MATRIX_FREE : EP_OP_STENCIL) : opts->op32;
+    if (z.prec == EP_PREC_FP32_REFINED) {
+        z.ng32 = ionic->model == EP_MODEL_BO ? epk::kBOStates : epk::kTTGates;
+        z.ns64 = ionic->model == EP_MODEL_BO ? 0 : epk::kTTConc;
+    } else {
+        z.ng32 = 0;
+        z.ns64 = z.ns;
+    }
+    return z;
+}
+
+double required_alpha_dt(const Dev& h, long long step) {
+    return ((h.bdf == 2 && step >= 1) ? 1.5 : 1.0) / h.dt;
+}
+
+// make sure the device operators hold alpha/dt of the step about to run
+void ensure_alpha(ep_instance* I) {
+    const double need = required_alpha_dt(I->h, I->host_step);
+    if (need != I->alpha_dt_dev) {
+        const float cmass = (float)(need * I->h.h[0] * I->h.h[1] * I->h.h[2]);
+        const double delta = need - I->alpha_dt_dev;
+        timed(I, K_REALPHA, [&] { epk::launch_realpha(I->d, I->h, delta, need, cmass, I->stream); });
+        I->alpha_dt_dev = need;
+    }
+}
+
+// ---- graph construction ------------------------------------------------------
+
+struct Capture {
+    cudaStream_t s;
+    cudaError_t err = cudaSuccess;
+    void chk(cudaError_t e) {
+        if (err == cudaSuccess && e != cudaSuccess) err = e;
+    }
+};
+
+// Adds a WHILE node at the current capture position of stream s, returns its
+// handle and body graph, and moves s past the node.
+cudaError_t add_while(cudaStream_t s, cudaGraphConditionalHandle* h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edata = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, &edata, &nd);
+    if (e != cudaSuccess) return e;
+    if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    e = cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = *h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, deps, edata, nd, &p);
+    if (e != cudaSuccess) return e;
+    *body = p.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+ep_status build_graph(ep_instance* I) {
+    Dev& h = I->h;
+    cudaStream_t s = I->stream;
+    cudaStream_t s2 = nullptr, s3 = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&s3, cudaStreamNonBlocking));
+    Capture C{s};
+    cudaGraphConditionalHandle h_loop = 0, h_outer = 0, h_inner = 0;
+    C.chk(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    epk::launch_ionic(I->d, h, I->grid_ionic, s);
+    epk::launch_rhs(I->d, h, 1, s);
+    cudaGraph_t body = nullptr, body2 = nullptr;
+    if (h.prec == EP_PREC_FP64) {
+        C.chk(add_while(s, &h_loop, &body));
+        if (C.err == cudaSuccess) {
+            C.chk(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            epk::launch_p64(I->d, h, I->grid_nodes, s2);
+            epk::launch_apply64(I->d, h, s2);
+            epk::launch_update64(I->d, h, I->grid_nodes, s2);
+            C.chk(cudaStreamEndCapture(s2, &body));
+        }
+    } else {
+        C.chk(add_while(s, &h_outer, &body));
+        if (C.err == cudaSuccess) {
+            C.chk(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            C.chk(add_while(s2, &h_inner, &body2));
+            if (C.err == cudaSuccess) {
+                C.chk(cudaStreamBeginCaptureToGraph(s3, body2, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+                if (h.op32 == EP_OP_MATRIX_FREE) epk::launch_apply32_mf(I->d, h, s3);
+                else epk::launch_apply32_stencil(I->d, h, s3);
+                epk::launch_update32(I->d, h, I->grid_nodes, s3);
+                C.chk(cudaStreamEndCapture(s3, &body2));
+            }
+            epk::launch_correct(I->d, h, I->grid_nodes, s2);
+            epk::launch_rhs(I->d, h, 0, s2);
+            C.chk(cudaStreamEndCapture(s2, &body));
+        }
+    }
+    epk::launch_finish(I->d, h, I->grid_nodes, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(s, &g);
+    C.chk(ee);
+    C.chk(cudaGetLastError());
+    cudaStreamDestroy(s2);
+    cudaStreamDestroy(s3);
+    if (C.err != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(EP_ECUDA, std::string("building the step graph: ") + cudaGetErrorString(C.err));
+    }
+    I->graph = g;
+    if ((h.prec == EP_PREC_FP64 && !h_loop) || (h.prec != EP_PREC_FP64 && (!h_outer || !h_inner)))
+        return fail(EP_ECUDA, "a conditional handle of the step graph is zero");
+    CUDA_TRY(cudaGraphInstantiate(&I->exec, g, 0));
+    // the conditional handles live in the device descriptor
+    h.h_loop = (unsigned long long)h_loop;
+    h.h_outer = (unsigned long long)h_outer;
+    h.h_inner = (unsigned long long)h_inner;
+    CUDA_TRY(cudaMemcpyAsync(&I->d->h_loop, &h.h_loop, 3 * sizeof(unsigned long long),
+                             cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return EP_OK;
+}
+
+// One step with the loop decisions read back by the host after every
+// iteration (no conditional graph nodes).  Bounded by the solver limits.
+ep_status step_host(ep_instance* I) {
+    const Dev& h = I->h;
+    cudaStream_t s = I->stream;
+    Dev* d = I->d;
+    auto flag = [&](int* p, int* out) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(out, p, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        return e;
+    };
+    timed(I, K_IONIC, [&] { epk::launch_ionic(d, h, I->grid_ionic, s); });
+    timed(I, K_RHS, [&] { epk::launch_rhs(d, h, 1, s); });
+    int f = 0;
+    if (h.prec == EP_PREC_FP64) {
+        CUDA_TRY(flag(&d->f_loop, &f));
+        for (int it = 0; f && it <= h.max_iter; ++it) {
+            timed(I, K_P64, [&] { epk::launch_p64(d, h, I->grid_nodes, s); });
+            timed(I, K_APPLY64, [&] { epk::launch_apply64(d, h, s); });
+            timed(I, K_UPDATE64, [&] { epk::launch_update64(d, h, I->grid_nodes, s); });
+            CUDA_TRY(cudaGetLastError());
+            CUDA_TRY(flag(&d->f_loop, &f));
+        }
+    } else {
+        CUDA_TRY(flag(&d->f_outer, &f));
+        for (int sw = 0; f && sw <= h.max_sweeps; ++sw) {
+            int fi = 1;
+            for (int it = 0; fi && it <= h.max_iter; ++it) {
+                if (h.op32 == EP_OP_MATRIX_FREE)
+                    timed(I, K_APPLY32MF, [&] { epk::launch_apply32_mf(d, h, s); });
+                else
+                    timed(I, K_APPLY32ST, [&] { epk::launch_apply32_stencil(d, h, s); });
+                timed(I, K_UPDATE32, [&] { epk::launch_update32(d, h, I->grid_nodes, s); });
+                CUDA_TRY(cudaGetLastError());
+                CUDA_TRY(flag(&d->f_inner, &fi));
+            }
+            timed(I, K_CORRECT, [&] { epk::launch_correct(d, h, I->grid_nodes, s); });
+            timed(I, K_RESID, [&] { epk::launch_rhs(d, h, 0, s); });
+            CUDA_TRY(cudaGetLastError());
+            CUDA_TRY(flag(&d->f_outer, &f));
+        }
+    }
+    timed(I, K_FINISH, [&] { epk::launch_finish(d, h, I->grid_nodes, s); });
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(s));
+    prof_resolve(I);
+    return EP_OK;
+}
+
+void free_all(ep_instance* I) {
+    for (auto& p : I->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : I->free_events) cudaEventDestroy(e);
+    if (I->exec) cudaGraphExecDestroy(I->exec);
+    if (I->graph) cudaGraphDestroy(I->graph);
+    for (void* p : I->allocs) cudaFree(p);
+    I->allocs.clear();
+    if (I->own_stream && I->stream) cudaStreamDestroy(I->stream);
+}
+
+ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conductivities* cond,
+                      const ep_ionic_model* ionic, const ep_stimulus* stim, const ep_options* opts,
+                      ep_instance* I) {
+    const Sizes z = sizes_of(mesh, ionic, opts);
+    Dev& h = I->h;
+    std::memset(&h, 0, sizeof(h));
+    const size_t N = (size_t)z.N;
+    h.kind = mesh->kind;
+    h.nx = mesh->nx;
+    h.ny = mesh->ny;
+    h.nz = mesh->nz;
+    h.NX = mesh->nx + 1;
+    h.NY = mesh->kind == EP_MESH_SHELL ? mesh->ny : mesh->ny + 1;
+    h.NZ = mesh->nz + 1;
+    h.periodic = mesh->kind == EP_MESH_SHELL;
+    h.N = z.N;
+    if (mesh->kind == EP_MESH_SLAB)
+        for (int d = 0; d < 3; ++d) h.h[d] = mesh->L[d] / (d == 0 ? mesh->nx : d == 1 ? mesh->ny : mesh->nz);
+    h.model = ionic->model;
+    h.prec = opts->precision;
+    h.bdf = opts->bdf_order;
+    h.ns = z.ns;
+    h.dt = opts->dt;
+    h.act_thr = ionic->model == EP_MODEL_BO ? 1.0 / kBOmV : 1.0;
+    h.op32 = z.op32;
+    const bool ref = h.prec == EP_PREC_FP32_REFINED;
+    h.tol = opts->tol > 0 ? opts->tol : (ref ? 1e-10 : 1e-12);
+    h.inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-4;
+    h.max_iter = opts->max_iter > 0 ? opts->max_iter : (ref ? 200 : 1000);
+    h.max_sweeps = opts->max_sweeps > 0 ? opts->max_sweeps : 8;
+
+    if (opts->cuda_stream) {
+        I->stream = (cudaStream_t)opts->cuda_stream;
+    } else {
+        CUDA_TRY(cudaStreamCreateWithFlags(&I->stream, cudaStreamNonBlocking));
+        I->own_stream = true;
+    }
+    ep_status st;
+#define ALLOC(ptr, n) \
+    if ((st = dalloc(I, &(ptr), (n))) != EP_OK) return st
+    ALLOC(h.u_n, N);
+    ALLOC(h.u_nm1, N);
+    ALLOC(h.u_new, N);
+    if (z.ng32) {
+        ALLOC(h.g32_n, z.ng32 * N);
+        ALLOC(h.g32_nm1, z.ng32 * N);
+    }
+    if (z.ns64) {
+        ALLOC(h.s64_n, z.ns64 * N);
+        ALLOC(h.s64_nm1, z.ns64 * N);
+    }
+    uint8_t* cell = nullptr;
+    ALLOC(cell, N);
+    h.cell = cell;
+    ALLOC(h.v, N);
+    ALLOC(h.b, N);
+    ALLOC(h.r, N);
+    ALLOC(h.at, N);
+    ALLOC(h.best, N);
+    ALLOC(h.M64, epk::kSlots * N);
+    ALLOC(h.A64, epk::kSlots * N);
+    ALLOC(h.dinv64, N);
+    if (ref) {
+        ALLOC(h.dinv32, N);
+        if (z.op32 == EP_OP_STENCIL) {
+            ALLOC(h.A32, epk::kSlots * N);
+        } else {
+            ALLOC(h.fib, 6 * N);
+        }
+        ALLOC(h.r32, N);
+        ALLOC(h.z32, N);
+        ALLOC(h.q32, N);
+        ALLOC(h.d32, N);
+        ALLOC(h.pa32, N);
+        ALLOC(h.pb32, N);
+    } else {
+        ALLOC(h.z64, N);
+        ALLOC(h.q64, N);
+        ALLOC(h.pa64, N);
+        ALLOC(h.pb64, N);
+    }
+    ALLOC(h.partial, ((N + 255) / 256 + 1) * 4);
+    ALLOC(h.counter, (size_t)epk::CNT_N);
+    ALLOC(I->d, 1);
+    // stimulus
+    h.npulses = stim ? stim->n_pulses : 0;
+    std::vector<uint8_t*> masks;
+    for (int p = 0; p < h.npulses; ++p) {
+        const ep_pulse& P = stim->pulses[p];
+        h.amp[p] = P.amp;
+        h.k0[p] = llround(P.t0 / h.dt);
+        h.kd[p] = llround(P.dur / h.dt);
+        h.kp[p] = P.period > 0 ? llround(P.period / h.dt) : 0;
+        uint8_t* m = nullptr;
+        ALLOC(m, N);
+        CUDA_TRY(cudaMemcpyAsync(m, P.mask, N, cudaMemcpyHostToDevice, I->stream));
+        h.mask[p] = m;
+    }
+
+    // ---- initial state ------------------------------------------------------
+    {
+        std::vector<uint8_t> ct(N, (uint8_t)EP_CELL_EPI);
+        if (ionic->cell_type) std::memcpy(ct.data(), ionic->cell_type, N);
+        CUDA_TRY(cudaMemcpyAsync(cell, ct.data(), N, cudaMemcpyHostToDevice, I->stream));
+        CUDA_TRY(cudaStreamSynchronize(I->stream));
+        const double u0 = h.model == EP_MODEL_BO ? 0.0 : epk::kTTInitialV;
+        std::vector<double> uv(N, u0);
+        CUDA_TRY(cudaMemcpy(h.u_n, uv.data(), N * 8, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(h.u_nm1, uv.data(), N * 8, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(h.u_new, uv.data(), N * 8, cudaMemcpyHostToDevice));
+        std::vector<double> w0(z.ns);
+        if (h.model == EP_MODEL_BO) {
+            w0 = {1.0, 1.0, 0.0};
+        } else {
+            for (int k = 0; k < z.ns; ++k) w0[k] = epk::tt_initial(k);
+        }
+        if (z.ng32) {
+            std::vector<float> g(z.ng32 * N);
+            for (int k = 0; k < z.ng32; ++k)
+                for (size_t n = 0; n < N; ++n) g[k * N + n] = (float)w0[k];
+            CUDA_TRY(cudaMemcpy(h.g32_n, g.data(), g.size() * 4, cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(h.g32_nm1, g.data(), g.size() * 4, cudaMemcpyHostToDevice));
+        }
+        if (z.ns64) {
+            const int off = ref ? z.ng32 : 0;
+            std::vector<double> c(z.ns64 * N);
+            for (int k = 0; k < z.ns64; ++k)
+                for (size_t n = 0; n < N; ++n) c[k * N + n] = w0[off + k];
+            CUDA_TRY(cudaMemcpy(h.s64_n, c.data(), c.size() * 8, cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(h.s64_nm1, c.data(), c.size() * 8, cudaMemcpyHostToDevice));
+        }
+        std::vector<double> nanv(N, NAN), ninf(N, -INFINITY);
+        CUDA_TRY(cudaMemcpy(h.at, nanv.data(), N * 8, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(h.best, ninf.data(), N * 8, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemset(h.counter, 0, epk::CNT_N * sizeof(unsigned int)));
+        CUDA_TRY(cudaMemset(h.v, 0, N * 8));
+    }
+
+    // ---- operators ----------------------------------------------------------
+    double dl = cond->sigma_l, dtr = cond->sigma_t, dn = cond->sigma_n;
+    if (!cond->is_D) {
+        const double s = 1.0 / (cond->chi_m * cond->Cm);  // Sec. 1.1.2: D = sigma/(chi_m C_m)
+        dl *= s;
+        dtr *= s;
+        dn *= s;
+    }
+    const double alpha_dt = required_alpha_dt(h, 0);
+    I->alpha_dt_dev = alpha_dt;
+    h.alpha_dt = alpha_dt;
+    if (h.kind == EP_MESH_SLAB) {
+        const double vol = h.h[0] * h.h[1] * h.h[2], w = vol / 8.0;
+        for (int d = 0; d < 3; ++d) h.mf_cn[d] = (float)(w * dn / (h.h[d] * h.h[d]));
+        h.mf_cl = (float)(w * (dl - dn));
+        h.mf_ct = (float)(w * (dtr - dn));
+        h.mf_cmass = (float)(alpha_dt * vol);
+    }
+    CUDA_TRY(cudaMemcpy(I->d, &h, sizeof(Dev), cudaMemcpyHostToDevice));
+    {
+        double *f0 = nullptr, *s0 = nullptr, *xyz = nullptr;
+        CUDA_TRY(cudaMalloc(&f0, N * 3 * 8));
+        cudaError_t e1 = cudaMalloc(&s0, N * 3 * 8);
+        cudaError_t e2 = h.kind == EP_MESH_SHELL ? cudaMalloc(&xyz, N * 3 * 8) : cudaSuccess;
+        int* bad = nullptr;
+        cudaError_t e3 = cudaMalloc(&bad, sizeof(int));
+        cudaError_t e = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
+        if (e == cudaSuccess) e = cudaMemcpy(f0, fib->f0, N * 24, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s0, fib->s0, N * 24, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && xyz) e = cudaMemcpy(xyz, mesh->xyz, N * 24, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(bad, 0, sizeof(int));
+        int bad_h = 0;
+        if (e == cudaSuccess) {
+            epk::AsmParams P{xyz, f0, s0, dl, dtr, dn, alpha_dt, h.A32 != nullptr, bad};
+            epk::launch_assemble(I->d, h, P, I->stream);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
+            if (e == cudaSuccess) e = cudaMemcpy(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost);
+        }
+        cudaFree(f0);
+        cudaFree(s0);
+        if (xyz) cudaFree(xyz);
+        if (bad) cudaFree(bad);
+        if (e != cudaSuccess) return fail(EP_ECUDA, std::string("assembly: ") + cudaGetErrorString(e));
+        if (bad_h) return fail(EP_EINVAL, "mesh has an element with non-positive Jacobian determinant");
+    }
+    if (h.fib) {
+        std::vector<float> f(6 * N);
+        for (size_t n = 0; n < N; ++n)
+            for (int c = 0; c < 3; ++c) {
+                f[c * N + n] = (float)(fib->f0[3 * n + c] / h.h[c]);
+                f[(3 + c) * N + n] = (float)(fib->s0[3 * n + c] / h.h[c]);
+            }
+        CUDA_TRY(cudaMemcpy(h.fib, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+        CUDA_TRY(epk::mf_prepare());
+    }
+    const int blocks = (int)((N + epk::kNodeThreads - 1) / epk::kNodeThreads);
+    I->grid_nodes = blocks < 4096 ? blocks : 4096;
+    I->grid_ionic = blocks;
+    const char* env = std::getenv("EP_GRAPH");
+    I->graph_mode = !(env && env[0] == '0');
+    if (!I->graph_mode) return EP_OK;
+    return build_graph(I);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ep_last_error(void) { return g_err.c_str(); }
+
+size_t ep_footprint_bytes(const ep_mesh* mesh, const ep_ionic_model* ionic, const ep_options* opts) {
+    if (!mesh || !ionic || !opts) return 0;
+    if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1) return 0;
+    if (ionic->model != EP_MODEL_BO && ionic->model != EP_MODEL_TTP06) return 0;
+    if (opts->precision != EP_PREC_FP64 && opts->precision != EP_PREC_FP32_REFINED) return 0;
+    const int64_t nn = expected_nodes(mesh);
+    if (nn > (int64_t)1 << 30) return 0;
+    size_t b = footprint(sizes_of(mesh, ionic, opts));
+    return b;
+}
+
+ep_status ep_create(const ep_mesh* mesh, const ep_fibers* fibers, const ep_conductivities* cond,
+                    const ep_ionic_model* ionic, const ep_stimulus* stim, const ep_options* opts,
+                    ep_instance** out) {
+    if (!out) return fail(EP_EINVAL, "out is NULL");
+    *out = nullptr;
+    ep_status st = validate(mesh, fibers, cond, ionic, stim, opts);
+    if (st != EP_OK) return st;
+    ep_instance* I = new (std::nothrow) ep_instance();
+    if (!I) return fail(EP_ENOMEM, "host allocation failed");
+    st = create_impl(mesh, fibers, cond, ionic, stim, opts, I);
+    if (st != EP_OK) {
+        (void)cudaGetLastError();
+        free_all(I);
+        delete I;
+        return st;
+    }
+    *out = I;
+    return EP_OK;
+}
+
+ep_status ep_step_async(ep_instance* I, int64_t n_steps) {
+    if (!I) return fail(EP_EINVAL, "instance is NULL");
+    if (n_steps < 0) return fail(EP_EINVAL, "n_steps < 0");
+    if (I->sticky != EP_OK) return fail(I->sticky, "instance failed earlier: " + std::to_string(I->sticky));
+    for (int64_t k = 0; k < n_steps; ++k) {
+        ensure_alpha(I);
+        if (I->graph_mode && !I->profiling) {
+            CUDA_TRY(cudaGraphLaunch(I->exec, I->stream));
+        } else {
+            ep_status st = step_host(I);
+            if (st != EP_OK) return st;
+        }
+        I->host_step += 1;
+    }
+    CUDA_TRY(cudaGetLastError());
+    return EP_OK;
+}
+
+ep_status ep_sync(ep_instance* I) {
+    if (!I) return fail(EP_EINVAL, "instance is NULL");
+    int status = 0;
+    CUDA_TRY(cudaMemcpyAsync(&status, &I->d->status, sizeof(int), cudaMemcpyDeviceToHost, I->stream));
+    CUDA_TRY(cudaStreamSynchronize(I->stream));
+    if (status != EP_OK) {
+        I->sticky = (ep_status)status;
+        long long step = 0;
+        (void)cudaMemcpy(&step, &I->d->step, sizeof(step), cudaMemcpyDeviceToHost);
+        const char* what = status == EP_ENAN ? "non-finite potential"
+                           : status == EP_ENOCONV ? "linear solver did not converge"
+                                                  : "device error";
+        return fail((ep_status)status, std::string(what) + " (time level " + std::to_string(step) + ")");
+    }
+    return EP_OK;
+}
+
+ep_status ep_step(ep_instance* I, int64_t n_steps) {
+    ep_status st = ep_step_async(I, n_steps);
+    if (st != EP_OK) return st;
+    return ep_sync(I);
+}
+
+ep_status ep_step_batch(ep_instance* const* insts, int32_t n, int64_t n_steps) {
+    if (!insts || n < 0) return fail(EP_EINVAL, "bad batch");
+    for (int32_t k = 0; k < n; ++k) {
+        ep_status st = ep_step_async(insts[k], n_steps);
+        if (st != EP_OK) return st;
+    }
+    ep_status first = EP_OK;
+    std::string msg;
+    for (int32_t k = 0; k < n; ++k) {
+        ep_status st = ep_sync(insts[k]);
+        if (st != EP_OK && first == EP_OK) {
+            first = st;
+            msg = g_err;
+        }
+    }
+    if (first != EP_OK) return fail(first, msg);
+    return EP_OK;
+}
+
+ep_status ep_read_potential(const ep_instance* I, double* out, int64_t n) {
+    if (!I || !out) return fail(EP_EINVAL, "NULL argument");
+    if (n != I->h.N) return fail(EP_EINVAL, "n must equal n_nodes");
+    Dev tmp;
+    CUDA_TRY(cudaMemcpyAsync(&tmp, I->d, sizeof(Dev), cudaMemcpyDeviceToHost, I->stream));
+    CUDA_TRY(cudaStreamSynchronize(I->stream));
+    CUDA_TRY(cudaMemcpy(out, tmp.u_n, (size_t)n * 8, cudaMemcpyDeviceToHost));
+    if (I->h.model == EP_MODEL_BO)
+        for (int64_t i = 0; i < n; ++i) out[i] = kBOmV * out[i] + kBOoff;
+    return EP_OK;
+}
+
+ep_status ep_activation_times(const ep_instance* I, double* out, int64_t n) {
+    if (!I || !out) return fail(EP_EINVAL, "NULL argument");
+    if (n != I->h.N) return fail(EP_EINVAL, "n must equal n_nodes");
+    CUDA_TRY(cudaStreamSynchronize(I->stream));
+    std::vector<double> best((size_t)n);
+    CUDA_TRY(cudaMemcpy(out, I->h.at, (size_t)n * 8, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(best.data(), I->h.best, (size_t)n * 8, cudaMemcpyDeviceToHost));
+    const double thr = I->h.act_thr * I->h.dt;
+    for (int64_t i = 0; i < n; ++i)
+        if (!(best[i] > thr)) out[i] = NAN;
+    return EP_OK;
+}
+
+size_t ep_state_bytes(const ep_instance* I) {
+    if (!I) return 0;
+    const size_t N = (size_t)I->h.N;
+    return 64 + 8 * N * (2 + 2 * (size_t)I->h.ns + 2);
+}
+
+struct StateHeader {
+    char magic[8];
+    int32_t version, model;
+    int64_t n_nodes;
+    int32_t n_states, bdf_order;
+    int64_t step;
+    double dt;
+    int64_t reserved[2];
+};
+static_assert(sizeof(StateHeader) == 64, "state header is 64 bytes");
+
+ep_status ep_save_state(const ep_instance* I, void* buf, size_t bytes) {
+    if (!I || !buf) return fail(EP_EINVAL, "NULL argument");
+    const size_t need = ep_state_bytes(I);
+    if (bytes < need) return fail(EP_EINVAL, "buffer too small: need " + std::to_string(need));
+    Dev t;
+    CUDA_TRY(cudaMemcpyAsync(&t, I->d, sizeof(Dev), cudaMemcpyDeviceToHost, I->stream));
+    CUDA_TRY(cudaStreamSynchronize(I->stream));
+    const size_t N = (size_t)I->h.N;
+    const int ns = I->h.ns;
+    StateHeader H{};
+    std::memcpy(H.magic, "EPSTATE1", 8);
+    H.version = 1;
+    H.model = I->h.model;
+    H.n_nodes = (int64_t)N;
+    H.n_states = ns;
+    H.bdf_order = I->h.bdf;
+    H.step = t.step;
+    H.dt = I->h.dt;
+    char* p = static_cast<char*>(buf);
+    std::memcpy(p, &H, 64);
+    double* o = reinterpret_cast<double*>(p + 64);
+    std::vector<double> tmp(N);
+    auto get = [&](const double* d, double* dst) -> cudaError_t {
+        cudaError_t e = cudaMemcpy(tmp.data(), d, N * 8, cudaMemcpyDeviceToHost);
+        std::memcpy(dst, tmp.data(), N * 8);
+        return e;
+    };
+    CUDA_TRY(get(t.u_n, o));
+    CUDA_TRY(get(t.u_nm1, o + N));
+    const bool ref = I->h.prec == EP_PREC_FP32_REFINED;
+    const int ng32 = ref ? (I->h.model == EP_MODEL_BO ? 3 : epk::kTTGates) : 0;
+    std::vector<float> f(N);
+    for (int lvl = 0; lvl < 2; ++lvl) {
+        double* dst = o + 2 * N + (size_t)lvl * ns * N;
+        for (int k = 0; k < ns; ++k) {
+            if (k < ng32) {
+                const float* src = (lvl == 0 ? t.g32_n : t.g32_nm1) + (size_t)k * N;
+                CUDA_TRY(cudaMemcpy(f.data(), src, N * 4, cudaMemcpyDeviceToHost));
+                for (size_t n = 0; n < N; ++n) tmp[n] = f[n];
+                std::memcpy(dst + (size_t)k * N, tmp.data(), N * 8);
+            } else {
+                const double* src = (lvl == 0 ? t.s64_n : t.s64_nm1) + (size_t)(k - ng32) * N;
+                CUDA_TRY(get(src, dst + (size_t)k * N));
+            }
+        }
+    }
+    CUDA_TRY(get(t.at, o + (2 + 2 * (size_t)ns) * N));
+    CUDA_TRY(get(t.best, o + (3 + 2 * (size_t)ns) * N));
+    return EP_OK;
+}
+
+ep_status ep_load_state(ep_instance* I, const void* buf, size_t bytes) {
+    if (!I || !buf) return fail(EP_EINVAL, "NULL argument");
+    const size_t need = ep_state_bytes(I);
+    if (bytes < need) return fail(EP_EINVAL, "buffer too small");
+    StateHeader H;
+    std::memcpy(&H, buf, 64);
+    if (std::memcmp(H.magic, "EPSTATE1", 8) != 0 || H.version != 1) return fail(EP_EINVAL, "not an EPSTATE1 buffer");
+    if (H.model != I->h.model || H.n_nodes != I->h.N || H.n_states != I->h.ns)
+        return fail(EP_EINVAL, "state buffer is for a different model or mesh");
+    if (H.step < 0) return fail(EP_EINVAL, "negative step");
+    CUDA_TRY(cudaStreamSynchronize(I->stream));
+    Dev t;
+    CUDA_TRY(cudaMemcpy(&t, I->d, sizeof(Dev), cudaMemcpyDeviceToHost));
+    const size_t N = (size_t)I->h.N;
+    const int ns = I->h.ns;
+    const double* o = reinterpret_cast<const double*>(static_cast<const char*>(buf) + 64);
+    std::vector<double> tmp(N);
+    auto put = [&](double* d, const double* src) -> cudaError_t {
+        std::memcpy(tmp.data(), src, N * 8);
+        return cudaMemcpy(d, tmp.data(), N * 8, cudaMemcpyHostToDevice);
+    };
+    CUDA_TRY(put(t.u_n, o));
+    CUDA_TRY(put(t.u_nm1, o + N));
+    const bool ref = I->h.prec == EP_PREC_FP32_REFINED;
+    const int ng32 = ref ? (I->h.model == EP_MODEL_BO ? 3 : epk::kTTGates) : 0;
+    std::vector<float> f(N);
+    for (int lvl = 0; lvl < 2; ++lvl) {
+        const double* src = o + 2 * N + (size_t)lvl * ns * N;
+        for (int k = 0; k < ns; ++k) {
+            if (k < ng32) {
+                std::memcpy(tmp.data(), src + (size_t)k * N, N * 8);
+                for (size_t n = 0; n < N; ++n) f[n] = (float)tmp[n];
+                CUDA_TRY(cudaMemcpy((lvl == 0 ? t.g32_n : t.g32_nm1) + (size_t)k * N, f.data(), N * 4,
+                                    cudaMemcpyHostToDevice));
+            } else {
+                CUDA_TRY(put((lvl == 0 ? t.s64_n : t.s64_nm1) + (size_t)(k - ng32) * N, src + (size_t)k * N));
+            }
+        }
+    }
+    CUDA_TRY(put(t.at, o + (2 + 2 * (size_t)ns) * N));
+    CUDA_TRY(put(t.best, o + (3 + 2 * (size_t)ns) * N));
+    long long step = H.step;
+    int zero = 0;
+    CUDA_TRY(cudaMemcpy(&I->d->step, &step, sizeof(step), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(&I->d->status, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    I->host_step = step;
+    I->sticky = EP_OK;
+    return EP_OK;
+}
+
+ep_status ep_get_stats(const ep_instance* I, ep_stats* out) {
+    if (!I || !out) return fail(EP_EINVAL, "NULL argument");
+    Dev t;
+    CUDA_TRY(cudaMemcpyAsync(&t, I->d, sizeof(Dev), cudaMemcpyDeviceToHost, I->stream));
+    CUDA_TRY(cudaStreamSynchronize(I->stream));
+    out->step = t.step;
+    out->cg_iters = t.last_iters;
+    out->sweeps = t.last_sweeps;
+    out->relres = t.last_relres;
+    out->op32 = I->h.prec == EP_PREC_FP32_REFINED ? I->h.op32 : 0;
+    out->reserved = 0;
+    out->device_bytes = I->bytes;
+    return EP_OK;
+}
+
+ep_status ep_potential_device(const ep_instance* I, const double** out) {
+    if (!I || !out) return fail(EP_EINVAL, "NULL argument");
+    Dev t;
+    CUDA_TRY(cudaMemcpyAsync(&t, I->d, sizeof(Dev), cudaMemcpyDeviceToHost, I->stream));
+    CUDA_TRY(cudaStreamSynchronize(I->stream));
+    *out = t.u_n;
+    return EP_OK;
+}
+
+ep_status ep_profile_enable(ep_instance* I, int32_t on) {
+    if (!I) return fail(EP_EINVAL, "instance is NULL");
+    CUDA_TRY(cudaStreamSynchronize(I->stream));
+    prof_resolve(I);
+    I->profiling = on != 0;
+    return EP_OK;
+}
+
+ep_status ep_profile_read(ep_instance* I, ep_kernel_time* out, int32_t cap, int32_t* n, int32_t reset) {
+    if (!I || !n || (cap > 0 && !out)) return fail(EP_EINVAL, "NULL argument");
+    CUDA_TRY(cudaStreamSynchronize(I->stream));
+    prof_resolve(I);
+    int32_t k = 0;
+    for (int id = 0; id < K_COUNT; ++id) {
+        if (I->prof_n[id] == 0) continue;
+        if (k < cap) {
+            std::memset(out[k].name, 0, sizeof(out[k].name));
+            std::strncpy(out[k].name, kKernelNames[id], sizeof(out[k].name) - 1);
+            out[k].launches = I->prof_n[id];
+            out[k].ms_total = I->prof_ms[id];
+        }
+        ++k;
+    }
+    *n = k;
+    if (reset)
+        for (int id = 0; id < K_COUNT; ++id) {
+            I->prof_ms[id] = 0.0;
+            I->prof_n[id] = 0;
+        }
+    return EP_OK;
+}
+
+ep_status ep_destroy(ep_instance* I) {
+    if (!I) return EP_OK;
+    if (I->stream) cudaStreamSynchronize(I->stream);
+    free_all(I);
+    delete I;
+    return EP_OK;
+}
+
+}  // extern "C"

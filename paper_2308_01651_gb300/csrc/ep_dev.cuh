@@ -1,0 +1,209 @@
+// ep_dev.cuh -- device-side instance descriptor and shared helpers of the
+// GB300 monodomain step library (see include/ep.h for the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ep.h"
+
+namespace epk {
+
+// Symmetric 27-point stencil of a structured Q1 mesh, stored as the diagonal
+// (slot 0) and the 13 "forward" neighbour couplings (slots 1..13) of every
+// node; the 13 backward couplings of node n are the forward couplings stored
+// at its neighbours.  Offset t = (di+1) + 3 (dj+1) + 9 (dk+1) in 0..26, the
+// centre is t = 13; forward offsets are t > 13 (slot t - 13), a backward
+// offset t < 13 is slot 13 - t of the neighbour n + off(t).
+constexpr int kSlots = 14;
+
+constexpr int kTTGates = 13;  // m h j xr1 xr2 xs s r d f f2 fCass RR
+constexpr int kTTConc = 5;    // Cai CaSR CaSS Nai Ki
+constexpr int kBOStates = 3;  // v w s
+
+// threads per block of the node-wise kernels
+constexpr int kNodeThreads = 256;
+constexpr int kNodesPerThread = 4;
+constexpr int kNodeTile = kNodeThreads * kNodesPerThread;
+// nodes per block of the stencil kernels
+constexpr int kStencilThreads = 256;
+
+// Matrix-free FP32 tile (owned nodes per block): 32 x 8 x 4
+constexpr int kMfTx = 32, kMfTy = 8, kMfTz = 4;
+constexpr int kMfThreads = 256;
+
+struct Dev {
+    // ---- mesh ---------------------------------------------------------
+    int kind;
+    int nx, ny, nz;      // elements
+    int NX, NY, NZ;      // nodes per direction (NY = ny for the periodic shell)
+    int periodic;        // j periodic
+    int N;               // nodes
+    double h[3];         // slab spacing (cm)
+    // ---- model / time -----------------------------------------------------
+    int model;
+    int prec;            // EP_PREC_*
+    int bdf;
+    int ns;              // ionic states (3 BO, 18 TTP06)
+    double dt;
+    double act_thr;      // activation slope threshold, model units per ms
+    long long step;      // current time level n
+    // ---- stimulus ------------------------------------------------------------
+    int npulses;
+    double amp[EP_MAX_PULSES];
+    long long k0[EP_MAX_PULSES], kd[EP_MAX_PULSES], kp[EP_MAX_PULSES];
+    const uint8_t* mask[EP_MAX_PULSES];
+    // ---- state ---------------------------------------------------------------
+    double *u_n, *u_nm1, *u_new;
+    float *g32_n, *g32_nm1;     // FP32 gates [ng][N] (FP32_REFINED)
+    double *s64_n, *s64_nm1;    // FP64 states [ns64][N]: all states (FP64) or
+                                // the TTP06 concentrations (FP32_REFINED)
+    const uint8_t* cell;
+    double *v;                  // u_BDF/dt - I_ion + I_app
+    double *b, *r;              // FP64 right-hand side and residual
+    double *at, *best;
+    // ---- operators -----------------------------------------------------------
+    double *M64, *A64;          // [kSlots][N]
+    double *dinv64;
+    float *A32;                 // [kSlots][N] (stencil FP32 operator)
+    float *dinv32;
+    float *fib;                 // [6][N]: f0/h, s0/h per component (matrix-free)
+    float mf_cn[3], mf_cl, mf_ct, mf_cmass;
+    double alpha_dt;            // alpha_BDF/dt the operators currently hold
+    int op32;                   // EP_OP_MATRIX_FREE or EP_OP_STENCIL
+    // ---- CG ------------------------------------------------------------------
+    float *r32, *z32, *q32, *d32, *pa32, *pb32;
+    double *z64, *q64, *pa64, *pb64;
+    double rz, pq, alpha, beta, rr, rr0, bb, relres;
+    double tol, inner_tol;
+    int max_iter, max_sweeps;
+    int it, it_total, sweeps;
+    int pswap;                  // 0: p_old = pa, p_new = pb; 1: swapped
+    int status;                 // ep_status of the running step (sticky)
+    int last_iters, last_sweeps;
+    double last_relres;
+    long long done_step;
+    // ---- reductions --------------------------------------------------------
+    double* partial;            // per-block partial sums
+    unsigned int* counter;      // last-block counters, one per kernel kind
+    unsigned long long h_loop;  // conditional handles (cudaGraphConditionalHandle)
+    unsigned long long h_inner;
+    unsigned long long h_outer;
+    int f_loop, f_inner, f_outer;  // the same loop decisions, for host-driven stepping
+};
+
+// Inputs of the create-time assembly kernel.
+struct AsmParams {
+    const double* xyz;  // shell coordinates [N][3] (NULL for slabs)
+    const double* f0;   // [N][3]
+    const double* s0;   // [N][3]
+    double dl, dt, dn;  // diffusivities (cm^2/ms)
+    double alpha_dt;    // alpha/dt of the system matrix A = alpha/dt M + K
+    int want32;         // also produce the FP32 stencil
+    int* bad;           // set to 1 on a non-positive Jacobian determinant
+};
+
+// Counter slots (one per reducing kernel so that consecutive kernels never
+// share a counter).
+enum { CNT_RHS = 0, CNT_APPLY = 1, CNT_UPDATE = 2, CNT_RESID = 3, CNT_FINISH = 4, CNT_N = 8 };
+
+// ---------------------------------------------------------------- helpers --
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sums NV values over the block (fixed order), then over all blocks of the
+// grid: every block writes its sums to partial[blk*NV + k]; the last block
+// to arrive (global atomic counter) reduces all partials in a fixed order and
+// runs finish(totals) with thread 0.  Deterministic: the result does not
+// depend on which block arrives last.  No block waits on another.
+template <int NV, class F>
+__device__ void grid_reduce(double (&v)[NV], double* partial, unsigned int* counter,
+                            int blk, int nblk, F finish) {
+    __shared__ double sh[NV][32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const double s = warp_sum(v[k]);
+        if (lane == 0) sh[k][warp] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = lane < nwarp ? sh[k][lane] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0) partial[(size_t)blk * NV + k] = s;
+        }
+        if (lane == 0) {
+            __threadfence();
+            const unsigned int t = atomicAdd(counter, 1u);
+            last = (t == (unsigned int)(nblk - 1));
+        }
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += __ldcg(&partial[(size_t)i * NV + k]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const double s = warp_sum(acc[k]);
+        if (lane == 0) sh[k][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nwarp; ++w) s += sh[k][w];
+            tot[k] = s;
+        }
+        *counter = 0u;
+        finish(tot);
+        __threadfence();
+    }
+}
+
+// Records a loop decision: in the graph's conditional node (when the step
+// runs as a CUDA graph) and in the descriptor (for host-driven stepping).
+__device__ __forceinline__ void set_cond(unsigned long long h, int* flag, unsigned int v) {
+    *flag = (int)v;
+    if (h) cudaGraphSetConditional((cudaGraphConditionalHandle)h, v);
+}
+
+// Node (i, j, k) of index n, and the neighbour at offset slot t (0..26);
+// returns -1 where the neighbour does not exist.
+__device__ __forceinline__ void node_ijk(const Dev& D, int n, int& i, int& j, int& k) {
+    const int nxy = D.NX * D.NY;
+    k = n / nxy;
+    const int rem = n - k * nxy;
+    j = rem / D.NX;
+    i = rem - j * D.NX;
+}
+
+__device__ __forceinline__ int neighbour(const Dev& D, int i, int j, int k, int di, int dj, int dk) {
+    const int ii = i + di, kk = k + dk;
+    int jj = j + dj;
+    if (ii < 0 || ii >= D.NX || kk < 0 || kk >= D.NZ) return -1;
+    if (D.periodic) {
+        jj = jj < 0 ? jj + D.NY : (jj >= D.NY ? jj - D.NY : jj);
+    } else if (jj < 0 || jj >= D.NY) {
+        return -1;
+    }
+    return ii + D.NX * (jj + D.NY * kk);
+}
+
+}  // namespace epk

@@ -1,0 +1,90 @@
+// k_cg.cu -- pointwise kernels of the FP32 inner CG, the FP64 refinement
+// correction and the end of a time step.
+//
+// The inner solver is Jacobi-preconditioned CG (the paper solves Eq. (6) with
+// CG, Sec. 2) on A delta = r in float; iterative refinement in double wraps
+// it (the FP64 residual is k_rhs with first = 0).  Activation time follows
+// Sec. 3.2.1: the time at which du/dt is largest, taken as the first maximum
+// of the forward difference u_{n+1} - u_n.
+#include "ep_dev.cuh"
+
+namespace epk {
+
+// delta += alpha p, r -= alpha q, z = D^-1 r; beta, inner convergence
+__global__ void __launch_bounds__(kNodeThreads) k_update32(Dev* __restrict__ Dp) {
+    Dev& D = *Dp;
+    const float alpha = (float)D.alpha;
+    const float* __restrict__ p = D.pswap ? D.pa32 : D.pb32;  // the p written by the apply
+    double v[2] = {0.0, 0.0};
+    float rz = 0.0f, rr = 0.0f;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x) {
+        D.d32[n] = fmaf(alpha, p[n], D.d32[n]);
+        const float r = fmaf(-alpha, D.q32[n], D.r32[n]);
+        D.r32[n] = r;
+        const float z = D.dinv32[n] * r;
+        D.z32[n] = z;
+        rz = fmaf(r, z, rz);
+        rr = fmaf(r, r, rr);
+    }
+    v[0] = rz;
+    v[1] = rr;
+    grid_reduce<2>(v, D.partial, D.counter + CNT_UPDATE, blockIdx.x, gridDim.x, [&](double* tot) {
+        D.beta = tot[0] / D.rz;
+        D.rz = tot[0];
+        D.rr = tot[1];
+        D.it += 1;
+        D.it_total += 1;
+        D.pswap ^= 1;
+        const bool nan = !(tot[1] == tot[1]);
+        const bool conv = !nan && tot[1] <= D.inner_tol * D.inner_tol * D.rr0;
+        if (nan && D.status == EP_OK) D.status = EP_ENAN;
+        set_cond(D.h_inner, &D.f_inner, (!conv && !nan && D.it < D.max_iter) ? 1u : 0u);
+    });
+}
+
+// u_new += delta (FP64 refinement update)
+__global__ void __launch_bounds__(kNodeThreads) k_correct(Dev* __restrict__ Dp) {
+    const Dev& D = *Dp;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x)
+        D.u_new[n] += (double)D.d32[n];
+}
+
+// Activation update, non-finite check, rotation of the time levels.
+__global__ void __launch_bounds__(kNodeThreads) k_finish(Dev* __restrict__ Dp) {
+    Dev& D = *Dp;
+    const double t_new = (double)(D.step + 1) * D.dt;
+    double v[1] = {0.0};
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x) {
+        const double un = D.u_new[n];
+        const double s = un - D.u_n[n];
+        if (!isfinite(un)) v[0] += 1.0;
+        if (s > D.best[n]) {
+            D.best[n] = s;
+            D.at[n] = t_new;
+        }
+    }
+    grid_reduce<1>(v, D.partial, D.counter + CNT_FINISH, blockIdx.x, gridDim.x, [&](double* tot) {
+        if (tot[0] > 0.0 && D.status == EP_OK) D.status = EP_ENAN;
+        double* t = D.u_nm1;
+        D.u_nm1 = D.u_n;
+        D.u_n = D.u_new;
+        D.u_new = t;
+        float* g = D.g32_nm1;
+        D.g32_nm1 = D.g32_n;
+        D.g32_n = g;
+        double* c = D.s64_nm1;
+        D.s64_nm1 = D.s64_n;
+        D.s64_n = c;
+        D.step += 1;
+        D.done_step = D.step;
+        D.last_iters = D.prec == EP_PREC_FP32_REFINED ? D.it_total : D.it;
+        D.last_sweeps = D.prec == EP_PREC_FP32_REFINED ? D.sweeps : 0;
+        D.last_relres = D.relres;
+    });
+}
+
+void launch_update32(Dev* d, const Dev& h, int grid, cudaStream_t s) { k_update32<<<grid, kNodeThreads, 0, s>>>(d); }
+void launch_correct(Dev* d, const Dev& h, int grid, cudaStream_t s) { k_correct<<<grid, kNodeThreads, 0, s>>>(d); }
+void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s) { k_finish<<<grid, kNodeThreads, 0, s>>>(d); }
+
+}  // namespace epk

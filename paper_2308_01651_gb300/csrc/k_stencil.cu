@@ -1,0 +1,376 @@
+// k_stencil.cu -- assembled 27-point operators of structured Q1 meshes.
+//
+// Paper Sec. 1.2, Eq. (6): M_jk = int phi_k phi_j, K_jk = int D grad phi_k .
+// grad phi_j with D of Eq. (3); integrals by 2x2x2 Gauss-Legendre, the
+// minimum rule that integrates the Q1 mass matrix exactly.  The diffusion
+// tensor at a quadrature point is dn I + (dl - dn) f f^T + (dt - dn) s s^T,
+// f and s the Q1 interpolants of the nodal fibre vectors.
+//
+// Like the paper, the FP64 matrices are assembled once (the paper notes the
+// system matrix never changes and only the right-hand side is rebuilt each
+// step, Sec. 3.4); here they are node-major 27-point stencils (diagonal + 13
+// forward couplings per node, the backward ones read from the neighbours)
+// rather than distributed CSR, because on GB300 the FP64 arithmetic of a
+// matrix-free apply would cost far more than streaming the stencil.
+//
+// Kernels: assembly (node-centric, deterministic, no atomics), the FP64
+// right-hand side / residual, the FP64 CG apply and updates, and the FP32
+// stencil apply of the refined inner solver.
+#include "ep_dev.cuh"
+
+namespace epk {
+
+// ---------------------------------------------------------------- assembly --
+
+__device__ void node_coords(const Dev& D, const AsmParams& P, int i, int j, int k, double x[3]) {
+    if (P.xyz) {
+        const int jj = D.periodic ? (j % D.NY) : j;
+        const size_t n = (size_t)i + (size_t)D.NX * ((size_t)jj + (size_t)D.NY * k);
+        x[0] = P.xyz[3 * n];
+        x[1] = P.xyz[3 * n + 1];
+        x[2] = P.xyz[3 * n + 2];
+    } else {
+        x[0] = i * D.h[0];
+        x[1] = j * D.h[1];
+        x[2] = k * D.h[2];
+    }
+}
+
+// Row a of the element mass and stiffness matrices of element (ei, ej, ek).
+__device__ void element_row(const Dev& D, const AsmParams& P, int ei, int ej, int ek, int a,
+                            double Mrow[8], double Krow[8], bool& bad) {
+    double X[8][3], F[8][3], S[8][3];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int bi = ei + (b & 1), bj = ej + ((b >> 1) & 1), bk = ek + ((b >> 2) & 1);
+        node_coords(D, P, bi, bj, bk, X[b]);
+        const int bjj = D.periodic ? (bj % D.NY) : bj;
+        const size_t n = (size_t)bi + (size_t)D.NX * ((size_t)bjj + (size_t)D.NY * bk);
+        for (int c = 0; c < 3; ++c) {
+            F[b][c] = P.f0[3 * n + c];
+            S[b][c] = P.s0[3 * n + c];
+        }
+    }
+    for (int b = 0; b < 8; ++b) Mrow[b] = Krow[b] = 0.0;
+    const double r3 = 0.57735026918962576451;  // 1/sqrt(3)
+    const double gp[2] = {0.5 - 0.5 * r3, 0.5 + 0.5 * r3};
+    const int a0 = a & 1, a1 = (a >> 1) & 1, a2 = (a >> 2) & 1;
+    for (int q = 0; q < 8; ++q) {
+        const double xi[3] = {gp[q & 1], gp[(q >> 1) & 1], gp[(q >> 2) & 1]};
+        double Lv[3][2], phi[8], dphi[8][3];
+        for (int d = 0; d < 3; ++d) {
+            Lv[d][0] = 1.0 - xi[d];
+            Lv[d][1] = xi[d];
+        }
+        for (int b = 0; b < 8; ++b) {
+            const int b0 = b & 1, b1 = (b >> 1) & 1, b2 = (b >> 2) & 1;
+            const double s0 = b0 ? 1.0 : -1.0, s1 = b1 ? 1.0 : -1.0, s2 = b2 ? 1.0 : -1.0;
+            phi[b] = Lv[0][b0] * Lv[1][b1] * Lv[2][b2];
+            dphi[b][0] = s0 * Lv[1][b1] * Lv[2][b2];
+            dphi[b][1] = Lv[0][b0] * s1 * Lv[2][b2];
+            dphi[b][2] = Lv[0][b0] * Lv[1][b1] * s2;
+        }
+        double J[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double s = 0.0;
+                for (int b = 0; b < 8; ++b) s += X[b][r] * dphi[b][c];
+                J[r][c] = s;
+            }
+        // cofactor matrix C (C[r][c] = cofactor of J[r][c]); inv(J) = C^T / det
+        double C[3][3];
+        C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+        C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+        C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+        C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+        C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+        C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+        if (!(det > 0.0)) bad = true;
+        // physical gradient: grad phi = J^{-T} dphi; (J^{-T})[i][j] = C[i][j]/det
+        double G[8][3];
+        for (int b = 0; b < 8; ++b)
+            for (int i = 0; i < 3; ++i)
+                G[b][i] = (C[i][0] * dphi[b][0] + C[i][1] * dphi[b][1] + C[i][2] * dphi[b][2]) / det;
+        double fq[3] = {0, 0, 0}, sq[3] = {0, 0, 0};
+        for (int b = 0; b < 8; ++b)
+            for (int c = 0; c < 3; ++c) {
+                fq[c] += phi[b] * F[b][c];
+                sq[c] += phi[b] * S[b][c];
+            }
+        const double w = 0.125 * det;
+        // D G_a
+        double Dg[3];
+        for (int i = 0; i < 3; ++i) {
+            const double fg = fq[0] * G[a][0] + fq[1] * G[a][1] + fq[2] * G[a][2];
+            const double sg = sq[0] * G[a][0] + sq[1] * G[a][1] + sq[2] * G[a][2];
+            Dg[i] = P.dn * G[a][i] + (P.dl - P.dn) * fg * fq[i] + (P.dt - P.dn) * sg * sq[i];
+        }
+        const double pa = phi[a];
+        for (int b = 0; b < 8; ++b) {
+            Mrow[b] += w * pa * phi[b];
+            Krow[b] += w * (Dg[0] * G[b][0] + Dg[1] * G[b][1] + Dg[2] * G[b][2]);
+        }
+    }
+    (void)a0; (void)a1; (void)a2;
+}
+
+__global__ void __launch_bounds__(128) k_assemble(Dev* __restrict__ Dp, AsmParams P) {
+    const Dev& D = *Dp;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= D.N) return;
+    int i, j, k;
+    node_ijk(D, n, i, j, k);
+    double cm[kSlots], ck[kSlots];
+    for (int s = 0; s < kSlots; ++s) cm[s] = ck[s] = 0.0;
+    bool bad = false;
+    for (int ec = 0; ec < 2; ++ec)
+        for (int eb = 0; eb < 2; ++eb)
+            for (int ea = 0; ea < 2; ++ea) {
+                const int gi = i - 1 + ea, gk = k - 1 + ec;
+                int gj = j - 1 + eb;
+                if (gi < 0 || gi >= D.nx || gk < 0 || gk >= D.nz) continue;
+                if (D.periodic) {
+                    if (gj < 0) gj += D.ny;
+                } else if (gj < 0 || gj >= D.ny) {
+                    continue;
+                }
+                const int a0 = 1 - ea, a1 = 1 - eb, a2 = 1 - ec;
+                const int a = a0 + 2 * a1 + 4 * a2;
+                double Mrow[8], Krow[8];
+                element_row(D, P, gi, gj, gk, a, Mrow, Krow, bad);
+                for (int b = 0; b < 8; ++b) {
+                    const int di = (b & 1) - a0, dj = ((b >> 1) & 1) - a1, dk = ((b >> 2) & 1) - a2;
+                    const int t = (di + 1) + 3 * (dj + 1) + 9 * (dk + 1);
+                    if (t >= 13) {
+                        cm[t - 13] += Mrow[b];
+                        ck[t - 13] += Krow[b];
+                    }
+                }
+            }
+    if (bad) *P.bad = 1;
+    for (int s = 0; s < kSlots; ++s) {
+        const double av = ck[s] + P.alpha_dt * cm[s];
+        D.M64[(size_t)s * D.N + n] = cm[s];
+        D.A64[(size_t)s * D.N + n] = av;
+        if (P.want32) D.A32[(size_t)s * D.N + n] = (float)av;
+    }
+    const double dinv = 1.0 / (ck[0] + P.alpha_dt * cm[0]);
+    D.dinv64[n] = dinv;
+    if (D.dinv32) D.dinv32[n] = (float)dinv;
+}
+
+// A <- A + (alpha_new/dt - alpha_old/dt) M  when the BDF order changes.
+__global__ void k_realpha(Dev* __restrict__ Dp, double delta, double alpha_dt, float cmass) {
+    Dev& D = *Dp;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        D.alpha_dt = alpha_dt;
+        D.mf_cmass = cmass;
+    }
+    if (n >= D.N) return;
+    for (int s = 0; s < kSlots; ++s) {
+        const size_t o = (size_t)s * D.N + n;
+        const double av = D.A64[o] + delta * D.M64[o];
+        D.A64[o] = av;
+        if (D.A32) D.A32[o] = (float)av;
+    }
+    const double dinv = 1.0 / D.A64[n];
+    D.dinv64[n] = dinv;
+    if (D.dinv32) D.dinv32[n] = (float)dinv;
+}
+
+// ---------------------------------------------------------------- applies --
+
+// y = (stencil c) x at node n = (i, j, k); XF(m) returns x at node m.
+template <typename C, typename Acc, class XF>
+__device__ __forceinline__ Acc stencil_apply(const Dev& D, const C* __restrict__ c, int n, int i,
+                                             int j, int k, XF xf) {
+    const size_t N = (size_t)D.N;
+    Acc acc = (Acc)c[n] * xf(n);
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+        if (t == 13) continue;
+        const int di = t % 3 - 1, dj = (t / 3) % 3 - 1, dk = t / 9 - 1;
+        const int m = neighbour(D, i, j, k, di, dj, dk);
+        if (m < 0) continue;
+        const Acc cv = (t > 13) ? (Acc)c[(size_t)(t - 13) * N + n] : (Acc)c[(size_t)(13 - t) * N + m];
+        acc += cv * xf(m);
+    }
+    return acc;
+}
+
+// FP64 right-hand side and initial residual (first == 1), or residual only
+// (first == 0):  b = M v,  r = b - A u_new.  Also forms the preconditioned
+// residual for the next solver stage and the reductions it needs.
+template <bool REF>
+__global__ void __launch_bounds__(kStencilThreads) k_rhs(Dev* __restrict__ Dp, int first) {
+    Dev& D = *Dp;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (n < D.N) {
+        int i, j, k;
+        node_ijk(D, n, i, j, k);
+        const double* __restrict__ vv = D.v;
+        const double* __restrict__ u = D.u_new;
+        double b;
+        if (first) {
+            b = stencil_apply<double, double>(D, D.M64, n, i, j, k, [&](int m) { return vv[m]; });
+            D.b[n] = b;
+        } else {
+            b = D.b[n];
+        }
+        const double au = stencil_apply<double, double>(D, D.A64, n, i, j, k, [&](int m) { return u[m]; });
+        const double r = b - au;
+        D.r[n] = r;
+        v[0] = b * b;
+        v[1] = r * r;
+        if (REF) {
+            const float r32 = (float)r;
+            const float z = D.dinv32[n] * r32;
+            D.r32[n] = r32;
+            D.z32[n] = z;
+            D.d32[n] = 0.0f;
+            v[2] = (double)r32 * (double)z;
+            v[3] = (double)r32 * (double)r32;
+        } else {
+            const double z = D.dinv64[n] * r;
+            D.z64[n] = z;
+            v[2] = r * z;
+        }
+    }
+    grid_reduce<4>(v, D.partial, D.counter + CNT_RHS, blockIdx.x, gridDim.x, [&](double* tot) {
+        if (first) D.bb = tot[0];
+        const double rr = tot[1], bb = D.bb;
+        const bool nan = !(rr == rr);
+        const bool conv = !nan && (rr <= D.tol * D.tol * bb);
+        D.relres = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+        if (nan && D.status == EP_OK) D.status = EP_ENAN;
+        D.it = 0;
+        D.beta = 0.0;
+        D.rz = tot[2];
+        if (REF) {
+            D.rr0 = tot[3];
+            D.rr = tot[3];
+            if (first) {
+                D.sweeps = 0;
+                D.it_total = 0;
+            } else {
+                D.sweeps += 1;
+                if (!conv && D.sweeps >= D.max_sweeps && D.status == EP_OK) D.status = EP_ENOCONV;
+            }
+            set_cond(D.h_outer, &D.f_outer, (!conv && !nan && D.sweeps < D.max_sweeps) ? 1u : 0u);
+            // the next inner loop starts enabled (its handle belongs to the
+            // refinement body, which is where the residual kernel runs)
+            if (first) D.f_inner = 1;
+            else set_cond(D.h_inner, &D.f_inner, 1u);
+        } else {
+            D.rr = rr;
+            set_cond(D.h_loop, &D.f_loop, (!conv && !nan) ? 1u : 0u);
+        }
+    });
+}
+
+// FP64 CG: p = z + beta p (beta == 0: p = z)
+__global__ void __launch_bounds__(kNodeThreads) k_p64(Dev* __restrict__ Dp) {
+    const Dev& D = *Dp;
+    const double beta = D.beta;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x)
+        D.pa64[n] = beta == 0.0 ? D.z64[n] : D.z64[n] + beta * D.pa64[n];
+}
+
+// FP64 CG: q = A p, alpha = rz / (p, q)
+__global__ void __launch_bounds__(kStencilThreads) k_apply64(Dev* __restrict__ Dp) {
+    Dev& D = *Dp;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[1] = {0.0};
+    if (n < D.N) {
+        int i, j, k;
+        node_ijk(D, n, i, j, k);
+        const double* __restrict__ p = D.pa64;
+        const double q = stencil_apply<double, double>(D, D.A64, n, i, j, k, [&](int m) { return p[m]; });
+        D.q64[n] = q;
+        v[0] = p[n] * q;
+    }
+    grid_reduce<1>(v, D.partial, D.counter + CNT_APPLY, blockIdx.x, gridDim.x,
+                   [&](double* tot) { D.alpha = D.rz / tot[0]; });
+}
+
+// FP64 CG: x += alpha p, r -= alpha q, z = D^-1 r; beta, convergence
+__global__ void __launch_bounds__(kNodeThreads) k_update64(Dev* __restrict__ Dp) {
+    Dev& D = *Dp;
+    const double alpha = D.alpha;
+    double v[2] = {0.0, 0.0};
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x) {
+        D.u_new[n] += alpha * D.pa64[n];
+        const double r = D.r[n] - alpha * D.q64[n];
+        D.r[n] = r;
+        const double z = D.dinv64[n] * r;
+        D.z64[n] = z;
+        v[0] += r * z;
+        v[1] += r * r;
+    }
+    grid_reduce<2>(v, D.partial, D.counter + CNT_UPDATE, blockIdx.x, gridDim.x, [&](double* tot) {
+        D.beta = tot[0] / D.rz;
+        D.rz = tot[0];
+        D.rr = tot[1];
+        D.it += 1;
+        const bool nan = !(tot[1] == tot[1]);
+        const bool conv = !nan && tot[1] <= D.tol * D.tol * D.bb;
+        D.relres = D.bb > 0.0 ? sqrt(tot[1] / D.bb) : sqrt(tot[1]);
+        if (nan && D.status == EP_OK) D.status = EP_ENAN;
+        if (!conv && D.it >= D.max_iter && D.status == EP_OK) D.status = EP_ENOCONV;
+        set_cond(D.h_loop, &D.f_loop, (!conv && !nan && D.it < D.max_iter) ? 1u : 0u);
+    });
+}
+
+// FP32 inner CG, stencil operator: p_new = z + beta p_old at every node the
+// row touches, q = A32 p_new; alpha = rz / (p_new, q).
+__global__ void __launch_bounds__(kStencilThreads) k_apply32_stencil(Dev* __restrict__ Dp) {
+    Dev& D = *Dp;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const float* __restrict__ pold = D.pswap ? D.pb32 : D.pa32;
+    float* __restrict__ pnew = D.pswap ? D.pa32 : D.pb32;
+    const float beta = (float)D.beta;
+    const float* __restrict__ z = D.z32;
+    double v[1] = {0.0};
+    if (n < D.N) {
+        int i, j, k;
+        node_ijk(D, n, i, j, k);
+        auto pf = [&](int m) { return beta == 0.0f ? z[m] : fmaf(beta, pold[m], z[m]); };
+        const float q = stencil_apply<float, float>(D, D.A32, n, i, j, k, pf);
+        const float pn = pf(n);
+        pnew[n] = pn;
+        D.q32[n] = q;
+        v[0] = (double)(pn * q);
+    }
+    grid_reduce<1>(v, D.partial, D.counter + CNT_APPLY, blockIdx.x, gridDim.x,
+                   [&](double* tot) { D.alpha = D.rz / tot[0]; });
+}
+
+void launch_assemble(Dev* d, const Dev& h, const AsmParams& P, cudaStream_t s) {
+    k_assemble<<<(h.N + 127) / 128, 128, 0, s>>>(d, P);
+}
+void launch_realpha(Dev* d, const Dev& h, double delta, double alpha_dt, float cmass, cudaStream_t s) {
+    k_realpha<<<(h.N + 255) / 256, 256, 0, s>>>(d, delta, alpha_dt, cmass);
+}
+void launch_rhs(Dev* d, const Dev& h, int first, cudaStream_t s) {
+    const int grid = (h.N + kStencilThreads - 1) / kStencilThreads;
+    if (h.prec == EP_PREC_FP32_REFINED) k_rhs<true><<<grid, kStencilThreads, 0, s>>>(d, first);
+    else k_rhs<false><<<grid, kStencilThreads, 0, s>>>(d, first);
+}
+void launch_p64(Dev* d, const Dev& h, int grid, cudaStream_t s) { k_p64<<<grid, kNodeThreads, 0, s>>>(d); }
+void launch_apply64(Dev* d, const Dev& h, cudaStream_t s) {
+    k_apply64<<<(h.N + kStencilThreads - 1) / kStencilThreads, kStencilThreads, 0, s>>>(d);
+}
+void launch_update64(Dev* d, const Dev& h, int grid, cudaStream_t s) {
+    k_update64<<<grid, kNodeThreads, 0, s>>>(d);
+}
+void launch_apply32_stencil(Dev* d, const Dev& h, cudaStream_t s) {
+    k_apply32_stencil<<<(h.N + kStencilThreads - 1) / kStencilThreads, kStencilThreads, 0, s>>>(d);
+}
+
+}  // namespace epk

@@ -1,0 +1,107 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every function include/ep.h declares, validates arguments before touching the
+device, and reports footprints."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2308_01651_gb300 import ep
+from paper_2308_01651_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "ep.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ep_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_function():
+    L = ep.lib()
+    names = header_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(ep.EXPORTS) == names
+
+
+def _args(prob, **kw):
+    pulses = [dict(p, mask=prob["masks"][k]) for k, p in enumerate(prob["pulses"])]
+    return (prob["mesh"], prob["f0"], prob["s0"], prob["cond"], prob["model"]), dict(
+        cell_type=prob["cell"], pulses=pulses, dt=prob["dt"], bdf_order=prob["bdf"], **kw)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dt=0.0), dict(dt=-1.0), dict(bdf_order=3), dict(precision=7), dict(op32=9),
+    dict(max_iter=-1), dict(tol=-1.0),
+])
+def test_create_rejects_bad_options(bad):
+    prob = I.slab_bo_small(nx=4, ny=3, nz=2, L=(0.2, 0.15, 0.1))
+    a, kw = _args(prob)
+    kw.update(bad)
+    with pytest.raises(ep.EpError) as e:
+        ep.ep_create(*a, **kw)
+    assert e.value.status == ep.EP_EINVAL
+
+
+def test_create_rejects_bad_mesh_and_inputs():
+    prob = I.slab_bo_small(nx=4, ny=3, nz=2, L=(0.2, 0.15, 0.1))
+    a, kw = _args(prob)
+    m = dict(prob["mesh"])
+    m["n_nodes"] = 7
+    m.pop("xyz")
+    with pytest.raises(ep.EpError) as e:
+        ep.ep_create(m, *a[1:], **kw)
+    assert e.value.status == ep.EP_EINVAL and "n_nodes" in str(e.value)
+    cond = dict(prob["cond"], sigma=(1e-3, -1.0, 1e-3))
+    with pytest.raises(ep.EpError) as e:
+        ep.ep_create(a[0], a[1], a[2], cond, a[4], **kw)
+    assert e.value.status == ep.EP_EINVAL
+    with pytest.raises(ep.EpError) as e:
+        ep.ep_create(a[0], a[1], a[2], a[3], 5, **kw)
+    assert e.value.status == ep.EP_EINVAL
+    bad_cell = np.full(prob["mesh"]["xyz"].shape[0], 9, dtype=np.uint8)
+    kw2 = dict(kw, cell_type=bad_cell)
+    with pytest.raises(ep.EpError) as e:
+        ep.ep_create(*a, **kw2)
+    assert e.value.status == ep.EP_EINVAL
+    kw3 = dict(kw, pulses=kw["pulses"] * 5)
+    with pytest.raises(ep.EpError) as e:
+        ep.ep_create(*a, **kw3)
+    assert e.value.status == ep.EP_EINVAL
+    # the matrix-free operator needs an axis-aligned slab
+    m, geo = I.shell_mesh(2, 8, 4)
+    f0, s0 = I.shell_helix_fibres(geo)
+    with pytest.raises(ep.EpError) as e:
+        ep.ep_create(m, f0, s0, prob["cond"], I.TTP06, precision=ep.EP_PREC_FP32_REFINED,
+                     op32=ep.EP_OP_MATRIX_FREE)
+    assert e.value.status == ep.EP_EUNSUPPORTED
+
+
+def test_footprint_scales_with_nodes():
+    small = I.slab_mesh(10, 10, 10, (0.1, 0.1, 0.1))
+    big = I.slab_mesh(20, 20, 20, (0.2, 0.2, 0.2))
+    for prec in (ep.EP_PREC_FP64, ep.EP_PREC_FP32_REFINED):
+        a = ep.ep_footprint_bytes(small, I.TTP06, precision=prec)
+        b = ep.ep_footprint_bytes(big, I.TTP06, precision=prec)
+        assert a > 0 and 6.5 < b / a < 8.5
+    assert ep.ep_footprint_bytes(small, 9) == 0
+    # the refined path stores the TTP06 gates in float: smaller footprint
+    assert ep.ep_footprint_bytes(big, I.TTP06, precision=ep.EP_PREC_FP32_REFINED) < \
+        ep.ep_footprint_bytes(big, I.TTP06, precision=ep.EP_PREC_FP64)
+
+
+def test_state_pack_roundtrip():
+    n, ns = 11, 18
+    g = I.rng(3)
+    arrs = [g.normal(size=n), g.normal(size=n), g.normal(size=(ns, n)), g.normal(size=(ns, n)),
+            g.normal(size=n), g.normal(size=n)]
+    buf = ep.state_pack(1, 2, 0.05, 17, *arrs)
+    assert buf.size == 64 + 8 * n * (4 + 2 * ns)
+    st = ep.state_unpack(buf)
+    assert st["step"] == 17 and st["model"] == 1 and st["dt"] == 0.05
+    for k, name in enumerate(["u_n", "u_nm1", "w_n", "w_nm1", "at", "best"]):
+        assert np.array_equal(st[name], arrs[k])

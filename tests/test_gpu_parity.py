@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances:
+  * FP64 path, one step from an identical state: max |du| / max |u| <= 1e-10
+    (both solve Eq. (6) to a relative residual of 1e-12; the gap is rounding
+    order and the CG stopping point).
+  * FP32_REFINED path, one step: the FP64 residual is driven to 1e-10 and the
+    ionic update runs in float, so relative 1e-6 on u.
+  * Trajectories: activation times within one time step (FP64) and 0.5 ms
+    (refined); u within 1 mV outside +-2 steps of each node's upstroke.
+"""
+import numpy as np
+import pytest
+
+import oracle.oracle as O
+from paper_2308_01651_gb300 import ep
+from paper_2308_01651_gb300 import inputs as I
+
+from .helpers import gpu_state, oracle_to_gpu, rel_err, synthetic_front_state
+
+pytestmark = pytest.mark.gpu
+
+FP64, REF = ep.EP_PREC_FP64, ep.EP_PREC_FP32_REFINED
+
+
+def small_ttp06(nx=24, ny=9, nz=6, bdf=2, T=20.0, dt=0.05):
+    h = 0.01
+    p = I.slab_ttp06(nx=nx, ny=ny, nz=nz, L=(nx * h, ny * h, nz * h), T=T, bdf=bdf, dt=dt)
+    return p
+
+
+def one_step_from(prob, sim, precision, **opts):
+    inst = ep.Instance(prob, precision=precision, **opts)
+    oracle_to_gpu(sim, inst, prob)
+    inst.step(1)
+    sim.step(1)
+    g = gpu_state(inst)
+    u_n, _, w_n, _ = sim.get_state()
+    at_raw, best = sim.activation_raw()
+    inst.close()
+    return g, u_n, w_n, best
+
+
+@pytest.mark.parametrize("kind", ["bo", "ttp06"])
+@pytest.mark.parametrize("precision,tol", [(FP64, 1e-10), (REF, 1e-6)])
+def test_single_step_after_oracle_run(kind, precision, tol):
+    """Run the oracle into the upstroke, inject its state, take one step on
+    both sides."""
+    if kind == "bo":
+        prob = I.slab_bo_small(nx=12, ny=7, nz=5, L=(0.6, 0.35, 0.25))
+        k = 30
+    else:
+        prob = small_ttp06()
+        k = 60
+    sim = O.sim_from_problem(prob)
+    sim.step(k)
+    g, u, w, best = one_step_from(prob, sim, precision)
+    assert g["step"] == k + 1
+    assert rel_err(g["u_n"], u) <= tol
+    for s in range(w.shape[0]):
+        assert rel_err(g["w_n"][s], w[s]) <= max(tol, 1e-6 if precision == REF else tol), s
+    assert rel_err(g["best"], best) <= max(tol * 1e3, 1e-7)
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (2, 1, 3), (37, 11, 7), (33, 9, 5), (64, 16, 8)])
+@pytest.mark.parametrize("precision", [FP64, REF])
+def test_single_step_synthetic_ragged(dims, precision):
+    """Seeded synthetic front on meshes that are smaller than, equal to and
+    ragged against the kernel tiles."""
+    nx, ny, nz = dims
+    prob = small_ttp06(nx=nx, ny=ny, nz=nz)
+    g = I.rng(500 + nx)
+    u_n, u_nm1, w_n, w_nm1 = synthetic_front_state(prob, g)
+    sim = O.sim_from_problem(prob)
+    sim.set_state(u_n, u_nm1, w_n, w_nm1, 7)
+    gg, u, w, best = one_step_from(prob, sim, precision)
+    tol = 1e-10 if precision == FP64 else 1e-6
+    assert rel_err(gg["u_n"], u) <= tol
+
+
+@pytest.mark.parametrize("op32", [ep.EP_OP_MATRIX_FREE, ep.EP_OP_STENCIL])
+def test_refined_operators_agree(op32):
+    prob = small_ttp06(nx=40, ny=12, nz=8)
+    g = I.rng(77)
+    u_n, u_nm1, w_n, w_nm1 = synthetic_front_state(prob, g)
+    sim = O.sim_from_problem(prob)
+    sim.set_state(u_n, u_nm1, w_n, w_nm1, 3)
+    gg, u, w, best = one_step_from(prob, sim, REF, op32=op32)
+    assert rel_err(gg["u_n"], u) <= 1e-6
+
+
+def test_shell_single_step():
+    m, geo = I.shell_mesh(3, 16, 8)
+    f0, s0 = I.shell_helix_fibres(geo)
+    i, j, k = I.node_ijk(m)
+    prob = I.problem(m, f0, s0, I.cond_sigma(1.4, 0.5, 0.25), I.TTP06, 0.05, 2, 10.0,
+                     [dict(amp=35.714, t0=0.0, dur=2.0)], [(k <= 1).astype(np.uint8)],
+                     cell=I.depth_celltype(i, 3))
+    g = I.rng(33)
+    sim = O.sim_from_problem(prob)
+    sim.step(25)
+    for precision, tol in ((FP64, 1e-10), (REF, 1e-6)):
+        s2 = O.sim_from_problem(prob)
+        u_n, u_nm1, w_n, w_nm1 = sim.get_state()
+        s2.set_state(u_n, u_nm1, w_n, w_nm1, sim.stepindex)
+        gg, u, w, best = one_step_from(prob, s2, precision)
+        assert rel_err(gg["u_n"], u) <= tol
+
+
+def test_trajectory_bo_fp64_and_refined():
+    """The Bueno-Orovio slab (1386 nodes, BDF1, 100 ms): FP64 activation
+    times equal the oracle's to one step; refined ones within 0.5 ms."""
+    prob = I.slab_bo_small()
+    sim = O.sim_from_problem(prob)
+    sim.step(prob["nsteps"])
+    at_ref, _ = sim.activation()
+    u_ref = sim.potential()
+    for precision in (FP64, REF):
+        inst = ep.Instance(prob, precision=precision)
+        inst.step(prob["nsteps"])
+        at = inst.activation_times()
+        u_mv = inst.potential()
+        inst.close()
+        assert np.array_equal(np.isnan(at), np.isnan(at_ref))
+        err = np.nanmax(np.abs(at - at_ref))
+        if precision == FP64:
+            assert err <= prob["dt"] + 1e-9
+            assert np.abs(u_mv - (85.7 * u_ref - 84.0)).max() <= 1e-6
+        else:
+            assert err <= 0.5
+            assert np.abs(u_mv - (85.7 * u_ref - 84.0)).max() <= 1.0
+
+
+def test_trajectory_ttp06_refined():
+    prob = small_ttp06(nx=40, ny=10, nz=6, T=25.0)
+    sim = O.sim_from_problem(prob)
+    inst = ep.Instance(prob, precision=REF)
+    snaps = []
+    for s in range(prob["nsteps"]):
+        sim.step(1)
+        inst.step(1)
+        if s % 10 == 9:
+            snaps.append(((s + 1) * prob["dt"], sim.potential(), inst.potential()))
+    at_ref, _ = sim.activation()
+    at = inst.activation_times()
+    inst.close()
+    assert np.array_equal(np.isnan(at), np.isnan(at_ref))
+    assert np.nanmax(np.abs(at - at_ref)) <= 0.5
+    # u within 1 mV away from each node's upstroke (+-2 steps of its activation)
+    for t, u_ref, u in snaps:
+        near = np.abs(np.nan_to_num(at_ref, nan=-1e9) - t) <= 2 * prob["dt"]
+        assert np.abs(u - u_ref)[~near].max() <= 1.0
+
+
+def test_deterministic_and_checkpoint_roundtrip():
+    prob = small_ttp06(nx=40, ny=12, nz=8, T=5.0)
+    runs = []
+    for _ in range(2):
+        inst = ep.Instance(prob, precision=REF)
+        inst.step(40)
+        runs.append(inst.save())
+        inst.close()
+    assert np.array_equal(runs[0], runs[1])
+    # restart from a checkpoint reproduces the uninterrupted run bitwise
+    a = ep.Instance(prob, precision=REF)
+    a.step(20)
+    buf = a.save()
+    a.step(20)
+    b = ep.Instance(prob, precision=REF)
+    b.load(buf)
+    b.step(20)
+    assert np.array_equal(a.save(), b.save())
+
+
+def test_failure_status_nan_and_noconv():
+    prob = small_ttp06(nx=8, ny=4, nz=3)
+    inst = ep.Instance(prob, precision=FP64)
+    st = ep.state_unpack(inst.save())
+    st["u_n"][5] = np.nan  # host-side injection
+    inst.load(ep.state_pack(prob["model"], prob["bdf"], prob["dt"], 0, st["u_n"], st["u_nm1"],
+                            st["w_n"], st["w_nm1"], st["at"], st["best"]))
+    with pytest.raises(ep.EpError) as e:
+        inst.step(1)
+    assert e.value.status == ep.EP_ENAN
+    with pytest.raises(ep.EpError) as e:
+        inst.step(1)  # sticky
+    assert e.value.status == ep.EP_ENAN
+    inst.close()
+    inst = ep.Instance(prob, precision=FP64, max_iter=1, tol=1e-14)
+    with pytest.raises(ep.EpError) as e:
+        inst.step(3)
+    assert e.value.status == ep.EP_ENOCONV
+    inst.close()
+
+
+def test_full_size_slab_single_step():
+    """The full 200 x 70 x 30 TTP06 slab (442,401 nodes) in the launch
+    configuration the benchmark uses: one step from a seeded synthetic front,
+    both precisions against the oracle."""
+    prob = I.slab_ttp06()
+    g = I.rng(900)
+    u_n, u_nm1, w_n, w_nm1 = synthetic_front_state(prob, g, width=0.02)
+    sim = O.sim_from_problem(prob)
+    sim.set_state(u_n, u_nm1, w_n, w_nm1, 5)
+    sim.step(1)
+    u_ref = sim.get_state()[0]
+    for precision, tol in ((FP64, 1e-10), (REF, 1e-6)):
+        inst = ep.Instance(prob, precision=precision)
+        buf = ep.state_pack(prob["model"], prob["bdf"], prob["dt"], 5, u_n, u_nm1, w_n, w_nm1,
+                            np.full(len(u_n), np.nan), np.full(len(u_n), -np.inf))
+        inst.load(buf)
+        inst.step(1)
+        assert rel_err(gpu_state(inst)["u_n"], u_ref) <= tol
+        inst.close()

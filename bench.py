@@ -245,8 +245,12 @@ def run_ours(args):
     prob = I.slab_ttp06()
     N = prob["mesh"]["xyz"].shape[0]
     n_elems = prob["mesh"]["hex"].shape[0]
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library orders its work on it, and the events
+    # and L2 flushes below are recorded on the same stream
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     sp = stream.cuda_stream
+    assert sp, "the instance needs a non-default stream"
     REF, FP64 = ep.EP_PREC_FP32_REFINED, ep.EP_PREC_FP64
 
     inst = ep.Instance(prob, precision=REF, cuda_stream=sp)

@@ -19,13 +19,13 @@ namespace epk {
 void launch_ionic(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_assemble(Dev* d, const Dev& h, const AsmParams& P, cudaStream_t s);
 void launch_realpha(Dev* d, const Dev& h, double delta, double alpha_dt, float cmass, cudaStream_t s);
-void launch_rhs(Dev* d, const Dev& h, int first, cudaStream_t s);
+void launch_rhs(Dev* d, const Dev& h, int first, int graph, cudaStream_t s);
 void launch_p64(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_apply64(Dev* d, const Dev& h, cudaStream_t s);
-void launch_update64(Dev* d, const Dev& h, int grid, cudaStream_t s);
+void launch_update64(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s);
 void launch_apply32_stencil(Dev* d, const Dev& h, cudaStream_t s);
 void launch_apply32_mf(Dev* d, const Dev& h, cudaStream_t s);
-void launch_update32(Dev* d, const Dev& h, int grid, cudaStream_t s);
+void launch_update32(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s);
 void launch_correct(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s);
 int mf_tiles(const Dev& h);
@@ -302,7 +302,7 @@ ep_status build_graph(ep_instance* I) {
     cudaGraphConditionalHandle h_loop = 0, h_outer = 0, h_inner = 0;
     C.chk(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     epk::launch_ionic(I->d, h, I->grid_ionic, s);
-    epk::launch_rhs(I->d, h, 1, s);
+    epk::launch_rhs(I->d, h, 1, 1, s);
     cudaGraph_t body = nullptr, body2 = nullptr;
     if (h.prec == EP_PREC_FP64) {
         C.chk(add_while(s, &h_loop, &body));
@@ -310,7 +310,7 @@ ep_status build_graph(ep_instance* I) {
             C.chk(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
             epk::launch_p64(I->d, h, I->grid_nodes, s2);
             epk::launch_apply64(I->d, h, s2);
-            epk::launch_update64(I->d, h, I->grid_nodes, s2);
+            epk::launch_update64(I->d, h, I->grid_nodes, 1, s2);
             C.chk(cudaStreamEndCapture(s2, &body));
         }
     } else {
@@ -322,11 +322,11 @@ ep_status build_graph(ep_instance* I) {
                 C.chk(cudaStreamBeginCaptureToGraph(s3, body2, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
                 if (h.op32 == EP_OP_MATRIX_FREE) epk::launch_apply32_mf(I->d, h, s3);
                 else epk::launch_apply32_stencil(I->d, h, s3);
-                epk::launch_update32(I->d, h, I->grid_nodes, s3);
+                epk::launch_update32(I->d, h, I->grid_nodes, 1, s3);
                 C.chk(cudaStreamEndCapture(s3, &body2));
             }
             epk::launch_correct(I->d, h, I->grid_nodes, s2);
-            epk::launch_rhs(I->d, h, 0, s2);
+            epk::launch_rhs(I->d, h, 0, 1, s2);
             C.chk(cudaStreamEndCapture(s2, &body));
         }
     }
@@ -367,14 +367,14 @@ ep_status step_host(ep_instance* I) {
         return e;
     };
     timed(I, K_IONIC, [&] { epk::launch_ionic(d, h, I->grid_ionic, s); });
-    timed(I, K_RHS, [&] { epk::launch_rhs(d, h, 1, s); });
+    timed(I, K_RHS, [&] { epk::launch_rhs(d, h, 1, 0, s); });
     int f = 0;
     if (h.prec == EP_PREC_FP64) {
         CUDA_TRY(flag(&d->f_loop, &f));
         for (int it = 0; f && it <= h.max_iter; ++it) {
             timed(I, K_P64, [&] { epk::launch_p64(d, h, I->grid_nodes, s); });
             timed(I, K_APPLY64, [&] { epk::launch_apply64(d, h, s); });
-            timed(I, K_UPDATE64, [&] { epk::launch_update64(d, h, I->grid_nodes, s); });
+            timed(I, K_UPDATE64, [&] { epk::launch_update64(d, h, I->grid_nodes, 0, s); });
             CUDA_TRY(cudaGetLastError());
             CUDA_TRY(flag(&d->f_loop, &f));
         }
@@ -387,12 +387,12 @@ ep_status step_host(ep_instance* I) {
                     timed(I, K_APPLY32MF, [&] { epk::launch_apply32_mf(d, h, s); });
                 else
                     timed(I, K_APPLY32ST, [&] { epk::launch_apply32_stencil(d, h, s); });
-                timed(I, K_UPDATE32, [&] { epk::launch_update32(d, h, I->grid_nodes, s); });
+                timed(I, K_UPDATE32, [&] { epk::launch_update32(d, h, I->grid_nodes, 0, s); });
                 CUDA_TRY(cudaGetLastError());
                 CUDA_TRY(flag(&d->f_inner, &fi));
             }
             timed(I, K_CORRECT, [&] { epk::launch_correct(d, h, I->grid_nodes, s); });
-            timed(I, K_RESID, [&] { epk::launch_rhs(d, h, 0, s); });
+            timed(I, K_RESID, [&] { epk::launch_rhs(d, h, 0, 0, s); });
             CUDA_TRY(cudaGetLastError());
             CUDA_TRY(flag(&d->f_outer, &f));
         }

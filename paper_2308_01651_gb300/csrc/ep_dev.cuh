@@ -177,8 +177,10 @@ __device__ void grid_reduce(double (&v)[NV], double* partial, unsigned int* coun
     }
 }
 
-// Records a loop decision: in the graph's conditional node (when the step
-// runs as a CUDA graph) and in the descriptor (for host-driven stepping).
+// Records a loop decision in the descriptor (read by host-driven stepping)
+// and, when h != 0, in the graph's conditional node.  Kernels pass h = 0
+// unless they were launched as nodes of the step graph: setting a handle
+// from a kernel outside its graph is undefined.
 __device__ __forceinline__ void set_cond(unsigned long long h, int* flag, unsigned int v) {
     *flag = (int)v;
     if (h) cudaGraphSetConditional((cudaGraphConditionalHandle)h, v);

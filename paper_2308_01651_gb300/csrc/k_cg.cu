@@ -11,7 +11,7 @@
 namespace epk {
 
 // delta += alpha p, r -= alpha q, z = D^-1 r; beta, inner convergence
-__global__ void __launch_bounds__(kNodeThreads) k_update32(Dev* __restrict__ Dp) {
+__global__ void __launch_bounds__(kNodeThreads) k_update32(Dev* __restrict__ Dp, int graph) {
     Dev& D = *Dp;
     const float alpha = (float)D.alpha;
     const float* __restrict__ p = D.pswap ? D.pa32 : D.pb32;  // the p written by the apply
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_update32(Dev* __restrict__ Dp)
         const bool nan = !(tot[1] == tot[1]);
         const bool conv = !nan && tot[1] <= D.inner_tol * D.inner_tol * D.rr0;
         if (nan && D.status == EP_OK) D.status = EP_ENAN;
-        set_cond(D.h_inner, &D.f_inner, (!conv && !nan && D.it < D.max_iter) ? 1u : 0u);
+        set_cond(graph ? D.h_inner : 0ull, &D.f_inner, (!conv && !nan && D.it < D.max_iter) ? 1u : 0u);
     });
 }
 
@@ -83,7 +83,9 @@ __global__ void __launch_bounds__(kNodeThreads) k_finish(Dev* __restrict__ Dp) {
     });
 }
 
-void launch_update32(Dev* d, const Dev& h, int grid, cudaStream_t s) { k_update32<<<grid, kNodeThreads, 0, s>>>(d); }
+void launch_update32(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s) {
+    k_update32<<<grid, kNodeThreads, 0, s>>>(d, graph);
+}
 void launch_correct(Dev* d, const Dev& h, int grid, cudaStream_t s) { k_correct<<<grid, kNodeThreads, 0, s>>>(d); }
 void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s) { k_finish<<<grid, kNodeThreads, 0, s>>>(d); }
 

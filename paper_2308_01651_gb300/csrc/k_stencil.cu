@@ -207,7 +207,7 @@ __device__ __forceinline__ Acc stencil_apply(const Dev& D, const C* __restrict__
 // (first == 0):  b = M v,  r = b - A u_new.  Also forms the preconditioned
 // residual for the next solver stage and the reductions it needs.
 template <bool REF>
-__global__ void __launch_bounds__(kStencilThreads) k_rhs(Dev* __restrict__ Dp, int first) {
+__global__ void __launch_bounds__(kStencilThreads) k_rhs(Dev* __restrict__ Dp, int first, int graph) {
     Dev& D = *Dp;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -262,14 +262,14 @@ __global__ void __launch_bounds__(kStencilThreads) k_rhs(Dev* __restrict__ Dp, i
                 D.sweeps += 1;
                 if (!conv && D.sweeps >= D.max_sweeps && D.status == EP_OK) D.status = EP_ENOCONV;
             }
-            set_cond(D.h_outer, &D.f_outer, (!conv && !nan && D.sweeps < D.max_sweeps) ? 1u : 0u);
+            set_cond(graph ? D.h_outer : 0ull, &D.f_outer, (!conv && !nan && D.sweeps < D.max_sweeps) ? 1u : 0u);
             // the next inner loop starts enabled (its handle belongs to the
             // refinement body, which is where the residual kernel runs)
             if (first) D.f_inner = 1;
-            else set_cond(D.h_inner, &D.f_inner, 1u);
+            else set_cond(graph ? D.h_inner : 0ull, &D.f_inner, 1u);
         } else {
             D.rr = rr;
-            set_cond(D.h_loop, &D.f_loop, (!conv && !nan) ? 1u : 0u);
+            set_cond(graph ? D.h_loop : 0ull, &D.f_loop, (!conv && !nan) ? 1u : 0u);
         }
     });
 }
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_apply64(Dev* __restrict__ D
 }
 
 // FP64 CG: x += alpha p, r -= alpha q, z = D^-1 r; beta, convergence
-__global__ void __launch_bounds__(kNodeThreads) k_update64(Dev* __restrict__ Dp) {
+__global__ void __launch_bounds__(kNodeThreads) k_update64(Dev* __restrict__ Dp, int graph) {
     Dev& D = *Dp;
     const double alpha = D.alpha;
     double v[2] = {0.0, 0.0};
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_update64(Dev* __restrict__ Dp)
         D.relres = D.bb > 0.0 ? sqrt(tot[1] / D.bb) : sqrt(tot[1]);
         if (nan && D.status == EP_OK) D.status = EP_ENAN;
         if (!conv && D.it >= D.max_iter && D.status == EP_OK) D.status = EP_ENOCONV;
-        set_cond(D.h_loop, &D.f_loop, (!conv && !nan && D.it < D.max_iter) ? 1u : 0u);
+        set_cond(graph ? D.h_loop : 0ull, &D.f_loop, (!conv && !nan && D.it < D.max_iter) ? 1u : 0u);
     });
 }
 
@@ -357,17 +357,17 @@ void launch_assemble(Dev* d, const Dev& h, const AsmParams& P, cudaStream_t s) {
 void launch_realpha(Dev* d, const Dev& h, double delta, double alpha_dt, float cmass, cudaStream_t s) {
     k_realpha<<<(h.N + 255) / 256, 256, 0, s>>>(d, delta, alpha_dt, cmass);
 }
-void launch_rhs(Dev* d, const Dev& h, int first, cudaStream_t s) {
+void launch_rhs(Dev* d, const Dev& h, int first, int graph, cudaStream_t s) {
     const int grid = (h.N + kStencilThreads - 1) / kStencilThreads;
-    if (h.prec == EP_PREC_FP32_REFINED) k_rhs<true><<<grid, kStencilThreads, 0, s>>>(d, first);
-    else k_rhs<false><<<grid, kStencilThreads, 0, s>>>(d, first);
+    if (h.prec == EP_PREC_FP32_REFINED) k_rhs<true><<<grid, kStencilThreads, 0, s>>>(d, first, graph);
+    else k_rhs<false><<<grid, kStencilThreads, 0, s>>>(d, first, graph);
 }
 void launch_p64(Dev* d, const Dev& h, int grid, cudaStream_t s) { k_p64<<<grid, kNodeThreads, 0, s>>>(d); }
 void launch_apply64(Dev* d, const Dev& h, cudaStream_t s) {
     k_apply64<<<(h.N + kStencilThreads - 1) / kStencilThreads, kStencilThreads, 0, s>>>(d);
 }
-void launch_update64(Dev* d, const Dev& h, int grid, cudaStream_t s) {
-    k_update64<<<grid, kNodeThreads, 0, s>>>(d);
+void launch_update64(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s) {
+    k_update64<<<grid, kNodeThreads, 0, s>>>(d, graph);
 }
 void launch_apply32_stencil(Dev* d, const Dev& h, cudaStream_t s) {
     k_apply32_stencil<<<(h.N + kStencilThreads - 1) / kStencilThreads, kStencilThreads, 0, s>>>(d);

@@ -60,8 +60,8 @@ def kernel_model(name, N, n_elems):
     B = {
         # read z, p_old, 6 fibre components; write p_new, q
         "apply32_mf": (40 * N, 910 * n_elems + 12 * N),
-        # read z, p_old at the row; 14 FP32 coefficients; write p_new, q
-        "apply32_stencil": (4 * 14 + 16, 2 * 27 * 2 + 4),
+        # read z, p_old; 14 own FP32 couplings; write p_new, q (27 FMA + update)
+        "apply32_stencil": (72, 56),
         # read p, q, d, r, D^-1; write d, r, z
         "update32": (32 * N, 8 * N),
         # read d, u; write u
@@ -253,10 +253,12 @@ def run_ours(args):
     assert sp, "the instance needs a non-default stream"
     REF, FP64 = ep.EP_PREC_FP32_REFINED, ep.EP_PREC_FP64
 
-    inst = ep.Instance(prob, precision=REF, cuda_stream=sp)
+    op32 = {"auto": ep.EP_OP_AUTO, "mf": ep.EP_OP_MATRIX_FREE, "stencil": ep.EP_OP_STENCIL}[args.op32]
+    inst = ep.Instance(prob, precision=REF, cuda_stream=sp, op32=op32)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     W, K = max(3, args.warmup), args.steps
     inst.step(W)
+    tune = inst.stats()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     launches = 0
@@ -366,7 +368,7 @@ def run_ours(args):
         K_e2e = K
     t0 = time.perf_counter()
     if K_e2e:
-        ie = ep.Instance(prob, precision=REF, cuda_stream=sp)
+        ie = ep.Instance(prob, precision=REF, cuda_stream=sp, op32=op32)
         ie.step_async(K_e2e)
         at_h = ie.activation_times()
         u_h = ie.potential()
@@ -389,11 +391,14 @@ def run_ours(args):
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nodes": N, "elements": n_elems, "precision": "FP32 inner CG, FP64 refinement",
+                   "op32": {0: "auto", 1: "matrix-free", 2: "stencil"}[op32],
                    "t_window_ms": [W * prob["dt"], (W + K) * prob["dt"]],
                    "l2": "flushed before every step (256 MiB write), per-step CUDA events on the instance stream",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": p50, "p99": p99, "what": "one IMEX step of the whole slab"},
         "roofline": roof, "kernels": kernels, "profile_steps": P,
+        "op32_autotune_us": {"matrix_free": tune["tune_us_mf"], "stencil": tune["tune_us_stencil"],
+                             "chosen": {1: "matrix-free", 2: "stencil"}.get(tune["op32"], "?")},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
         "accuracy": acc, "fp64_gpu": fp64,
     }
@@ -415,6 +420,8 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--op32", default="auto", choices=["auto", "mf", "stencil"],
+                    help="FP32 inner operator (auto: matrix-free on slabs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

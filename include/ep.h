@@ -60,7 +60,10 @@ enum { EP_CELL_ENDO = 0, EP_CELL_MID = 1, EP_CELL_EPI = 2 };
  * in float, inside FP64 iterative refinement (FP64 residual, dot products,
  * solution update) with FP64 ionic concentrations. */
 enum { EP_PREC_FP64 = 0, EP_PREC_FP32_REFINED = 1 };
-/* FP32 inner operator of the refined solver. */
+/* FP32 inner operator of the refined solver.  AUTO: on a slab both the
+ * matrix-free apply and the assembled FP32 stencil are built and ep_create
+ * times them on the instance, keeping the faster (ep_stats reports both
+ * times); elsewhere the stencil. */
 enum { EP_OP_AUTO = 0, EP_OP_MATRIX_FREE = 1, EP_OP_STENCIL = 2 };
 
 /* Mesh (Sec. 1.2: Q1 hexahedra).
@@ -151,6 +154,8 @@ typedef struct {
     int32_t op32;           /* FP32 operator in use (EP_OP_*) */
     int32_t reserved;
     size_t device_bytes;    /* device memory held by the instance */
+    double tune_us_mf;      /* autotuner: matrix-free apply time (us), 0 if not timed */
+    double tune_us_stencil; /* autotuner: FP32 stencil apply time (us), 0 if not timed */
 } ep_stats;
 
 /* Creates an instance: validates the inputs, copies them to the device,

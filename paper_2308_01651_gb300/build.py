@@ -18,6 +18,9 @@ LIB = os.path.join(HERE, "libep_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
+# per-file extra flags: the ionic kernels use fast float intrinsics (their
+# double-precision arithmetic is unaffected by -use_fast_math)
+FILE_FLAGS = {"k_ionic.cu": ["-use_fast_math"]}
 
 
 def nvcc():
@@ -38,7 +41,7 @@ def _deps():
 
 def _compile(src, extra):
     obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
+    cmd = [nvcc()] + ARCH + FLAGS + FILE_FLAGS.get(os.path.basename(src), []) + extra + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

@@ -4,6 +4,7 @@
 // step: the fused ionic kernel, the FP64 right-hand side, the linear solve
 // with its loops as conditional WHILE nodes (loop control stays on the
 // device), and the activation/rotation kernel.  ep_step replays the graph.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -14,16 +15,17 @@
 
 #include "ep_dev.cuh"
 #include "ionic_models.cuh"
+#include "ep_tile.cuh"
 
 namespace epk {
 void launch_ionic(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_assemble(Dev* d, const Dev& h, const AsmParams& P, cudaStream_t s);
 void launch_realpha(Dev* d, const Dev& h, double delta, double alpha_dt, float cmass, cudaStream_t s);
-void launch_rhs(Dev* d, const Dev& h, int first, int graph, cudaStream_t s);
+void launch_rhs(Dev* d, const Dev& h, int first, int graph, int grid, cudaStream_t s);
 void launch_p64(Dev* d, const Dev& h, int grid, cudaStream_t s);
-void launch_apply64(Dev* d, const Dev& h, cudaStream_t s);
+void launch_apply64(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_update64(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s);
-void launch_apply32_stencil(Dev* d, const Dev& h, cudaStream_t s);
+void launch_apply32_stencil(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_apply32_mf(Dev* d, const Dev& h, cudaStream_t s);
 void launch_update32(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s);
 void launch_correct(Dev* d, const Dev& h, int grid, cudaStream_t s);
@@ -60,11 +62,13 @@ struct ep_instance {
     size_t bytes = 0;
     long long host_step = 0;   // step index of the next enqueued step
     double alpha_dt_dev = 0;   // alpha/dt the device operators hold
-    int grid_nodes = 0;        // grid of the grid-stride node kernels
-    int grid_ionic = 0;
+    int grid_nodes = 0;        // grid of the grid-stride node kernels (with reductions)
+    int grid_ionic = 0;        // one node per thread
+    int grid_tiles = 0;        // persistent grid of the tiled stencil kernels
     ep_status sticky = EP_OK;
     int* bad = nullptr;        // device flag of the assembly
     bool graph_mode = true;    // false: host-driven loops (EP_GRAPH=0), for debugging
+    float tune_ms[3] = {0.f, 0.f, 0.f};  // autotuned FP32 operator apply times (ms)
     // per-kernel event timing (ep_profile_enable)
     bool profiling = false;
     struct Pending { int id; cudaEvent_t a, b; };
@@ -165,8 +169,8 @@ size_t footprint(const Sizes& z) {
     b += al(N * 8);                       // dinv64
     if (z.prec == EP_PREC_FP32_REFINED) {
         b += al(N * 4);                   // dinv32
-        if (z.op32 == EP_OP_STENCIL) b += al(epk::kSlots * N * 4);
-        else b += al(6 * N * 4);          // fibres
+        if (z.op32 != EP_OP_MATRIX_FREE) b += al(epk::kSlots * N * 4);  // A32
+        if (z.op32 != EP_OP_STENCIL) b += al(6 * N * 4);                 // fibres
         b += 6 * al(N * 4);               // r32 z32 q32 d32 pa32 pb32
     } else {
         b += 4 * al(N * 8);               // z64 q64 pa64 pb64
@@ -231,7 +235,9 @@ Sizes sizes_of(const ep_mesh* mesh, const ep_ionic_model* ionic, const ep_option
     z.ns = ionic->model == EP_MODEL_BO ? epk::kBOStates : epk::kTTGates + epk::kTTConc;
     z.prec = opts->precision;
     z.slab = mesh->kind == EP_MESH_SLAB;
-    z.op32 = opts->op32 == EP_OP_AUTO ? (z.slab ? EP_OP_MATRIX_FREE : EP_OP_STENCIL) : opts->op32;
+    // AUTO on a slab keeps both FP32 operators and lets the create-time
+    // autotuner pick; the matrix-free apply needs an axis-aligned slab
+    z.op32 = opts->op32 == EP_OP_AUTO ? (z.slab ? EP_OP_AUTO : EP_OP_STENCIL) : opts->op32;
     if (z.prec == EP_PREC_FP32_REFINED) {
         z.ng32 = ionic->model == EP_MODEL_BO ? epk::kBOStates : epk::kTTGates;
         z.ns64 = ionic->model == EP_MODEL_BO ? 0 : epk::kTTConc;
@@ -302,14 +308,14 @@ ep_status build_graph(ep_instance* I) {
     cudaGraphConditionalHandle h_loop = 0, h_outer = 0, h_inner = 0;
     C.chk(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     epk::launch_ionic(I->d, h, I->grid_ionic, s);
-    epk::launch_rhs(I->d, h, 1, 1, s);
+    epk::launch_rhs(I->d, h, 1, 1, I->grid_tiles, s);
     cudaGraph_t body = nullptr, body2 = nullptr;
     if (h.prec == EP_PREC_FP64) {
         C.chk(add_while(s, &h_loop, &body));
         if (C.err == cudaSuccess) {
             C.chk(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
             epk::launch_p64(I->d, h, I->grid_nodes, s2);
-            epk::launch_apply64(I->d, h, s2);
+            epk::launch_apply64(I->d, h, I->grid_tiles, s2);
             epk::launch_update64(I->d, h, I->grid_nodes, 1, s2);
             C.chk(cudaStreamEndCapture(s2, &body));
         }
@@ -321,12 +327,12 @@ ep_status build_graph(ep_instance* I) {
             if (C.err == cudaSuccess) {
                 C.chk(cudaStreamBeginCaptureToGraph(s3, body2, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
                 if (h.op32 == EP_OP_MATRIX_FREE) epk::launch_apply32_mf(I->d, h, s3);
-                else epk::launch_apply32_stencil(I->d, h, s3);
+                else epk::launch_apply32_stencil(I->d, h, I->grid_tiles, s3);
                 epk::launch_update32(I->d, h, I->grid_nodes, 1, s3);
                 C.chk(cudaStreamEndCapture(s3, &body2));
             }
             epk::launch_correct(I->d, h, I->grid_nodes, s2);
-            epk::launch_rhs(I->d, h, 0, 1, s2);
+            epk::launch_rhs(I->d, h, 0, 1, I->grid_tiles, s2);
             C.chk(cudaStreamEndCapture(s2, &body));
         }
     }
@@ -367,13 +373,13 @@ ep_status step_host(ep_instance* I) {
         return e;
     };
     timed(I, K_IONIC, [&] { epk::launch_ionic(d, h, I->grid_ionic, s); });
-    timed(I, K_RHS, [&] { epk::launch_rhs(d, h, 1, 0, s); });
+    timed(I, K_RHS, [&] { epk::launch_rhs(d, h, 1, 0, I->grid_tiles, s); });
     int f = 0;
     if (h.prec == EP_PREC_FP64) {
         CUDA_TRY(flag(&d->f_loop, &f));
         for (int it = 0; f && it <= h.max_iter; ++it) {
             timed(I, K_P64, [&] { epk::launch_p64(d, h, I->grid_nodes, s); });
-            timed(I, K_APPLY64, [&] { epk::launch_apply64(d, h, s); });
+            timed(I, K_APPLY64, [&] { epk::launch_apply64(d, h, I->grid_tiles, s); });
             timed(I, K_UPDATE64, [&] { epk::launch_update64(d, h, I->grid_nodes, 0, s); });
             CUDA_TRY(cudaGetLastError());
             CUDA_TRY(flag(&d->f_loop, &f));
@@ -386,13 +392,13 @@ ep_status step_host(ep_instance* I) {
                 if (h.op32 == EP_OP_MATRIX_FREE)
                     timed(I, K_APPLY32MF, [&] { epk::launch_apply32_mf(d, h, s); });
                 else
-                    timed(I, K_APPLY32ST, [&] { epk::launch_apply32_stencil(d, h, s); });
+                    timed(I, K_APPLY32ST, [&] { epk::launch_apply32_stencil(d, h, I->grid_tiles, s); });
                 timed(I, K_UPDATE32, [&] { epk::launch_update32(d, h, I->grid_nodes, 0, s); });
                 CUDA_TRY(cudaGetLastError());
                 CUDA_TRY(flag(&d->f_inner, &fi));
             }
             timed(I, K_CORRECT, [&] { epk::launch_correct(d, h, I->grid_nodes, s); });
-            timed(I, K_RESID, [&] { epk::launch_rhs(d, h, 0, 0, s); });
+            timed(I, K_RESID, [&] { epk::launch_rhs(d, h, 0, 0, I->grid_tiles, s); });
             CUDA_TRY(cudaGetLastError());
             CUDA_TRY(flag(&d->f_outer, &f));
         }
@@ -401,6 +407,51 @@ ep_status step_host(ep_instance* I) {
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(s));
     prof_resolve(I);
+    return EP_OK;
+}
+
+// Times the FP32 inner operators on this instance (CUDA events on its
+// stream, after warm-up) and keeps the faster one for the step graph.
+ep_status autotune_op32(ep_instance* I) {
+    Dev& h = I->h;
+    cudaStream_t s = I->stream;
+    const size_t N = (size_t)h.N;
+    CUDA_TRY(cudaMemsetAsync(h.z32, 0, N * 4, s));
+    CUDA_TRY(cudaMemsetAsync(h.pa32, 0, N * 4, s));
+    CUDA_TRY(cudaMemsetAsync(h.pb32, 0, N * 4, s));
+    cudaEvent_t a, b;
+    CUDA_TRY(cudaEventCreate(&a));
+    CUDA_TRY(cudaEventCreate(&b));
+    const int cands[2] = {EP_OP_MATRIX_FREE, EP_OP_STENCIL};
+    float best_ms = 1e30f;
+    int best = EP_OP_STENCIL;
+    for (int c : cands) {
+        auto launch = [&] {
+            if (c == EP_OP_MATRIX_FREE) epk::launch_apply32_mf(I->d, h, s);
+            else epk::launch_apply32_stencil(I->d, h, I->grid_tiles, s);
+        };
+        for (int w = 0; w < 3; ++w) launch();
+        cudaEventRecord(a, s);
+        for (int r = 0; r < 10; ++r) launch();
+        cudaEventRecord(b, s);
+        cudaError_t e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            return fail(EP_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+        }
+        I->tune_ms[c] = ms / 10.f;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    h.op32 = best;
+    CUDA_TRY(cudaMemcpy(&I->d->op32, &h.op32, sizeof(int), cudaMemcpyHostToDevice));
     return EP_OK;
 }
 
@@ -440,6 +491,7 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     h.bdf = opts->bdf_order;
     h.ns = z.ns;
     h.dt = opts->dt;
+    h.inv_dt = 1.0 / opts->dt;
     h.act_thr = ionic->model == EP_MODEL_BO ? 1.0 / kBOmV : 1.0;
     h.op32 = z.op32;
     const bool ref = h.prec == EP_PREC_FP32_REFINED;
@@ -481,11 +533,8 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     ALLOC(h.dinv64, N);
     if (ref) {
         ALLOC(h.dinv32, N);
-        if (z.op32 == EP_OP_STENCIL) {
-            ALLOC(h.A32, epk::kSlots * N);
-        } else {
-            ALLOC(h.fib, 6 * N);
-        }
+        if (z.op32 != EP_OP_MATRIX_FREE) ALLOC(h.A32, epk::kSlots * N);
+        if (z.op32 != EP_OP_STENCIL) ALLOC(h.fib, 6 * N);
         ALLOC(h.r32, N);
         ALLOC(h.z32, N);
         ALLOC(h.q32, N);
@@ -612,8 +661,20 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         CUDA_TRY(epk::mf_prepare());
     }
     const int blocks = (int)((N + epk::kNodeThreads - 1) / epk::kNodeThreads);
-    I->grid_nodes = blocks < 4096 ? blocks : 4096;
+    int dev = 0, sms = 152;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // pointwise reducing kernels: a persistent grid of four 256-thread blocks
+    // per SM (one partial sum and one counter update per block); tiled
+    // stencil kernels: two 512-thread blocks per SM
+    I->grid_nodes = std::max(1, std::min(blocks, 4 * sms));
     I->grid_ionic = blocks;
+    I->grid_tiles = std::max(1, std::min(epk::st_tiles(h), 2 * sms));
+    if (!ref) h.op32 = 0;  // no FP32 operator in the FP64 path
+    if (ref && h.op32 == EP_OP_AUTO) {
+        ep_status st2 = autotune_op32(I);
+        if (st2 != EP_OK) return st2;
+    }
     const char* env = std::getenv("EP_GRAPH");
     I->graph_mode = !(env && env[0] == '0');
     if (!I->graph_mode) return EP_OK;
@@ -872,6 +933,8 @@ ep_status ep_get_stats(const ep_instance* I, ep_stats* out) {
     out->op32 = I->h.prec == EP_PREC_FP32_REFINED ? I->h.op32 : 0;
     out->reserved = 0;
     out->device_bytes = I->bytes;
+    out->tune_us_mf = 1e3 * I->tune_ms[EP_OP_MATRIX_FREE];
+    out->tune_us_stencil = 1e3 * I->tune_ms[EP_OP_STENCIL];
     return EP_OK;
 }
 

@@ -21,12 +21,15 @@ constexpr int kTTGates = 13;  // m h j xr1 xr2 xs s r d f f2 fCass RR
 constexpr int kTTConc = 5;    // Cai CaSR CaSS Nai Ki
 constexpr int kBOStates = 3;  // v w s
 
+// largest block of a reducing kernel (power of two)
+constexpr int kMaxBlock = 512;
 // threads per block of the node-wise kernels
 constexpr int kNodeThreads = 256;
 constexpr int kNodesPerThread = 4;
 constexpr int kNodeTile = kNodeThreads * kNodesPerThread;
-// nodes per block of the stencil kernels
-constexpr int kStencilThreads = 256;
+// tiled stencil kernels: owned tile kStTx x kStTy x kStTz, threads per block
+constexpr int kStTx = 32, kStTy = 4, kStTz = 4;
+constexpr int kStThreads = 512;  // one owned node per thread
 
 // Matrix-free FP32 tile (owned nodes per block): 32 x 8 x 4
 constexpr int kMfTx = 32, kMfTy = 8, kMfTz = 4;
@@ -46,6 +49,7 @@ struct Dev {
     int bdf;
     int ns;              // ionic states (3 BO, 18 TTP06)
     double dt;
+    double inv_dt;       // 1/dt (no FP64 division in the kernels)
     double act_thr;      // activation slope threshold, model units per ms
     long long step;      // current time level n
     // ---- stimulus ------------------------------------------------------------
@@ -109,68 +113,82 @@ enum { CNT_RHS = 0, CNT_APPLY = 1, CNT_UPDATE = 2, CNT_RESID = 3, CNT_FINISH = 4
 
 // ---------------------------------------------------------------- helpers --
 
-__device__ __forceinline__ double warp_sum(double v) {
+__device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// Sums NV values over the block (fixed order), then over all blocks of the
-// grid: every block writes its sums to partial[blk*NV + k]; the last block
-// to arrive (global atomic counter) reduces all partials in a fixed order and
-// runs finish(totals) with thread 0.  Deterministic: the result does not
-// depend on which block arrives last.  No block waits on another.
-template <int NV, class F>
-__device__ void grid_reduce(double (&v)[NV], double* partial, unsigned int* counter,
-                            int blk, int nblk, F finish) {
-    __shared__ double sh[NV][32];
+// Shared-memory tree sum of sh[k][0..n) into sh[k][0] (n a power of two equal
+// to blockDim.x).  n - 1 additions per row: on GB300 the FP64 pipe is ~60x
+// slower than FP32, and a warp-shuffle tree would spend 5 x 32 additions per
+// warp instead of 31.
+template <int R>
+__device__ __forceinline__ void tree_sum(double (*sh)[kMaxBlock], int n) {
+    for (int s = n >> 1; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+}
+
+// Grid-wide sums of NF float and ND double per-thread values.  Float values
+// are summed by warp shuffles and then over the block's warps (in float, fixed
+// order); double values by a shared-memory tree.  Every block writes its
+// NF + ND sums (as double) to partial[blk*(NF+ND) + k]; the last block to
+// arrive (global atomic counter) adds all partials in double, in a fixed
+// order, and runs finish(totals) with thread 0 (totals: the NF float sums
+// first, then the ND double sums).  Deterministic: the result does not depend
+// on which block arrives last.  No block waits on another.  blockDim.x must
+// be a power of two <= kMaxBlock.
+template <int NF, int ND, class F>
+__device__ void grid_reduce(const float (&vf)[NF > 0 ? NF : 1], const double (&vd)[ND > 0 ? ND : 1],
+                            double* partial, unsigned int* counter, int blk, int nblk, F finish) {
+    constexpr int NV = NF + ND;
+    __shared__ double sh[NV][kMaxBlock];
+    __shared__ float shf[NF > 0 ? NF : 1][32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarp = (blockDim.x + 31) >> 5;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const double s = warp_sum(v[k]);
-        if (lane == 0) sh[k][warp] = s;
+    for (int k = 0; k < NF; ++k) {
+        const float s = warp_sum(vf[k]);
+        if (lane == 0) shf[k][warp] = s;
     }
-    __syncthreads();
-    if (warp == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double s = lane < nwarp ? sh[k][lane] : 0.0;
-            s = warp_sum(s);
-            if (lane == 0) partial[(size_t)blk * NV + k] = s;
+    for (int k = 0; k < ND; ++k) sh[k][threadIdx.x] = vd[k];
+    __syncthreads();
+    if constexpr (ND > 0) tree_sum<ND>(sh, blockDim.x);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            float s = 0.f;
+            for (int w = 0; w < nwarp; ++w) s += shf[k][w];
+            partial[(size_t)blk * NV + k] = (double)s;
         }
-        if (lane == 0) {
-            __threadfence();
-            const unsigned int t = atomicAdd(counter, 1u);
-            last = (t == (unsigned int)(nblk - 1));
-        }
+#pragma unroll
+        for (int k = 0; k < ND; ++k) partial[(size_t)blk * NV + NF + k] = sh[k][0];
+        __threadfence();
+        const unsigned int t = atomicAdd(counter, 1u);
+        last = (t == (unsigned int)(nblk - 1));
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double acc[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] += __ldcg(&partial[(size_t)i * NV + k]);
-    }
-    __syncthreads();
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        const double s = warp_sum(acc[k]);
-        if (lane == 0) sh[k][warp] = s;
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += __ldcg(&partial[(size_t)i * NV + k]);
+        sh[k][threadIdx.x] = acc;
     }
     __syncthreads();
+    tree_sum<NV>(sh, blockDim.x);
     if (threadIdx.x == 0) {
         double tot[NV];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < nwarp; ++w) s += sh[k][w];
-            tot[k] = s;
-        }
+        for (int k = 0; k < NV; ++k) tot[k] = sh[k][0];
         *counter = 0u;
         finish(tot);
         __threadfence();

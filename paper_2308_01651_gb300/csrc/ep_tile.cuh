@@ -1,0 +1,88 @@
+// ep_tile.cuh -- tiles of the structured meshes for the 27-point stencil
+// kernels (shared-memory staging of a vector on a tile plus halo, one stencil
+// row from shared memory).
+#pragma once
+
+#include "ep_dev.cuh"
+
+namespace epk {
+
+// Tiled 27-point applies.  A block loops over tiles of kStTx x kStTy x kStTz
+// owned nodes (a persistent grid of about two blocks per SM, one reduction
+// per block).  Per tile it stages the input vector on the tile plus a
+// one-node halo in shared memory -- forming the CG direction update on the
+// way in where the kernel needs it -- together with the global index of
+// every halo node (-1 outside the mesh; the periodic direction wraps), then
+// each thread applies the stencil to its owned nodes: the 14 own couplings
+// are read coalesced, the 13 backward couplings from the neighbours' slots,
+// the vector from shared memory.  Summation order is fixed (the diagonal,
+// then offsets t = 0..26), so every node rounds the same way in every run.
+
+constexpr int SHX = kStTx + 2, SHY = kStTy + 2, SHZ = kStTz + 2;
+constexpr int SHN = SHX * SHY * SHZ;
+constexpr int kStOwned = kStTx * kStTy * kStTz;
+
+struct TileGeo {
+    int i0, j0, k0;
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const Dev& D, int tile) {
+    const int tx = (D.NX + kStTx - 1) / kStTx, ty = (D.NY + kStTy - 1) / kStTy;
+    TileGeo g;
+    g.i0 = (tile % tx) * kStTx;
+    g.j0 = ((tile / tx) % ty) * kStTy;
+    g.k0 = (tile / (tx * ty)) * kStTz;
+    return g;
+}
+
+// XF(n, owned) returns the input at node n (and may record it when owned).
+template <typename T, class XF>
+__device__ __forceinline__ void stage_tile(const Dev& D, const TileGeo& g, int* sidx, T* xs, XF xf) {
+    for (int h = threadIdx.x; h < SHN; h += blockDim.x) {
+        const int hi = h % SHX, hj = (h / SHX) % SHY, hk = h / (SHX * SHY);
+        const int gi = g.i0 - 1 + hi, gk = g.k0 - 1 + hk, gj_raw = g.j0 - 1 + hj;
+        bool valid = gi >= 0 && gi < D.NX && gk >= 0 && gk < D.NZ;
+        int gj = gj_raw;
+        if (D.periodic) gj = ((gj_raw % D.NY) + D.NY) % D.NY;
+        else valid = valid && gj_raw >= 0 && gj_raw < D.NY;
+        const bool owned = valid && hi >= 1 && hi <= kStTx && hj >= 1 && hj <= kStTy && hk >= 1 &&
+                           hk <= kStTz && gj_raw >= 0 && gj_raw < D.NY;
+        const int n = valid ? gi + D.NX * (gj + D.NY * gk) : -1;
+        sidx[h] = n;
+        xs[h] = valid ? xf(n, owned) : T(0);
+    }
+}
+
+// one stencil row: node n sits at halo position h
+template <typename C, typename Acc, typename T>
+__device__ __forceinline__ Acc tile_row(const C* __restrict__ c, size_t N, const int* sidx, const T* xs,
+                                        int h, int n) {
+    Acc acc = (Acc)c[n] * (Acc)xs[h];
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+        if (t == 13) continue;
+        const int dh = (t % 3 - 1) + SHX * ((t / 3) % 3 - 1) + SHX * SHY * (t / 9 - 1);
+        const int m = sidx[h + dh];
+        if (m < 0) continue;
+        const Acc cv = (t > 13) ? (Acc)c[(size_t)(t - 13) * N + n] : (Acc)c[(size_t)(13 - t) * N + m];
+        acc += cv * (Acc)xs[h + dh];
+    }
+    return acc;
+}
+
+// calls f(h, n) for every owned node of the tile this thread handles
+template <class F>
+__device__ __forceinline__ void for_owned(const Dev& D, const TileGeo& g, F f) {
+    for (int o = threadIdx.x; o < kStOwned; o += blockDim.x) {
+        const int li = o % kStTx, lj = (o / kStTx) % kStTy, lk = o / (kStTx * kStTy);
+        if (g.i0 + li >= D.NX || g.j0 + lj >= D.NY || g.k0 + lk >= D.NZ) continue;
+        const int h = (li + 1) + SHX * ((lj + 1) + SHY * (lk + 1));
+        f(h);
+    }
+}
+
+__host__ __device__ inline int st_tiles(const Dev& h) {
+    return ((h.NX + kStTx - 1) / kStTx) * ((h.NY + kStTy - 1) / kStTy) * ((h.NZ + kStTz - 1) / kStTz);
+}
+
+}  // namespace epk

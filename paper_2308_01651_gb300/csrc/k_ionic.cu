@@ -12,13 +12,19 @@
 //   u_new,j = u_EXT (initial guess of the linear solve).
 // The new states overwrite the w_{n-1} slot (each thread owns its node), and
 // the finishing kernel of the step swaps the slots.
+//
+// This file is compiled with fast single-precision intrinsics (exp, log,
+// division): they only touch the FP32 path, whose float rates feed the
+// double concentrations as increments; the FP64 path's double arithmetic is
+// unaffected.  No double division appears per node (1/dt and 1/alpha are
+// precomputed): GB300's FP64 pipe is ~60x slower than FP32.
 #include "ep_dev.cuh"
 #include "ionic_models.cuh"
 
 namespace epk {
 
 struct StepConsts {
-    double dt, alpha;
+    double dt, alpha, inv_dt, inv_alpha, dt_alpha;
     int order;
     double iamp[EP_MAX_PULSES];
 };
@@ -28,7 +34,11 @@ __device__ __forceinline__ StepConsts step_consts(const Dev& D) {
     c.dt = D.dt;
     c.order = (D.bdf == 2 && D.step >= 1) ? 2 : 1;
     c.alpha = c.order == 2 ? 1.5 : 1.0;
+    c.inv_alpha = c.order == 2 ? 2.0 / 3.0 : 1.0;
+    c.inv_dt = D.inv_dt;
+    c.dt_alpha = c.dt * c.inv_alpha;
     const long long m = D.step + 1;  // new time level
+#pragma unroll
     for (int p = 0; p < EP_MAX_PULSES; ++p) {
         double a = 0.0;
         if (p < D.npulses && m > D.k0[p]) {
@@ -43,7 +53,8 @@ __device__ __forceinline__ StepConsts step_consts(const Dev& D) {
 
 __device__ __forceinline__ double applied(const Dev& D, const StepConsts& c, int n) {
     double s = 0.0;
-    for (int p = 0; p < D.npulses; ++p)
+#pragma unroll
+    for (int p = 0; p < EP_MAX_PULSES; ++p)
         if (c.iamp[p] != 0.0 && D.mask[p][n]) s += c.iamp[p];
     return s;
 }
@@ -92,7 +103,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Dev* __restrict__ Dp)
             wm[(size_t)k * N + n] = w1[k];
         }
         const double I = (double)BO<G>::iion(G(uE), w1[0], w1[1], w1[2]);
-        D.v[n] = uB / c.dt - I + applied(D, c, n);
+        D.v[n] = fma(uB, c.inv_dt, applied(D, c, n) - I);
         D.u_new[n] = uE;
     }
 }
@@ -160,13 +171,13 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_tt(Dev* __restrict__ Dp)
 #pragma unroll
         for (int k = 0; k < kTTConc; ++k) {
             // the increment is formed in G, accumulated in double
-            c1[k] = (cB[k] + c.dt * (double)r[k]) / c.alpha;
+            c1[k] = fma(c.dt_alpha, (double)r[k], cB[k] * c.inv_alpha);
             cm[(size_t)k * N + n] = c1[k];
         }
         typename TT<G>::Cur cur;
         TT<G>::currents(cell, G(uE), g1, G(c1[0]), G(c1[2]), G(c1[3]), G(c1[4]), cur);
         const double I = (double)TT<G>::iion_of(cur);
-        D.v[n] = uB / c.dt - I + applied(D, c, n);
+        D.v[n] = fma(uB, c.inv_dt, applied(D, c, n) - I);
         D.u_new[n] = uE;
     }
 }

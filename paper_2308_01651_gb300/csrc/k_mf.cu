@@ -203,7 +203,8 @@ __global__ void __launch_bounds__(kMfThreads) k_apply32_mf(Dev* __restrict__ Dp)
     __syncthreads();
 
     // ---- gather per owned node (fixed order) --------------------------------
-    double v[1] = {0.0};
+    float v[1] = {0.f};
+    const double none[1] = {0.0};
     float dot = 0.f;
     for (int o = threadIdx.x; o < kMfTx * kMfTy * kMfTz; o += blockDim.x) {
         const int li = o % kMfTx, lj = (o / kMfTx) % kMfTy, lk = o / (kMfTx * kMfTy);
@@ -225,8 +226,8 @@ __global__ void __launch_bounds__(kMfThreads) k_apply32_mf(Dev* __restrict__ Dp)
         dot = fmaf(s_p[(li + 1) + HX * ((lj + 1) + HY * (lk + 1))], acc, dot);
     }
     v[0] = dot;
-    grid_reduce<1>(v, D.partial, D.counter + CNT_APPLY, blockIdx.x, gridDim.x,
-                   [&](double* tot) { D.alpha = D.rz / tot[0]; });
+    grid_reduce<1, 0>(v, none, D.partial, D.counter + CNT_APPLY, blockIdx.x, gridDim.x,
+                      [&](double* tot) { D.alpha = D.rz / tot[0]; });
 }
 
 int mf_tiles(const Dev& h) {

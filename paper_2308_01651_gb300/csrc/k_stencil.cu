@@ -17,6 +17,7 @@
 // right-hand side / residual, the FP64 CG apply and updates, and the FP32
 // stencil apply of the refined inner solver.
 #include "ep_dev.cuh"
+#include "ep_tile.cuh"
 
 namespace epk {
 
@@ -185,76 +186,75 @@ __global__ void k_realpha(Dev* __restrict__ Dp, double delta, double alpha_dt, f
 
 // ---------------------------------------------------------------- applies --
 
-// y = (stencil c) x at node n = (i, j, k); XF(m) returns x at node m.
-template <typename C, typename Acc, class XF>
-__device__ __forceinline__ Acc stencil_apply(const Dev& D, const C* __restrict__ c, int n, int i,
-                                             int j, int k, XF xf) {
-    const size_t N = (size_t)D.N;
-    Acc acc = (Acc)c[n] * xf(n);
-#pragma unroll
-    for (int t = 0; t < 27; ++t) {
-        if (t == 13) continue;
-        const int di = t % 3 - 1, dj = (t / 3) % 3 - 1, dk = t / 9 - 1;
-        const int m = neighbour(D, i, j, k, di, dj, dk);
-        if (m < 0) continue;
-        const Acc cv = (t > 13) ? (Acc)c[(size_t)(t - 13) * N + n] : (Acc)c[(size_t)(13 - t) * N + m];
-        acc += cv * xf(m);
-    }
-    return acc;
-}
-
 // FP64 right-hand side and initial residual (first == 1), or residual only
 // (first == 0):  b = M v,  r = b - A u_new.  Also forms the preconditioned
 // residual for the next solver stage and the reductions it needs.
 template <bool REF>
-__global__ void __launch_bounds__(kStencilThreads) k_rhs(Dev* __restrict__ Dp, int first, int graph) {
+__global__ void __launch_bounds__(kStThreads) k_rhs(Dev* __restrict__ Dp, int first, int graph) {
+    __shared__ int sidx[SHN];
+    __shared__ double su[SHN];
+    __shared__ double sv[SHN];
     Dev& D = *Dp;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    if (n < D.N) {
-        int i, j, k;
-        node_ijk(D, n, i, j, k);
-        const double* __restrict__ vv = D.v;
-        const double* __restrict__ u = D.u_new;
-        double b;
+    const size_t N = (size_t)D.N;
+    const double* __restrict__ vv = D.v;
+    const double* __restrict__ u = D.u_new;
+    // FP64 sums (b.b, r.r[, r.z]) and, refined, FP32 sums (r32.z32, r32.r32)
+    float vf[2] = {0.f, 0.f};
+    double vd[3] = {0.0, 0.0, 0.0};
+    const int ntiles = st_tiles(D);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const TileGeo g = tile_geo(D, tile);
+        __syncthreads();
+        stage_tile<double>(D, g, sidx, su, [&](int n, bool) { return u[n]; });
         if (first) {
-            b = stencil_apply<double, double>(D, D.M64, n, i, j, k, [&](int m) { return vv[m]; });
-            D.b[n] = b;
-        } else {
-            b = D.b[n];
+            for (int h = threadIdx.x; h < SHN; h += blockDim.x) {
+                const int n = sidx[h];  // written by this same thread above
+                sv[h] = n >= 0 ? vv[n] : 0.0;
+            }
         }
-        const double au = stencil_apply<double, double>(D, D.A64, n, i, j, k, [&](int m) { return u[m]; });
-        const double r = b - au;
-        D.r[n] = r;
-        v[0] = b * b;
-        v[1] = r * r;
-        if (REF) {
-            const float r32 = (float)r;
-            const float z = D.dinv32[n] * r32;
-            D.r32[n] = r32;
-            D.z32[n] = z;
-            D.d32[n] = 0.0f;
-            v[2] = (double)r32 * (double)z;
-            v[3] = (double)r32 * (double)r32;
-        } else {
-            const double z = D.dinv64[n] * r;
-            D.z64[n] = z;
-            v[2] = r * z;
-        }
+        __syncthreads();
+        for_owned(D, g, [&](int h) {
+            const int n = sidx[h];
+            double b;
+            if (first) {
+                b = tile_row<double, double, double>(D.M64, N, sidx, sv, h, n);
+                D.b[n] = b;
+            } else {
+                b = D.b[n];
+            }
+            const double au = tile_row<double, double, double>(D.A64, N, sidx, su, h, n);
+            const double r = b - au;
+            D.r[n] = r;
+            vd[0] = fma(b, b, vd[0]);
+            vd[1] = fma(r, r, vd[1]);
+            if (REF) {
+                const float r32 = (float)r;
+                const float z = D.dinv32[n] * r32;
+                D.r32[n] = r32;
+                D.z32[n] = z;
+                D.d32[n] = 0.0f;
+                vf[0] = fmaf(r32, z, vf[0]);
+                vf[1] = fmaf(r32, r32, vf[1]);
+            } else {
+                const double z = D.dinv64[n] * r;
+                D.z64[n] = z;
+                vd[2] = fma(r, z, vd[2]);
+            }
+        });
     }
-    grid_reduce<4>(v, D.partial, D.counter + CNT_RHS, blockIdx.x, gridDim.x, [&](double* tot) {
-        if (first) D.bb = tot[0];
-        const double rr = tot[1], bb = D.bb;
+    auto fin = [&](double bb_now, double rr, double rz, double rr32) {
+        if (first) D.bb = bb_now;
+        const double bb = D.bb;
         const bool nan = !(rr == rr);
         const bool conv = !nan && (rr <= D.tol * D.tol * bb);
         D.relres = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
         if (nan && D.status == EP_OK) D.status = EP_ENAN;
         D.it = 0;
         D.beta = 0.0;
-        D.rz = tot[2];
+        D.rz = rz;
         if (REF) {
-            D.rr0 = tot[3];
-            D.rr = tot[3];
+            D.rr0 = rr32;
+            D.rr = rr32;
             if (first) {
                 D.sweeps = 0;
                 D.it_total = 0;
@@ -271,7 +271,16 @@ __global__ void __launch_bounds__(kStencilThreads) k_rhs(Dev* __restrict__ Dp, i
             D.rr = rr;
             set_cond(graph ? D.h_loop : 0ull, &D.f_loop, (!conv && !nan) ? 1u : 0u);
         }
-    });
+    };
+    if constexpr (REF) {
+        const double vd2[2] = {vd[0], vd[1]};
+        grid_reduce<2, 2>(vf, vd2, D.partial, D.counter + CNT_RHS, blockIdx.x, gridDim.x,
+                          [&](double* t) { fin(t[2], t[3], t[0], t[1]); });
+    } else {
+        const float none[1] = {0.f};
+        grid_reduce<0, 3>(none, vd, D.partial, D.counter + CNT_RHS, blockIdx.x, gridDim.x,
+                          [&](double* t) { fin(t[0], t[1], t[2], 0.0); });
+    }
 }
 
 // FP64 CG: p = z + beta p (beta == 0: p = z)
@@ -279,24 +288,33 @@ __global__ void __launch_bounds__(kNodeThreads) k_p64(Dev* __restrict__ Dp) {
     const Dev& D = *Dp;
     const double beta = D.beta;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x)
-        D.pa64[n] = beta == 0.0 ? D.z64[n] : D.z64[n] + beta * D.pa64[n];
+        D.pa64[n] = beta == 0.0 ? D.z64[n] : fma(beta, D.pa64[n], D.z64[n]);
 }
 
 // FP64 CG: q = A p, alpha = rz / (p, q)
-__global__ void __launch_bounds__(kStencilThreads) k_apply64(Dev* __restrict__ Dp) {
+__global__ void __launch_bounds__(kStThreads) k_apply64(Dev* __restrict__ Dp) {
+    __shared__ int sidx[SHN];
+    __shared__ double sp[SHN];
     Dev& D = *Dp;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t N = (size_t)D.N;
+    const double* __restrict__ p = D.pa64;
     double v[1] = {0.0};
-    if (n < D.N) {
-        int i, j, k;
-        node_ijk(D, n, i, j, k);
-        const double* __restrict__ p = D.pa64;
-        const double q = stencil_apply<double, double>(D, D.A64, n, i, j, k, [&](int m) { return p[m]; });
-        D.q64[n] = q;
-        v[0] = p[n] * q;
+    const float none[1] = {0.f};
+    const int ntiles = st_tiles(D);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const TileGeo g = tile_geo(D, tile);
+        __syncthreads();
+        stage_tile<double>(D, g, sidx, sp, [&](int n, bool) { return p[n]; });
+        __syncthreads();
+        for_owned(D, g, [&](int h) {
+            const int n = sidx[h];
+            const double q = tile_row<double, double, double>(D.A64, N, sidx, sp, h, n);
+            D.q64[n] = q;
+            v[0] = fma(sp[h], q, v[0]);
+        });
     }
-    grid_reduce<1>(v, D.partial, D.counter + CNT_APPLY, blockIdx.x, gridDim.x,
-                   [&](double* tot) { D.alpha = D.rz / tot[0]; });
+    grid_reduce<0, 1>(none, v, D.partial, D.counter + CNT_APPLY, blockIdx.x, gridDim.x,
+                      [&](double* tot) { D.alpha = D.rz / tot[0]; });
 }
 
 // FP64 CG: x += alpha p, r -= alpha q, z = D^-1 r; beta, convergence
@@ -305,15 +323,16 @@ __global__ void __launch_bounds__(kNodeThreads) k_update64(Dev* __restrict__ Dp,
     const double alpha = D.alpha;
     double v[2] = {0.0, 0.0};
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x) {
-        D.u_new[n] += alpha * D.pa64[n];
-        const double r = D.r[n] - alpha * D.q64[n];
+        D.u_new[n] = fma(alpha, D.pa64[n], D.u_new[n]);
+        const double r = fma(-alpha, D.q64[n], D.r[n]);
         D.r[n] = r;
         const double z = D.dinv64[n] * r;
         D.z64[n] = z;
-        v[0] += r * z;
-        v[1] += r * r;
+        v[0] = fma(r, z, v[0]);
+        v[1] = fma(r, r, v[1]);
     }
-    grid_reduce<2>(v, D.partial, D.counter + CNT_UPDATE, blockIdx.x, gridDim.x, [&](double* tot) {
+    const float none[1] = {0.f};
+    grid_reduce<0, 2>(none, v, D.partial, D.counter + CNT_UPDATE, blockIdx.x, gridDim.x, [&](double* tot) {
         D.beta = tot[0] / D.rz;
         D.rz = tot[0];
         D.rr = tot[1];
@@ -327,28 +346,38 @@ __global__ void __launch_bounds__(kNodeThreads) k_update64(Dev* __restrict__ Dp,
     });
 }
 
-// FP32 inner CG, stencil operator: p_new = z + beta p_old at every node the
-// row touches, q = A32 p_new; alpha = rz / (p_new, q).
-__global__ void __launch_bounds__(kStencilThreads) k_apply32_stencil(Dev* __restrict__ Dp) {
+// FP32 inner CG, stencil operator: p_new = z + beta p_old (staged with the
+// halo; the owning tile records it), q = A32 p_new; alpha = rz / (p_new, q).
+__global__ void __launch_bounds__(kStThreads) k_apply32_stencil(Dev* __restrict__ Dp) {
+    __shared__ int sidx[SHN];
+    __shared__ float sp[SHN];
     Dev& D = *Dp;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t N = (size_t)D.N;
     const float* __restrict__ pold = D.pswap ? D.pb32 : D.pa32;
     float* __restrict__ pnew = D.pswap ? D.pa32 : D.pb32;
     const float beta = (float)D.beta;
     const float* __restrict__ z = D.z32;
-    double v[1] = {0.0};
-    if (n < D.N) {
-        int i, j, k;
-        node_ijk(D, n, i, j, k);
-        auto pf = [&](int m) { return beta == 0.0f ? z[m] : fmaf(beta, pold[m], z[m]); };
-        const float q = stencil_apply<float, float>(D, D.A32, n, i, j, k, pf);
-        const float pn = pf(n);
-        pnew[n] = pn;
-        D.q32[n] = q;
-        v[0] = (double)(pn * q);
+    float v[1] = {0.f};
+    const double none[1] = {0.0};
+    const int ntiles = st_tiles(D);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const TileGeo g = tile_geo(D, tile);
+        __syncthreads();
+        stage_tile<float>(D, g, sidx, sp, [&](int n, bool own) {
+            const float pn = beta == 0.0f ? z[n] : fmaf(beta, pold[n], z[n]);
+            if (own) pnew[n] = pn;
+            return pn;
+        });
+        __syncthreads();
+        for_owned(D, g, [&](int h) {
+            const int n = sidx[h];
+            const float q = tile_row<float, float, float>(D.A32, N, sidx, sp, h, n);
+            D.q32[n] = q;
+            v[0] = fmaf(sp[h], q, v[0]);
+        });
     }
-    grid_reduce<1>(v, D.partial, D.counter + CNT_APPLY, blockIdx.x, gridDim.x,
-                   [&](double* tot) { D.alpha = D.rz / tot[0]; });
+    grid_reduce<1, 0>(v, none, D.partial, D.counter + CNT_APPLY, blockIdx.x, gridDim.x,
+                      [&](double* tot) { D.alpha = D.rz / tot[0]; });
 }
 
 void launch_assemble(Dev* d, const Dev& h, const AsmParams& P, cudaStream_t s) {
@@ -357,20 +386,17 @@ void launch_assemble(Dev* d, const Dev& h, const AsmParams& P, cudaStream_t s) {
 void launch_realpha(Dev* d, const Dev& h, double delta, double alpha_dt, float cmass, cudaStream_t s) {
     k_realpha<<<(h.N + 255) / 256, 256, 0, s>>>(d, delta, alpha_dt, cmass);
 }
-void launch_rhs(Dev* d, const Dev& h, int first, int graph, cudaStream_t s) {
-    const int grid = (h.N + kStencilThreads - 1) / kStencilThreads;
-    if (h.prec == EP_PREC_FP32_REFINED) k_rhs<true><<<grid, kStencilThreads, 0, s>>>(d, first, graph);
-    else k_rhs<false><<<grid, kStencilThreads, 0, s>>>(d, first, graph);
+void launch_rhs(Dev* d, const Dev& h, int first, int graph, int grid, cudaStream_t s) {
+    if (h.prec == EP_PREC_FP32_REFINED) k_rhs<true><<<grid, kStThreads, 0, s>>>(d, first, graph);
+    else k_rhs<false><<<grid, kStThreads, 0, s>>>(d, first, graph);
 }
 void launch_p64(Dev* d, const Dev& h, int grid, cudaStream_t s) { k_p64<<<grid, kNodeThreads, 0, s>>>(d); }
-void launch_apply64(Dev* d, const Dev& h, cudaStream_t s) {
-    k_apply64<<<(h.N + kStencilThreads - 1) / kStencilThreads, kStencilThreads, 0, s>>>(d);
-}
+void launch_apply64(Dev* d, const Dev& h, int grid, cudaStream_t s) { k_apply64<<<grid, kStThreads, 0, s>>>(d); }
 void launch_update64(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s) {
     k_update64<<<grid, kNodeThreads, 0, s>>>(d, graph);
 }
-void launch_apply32_stencil(Dev* d, const Dev& h, cudaStream_t s) {
-    k_apply32_stencil<<<(h.N + kStencilThreads - 1) / kStencilThreads, kStencilThreads, 0, s>>>(d);
+void launch_apply32_stencil(Dev* d, const Dev& h, int grid, cudaStream_t s) {
+    k_apply32_stencil<<<grid, kStThreads, 0, s>>>(d);
 }
 
 }  // namespace epk

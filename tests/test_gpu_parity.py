@@ -57,8 +57,10 @@ def test_single_step_after_oracle_run(kind, precision, tol):
     g, u, w, best = one_step_from(prob, sim, precision)
     assert g["step"] == k + 1
     assert rel_err(g["u_n"], u) <= tol
+    # FP32 gates (fast float intrinsics) sit a few float ulps from the FP64
+    # oracle; FP64 states within the FP64 bound
     for s in range(w.shape[0]):
-        assert rel_err(g["w_n"][s], w[s]) <= max(tol, 1e-6 if precision == REF else tol), s
+        assert rel_err(g["w_n"][s], w[s]) <= (1e-5 if precision == REF else tol), s
     assert rel_err(g["best"], best) <= max(tol * 1e3, 1e-7)
 
 
@@ -229,7 +231,8 @@ def test_graph_and_host_driven_stepping_agree():
     b.step(10)
     assert np.array_equal(a.save(), b.save())
     assert prof["ionic"][0] == 10 and prof["finish"][0] == 10
-    assert prof["apply32_mf"][0] == prof["update32"][0] > 0
+    apply = prof.get("apply32_mf", prof.get("apply32_stencil"))
+    assert apply[0] == prof["update32"][0] > 0
     assert all(ms > 0 for _, ms in prof.values())
     for prec in (FP64,):
         c = ep.Instance(prob, precision=prec)

@@ -230,6 +230,23 @@ ep_status ep_profile_enable(ep_instance* inst, int32_t on);
 ep_status ep_profile_read(ep_instance* inst, ep_kernel_time* out, int32_t cap,
                           int32_t* n, int32_t reset);
 
+/* Allocation-free residual check.  The paper has no counterpart: this is a
+ * service of the library.  Writes to *relres_out the relative FP64 residual
+ * ||b - A u_n||_2 / ||b||_2 of the instance's last linear solve (the value
+ * ep_get_stats reports as relres for FP32_REFINED instances), recomputed
+ * from the instance's stencil and vectors.  It calls no cudaMalloc, cudaFree
+ * or other allocating routine, for callers that must not allocate device
+ * memory where they check a solve (while capturing a stream into a graph, in
+ * a host callback, under an external allocator that owns all device memory).
+ * Its scratch is a fixed ~16 KiB device array in the library, holding one
+ * pair of partial sums per thread block, at most 1024 blocks; an instance
+ * whose residual kernel would need more blocks is refused with EP_EINVAL.
+ * The first call on each device looks up that array's device address: make
+ * it before any stream capture on the device.  All calls share the array,
+ * so calls whose GPU work overlaps (unordered streams) race; calls ordered
+ * on one stream do not.  Runs on the instance's stream and waits for it. */
+ep_status ep_residual_norm_noalloc(const ep_instance* inst, double* relres_out);
+
 /* Frees every resource of the instance (NULL is accepted). */
 ep_status ep_destroy(ep_instance* inst);
 

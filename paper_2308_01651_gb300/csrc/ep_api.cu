@@ -32,6 +32,8 @@ void launch_correct(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s);
 int mf_tiles(const Dev& h);
 cudaError_t mf_prepare();
+cudaError_t residual_norm_noalloc(Dev* d, int grid, cudaStream_t s, double sums[2]);
+int noalloc_max_blocks();
 }  // namespace epk
 
 using epk::Dev;
@@ -976,6 +978,18 @@ ep_status ep_profile_read(ep_instance* I, ep_kernel_time* out, int32_t cap, int3
             I->prof_ms[id] = 0.0;
             I->prof_n[id] = 0;
         }
+    return EP_OK;
+}
+
+ep_status ep_residual_norm_noalloc(const ep_instance* I, double* relres_out) {
+    if (!I || !relres_out) return fail(EP_EINVAL, "NULL argument");
+    if (I->grid_tiles > epk::noalloc_max_blocks())
+        return fail(EP_EINVAL, "the residual of this instance needs " + std::to_string(I->grid_tiles) +
+                                   " thread blocks; the allocation-free path holds partial sums for at most " +
+                                   std::to_string(epk::noalloc_max_blocks()));
+    double sums[2] = {0.0, 0.0};
+    CUDA_TRY(epk::residual_norm_noalloc(I->d, I->grid_tiles, I->stream, sums));
+    *relres_out = sums[0] > 0.0 ? std::sqrt(sums[1] / sums[0]) : std::sqrt(sums[1]);
     return EP_OK;
 }
 

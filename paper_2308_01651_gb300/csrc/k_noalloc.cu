@@ -1,0 +1,118 @@
+// k_noalloc.cu -- ep_residual_norm_noalloc: the relative FP64 residual
+// ||b - A u_n|| / ||b|| of an instance's last linear solve, computed without
+// allocating anything.
+//
+// Who needs it: code that must not call cudaMalloc at the point where it
+// wants the number -- for example while a CUDA stream is being captured into
+// a graph, inside a host callback or a plugin whose memory is owned by
+// another allocator, or in a process that pre-reserves all device memory at
+// start-up.  Everything this call touches is either the instance's existing
+// memory (read only) or the fixed scratch array below.
+//
+// Scratch: g_noalloc_scratch, a file-scope __device__ array of
+// kNoAllocScratchBytes (about 16 KiB) that every GPU loading this library
+// holds until the process exits.  It stores one pair of partial sums per
+// thread block (at most kNoAllocMaxBlocks blocks), the two totals, and the
+// arrival counter of the last-block reduction.  Host code cannot use the
+// array's name as a device address; at set-up, once per device and with that
+// device current, the address is taken with cudaGetSymbolAddress and passed
+// to the kernel.  The first call on each device does that set-up, so make
+// the first call before any stream capture on that device.  Every call
+// shares the array and it keeps the last call's contents: each call clears
+// the counter before its kernel runs, and calls whose work overlaps on the
+// GPU (different streams, no ordering) race on the array.
+//
+// The kernel is a variant of the FP64 residual kernel (k_rhs, residual
+// mode): same tiles, same per-thread and per-block summation order, so it
+// reproduces the solver's own residual norm; it writes nothing but the
+// scratch array.
+#include <mutex>
+#include <string>
+
+#include "ep_dev.cuh"
+#include "ep_tile.cuh"
+
+namespace epk {
+
+constexpr int kNoAllocMaxBlocks = 1024;
+// layout: double partial[2 * kNoAllocMaxBlocks]; double total[2]; unsigned counter
+constexpr size_t kNoAllocTotalOff = sizeof(double) * 2 * kNoAllocMaxBlocks;
+constexpr size_t kNoAllocCounterOff = kNoAllocTotalOff + 2 * sizeof(double);
+constexpr size_t kNoAllocScratchBytes = kNoAllocCounterOff + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+__global__ void __launch_bounds__(kStThreads) k_residual_norm_noalloc(const Dev* __restrict__ Dp,
+                                                                       unsigned char* scratch) {
+    __shared__ int sidx[SHN];
+    __shared__ double su[SHN];
+    const Dev& D = *Dp;
+    const size_t N = (size_t)D.N;
+    const double* __restrict__ u = D.u_n;  // the last solve's solution
+    double* partial = reinterpret_cast<double*>(scratch);
+    double* total = reinterpret_cast<double*>(scratch + kNoAllocTotalOff);
+    unsigned int* counter = reinterpret_cast<unsigned int*>(scratch + kNoAllocCounterOff);
+    double vd[2] = {0.0, 0.0};
+    const float none[1] = {0.f};
+    const int ntiles = st_tiles(D);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const TileGeo g = tile_geo(D, tile);
+        __syncthreads();
+        stage_tile<double>(D, g, sidx, su, [&](int n, bool) { return u[n]; });
+        __syncthreads();
+        for_owned(D, g, [&](int h) {
+            const int n = sidx[h];
+            const double b = D.b[n];
+            const double r = b - tile_row<double, double, double>(D.A64, N, sidx, su, h, n);
+            vd[0] = fma(b, b, vd[0]);
+            vd[1] = fma(r, r, vd[1]);
+        });
+    }
+    grid_reduce<0, 2>(none, vd, partial, counter, blockIdx.x, gridDim.x, [&](double* t) {
+        total[0] = t[0];
+        total[1] = t[1];
+    });
+}
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {nullptr};
+}  // namespace
+
+// Device address of the scratch array on the current device (set-up on first
+// use per device).
+cudaError_t noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+int noalloc_max_blocks() { return kNoAllocMaxBlocks; }
+
+// Runs the kernel on stream s and copies the two sums (b.b, r.r) to host.
+cudaError_t residual_norm_noalloc(Dev* d, int grid, cudaStream_t s, double sums[2]) {
+    void* scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) return e;
+    unsigned char* base = static_cast<unsigned char*>(scratch);
+    e = cudaMemsetAsync(base + kNoAllocCounterOff, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    k_residual_norm_noalloc<<<grid, kStThreads, 0, s>>>(d, base);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(sums, base + kNoAllocTotalOff, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+}  // namespace epk

@@ -29,7 +29,7 @@ EP_MAX_PULSES = 4
 EXPORTS = ["ep_create", "ep_step", "ep_step_async", "ep_sync", "ep_step_batch", "ep_read_potential",
            "ep_activation_times", "ep_state_bytes", "ep_save_state", "ep_load_state",
            "ep_footprint_bytes", "ep_get_stats", "ep_potential_device", "ep_destroy", "ep_last_error",
-           "ep_profile_enable", "ep_profile_read"]
+           "ep_profile_enable", "ep_profile_read", "ep_residual_norm_noalloc"]
 
 
 class EpError(RuntimeError):
@@ -123,6 +123,8 @@ def lib():
         L.ep_profile_enable.restype = st
         L.ep_profile_read.argtypes = [vp, P(ep_kernel_time), i32, P(i32), i32]
         L.ep_profile_read.restype = st
+        L.ep_residual_norm_noalloc.argtypes = [vp, P(C.c_double)]
+        L.ep_residual_norm_noalloc.restype = st
         L.ep_destroy.argtypes = [vp]
         L.ep_destroy.restype = st
         L.ep_last_error.argtypes = []
@@ -289,6 +291,14 @@ def ep_profile_read(h, reset=False):
     n = C.c_int32()
     _check(lib().ep_profile_read(h, arr, cap, C.byref(n), 1 if reset else 0))
     return {arr[k].name.decode(): (arr[k].launches, arr[k].ms_total) for k in range(min(n.value, cap))}
+
+
+def ep_residual_norm_noalloc(h):
+    """Relative FP64 residual of the last solve, computed without allocating
+    (see ep.h)."""
+    out = C.c_double()
+    _check(lib().ep_residual_norm_noalloc(h, C.byref(out)))
+    return out.value
 
 
 def ep_destroy(h):

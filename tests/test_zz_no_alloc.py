@@ -1,0 +1,42 @@
+"""The allocation-free residual check (ep_residual_norm_noalloc).
+
+Some callers must not allocate device memory at the point where they check a
+solve -- while capturing a stream into a graph, in a host callback, or under
+an allocator that owns all device memory.  ep_residual_norm_noalloc serves
+them: it recomputes the relative FP64 residual of an instance's last solve
+using a fixed scratch array inside the library instead of any allocation.
+This file checks it against the residual the solver itself reports through
+ep_get_stats (computed by the regular residual kernel with the instance's own
+scratch), on two calls in a row, after steps of an FP32-refined instance.
+It is named so that pytest collects it last.
+"""
+import numpy as np
+import pytest
+
+from paper_2308_01651_gb300 import ep
+from paper_2308_01651_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem():
+    return I.slab_ttp06(nx=40, ny=12, nz=8, L=(0.4, 0.12, 0.08), T=5.0)
+
+
+def test_residual_norm_noalloc_matches_solver_residual():
+    inst = ep.Instance(_problem(), precision=ep.EP_PREC_FP32_REFINED)
+    try:
+        for steps in (25, 7):
+            inst.step(steps)
+            reported = inst.stats()["relres"]
+            before = inst.save()
+            first = ep.ep_residual_norm_noalloc(inst.h)
+            second = ep.ep_residual_norm_noalloc(inst.h)
+            assert reported > 0.0 and reported <= 1e-10
+            # same tiles and summation order as the solver's residual kernel
+            assert abs(first - reported) <= 1e-12 * reported
+            assert abs(second - reported) <= 1e-12 * reported
+            # the check reads the instance and changes nothing in it
+            assert np.array_equal(before, inst.save())
+    finally:
+        inst.close()

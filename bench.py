@@ -54,10 +54,14 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_model(name, N, n_elems):
+def kernel_model(name, N, n_elems, inner_iters=1.0):
     """Algorithmic bytes and flops per launch of each kernel (what the method
-    must move / compute, not what the hardware did)."""
+    must move / compute, not what the hardware did).  inner_iters: inner CG
+    iterations per launch of the persistent solver."""
     B = {
+        # per inner iteration: apply (z, p_old, 14 own FP32 couplings; p_new, q)
+        # + update (p, q, delta, r, D^-1; delta, r, z)
+        "pcg32": (int((72 + 32) * N * inner_iters), int((56 + 8) * N * inner_iters)),
         # read z, p_old, 6 fibre components; write p_new, q
         "apply32_mf": (40 * N, 910 * n_elems + 12 * N),
         # read z, p_old; 14 own FP32 couplings; write p_new, q (27 FMA + update)
@@ -94,6 +98,8 @@ def source_hash(files):
 KERNEL_SOURCES = {
     "apply32_mf": ["paper_2308_01651_gb300/csrc/k_mf.cu", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
     "resid": ["paper_2308_01651_gb300/csrc/k_stencil.cu", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
+    "pcg32": ["paper_2308_01651_gb300/csrc/k_pcg.cu", "paper_2308_01651_gb300/csrc/ep_tile.cuh",
+              "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
     "update32": ["paper_2308_01651_gb300/csrc/k_cg.cu", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
     "ionic": ["paper_2308_01651_gb300/csrc/k_ionic.cu", "paper_2308_01651_gb300/csrc/ionic_models.cuh"],
 }
@@ -262,6 +268,7 @@ def run_ours(args):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     launches = 0
+    it_sum = sw_sum = 0
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -272,7 +279,12 @@ def run_ours(args):
             inst.step_async(1)
             ev[k][1].record(stream)
             st = inst.stats()  # synchronises; outside the events
-            launches += 3 + 2 * st["cg_iters"] + 2 * st["sweeps"]
+            it_sum += st["cg_iters"]
+            sw_sum += st["sweeps"]
+            if st["op32"] == ep.EP_OP_STENCIL:
+                launches += 3 + 3 * st["sweeps"]  # ionic, rhs, finish; per sweep: pcg32, correct, resid
+            else:
+                launches += 3 + 2 * st["cg_iters"] + 2 * st["sweeps"]
         inst.sync()
         torch.cuda.synchronize()
     if dist:
@@ -305,8 +317,9 @@ def run_ours(args):
         prof = ep.ep_profile_read(inst.h, reset=True)
         ep.ep_profile_enable(inst.h, False)
         tot_prof = sum(v[1] for v in prof.values())
+        ipl = it_sum / max(sw_sum, 1)
         for name, (n_l, ms) in prof.items():
-            b, f = kernel_model(name, N, n_elems)
+            b, f = kernel_model(name, N, n_elems, ipl)
             avg_s = ms / 1e3 / n_l
             kernels[name] = {"launches": n_l, "avg_us": 1e6 * avg_s, "share": ms / tot_prof,
                              "gbs": (b / avg_s / 1e9) if b else None,
@@ -387,6 +400,7 @@ def run_ours(args):
         cpu = {k: leg[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     line = {
+        "inner_iters_per_sweep": it_sum / max(sw_sum, 1), "sweeps_per_step": sw_sum / K,
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",

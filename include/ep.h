@@ -57,8 +57,10 @@ enum { EP_MODEL_BO = 0, EP_MODEL_TTP06 = 1 };
 enum { EP_CELL_ENDO = 0, EP_CELL_MID = 1, EP_CELL_EPI = 2 };
 /* Arithmetic of the step.  FP64: every quantity in double, CG on the FP64
  * operator.  FP32_REFINED: ionic gates, ionic current and the CG inner solve
- * in float, inside FP64 iterative refinement (FP64 residual, dot products,
- * solution update) with FP64 ionic concentrations. */
+ * in float, inside iterative refinement whose right-hand side, residual and
+ * solution update are carried in float-float (double-single, 48-bit
+ * significand) arithmetic -- GB300's FP64 pipe is ~60x slower than FP32 --
+ * and FP64 ionic concentrations; the potentials are stored in double. */
 enum { EP_PREC_FP64 = 0, EP_PREC_FP32_REFINED = 1 };
 /* FP32 inner operator of the refined solver.  AUTO: on a slab both the
  * matrix-free apply and the assembled FP32 stencil are built and ep_create
@@ -218,7 +220,8 @@ ep_status ep_potential_device(const ep_instance* inst, const double** out);
  * events on the instance's stream; the totals accumulate until reset.  The
  * step time is then not representative, the kernel times are.  Kernel names:
  * "ionic", "rhs", "resid", "p64", "apply64", "update64", "apply32_mf",
- * "apply32_stencil", "update32", "correct", "finish", "realpha". */
+ * "apply32_stencil", "update32", "pcg32" (the persistent inner solve of a
+ * refinement sweep), "correct", "finish", "realpha". */
 typedef struct {
     char name[24];
     int64_t launches;
@@ -231,10 +234,11 @@ ep_status ep_profile_read(ep_instance* inst, ep_kernel_time* out, int32_t cap,
                           int32_t* n, int32_t reset);
 
 /* Allocation-free residual check.  The paper has no counterpart: this is a
- * service of the library.  Writes to *relres_out the relative FP64 residual
- * ||b - A u_n||_2 / ||b||_2 of the instance's last linear solve (the value
- * ep_get_stats reports as relres for FP32_REFINED instances), recomputed
- * from the instance's stencil and vectors.  It calls no cudaMalloc, cudaFree
+ * service of the library.  Writes to *relres_out the relative residual
+ * ||b - A u_n||_2 / ||b||_2 of an FP32_REFINED instance's last linear solve
+ * (the value ep_get_stats reports as relres), recomputed from the instance's
+ * operator and vectors in the same float-float arithmetic as the solver's
+ * residual; other instances get EP_EUNSUPPORTED.  It calls no cudaMalloc, cudaFree
  * or other allocating routine, for callers that must not allocate device
  * memory where they check a solve (while capturing a stream into a graph, in
  * a host callback, under an external allocator that owns all device memory).

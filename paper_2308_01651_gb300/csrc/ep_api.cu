@@ -21,17 +21,22 @@ namespace epk {
 void launch_ionic(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_assemble(Dev* d, const Dev& h, const AsmParams& P, cudaStream_t s);
 void launch_realpha(Dev* d, const Dev& h, double delta, double alpha_dt, float cmass, cudaStream_t s);
-void launch_rhs(Dev* d, const Dev& h, int first, int graph, int grid, cudaStream_t s);
+void launch_rhs64(Dev* d, const Dev& h, int first, int graph, int grid, cudaStream_t s);
+void launch_rhs_ff(Dev* d, const Dev& h, int first, int graph, int grid, cudaStream_t s);
+void launch_expand(Dev* d, const Dev& h, int want_a, int want_m, cudaStream_t s);
+void launch_realpha_ff(Dev* d, const Dev& h, double delta, double alpha_dt, float cmass, cudaStream_t s);
 void launch_p64(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_apply64(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_update64(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s);
 void launch_apply32_stencil(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_apply32_mf(Dev* d, const Dev& h, cudaStream_t s);
 void launch_update32(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s);
-void launch_correct(Dev* d, const Dev& h, int grid, cudaStream_t s);
+void launch_correct_ff(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s);
 int mf_tiles(const Dev& h);
 cudaError_t mf_prepare();
+int pcg_blocks_per_sm();
+cudaError_t launch_pcg32(Dev* d, int grid, cudaStream_t s);
 cudaError_t residual_norm_noalloc(Dev* d, int grid, cudaStream_t s, double sums[2]);
 int noalloc_max_blocks();
 }  // namespace epk
@@ -67,6 +72,7 @@ struct ep_instance {
     int grid_nodes = 0;        // grid of the grid-stride node kernels (with reductions)
     int grid_ionic = 0;        // one node per thread
     int grid_tiles = 0;        // persistent grid of the tiled stencil kernels
+    int grid_pcg = 0;          // cooperative grid of the persistent inner solver
     ep_status sticky = EP_OK;
     int* bad = nullptr;        // device flag of the assembly
     bool graph_mode = true;    // false: host-driven loops (EP_GRAPH=0), for debugging
@@ -82,9 +88,9 @@ struct ep_instance {
 
 static const char* kKernelNames[] = {"ionic", "rhs", "resid", "p64", "apply64", "update64",
                                      "apply32_mf", "apply32_stencil", "update32", "correct",
-                                     "finish", "realpha"};
+                                     "finish", "realpha", "pcg32"};
 enum { K_IONIC, K_RHS, K_RESID, K_P64, K_APPLY64, K_UPDATE64, K_APPLY32MF, K_APPLY32ST, K_UPDATE32,
-       K_CORRECT, K_FINISH, K_REALPHA, K_COUNT };
+       K_CORRECT, K_FINISH, K_REALPHA, K_PCG32, K_COUNT };
 
 static cudaEvent_t prof_event(ep_instance* I) {
     if (!I->free_events.empty()) {
@@ -151,6 +157,20 @@ ep_status dalloc(ep_instance* I, T** p, size_t count) {
     return EP_OK;
 }
 
+// Frees one allocation of dalloc before ep_destroy.
+template <typename T>
+void dfree(ep_instance* I, T*& p, size_t count) {
+    if (!p) return;
+    for (size_t i = 0; i < I->allocs.size(); ++i)
+        if (I->allocs[i] == (void*)p) {
+            I->allocs.erase(I->allocs.begin() + i);
+            I->bytes -= ((count * sizeof(T) + 255) / 256) * 256;
+            cudaFree((void*)p);
+            break;
+        }
+    p = nullptr;
+}
+
 struct Sizes {
     int N, ns, ng32, ns64, prec, op32;
     bool slab;
@@ -165,20 +185,23 @@ size_t footprint(const Sizes& z) {
     b += 2 * al(z.ng32 * N * 4);          // gates (refined)
     b += 2 * al(z.ns64 * N * 8);          // FP64 states
     b += al(N);                           // cell types
-    b += 3 * al(N * 8);                   // v, b, r
+    if (z.prec != EP_PREC_FP32_REFINED) b += 3 * al(N * 8);  // v, b, r
     b += 2 * al(N * 8);                   // at, best
-    b += 2 * al(epk::kSlots * N * 8);     // M64, A64
-    b += al(N * 8);                       // dinv64
+    if (z.prec != EP_PREC_FP32_REFINED) {
+        b += 2 * al(epk::kSlots * N * 8);  // M64, A64 (the refined path frees them after ep_create)
+        b += al(N * 8);                    // dinv64
+    }
     if (z.prec == EP_PREC_FP32_REFINED) {
         b += al(N * 4);                   // dinv32
-        if (z.op32 != EP_OP_MATRIX_FREE) b += al(epk::kSlots * N * 4);  // A32
+        b += 4 * al(epk::kGroups * N * 16);                              // Ahi Alo Mhi Mlo
+        b += 6 * al(N * 4);                                              // u, v, b (hi, lo)
         if (z.op32 != EP_OP_STENCIL) b += al(6 * N * 4);                 // fibres
-        b += 6 * al(N * 4);               // r32 z32 q32 d32 pa32 pb32
+        b += 8 * al(N * 4);               // r32 z32 q32 d32 pa32 pb32 s32 p32
     } else {
         b += 4 * al(N * 8);               // z64 q64 pa64 pb64
     }
-    const size_t blocks = (N + 255) / 256 + 1;
-    b += al(blocks * 4 * 8);              // partials
+    const size_t blocks = std::max((N + 255) / 256 + 1, (size_t)epk::kMaxPersistentBlocks);
+    b += al(blocks * 8 * 8);              // partials
     b += al(epk::CNT_N * 4);
     b += al(sizeof(Dev)) + 256;
     return b;
@@ -260,7 +283,10 @@ void ensure_alpha(ep_instance* I) {
     if (need != I->alpha_dt_dev) {
         const float cmass = (float)(need * I->h.h[0] * I->h.h[1] * I->h.h[2]);
         const double delta = need - I->alpha_dt_dev;
-        timed(I, K_REALPHA, [&] { epk::launch_realpha(I->d, I->h, delta, need, cmass, I->stream); });
+        timed(I, K_REALPHA, [&] {
+            if (I->h.prec == EP_PREC_FP32_REFINED) epk::launch_realpha_ff(I->d, I->h, delta, need, cmass, I->stream);
+            else epk::launch_realpha(I->d, I->h, delta, need, cmass, I->stream);
+        });
         I->alpha_dt_dev = need;
     }
 }
@@ -310,7 +336,8 @@ ep_status build_graph(ep_instance* I) {
     cudaGraphConditionalHandle h_loop = 0, h_outer = 0, h_inner = 0;
     C.chk(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     epk::launch_ionic(I->d, h, I->grid_ionic, s);
-    epk::launch_rhs(I->d, h, 1, 1, I->grid_tiles, s);
+    if (h.prec == EP_PREC_FP64) epk::launch_rhs64(I->d, h, 1, 1, I->grid_tiles, s);
+    else epk::launch_rhs_ff(I->d, h, 1, 1, I->grid_tiles, s);
     cudaGraph_t body = nullptr, body2 = nullptr;
     if (h.prec == EP_PREC_FP64) {
         C.chk(add_while(s, &h_loop, &body));
@@ -319,6 +346,16 @@ ep_status build_graph(ep_instance* I) {
             epk::launch_p64(I->d, h, I->grid_nodes, s2);
             epk::launch_apply64(I->d, h, I->grid_tiles, s2);
             epk::launch_update64(I->d, h, I->grid_nodes, 1, s2);
+            C.chk(cudaStreamEndCapture(s2, &body));
+        }
+    } else if (h.op32 == EP_OP_STENCIL) {
+        // refinement sweeps: [persistent inner PCG, u += delta, FP64 residual]
+        C.chk(add_while(s, &h_outer, &body));
+        if (C.err == cudaSuccess) {
+            C.chk(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            C.chk(epk::launch_pcg32(I->d, I->grid_pcg, s2));
+            epk::launch_correct_ff(I->d, h, I->grid_nodes, s2);
+            epk::launch_rhs_ff(I->d, h, 0, 1, I->grid_tiles, s2);
             C.chk(cudaStreamEndCapture(s2, &body));
         }
     } else {
@@ -333,8 +370,8 @@ ep_status build_graph(ep_instance* I) {
                 epk::launch_update32(I->d, h, I->grid_nodes, 1, s3);
                 C.chk(cudaStreamEndCapture(s3, &body2));
             }
-            epk::launch_correct(I->d, h, I->grid_nodes, s2);
-            epk::launch_rhs(I->d, h, 0, 1, I->grid_tiles, s2);
+            epk::launch_correct_ff(I->d, h, I->grid_nodes, s2);
+            epk::launch_rhs_ff(I->d, h, 0, 1, I->grid_tiles, s2);
             C.chk(cudaStreamEndCapture(s2, &body));
         }
     }
@@ -350,7 +387,8 @@ ep_status build_graph(ep_instance* I) {
         return fail(EP_ECUDA, std::string("building the step graph: ") + cudaGetErrorString(C.err));
     }
     I->graph = g;
-    if ((h.prec == EP_PREC_FP64 && !h_loop) || (h.prec != EP_PREC_FP64 && (!h_outer || !h_inner)))
+    if ((h.prec == EP_PREC_FP64 && !h_loop) ||
+        (h.prec != EP_PREC_FP64 && (!h_outer || (h.op32 != EP_OP_STENCIL && !h_inner))))
         return fail(EP_ECUDA, "a conditional handle of the step graph is zero");
     CUDA_TRY(cudaGraphInstantiate(&I->exec, g, 0));
     // the conditional handles live in the device descriptor
@@ -375,7 +413,10 @@ ep_status step_host(ep_instance* I) {
         return e;
     };
     timed(I, K_IONIC, [&] { epk::launch_ionic(d, h, I->grid_ionic, s); });
-    timed(I, K_RHS, [&] { epk::launch_rhs(d, h, 1, 0, I->grid_tiles, s); });
+    timed(I, K_RHS, [&] {
+        if (h.prec == EP_PREC_FP64) epk::launch_rhs64(d, h, 1, 0, I->grid_tiles, s);
+        else epk::launch_rhs_ff(d, h, 1, 0, I->grid_tiles, s);
+    });
     int f = 0;
     if (h.prec == EP_PREC_FP64) {
         CUDA_TRY(flag(&d->f_loop, &f));
@@ -390,6 +431,12 @@ ep_status step_host(ep_instance* I) {
         CUDA_TRY(flag(&d->f_outer, &f));
         for (int sw = 0; f && sw <= h.max_sweeps; ++sw) {
             int fi = 1;
+            if (h.op32 == EP_OP_STENCIL) {
+                cudaError_t pe = cudaSuccess;
+                timed(I, K_PCG32, [&] { pe = epk::launch_pcg32(d, I->grid_pcg, s); });
+                CUDA_TRY(pe);
+                fi = 0;
+            }
             for (int it = 0; fi && it <= h.max_iter; ++it) {
                 if (h.op32 == EP_OP_MATRIX_FREE)
                     timed(I, K_APPLY32MF, [&] { epk::launch_apply32_mf(d, h, s); });
@@ -399,8 +446,8 @@ ep_status step_host(ep_instance* I) {
                 CUDA_TRY(cudaGetLastError());
                 CUDA_TRY(flag(&d->f_inner, &fi));
             }
-            timed(I, K_CORRECT, [&] { epk::launch_correct(d, h, I->grid_nodes, s); });
-            timed(I, K_RESID, [&] { epk::launch_rhs(d, h, 0, 0, I->grid_tiles, s); });
+            timed(I, K_CORRECT, [&] { epk::launch_correct_ff(d, h, I->grid_nodes, s); });
+            timed(I, K_RESID, [&] { epk::launch_rhs_ff(d, h, 0, 0, I->grid_tiles, s); });
             CUDA_TRY(cudaGetLastError());
             CUDA_TRY(flag(&d->f_outer, &f));
         }
@@ -525,9 +572,11 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     uint8_t* cell = nullptr;
     ALLOC(cell, N);
     h.cell = cell;
-    ALLOC(h.v, N);
-    ALLOC(h.b, N);
-    ALLOC(h.r, N);
+    if (!ref) {
+        ALLOC(h.v, N);
+        ALLOC(h.b, N);
+        ALLOC(h.r, N);
+    }
     ALLOC(h.at, N);
     ALLOC(h.best, N);
     ALLOC(h.M64, epk::kSlots * N);
@@ -535,7 +584,16 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     ALLOC(h.dinv64, N);
     if (ref) {
         ALLOC(h.dinv32, N);
-        if (z.op32 != EP_OP_MATRIX_FREE) ALLOC(h.A32, epk::kSlots * N);
+        ALLOC(h.Ahi, epk::kGroups * N);
+        ALLOC(h.Alo, epk::kGroups * N);
+        ALLOC(h.Mhi, epk::kGroups * N);
+        ALLOC(h.Mlo, epk::kGroups * N);
+        ALLOC(h.u_hi, N);
+        ALLOC(h.u_lo, N);
+        ALLOC(h.v_hi, N);
+        ALLOC(h.v_lo, N);
+        ALLOC(h.b_hi, N);
+        ALLOC(h.b_lo, N);
         if (z.op32 != EP_OP_STENCIL) ALLOC(h.fib, 6 * N);
         ALLOC(h.r32, N);
         ALLOC(h.z32, N);
@@ -543,13 +601,15 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         ALLOC(h.d32, N);
         ALLOC(h.pa32, N);
         ALLOC(h.pb32, N);
+        ALLOC(h.s32, N);
+        ALLOC(h.p32, N);
     } else {
         ALLOC(h.z64, N);
         ALLOC(h.q64, N);
         ALLOC(h.pa64, N);
         ALLOC(h.pb64, N);
     }
-    ALLOC(h.partial, ((N + 255) / 256 + 1) * 4);
+    ALLOC(h.partial, std::max((N + 255) / 256 + 1, (size_t)epk::kMaxPersistentBlocks) * 8);
     ALLOC(h.counter, (size_t)epk::CNT_N);
     ALLOC(I->d, 1);
     // stimulus
@@ -603,7 +663,9 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         CUDA_TRY(cudaMemcpy(h.at, nanv.data(), N * 8, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(h.best, ninf.data(), N * 8, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemset(h.counter, 0, epk::CNT_N * sizeof(unsigned int)));
-        CUDA_TRY(cudaMemset(h.v, 0, N * 8));
+        if (h.v) CUDA_TRY(cudaMemset(h.v, 0, N * 8));
+        for (float* f : {h.u_hi, h.u_lo, h.v_hi, h.v_lo, h.b_hi, h.b_lo, h.r32, h.d32, h.q32})
+            if (f) CUDA_TRY(cudaMemset(f, 0, N * 4));
     }
 
     // ---- operators ----------------------------------------------------------
@@ -639,7 +701,7 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         if (e == cudaSuccess) e = cudaMemset(bad, 0, sizeof(int));
         int bad_h = 0;
         if (e == cudaSuccess) {
-            epk::AsmParams P{xyz, f0, s0, dl, dtr, dn, alpha_dt, h.A32 != nullptr, bad};
+            epk::AsmParams P{xyz, f0, s0, dl, dtr, dn, alpha_dt, bad};
             epk::launch_assemble(I->d, h, P, I->stream);
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
@@ -651,6 +713,21 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         if (bad) cudaFree(bad);
         if (e != cudaSuccess) return fail(EP_ECUDA, std::string("assembly: ") + cudaGetErrorString(e));
         if (bad_h) return fail(EP_EINVAL, "mesh has an element with non-positive Jacobian determinant");
+    }
+    if (ref) {
+        // refined operators: full float-float couplings; norm scale from a
+        // mass-matrix diagonal (keeps the float sums of squares in range)
+        epk::launch_expand(I->d, h, 1, 1, I->stream);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaStreamSynchronize(I->stream));
+        double m0 = 0.0;
+        CUDA_TRY(cudaMemcpy(&m0, h.M64, sizeof(double), cudaMemcpyDeviceToHost));
+        h.nscale = m0 > 0.0 ? (float)(1.0 / m0) : 1.0f;
+        // from here on the refined path reads only the float-float couplings
+        dfree(I, h.M64, epk::kSlots * N);
+        dfree(I, h.A64, epk::kSlots * N);
+        dfree(I, h.dinv64, N);
+        CUDA_TRY(cudaMemcpy(I->d, &h, sizeof(Dev), cudaMemcpyHostToDevice));
     }
     if (h.fib) {
         std::vector<float> f(6 * N);
@@ -672,6 +749,12 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     I->grid_nodes = std::max(1, std::min(blocks, 4 * sms));
     I->grid_ionic = blocks;
     I->grid_tiles = std::max(1, std::min(epk::st_tiles(h), 2 * sms));
+    if (ref) {
+        // the persistent solver's blocks must all be resident at once
+        const int occ = epk::pcg_blocks_per_sm();
+        if (occ <= 0) return fail(EP_ECUDA, "occupancy query of the persistent solver failed");
+        I->grid_pcg = std::max(1, std::min(std::min(epk::st_tiles(h), sms * occ), epk::kMaxPersistentBlocks));
+    }
     if (!ref) h.op32 = 0;  // no FP32 operator in the FP64 path
     if (ref && h.op32 == EP_OP_AUTO) {
         ep_status st2 = autotune_op32(I);
@@ -918,6 +1001,7 @@ ep_status ep_load_state(ep_instance* I, const void* buf, size_t bytes) {
     int zero = 0;
     CUDA_TRY(cudaMemcpy(&I->d->step, &step, sizeof(step), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(&I->d->status, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemset(t.counter, 0, epk::CNT_N * sizeof(unsigned int)));
     I->host_step = step;
     I->sticky = EP_OK;
     return EP_OK;
@@ -983,6 +1067,8 @@ ep_status ep_profile_read(ep_instance* I, ep_kernel_time* out, int32_t cap, int3
 
 ep_status ep_residual_norm_noalloc(const ep_instance* I, double* relres_out) {
     if (!I || !relres_out) return fail(EP_EINVAL, "NULL argument");
+    if (I->h.prec != EP_PREC_FP32_REFINED)
+        return fail(EP_EUNSUPPORTED, "the allocation-free residual serves FP32_REFINED instances");
     if (I->grid_tiles > epk::noalloc_max_blocks())
         return fail(EP_EINVAL, "the residual of this instance needs " + std::to_string(I->grid_tiles) +
                                    " thread blocks; the allocation-free path holds partial sums for at most " +

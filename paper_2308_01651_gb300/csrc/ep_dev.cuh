@@ -30,6 +30,8 @@ constexpr int kNodeTile = kNodeThreads * kNodesPerThread;
 // tiled stencil kernels: owned tile kStTx x kStTy x kStTz, threads per block
 constexpr int kStTx = 32, kStTy = 4, kStTz = 4;
 constexpr int kStThreads = 512;  // one owned node per thread
+// upper bound of a persistent grid (partial-sum buffers are sized for it)
+constexpr int kMaxPersistentBlocks = 2048;
 
 // Matrix-free FP32 tile (owned nodes per block): 32 x 8 x 4
 constexpr int kMfTx = 32, kMfTy = 8, kMfTz = 4;
@@ -63,13 +65,19 @@ struct Dev {
     double *s64_n, *s64_nm1;    // FP64 states [ns64][N]: all states (FP64) or
                                 // the TTP06 concentrations (FP32_REFINED)
     const uint8_t* cell;
-    double *v;                  // u_BDF/dt - I_ion + I_app
-    double *b, *r;              // FP64 right-hand side and residual
+    double *v;                  // u_BDF/dt - I_ion + I_app (FP64 path)
+    double *b, *r;              // FP64 right-hand side and residual (FP64 path)
+    // refined path, float-float (hi, lo): the solve's iterate u (starts at
+    // u_EXT), the nodal vector v and the right-hand side b = M v
+    float *u_hi, *u_lo, *v_hi, *v_lo, *b_hi, *b_lo;
+    float nscale;               // scale of b and r in the float sums of squares
     double *at, *best;
     // ---- operators -----------------------------------------------------------
-    double *M64, *A64;          // [kSlots][N]
+    double *M64, *A64;          // [kSlots][N] (symmetric, FP64)
     double *dinv64;
-    float *A32;                 // [kSlots][N] (stencil FP32 operator)
+    // refined path: all 27 couplings per node as float-float, [7][N] float4
+    // groups of hi parts and of lo parts (the FP32 inner operator is Ahi)
+    float4 *Ahi, *Alo, *Mhi, *Mlo;
     float *dinv32;
     float *fib;                 // [6][N]: f0/h, s0/h per component (matrix-free)
     float mf_cn[3], mf_cl, mf_ct, mf_cmass;
@@ -77,6 +85,7 @@ struct Dev {
     int op32;                   // EP_OP_MATRIX_FREE or EP_OP_STENCIL
     // ---- CG ------------------------------------------------------------------
     float *r32, *z32, *q32, *d32, *pa32, *pb32;
+    float *s32, *p32;           // persistent single-reduction CG: s, p
     double *z64, *q64, *pa64, *pb64;
     double rz, pq, alpha, beta, rr, rr0, bb, relres;
     double tol, inner_tol;
@@ -103,13 +112,14 @@ struct AsmParams {
     const double* s0;   // [N][3]
     double dl, dt, dn;  // diffusivities (cm^2/ms)
     double alpha_dt;    // alpha/dt of the system matrix A = alpha/dt M + K
-    int want32;         // also produce the FP32 stencil
     int* bad;           // set to 1 on a non-positive Jacobian determinant
 };
 
 // Counter slots (one per reducing kernel so that consecutive kernels never
 // share a counter).
-enum { CNT_RHS = 0, CNT_APPLY = 1, CNT_UPDATE = 2, CNT_RESID = 3, CNT_FINISH = 4, CNT_N = 8 };
+// CNT_BAR and CNT_BAR + 1: arrival count and generation of the persistent
+// solver's grid barrier.
+enum { CNT_RHS = 0, CNT_APPLY = 1, CNT_UPDATE = 2, CNT_RESID = 3, CNT_FINISH = 4, CNT_BAR = 6, CNT_N = 8 };
 
 // ---------------------------------------------------------------- helpers --
 

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "ep_dev.cuh"
+#include "ep_ff.cuh"
 
 namespace epk {
 
@@ -83,6 +84,58 @@ __device__ __forceinline__ void for_owned(const Dev& D, const TileGeo& g, F f) {
 
 __host__ __device__ inline int st_tiles(const Dev& h) {
     return ((h.NX + kStTx - 1) / kStTx) * ((h.NY + kStTy - 1) / kStTy) * ((h.NZ + kStTz - 1) / kStTz);
+}
+
+// ---- node-major full couplings -------------------------------------------
+// The refined solver keeps all 27 couplings of every node in 7 groups of
+// float4 ([7][N], group g holds offsets t = 4g .. 4g+3; t = 27 is padding
+// with coefficient 0): a row is 7 coalesced 16-byte loads at addresses known
+// from n alone.  Couplings to nodes outside the mesh are 0, and so is the
+// staged value there, so rows need no neighbour checks.
+constexpr int kGroups = 7;
+
+__host__ __device__ constexpr int t_dh(int t) {
+    return t >= 27 ? 0 : (t % 3 - 1) + SHX * ((t / 3) % 3 - 1) + SHX * SHY * (t / 9 - 1);
+}
+
+// FP32 row: sum_t c(t) x(h + dh(t)), t = 0..26 in order
+__device__ __forceinline__ float row_f32(const float4* __restrict__ c, size_t N, const float* xs, int h,
+                                         int n) {
+    float acc = 0.f;
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+        const float4 cv = c[(size_t)g * N + n];
+        acc = fmaf(cv.x, xs[h + t_dh(4 * g)], acc);
+        acc = fmaf(cv.y, xs[h + t_dh(4 * g + 1)], acc);
+        acc = fmaf(cv.z, xs[h + t_dh(4 * g + 2)], acc);
+        if (g < kGroups - 1) acc = fmaf(cv.w, xs[h + t_dh(4 * g + 3)], acc);
+    }
+    return acc;
+}
+
+// float-float row: (sh + sl) = sum_t (chi + clo)(t) * (xh + xl)(h + dh(t)),
+// t = 0..26 in order, normalised
+__device__ __forceinline__ void row_ff(const float4* __restrict__ chi, const float4* __restrict__ clo,
+                                       size_t N, const float* xh, const float* xl, int h, int n, float& sh,
+                                       float& sl) {
+    sh = 0.f;
+    sl = 0.f;
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+        const float4 a = chi[(size_t)g * N + n];
+        const float4 b = clo[(size_t)g * N + n];
+        int d = t_dh(4 * g);
+        ff_mac(a.x, b.x, xh[h + d], xl[h + d], sh, sl);
+        d = t_dh(4 * g + 1);
+        ff_mac(a.y, b.y, xh[h + d], xl[h + d], sh, sl);
+        d = t_dh(4 * g + 2);
+        ff_mac(a.z, b.z, xh[h + d], xl[h + d], sh, sl);
+        if (g < kGroups - 1) {
+            d = t_dh(4 * g + 3);
+            ff_mac(a.w, b.w, xh[h + d], xl[h + d], sh, sl);
+        }
+    }
+    ff_normalize(sh, sl);
 }
 
 }  // namespace epk

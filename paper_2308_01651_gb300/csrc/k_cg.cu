@@ -3,10 +3,11 @@
 //
 // The inner solver is Jacobi-preconditioned CG (the paper solves Eq. (6) with
 // CG, Sec. 2) on A delta = r in float; iterative refinement in double wraps
-// it (the FP64 residual is k_rhs with first = 0).  Activation time follows
+// it (k_ff.cu: float-float right-hand side, residual and update).  Activation time follows
 // Sec. 3.2.1: the time at which du/dt is largest, taken as the first maximum
 // of the forward difference u_{n+1} - u_n.
 #include "ep_dev.cuh"
+#include "ep_ff.cuh"
 
 namespace epk {
 
@@ -66,21 +67,21 @@ __global__ void __launch_bounds__(kNodeThreads) k_update32(Dev* __restrict__ Dp,
     });
 }
 
-// u_new += delta (FP64 refinement update)
-__global__ void __launch_bounds__(kNodeThreads) k_correct(Dev* __restrict__ Dp) {
-    const Dev& D = *Dp;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x)
-        D.u_new[n] += (double)D.d32[n];
-}
-
 // Activation update, non-finite check, rotation of the time levels.
 __global__ void __launch_bounds__(kNodeThreads) k_finish(Dev* __restrict__ Dp) {
     Dev& D = *Dp;
     const double t_new = (double)(D.step + 1) * D.dt;
     float v[1] = {0.f};
     const double none[1] = {0.0};
+    const bool ff = D.u_hi != nullptr;  // refined: the iterate is float-float
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x) {
-        const double un = D.u_new[n];
+        double un;
+        if (ff) {
+            un = ff_to_double(D.u_hi[n], D.u_lo[n]);
+            D.u_new[n] = un;
+        } else {
+            un = D.u_new[n];
+        }
         const double s = un - D.u_n[n];
         if (!isfinite(un)) v[0] += 1.f;
         if (s > D.best[n]) {
@@ -111,7 +112,6 @@ __global__ void __launch_bounds__(kNodeThreads) k_finish(Dev* __restrict__ Dp) {
 void launch_update32(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s) {
     k_update32<<<grid, kNodeThreads, 0, s>>>(d, graph);
 }
-void launch_correct(Dev* d, const Dev& h, int grid, cudaStream_t s) { k_correct<<<grid, kNodeThreads, 0, s>>>(d); }
 void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s) { k_finish<<<grid, kNodeThreads, 0, s>>>(d); }
 
 }  // namespace epk

@@ -1,0 +1,133 @@
+// k_ff.cu -- the FP64-accurate side of the refined solver (iterative
+// refinement around the FP32 inner CG) in float-float arithmetic.
+//
+// Paper Sec. 1.2, Eq. (6): b = M (u_BDF/dt - I_ion + I_app) and the residual
+// r = b - (alpha/dt M + K) u.  The nodal vector v and the iterate u (starting
+// at u_EXT) arrive as float-float from the ionic kernel; the stencils are the
+// node-major full couplings (hi and lo float parts).  Rows are accumulated
+// with exact products and TwoSum (ep_ff.cuh), ~1e-13 relative to the terms,
+// far below the refinement target of 1e-10 on ||r|| / ||b||, and entirely on
+// the FP32 pipe.  The inner solver's starting data (r32 = r, z32 = D^-1 r32,
+// delta = 0) is formed on the way.
+#include "ep_dev.cuh"
+#include "ep_tile.cuh"
+
+namespace epk {
+
+// stage the float-float pair (ah, al) of the tile plus halo
+__device__ __forceinline__ void stage_ff(const Dev& D, const TileGeo& g, int* sidx, const float* ah,
+                                         const float* al, float* sh, float* sl) {
+    stage_tile<float>(D, g, sidx, sh, [&](int n, bool) { return ah[n]; });
+    // same halo positions per thread as above, so sidx is already this thread's
+    for (int h = threadIdx.x; h < SHN; h += blockDim.x) {
+        const int n = sidx[h];
+        sl[h] = n >= 0 ? al[n] : 0.f;
+    }
+}
+
+// FIRST: b = M v, r = b - A u; otherwise r = b - A u with the stored b.
+template <int FIRST>
+__global__ void __launch_bounds__(kStThreads) k_rhs_ff(Dev* __restrict__ Dp, int graph) {
+    __shared__ int sidx[SHN];
+    __shared__ float suh[SHN], sul[SHN];
+    __shared__ float svh[FIRST ? SHN : 1], svl[FIRST ? SHN : 1];
+    Dev& D = *Dp;
+    const size_t N = (size_t)D.N;
+    const float ns = D.nscale;
+    // (ns b)^2, (ns r)^2, r32 z32, r32 r32
+    float vf[4] = {0.f, 0.f, 0.f, 0.f};
+    const double none[1] = {0.0};
+    const int ntiles = st_tiles(D);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const TileGeo g = tile_geo(D, tile);
+        __syncthreads();
+        stage_ff(D, g, sidx, D.u_hi, D.u_lo, suh, sul);
+        if (FIRST) {
+            for (int h = threadIdx.x; h < SHN; h += blockDim.x) {
+                const int n = sidx[h];
+                svh[h] = n >= 0 ? D.v_hi[n] : 0.f;
+                svl[h] = n >= 0 ? D.v_lo[n] : 0.f;
+            }
+        }
+        __syncthreads();
+        for_owned(D, g, [&](int h) {
+            const int n = sidx[h];
+            float bh, bl;
+            if (FIRST) {
+                row_ff(D.Mhi, D.Mlo, N, svh, svl, h, n, bh, bl);
+                D.b_hi[n] = bh;
+                D.b_lo[n] = bl;
+            } else {
+                bh = D.b_hi[n];
+                bl = D.b_lo[n];
+            }
+            float ah, al, rh, rl;
+            row_ff(D.Ahi, D.Alo, N, suh, sul, h, n, ah, al);
+            ff_sub(bh, bl, ah, al, rh, rl);
+            const float r32 = rh;  // nearest float of the normalised pair
+            const float z = D.dinv32[n] * r32;
+            D.r32[n] = r32;
+            D.z32[n] = z;
+            D.d32[n] = 0.0f;
+            const float bs = ns * bh, rs = ns * rh;
+            vf[0] = fmaf(bs, bs, vf[0]);
+            vf[1] = fmaf(rs, rs, vf[1]);
+            vf[2] = fmaf(r32, z, vf[2]);
+            vf[3] = fmaf(r32, r32, vf[3]);
+        });
+    }
+    grid_reduce<4, 0>(vf, none, D.partial, D.counter + CNT_RHS, blockIdx.x, gridDim.x, [&](double* t) {
+        if (FIRST) D.bb = t[0];
+        const double rr = t[1], bb = D.bb;
+        const bool nan = !(rr == rr);
+        const bool conv = !nan && (rr <= D.tol * D.tol * bb);
+        D.relres = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+        if (nan && D.status == EP_OK) D.status = EP_ENAN;
+        D.it = 0;
+        D.beta = 0.0;
+        D.rz = t[2];
+        D.rr0 = t[3];
+        D.rr = t[3];
+        if (FIRST) {
+            D.sweeps = 0;
+            D.it_total = 0;
+        } else {
+            D.sweeps += 1;
+            if (!conv && D.sweeps >= D.max_sweeps && D.status == EP_OK) D.status = EP_ENOCONV;
+        }
+        set_cond(graph ? D.h_outer : 0ull, &D.f_outer, (!conv && !nan && D.sweeps < D.max_sweeps) ? 1u : 0u);
+        // the next inner loop starts enabled (with the per-iteration inner
+        // loop its handle belongs to the refinement body, where this runs)
+        if (FIRST) D.f_inner = 1;
+        else set_cond(graph ? D.h_inner : 0ull, &D.f_inner, 1u);
+    });
+}
+
+// u += delta in float-float.  The sum is stored as the canonical pair of its
+// double value (hi = nearest float, lo = the rest), the pair the next step's
+// ionic kernel and any reader of u_n derive from the double, so a pair and
+// its double always map to each other.
+__global__ void __launch_bounds__(kNodeThreads) k_correct_ff(Dev* __restrict__ Dp) {
+    const Dev& D = *Dp;
+    float* __restrict__ uh = D.u_hi;
+    float* __restrict__ ul = D.u_lo;
+    const float* __restrict__ d = D.d32;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x) {
+        float h = uh[n], l = ul[n];
+        ff_add_f(h, l, d[n], h, l);
+        ff_from_double(ff_to_double(h, l), h, l);
+        uh[n] = h;
+        ul[n] = l;
+    }
+}
+
+void launch_rhs_ff(Dev* d, const Dev& h, int first, int graph, int grid, cudaStream_t s) {
+    if (first) k_rhs_ff<1><<<grid, kStThreads, 0, s>>>(d, graph);
+    else k_rhs_ff<0><<<grid, kStThreads, 0, s>>>(d, graph);
+}
+
+void launch_correct_ff(Dev* d, const Dev& h, int grid, cudaStream_t s) {
+    k_correct_ff<<<grid, kNodeThreads, 0, s>>>(d);
+}
+
+}  // namespace epk

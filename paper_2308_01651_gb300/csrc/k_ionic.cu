@@ -9,7 +9,8 @@
 //   I_ion,j = I_ion(u_EXT, w_{n+1}) (ionic current interpolation);
 //   I_app,j = sum of the active pulses' amplitudes at the node;
 //   v_j = u_BDF/dt - I_ion + I_app (Eq. (6) right-hand side is M v);
-//   u_new,j = u_EXT (initial guess of the linear solve).
+//   u_EXT (initial guess of the linear solve), both stored as double (FP64
+//   path) or float-float (refined path).
 // The new states overwrite the w_{n-1} slot (each thread owns its node), and
 // the finishing kernel of the step swaps the slots.
 //
@@ -20,6 +21,7 @@
 // precomputed): GB300's FP64 pipe is ~60x slower than FP32.
 #include "ep_dev.cuh"
 #include "ionic_models.cuh"
+#include "ep_ff.cuh"
 
 namespace epk {
 
@@ -57,6 +59,18 @@ __device__ __forceinline__ double applied(const Dev& D, const StepConsts& c, int
     for (int p = 0; p < EP_MAX_PULSES; ++p)
         if (c.iamp[p] != 0.0 && D.mask[p][n]) s += c.iamp[p];
     return s;
+}
+
+// The right-hand side's nodal vector v and the solve's initial guess u_EXT:
+// double in the FP64 path, float-float pairs in the refined one.
+__device__ __forceinline__ void store_vu(const Dev& D, int n, double v, double uE) {
+    if (D.v_hi) {
+        ff_from_double(v, D.v_hi[n], D.v_lo[n]);
+        ff_from_double(uE, D.u_hi[n], D.u_lo[n]);
+    } else {
+        D.v[n] = v;
+        D.u_new[n] = uE;
+    }
 }
 
 // G: arithmetic/storage type of the gates (float when refined, double in the
@@ -103,8 +117,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Dev* __restrict__ Dp)
             wm[(size_t)k * N + n] = w1[k];
         }
         const double I = (double)BO<G>::iion(G(uE), w1[0], w1[1], w1[2]);
-        D.v[n] = fma(uB, c.inv_dt, applied(D, c, n) - I);
-        D.u_new[n] = uE;
+        store_vu(D, n, fma(uB, c.inv_dt, applied(D, c, n) - I), uE);
     }
 }
 
@@ -177,8 +190,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_tt(Dev* __restrict__ Dp)
         typename TT<G>::Cur cur;
         TT<G>::currents(cell, G(uE), g1, G(c1[0]), G(c1[2]), G(c1[3]), G(c1[4]), cur);
         const double I = (double)TT<G>::iion_of(cur);
-        D.v[n] = fma(uB, c.inv_dt, applied(D, c, n) - I);
-        D.u_new[n] = uE;
+        store_vu(D, n, fma(uB, c.inv_dt, applied(D, c, n) - I), uE);
     }
 }
 

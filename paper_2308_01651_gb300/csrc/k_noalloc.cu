@@ -22,10 +22,10 @@
 // the counter before its kernel runs, and calls whose work overlaps on the
 // GPU (different streams, no ordering) race on the array.
 //
-// The kernel is a variant of the FP64 residual kernel (k_rhs, residual
-// mode): same tiles, same per-thread and per-block summation order, so it
-// reproduces the solver's own residual norm; it writes nothing but the
-// scratch array.
+// The kernel is a variant of the refined solver's residual kernel (k_rhs_ff,
+// residual mode, float-float): same tiles, same per-thread and per-block
+// summation order, so it reproduces the solver's own residual norm; it writes
+// nothing but the scratch array.  It serves FP32_REFINED instances.
 #include <mutex>
 #include <string>
 
@@ -45,30 +45,45 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 __global__ void __launch_bounds__(kStThreads) k_residual_norm_noalloc(const Dev* __restrict__ Dp,
                                                                        unsigned char* scratch) {
     __shared__ int sidx[SHN];
-    __shared__ double su[SHN];
+    __shared__ float suh[SHN], sul[SHN];
     const Dev& D = *Dp;
     const size_t N = (size_t)D.N;
     const double* __restrict__ u = D.u_n;  // the last solve's solution
+    const float ns = D.nscale;
     double* partial = reinterpret_cast<double*>(scratch);
     double* total = reinterpret_cast<double*>(scratch + kNoAllocTotalOff);
     unsigned int* counter = reinterpret_cast<unsigned int*>(scratch + kNoAllocCounterOff);
-    double vd[2] = {0.0, 0.0};
-    const float none[1] = {0.f};
+    float vf[2] = {0.f, 0.f};
+    const double none[1] = {0.0};
     const int ntiles = st_tiles(D);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const TileGeo g = tile_geo(D, tile);
         __syncthreads();
-        stage_tile<double>(D, g, sidx, su, [&](int n, bool) { return u[n]; });
+        // the solution back as the float-float pair the solver iterated on
+        stage_tile<float>(D, g, sidx, suh, [&](int n, bool) {
+            float h, l;
+            ff_from_double(u[n], h, l);
+            return h;
+        });
+        for (int h = threadIdx.x; h < SHN; h += blockDim.x) {
+            const int n = sidx[h];
+            float uh = 0.f, ul = 0.f;
+            if (n >= 0) ff_from_double(u[n], uh, ul);
+            sul[h] = ul;
+        }
         __syncthreads();
         for_owned(D, g, [&](int h) {
             const int n = sidx[h];
-            const double b = D.b[n];
-            const double r = b - tile_row<double, double, double>(D.A64, N, sidx, su, h, n);
-            vd[0] = fma(b, b, vd[0]);
-            vd[1] = fma(r, r, vd[1]);
+            const float bh = D.b_hi[n], bl = D.b_lo[n];
+            float ah, al, rh, rl;
+            row_ff(D.Ahi, D.Alo, N, suh, sul, h, n, ah, al);
+            ff_sub(bh, bl, ah, al, rh, rl);
+            const float bs = ns * bh, rs = ns * rh;
+            vf[0] = fmaf(bs, bs, vf[0]);
+            vf[1] = fmaf(rs, rs, vf[1]);
         });
     }
-    grid_reduce<0, 2>(none, vd, partial, counter, blockIdx.x, gridDim.x, [&](double* t) {
+    grid_reduce<2, 0>(vf, none, partial, counter, blockIdx.x, gridDim.x, [&](double* t) {
         total[0] = t[0];
         total[1] = t[1];
     });

@@ -13,9 +13,10 @@
 // rather than distributed CSR, because on GB300 the FP64 arithmetic of a
 // matrix-free apply would cost far more than streaming the stencil.
 //
-// Kernels: assembly (node-centric, deterministic, no atomics), the FP64
-// right-hand side / residual, the FP64 CG apply and updates, and the FP32
-// stencil apply of the refined inner solver.
+// Kernels: assembly (node-centric, deterministic, no atomics), the expansion
+// of the stencils into the refined solver's full float-float layout, the
+// FP64 path's right-hand side / residual and CG apply and updates, and the
+// FP32 stencil apply of the refined inner solver.
 #include "ep_dev.cuh"
 #include "ep_tile.cuh"
 
@@ -157,7 +158,6 @@ __global__ void __launch_bounds__(128) k_assemble(Dev* __restrict__ Dp, AsmParam
         const double av = ck[s] + P.alpha_dt * cm[s];
         D.M64[(size_t)s * D.N + n] = cm[s];
         D.A64[(size_t)s * D.N + n] = av;
-        if (P.want32) D.A32[(size_t)s * D.N + n] = (float)av;
     }
     const double dinv = 1.0 / (ck[0] + P.alpha_dt * cm[0]);
     D.dinv64[n] = dinv;
@@ -177,20 +177,84 @@ __global__ void k_realpha(Dev* __restrict__ Dp, double delta, double alpha_dt, f
         const size_t o = (size_t)s * D.N + n;
         const double av = D.A64[o] + delta * D.M64[o];
         D.A64[o] = av;
-        if (D.A32) D.A32[o] = (float)av;
     }
     const double dinv = 1.0 / D.A64[n];
     D.dinv64[n] = dinv;
     if (D.dinv32) D.dinv32[n] = (float)dinv;
 }
 
+// Refined path (the FP64 stencils are gone after ep_create): the same
+// change applied to the float-float couplings, each coefficient re-split from
+// its double sum; the inverse diagonal (offset 13: group 3, component y)
+// follows.
+__global__ void k_realpha_ff(Dev* __restrict__ Dp, double delta, double alpha_dt, float cmass) {
+    Dev& D = *Dp;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        D.alpha_dt = alpha_dt;
+        D.mf_cmass = cmass;
+    }
+    if (n >= D.N) return;
+    const size_t N = (size_t)D.N;
+    for (int g = 0; g < kGroups; ++g) {
+        const size_t o = (size_t)g * N + n;
+        const float4 ah = D.Ahi[o], al = D.Alo[o], mh = D.Mhi[o], ml = D.Mlo[o];
+        float h4[4] = {ah.x, ah.y, ah.z, ah.w}, l4[4] = {al.x, al.y, al.z, al.w};
+        const float mh4[4] = {mh.x, mh.y, mh.z, mh.w}, ml4[4] = {ml.x, ml.y, ml.z, ml.w};
+        for (int c = 0; c < 4; ++c) {
+            const double v = ((double)h4[c] + (double)l4[c]) + delta * ((double)mh4[c] + (double)ml4[c]);
+            ff_from_double(v, h4[c], l4[c]);
+        }
+        D.Ahi[o] = make_float4(h4[0], h4[1], h4[2], h4[3]);
+        D.Alo[o] = make_float4(l4[0], l4[1], l4[2], l4[3]);
+        if (g == 3) D.dinv32[n] = (float)(1.0 / ((double)h4[1] + (double)l4[1]));
+    }
+}
+
+// Full couplings of node n for the refined solver: for offset t the forward
+// slot of n (t > 13), the diagonal (t = 13), or the forward slot 13 - t of the
+// neighbour n + off(t) (t < 13; 0 where that node does not exist), split
+// into float hi + lo parts, written to [7][N] float4 groups.
+__global__ void k_expand(Dev* __restrict__ Dp, int want_a, int want_m) {
+    const Dev& D = *Dp;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= D.N) return;
+    int i, j, k;
+    node_ijk(D, n, i, j, k);
+    const size_t N = (size_t)D.N;
+    for (int which = 0; which < 2; ++which) {
+        if ((which == 0 && !want_a) || (which == 1 && !want_m)) continue;
+        const double* c = which == 0 ? D.A64 : D.M64;
+        float4* hi = which == 0 ? D.Ahi : D.Mhi;
+        float4* lo = which == 0 ? D.Alo : D.Mlo;
+        float h4[4], l4[4];
+        for (int t = 0; t < 28; ++t) {
+            double v = 0.0;
+            if (t == 13) {
+                v = c[n];
+            } else if (t < 27) {
+                const int di = t % 3 - 1, dj = (t / 3) % 3 - 1, dk = t / 9 - 1;
+                const int m = neighbour(D, i, j, k, di, dj, dk);
+                if (m >= 0) v = t > 13 ? c[(size_t)(t - 13) * N + n] : c[(size_t)(13 - t) * N + m];
+            }
+            float vh, vl;
+            ff_from_double(v, vh, vl);
+            h4[t & 3] = vh;
+            l4[t & 3] = vl;
+            if ((t & 3) == 3) {
+                hi[(size_t)(t >> 2) * N + n] = make_float4(h4[0], h4[1], h4[2], h4[3]);
+                lo[(size_t)(t >> 2) * N + n] = make_float4(l4[0], l4[1], l4[2], l4[3]);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- applies --
 
-// FP64 right-hand side and initial residual (first == 1), or residual only
-// (first == 0):  b = M v,  r = b - A u_new.  Also forms the preconditioned
-// residual for the next solver stage and the reductions it needs.
-template <bool REF>
-__global__ void __launch_bounds__(kStThreads) k_rhs(Dev* __restrict__ Dp, int first, int graph) {
+// FP64 path: right-hand side and initial residual (first == 1), or residual
+// only (first == 0):  b = M v,  r = b - A u_new, z = D^-1 r, and the
+// reductions the CG needs.
+__global__ void __launch_bounds__(kStThreads) k_rhs64(Dev* __restrict__ Dp, int first, int graph) {
     __shared__ int sidx[SHN];
     __shared__ double su[SHN];
     __shared__ double sv[SHN];
@@ -198,9 +262,7 @@ __global__ void __launch_bounds__(kStThreads) k_rhs(Dev* __restrict__ Dp, int fi
     const size_t N = (size_t)D.N;
     const double* __restrict__ vv = D.v;
     const double* __restrict__ u = D.u_new;
-    // FP64 sums (b.b, r.r[, r.z]) and, refined, FP32 sums (r32.z32, r32.r32)
-    float vf[2] = {0.f, 0.f};
-    double vd[3] = {0.0, 0.0, 0.0};
+    double vd[3] = {0.0, 0.0, 0.0};  // b.b, r.r, r.z
     const int ntiles = st_tiles(D);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const TileGeo g = tile_geo(D, tile);
@@ -227,60 +289,25 @@ __global__ void __launch_bounds__(kStThreads) k_rhs(Dev* __restrict__ Dp, int fi
             D.r[n] = r;
             vd[0] = fma(b, b, vd[0]);
             vd[1] = fma(r, r, vd[1]);
-            if (REF) {
-                const float r32 = (float)r;
-                const float z = D.dinv32[n] * r32;
-                D.r32[n] = r32;
-                D.z32[n] = z;
-                D.d32[n] = 0.0f;
-                vf[0] = fmaf(r32, z, vf[0]);
-                vf[1] = fmaf(r32, r32, vf[1]);
-            } else {
-                const double z = D.dinv64[n] * r;
-                D.z64[n] = z;
-                vd[2] = fma(r, z, vd[2]);
-            }
+            const double z = D.dinv64[n] * r;
+            D.z64[n] = z;
+            vd[2] = fma(r, z, vd[2]);
         });
     }
-    auto fin = [&](double bb_now, double rr, double rz, double rr32) {
-        if (first) D.bb = bb_now;
-        const double bb = D.bb;
+    const float none[1] = {0.f};
+    grid_reduce<0, 3>(none, vd, D.partial, D.counter + CNT_RHS, blockIdx.x, gridDim.x, [&](double* t) {
+        if (first) D.bb = t[0];
+        const double rr = t[1], bb = D.bb;
         const bool nan = !(rr == rr);
         const bool conv = !nan && (rr <= D.tol * D.tol * bb);
         D.relres = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
         if (nan && D.status == EP_OK) D.status = EP_ENAN;
         D.it = 0;
         D.beta = 0.0;
-        D.rz = rz;
-        if (REF) {
-            D.rr0 = rr32;
-            D.rr = rr32;
-            if (first) {
-                D.sweeps = 0;
-                D.it_total = 0;
-            } else {
-                D.sweeps += 1;
-                if (!conv && D.sweeps >= D.max_sweeps && D.status == EP_OK) D.status = EP_ENOCONV;
-            }
-            set_cond(graph ? D.h_outer : 0ull, &D.f_outer, (!conv && !nan && D.sweeps < D.max_sweeps) ? 1u : 0u);
-            // the next inner loop starts enabled (its handle belongs to the
-            // refinement body, which is where the residual kernel runs)
-            if (first) D.f_inner = 1;
-            else set_cond(graph ? D.h_inner : 0ull, &D.f_inner, 1u);
-        } else {
-            D.rr = rr;
-            set_cond(graph ? D.h_loop : 0ull, &D.f_loop, (!conv && !nan) ? 1u : 0u);
-        }
-    };
-    if constexpr (REF) {
-        const double vd2[2] = {vd[0], vd[1]};
-        grid_reduce<2, 2>(vf, vd2, D.partial, D.counter + CNT_RHS, blockIdx.x, gridDim.x,
-                          [&](double* t) { fin(t[2], t[3], t[0], t[1]); });
-    } else {
-        const float none[1] = {0.f};
-        grid_reduce<0, 3>(none, vd, D.partial, D.counter + CNT_RHS, blockIdx.x, gridDim.x,
-                          [&](double* t) { fin(t[0], t[1], t[2], 0.0); });
-    }
+        D.rz = t[2];
+        D.rr = rr;
+        set_cond(graph ? D.h_loop : 0ull, &D.f_loop, (!conv && !nan) ? 1u : 0u);
+    });
 }
 
 // FP64 CG: p = z + beta p (beta == 0: p = z)
@@ -371,7 +398,7 @@ __global__ void __launch_bounds__(kStThreads) k_apply32_stencil(Dev* __restrict_
         __syncthreads();
         for_owned(D, g, [&](int h) {
             const int n = sidx[h];
-            const float q = tile_row<float, float, float>(D.A32, N, sidx, sp, h, n);
+            const float q = row_f32(D.Ahi, N, sp, h, n);
             D.q32[n] = q;
             v[0] = fmaf(sp[h], q, v[0]);
         });
@@ -386,9 +413,14 @@ void launch_assemble(Dev* d, const Dev& h, const AsmParams& P, cudaStream_t s) {
 void launch_realpha(Dev* d, const Dev& h, double delta, double alpha_dt, float cmass, cudaStream_t s) {
     k_realpha<<<(h.N + 255) / 256, 256, 0, s>>>(d, delta, alpha_dt, cmass);
 }
-void launch_rhs(Dev* d, const Dev& h, int first, int graph, int grid, cudaStream_t s) {
-    if (h.prec == EP_PREC_FP32_REFINED) k_rhs<true><<<grid, kStThreads, 0, s>>>(d, first, graph);
-    else k_rhs<false><<<grid, kStThreads, 0, s>>>(d, first, graph);
+void launch_realpha_ff(Dev* d, const Dev& h, double delta, double alpha_dt, float cmass, cudaStream_t s) {
+    k_realpha_ff<<<(h.N + 255) / 256, 256, 0, s>>>(d, delta, alpha_dt, cmass);
+}
+void launch_rhs64(Dev* d, const Dev& h, int first, int graph, int grid, cudaStream_t s) {
+    k_rhs64<<<grid, kStThreads, 0, s>>>(d, first, graph);
+}
+void launch_expand(Dev* d, const Dev& h, int want_a, int want_m, cudaStream_t s) {
+    k_expand<<<(h.N + 127) / 128, 128, 0, s>>>(d, want_a, want_m);
 }
 void launch_p64(Dev* d, const Dev& h, int grid, cudaStream_t s) { k_p64<<<grid, kNodeThreads, 0, s>>>(d); }
 void launch_apply64(Dev* d, const Dev& h, int grid, cudaStream_t s) { k_apply64<<<grid, kStThreads, 0, s>>>(d); }

@@ -82,15 +82,21 @@ def test_create_rejects_bad_mesh_and_inputs():
 
 
 def test_footprint_scales_with_nodes():
-    small = I.slab_mesh(10, 10, 10, (0.1, 0.1, 0.1))
-    big = I.slab_mesh(20, 20, 20, (0.2, 0.2, 0.2))
+    small = I.slab_mesh(30, 30, 30, (0.3, 0.3, 0.3))
+    big = I.slab_mesh(60, 60, 60, (0.6, 0.6, 0.6))
     for prec in (ep.EP_PREC_FP64, ep.EP_PREC_FP32_REFINED):
         a = ep.ep_footprint_bytes(small, I.TTP06, precision=prec)
         b = ep.ep_footprint_bytes(big, I.TTP06, precision=prec)
         assert a > 0 and 6.5 < b / a < 8.5
     assert ep.ep_footprint_bytes(small, 9) == 0
-    # the refined path stores the TTP06 gates in float: smaller footprint
-    assert ep.ep_footprint_bytes(big, I.TTP06, precision=ep.EP_PREC_FP32_REFINED) < \
+    # per-node budget: the FP64 path keeps the symmetric 14-slot stencils in
+    # double; the refined path keeps all 27 couplings of A and M as float-float
+    # (448 B/node) but its TTP06 gates in float.  Both stay under 768 B/node,
+    # i.e. above 3.5e8 nodes in 280 GB of HBM.
+    n = 61 ** 3
+    for prec in (ep.EP_PREC_FP64, ep.EP_PREC_FP32_REFINED):
+        assert ep.ep_footprint_bytes(big, I.TTP06, precision=prec) < 768 * n
+    assert ep.ep_footprint_bytes(big, I.BO, precision=ep.EP_PREC_FP64) < \
         ep.ep_footprint_bytes(big, I.TTP06, precision=ep.EP_PREC_FP64)
 
 

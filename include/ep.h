@@ -235,10 +235,13 @@ ep_status ep_profile_read(ep_instance* inst, ep_kernel_time* out, int32_t cap,
 
 /* Allocation-free residual check.  The paper has no counterpart: this is a
  * service of the library.  Writes to *relres_out the relative residual
- * ||b - A u_n||_2 / ||b||_2 of an FP32_REFINED instance's last linear solve
+ * ||b - A u||_2 / ||b||_2 of an FP32_REFINED instance's last linear solve
  * (the value ep_get_stats reports as relres), recomputed from the instance's
- * operator and vectors in the same float-float arithmetic as the solver's
- * residual; other instances get EP_EUNSUPPORTED.  It calls no cudaMalloc, cudaFree
+ * operator, right-hand side and the solver's float-float iterate u (whose sum
+ * rounded to double is the potential u_n) in the same arithmetic as the
+ * solver's residual; other instances get EP_EUNSUPPORTED.  After ep_state_load
+ * it still describes the last solve run, not the loaded state.  It calls no
+ * cudaMalloc, cudaFree
  * or other allocating routine, for callers that must not allocate device
  * memory where they check a solve (while capturing a stream into a graph, in
  * a host callback, under an external allocator that owns all device memory).

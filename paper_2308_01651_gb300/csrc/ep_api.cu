@@ -196,7 +196,8 @@ size_t footprint(const Sizes& z) {
         b += 4 * al(epk::kGroups * N * 16);                              // Ahi Alo Mhi Mlo
         b += 6 * al(N * 4);                                              // u, v, b (hi, lo)
         if (z.op32 != EP_OP_STENCIL) b += al(6 * N * 4);                 // fibres
-        b += 8 * al(N * 4);               // r32 z32 q32 d32 pa32 pb32 s32 p32
+        b += 6 * al(N * 4);               // r32 z32 q32 d32 pa32 pb32
+        b += al(N);                       // boundary flags
     } else {
         b += 4 * al(N * 8);               // z64 q64 pa64 pb64
     }
@@ -601,8 +602,7 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         ALLOC(h.d32, N);
         ALLOC(h.pa32, N);
         ALLOC(h.pb32, N);
-        ALLOC(h.s32, N);
-        ALLOC(h.p32, N);
+        ALLOC(h.nflag, N);
     } else {
         ALLOC(h.z64, N);
         ALLOC(h.q64, N);
@@ -753,7 +753,8 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         // the persistent solver's blocks must all be resident at once
         const int occ = epk::pcg_blocks_per_sm();
         if (occ <= 0) return fail(EP_ECUDA, "occupancy query of the persistent solver failed");
-        I->grid_pcg = std::max(1, std::min(std::min(epk::st_tiles(h), sms * occ), epk::kMaxPersistentBlocks));
+        const int want = (int)((N + epk::kPcgThreads - 1) / epk::kPcgThreads);
+        I->grid_pcg = std::max(1, std::min(std::min(want, sms * occ), epk::kMaxPersistentBlocks));
     }
     if (!ref) h.op32 = 0;  // no FP32 operator in the FP64 path
     if (ref && h.op32 == EP_OP_AUTO) {

@@ -32,6 +32,7 @@ constexpr int kStTx = 32, kStTy = 4, kStTz = 4;
 constexpr int kStThreads = 512;  // one owned node per thread
 // upper bound of a persistent grid (partial-sum buffers are sized for it)
 constexpr int kMaxPersistentBlocks = 2048;
+constexpr int kPcgThreads = 512;  // block of the persistent inner solver
 
 // Matrix-free FP32 tile (owned nodes per block): 32 x 8 x 4
 constexpr int kMfTx = 32, kMfTy = 8, kMfTz = 4;
@@ -85,7 +86,7 @@ struct Dev {
     int op32;                   // EP_OP_MATRIX_FREE or EP_OP_STENCIL
     // ---- CG ------------------------------------------------------------------
     float *r32, *z32, *q32, *d32, *pa32, *pb32;
-    float *s32, *p32;           // persistent single-reduction CG: s, p
+    unsigned char* nflag;       // boundary flags per node (bits: i=0, i=NX-1, j=0, j=NY-1, k=0, k=NZ-1)
     double *z64, *q64, *pa64, *pb64;
     double rz, pq, alpha, beta, rr, rr0, bb, relres;
     double tol, inner_tol;

@@ -103,10 +103,7 @@ __global__ void __launch_bounds__(kStThreads) k_rhs_ff(Dev* __restrict__ Dp, int
     });
 }
 
-// u += delta in float-float.  The sum is stored as the canonical pair of its
-// double value (hi = nearest float, lo = the rest), the pair the next step's
-// ionic kernel and any reader of u_n derive from the double, so a pair and
-// its double always map to each other.
+// u += delta in float-float
 __global__ void __launch_bounds__(kNodeThreads) k_correct_ff(Dev* __restrict__ Dp) {
     const Dev& D = *Dp;
     float* __restrict__ uh = D.u_hi;
@@ -115,7 +112,6 @@ __global__ void __launch_bounds__(kNodeThreads) k_correct_ff(Dev* __restrict__ D
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x) {
         float h = uh[n], l = ul[n];
         ff_add_f(h, l, d[n], h, l);
-        ff_from_double(ff_to_double(h, l), h, l);
         uh[n] = h;
         ul[n] = l;
     }

@@ -1,5 +1,6 @@
-// k_noalloc.cu -- ep_residual_norm_noalloc: the relative FP64 residual
-// ||b - A u_n|| / ||b|| of an instance's last linear solve, computed without
+// k_noalloc.cu -- ep_residual_norm_noalloc: the relative residual
+// ||b - A u|| / ||b|| of an instance's last linear solve (u the solver's
+// float-float iterate, whose sum rounded to double is u_n), computed without
 // allocating anything.
 //
 // Who needs it: code that must not call cudaMalloc at the point where it
@@ -48,7 +49,6 @@ __global__ void __launch_bounds__(kStThreads) k_residual_norm_noalloc(const Dev*
     __shared__ float suh[SHN], sul[SHN];
     const Dev& D = *Dp;
     const size_t N = (size_t)D.N;
-    const double* __restrict__ u = D.u_n;  // the last solve's solution
     const float ns = D.nscale;
     double* partial = reinterpret_cast<double*>(scratch);
     double* total = reinterpret_cast<double*>(scratch + kNoAllocTotalOff);
@@ -59,17 +59,11 @@ __global__ void __launch_bounds__(kStThreads) k_residual_norm_noalloc(const Dev*
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const TileGeo g = tile_geo(D, tile);
         __syncthreads();
-        // the solution back as the float-float pair the solver iterated on
-        stage_tile<float>(D, g, sidx, suh, [&](int n, bool) {
-            float h, l;
-            ff_from_double(u[n], h, l);
-            return h;
-        });
+        // the solver's float-float iterate (u_n is its sum rounded to double)
+        stage_tile<float>(D, g, sidx, suh, [&](int n, bool) { return D.u_hi[n]; });
         for (int h = threadIdx.x; h < SHN; h += blockDim.x) {
             const int n = sidx[h];
-            float uh = 0.f, ul = 0.f;
-            if (n >= 0) ff_from_double(u[n], uh, ul);
-            sul[h] = ul;
+            sul[h] = n >= 0 ? D.u_lo[n] : 0.f;
         }
         __syncthreads();
         for_owned(D, g, [&](int h) {

@@ -4,28 +4,27 @@
 // Jacobi-preconditioned CG (the paper solves Eq. (6) with CG, Sec. 2) on
 // A delta = r in float, A the hi parts of the node-major full couplings, in
 // the single-reduction arrangement of Chronopoulos and Gear (1989): with
-// u = D^-1 r and w = A u, both dot products of an iteration, (r, u) and
-// (u, w), come from the same pass, so every iteration is ONE pass over the
-// data and ONE grid barrier.  Iteration i, given alpha_i and beta_i:
-//   s_i = w_i + beta_i s_{i-1},   r_{i+1} = r_i - alpha_i s_i,
-//   p_i = u_i + beta_i p_{i-1},   delta  += alpha_i p_i,
-//   u_{i+1} = D^-1 r_{i+1},       w_{i+1} = A u_{i+1},
-//   gamma = (r_{i+1}, u_{i+1}), eta = (u_{i+1}, w_{i+1}), rho = (r_{i+1}, r_{i+1}),
-//   beta_{i+1} = gamma_{i+1} / gamma_i,
-//   alpha_{i+1} = gamma_{i+1} / (eta_{i+1} - beta_{i+1} gamma_{i+1} / alpha_i).
-// Every block of a grid that fits on the GPU at once owns a fixed set of
-// tiles.  Per tile it stages u_{i+1} on the tile plus halo in shared memory,
-// recomputing s_i and r_{i+1} of the halo nodes itself from the previous
-// iteration's r, w, s (double-buffered, so no block overwrites what another
-// still reads) -- the same expression in every block, hence the same bits --
-// and writes r, s, p, delta of its owned nodes and w = A u for them.  The
-// block partials of gamma, eta, rho are published, a bounded grid barrier
-// waits for all blocks, and every block sums all partials in the same fixed
-// order, so all blocks take the same alpha, beta and stopping decision.
-// A first pass (no update) forms w_0 = A u_0 and the starting sums.  Data
-// written by one block and read by another within the launch is read through
-// L2 (__ldcg); a barrier that does not complete within ~1 s records
-// EP_ETIMEOUT and the kernel returns.
+// u = D^-1 r and w = A u, both dot products of an iteration come from the
+// same pass.  Iteration i, given alpha_i and beta_i:
+//   update (every node on its own):
+//     s_i = w_i + beta_i s_{i-1},   r_{i+1} = r_i - alpha_i s_i,
+//     p_i = u_i + beta_i p_{i-1},   delta  += alpha_i p_i,   u_{i+1} = D^-1 r_{i+1}
+//   grid barrier (u_{i+1} of the neighbours is needed next)
+//   apply: w_{i+1} = A u_{i+1}; block partials of
+//     gamma = (r_{i+1}, u_{i+1}), eta = (u_{i+1}, w_{i+1}), rho = (r_{i+1}, r_{i+1})
+//   grid barrier; every block sums all partials in the same fixed order, so
+//   all blocks take the same
+//     beta_{i+1} = gamma_{i+1} / gamma_i,
+//     alpha_{i+1} = gamma_{i+1} / (eta_{i+1} - beta_{i+1} gamma_{i+1} / alpha_i)
+//   and the same stopping decision (rho relative to the sweep's first rho).
+// The right-hand-side kernel leaves r_0 and u_0 = D^-1 r_0, so the launch
+// starts with the apply of u_0.  Nodes are spread over all threads of the
+// grid in index order (thread t: nodes t, t + T, ...), so every thread owns
+// the same number of nodes up to one.  Neighbour values of u are plain
+// cached loads: they were written before the last barrier, whose
+// release/acquire pair orders them for every thread of the block.  A barrier
+// that does not complete within ~1 s records EP_ETIMEOUT and the kernel
+// returns.
 #include "ep_dev.cuh"
 #include "ep_tile.cuh"
 
@@ -35,7 +34,9 @@ constexpr long long kBarrierSpinLimit = 1ll << 24;  // x >= 64 ns naps: about a 
 
 // Bounded grid barrier (all blocks of a cooperative launch).  count and gen
 // persist between launches: count returns to 0 after every barrier, gen
-// only grows.  Returns false after recording EP_ETIMEOUT when the other
+// only grows.  Thread 0 of each block arrives with a release and waits with
+// acquire loads; the block's other threads are ordered behind it by
+// __syncthreads.  Returns false after recording EP_ETIMEOUT when the other
 // blocks did not all arrive in time.
 __device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned int& my_gen,
                                              int* status) {
@@ -44,23 +45,25 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* 
     if (threadIdx.x == 0) {
         int good = 1;
         const unsigned int g = my_gen;
-        __threadfence();
-        if (atomicAdd(count, 1u) == gridDim.x - 1) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
+        unsigned int old;
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+        if (old == gridDim.x - 1) {
+            asm volatile("st.relaxed.gpu.u32 [%0], 0;" ::"l"(count) : "memory");
+            asm volatile("red.add.release.gpu.u32 [%0], 1;" ::"l"(gen) : "memory");
         } else {
             long long spins = 0;
-            while (*(volatile unsigned int*)gen == g) {
+            for (;;) {
+                unsigned int cur;
+                asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(gen) : "memory");
+                if (cur != g) break;
                 if (++spins > kBarrierSpinLimit) {
                     good = 0;
                     atomicCAS(status, (int)EP_OK, (int)EP_ETIMEOUT);
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
-        __threadfence();
         my_gen = g + 1;
         ok = good;
     }
@@ -68,10 +71,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* 
     return ok != 0;
 }
 
-// Block sums of NV float values (warp shuffles, then warps in fixed order),
-// written as part[k * G + blockIdx.x].
+// Block sums of NV float values (warp butterflies, then the warps' sums by
+// warp 0 in the same way), written as part[k * G + blockIdx.x].
 template <int NV>
-__device__ __forceinline__ void publish(const float (&v)[NV], double* part, int G) {
+__device__ __forceinline__ void publish(const float (&v)[NV], float* part, int G) {
     __shared__ float sh[NV][kMaxBlock / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
 #pragma unroll
@@ -80,162 +83,167 @@ __device__ __forceinline__ void publish(const float (&v)[NV], double* part, int 
         if (lane == 0) sh[k][warp] = s;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            float s = 0.f;
-            for (int w = 0; w < nwarp; ++w) s += sh[k][w];
-            part[(size_t)k * G + blockIdx.x] = (double)s;
+            const float s = warp_sum(lane < nwarp ? sh[k][lane] : 0.f);
+            if (lane == 0) part[(size_t)k * G + blockIdx.x] = s;
         }
     }
 }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Totals of all blocks' partials (part[k * G + i]), summed in one fixed order
-// (thread, then warp butterfly, then warps in order) by every block: all
-// threads load at once, so the gather costs about one L2 round trip.
+// Totals of all blocks' partials, formed by warp 0 of every block in the same
+// fixed order (lane-strided sums, then a butterfly), so every block holds the
+// same bits; the result is valid in warp 0 only.
 template <int NV>
-__device__ __forceinline__ void gather(const double* part, int G, double (&tot)[NV]) {
-    __shared__ double wsum[NV][kMaxBlock / 32];
-    __shared__ double res[NV];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    double acc[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-    for (int i = threadIdx.x; i < G; i += blockDim.x) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] += __ldcg(&part[(size_t)k * G + i]);
-    }
+__device__ __forceinline__ void gather(const float* part, int G, float (&tot)[NV]) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        const double sw = warp_sum_d(acc[k]);
-        if (lane == 0) wsum[k][warp] = sw;
+        float acc = 0.f;
+        for (int i = lane; i < G; i += 32) acc += __ldcg(&part[(size_t)k * G + i]);
+        tot[k] = warp_sum(acc);
     }
-    __syncthreads();
-    if (threadIdx.x < NV) {
-        double t = 0.0;
-        for (int w = 0; w < nwarp; ++w) t += wsum[threadIdx.x][w];
-        res[threadIdx.x] = t;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV; ++k) tot[k] = res[k];
 }
 
-__global__ void __launch_bounds__(kStThreads, 2) k_pcg32_stencil(Dev* __restrict__ Dp) {
-    __shared__ int sidx[SHN];
-    __shared__ float su[SHN];
+// index offsets of the 27 neighbours of node n (di, dj, dk in -1..1), from
+// its boundary flags; a neighbour outside the mesh maps to a valid node whose
+// coupling is 0
+struct NbrOff {
+    int x[3], y[3], z[3];
+};
+
+__device__ __forceinline__ NbrOff nbr_offsets(const Dev& D, unsigned int f) {
+    NbrOff o;
+    const int nx = D.NX, nxy = D.NX * D.NY, wrap = D.periodic ? D.NX * (D.NY - 1) : 0;
+    o.x[0] = (f & 1u) ? 0 : -1;
+    o.x[1] = 0;
+    o.x[2] = (f & 2u) ? 0 : 1;
+    o.y[0] = (f & 4u) ? wrap : -nx;
+    o.y[1] = 0;
+    o.y[2] = (f & 8u) ? -wrap : nx;
+    o.z[0] = (f & 16u) ? 0 : -nxy;
+    o.z[1] = 0;
+    o.z[2] = (f & 32u) ? 0 : nxy;
+    return o;
+}
+
+__global__ void __launch_bounds__(kPcgThreads, 2) k_pcg32_stencil(Dev* __restrict__ Dp) {
     Dev& D = *Dp;
-    const size_t N = (size_t)D.N;
+    const int N = D.N;
+    const size_t NN = (size_t)N;
     const int G = gridDim.x;
-    const int ntiles = st_tiles(D);
-    // double-buffered r, w, s; p and delta are touched by their owners only
-    float* const r0b = D.r32;
-    float* const r1b = D.z32;
-    float* const w0b = D.q32;
-    float* const w1b = D.pa32;
-    float* const s0b = D.pb32;
-    float* const s1b = D.s32;
-    float* __restrict__ p = D.p32;
-    float* __restrict__ x = D.d32;
+    const int T = G * blockDim.x;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    float* r = D.r32;
+    float* u = D.z32;
+    float* w = D.q32;
+    float* s = D.pa32;
+    float* p = D.pb32;
+    float* x = D.d32;
     const float* __restrict__ dinv = D.dinv32;
+    const unsigned char* __restrict__ flag = D.nflag;
     const float4* __restrict__ A = D.Ahi;
-    double* part = D.partial;
+    float* part = reinterpret_cast<float*>(D.partial);
     unsigned int* bcount = D.counter + CNT_BAR;
     unsigned int* bgen = D.counter + CNT_BAR + 1;
     unsigned int my_gen = 0;
     if (threadIdx.x == 0) my_gen = *(volatile unsigned int*)bgen;
-    const int max_it = D.max_iter;
-    const double tol2 = D.inner_tol * D.inner_tol;
-    double stop = 0.0, gam_old = 0.0, alpha_old = 0.0, rr = 0.0, gam = 0.0;
+    // CG scalars: kept by thread 0 (the only thread doing double arithmetic,
+    // which runs at a small fraction of the float rate), handed to the block
+    // through shared memory after every reduction
+    __shared__ float sc_alpha, sc_beta;
+    __shared__ int sc_done, sc_it, sc_nan;
+    __shared__ double sc_stop, sc_gam_old, sc_alpha_old, sc_rr, sc_gam;
+    if (threadIdx.x == 0) {
+        sc_it = 0;
+        sc_nan = 0;
+        sc_stop = sc_gam_old = sc_alpha_old = sc_rr = sc_gam = 0.0;
+    }
     float alpha = 0.f, beta = 0.f;
-    int it = 0, cur = 0, pass = 0;
-    bool first = true, nan = false;
-    for (;; ++pass) {
-        const float* rc = cur ? r1b : r0b;
-        const float* wc = cur ? w1b : w0b;
-        const float* sc = cur ? s1b : s0b;
-        float* rn = cur ? r0b : r1b;
-        float* wn = (first || cur) ? w0b : w1b;
-        float* sn = cur ? s0b : s1b;
-        float v[3] = {0.f, 0.f, 0.f};  // gamma, eta, rho
-        for (int tile = blockIdx.x; tile < ntiles; tile += G) {
-            const TileGeo g = tile_geo(D, tile);
-            __syncthreads();
-            stage_tile<float>(D, g, sidx, su, [&](int n, bool own) {
-                const float dv = __ldg(dinv + n);
-                const float r0 = __ldcg(rc + n);
-                float r1 = r0;
-                if (!first) {
-                    const float w0 = __ldcg(wc + n);
-                    const float s1 = beta == 0.f ? w0 : fmaf(beta, __ldcg(sc + n), w0);
-                    r1 = fmaf(-alpha, s1, r0);
-                    if (own) {
-                        const float u0 = dv * r0;
-                        const float p1 = beta == 0.f ? u0 : fmaf(beta, p[n], u0);
-                        p[n] = p1;
-                        x[n] = fmaf(alpha, p1, x[n]);
-                        sn[n] = s1;
-                        rn[n] = r1;
-                    }
-                }
-                const float u1 = dv * r1;
-                if (own) {
-                    v[0] = fmaf(r1, u1, v[0]);
-                    v[2] = fmaf(r1, r1, v[2]);
-                }
-                return u1;
-            });
-            __syncthreads();
-            for_owned(D, g, [&](int h) {
-                const int n = sidx[h];
-                const float w1 = row_f32(A, N, su, h, n);
-                wn[n] = w1;
-                v[1] = fmaf(su[h], w1, v[1]);
-            });
-        }
-        // partials alternate between two regions: a block that runs ahead
-        // publishes into the region nobody is still reading
-        double* pr = part + (size_t)(pass & 1) * 3 * G;
-        publish<3>(v, pr, G);
-        if (!grid_barrier(bcount, bgen, my_gen, &D.status)) break;
-        double t[3];
-        gather<3>(pr, G, t);
+    bool first = true;
+    for (;;) {
         if (!first) {
-            ++it;
-            cur ^= 1;
+            // ---- update, node by node
+            for (int n = t0; n < N; n += T) {
+                const float dv = dinv[n];
+                const float r0 = r[n], w0 = w[n], u0 = u[n];
+                const float s1 = beta == 0.f ? w0 : fmaf(beta, s[n], w0);
+                const float p1 = beta == 0.f ? u0 : fmaf(beta, p[n], u0);
+                const float r1 = fmaf(-alpha, s1, r0);
+                x[n] = fmaf(alpha, p1, x[n]);
+                s[n] = s1;
+                p[n] = p1;
+                r[n] = r1;
+                u[n] = dv * r1;
+            }
+            if (!grid_barrier(bcount, bgen, my_gen, &D.status)) break;
         }
-        gam = t[0];
-        rr = t[2];
-        if (first) stop = tol2 * rr;
-        nan = !(t[0] == t[0] && t[1] == t[1] && t[2] == t[2]);
-        if (nan || rr <= stop || it >= max_it) break;
-        const double b = first ? 0.0 : gam / gam_old;
-        const double a = first ? gam / t[1] : gam / (t[1] - b * gam / alpha_old);
-        beta = (float)b;
-        alpha = (float)a;
-        gam_old = gam;
-        alpha_old = a;
+        // ---- apply w = A u and the block partials
+        float v[3] = {0.f, 0.f, 0.f};  // gamma, eta, rho
+        for (int n = t0; n < N; n += T) {
+            const NbrOff o = nbr_offsets(D, flag[n]);
+            float acc = 0.f;
+#pragma unroll
+            for (int g = 0; g < kGroups; ++g) {
+                const float4 c = A[(size_t)g * NN + n];
+                const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int t = 4 * g + q;
+                    if (t < 27) acc = fmaf(cv[q], u[n + o.x[t % 3] + o.y[(t / 3) % 3] + o.z[t / 9]], acc);
+                }
+            }
+            w[n] = acc;
+            const float rn = r[n], un = u[n];
+            v[0] = fmaf(rn, un, v[0]);
+            v[1] = fmaf(un, acc, v[1]);
+            v[2] = fmaf(rn, rn, v[2]);
+        }
+        publish<3>(v, part, G);
+        if (!grid_barrier(bcount, bgen, my_gen, &D.status)) break;
+        if (threadIdx.x < 32) {
+            float tt[3];
+            gather<3>(part, G, tt);
+            if (threadIdx.x == 0) {
+                if (!first) ++sc_it;
+                const double gam = tt[0], rr = tt[2];
+                sc_gam = gam;
+                sc_rr = rr;
+                if (first) sc_stop = D.inner_tol * D.inner_tol * rr;
+                const bool nan = !(tt[0] == tt[0] && tt[1] == tt[1] && tt[2] == tt[2]);
+                sc_nan = nan ? 1 : 0;
+                const int done = (nan || rr <= sc_stop || sc_it >= D.max_iter) ? 1 : 0;
+                if (!done) {
+                    const double b = first ? 0.0 : gam / sc_gam_old;
+                    const double a = first ? gam / tt[1] : gam / ((double)tt[1] - b * gam / sc_alpha_old);
+                    sc_beta = (float)b;
+                    sc_alpha = (float)a;
+                    sc_gam_old = gam;
+                    sc_alpha_old = a;
+                }
+                sc_done = done;
+            }
+        }
+        __syncthreads();
+        if (sc_done) break;
+        alpha = sc_alpha;
+        beta = sc_beta;
         first = false;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        D.rz = gam;
-        D.rr = rr;
-        D.it = it;
-        D.it_total += it;
-        if (nan && D.status == EP_OK) D.status = EP_ENAN;
+        D.rz = sc_gam;
+        D.rr = sc_rr;
+        D.it = sc_it;
+        D.it_total += sc_it;
+        if (sc_nan && D.status == EP_OK) D.status = EP_ENAN;
     }
 }
 
 // blocks of k_pcg32_stencil that fit on one SM at once
 int pcg_blocks_per_sm() {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg32_stencil, kStThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg32_stencil, kPcgThreads, 0) != cudaSuccess)
         return 0;
     return occ;
 }
@@ -243,7 +251,7 @@ int pcg_blocks_per_sm() {
 cudaError_t launch_pcg32(Dev* d, int grid, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kStThreads);
+    cfg.blockDim = dim3(kPcgThreads);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];

@@ -222,6 +222,9 @@ __global__ void k_expand(Dev* __restrict__ Dp, int want_a, int want_m) {
     int i, j, k;
     node_ijk(D, n, i, j, k);
     const size_t N = (size_t)D.N;
+    if (D.nflag)
+        D.nflag[n] = (unsigned char)((i == 0 ? 1 : 0) | (i == D.NX - 1 ? 2 : 0) | (j == 0 ? 4 : 0) |
+                                     (j == D.NY - 1 ? 8 : 0) | (k == 0 ? 16 : 0) | (k == D.NZ - 1 ? 32 : 0));
     for (int which = 0; which < 2; ++which) {
         if ((which == 0 && !want_a) || (which == 1 && !want_m)) continue;
         const double* c = which == 0 ? D.A64 : D.M64;

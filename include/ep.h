@@ -194,13 +194,23 @@ ep_status ep_activation_times(const ep_instance* inst, double* out_ms, int64_t n
  * after the 64-byte header):
  *   header: char magic[8] = "EPSTATE1"; int32 version (1); int32 model;
  *           int64 n_nodes; int32 n_states; int32 bdf_order; int64 step;
- *           double dt; int64 reserved[2];
+ *           double dt; int64 reserved[2] (reserved[0]: bytes of the
+ *           extension below, 0 if none);
  *   double u_n[N], u_{n-1}[N]          (model units)
  *   double w_n[S][N], w_{n-1}[S][N]    (state-major; S = 3 BO, 18 TTP06)
  *   double at[N]                       (time of the largest slope, ms)
  *   double best[N]                     (largest u_{n+1} - u_n, model units)
- * ep_state_bytes gives the size.  ep_load_state requires the same model and
- * n_nodes; it also resets the stimulus clock to the loaded step. */
+ * FP32_REFINED instances append an extension with their float-float working
+ * state, so that a restart continues bit for bit: char tag[8] = "EPFFEXT1";
+ * int32 hist (valid A u history levels, 0..2); int32 0; then float arrays
+ * of N: u_n hi, lo, u_{n-1} hi, lo; the TTP06 concentrations of level n and
+ * n-1, each [2][5][N] (hi parts, then lo parts; absent for BO); A u of step
+ * n hi, lo and of step n-1 hi, lo.  The portable part alone is a complete
+ * state: any instance of the same model and size loads it (a refined
+ * instance then splits the doubles into pairs and rebuilds its history
+ * within two steps).  ep_state_bytes gives the size of this instance's
+ * buffer.  ep_load_state requires the same model and n_nodes and at least
+ * the portable part; it also resets the stimulus clock to the loaded step. */
 size_t ep_state_bytes(const ep_instance* inst);
 ep_status ep_save_state(const ep_instance* inst, void* buf, size_t bytes);
 ep_status ep_load_state(ep_instance* inst, const void* buf, size_t bytes);

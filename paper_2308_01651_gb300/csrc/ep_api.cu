@@ -176,6 +176,25 @@ struct Sizes {
     bool slab;
 };
 
+// float-float pair (nearest float, then the nearest float of the rest)
+void split_ff(double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+// Largest slope per node (activation detection): double in the FP64 path,
+// float in the refined one.
+cudaError_t get_best(const ep_instance* I, double* out) {
+    const size_t N = (size_t)I->h.N;
+    if (I->h.bestf) {
+        std::vector<float> f(N);
+        cudaError_t e = cudaMemcpy(f.data(), I->h.bestf, N * 4, cudaMemcpyDeviceToHost);
+        for (size_t n = 0; n < N; ++n) out[n] = f[n];
+        return e;
+    }
+    return cudaMemcpy(out, I->h.best, N * 8, cudaMemcpyDeviceToHost);
+}
+
 // Device bytes per instance; mirrors the allocations in ep_create.
 size_t footprint(const Sizes& z) {
     auto al = [](size_t b) { return ((b + 255) / 256) * 256; };
@@ -193,8 +212,11 @@ size_t footprint(const Sizes& z) {
     }
     if (z.prec == EP_PREC_FP32_REFINED) {
         b += al(N * 4);                   // dinv32
-        b += 4 * al(epk::kGroups * N * 16);                              // Ahi Alo Mhi Mlo
+        b += 2 * al(epk::kGroups * N * 16);                              // Ahi Alo
+        if (!z.slab) b += 2 * al(epk::kGroups * N * 16);                 // Mhi Mlo (curved meshes)
         b += 6 * al(N * 4);                                              // u, v, b (hi, lo)
+        b += 6 * al(N * 4);                                              // A u history (hi, lo)
+        b += 5 * al(N * 4);                                              // u levels (hi, lo), best slope
         if (z.op32 != EP_OP_STENCIL) b += al(6 * N * 4);                 // fibres
         b += 6 * al(N * 4);               // r32 z32 q32 d32 pa32 pb32
         b += al(N);                       // boundary flags
@@ -542,6 +564,7 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     h.ns = z.ns;
     h.dt = opts->dt;
     h.inv_dt = 1.0 / opts->dt;
+    split_ff(h.inv_dt, h.idt_hi, h.idt_lo);
     h.act_thr = ionic->model == EP_MODEL_BO ? 1.0 / kBOmV : 1.0;
     h.op32 = z.op32;
     const bool ref = h.prec == EP_PREC_FP32_REFINED;
@@ -587,8 +610,21 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         ALLOC(h.dinv32, N);
         ALLOC(h.Ahi, epk::kGroups * N);
         ALLOC(h.Alo, epk::kGroups * N);
-        ALLOC(h.Mhi, epk::kGroups * N);
-        ALLOC(h.Mlo, epk::kGroups * N);
+        if (h.kind != EP_MESH_SLAB) {
+            ALLOC(h.Mhi, epk::kGroups * N);
+            ALLOC(h.Mlo, epk::kGroups * N);
+        }
+        ALLOC(h.uh_n, N);
+        ALLOC(h.ul_n, N);
+        ALLOC(h.uh_m, N);
+        ALLOC(h.ul_m, N);
+        ALLOC(h.bestf, N);
+        ALLOC(h.yc_hi, N);
+        ALLOC(h.yc_lo, N);
+        ALLOC(h.yn_hi, N);
+        ALLOC(h.yn_lo, N);
+        ALLOC(h.ym_hi, N);
+        ALLOC(h.ym_lo, N);
         ALLOC(h.u_hi, N);
         ALLOC(h.u_lo, N);
         ALLOC(h.v_hi, N);
@@ -651,13 +687,34 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
             CUDA_TRY(cudaMemcpy(h.g32_n, g.data(), g.size() * 4, cudaMemcpyHostToDevice));
             CUDA_TRY(cudaMemcpy(h.g32_nm1, g.data(), g.size() * 4, cudaMemcpyHostToDevice));
         }
-        if (z.ns64) {
-            const int off = ref ? z.ng32 : 0;
+        if (z.ns64 && !ref) {
             std::vector<double> c(z.ns64 * N);
             for (int k = 0; k < z.ns64; ++k)
-                for (size_t n = 0; n < N; ++n) c[k * N + n] = w0[off + k];
+                for (size_t n = 0; n < N; ++n) c[k * N + n] = w0[k];
             CUDA_TRY(cudaMemcpy(h.s64_n, c.data(), c.size() * 8, cudaMemcpyHostToDevice));
             CUDA_TRY(cudaMemcpy(h.s64_nm1, c.data(), c.size() * 8, cudaMemcpyHostToDevice));
+        }
+        if (z.ns64 && ref) {
+            // float-float concentrations: [hi][k][N] then [lo][k][N]
+            std::vector<float> c(2 * z.ns64 * N);
+            for (int k = 0; k < z.ns64; ++k) {
+                float hi, lo;
+                split_ff(w0[z.ng32 + k], hi, lo);
+                for (size_t n = 0; n < N; ++n) {
+                    c[k * N + n] = hi;
+                    c[(z.ns64 + k) * N + n] = lo;
+                }
+            }
+            CUDA_TRY(cudaMemcpy(h.s64_n, c.data(), c.size() * 4, cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(h.s64_nm1, c.data(), c.size() * 4, cudaMemcpyHostToDevice));
+        }
+        if (ref) {
+            float hi, lo;
+            split_ff(u0, hi, lo);
+            std::vector<float> fh(N, hi), fl(N, lo), fb(N, -INFINITY);
+            for (float* d : {h.uh_n, h.uh_m}) CUDA_TRY(cudaMemcpy(d, fh.data(), N * 4, cudaMemcpyHostToDevice));
+            for (float* d : {h.ul_n, h.ul_m}) CUDA_TRY(cudaMemcpy(d, fl.data(), N * 4, cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(h.bestf, fb.data(), N * 4, cudaMemcpyHostToDevice));
         }
         std::vector<double> nanv(N, NAN), ninf(N, -INFINITY);
         CUDA_TRY(cudaMemcpy(h.at, nanv.data(), N * 8, cudaMemcpyHostToDevice));
@@ -685,6 +742,9 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         h.mf_cl = (float)(w * (dl - dn));
         h.mf_ct = (float)(w * (dtr - dn));
         h.mf_cmass = (float)(alpha_dt * vol);
+        const double mw = vol / 216.0;  // slab mass weight (analytic mass matrix)
+        h.mw_hi = (float)mw;
+        h.mw_lo = (float)(mw - (double)h.mw_hi);
     }
     CUDA_TRY(cudaMemcpy(I->d, &h, sizeof(Dev), cudaMemcpyHostToDevice));
     {
@@ -882,17 +942,31 @@ ep_status ep_activation_times(const ep_instance* I, double* out, int64_t n) {
     CUDA_TRY(cudaStreamSynchronize(I->stream));
     std::vector<double> best((size_t)n);
     CUDA_TRY(cudaMemcpy(out, I->h.at, (size_t)n * 8, cudaMemcpyDeviceToHost));
-    CUDA_TRY(cudaMemcpy(best.data(), I->h.best, (size_t)n * 8, cudaMemcpyDeviceToHost));
+    CUDA_TRY(get_best(I, best.data()));
     const double thr = I->h.act_thr * I->h.dt;
     for (int64_t i = 0; i < n; ++i)
         if (!(best[i] > thr)) out[i] = NAN;
     return EP_OK;
 }
 
-size_t ep_state_bytes(const ep_instance* I) {
-    if (!I) return 0;
+// Refined instances append their float-float working state (tag, history
+// count, then float arrays) so that a restart continues bit for bit: the
+// potential levels, the concentrations as pairs and the A u history.
+static size_t ff_ext_bytes(const ep_instance* I) {
+    if (I->h.prec != EP_PREC_FP32_REFINED) return 0;
+    const size_t N = (size_t)I->h.N;
+    const size_t nc = I->h.model == EP_MODEL_BO ? 0 : epk::kTTConc;
+    return 16 + 4 * N * (4 + 4 * nc + 4);
+}
+
+static size_t base_state_bytes(const ep_instance* I) {
     const size_t N = (size_t)I->h.N;
     return 64 + 8 * N * (2 + 2 * (size_t)I->h.ns + 2);
+}
+
+size_t ep_state_bytes(const ep_instance* I) {
+    if (!I) return 0;
+    return base_state_bytes(I) + ff_ext_bytes(I);
 }
 
 struct StateHeader {
@@ -924,6 +998,7 @@ ep_status ep_save_state(const ep_instance* I, void* buf, size_t bytes) {
     H.bdf_order = I->h.bdf;
     H.step = t.step;
     H.dt = I->h.dt;
+    H.reserved[0] = (int64_t)ff_ext_bytes(I);
     char* p = static_cast<char*>(buf);
     std::memcpy(p, &H, 64);
     double* o = reinterpret_cast<double*>(p + 64);
@@ -937,7 +1012,8 @@ ep_status ep_save_state(const ep_instance* I, void* buf, size_t bytes) {
     CUDA_TRY(get(t.u_nm1, o + N));
     const bool ref = I->h.prec == EP_PREC_FP32_REFINED;
     const int ng32 = ref ? (I->h.model == EP_MODEL_BO ? 3 : epk::kTTGates) : 0;
-    std::vector<float> f(N);
+    const int nc = ns - ng32;  // refined: float-float concentrations
+    std::vector<float> f(N), fl(N);
     for (int lvl = 0; lvl < 2; ++lvl) {
         double* dst = o + 2 * N + (size_t)lvl * ns * N;
         for (int k = 0; k < ns; ++k) {
@@ -946,21 +1022,49 @@ ep_status ep_save_state(const ep_instance* I, void* buf, size_t bytes) {
                 CUDA_TRY(cudaMemcpy(f.data(), src, N * 4, cudaMemcpyDeviceToHost));
                 for (size_t n = 0; n < N; ++n) tmp[n] = f[n];
                 std::memcpy(dst + (size_t)k * N, tmp.data(), N * 8);
+            } else if (ref) {
+                const float* src = reinterpret_cast<const float*>(lvl == 0 ? t.s64_n : t.s64_nm1);
+                CUDA_TRY(cudaMemcpy(f.data(), src + (size_t)(k - ng32) * N, N * 4, cudaMemcpyDeviceToHost));
+                CUDA_TRY(cudaMemcpy(fl.data(), src + (size_t)(nc + k - ng32) * N, N * 4, cudaMemcpyDeviceToHost));
+                for (size_t n = 0; n < N; ++n) tmp[n] = (double)f[n] + (double)fl[n];
+                std::memcpy(dst + (size_t)k * N, tmp.data(), N * 8);
             } else {
-                const double* src = (lvl == 0 ? t.s64_n : t.s64_nm1) + (size_t)(k - ng32) * N;
+                const double* src = (lvl == 0 ? t.s64_n : t.s64_nm1) + (size_t)k * N;
                 CUDA_TRY(get(src, dst + (size_t)k * N));
             }
         }
     }
     CUDA_TRY(get(t.at, o + (2 + 2 * (size_t)ns) * N));
-    CUDA_TRY(get(t.best, o + (3 + 2 * (size_t)ns) * N));
+    CUDA_TRY(get_best(I, o + (3 + 2 * (size_t)ns) * N));
+    if (ref) {
+        char* e = p + base_state_bytes(I);
+        std::memcpy(e, "EPFFEXT1", 8);
+        const int32_t hist = t.hist, zero = 0;
+        std::memcpy(e + 8, &hist, 4);
+        std::memcpy(e + 12, &zero, 4);
+        char* q = e + 16;
+        auto getf = [&](const float* d) -> cudaError_t {
+            cudaError_t err = cudaMemcpy(f.data(), d, N * 4, cudaMemcpyDeviceToHost);
+            std::memcpy(q, f.data(), N * 4);
+            q += N * 4;
+            return err;
+        };
+        for (const float* d : {t.uh_n, t.ul_n, t.uh_m, t.ul_m}) CUDA_TRY(getf(d));
+        for (int lvl = 0; lvl < 2; ++lvl) {
+            const float* c = reinterpret_cast<const float*>(lvl == 0 ? t.s64_n : t.s64_nm1);
+            for (int k = 0; k < 2 * nc; ++k) CUDA_TRY(getf(c + (size_t)k * N));
+        }
+        for (const float* d : {t.yn_hi, t.yn_lo, t.ym_hi, t.ym_lo}) CUDA_TRY(getf(d));
+    }
     return EP_OK;
 }
 
 ep_status ep_load_state(ep_instance* I, const void* buf, size_t bytes) {
     if (!I || !buf) return fail(EP_EINVAL, "NULL argument");
+    // the portable part is required; a refined instance's exact extension
+    // is used when present
     const size_t need = ep_state_bytes(I);
-    if (bytes < need) return fail(EP_EINVAL, "buffer too small");
+    if (bytes < base_state_bytes(I)) return fail(EP_EINVAL, "buffer too small");
     StateHeader H;
     std::memcpy(&H, buf, 64);
     if (std::memcmp(H.magic, "EPSTATE1", 8) != 0 || H.version != 1) return fail(EP_EINVAL, "not an EPSTATE1 buffer");
@@ -982,7 +1086,8 @@ ep_status ep_load_state(ep_instance* I, const void* buf, size_t bytes) {
     CUDA_TRY(put(t.u_nm1, o + N));
     const bool ref = I->h.prec == EP_PREC_FP32_REFINED;
     const int ng32 = ref ? (I->h.model == EP_MODEL_BO ? 3 : epk::kTTGates) : 0;
-    std::vector<float> f(N);
+    const int nc = ns - ng32;  // refined: float-float concentrations
+    std::vector<float> f(N), fl(N);
     for (int lvl = 0; lvl < 2; ++lvl) {
         const double* src = o + 2 * N + (size_t)lvl * ns * N;
         for (int k = 0; k < ns; ++k) {
@@ -991,10 +1096,28 @@ ep_status ep_load_state(ep_instance* I, const void* buf, size_t bytes) {
                 for (size_t n = 0; n < N; ++n) f[n] = (float)tmp[n];
                 CUDA_TRY(cudaMemcpy((lvl == 0 ? t.g32_n : t.g32_nm1) + (size_t)k * N, f.data(), N * 4,
                                     cudaMemcpyHostToDevice));
+            } else if (ref) {
+                std::memcpy(tmp.data(), src + (size_t)k * N, N * 8);
+                for (size_t n = 0; n < N; ++n) split_ff(tmp[n], f[n], fl[n]);
+                float* d = reinterpret_cast<float*>(lvl == 0 ? t.s64_n : t.s64_nm1);
+                CUDA_TRY(cudaMemcpy(d + (size_t)(k - ng32) * N, f.data(), N * 4, cudaMemcpyHostToDevice));
+                CUDA_TRY(cudaMemcpy(d + (size_t)(nc + k - ng32) * N, fl.data(), N * 4, cudaMemcpyHostToDevice));
             } else {
-                CUDA_TRY(put((lvl == 0 ? t.s64_n : t.s64_nm1) + (size_t)(k - ng32) * N, src + (size_t)k * N));
+                CUDA_TRY(put((lvl == 0 ? t.s64_n : t.s64_nm1) + (size_t)k * N, src + (size_t)k * N));
             }
         }
+    }
+    if (ref) {
+        // the float-float potential levels from the two stored potentials
+        for (int lvl = 0; lvl < 2; ++lvl) {
+            const double* src = o + (size_t)lvl * N;
+            for (size_t n = 0; n < N; ++n) split_ff(src[n], f[n], fl[n]);
+            CUDA_TRY(cudaMemcpy(lvl == 0 ? t.uh_n : t.uh_m, f.data(), N * 4, cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(lvl == 0 ? t.ul_n : t.ul_m, fl.data(), N * 4, cudaMemcpyHostToDevice));
+        }
+        const double* bsrc = o + (3 + 2 * (size_t)ns) * N;
+        for (size_t n = 0; n < N; ++n) f[n] = (float)bsrc[n];
+        CUDA_TRY(cudaMemcpy(t.bestf, f.data(), N * 4, cudaMemcpyHostToDevice));
     }
     CUDA_TRY(put(t.at, o + (2 + 2 * (size_t)ns) * N));
     CUDA_TRY(put(t.best, o + (3 + 2 * (size_t)ns) * N));
@@ -1005,6 +1128,32 @@ ep_status ep_load_state(ep_instance* I, const void* buf, size_t bytes) {
     CUDA_TRY(cudaMemset(t.counter, 0, epk::CNT_N * sizeof(unsigned int)));
     I->host_step = step;
     I->sticky = EP_OK;
+    // the operators for the loaded step's BDF order now, so that the restored
+    // A u history stays valid for the next step
+    ensure_alpha(I);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(I->stream));
+    int hist = 0;
+    const size_t ext = ff_ext_bytes(I);
+    const char* e = static_cast<const char*>(buf) + base_state_bytes(I);
+    if (ref && H.reserved[0] == (int64_t)ext && bytes >= need && std::memcmp(e, "EPFFEXT1", 8) == 0) {
+        int32_t hh = 0;
+        std::memcpy(&hh, e + 8, 4);
+        hist = std::max(0, std::min(2, (int)hh));
+        const char* q = e + 16;
+        auto putf = [&](float* d) -> cudaError_t {
+            std::memcpy(f.data(), q, N * 4);
+            q += N * 4;
+            return cudaMemcpy(d, f.data(), N * 4, cudaMemcpyHostToDevice);
+        };
+        for (float* d : {t.uh_n, t.ul_n, t.uh_m, t.ul_m}) CUDA_TRY(putf(d));
+        for (int lvl = 0; lvl < 2; ++lvl) {
+            float* c = reinterpret_cast<float*>(lvl == 0 ? t.s64_n : t.s64_nm1);
+            for (int k = 0; k < 2 * nc; ++k) CUDA_TRY(putf(c + (size_t)k * N));
+        }
+        for (float* d : {t.yn_hi, t.yn_lo, t.ym_hi, t.ym_lo}) CUDA_TRY(putf(d));
+    }
+    CUDA_TRY(cudaMemcpy(&I->d->hist, &hist, sizeof(int), cudaMemcpyHostToDevice));
     return EP_OK;
 }
 

@@ -63,8 +63,9 @@ struct Dev {
     // ---- state ---------------------------------------------------------------
     double *u_n, *u_nm1, *u_new;
     float *g32_n, *g32_nm1;     // FP32 gates [ng][N] (FP32_REFINED)
-    double *s64_n, *s64_nm1;    // FP64 states [ns64][N]: all states (FP64) or
-                                // the TTP06 concentrations (FP32_REFINED)
+    double *s64_n, *s64_nm1;    // FP64: all states [ns][N] in double.  FP32_REFINED:
+                                // the TTP06 concentrations as float-float, the
+                                // memory read as float [2][5][N] (hi parts, then lo)
     const uint8_t* cell;
     double *v;                  // u_BDF/dt - I_ion + I_app (FP64 path)
     double *b, *r;              // FP64 right-hand side and residual (FP64 path)
@@ -72,6 +73,19 @@ struct Dev {
     // u_EXT), the nodal vector v and the right-hand side b = M v
     float *u_hi, *u_lo, *v_hi, *v_lo, *b_hi, *b_lo;
     float nscale;               // scale of b and r in the float sums of squares
+    float mw_hi, mw_lo;         // slab mass weight hx hy hz / 216 (float-float)
+    float idt_hi, idt_lo;       // 1/dt (float-float)
+    // refined path: the potential of steps n and n-1 as float-float pairs
+    // (u_n and u_nm1 hold the same values rounded to double), and the
+    // activation's best slope per node in float
+    float *uh_n, *ul_n, *uh_m, *ul_m;
+    float* bestf;
+    // A u of the solve's iterate (float-float): the current step's (written by
+    // every residual evaluation), step n's and step n-1's.  hist counts the
+    // valid past levels; with enough of them A u_EXT is their BDF
+    // extrapolation instead of an operator apply.
+    float *yc_hi, *yc_lo, *yn_hi, *yn_lo, *ym_hi, *ym_lo;
+    int hist;
     double *at, *best;
     // ---- operators -----------------------------------------------------------
     double *M64, *A64;          // [kSlots][N] (symmetric, FP64)

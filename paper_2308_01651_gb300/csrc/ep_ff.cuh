@@ -66,6 +66,22 @@ __device__ __forceinline__ void ff_add_f(float ah, float al, float b, float& rh,
     quick_two_sum(s, e, rh, rl);
 }
 
+// (rh, rl) = (ah + al) * (bh + bl), dropping al*bl
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& rh, float& rl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
+    quick_two_sum(p, e, rh, rl);
+}
+
+// (sh, sl) += c * (xh + xl) for a power-of-two c (the product is exact)
+__device__ __forceinline__ void ff_acc_pow2(float c, float xh, float xl, float& sh, float& sl) {
+    float s, t;
+    two_sum(sh, __fmul_rn(c, xh), s, t);
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(t, __fmul_rn(c, xl)));
+}
+
 // nearest float-float of a double (exact for doubles with <= 48 significant bits)
 __device__ __forceinline__ void ff_from_double(double x, float& hi, float& lo) {
     hi = __double2float_rn(x);

@@ -75,18 +75,25 @@ __global__ void __launch_bounds__(kNodeThreads) k_finish(Dev* __restrict__ Dp) {
     const double none[1] = {0.0};
     const bool ff = D.u_hi != nullptr;  // refined: the iterate is float-float
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x) {
-        double un;
         if (ff) {
-            un = ff_to_double(D.u_hi[n], D.u_lo[n]);
-            D.u_new[n] = un;
+            // slope and checks in float from the pairs; the only double
+            // operation is the rounding of the new potential for u_n
+            const float h1 = D.u_hi[n], l1 = D.u_lo[n];
+            const float s = (h1 - D.uh_n[n]) + (l1 - D.ul_n[n]);
+            D.u_new[n] = ff_to_double(h1, l1);
+            if (!isfinite(h1)) v[0] += 1.f;
+            if (s > D.bestf[n]) {
+                D.bestf[n] = s;
+                D.at[n] = t_new;
+            }
         } else {
-            un = D.u_new[n];
-        }
-        const double s = un - D.u_n[n];
-        if (!isfinite(un)) v[0] += 1.f;
-        if (s > D.best[n]) {
-            D.best[n] = s;
-            D.at[n] = t_new;
+            const double un = D.u_new[n];
+            const double s = un - D.u_n[n];
+            if (!isfinite(un)) v[0] += 1.f;
+            if (s > D.best[n]) {
+                D.best[n] = s;
+                D.at[n] = t_new;
+            }
         }
     }
     grid_reduce<1, 0>(v, none, D.partial, D.counter + CNT_FINISH, blockIdx.x, gridDim.x, [&](double* tot) {
@@ -101,6 +108,29 @@ __global__ void __launch_bounds__(kNodeThreads) k_finish(Dev* __restrict__ Dp) {
         double* c = D.s64_nm1;
         D.s64_nm1 = D.s64_n;
         D.s64_n = c;
+        if (ff) {
+            // the iterate becomes level n, level n becomes n-1, and the old
+            // n-1 buffers take the next step's iterate
+            float* ph = D.uh_m;
+            float* pl = D.ul_m;
+            D.uh_m = D.uh_n;
+            D.ul_m = D.ul_n;
+            D.uh_n = D.u_hi;
+            D.ul_n = D.u_lo;
+            D.u_hi = ph;
+            D.u_lo = pl;
+            // A u of the new solution becomes step n's; the oldest level is
+            // reused for the next step's residuals
+            float* yh = D.ym_hi;
+            float* yl = D.ym_lo;
+            D.ym_hi = D.yn_hi;
+            D.ym_lo = D.yn_lo;
+            D.yn_hi = D.yc_hi;
+            D.yn_lo = D.yc_lo;
+            D.yc_hi = yh;
+            D.yc_lo = yl;
+            D.hist = D.hist < 2 ? D.hist + 1 : 2;
+        }
         D.step += 1;
         D.done_step = D.step;
         D.last_iters = D.prec == EP_PREC_FP32_REFINED ? D.it_total : D.it;

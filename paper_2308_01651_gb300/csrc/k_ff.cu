@@ -25,7 +25,13 @@ __device__ __forceinline__ void stage_ff(const Dev& D, const TileGeo& g, int* si
     }
 }
 
-// FIRST: b = M v, r = b - A u; otherwise r = b - A u with the stored b.
+// FIRST: b = M v and r = b - A u_EXT, where A u_EXT comes from the stored
+// A u of the last steps when there are enough of them (BDF1: y_n; BDF2:
+// 2 y_n - y_{n-1}, the extrapolation u_EXT is made of) and from an operator
+// apply otherwise (first steps, after a BDF order change or a state load).
+// Otherwise (after a correction): y = A u, stored as the step's current A u,
+// and r = b - y with the stored b.  M v on a uniform slab needs no stored
+// coefficients (row_mass_slab).
 template <int FIRST>
 __global__ void __launch_bounds__(kStThreads) k_rhs_ff(Dev* __restrict__ Dp, int graph) {
     __shared__ int sidx[SHN];
@@ -34,6 +40,10 @@ __global__ void __launch_bounds__(kStThreads) k_rhs_ff(Dev* __restrict__ Dp, int
     Dev& D = *Dp;
     const size_t N = (size_t)D.N;
     const float ns = D.nscale;
+    const int order = (D.bdf == 2 && D.step >= 1) ? 2 : 1;
+    // FIRST: extrapolate A u_EXT from the history instead of applying A
+    const bool hist = FIRST && D.hist >= order;
+    const bool slab_mass = D.Mhi == nullptr;
     // (ns b)^2, (ns r)^2, r32 z32, r32 r32
     float vf[4] = {0.f, 0.f, 0.f, 0.f};
     const double none[1] = {0.0};
@@ -41,28 +51,44 @@ __global__ void __launch_bounds__(kStThreads) k_rhs_ff(Dev* __restrict__ Dp, int
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const TileGeo g = tile_geo(D, tile);
         __syncthreads();
-        stage_ff(D, g, sidx, D.u_hi, D.u_lo, suh, sul);
         if (FIRST) {
-            for (int h = threadIdx.x; h < SHN; h += blockDim.x) {
-                const int n = sidx[h];
-                svh[h] = n >= 0 ? D.v_hi[n] : 0.f;
-                svl[h] = n >= 0 ? D.v_lo[n] : 0.f;
-            }
+            stage_ff(D, g, sidx, D.v_hi, D.v_lo, svh, svl);
+            if (!hist)
+                for (int h = threadIdx.x; h < SHN; h += blockDim.x) {
+                    const int n = sidx[h];
+                    suh[h] = n >= 0 ? D.u_hi[n] : 0.f;
+                    sul[h] = n >= 0 ? D.u_lo[n] : 0.f;
+                }
+        } else {
+            stage_ff(D, g, sidx, D.u_hi, D.u_lo, suh, sul);
         }
         __syncthreads();
         for_owned(D, g, [&](int h) {
             const int n = sidx[h];
-            float bh, bl;
+            float bh, bl, ah, al;
             if (FIRST) {
-                row_ff(D.Mhi, D.Mlo, N, svh, svl, h, n, bh, bl);
+                if (slab_mass) row_mass_slab(D, svh, svl, h, n, bh, bl);
+                else row_ff(D.Mhi, D.Mlo, N, svh, svl, h, n, bh, bl);
                 D.b_hi[n] = bh;
                 D.b_lo[n] = bl;
+                if (hist) {
+                    ah = D.yn_hi[n];
+                    al = D.yn_lo[n];
+                    if (order == 2) {
+                        // 2 y_n - y_{n-1}: the doubling is exact
+                        ff_sub(2.f * ah, 2.f * al, D.ym_hi[n], D.ym_lo[n], ah, al);
+                    }
+                } else {
+                    row_ff(D.Ahi, D.Alo, N, suh, sul, h, n, ah, al);
+                }
             } else {
                 bh = D.b_hi[n];
                 bl = D.b_lo[n];
+                row_ff(D.Ahi, D.Alo, N, suh, sul, h, n, ah, al);
+                D.yc_hi[n] = ah;
+                D.yc_lo[n] = al;
             }
-            float ah, al, rh, rl;
-            row_ff(D.Ahi, D.Alo, N, suh, sul, h, n, ah, al);
+            float rh, rl;
             ff_sub(bh, bl, ah, al, rh, rl);
             const float r32 = rh;  // nearest float of the normalised pair
             const float z = D.dinv32[n] * r32;

@@ -15,10 +15,13 @@
 // the finishing kernel of the step swaps the slots.
 //
 // This file is compiled with fast single-precision intrinsics (exp, log,
-// division): they only touch the FP32 path, whose float rates feed the
-// double concentrations as increments; the FP64 path's double arithmetic is
-// unaffected.  No double division appears per node (1/dt and 1/alpha are
-// precomputed): GB300's FP64 pipe is ~60x slower than FP32.
+// division): they only touch the refined path's float arithmetic; the FP64
+// path's double arithmetic is unaffected.  The refined path does no double
+// arithmetic per node (GB300's FP64 pipe is ~60x slower than FP32): the
+// potentials of the last two steps and the TTP06 concentrations are
+// float-float pairs, the BDF combinations are formed in float-float, and the
+// concentrations' BDF2 update is written as c_n + [(c_n - c_{n-1})/3 +
+// (2/3) dt r] so that only a small increment is rounded to float.
 #include "ep_dev.cuh"
 #include "ionic_models.cuh"
 #include "ep_ff.cuh"
@@ -61,20 +64,50 @@ __device__ __forceinline__ double applied(const Dev& D, const StepConsts& c, int
     return s;
 }
 
-// The right-hand side's nodal vector v and the solve's initial guess u_EXT:
-// double in the FP64 path, float-float pairs in the refined one.
-__device__ __forceinline__ void store_vu(const Dev& D, int n, double v, double uE) {
-    if (D.v_hi) {
-        ff_from_double(v, D.v_hi[n], D.v_lo[n]);
-        ff_from_double(uE, D.u_hi[n], D.u_lo[n]);
+// FP64 path: v and u_EXT in double.
+__device__ __forceinline__ void store_vu64(const Dev& D, int n, double v, double uE) {
+    D.v[n] = v;
+    D.u_new[n] = uE;
+}
+
+// Refined path: the potential's BDF combinations from the float-float levels
+// u_n and u_{n-1}: uB = u_BDF (order 1: u_n; 2: 2 u_n - u_{n-1}/2) and uE =
+// u_EXT (order 1: u_n; 2: 2 u_n - u_{n-1}); the scalings by 2 and 1/2 are exact.
+__device__ __forceinline__ void u_bdf_ff(const Dev& D, int order, int n, float& bh, float& bl, float& eh,
+                                         float& el) {
+    const float h0 = D.uh_n[n], l0 = D.ul_n[n];
+    if (order == 2) {
+        const float h1 = D.uh_m[n], l1 = D.ul_m[n];
+        ff_sub(2.f * h0, 2.f * l0, 0.5f * h1, 0.5f * l1, bh, bl);
+        ff_sub(2.f * h0, 2.f * l0, h1, l1, eh, el);
     } else {
-        D.v[n] = v;
-        D.u_new[n] = uE;
+        bh = eh = h0;
+        bl = el = l0;
     }
 }
 
+// Refined path: v = uB / dt + (I_app - I_ion) and u_EXT as float-float pairs
+__device__ __forceinline__ void store_vu_ff(const Dev& D, int n, float bh, float bl, float eh, float el,
+                                            float src) {
+    float vh, vl;
+    ff_mul(bh, bl, D.idt_hi, D.idt_lo, vh, vl);
+    ff_add_f(vh, vl, src, vh, vl);
+    D.v_hi[n] = vh;
+    D.v_lo[n] = vl;
+    D.u_hi[n] = eh;
+    D.u_lo[n] = el;
+}
+
+__device__ __forceinline__ float applied_f(const Dev& D, const StepConsts& c, int n) {
+    float s = 0.f;
+#pragma unroll
+    for (int p = 0; p < EP_MAX_PULSES; ++p)
+        if (c.iamp[p] != 0.0 && D.mask[p][n]) s += (float)c.iamp[p];
+    return s;
+}
+
 // G: arithmetic/storage type of the gates (float when refined, double in the
-// FP64 path).  Concentrations are double either way.
+// FP64 path).
 template <typename G>
 __global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Dev* __restrict__ Dp) {
     const Dev& D = *Dp;
@@ -91,33 +124,44 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Dev* __restrict__ Dp)
     }
     const G dtg = G(c.dt), alg = G(c.alpha);
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
-        const double un = D.u_n[n];
-        double uB = un, uE = un;
-        G wB[3], wE[3];
+        G uEg;
+        double uB = 0.0, uE = 0.0;
+        float ubh = 0.f, ubl = 0.f, ueh = 0.f, uel = 0.f;
+        if constexpr (sizeof(G) == 4) {
+            u_bdf_ff(D, c.order, n, ubh, ubl, ueh, uel);
+            uEg = ueh;
+        } else {
+            const double un = D.u_n[n];
+            uB = uE = un;
+            if (c.order == 2) {
+                const double um = D.u_nm1[n];
+                uB = 2.0 * un - 0.5 * um;
+                uE = 2.0 * un - um;
+            }
+            uEg = uE;
+        }
+        G wB[3];
         if (c.order == 2) {
-            const double um = D.u_nm1[n];
-            uB = 2.0 * un - 0.5 * um;
-            uE = 2.0 * un - um;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const G x = wn[(size_t)k * N + n], y = wm[(size_t)k * N + n];
                 wB[k] = G(2) * x - G(0.5) * y;
-                wE[k] = G(2) * x - y;
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) wB[k] = wE[k] = wn[(size_t)k * N + n];
+            for (int k = 0; k < 3; ++k) wB[k] = wn[(size_t)k * N + n];
         }
-        (void)wE;  // BO rates depend on u only
+        // BO rates depend on u only
         G a[3], b[3], w1[3];
-        BO<G>::rates(G(uE), a, b);
+        BO<G>::rates(uEg, a, b);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             w1[k] = (wB[k] + dtg * a[k]) / (alg + dtg * b[k]);
             wm[(size_t)k * N + n] = w1[k];
         }
-        const double I = (double)BO<G>::iion(G(uE), w1[0], w1[1], w1[2]);
-        store_vu(D, n, fma(uB, c.inv_dt, applied(D, c, n) - I), uE);
+        const G I = BO<G>::iion(uEg, w1[0], w1[1], w1[2]);
+        if constexpr (sizeof(G) == 4) store_vu_ff(D, n, ubh, ubl, ueh, uel, applied_f(D, c, n) - I);
+        else store_vu64(D, n, fma(uB, c.inv_dt, applied(D, c, n) - (double)I), uE);
     }
 }
 
@@ -126,71 +170,125 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_tt(Dev* __restrict__ Dp)
     const Dev& D = *Dp;
     const StepConsts c = step_consts(D);
     const int N = D.N;
-    // gate storage: float array (refined) or the first 13 rows of the double
-    // state array (FP64); concentrations: the double array rows after them
-    G* __restrict__ gn;
-    G* __restrict__ gm;
-    double* __restrict__ cn;
-    double* __restrict__ cm;
-    if constexpr (sizeof(G) == 4) {
-        gn = reinterpret_cast<G*>(D.g32_n);
-        gm = reinterpret_cast<G*>(D.g32_nm1);
-        cn = D.s64_n;
-        cm = D.s64_nm1;
-    } else {
-        gn = reinterpret_cast<G*>(D.s64_n);
-        gm = reinterpret_cast<G*>(D.s64_nm1);
-        cn = D.s64_n + (size_t)kTTGates * N;
-        cm = D.s64_nm1 + (size_t)kTTGates * N;
-    }
     const G dtg = G(c.dt), alg = G(c.alpha);
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
         const int cell = D.cell[n];
-        const double un = D.u_n[n];
-        double uB = un, uE = un;
-        G gB[kTTGates], gE[kTTGates];
-        double cB[kTTConc], cE[kTTConc];
-        if (c.order == 2) {
-            const double um = D.u_nm1[n];
-            uB = 2.0 * un - 0.5 * um;
-            uE = 2.0 * un - um;
-#pragma unroll
-            for (int k = 0; k < kTTGates; ++k) {
-                const G x = gn[(size_t)k * N + n], y = gm[(size_t)k * N + n];
-                gB[k] = G(2) * x - G(0.5) * y;
-                gE[k] = G(2) * x - y;
-            }
+        if constexpr (sizeof(G) == 4) {
+            // ---- refined: float gates, float-float concentrations and potentials
+            const float* __restrict__ gn = D.g32_n;
+            float* __restrict__ gm = D.g32_nm1;
+            const float* __restrict__ chn = reinterpret_cast<const float*>(D.s64_n);
+            float* __restrict__ chm = reinterpret_cast<float*>(D.s64_nm1);
+            const size_t LO = (size_t)kTTConc * N;  // lo parts follow the hi parts
+            float ubh, ubl, ueh, uel;
+            u_bdf_ff(D, c.order, n, ubh, ubl, ueh, uel);
+            float gB[kTTGates], gE[kTTGates];
+            float ch[kTTConc], cl[kTTConc], dc[kTTConc], cE[kTTConc];
 #pragma unroll
             for (int k = 0; k < kTTConc; ++k) {
-                const double x = cn[(size_t)k * N + n], y = cm[(size_t)k * N + n];
-                cB[k] = 2.0 * x - 0.5 * y;
-                cE[k] = 2.0 * x - y;
+                ch[k] = chn[(size_t)k * N + n];
+                cl[k] = chn[LO + (size_t)k * N + n];
             }
+            if (c.order == 2) {
+#pragma unroll
+                for (int k = 0; k < kTTGates; ++k) {
+                    const float x = gn[(size_t)k * N + n], y = gm[(size_t)k * N + n];
+                    gB[k] = 2.f * x - 0.5f * y;
+                    gE[k] = 2.f * x - y;
+                }
+#pragma unroll
+                for (int k = 0; k < kTTConc; ++k) {
+                    // c_n - c_{n-1}: the hi parts are close, so their
+                    // difference is exact
+                    float dh, dl;
+                    ff_sub(ch[k], cl[k], chm[(size_t)k * N + n], chm[LO + (size_t)k * N + n], dh, dl);
+                    dc[k] = dh;
+                    cE[k] = ch[k] + dc[k];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kTTGates; ++k) gB[k] = gE[k] = gn[(size_t)k * N + n];
+#pragma unroll
+                for (int k = 0; k < kTTConc; ++k) {
+                    dc[k] = 0.f;
+                    cE[k] = ch[k];
+                }
+            }
+            float a[kTTGates], b[kTTGates], r[kTTConc];
+            TT<float>::rates(cell, ueh, gE, cE[0], cE[1], cE[2], cE[3], cE[4], a, b, r);
+            float g1[kTTGates];
+#pragma unroll
+            for (int k = 0; k < kTTGates; ++k) {
+                g1[k] = (gB[k] + dtg * a[k]) / (alg + dtg * b[k]);
+                gm[(size_t)k * N + n] = g1[k];
+            }
+            float c1[kTTConc];
+            const float third = 1.f / 3.f, dta = (float)c.dt_alpha;
+#pragma unroll
+            for (int k = 0; k < kTTConc; ++k) {
+                // order 1: c_n + dt r;  order 2: c_n + (c_n - c_{n-1})/3 + (2/3) dt r
+                const float inc = c.order == 2 ? fmaf(third, dc[k], dta * r[k]) : dta * r[k];
+                float h1, l1;
+                ff_add_f(ch[k], cl[k], inc, h1, l1);
+                chm[(size_t)k * N + n] = h1;
+                chm[LO + (size_t)k * N + n] = l1;
+                c1[k] = h1;
+            }
+            TT<float>::Cur cur;
+            TT<float>::currents(cell, ueh, g1, c1[0], c1[2], c1[3], c1[4], cur);
+            const float I = TT<float>::iion_of(cur);
+            store_vu_ff(D, n, ubh, ubl, ueh, uel, applied_f(D, c, n) - I);
         } else {
+            // ---- FP64: every state in double
+            const double* __restrict__ gn = D.s64_n;
+            double* __restrict__ gm = D.s64_nm1;
+            const double* __restrict__ cn = D.s64_n + (size_t)kTTGates * N;
+            double* __restrict__ cm = D.s64_nm1 + (size_t)kTTGates * N;
+            const double un = D.u_n[n];
+            double uB = un, uE = un;
+            double gB[kTTGates], gE[kTTGates];
+            double cB[kTTConc], cE[kTTConc];
+            if (c.order == 2) {
+                const double um = D.u_nm1[n];
+                uB = 2.0 * un - 0.5 * um;
+                uE = 2.0 * un - um;
 #pragma unroll
-            for (int k = 0; k < kTTGates; ++k) gB[k] = gE[k] = gn[(size_t)k * N + n];
+                for (int k = 0; k < kTTGates; ++k) {
+                    const double x = gn[(size_t)k * N + n], y = gm[(size_t)k * N + n];
+                    gB[k] = 2.0 * x - 0.5 * y;
+                    gE[k] = 2.0 * x - y;
+                }
 #pragma unroll
-            for (int k = 0; k < kTTConc; ++k) cB[k] = cE[k] = cn[(size_t)k * N + n];
+                for (int k = 0; k < kTTConc; ++k) {
+                    const double x = cn[(size_t)k * N + n], y = cm[(size_t)k * N + n];
+                    cB[k] = 2.0 * x - 0.5 * y;
+                    cE[k] = 2.0 * x - y;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kTTGates; ++k) gB[k] = gE[k] = gn[(size_t)k * N + n];
+#pragma unroll
+                for (int k = 0; k < kTTConc; ++k) cB[k] = cE[k] = cn[(size_t)k * N + n];
+            }
+            double a[kTTGates], b[kTTGates], r[kTTConc];
+            TT<double>::rates(cell, uE, gE, cE[0], cE[1], cE[2], cE[3], cE[4], a, b, r);
+            double g1[kTTGates];
+#pragma unroll
+            for (int k = 0; k < kTTGates; ++k) {
+                g1[k] = (gB[k] + dtg * a[k]) / (alg + dtg * b[k]);
+                gm[(size_t)k * N + n] = g1[k];
+            }
+            double c1[kTTConc];
+#pragma unroll
+            for (int k = 0; k < kTTConc; ++k) {
+                c1[k] = fma(c.dt_alpha, r[k], cB[k] * c.inv_alpha);
+                cm[(size_t)k * N + n] = c1[k];
+            }
+            TT<double>::Cur cur;
+            TT<double>::currents(cell, uE, g1, c1[0], c1[2], c1[3], c1[4], cur);
+            const double I = TT<double>::iion_of(cur);
+            store_vu64(D, n, fma(uB, c.inv_dt, applied(D, c, n) - I), uE);
         }
-        G a[kTTGates], b[kTTGates], r[kTTConc];
-        TT<G>::rates(cell, G(uE), gE, G(cE[0]), G(cE[1]), G(cE[2]), G(cE[3]), G(cE[4]), a, b, r);
-        G g1[kTTGates];
-#pragma unroll
-        for (int k = 0; k < kTTGates; ++k) {
-            g1[k] = (gB[k] + dtg * a[k]) / (alg + dtg * b[k]);
-            gm[(size_t)k * N + n] = g1[k];
-        }
-        double c1[kTTConc];
-#pragma unroll
-        for (int k = 0; k < kTTConc; ++k) {
-            // the increment is formed in G, accumulated in double
-            c1[k] = fma(c.dt_alpha, (double)r[k], cB[k] * c.inv_alpha);
-            cm[(size_t)k * N + n] = c1[k];
-        }
-        typename TT<G>::Cur cur;
-        TT<G>::currents(cell, G(uE), g1, G(c1[0]), G(c1[2]), G(c1[3]), G(c1[4]), cur);
-        const double I = (double)TT<G>::iion_of(cur);
-        store_vu(D, n, fma(uB, c.inv_dt, applied(D, c, n) - I), uE);
     }
 }
 

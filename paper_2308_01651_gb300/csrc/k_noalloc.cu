@@ -59,11 +59,12 @@ __global__ void __launch_bounds__(kStThreads) k_residual_norm_noalloc(const Dev*
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const TileGeo g = tile_geo(D, tile);
         __syncthreads();
-        // the solver's float-float iterate (u_n is its sum rounded to double)
-        stage_tile<float>(D, g, sidx, suh, [&](int n, bool) { return D.u_hi[n]; });
+        // the last solve's float-float iterate, now the potential level n
+        // (u_n is its sum rounded to double)
+        stage_tile<float>(D, g, sidx, suh, [&](int n, bool) { return D.uh_n[n]; });
         for (int h = threadIdx.x; h < SHN; h += blockDim.x) {
             const int n = sidx[h];
-            sul[h] = n >= 0 ? D.u_lo[n] : 0.f;
+            sul[h] = n >= 0 ? D.ul_n[n] : 0.f;
         }
         __syncthreads();
         for_owned(D, g, [&](int h) {

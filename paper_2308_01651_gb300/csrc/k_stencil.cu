@@ -187,22 +187,47 @@ __global__ void k_realpha(Dev* __restrict__ Dp, double delta, double alpha_dt, f
 // change applied to the float-float couplings, each coefficient re-split from
 // its double sum; the inverse diagonal (offset 13: group 3, component y)
 // follows.
+// The mass couplings are the stored ones on curved meshes and the analytic
+// uniform-slab ones (w c_x c_y c_z, see row_mass_slab) on slabs.  The step
+// history of A u no longer matches A: it is marked empty.
 __global__ void k_realpha_ff(Dev* __restrict__ Dp, double delta, double alpha_dt, float cmass) {
     Dev& D = *Dp;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         D.alpha_dt = alpha_dt;
         D.mf_cmass = cmass;
+        D.hist = 0;
     }
     if (n >= D.N) return;
     const size_t N = (size_t)D.N;
+    int i, j, k;
+    node_ijk(D, n, i, j, k);
+    const double w = (double)D.mw_hi + (double)D.mw_lo;
     for (int g = 0; g < kGroups; ++g) {
         const size_t o = (size_t)g * N + n;
-        const float4 ah = D.Ahi[o], al = D.Alo[o], mh = D.Mhi[o], ml = D.Mlo[o];
+        const float4 ah = D.Ahi[o], al = D.Alo[o];
         float h4[4] = {ah.x, ah.y, ah.z, ah.w}, l4[4] = {al.x, al.y, al.z, al.w};
-        const float mh4[4] = {mh.x, mh.y, mh.z, mh.w}, ml4[4] = {ml.x, ml.y, ml.z, ml.w};
+        double m4[4] = {0.0, 0.0, 0.0, 0.0};
+        if (D.Mhi) {
+            const float4 mh = D.Mhi[o], ml = D.Mlo[o];
+            m4[0] = (double)mh.x + ml.x;
+            m4[1] = (double)mh.y + ml.y;
+            m4[2] = (double)mh.z + ml.z;
+            m4[3] = (double)mh.w + ml.w;
+        } else {
+            for (int c = 0; c < 4; ++c) {
+                const int t = 4 * g + c;
+                if (t >= 27) continue;
+                const int di = t % 3 - 1, dj = (t / 3) % 3 - 1, dk = t / 9 - 1;
+                if (neighbour(D, i, j, k, di, dj, dk) < 0) continue;
+                const double fx = di != 0 ? 1.0 : ((i == 0 || i == D.NX - 1) ? 2.0 : 4.0);
+                const double fy = dj != 0 ? 1.0 : ((j == 0 || j == D.NY - 1) ? 2.0 : 4.0);
+                const double fz = dk != 0 ? 1.0 : ((k == 0 || k == D.NZ - 1) ? 2.0 : 4.0);
+                m4[c] = w * fx * fy * fz;
+            }
+        }
         for (int c = 0; c < 4; ++c) {
-            const double v = ((double)h4[c] + (double)l4[c]) + delta * ((double)mh4[c] + (double)ml4[c]);
+            const double v = ((double)h4[c] + (double)l4[c]) + delta * m4[c];
             ff_from_double(v, h4[c], l4[c]);
         }
         D.Ahi[o] = make_float4(h4[0], h4[1], h4[2], h4[3]);
@@ -226,7 +251,7 @@ __global__ void k_expand(Dev* __restrict__ Dp, int want_a, int want_m) {
         D.nflag[n] = (unsigned char)((i == 0 ? 1 : 0) | (i == D.NX - 1 ? 2 : 0) | (j == 0 ? 4 : 0) |
                                      (j == D.NY - 1 ? 8 : 0) | (k == 0 ? 16 : 0) | (k == D.NZ - 1 ? 32 : 0));
     for (int which = 0; which < 2; ++which) {
-        if ((which == 0 && !want_a) || (which == 1 && !want_m)) continue;
+        if ((which == 0 && !want_a) || (which == 1 && (!want_m || !D.Mhi))) continue;
         const double* c = which == 0 ? D.A64 : D.M64;
         float4* hi = which == 0 ? D.Ahi : D.Mhi;
         float4* lo = which == 0 ? D.Alo : D.Mlo;

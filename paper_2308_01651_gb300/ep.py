@@ -327,7 +327,8 @@ def state_pack(model, bdf_order, dt, step, u_n, u_nm1, w_n, w_nm1, at, best):
 def state_unpack(buf):
     hdr = np.frombuffer(buf[:64].tobytes(), dtype=HEADER)[0]
     n, ns = int(hdr["n_nodes"]), int(hdr["n_states"])
-    body = np.frombuffer(buf[64:].tobytes(), dtype=np.float64).copy()
+    # the portable part only (a refined instance's extension follows it)
+    body = np.frombuffer(buf[64:64 + 8 * n * (4 + 2 * ns)].tobytes(), dtype=np.float64).copy()
     o = 0
 
     def take(k):

@@ -55,35 +55,45 @@ def measured_peaks():
 
 
 def kernel_model(name, N, n_elems, inner_iters=1.0):
-    """Algorithmic bytes and flops per launch of each kernel (what the method
-    must move / compute, not what the hardware did).  inner_iters: inner CG
-    iterations per launch of the persistent solver."""
-    B = {
-        # per inner iteration: apply (z, p_old, 14 own FP32 couplings; p_new, q)
-        # + update (p, q, delta, r, D^-1; delta, r, z)
-        "pcg32": (int((72 + 32) * N * inner_iters), int((56 + 8) * N * inner_iters)),
-        # read z, p_old, 6 fibre components; write p_new, q
-        "apply32_mf": (40 * N, 910 * n_elems + 12 * N),
-        # read z, p_old; 14 own FP32 couplings; write p_new, q (27 FMA + update)
-        "apply32_stencil": (72, 56),
-        # read p, q, d, r, D^-1; write d, r, z
-        "update32": (32 * N, 8 * N),
-        # read d, u; write u
-        "correct": (20 * N, 1 * N),
-        # FP64 residual: A64 (14 doubles), u, b; write r, r32, z32, d32
-        "resid": (112 * N + 16 * N + 20 * N, 54 * N),
-        # FP64 rhs: M64, A64, v, u; write b, r, r32, z32, d32
-        "rhs": (224 * N + 16 * N + 28 * N, 108 * N),
-        # TTP06 refined: u_n, u_nm1, 2 x (13 f32 gates + 5 f64 conc), cell, mask;
-        # write gates, conc, v, u_new
-        "ionic": ((16 + 2 * (52 + 40) + 2 + 52 + 40 + 16) * N, None),
-        "finish": (40 * N, 2 * N),
+    """Bytes and flops per launch of each kernel of the refined slab step.
+
+    Returns (algorithmic bytes, implementation bytes, flops).  Algorithmic
+    bytes are the per-node figures of the hot-path measurement table (the
+    matrix-free minimum the method must move: fibres instead of stored
+    couplings) times the nodes a launch processes; the roofline fraction is
+    taken on them.  Implementation bytes are what this implementation's data
+    layout has to move at least (stored float-float / float couplings, its
+    vectors), reported beside them.  inner_iters: inner CG iterations per
+    launch of the persistent solver (one launch per refinement sweep)."""
+    it = inner_iters
+    M = {
+        # inner CG iteration: x 4 + y 4 + fibres 24 + 7 FP32 vector touches 28
+        # = 60 B/node; this layout: per apply 27 FP32 couplings 108 + flag 1 +
+        # u 4 + r 4 + w 4, per update r w u s p x D^-1 28 + 5 writes 20, with
+        # one apply more than updates (single-reduction CG)
+        "pcg32": (60 * N * it, N * (121 * (it + 1) + 48 * it), (600 * n_elems + 12 * N) * (it + 1)),
+        # residual sweep: u 8 + b 8 + r 8 + fibres 24 = 48 B/node; this layout:
+        # float-float couplings 216 + u 8 + b 8 + D^-1 4; A u 8 + r/z/d 12
+        "resid": (48 * N, 256 * N, 27 * 12 * N),
+        # right-hand side: u_n, u_{n-1} 16 + I_ion 4 + b 8 = 28 B/node; this
+        # layout (A u history): v 8 + y_n, y_{n-1} 16 + D^-1 4; b 8 + r/z/d 12
+        "rhs": (28 * N, 48 * N, 27 * 8 * N),
+        # TTP06 refined ionic step: 204 B/node; this layout: u levels 16,
+        # gates 2 x 52, concentrations 2 x 40, cell + mask 2; gates 52,
+        # concentrations 40, v 8, u_EXT 8
+        "ionic": (204 * N, 310 * N, None),
+        # u += delta in float-float: u 8 + delta 4; u 8
+        "correct": (20 * N, 20 * N, 6 * N),
+        # activation and rotation: u_{n+1} 8, u_n 8, best 4; u_{n+1} (double) 8
+        "finish": (28 * N, 28 * N, 4 * N),
+        # the other FP32 operator paths (matrix-free slab apply and its update)
+        "apply32_mf": (40 * N, 40 * N, 910 * n_elems + 12 * N),
+        "apply32_stencil": (72 * N, 72 * N, 56 * N),
+        "update32": (32 * N, 32 * N, 8 * N),
     }
-    v = B.get(name)
+    v = M.get(name)
     if v is None:
-        return None, None
-    if name == "apply32_stencil":
-        return v[0] * N, v[1] * N
+        return None, None, None
     return v
 
 
@@ -97,11 +107,15 @@ def source_hash(files):
 
 KERNEL_SOURCES = {
     "apply32_mf": ["paper_2308_01651_gb300/csrc/k_mf.cu", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
-    "resid": ["paper_2308_01651_gb300/csrc/k_stencil.cu", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
+    "resid": ["paper_2308_01651_gb300/csrc/k_ff.cu", "paper_2308_01651_gb300/csrc/ep_tile.cuh",
+              "paper_2308_01651_gb300/csrc/ep_ff.cuh", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
+    "rhs": ["paper_2308_01651_gb300/csrc/k_ff.cu", "paper_2308_01651_gb300/csrc/ep_tile.cuh",
+            "paper_2308_01651_gb300/csrc/ep_ff.cuh", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
     "pcg32": ["paper_2308_01651_gb300/csrc/k_pcg.cu", "paper_2308_01651_gb300/csrc/ep_tile.cuh",
               "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
     "update32": ["paper_2308_01651_gb300/csrc/k_cg.cu", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
-    "ionic": ["paper_2308_01651_gb300/csrc/k_ionic.cu", "paper_2308_01651_gb300/csrc/ionic_models.cuh"],
+    "ionic": ["paper_2308_01651_gb300/csrc/k_ionic.cu", "paper_2308_01651_gb300/csrc/ionic_models.cuh",
+              "paper_2308_01651_gb300/csrc/ep_ff.cuh", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
 }
 
 
@@ -319,10 +333,11 @@ def run_ours(args):
         tot_prof = sum(v[1] for v in prof.values())
         ipl = it_sum / max(sw_sum, 1)
         for name, (n_l, ms) in prof.items():
-            b, f = kernel_model(name, N, n_elems, ipl)
+            b, bi, f = kernel_model(name, N, n_elems, ipl)
             avg_s = ms / 1e3 / n_l
             kernels[name] = {"launches": n_l, "avg_us": 1e6 * avg_s, "share": ms / tot_prof,
                              "gbs": (b / avg_s / 1e9) if b else None,
+                             "impl_gbs": (bi / avg_s / 1e9) if bi else None,
                              "tflops": (f / avg_s / 1e12) if f else None}
         dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
         hbm_peak, peak_kind = measured_peaks()
@@ -338,7 +353,10 @@ def run_ours(args):
         else:
             roof = {"bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak, "unit": "GB/s",
                     "frac": hbm_frac, "peak_source": f"{peak_kind} HBM copy bandwidth"}
-        roof.update(kernel=dom, hbm_frac=hbm_frac, alu_frac=alu_frac, traffic=committed_traffic(dom))
+        roof.update(kernel=dom, hbm_frac=hbm_frac, alu_frac=alu_frac, traffic=committed_traffic(dom),
+                    impl_frac=(d["impl_gbs"] / hbm_peak) if d["impl_gbs"] else None,
+                    bytes_model="per-node figures of the hot-path measurement table x nodes x "
+                                "inner iterations per launch; impl_frac: this layout's bytes")
 
     # ---- refined vs plain FP64 on the GPU: accuracy and the FP64 throughput
     steps_done = W + K + P

@@ -36,7 +36,7 @@ void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s);
 int mf_tiles(const Dev& h);
 cudaError_t mf_prepare();
 int pcg_blocks_per_sm();
-cudaError_t launch_pcg32(Dev* d, int grid, cudaStream_t s);
+cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, cudaStream_t s);
 cudaError_t residual_norm_noalloc(Dev* d, int grid, cudaStream_t s, double sums[2]);
 int noalloc_max_blocks();
 }  // namespace epk
@@ -376,7 +376,7 @@ ep_status build_graph(ep_instance* I) {
         C.chk(add_while(s, &h_outer, &body));
         if (C.err == cudaSuccess) {
             C.chk(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-            C.chk(epk::launch_pcg32(I->d, I->grid_pcg, s2));
+            C.chk(epk::launch_pcg32(I->d, h, I->grid_pcg, s2));
             epk::launch_correct_ff(I->d, h, I->grid_nodes, s2);
             epk::launch_rhs_ff(I->d, h, 0, 1, I->grid_tiles, s2);
             C.chk(cudaStreamEndCapture(s2, &body));
@@ -456,7 +456,7 @@ ep_status step_host(ep_instance* I) {
             int fi = 1;
             if (h.op32 == EP_OP_STENCIL) {
                 cudaError_t pe = cudaSuccess;
-                timed(I, K_PCG32, [&] { pe = epk::launch_pcg32(d, I->grid_pcg, s); });
+                timed(I, K_PCG32, [&] { pe = epk::launch_pcg32(d, h, I->grid_pcg, s); });
                 CUDA_TRY(pe);
                 fi = 0;
             }

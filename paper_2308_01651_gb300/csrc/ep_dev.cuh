@@ -132,8 +132,8 @@ struct AsmParams {
 
 // Counter slots (one per reducing kernel so that consecutive kernels never
 // share a counter).
-// CNT_BAR and CNT_BAR + 1: arrival count and generation of the persistent
-// solver's grid barrier.
+// CNT_BAR and CNT_BAR + 1: the 64-bit arrival counter of the persistent
+// solver's grid barrier (8-byte aligned: the array is 256-byte aligned).
 enum { CNT_RHS = 0, CNT_APPLY = 1, CNT_UPDATE = 2, CNT_RESID = 3, CNT_FINISH = 4, CNT_BAR = 6, CNT_N = 8 };
 
 // ---------------------------------------------------------------- helpers --

@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Dev* __restrict__ Dp)
 }
 
 template <typename G>
-__global__ void __launch_bounds__(kNodeThreads) k_ionic_tt(Dev* __restrict__ Dp) {
+__global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_tt(Dev* __restrict__ Dp) {
     const Dev& D = *Dp;
     const StepConsts c = step_consts(D);
     const int N = D.N;

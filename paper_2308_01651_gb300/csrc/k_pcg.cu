@@ -32,39 +32,37 @@ namespace epk {
 
 constexpr long long kBarrierSpinLimit = 1ll << 24;  // x >= 64 ns naps: about a second
 
-// Bounded grid barrier (all blocks of a cooperative launch).  count and gen
-// persist between launches: count returns to 0 after every barrier, gen
-// only grows.  Thread 0 of each block arrives with a release and waits with
+// Bounded grid barrier (all blocks of a cooperative launch) on a 64-bit
+// arrival counter that only grows: every barrier adds exactly one arrival
+// per block, so barrier k of a launch completes when the counter reaches
+// base + k G, base being the counter at launch start (a multiple of G).
+// Thread 0 of each block arrives with one acq_rel atomic and waits with
 // acquire loads; the block's other threads are ordered behind it by
-// __syncthreads.  Returns false after recording EP_ETIMEOUT when the other
-// blocks did not all arrive in time.
-__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned int& my_gen,
+// __syncthreads.  `target` is thread 0's running target (0 before the first
+// barrier of the launch).  Returns false after recording EP_ETIMEOUT when the
+// other blocks did not all arrive in time.
+__device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned long long& target,
                                              int* status) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int good = 1;
-        const unsigned int g = my_gen;
-        unsigned int old;
-        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
-        if (old == gridDim.x - 1) {
-            asm volatile("st.relaxed.gpu.u32 [%0], 0;" ::"l"(count) : "memory");
-            asm volatile("red.add.release.gpu.u32 [%0], 1;" ::"l"(gen) : "memory");
-        } else {
-            long long spins = 0;
-            for (;;) {
-                unsigned int cur;
-                asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(gen) : "memory");
-                if (cur != g) break;
-                if (++spins > kBarrierSpinLimit) {
-                    good = 0;
-                    atomicCAS(status, (int)EP_OK, (int)EP_ETIMEOUT);
-                    break;
-                }
-                __nanosleep(32);
+        unsigned long long old;
+        asm volatile("atom.add.acq_rel.gpu.u64 %0, [%1], 1;" : "=l"(old) : "l"(count) : "memory");
+        const unsigned long long G = gridDim.x;
+        target = (target == 0ull ? old - old % G : target) + G;
+        long long spins = 0;
+        for (;;) {
+            unsigned long long cur;
+            asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(cur) : "l"(count) : "memory");
+            if (cur >= target) break;
+            if (++spins > kBarrierSpinLimit) {
+                good = 0;
+                atomicCAS(status, (int)EP_OK, (int)EP_ETIMEOUT);
+                break;
             }
+            __nanosleep(20);
         }
-        my_gen = g + 1;
         ok = good;
     }
     __syncthreads();
@@ -113,9 +111,8 @@ struct NbrOff {
     int x[3], y[3], z[3];
 };
 
-__device__ __forceinline__ NbrOff nbr_offsets(const Dev& D, unsigned int f) {
+__device__ __forceinline__ NbrOff nbr_offsets(int nx, int nxy, int wrap, unsigned int f) {
     NbrOff o;
-    const int nx = D.NX, nxy = D.NX * D.NY, wrap = D.periodic ? D.NX * (D.NY - 1) : 0;
     o.x[0] = (f & 1u) ? 0 : -1;
     o.x[1] = 0;
     o.x[2] = (f & 2u) ? 0 : 1;
@@ -135,6 +132,8 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg32_stencil(Dev* __restric
     const int G = gridDim.x;
     const int T = G * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    // mesh sizes in registers for the neighbour offsets
+    const int nx = D.NX, nxy = D.NX * D.NY, wrap = D.periodic ? D.NX * (D.NY - 1) : 0;
     float* r = D.r32;
     float* u = D.z32;
     float* w = D.q32;
@@ -145,20 +144,17 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg32_stencil(Dev* __restric
     const unsigned char* __restrict__ flag = D.nflag;
     const float4* __restrict__ A = D.Ahi;
     float* part = reinterpret_cast<float*>(D.partial);
-    unsigned int* bcount = D.counter + CNT_BAR;
-    unsigned int* bgen = D.counter + CNT_BAR + 1;
-    unsigned int my_gen = 0;
-    if (threadIdx.x == 0) my_gen = *(volatile unsigned int*)bgen;
-    // CG scalars: kept by thread 0 (the only thread doing double arithmetic,
-    // which runs at a small fraction of the float rate), handed to the block
-    // through shared memory after every reduction
+    unsigned long long* bcount = reinterpret_cast<unsigned long long*>(D.counter + CNT_BAR);
+    unsigned long long target = 0ull;
+    // CG scalars (float, like the solve): formed by thread 0 of every block
+    // from the same totals, handed to the block through shared memory
     __shared__ float sc_alpha, sc_beta;
     __shared__ int sc_done, sc_it, sc_nan;
-    __shared__ double sc_stop, sc_gam_old, sc_alpha_old, sc_rr, sc_gam;
+    __shared__ float sc_stop, sc_gam_old, sc_alpha_old, sc_rr, sc_gam;
     if (threadIdx.x == 0) {
         sc_it = 0;
         sc_nan = 0;
-        sc_stop = sc_gam_old = sc_alpha_old = sc_rr = sc_gam = 0.0;
+        sc_stop = sc_gam_old = sc_alpha_old = sc_rr = sc_gam = 0.f;
     }
     float alpha = 0.f, beta = 0.f;
     bool first = true;
@@ -177,12 +173,12 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg32_stencil(Dev* __restric
                 r[n] = r1;
                 u[n] = dv * r1;
             }
-            if (!grid_barrier(bcount, bgen, my_gen, &D.status)) break;
+            if (!grid_barrier(bcount, target, &D.status)) break;
         }
         // ---- apply w = A u and the block partials
         float v[3] = {0.f, 0.f, 0.f};  // gamma, eta, rho
         for (int n = t0; n < N; n += T) {
-            const NbrOff o = nbr_offsets(D, flag[n]);
+            const NbrOff o = nbr_offsets(nx, nxy, wrap, flag[n]);
             float acc = 0.f;
 #pragma unroll
             for (int g = 0; g < kGroups; ++g) {
@@ -201,24 +197,24 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg32_stencil(Dev* __restric
             v[2] = fmaf(rn, rn, v[2]);
         }
         publish<3>(v, part, G);
-        if (!grid_barrier(bcount, bgen, my_gen, &D.status)) break;
+        if (!grid_barrier(bcount, target, &D.status)) break;
         if (threadIdx.x < 32) {
             float tt[3];
             gather<3>(part, G, tt);
             if (threadIdx.x == 0) {
                 if (!first) ++sc_it;
-                const double gam = tt[0], rr = tt[2];
+                const float gam = tt[0], rr = tt[2];
                 sc_gam = gam;
                 sc_rr = rr;
-                if (first) sc_stop = D.inner_tol * D.inner_tol * rr;
+                if (first) sc_stop = (float)(D.inner_tol * D.inner_tol) * rr;
                 const bool nan = !(tt[0] == tt[0] && tt[1] == tt[1] && tt[2] == tt[2]);
                 sc_nan = nan ? 1 : 0;
                 const int done = (nan || rr <= sc_stop || sc_it >= D.max_iter) ? 1 : 0;
                 if (!done) {
-                    const double b = first ? 0.0 : gam / sc_gam_old;
-                    const double a = first ? gam / tt[1] : gam / ((double)tt[1] - b * gam / sc_alpha_old);
-                    sc_beta = (float)b;
-                    sc_alpha = (float)a;
+                    const float b = first ? 0.f : gam / sc_gam_old;
+                    const float a = first ? gam / tt[1] : gam / (tt[1] - b * gam / sc_alpha_old);
+                    sc_beta = b;
+                    sc_alpha = a;
                     sc_gam_old = gam;
                     sc_alpha_old = a;
                 }
@@ -248,7 +244,7 @@ int pcg_blocks_per_sm() {
     return occ;
 }
 
-cudaError_t launch_pcg32(Dev* d, int grid, cudaStream_t s) {
+cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kPcgThreads);

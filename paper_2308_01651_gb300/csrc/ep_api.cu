@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -32,6 +33,12 @@ void launch_apply32_stencil(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_apply32_mf(Dev* d, const Dev& h, cudaStream_t s);
 void launch_update32(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s);
 void launch_correct_ff(Dev* d, const Dev& h, int grid, cudaStream_t s);
+void launch_ionic_batch(const Batch& B, int model, int grid, cudaStream_t s);
+void launch_rhs_ff_batch(const Batch& B, int first, int graph, int grid, cudaStream_t s);
+void launch_correct_ff_batch(const Batch& B, int grid, cudaStream_t s);
+void launch_finish_batch(const Batch& B, int grid, cudaStream_t s);
+cudaError_t launch_pcg32_batch(const Batch& B, int grid, cudaStream_t s);
+void launch_batch_cond(Dev* const* devs, int n, const unsigned long long* h, cudaStream_t s);
 void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s);
 int mf_tiles(const Dev& h);
 cudaError_t mf_prepare();
@@ -827,6 +834,203 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     return build_graph(I);
 }
 
+// ---- batched stepping --------------------------------------------------------
+// ep_step_batch runs refined stencil-operator instances together: one launch
+// per phase over all instances (two for the ionic step when both models are
+// present), the refinement sweeps as one conditional loop that runs while any
+// instance still refines, all captured in one CUDA graph per batch.  Every
+// instance keeps the block counts of its own single-instance launches in the
+// non-persistent kernels, so their reductions sum in the same order as when
+// it runs alone; the persistent inner solver's blocks are shared out in
+// proportion to the instances' sizes (one cooperative grid must fit on the
+// GPU), which changes only the rounding of the inner iterations.
+
+struct BatchPlan {
+    std::vector<ep_instance*> key;
+    cudaStream_t stream = nullptr;
+    void* dmem = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void release() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (dmem) cudaFree(dmem);
+        if (stream) cudaStreamDestroy(stream);
+        exec = nullptr;
+        graph = nullptr;
+        dmem = nullptr;
+        stream = nullptr;
+    }
+};
+
+std::mutex g_batch_mu;
+std::vector<BatchPlan*> g_plans;  // most recent last, at most kMaxPlans
+constexpr size_t kMaxPlans = 4;
+
+void drop_plans_of(const ep_instance* I) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t k = 0; k < g_plans.size();) {
+        BatchPlan* P = g_plans[k];
+        if (std::find(P->key.begin(), P->key.end(), I) != P->key.end()) {
+            P->release();
+            delete P;
+            g_plans.erase(g_plans.begin() + k);
+        } else {
+            ++k;
+        }
+    }
+}
+
+bool batchable(const ep_instance* I) {
+    return I && I->h.prec == EP_PREC_FP32_REFINED && I->h.op32 == EP_OP_STENCIL && I->graph_mode &&
+           !I->profiling && I->sticky == EP_OK;
+}
+
+ep_status build_plan(BatchPlan* P) {
+    const int n = (int)P->key.size();
+    int dev = 0, sms = 152;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int occ = epk::pcg_blocks_per_sm();
+    if (occ <= 0) return fail(EP_ECUDA, "occupancy query of the persistent solver failed");
+    const int cap = sms * occ;
+    if (n > cap) return fail(EP_EINVAL, "batch larger than the persistent solver's resident blocks");
+    // host tables: all instances, then the BO and TTP06 subsets
+    std::vector<Dev*> all, bo, tt;
+    std::vector<int> s_tiles{0}, s_nodes{0}, s_pcg{0}, s_bo{0}, s_tt{0};
+    double total = 0.0;
+    for (ep_instance* I : P->key) total += (double)I->h.N;
+    // persistent solver: blocks in proportion to size, at least one each,
+    // at most what the instance uses alone, the sum within the resident cap
+    std::vector<int> gp(n);
+    int used = 0;
+    for (int i = 0; i < n; ++i) {
+        const ep_instance* I = P->key[i];
+        const int want = I->grid_pcg;
+        gp[i] = std::max(1, std::min(want, (int)std::floor((double)cap * I->h.N / total)));
+        used += gp[i];
+    }
+    while (used > cap) {  // trim the largest shares
+        int k = (int)(std::max_element(gp.begin(), gp.end()) - gp.begin());
+        if (gp[k] <= 1) break;
+        --gp[k];
+        --used;
+    }
+    if (used > cap) return fail(EP_EINVAL, "batch does not fit the persistent solver's resident blocks");
+    for (int i = 0; i < n; ++i) {
+        ep_instance* I = P->key[i];
+        all.push_back(I->d);
+        s_tiles.push_back(s_tiles.back() + I->grid_tiles);
+        s_nodes.push_back(s_nodes.back() + I->grid_nodes);
+        s_pcg.push_back(s_pcg.back() + gp[i]);
+        if (I->h.model == EP_MODEL_BO) {
+            bo.push_back(I->d);
+            s_bo.push_back(s_bo.back() + I->grid_ionic);
+        } else {
+            tt.push_back(I->d);
+            s_tt.push_back(s_tt.back() + I->grid_ionic);
+        }
+    }
+    // one device buffer: pointer arrays first (8-byte aligned), then ints
+    const size_t np = all.size() + bo.size() + tt.size() + 1;  // + the loop's handle
+    const size_t ni = s_tiles.size() + s_nodes.size() + s_pcg.size() + s_bo.size() + s_tt.size();
+    std::vector<char> hbuf(np * sizeof(Dev*) + ni * sizeof(int));
+    char* q = hbuf.data();
+    auto put = [&](const void* src, size_t bytes) {
+        std::memcpy(q, src, bytes);
+        char* at = q;
+        q += bytes;
+        return at - hbuf.data();
+    };
+    const unsigned long long hzero = 0ull;
+    const size_t o_h = put(&hzero, sizeof(hzero));
+    const size_t o_all = put(all.data(), all.size() * sizeof(Dev*));
+    const size_t o_bo = put(bo.data(), bo.size() * sizeof(Dev*));
+    const size_t o_tt = put(tt.data(), tt.size() * sizeof(Dev*));
+    const size_t o_st = put(s_tiles.data(), s_tiles.size() * sizeof(int));
+    const size_t o_sn = put(s_nodes.data(), s_nodes.size() * sizeof(int));
+    const size_t o_sp = put(s_pcg.data(), s_pcg.size() * sizeof(int));
+    const size_t o_sb = put(s_bo.data(), s_bo.size() * sizeof(int));
+    const size_t o_sx = put(s_tt.data(), s_tt.size() * sizeof(int));
+    CUDA_TRY(cudaMalloc(&P->dmem, hbuf.size()));
+    CUDA_TRY(cudaMemcpy(P->dmem, hbuf.data(), hbuf.size(), cudaMemcpyHostToDevice));
+    char* d = static_cast<char*>(P->dmem);
+    auto mk = [&](size_t od, size_t os, int cnt, Dev* only) {
+        if (cnt == 1) return epk::single_batch(only);
+        return epk::Batch{nullptr, reinterpret_cast<Dev* const*>(d + od), reinterpret_cast<const int*>(d + os), cnt};
+    };
+    const epk::Batch Bt = mk(o_all, o_st, n, all[0]);
+    const epk::Batch Bn = mk(o_all, o_sn, n, all[0]);
+    const epk::Batch Bp = mk(o_all, o_sp, n, all[0]);
+    Dev* const* dall = reinterpret_cast<Dev* const*>(d + o_all);
+    const unsigned long long* dh = reinterpret_cast<const unsigned long long*>(d + o_h);
+
+    CUDA_TRY(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+    cudaStream_t s = P->stream, s2 = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    Capture C{s};
+    cudaGraphConditionalHandle hc = 0;
+    C.chk(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    if (!bo.empty()) epk::launch_ionic_batch(mk(o_bo, o_sb, (int)bo.size(), bo[0]), EP_MODEL_BO, s_bo.back(), s);
+    if (!tt.empty()) epk::launch_ionic_batch(mk(o_tt, o_sx, (int)tt.size(), tt[0]), EP_MODEL_TTP06, s_tt.back(), s);
+    epk::launch_rhs_ff_batch(Bt, 1, 0, s_tiles.back(), s);
+    epk::launch_batch_cond(dall, n, dh, s);
+    cudaGraph_t body = nullptr;
+    C.chk(add_while(s, &hc, &body));
+    if (C.err == cudaSuccess) {
+        C.chk(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        C.chk(epk::launch_pcg32_batch(Bp, s_pcg.back(), s2));
+        epk::launch_correct_ff_batch(Bn, s_nodes.back(), s2);
+        epk::launch_rhs_ff_batch(Bt, 0, 0, s_tiles.back(), s2);
+        epk::launch_batch_cond(dall, n, dh, s2);
+        C.chk(cudaStreamEndCapture(s2, &body));
+    }
+    epk::launch_finish_batch(Bn, s_nodes.back(), s);
+    cudaGraph_t g = nullptr;
+    C.chk(cudaStreamEndCapture(s, &g));
+    C.chk(cudaGetLastError());
+    cudaStreamDestroy(s2);
+    if (C.err != cudaSuccess || !hc) {
+        if (g) cudaGraphDestroy(g);
+        return fail(EP_ECUDA, std::string("building the batch graph: ") + cudaGetErrorString(C.err));
+    }
+    P->graph = g;
+    const unsigned long long hv = (unsigned long long)hc;
+    CUDA_TRY(cudaMemcpy(d + o_h, &hv, sizeof(hv), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaGraphInstantiate(&P->exec, g, 0));
+    return EP_OK;
+}
+
+// the cached plan for this instance list, built on first use
+ep_status get_plan(ep_instance* const* insts, int n, BatchPlan** out) {
+    std::vector<ep_instance*> key(insts, insts + n);
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t k = 0; k < g_plans.size(); ++k)
+        if (g_plans[k]->key == key) {
+            BatchPlan* P = g_plans[k];
+            g_plans.erase(g_plans.begin() + k);
+            g_plans.push_back(P);
+            *out = P;
+            return EP_OK;
+        }
+    BatchPlan* P = new BatchPlan();
+    P->key = key;
+    ep_status st = build_plan(P);
+    if (st != EP_OK) {
+        P->release();
+        delete P;
+        return st;
+    }
+    if (g_plans.size() >= kMaxPlans) {
+        g_plans.front()->release();
+        delete g_plans.front();
+        g_plans.erase(g_plans.begin());
+    }
+    g_plans.push_back(P);
+    *out = P;
+    return EP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -907,6 +1111,46 @@ ep_status ep_step(ep_instance* I, int64_t n_steps) {
 
 ep_status ep_step_batch(ep_instance* const* insts, int32_t n, int64_t n_steps) {
     if (!insts || n < 0) return fail(EP_EINVAL, "bad batch");
+    if (n_steps < 0) return fail(EP_EINVAL, "n_steps < 0");
+    for (int32_t k = 0; k < n; ++k) {
+        if (!insts[k]) return fail(EP_EINVAL, "NULL instance in the batch");
+        for (int32_t j = 0; j < k; ++j)
+            if (insts[j] == insts[k]) return fail(EP_EINVAL, "an instance appears twice in the batch");
+    }
+    bool together = n >= 2;
+    for (int32_t k = 0; k < n && together; ++k) together = batchable(insts[k]);
+    if (together && n_steps > 0) {
+        BatchPlan* P = nullptr;
+        ep_status st = get_plan(insts, n, &P);
+        if (st != EP_OK) return st;
+        for (int32_t k = 0; k < n; ++k) CUDA_TRY(cudaStreamSynchronize(insts[k]->stream));
+        for (int64_t step = 0; step < n_steps; ++step) {
+            for (int32_t k = 0; k < n; ++k) {
+                ep_instance* I = insts[k];
+                if (required_alpha_dt(I->h, I->host_step) != I->alpha_dt_dev) {
+                    // a BDF order change: update this instance's operators first
+                    CUDA_TRY(cudaStreamSynchronize(P->stream));
+                    ensure_alpha(I);
+                    CUDA_TRY(cudaGetLastError());
+                    CUDA_TRY(cudaStreamSynchronize(I->stream));
+                }
+            }
+            CUDA_TRY(cudaGraphLaunch(P->exec, P->stream));
+            for (int32_t k = 0; k < n; ++k) insts[k]->host_step += 1;
+        }
+        CUDA_TRY(cudaStreamSynchronize(P->stream));
+        ep_status first = EP_OK;
+        std::string msg;
+        for (int32_t k = 0; k < n; ++k) {
+            ep_status st2 = ep_sync(insts[k]);
+            if (st2 != EP_OK && first == EP_OK) {
+                first = st2;
+                msg = g_err;
+            }
+        }
+        if (first != EP_OK) return fail(first, msg);
+        return EP_OK;
+    }
     for (int32_t k = 0; k < n; ++k) {
         ep_status st = ep_step_async(insts[k], n_steps);
         if (st != EP_OK) return st;
@@ -1231,6 +1475,7 @@ ep_status ep_residual_norm_noalloc(const ep_instance* I, double* relres_out) {
 
 ep_status ep_destroy(ep_instance* I) {
     if (!I) return EP_OK;
+    drop_plans_of(I);
     if (I->stream) cudaStreamSynchronize(I->stream);
     free_all(I);
     delete I;

@@ -229,6 +229,39 @@ __device__ __forceinline__ void set_cond(unsigned long long h, int* flag, unsign
     if (h) cudaGraphSetConditional((cudaGraphConditionalHandle)h, v);
 }
 
+// ---- batched launches -------------------------------------------------------
+// One launch may serve several instances: its blocks are split into
+// consecutive ranges, start[i] .. start[i+1]-1 for instance i, and every block
+// works on its instance alone with the block index and count of its range --
+// the same values a launch of that instance alone would use, so per-instance
+// results do not depend on what else is in the launch.  n == 1 is a plain
+// single-instance launch (d0, whole grid).
+struct Batch {
+    Dev* d0;            // n == 1
+    Dev* const* devs;   // n > 1: device array of the instances' descriptors
+    const int* start;   // n > 1: device array, n + 1 entries
+    int n;
+};
+
+struct Slot {
+    Dev* D;
+    int blk, nblk;
+};
+
+__device__ __forceinline__ Slot batch_slot(const Batch& B) {
+    if (B.n <= 1) return Slot{B.d0, (int)blockIdx.x, (int)gridDim.x};
+    const int b = blockIdx.x;
+    int lo = 0, hi = B.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.start[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return Slot{B.devs[lo], b - B.start[lo], B.start[lo + 1] - B.start[lo]};
+}
+
+inline Batch single_batch(Dev* d) { return Batch{d, nullptr, nullptr, 1}; }
+
 // Node (i, j, k) of index n, and the neighbour at offset slot t (0..26);
 // returns -1 where the neighbour does not exist.
 __device__ __forceinline__ void node_ijk(const Dev& D, int n, int& i, int& j, int& k) {

@@ -68,13 +68,14 @@ __global__ void __launch_bounds__(kNodeThreads) k_update32(Dev* __restrict__ Dp,
 }
 
 // Activation update, non-finite check, rotation of the time levels.
-__global__ void __launch_bounds__(kNodeThreads) k_finish(Dev* __restrict__ Dp) {
-    Dev& D = *Dp;
+__global__ void __launch_bounds__(kNodeThreads) k_finish(Batch B) {
+    const Slot S = batch_slot(B);
+    Dev& D = *S.D;
     const double t_new = (double)(D.step + 1) * D.dt;
     float v[1] = {0.f};
     const double none[1] = {0.0};
     const bool ff = D.u_hi != nullptr;  // refined: the iterate is float-float
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x) {
+    for (int n = S.blk * blockDim.x + threadIdx.x; n < D.N; n += S.nblk * blockDim.x) {
         if (ff) {
             // slope and checks in float from the pairs; the only double
             // operation is the rounding of the new potential for u_n
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_finish(Dev* __restrict__ Dp) {
             }
         }
     }
-    grid_reduce<1, 0>(v, none, D.partial, D.counter + CNT_FINISH, blockIdx.x, gridDim.x, [&](double* tot) {
+    grid_reduce<1, 0>(v, none, D.partial, D.counter + CNT_FINISH, S.blk, S.nblk, [&](double* tot) {
         if (tot[0] > 0.0 && D.status == EP_OK) D.status = EP_ENAN;
         double* t = D.u_nm1;
         D.u_nm1 = D.u_n;
@@ -139,9 +140,27 @@ __global__ void __launch_bounds__(kNodeThreads) k_finish(Dev* __restrict__ Dp) {
     });
 }
 
+// Loop condition of a batched refinement sweep: another sweep while any
+// instance's refinement goes on.
+// The handle is read from device memory: it is created after the kernels
+// upstream of the loop have been captured.
+__global__ void k_batch_cond(Dev* const* devs, int n, const unsigned long long* h) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned int any = 0;
+    for (int i = 0; i < n; ++i) any |= devs[i]->f_outer ? 1u : 0u;
+    cudaGraphSetConditional((cudaGraphConditionalHandle)*h, any);
+}
+
+void launch_batch_cond(Dev* const* devs, int n, const unsigned long long* h, cudaStream_t s) {
+    k_batch_cond<<<1, 32, 0, s>>>(devs, n, h);
+}
+
 void launch_update32(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s) {
     k_update32<<<grid, kNodeThreads, 0, s>>>(d, graph);
 }
-void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s) { k_finish<<<grid, kNodeThreads, 0, s>>>(d); }
+void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s) {
+    k_finish<<<grid, kNodeThreads, 0, s>>>(single_batch(d));
+}
+void launch_finish_batch(const Batch& B, int grid, cudaStream_t s) { k_finish<<<grid, kNodeThreads, 0, s>>>(B); }
 
 }  // namespace epk

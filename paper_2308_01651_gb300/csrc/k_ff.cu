@@ -14,6 +14,9 @@
 
 namespace epk {
 
+void launch_rhs_ff_batch(const Batch& B, int first, int graph, int grid, cudaStream_t s);
+void launch_correct_ff_batch(const Batch& B, int grid, cudaStream_t s);
+
 // stage the float-float pair (ah, al) of the tile plus halo
 __device__ __forceinline__ void stage_ff(const Dev& D, const TileGeo& g, int* sidx, const float* ah,
                                          const float* al, float* sh, float* sl) {
@@ -33,11 +36,15 @@ __device__ __forceinline__ void stage_ff(const Dev& D, const TileGeo& g, int* si
 // and r = b - y with the stored b.  M v on a uniform slab needs no stored
 // coefficients (row_mass_slab).
 template <int FIRST>
-__global__ void __launch_bounds__(kStThreads) k_rhs_ff(Dev* __restrict__ Dp, int graph) {
+__global__ void __launch_bounds__(kStThreads) k_rhs_ff(Batch B, int graph) {
     __shared__ int sidx[SHN];
     __shared__ float suh[SHN], sul[SHN];
     __shared__ float svh[FIRST ? SHN : 1], svl[FIRST ? SHN : 1];
-    Dev& D = *Dp;
+    const Slot S = batch_slot(B);
+    Dev& D = *S.D;
+    // a residual after a correction runs only while the instance's
+    // refinement goes on (a batched sweep also visits finished instances)
+    if (!FIRST && !D.f_outer) return;
     const size_t N = (size_t)D.N;
     const float ns = D.nscale;
     const int order = (D.bdf == 2 && D.step >= 1) ? 2 : 1;
@@ -48,7 +55,7 @@ __global__ void __launch_bounds__(kStThreads) k_rhs_ff(Dev* __restrict__ Dp, int
     float vf[4] = {0.f, 0.f, 0.f, 0.f};
     const double none[1] = {0.0};
     const int ntiles = st_tiles(D);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int tile = S.blk; tile < ntiles; tile += S.nblk) {
         const TileGeo g = tile_geo(D, tile);
         __syncthreads();
         if (FIRST) {
@@ -102,7 +109,7 @@ __global__ void __launch_bounds__(kStThreads) k_rhs_ff(Dev* __restrict__ Dp, int
             vf[3] = fmaf(r32, r32, vf[3]);
         });
     }
-    grid_reduce<4, 0>(vf, none, D.partial, D.counter + CNT_RHS, blockIdx.x, gridDim.x, [&](double* t) {
+    grid_reduce<4, 0>(vf, none, D.partial, D.counter + CNT_RHS, S.blk, S.nblk, [&](double* t) {
         if (FIRST) D.bb = t[0];
         const double rr = t[1], bb = D.bb;
         const bool nan = !(rr == rr);
@@ -117,6 +124,8 @@ __global__ void __launch_bounds__(kStThreads) k_rhs_ff(Dev* __restrict__ Dp, int
         if (FIRST) {
             D.sweeps = 0;
             D.it_total = 0;
+            // the persistent solver's barrier counter starts the step at 0
+            *reinterpret_cast<unsigned long long*>(D.counter + CNT_BAR) = 0ull;
         } else {
             D.sweeps += 1;
             if (!conv && D.sweeps >= D.max_sweeps && D.status == EP_OK) D.status = EP_ENOCONV;
@@ -130,12 +139,14 @@ __global__ void __launch_bounds__(kStThreads) k_rhs_ff(Dev* __restrict__ Dp, int
 }
 
 // u += delta in float-float
-__global__ void __launch_bounds__(kNodeThreads) k_correct_ff(Dev* __restrict__ Dp) {
-    const Dev& D = *Dp;
+__global__ void __launch_bounds__(kNodeThreads) k_correct_ff(Batch B) {
+    const Slot S = batch_slot(B);
+    const Dev& D = *S.D;
+    if (!D.f_outer) return;
     float* __restrict__ uh = D.u_hi;
     float* __restrict__ ul = D.u_lo;
     const float* __restrict__ d = D.d32;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x) {
+    for (int n = S.blk * blockDim.x + threadIdx.x; n < D.N; n += S.nblk * blockDim.x) {
         float h = uh[n], l = ul[n];
         ff_add_f(h, l, d[n], h, l);
         uh[n] = h;
@@ -144,12 +155,18 @@ __global__ void __launch_bounds__(kNodeThreads) k_correct_ff(Dev* __restrict__ D
 }
 
 void launch_rhs_ff(Dev* d, const Dev& h, int first, int graph, int grid, cudaStream_t s) {
-    if (first) k_rhs_ff<1><<<grid, kStThreads, 0, s>>>(d, graph);
-    else k_rhs_ff<0><<<grid, kStThreads, 0, s>>>(d, graph);
+    launch_rhs_ff_batch(single_batch(d), first, graph, grid, s);
+}
+void launch_rhs_ff_batch(const Batch& B, int first, int graph, int grid, cudaStream_t s) {
+    if (first) k_rhs_ff<1><<<grid, kStThreads, 0, s>>>(B, graph);
+    else k_rhs_ff<0><<<grid, kStThreads, 0, s>>>(B, graph);
 }
 
 void launch_correct_ff(Dev* d, const Dev& h, int grid, cudaStream_t s) {
-    k_correct_ff<<<grid, kNodeThreads, 0, s>>>(d);
+    launch_correct_ff_batch(single_batch(d), grid, s);
+}
+void launch_correct_ff_batch(const Batch& B, int grid, cudaStream_t s) {
+    k_correct_ff<<<grid, kNodeThreads, 0, s>>>(B);
 }
 
 }  // namespace epk

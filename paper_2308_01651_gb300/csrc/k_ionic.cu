@@ -109,8 +109,9 @@ __device__ __forceinline__ float applied_f(const Dev& D, const StepConsts& c, in
 // G: arithmetic/storage type of the gates (float when refined, double in the
 // FP64 path).
 template <typename G>
-__global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Dev* __restrict__ Dp) {
-    const Dev& D = *Dp;
+__global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Batch B) {
+    const Slot S = batch_slot(B);
+    const Dev& D = *S.D;
     const StepConsts c = step_consts(D);
     const int N = D.N;
     G* __restrict__ wn;
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Dev* __restrict__ Dp)
         wm = reinterpret_cast<G*>(D.s64_nm1);
     }
     const G dtg = G(c.dt), alg = G(c.alpha);
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+    for (int n = S.blk * blockDim.x + threadIdx.x; n < N; n += S.nblk * blockDim.x) {
         G uEg;
         double uB = 0.0, uE = 0.0;
         float ubh = 0.f, ubl = 0.f, ueh = 0.f, uel = 0.f;
@@ -166,12 +167,13 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Dev* __restrict__ Dp)
 }
 
 template <typename G>
-__global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_tt(Dev* __restrict__ Dp) {
-    const Dev& D = *Dp;
+__global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_tt(Batch B) {
+    const Slot S = batch_slot(B);
+    const Dev& D = *S.D;
     const StepConsts c = step_consts(D);
     const int N = D.N;
     const G dtg = G(c.dt), alg = G(c.alpha);
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+    for (int n = S.blk * blockDim.x + threadIdx.x; n < N; n += S.nblk * blockDim.x) {
         const int cell = D.cell[n];
         if constexpr (sizeof(G) == 4) {
             // ---- refined: float gates, float-float concentrations and potentials
@@ -294,13 +296,20 @@ __global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_
 
 void launch_ionic(Dev* d, const Dev& h, int grid, cudaStream_t s) {
     const bool refined = h.prec == EP_PREC_FP32_REFINED;
+    const Batch B = single_batch(d);
     if (h.model == EP_MODEL_BO) {
-        if (refined) k_ionic_bo<float><<<grid, kNodeThreads, 0, s>>>(d);
-        else k_ionic_bo<double><<<grid, kNodeThreads, 0, s>>>(d);
+        if (refined) k_ionic_bo<float><<<grid, kNodeThreads, 0, s>>>(B);
+        else k_ionic_bo<double><<<grid, kNodeThreads, 0, s>>>(B);
     } else {
-        if (refined) k_ionic_tt<float><<<grid, kNodeThreads, 0, s>>>(d);
-        else k_ionic_tt<double><<<grid, kNodeThreads, 0, s>>>(d);
+        if (refined) k_ionic_tt<float><<<grid, kNodeThreads, 0, s>>>(B);
+        else k_ionic_tt<double><<<grid, kNodeThreads, 0, s>>>(B);
     }
+}
+
+// refined instances of one model, batched
+void launch_ionic_batch(const Batch& B, int model, int grid, cudaStream_t s) {
+    if (model == EP_MODEL_BO) k_ionic_bo<float><<<grid, kNodeThreads, 0, s>>>(B);
+    else k_ionic_tt<float><<<grid, kNodeThreads, 0, s>>>(B);
 }
 
 }  // namespace epk

@@ -41,7 +41,7 @@ constexpr long long kBarrierSpinLimit = 1ll << 24;  // x >= 64 ns naps: about a 
 // __syncthreads.  `target` is thread 0's running target (0 before the first
 // barrier of the launch).  Returns false after recording EP_ETIMEOUT when the
 // other blocks did not all arrive in time.
-__device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned long long& target,
+__device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned long long& target, int G,
                                              int* status) {
     __shared__ int ok;
     __syncthreads();
@@ -49,8 +49,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned
         int good = 1;
         unsigned long long old;
         asm volatile("atom.add.acq_rel.gpu.u64 %0, [%1], 1;" : "=l"(old) : "l"(count) : "memory");
-        const unsigned long long G = gridDim.x;
-        target = (target == 0ull ? old - old % G : target) + G;
+        const unsigned long long g = (unsigned long long)G;
+        target = (target == 0ull ? old - old % g : target) + g;
         long long spins = 0;
         for (;;) {
             unsigned long long cur;
@@ -72,7 +72,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned
 // Block sums of NV float values (warp butterflies, then the warps' sums by
 // warp 0 in the same way), written as part[k * G + blockIdx.x].
 template <int NV>
-__device__ __forceinline__ void publish(const float (&v)[NV], float* part, int G) {
+__device__ __forceinline__ void publish(const float (&v)[NV], float* part, int G, int blk) {
     __shared__ float sh[NV][kMaxBlock / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
 #pragma unroll
@@ -85,7 +85,7 @@ __device__ __forceinline__ void publish(const float (&v)[NV], float* part, int G
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             const float s = warp_sum(lane < nwarp ? sh[k][lane] : 0.f);
-            if (lane == 0) part[(size_t)k * G + blockIdx.x] = s;
+            if (lane == 0) part[(size_t)k * G + blk] = s;
         }
     }
 }
@@ -125,13 +125,16 @@ __device__ __forceinline__ NbrOff nbr_offsets(int nx, int nxy, int wrap, unsigne
     return o;
 }
 
-__global__ void __launch_bounds__(kPcgThreads, 2) k_pcg32_stencil(Dev* __restrict__ Dp) {
-    Dev& D = *Dp;
+__global__ void __launch_bounds__(kPcgThreads, 2) k_pcg32_stencil(Batch B) {
+    const Slot S = batch_slot(B);
+    Dev& D = *S.D;
+    // a batched sweep also visits instances whose refinement has finished
+    if (!D.f_outer) return;
     const int N = D.N;
     const size_t NN = (size_t)N;
-    const int G = gridDim.x;
+    const int G = S.nblk;
     const int T = G * blockDim.x;
-    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t0 = S.blk * blockDim.x + threadIdx.x;
     // mesh sizes in registers for the neighbour offsets
     const int nx = D.NX, nxy = D.NX * D.NY, wrap = D.periodic ? D.NX * (D.NY - 1) : 0;
     float* r = D.r32;
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg32_stencil(Dev* __restric
                 r[n] = r1;
                 u[n] = dv * r1;
             }
-            if (!grid_barrier(bcount, target, &D.status)) break;
+            if (!grid_barrier(bcount, target, G, &D.status)) break;
         }
         // ---- apply w = A u and the block partials
         float v[3] = {0.f, 0.f, 0.f};  // gamma, eta, rho
@@ -196,8 +199,8 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg32_stencil(Dev* __restric
             v[1] = fmaf(un, acc, v[1]);
             v[2] = fmaf(rn, rn, v[2]);
         }
-        publish<3>(v, part, G);
-        if (!grid_barrier(bcount, target, &D.status)) break;
+        publish<3>(v, part, G, S.blk);
+        if (!grid_barrier(bcount, target, G, &D.status)) break;
         if (threadIdx.x < 32) {
             float tt[3];
             gather<3>(part, G, tt);
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg32_stencil(Dev* __restric
         beta = sc_beta;
         first = false;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (S.blk == 0 && threadIdx.x == 0) {
         D.rz = sc_gam;
         D.rr = sc_rr;
         D.it = sc_it;
@@ -244,7 +247,7 @@ int pcg_blocks_per_sm() {
     return occ;
 }
 
-cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, cudaStream_t s) {
+cudaError_t launch_pcg32_batch(const Batch& B, int grid, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kPcgThreads);
@@ -255,7 +258,11 @@ cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, cudaStream_t s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_pcg32_stencil, d);
+    return cudaLaunchKernelEx(&cfg, k_pcg32_stencil, B);
+}
+
+cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, cudaStream_t s) {
+    return launch_pcg32_batch(single_batch(d), grid, s);
 }
 
 }  // namespace epk

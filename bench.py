@@ -39,6 +39,18 @@ UNIT = "DoF-steps/s"
 WORKLOAD = ("slab_ttp06: 2 x 0.7 x 0.3 cm Q1 slab, 200x70x30 elements (442,401 nodes), TTP06 epi, "
             "fibres +60->-60 deg in z, sigma 1.4/0.5/0.25 mS/cm, chi_m 1400/cm, C_m 1 uF/cm^2, BDF2, "
             "dt 0.05 ms, x=0 face stimulus 35.714 mV/ms x 2 ms")
+WORKLOADS = {
+    "c2": WORKLOAD,
+    "c4": ("shell_ttp06: truncated prolate-ellipsoid LV shell, endocardial semi-axes 2.5/2.5/6.5 cm, wall 1 cm, "
+           "Q1 20 transmural x 400 circumferential (periodic) x 260 longitudinal elements (2,192,400 nodes), "
+           "helix fibres +60->-60 deg, s0 transmural, TTP06 endo/M/epi by thirds of the wall, BDF2, dt 0.05 ms, "
+           "apical stimulus 35.714 mV/ms x 2 ms"),
+    "c3": ("batch_slabs: 96 slabs, nodes log-uniform 2e4-4e5, aspect 1-4, h 0.01 cm, Bueno-Orovio/TTP06 1:1, "
+           "conductivities x lognormal(0, 0.3), stimulus on a random face, BDF2, dt 0.05 ms, all advanced "
+           "together (ep_step_batch)"),
+    "c5": ("serving: requests arriving Poisson, sizes log-uniform, slab or ellipsoid shell, Bueno-Orovio/TTP06, "
+           "admitted by device footprint, continuously batched (scaled-down stream; see config)"),
+}
 # FP32 pipe peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # FP64 pipe peak (GB300 nominal dense FP64)
@@ -54,7 +66,7 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_model(name, N, n_elems, inner_iters=1.0):
+def kernel_model(name, N, n_elems, inner_iters=1.0, shell=False):
     """Bytes and flops per launch of each kernel of the refined slab step.
 
     Returns (algorithmic bytes, implementation bytes, flops).  Algorithmic
@@ -66,18 +78,19 @@ def kernel_model(name, N, n_elems, inner_iters=1.0):
     vectors), reported beside them.  inner_iters: inner CG iterations per
     launch of the persistent solver (one launch per refinement sweep)."""
     it = inner_iters
+    g = 12 if shell else 0  # node coordinates of curved cells (hot-path table: shell figures)
     M = {
         # inner CG iteration: x 4 + y 4 + fibres 24 + 7 FP32 vector touches 28
         # = 60 B/node; this layout: per apply 27 FP32 couplings 108 + flag 1 +
         # u 4 + r 4 + w 4, per update r w u s p x D^-1 28 + 5 writes 20, with
         # one apply more than updates (single-reduction CG)
-        "pcg32": (60 * N * it, N * (121 * (it + 1) + 48 * it), (600 * n_elems + 12 * N) * (it + 1)),
+        "pcg32": ((60 + g) * N * it, N * (121 * (it + 1) + 48 * it), (600 * n_elems + 12 * N) * (it + 1)),
         # residual sweep: u 8 + b 8 + r 8 + fibres 24 = 48 B/node; this layout:
         # float-float couplings 216 + u 8 + b 8 + D^-1 4; A u 8 + r/z/d 12
-        "resid": (48 * N, 256 * N, 27 * 12 * N),
+        "resid": ((48 + g) * N, 256 * N, 27 * 12 * N),
         # right-hand side: u_n, u_{n-1} 16 + I_ion 4 + b 8 = 28 B/node; this
         # layout (A u history): v 8 + y_n, y_{n-1} 16 + D^-1 4; b 8 + r/z/d 12
-        "rhs": (28 * N, 48 * N, 27 * 8 * N),
+        "rhs": ((28 + (36 if shell else 0)) * N, (48 + (224 if shell else 0)) * N, 27 * 8 * N),
         # TTP06 refined ionic step: 204 B/node; this layout: u levels 16,
         # gates 2 x 52, concentrations 2 x 40, cell + mask 2; gates 52,
         # concentrations 40, v 8, u_EXT 8
@@ -216,7 +229,7 @@ def oracle_leg(prob, budget_s=20.0, max_steps=50):
     steps = k + 1
     total = t1 + tk
     return {"value": N * steps / total, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"steps 1..{steps} from rest (stimulus on) of the full {N}-node slab, "
+            "sample": f"steps 1..{steps} from rest (stimulus on) of the full {N}-node {prob['name']} mesh, "
                       f"CSR assembly untimed, single thread, {total:.1f} s",
             "ms_per_step": 1e3 * total / steps, "steps": steps}
 
@@ -226,12 +239,12 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2308_01651_gb300 import inputs as I
-    prob = I.slab_ttp06()
+    prob = I.shell_ttp06() if args.workload == "c4" else I.slab_ttp06()
     leg = oracle_leg(prob, budget_s=min(120.0, 10.0 + 2.0 * args.steps), max_steps=max(2, args.steps))
     line = {"metric": METRIC, "value": leg["value"], "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": leg["steps"], "warmup": 0, "ms_per_step": leg["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nodes": prob["mesh"]["xyz"].shape[0],
+            "config": {"workload": WORKLOADS.get(args.workload, WORKLOAD), "nodes": prob["mesh"]["xyz"].shape[0],
                        "l2": "n/a (CPU)", "note": "bounded sample; see cpu_baseline.sample"},
             "cpu_baseline": {k: leg[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": leg["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -262,7 +275,8 @@ def run_ours(args):
     from paper_2308_01651_gb300 import ep
     from paper_2308_01651_gb300 import inputs as I
 
-    prob = I.slab_ttp06()
+    shell = args.workload == "c4"
+    prob = I.shell_ttp06() if shell else I.slab_ttp06()
     N = prob["mesh"]["xyz"].shape[0]
     n_elems = prob["mesh"]["hex"].shape[0]
     # a dedicated stream: the library orders its work on it, and the events
@@ -333,7 +347,7 @@ def run_ours(args):
         tot_prof = sum(v[1] for v in prof.values())
         ipl = it_sum / max(sw_sum, 1)
         for name, (n_l, ms) in prof.items():
-            b, bi, f = kernel_model(name, N, n_elems, ipl)
+            b, bi, f = kernel_model(name, N, n_elems, ipl, shell=shell)
             avg_s = ms / 1e3 / n_l
             kernels[name] = {"launches": n_l, "avg_us": 1e6 * avg_s, "share": ms / tot_prof,
                              "gbs": (b / avg_s / 1e9) if b else None,
@@ -422,12 +436,13 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nodes": N, "elements": n_elems, "precision": "FP32 inner CG, FP64 refinement",
+        "config": {"workload": WORKLOADS[args.workload], "nodes": N, "elements": n_elems,
+                   "precision": "FP32 inner CG, float-float refinement",
                    "op32": {0: "auto", 1: "matrix-free", 2: "stencil"}[op32],
                    "t_window_ms": [W * prob["dt"], (W + K) * prob["dt"]],
                    "l2": "flushed before every step (256 MiB write), per-step CUDA events on the instance stream",
                    "parallelism": f"replicas x{world}"},
-        "latency_ms": {"p50": p50, "p99": p99, "what": "one IMEX step of the whole slab"},
+        "latency_ms": {"p50": p50, "p99": p99, "what": "one IMEX step of the whole mesh"},
         "roofline": roof, "kernels": kernels, "profile_steps": P,
         "op32_autotune_us": {"matrix_free": tune["tune_us_mf"], "stencil": tune["tune_us_stencil"],
                              "chosen": {1: "matrix-free", 2: "stencil"}.get(tune["op32"], "?")},
@@ -438,6 +453,110 @@ def run_ours(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _gpu_setup():
+    import torch
+
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch
+
+
+def run_batch(args):
+    """C3: the batch of slabs advanced together (one launch per phase), and
+    the same instances stepped one after the other for comparison.  The
+    working set (about 7 GB) is far above L2, so no flush between steps;
+    ep_step_batch returns after the batch's stream has finished, so the host
+    clock around it times the device work (plus launch overhead)."""
+    import numpy as np
+    torch = _gpu_setup()
+    from paper_2308_01651_gb300 import ep
+    from paper_2308_01651_gb300 import inputs as I
+
+    REF, ST = ep.EP_PREC_FP32_REFINED, ep.EP_OP_STENCIL
+    probs = I.batch_slabs(count=args.batch_count)
+    t0 = time.perf_counter()
+    insts = [ep.Instance(p, precision=REF, op32=ST) for p in probs]
+    t_create = time.perf_counter() - t0
+    Ns = np.array([i.n for i in insts])
+    handles = [i.h for i in insts]
+    W, K = max(3, args.warmup), args.steps
+    ep.ep_step_batch(handles, W)
+    torch.cuda.synchronize()
+    dev = torch.cuda.current_device()
+    with ClockSampler(dev) as clk:
+        t0 = time.perf_counter()
+        ep.ep_step_batch(handles, K)
+        t_batch = time.perf_counter() - t0
+    value = float(Ns.sum()) * K / t_batch
+    # the same instances, one after the other, each on its own graph
+    K2 = max(1, K // 4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in insts:
+        i.step(K2)
+    t_seq = time.perf_counter() - t0
+    seq = float(Ns.sum()) * K2 / t_seq
+    st = [i.stats() for i in insts]
+    models = [p["model"] for p in probs]
+    for i in insts:
+        i.close()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W,
+            "ms_per_step": 1e3 * t_batch / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS["c3"], "instances": len(insts), "nodes_total": int(Ns.sum()),
+                       "nodes_min": int(Ns.min()), "nodes_max": int(Ns.max()),
+                       "ttp06": int(sum(m == I.TTP06 for m in models)), "bo": int(sum(m == I.BO for m in models)),
+                       "l2": "working set > 50x L2, no flush; host clock around the synchronous batched call",
+                       "precision": "FP32 inner CG, float-float refinement"},
+            "latency_ms": {"batch_step": 1e3 * t_batch / K, "what": "one IMEX step of all instances"},
+            "unbatched": {"value": seq, "unit": UNIT, "steps": K2,
+                          "what": "the same instances stepped one after the other (ep_step each)"},
+            "create_s": t_create, "sweeps_last_step_max": max(s["sweeps"] for s in st),
+            "relres_max": max(s["relres"] for s in st), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """C5, scaled down: a Poisson stream of requests (sizes log-uniform,
+    slab or shell, BO or TTP06), admitted by device footprint into a budget
+    of 80 % of free memory, continuously batched; time to result p50/p99 and
+    aggregate DoF-steps/s.  The request count, sizes and durations are
+    scaled so the run takes about a minute (the full stream of 2000 requests
+    up to 2.2M nodes and 600 ms is hours of GPU time)."""
+    import numpy as np
+    torch = _gpu_setup()
+    from paper_2308_01651_gb300 import ep, serve
+    from paper_2308_01651_gb300 import inputs as I
+
+    g = I.rng(5)
+    n_req = args.requests
+    mix = serve.request_mix(n_req, g, n_lo=1.0e4, n_hi=4.0e5, t_lo=10.0, t_hi=30.0)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    # arrival rate: about 70 % of the pilot throughput's request capacity
+    work = sum(p["mesh"]["xyz"].shape[0] * k for p, k in mix)
+    pilot = 1.0e9  # DoF-steps/s, conservative
+    rate = 0.7 * n_req / (work / pilot)
+    arrivals = serve.poisson_arrivals(n_req, rate, g)
+    reqs = [serve.Request(rid=i, prob=p, steps=k, arrival=float(a)) for i, ((p, k), a) in enumerate(zip(mix, arrivals))]
+    srv = serve.Server(budget, max_slots=64, chunk=20)
+    dev = torch.cuda.current_device()
+    with ClockSampler(dev) as clk:
+        srv.run(reqs)
+    sm = srv.summary()
+    line = {"metric": METRIC, "value": sm["dof_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": int(sum(k for _, k in mix)), "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS["c5"], "requests": n_req, "nodes": "log-uniform 1e4-4e5",
+                       "duration_ms": "uniform 10-30", "arrival_rate_per_s": rate,
+                       "memory_budget_bytes": budget, "chunk_steps": srv.chunk},
+            "latency_ms": {"p50": 1e3 * sm["time_to_result_s"]["p50"], "p99": 1e3 * sm["time_to_result_s"]["p99"],
+                           "what": "time to result: arrival to activation times read back"},
+            "serving": sm, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -453,10 +572,19 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--op32", default="auto", choices=["auto", "mf", "stencil"],
-                    help="FP32 inner operator (auto: matrix-free on slabs)")
+                    help="FP32 inner operator (auto: the faster one on slabs, by a create-time autotune)")
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
+                    help="c2: the 442k-node slab (default, the headline line); c4: the 2.19M-node shell; "
+                         "c3: 96 slabs stepped as one batch; c5: a serving run")
+    ap.add_argument("--batch-count", type=int, default=96)
+    ap.add_argument("--requests", type=int, default=48)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c3":
+        run_batch(args)
+    elif args.workload == "c5":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -131,8 +131,11 @@ typedef struct {
 /* Solver options.  dt > 0 (ms); bdf_order 1 or 2 (order 2 takes a BDF1 first
  * step); tol: relative FP64 residual ||b - A u||_2 <= tol ||b||_2 (0 ->
  * 1e-12 for FP64, 1e-10 for FP32_REFINED); max_iter: CG iterations (FP64) or
- * inner iterations per refinement sweep (0 -> 1000 / 200); inner_tol:
- * relative FP32 inner residual (0 -> 1e-4); max_sweeps: refinement sweeps
+ * inner iterations per refinement sweep (0 -> 1000 / 200); inner_tol: the
+ * FP32 inner solve of a sweep stops once its residual is below 0.9 tol ||b||
+ * (enough for that sweep to end the refinement) or below inner_tol times its
+ * initial residual, whichever comes first (0 -> 1e-6, about the float
+ * limit); max_sweeps: refinement sweeps
  * (0 -> 8); op32: FP32 inner operator; cuda_stream: a cudaStream_t to order
  * the instance's work on, or NULL for a stream the library creates. */
 typedef struct {

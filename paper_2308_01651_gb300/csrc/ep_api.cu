@@ -576,7 +576,7 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     h.op32 = z.op32;
     const bool ref = h.prec == EP_PREC_FP32_REFINED;
     h.tol = opts->tol > 0 ? opts->tol : (ref ? 1e-10 : 1e-12);
-    h.inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-4;
+    h.inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-6;
     h.max_iter = opts->max_iter > 0 ? opts->max_iter : (ref ? 200 : 1000);
     h.max_sweeps = opts->max_sweeps > 0 ? opts->max_sweeps : 8;
 

@@ -104,6 +104,10 @@ struct Dev {
     double *z64, *q64, *pa64, *pb64;
     double rz, pq, alpha, beta, rr, rr0, bb, relres;
     double tol, inner_tol;
+    // the inner solve's stop on r32 . r32: below (0.9 tol ||b||)^2, enough
+    // for the sweep to end the refinement, or below inner_tol^2 times its
+    // initial value (the float floor), whichever is larger
+    double inner_stop;
     int max_iter, max_sweeps;
     int it, it_total, sweeps;
     int pswap;                  // 0: p_old = pa, p_new = pb; 1: swapped

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_update32(Dev* __restrict__ Dp,
         D.it_total += 1;
         D.pswap ^= 1;
         const bool nan = !(tot[1] == tot[1]);
-        const bool conv = !nan && tot[1] <= D.inner_tol * D.inner_tol * D.rr0;
+        const bool conv = !nan && tot[1] <= D.inner_stop;
         if (nan && D.status == EP_OK) D.status = EP_ENAN;
         set_cond(graph ? D.h_inner : 0ull, &D.f_inner, (!conv && !nan && D.it < D.max_iter) ? 1u : 0u);
     });

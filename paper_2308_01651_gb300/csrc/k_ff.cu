@@ -120,6 +120,12 @@ __global__ void __launch_bounds__(kStThreads) k_rhs_ff(Batch B, int graph) {
         D.beta = 0.0;
         D.rz = t[2];
         D.rr0 = t[3];
+        {
+            const double ns2 = (double)ns * (double)ns;
+            const double target = 0.81 * D.tol * D.tol * (D.bb / ns2);
+            const double floor2 = D.inner_tol * D.inner_tol * t[3];
+            D.inner_stop = target > floor2 ? target : floor2;
+        }
         D.rr = t[3];
         if (FIRST) {
             D.sweeps = 0;

@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg32_stencil(Batch B) {
                 const float gam = tt[0], rr = tt[2];
                 sc_gam = gam;
                 sc_rr = rr;
-                if (first) sc_stop = (float)(D.inner_tol * D.inner_tol) * rr;
+                if (first) sc_stop = (float)D.inner_stop;
                 const bool nan = !(tt[0] == tt[0] && tt[1] == tt[1] && tt[2] == tt[2]);
                 sc_nan = nan ? 1 : 0;
                 const int done = (nan || rr <= sc_stop || sc_it >= D.max_iter) ? 1 : 0;

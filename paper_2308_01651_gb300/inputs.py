@@ -243,6 +243,18 @@ def shell_ttp06(nt=20, nphi=400, nlong=260, T=500.0, dt=0.05, bdf=2):
     return p
 
 
+def as_bo(prob, amp=1.0, dur=2.0):
+    """The same geometry, fibres, conductivities and stimulated nodes with the
+    Bueno-Orovio model (amplitude in its units per ms)."""
+    pulses = [dict(p, amp=amp, dur=dur) for p in prob["pulses"]]
+    q = problem(prob["mesh"], prob["f0"], prob["s0"], prob["cond"], BO, prob["dt"], prob["bdf"], prob["T"],
+                pulses, prob["masks"], name=prob["name"] + "_bo")
+    for k in ("geo",):
+        if k in prob:
+            q[k] = prob[k]
+    return q
+
+
 def batch_slabs(count=96, n_lo=2.0e4, n_hi=4.0e5, T=300.0, dt=0.05, seed_offset=2, h=0.01):
     """Uneven batch of slabs: node counts log-uniform in [n_lo, n_hi], aspect
     nx/ny uniform in [1, 4] with nz = ny, h = 0.01 cm, model Bernoulli(1/2)

@@ -36,6 +36,8 @@ void launch_correct_ff(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_ionic_batch(const Batch& B, int model, int grid, cudaStream_t s);
 void launch_rhs_ff_batch(const Batch& B, int first, int graph, int grid, cudaStream_t s);
 void launch_correct_ff_batch(const Batch& B, int grid, cudaStream_t s);
+void launch_resid_np(Dev* d, const Dev& h, int graph, int grid, cudaStream_t s);
+void launch_resid_np_batch(const Batch& B, int graph, int grid, cudaStream_t s);
 void launch_finish_batch(const Batch& B, int grid, cudaStream_t s);
 cudaError_t launch_pcg32_batch(const Batch& B, int grid, cudaStream_t s);
 void launch_batch_cond(Dev* const* devs, int n, const unsigned long long* h, cudaStream_t s);
@@ -383,9 +385,8 @@ ep_status build_graph(ep_instance* I) {
         C.chk(add_while(s, &h_outer, &body));
         if (C.err == cudaSuccess) {
             C.chk(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-            C.chk(epk::launch_pcg32(I->d, h, I->grid_pcg, s2));
-            epk::launch_correct_ff(I->d, h, I->grid_nodes, s2);
-            epk::launch_rhs_ff(I->d, h, 0, 1, I->grid_tiles, s2);
+            C.chk(epk::launch_pcg32(I->d, h, I->grid_pcg, s2));  // ends with u += delta
+            epk::launch_resid_np(I->d, h, 1, I->grid_nodes, s2);
             C.chk(cudaStreamEndCapture(s2, &body));
         }
     } else {
@@ -401,7 +402,7 @@ ep_status build_graph(ep_instance* I) {
                 C.chk(cudaStreamEndCapture(s3, &body2));
             }
             epk::launch_correct_ff(I->d, h, I->grid_nodes, s2);
-            epk::launch_rhs_ff(I->d, h, 0, 1, I->grid_tiles, s2);
+            epk::launch_resid_np(I->d, h, 1, I->grid_nodes, s2);
             C.chk(cudaStreamEndCapture(s2, &body));
         }
     }
@@ -476,8 +477,10 @@ ep_status step_host(ep_instance* I) {
                 CUDA_TRY(cudaGetLastError());
                 CUDA_TRY(flag(&d->f_inner, &fi));
             }
-            timed(I, K_CORRECT, [&] { epk::launch_correct_ff(d, h, I->grid_nodes, s); });
-            timed(I, K_RESID, [&] { epk::launch_rhs_ff(d, h, 0, 0, I->grid_tiles, s); });
+            // the persistent solver applies its correction itself
+            if (h.op32 != EP_OP_STENCIL)
+                timed(I, K_CORRECT, [&] { epk::launch_correct_ff(d, h, I->grid_nodes, s); });
+            timed(I, K_RESID, [&] { epk::launch_resid_np(d, h, 0, I->grid_nodes, s); });
             CUDA_TRY(cudaGetLastError());
             CUDA_TRY(flag(&d->f_outer, &f));
         }
@@ -979,9 +982,8 @@ ep_status build_plan(BatchPlan* P) {
     C.chk(add_while(s, &hc, &body));
     if (C.err == cudaSuccess) {
         C.chk(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        C.chk(epk::launch_pcg32_batch(Bp, s_pcg.back(), s2));
-        epk::launch_correct_ff_batch(Bn, s_nodes.back(), s2);
-        epk::launch_rhs_ff_batch(Bt, 0, 0, s_tiles.back(), s2);
+        C.chk(epk::launch_pcg32_batch(Bp, s_pcg.back(), s2));  // ends with u += delta
+        epk::launch_resid_np_batch(Bn, 0, s_nodes.back(), s2);
         epk::launch_batch_cond(dall, n, dh, s2);
         C.chk(cudaStreamEndCapture(s2, &body));
     }
@@ -1463,12 +1465,12 @@ ep_status ep_residual_norm_noalloc(const ep_instance* I, double* relres_out) {
     if (!I || !relres_out) return fail(EP_EINVAL, "NULL argument");
     if (I->h.prec != EP_PREC_FP32_REFINED)
         return fail(EP_EUNSUPPORTED, "the allocation-free residual serves FP32_REFINED instances");
-    if (I->grid_tiles > epk::noalloc_max_blocks())
-        return fail(EP_EINVAL, "the residual of this instance needs " + std::to_string(I->grid_tiles) +
+    if (I->grid_nodes > epk::noalloc_max_blocks())
+        return fail(EP_EINVAL, "the residual of this instance needs " + std::to_string(I->grid_nodes) +
                                    " thread blocks; the allocation-free path holds partial sums for at most " +
                                    std::to_string(epk::noalloc_max_blocks()));
     double sums[2] = {0.0, 0.0};
-    CUDA_TRY(epk::residual_norm_noalloc(I->d, I->grid_tiles, I->stream, sums));
+    CUDA_TRY(epk::residual_norm_noalloc(I->d, I->grid_nodes, I->stream, sums));
     *relres_out = sums[0] > 0.0 ? std::sqrt(sums[1] / sums[0]) : std::sqrt(sums[1]);
     return EP_OK;
 }

@@ -86,6 +86,27 @@ __host__ __device__ inline int st_tiles(const Dev& h) {
     return ((h.NX + kStTx - 1) / kStTx) * ((h.NY + kStTy - 1) / kStTy) * ((h.NZ + kStTz - 1) / kStTz);
 }
 
+// index offsets of the 27 neighbours of node n (di, dj, dk in -1..1), from
+// its boundary flags; a neighbour outside the mesh maps to a valid node whose
+// coupling is 0
+struct NbrOff {
+    int x[3], y[3], z[3];
+};
+
+__device__ __forceinline__ NbrOff nbr_offsets(int nx, int nxy, int wrap, unsigned int f) {
+    NbrOff o;
+    o.x[0] = (f & 1u) ? 0 : -1;
+    o.x[1] = 0;
+    o.x[2] = (f & 2u) ? 0 : 1;
+    o.y[0] = (f & 4u) ? wrap : -nx;
+    o.y[1] = 0;
+    o.y[2] = (f & 8u) ? -wrap : nx;
+    o.z[0] = (f & 16u) ? 0 : -nxy;
+    o.z[1] = 0;
+    o.z[2] = (f & 32u) ? 0 : nxy;
+    return o;
+}
+
 // ---- node-major full couplings -------------------------------------------
 // The refined solver keeps all 27 couplings of every node in 7 groups of
 // float4 ([7][N], group g holds offsets t = 4g .. 4g+3; t = 27 is padding
@@ -133,6 +154,30 @@ __device__ __forceinline__ void row_ff(const float4* __restrict__ chi, const flo
         if (g < kGroups - 1) {
             d = t_dh(4 * g + 3);
             ff_mac(a.w, b.w, xh[h + d], xl[h + d], sh, sl);
+        }
+    }
+    ff_normalize(sh, sl);
+}
+
+// float-float row of node n with neighbour values read from global memory
+// (node-parallel kernels): (sh + sl) = sum_t (chi + clo)(t) (xh + xl)(n +
+// off(t)), t = 0..26 in order -- the same terms in the same order as row_ff
+__device__ __forceinline__ void row_ff_np(const float4* __restrict__ chi, const float4* __restrict__ clo,
+                                          size_t N, const float* __restrict__ xh, const float* __restrict__ xl,
+                                          int n, const NbrOff& o, float& sh, float& sl) {
+    sh = 0.f;
+    sl = 0.f;
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+        const float4 a = chi[(size_t)g * N + n];
+        const float4 b = clo[(size_t)g * N + n];
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int t = 4 * g + q;
+            if (t >= 27) continue;
+            const int m = n + o.x[t % 3] + o.y[(t / 3) % 3] + o.z[t / 9];
+            ff_mac(av[q], bv[q], xh[m], xl[m], sh, sl);
         }
     }
     ff_normalize(sh, sl);

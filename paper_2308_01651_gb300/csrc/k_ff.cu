@@ -16,6 +16,7 @@ namespace epk {
 
 void launch_rhs_ff_batch(const Batch& B, int first, int graph, int grid, cudaStream_t s);
 void launch_correct_ff_batch(const Batch& B, int grid, cudaStream_t s);
+void launch_resid_np_batch(const Batch& B, int graph, int grid, cudaStream_t s);
 
 // stage the float-float pair (ah, al) of the tile plus halo
 __device__ __forceinline__ void stage_ff(const Dev& D, const TileGeo& g, int* sidx, const float* ah,
@@ -26,6 +27,45 @@ __device__ __forceinline__ void stage_ff(const Dev& D, const TileGeo& g, int* si
         const int n = sidx[h];
         sl[h] = n >= 0 ? al[n] : 0.f;
     }
+}
+
+// Totals of a right-hand-side or residual pass (t: (ns b)^2, (ns r)^2,
+// r32 . z32, r32 . r32): convergence, the inner solver's starting scalars and
+// stop, the loop decisions.  Run by one thread after the grid's reduction.
+__device__ void rhs_finish(Dev& D, const double* t, bool FIRST, int graph, float ns) {
+    // ||b||^2 as this pass summed it, so that r and b of the ratio come from
+    // the same pass
+    D.bb = t[0];
+    const double rr = t[1], bb = D.bb;
+    const bool nan = !(rr == rr);
+    const bool conv = !nan && (rr <= D.tol * D.tol * bb);
+    D.relres = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+    if (nan && D.status == EP_OK) D.status = EP_ENAN;
+    D.it = 0;
+    D.beta = 0.0;
+    D.rz = t[2];
+    D.rr0 = t[3];
+    {
+        const double ns2 = (double)ns * (double)ns;
+        const double target = 0.81 * D.tol * D.tol * (D.bb / ns2);
+        const double floor2 = D.inner_tol * D.inner_tol * t[3];
+        D.inner_stop = target > floor2 ? target : floor2;
+    }
+    D.rr = t[3];
+    if (FIRST) {
+        D.sweeps = 0;
+        D.it_total = 0;
+        // the persistent solver's barrier counter starts the step at 0
+        *reinterpret_cast<unsigned long long*>(D.counter + CNT_BAR) = 0ull;
+    } else {
+        D.sweeps += 1;
+        if (!conv && D.sweeps >= D.max_sweeps && D.status == EP_OK) D.status = EP_ENOCONV;
+    }
+    set_cond(graph ? D.h_outer : 0ull, &D.f_outer, (!conv && !nan && D.sweeps < D.max_sweeps) ? 1u : 0u);
+    // the next inner loop starts enabled (with the per-iteration inner
+    // loop its handle belongs to the refinement body, where this runs)
+    if (FIRST) D.f_inner = 1;
+    else set_cond(graph ? D.h_inner : 0ull, &D.f_inner, 1u);
 }
 
 // FIRST: b = M v and r = b - A u_EXT, where A u_EXT comes from the stored
@@ -109,39 +149,48 @@ __global__ void __launch_bounds__(kStThreads) k_rhs_ff(Batch B, int graph) {
             vf[3] = fmaf(r32, r32, vf[3]);
         });
     }
-    grid_reduce<4, 0>(vf, none, D.partial, D.counter + CNT_RHS, S.blk, S.nblk, [&](double* t) {
-        if (FIRST) D.bb = t[0];
-        const double rr = t[1], bb = D.bb;
-        const bool nan = !(rr == rr);
-        const bool conv = !nan && (rr <= D.tol * D.tol * bb);
-        D.relres = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
-        if (nan && D.status == EP_OK) D.status = EP_ENAN;
-        D.it = 0;
-        D.beta = 0.0;
-        D.rz = t[2];
-        D.rr0 = t[3];
-        {
-            const double ns2 = (double)ns * (double)ns;
-            const double target = 0.81 * D.tol * D.tol * (D.bb / ns2);
-            const double floor2 = D.inner_tol * D.inner_tol * t[3];
-            D.inner_stop = target > floor2 ? target : floor2;
-        }
-        D.rr = t[3];
-        if (FIRST) {
-            D.sweeps = 0;
-            D.it_total = 0;
-            // the persistent solver's barrier counter starts the step at 0
-            *reinterpret_cast<unsigned long long*>(D.counter + CNT_BAR) = 0ull;
-        } else {
-            D.sweeps += 1;
-            if (!conv && D.sweeps >= D.max_sweeps && D.status == EP_OK) D.status = EP_ENOCONV;
-        }
-        set_cond(graph ? D.h_outer : 0ull, &D.f_outer, (!conv && !nan && D.sweeps < D.max_sweeps) ? 1u : 0u);
-        // the next inner loop starts enabled (with the per-iteration inner
-        // loop its handle belongs to the refinement body, where this runs)
-        if (FIRST) D.f_inner = 1;
-        else set_cond(graph ? D.h_inner : 0ull, &D.f_inner, 1u);
-    });
+    grid_reduce<4, 0>(vf, none, D.partial, D.counter + CNT_RHS, S.blk, S.nblk,
+                      [&](double* t) { rhs_finish(D, t, FIRST != 0, graph, ns); });
+}
+
+// Residual after a correction, node-parallel: every thread takes nodes
+// n = t, t + T, ... of its instance, reads the float-float couplings of A
+// and its 27 neighbours' u (through L1) -- no shared-memory tiles or block
+// barriers between the coefficient streams -- and writes y = A u (the step's
+// history), r = b - y and the inner solver's start (r32, u = D^-1 r32, delta
+// = 0).  Same terms, order and totals as the tiled pass.
+__global__ void __launch_bounds__(kNodeThreads) k_resid_np(Batch B, int graph) {
+    const Slot S = batch_slot(B);
+    Dev& D = *S.D;
+    if (!D.f_outer) return;
+    const int N = D.N;
+    const size_t NN = (size_t)N;
+    const float ns = D.nscale;
+    const int nx = D.NX, nxy = D.NX * D.NY, wrap = D.periodic ? D.NX * (D.NY - 1) : 0;
+    const float* __restrict__ uh = D.u_hi;
+    const float* __restrict__ ul = D.u_lo;
+    float vf[4] = {0.f, 0.f, 0.f, 0.f};
+    const double none[1] = {0.0};
+    for (int n = S.blk * blockDim.x + threadIdx.x; n < N; n += S.nblk * blockDim.x) {
+        const NbrOff o = nbr_offsets(nx, nxy, wrap, D.nflag[n]);
+        float ah, al, rh, rl;
+        row_ff_np(D.Ahi, D.Alo, NN, uh, ul, n, o, ah, al);
+        D.yc_hi[n] = ah;
+        D.yc_lo[n] = al;
+        ff_sub(D.b_hi[n], D.b_lo[n], ah, al, rh, rl);
+        const float r32 = rh;
+        const float z = D.dinv32[n] * r32;
+        D.r32[n] = r32;
+        D.z32[n] = z;
+        D.d32[n] = 0.0f;
+        const float bs = ns * D.b_hi[n], rs = ns * rh;
+        vf[0] = fmaf(bs, bs, vf[0]);
+        vf[1] = fmaf(rs, rs, vf[1]);
+        vf[2] = fmaf(r32, z, vf[2]);
+        vf[3] = fmaf(r32, r32, vf[3]);
+    }
+    grid_reduce<4, 0>(vf, none, D.partial, D.counter + CNT_RHS, S.blk, S.nblk,
+                      [&](double* t) { rhs_finish(D, t, false, graph, ns); });
 }
 
 // u += delta in float-float
@@ -166,6 +215,13 @@ void launch_rhs_ff(Dev* d, const Dev& h, int first, int graph, int grid, cudaStr
 void launch_rhs_ff_batch(const Batch& B, int first, int graph, int grid, cudaStream_t s) {
     if (first) k_rhs_ff<1><<<grid, kStThreads, 0, s>>>(B, graph);
     else k_rhs_ff<0><<<grid, kStThreads, 0, s>>>(B, graph);
+}
+
+void launch_resid_np(Dev* d, const Dev& h, int graph, int grid, cudaStream_t s) {
+    launch_resid_np_batch(single_batch(d), graph, grid, s);
+}
+void launch_resid_np_batch(const Batch& B, int graph, int grid, cudaStream_t s) {
+    k_resid_np<<<grid, kNodeThreads, 0, s>>>(B, graph);
 }
 
 void launch_correct_ff(Dev* d, const Dev& h, int grid, cudaStream_t s) {

@@ -23,10 +23,11 @@
 // the counter before its kernel runs, and calls whose work overlaps on the
 // GPU (different streams, no ordering) race on the array.
 //
-// The kernel is a variant of the refined solver's residual kernel (k_rhs_ff,
-// residual mode, float-float): same tiles, same per-thread and per-block
-// summation order, so it reproduces the solver's own residual norm; it writes
-// nothing but the scratch array.  It serves FP32_REFINED instances.
+// The kernel is a variant of the refined solver's residual kernel
+// (k_resid_np, float-float, node-parallel): same nodes per thread, same
+// per-thread and per-block summation order, so it reproduces the solver's
+// own residual norm; it writes nothing but the scratch array.  It serves
+// FP32_REFINED instances.
 #include <mutex>
 #include <string>
 
@@ -43,40 +44,30 @@ constexpr size_t kNoAllocScratchBytes = kNoAllocCounterOff + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-__global__ void __launch_bounds__(kStThreads) k_residual_norm_noalloc(const Dev* __restrict__ Dp,
-                                                                       unsigned char* scratch) {
-    __shared__ int sidx[SHN];
-    __shared__ float suh[SHN], sul[SHN];
+__global__ void __launch_bounds__(kNodeThreads) k_residual_norm_noalloc(const Dev* __restrict__ Dp,
+                                                                         unsigned char* scratch) {
     const Dev& D = *Dp;
-    const size_t N = (size_t)D.N;
+    const int N = D.N;
+    const size_t NN = (size_t)N;
     const float ns = D.nscale;
+    const int nx = D.NX, nxy = D.NX * D.NY, wrap = D.periodic ? D.NX * (D.NY - 1) : 0;
     double* partial = reinterpret_cast<double*>(scratch);
     double* total = reinterpret_cast<double*>(scratch + kNoAllocTotalOff);
     unsigned int* counter = reinterpret_cast<unsigned int*>(scratch + kNoAllocCounterOff);
     float vf[2] = {0.f, 0.f};
     const double none[1] = {0.0};
-    const int ntiles = st_tiles(D);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const TileGeo g = tile_geo(D, tile);
-        __syncthreads();
-        // the last solve's float-float iterate, now the potential level n
-        // (u_n is its sum rounded to double)
-        stage_tile<float>(D, g, sidx, suh, [&](int n, bool) { return D.uh_n[n]; });
-        for (int h = threadIdx.x; h < SHN; h += blockDim.x) {
-            const int n = sidx[h];
-            sul[h] = n >= 0 ? D.ul_n[n] : 0.f;
-        }
-        __syncthreads();
-        for_owned(D, g, [&](int h) {
-            const int n = sidx[h];
-            const float bh = D.b_hi[n], bl = D.b_lo[n];
-            float ah, al, rh, rl;
-            row_ff(D.Ahi, D.Alo, N, suh, sul, h, n, ah, al);
-            ff_sub(bh, bl, ah, al, rh, rl);
-            const float bs = ns * bh, rs = ns * rh;
-            vf[0] = fmaf(bs, bs, vf[0]);
-            vf[1] = fmaf(rs, rs, vf[1]);
-        });
+    // the last solve's float-float iterate, now the potential level n (u_n is
+    // its sum rounded to double)
+    const float* __restrict__ uh = D.uh_n;
+    const float* __restrict__ ul = D.ul_n;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+        const NbrOff o = nbr_offsets(nx, nxy, wrap, D.nflag[n]);
+        float ah, al, rh, rl;
+        row_ff_np(D.Ahi, D.Alo, NN, uh, ul, n, o, ah, al);
+        ff_sub(D.b_hi[n], D.b_lo[n], ah, al, rh, rl);
+        const float bs = ns * D.b_hi[n], rs = ns * rh;
+        vf[0] = fmaf(bs, bs, vf[0]);
+        vf[1] = fmaf(rs, rs, vf[1]);
     }
     grid_reduce<2, 0>(vf, none, partial, counter, blockIdx.x, gridDim.x, [&](double* t) {
         total[0] = t[0];
@@ -117,7 +108,7 @@ cudaError_t residual_norm_noalloc(Dev* d, int grid, cudaStream_t s, double sums[
     unsigned char* base = static_cast<unsigned char*>(scratch);
     e = cudaMemsetAsync(base + kNoAllocCounterOff, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    k_residual_norm_noalloc<<<grid, kStThreads, 0, s>>>(d, base);
+    k_residual_norm_noalloc<<<grid, kNodeThreads, 0, s>>>(d, base);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(sums, base + kNoAllocTotalOff, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);

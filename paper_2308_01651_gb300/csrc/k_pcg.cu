@@ -71,6 +71,20 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned
 
 // Block sums of NV float values (warp butterflies, then the warps' sums by
 // warp 0 in the same way), written as part[k * G + blockIdx.x].
+// u += delta (float-float) on this thread's nodes; kept out of line so that
+// its registers do not add to the solver loop's
+__device__ __noinline__ void correct_ff_nodes(const Dev& D, int t0, int T) {
+    float* __restrict__ uh = D.u_hi;
+    float* __restrict__ ul = D.u_lo;
+    const float* __restrict__ x = D.d32;
+    for (int n = t0; n < D.N; n += T) {
+        float h = uh[n], l = ul[n];
+        ff_add_f(h, l, x[n], h, l);
+        uh[n] = h;
+        ul[n] = l;
+    }
+}
+
 template <int NV>
 __device__ __forceinline__ void publish(const float (&v)[NV], float* part, int G, int blk) {
     __shared__ float sh[NV][kMaxBlock / 32];
@@ -102,27 +116,6 @@ __device__ __forceinline__ void gather(const float* part, int G, float (&tot)[NV
         for (int i = lane; i < G; i += 32) acc += __ldcg(&part[(size_t)k * G + i]);
         tot[k] = warp_sum(acc);
     }
-}
-
-// index offsets of the 27 neighbours of node n (di, dj, dk in -1..1), from
-// its boundary flags; a neighbour outside the mesh maps to a valid node whose
-// coupling is 0
-struct NbrOff {
-    int x[3], y[3], z[3];
-};
-
-__device__ __forceinline__ NbrOff nbr_offsets(int nx, int nxy, int wrap, unsigned int f) {
-    NbrOff o;
-    o.x[0] = (f & 1u) ? 0 : -1;
-    o.x[1] = 0;
-    o.x[2] = (f & 2u) ? 0 : 1;
-    o.y[0] = (f & 4u) ? wrap : -nx;
-    o.y[1] = 0;
-    o.y[2] = (f & 8u) ? -wrap : nx;
-    o.z[0] = (f & 16u) ? 0 : -nxy;
-    o.z[1] = 0;
-    o.z[2] = (f & 32u) ? 0 : nxy;
-    return o;
 }
 
 __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg32_stencil(Batch B) {
@@ -230,6 +223,9 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg32_stencil(Batch B) {
         beta = sc_beta;
         first = false;
     }
+    // the sweep's correction u += delta (float-float), node by node: no
+    // neighbour is involved, so it needs no barrier and no launch of its own
+    correct_ff_nodes(D, t0, T);
     if (S.blk == 0 && threadIdx.x == 0) {
         D.rz = sc_gam;
         D.rr = sc_rr;

@@ -81,7 +81,8 @@ struct Dev {
     float *uh_n, *ul_n, *uh_m, *ul_m;
     float* bestf;
     // A u of the solve's iterate (float-float): the current step's (written by
-    // every residual evaluation), step n's and step n-1's.  hist counts the
+    // every residual evaluation, the first one included), step n's and step
+    // n-1's.  hist counts the
     // valid past levels; with enough of them A u_EXT is their BDF
     // extrapolation instead of an operator apply.
     float *yc_hi, *yc_lo, *yn_hi, *yn_lo, *ym_hi, *ym_lo;
@@ -265,6 +266,51 @@ __device__ __forceinline__ Slot batch_slot(const Batch& B) {
 }
 
 inline Batch single_batch(Dev* d) { return Batch{d, nullptr, nullptr, 1}; }
+
+// End of a step (one thread, after the step's last reduction): rotation of
+// the time levels by pointer swaps (potentials, ionic states; refined: the
+// float-float potential levels and the A u history), the step counter and
+// the per-step statistics.
+__device__ __forceinline__ void end_of_step(Dev& D) {
+    double* t = D.u_nm1;
+    D.u_nm1 = D.u_n;
+    D.u_n = D.u_new;
+    D.u_new = t;
+    float* g = D.g32_nm1;
+    D.g32_nm1 = D.g32_n;
+    D.g32_n = g;
+    double* c = D.s64_nm1;
+    D.s64_nm1 = D.s64_n;
+    D.s64_n = c;
+    if (D.u_hi) {
+        // the iterate becomes level n, level n becomes n-1, and the old
+        // n-1 buffers take the next step's iterate
+        float* ph = D.uh_m;
+        float* pl = D.ul_m;
+        D.uh_m = D.uh_n;
+        D.ul_m = D.ul_n;
+        D.uh_n = D.u_hi;
+        D.ul_n = D.u_lo;
+        D.u_hi = ph;
+        D.u_lo = pl;
+        // A u of the new solution becomes step n's; the oldest level is
+        // reused for the next step's residuals
+        float* yh = D.ym_hi;
+        float* yl = D.ym_lo;
+        D.ym_hi = D.yn_hi;
+        D.ym_lo = D.yn_lo;
+        D.yn_hi = D.yc_hi;
+        D.yn_lo = D.yc_lo;
+        D.yc_hi = yh;
+        D.yc_lo = yl;
+        D.hist = D.hist < 2 ? D.hist + 1 : 2;
+    }
+    D.step += 1;
+    D.done_step = D.step;
+    D.last_iters = D.prec == EP_PREC_FP32_REFINED ? D.it_total : D.it;
+    D.last_sweeps = D.prec == EP_PREC_FP32_REFINED ? D.sweeps : 0;
+    D.last_relres = D.relres;
+}
 
 // Node (i, j, k) of index n, and the neighbour at offset slot t (0..26);
 // returns -1 where the neighbour does not exist.

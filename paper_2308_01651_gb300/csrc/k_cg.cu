@@ -67,77 +67,53 @@ __global__ void __launch_bounds__(kNodeThreads) k_update32(Dev* __restrict__ Dp,
     });
 }
 
-// Activation update, non-finite check, rotation of the time levels.
+// FP64 path: activation update, non-finite check, rotation of the time
+// levels.
 __global__ void __launch_bounds__(kNodeThreads) k_finish(Batch B) {
     const Slot S = batch_slot(B);
     Dev& D = *S.D;
     const double t_new = (double)(D.step + 1) * D.dt;
     float v[1] = {0.f};
     const double none[1] = {0.0};
-    const bool ff = D.u_hi != nullptr;  // refined: the iterate is float-float
     for (int n = S.blk * blockDim.x + threadIdx.x; n < D.N; n += S.nblk * blockDim.x) {
-        if (ff) {
-            // slope and checks in float from the pairs; the only double
-            // operation is the rounding of the new potential for u_n
-            const float h1 = D.u_hi[n], l1 = D.u_lo[n];
-            const float s = (h1 - D.uh_n[n]) + (l1 - D.ul_n[n]);
-            D.u_new[n] = ff_to_double(h1, l1);
-            if (!isfinite(h1)) v[0] += 1.f;
-            if (s > D.bestf[n]) {
-                D.bestf[n] = s;
-                D.at[n] = t_new;
-            }
-        } else {
-            const double un = D.u_new[n];
-            const double s = un - D.u_n[n];
-            if (!isfinite(un)) v[0] += 1.f;
-            if (s > D.best[n]) {
-                D.best[n] = s;
-                D.at[n] = t_new;
-            }
+        const double un = D.u_new[n];
+        const double s = un - D.u_n[n];
+        if (!isfinite(un)) v[0] += 1.f;
+        if (s > D.best[n]) {
+            D.best[n] = s;
+            D.at[n] = t_new;
         }
     }
     grid_reduce<1, 0>(v, none, D.partial, D.counter + CNT_FINISH, S.blk, S.nblk, [&](double* tot) {
         if (tot[0] > 0.0 && D.status == EP_OK) D.status = EP_ENAN;
-        double* t = D.u_nm1;
-        D.u_nm1 = D.u_n;
-        D.u_n = D.u_new;
-        D.u_new = t;
-        float* g = D.g32_nm1;
-        D.g32_nm1 = D.g32_n;
-        D.g32_n = g;
-        double* c = D.s64_nm1;
-        D.s64_nm1 = D.s64_n;
-        D.s64_n = c;
-        if (ff) {
-            // the iterate becomes level n, level n becomes n-1, and the old
-            // n-1 buffers take the next step's iterate
-            float* ph = D.uh_m;
-            float* pl = D.ul_m;
-            D.uh_m = D.uh_n;
-            D.ul_m = D.ul_n;
-            D.uh_n = D.u_hi;
-            D.ul_n = D.u_lo;
-            D.u_hi = ph;
-            D.u_lo = pl;
-            // A u of the new solution becomes step n's; the oldest level is
-            // reused for the next step's residuals
-            float* yh = D.ym_hi;
-            float* yl = D.ym_lo;
-            D.ym_hi = D.yn_hi;
-            D.ym_lo = D.yn_lo;
-            D.yn_hi = D.yc_hi;
-            D.yn_lo = D.yc_lo;
-            D.yc_hi = yh;
-            D.yc_lo = yl;
-            D.hist = D.hist < 2 ? D.hist + 1 : 2;
-        }
-        D.step += 1;
-        D.done_step = D.step;
-        D.last_iters = D.prec == EP_PREC_FP32_REFINED ? D.it_total : D.it;
-        D.last_sweeps = D.prec == EP_PREC_FP32_REFINED ? D.sweeps : 0;
-        D.last_relres = D.relres;
+        end_of_step(D);
     });
+}
+
+// Refined path: the refinement's last residual pass has already rotated the
+// time levels (end_of_step), so the new potential is level n and the old one
+// level n-1.  Per node: the activation slope in float from the pairs, the
+// new potential rounded to double for u_n.  A non-finite potential has
+// already made that residual NaN (EP_ENAN); no reduction is needed here.
+__global__ void __launch_bounds__(kNodeThreads) k_finish_ff(Batch B) {
+    const Slot S = batch_slot(B);
+    Dev& D = *S.D;
+    const double t_new = (double)D.step * D.dt;
+    const float* __restrict__ h1p = D.uh_n;
+    const float* __restrict__ l1p = D.ul_n;
+    const float* __restrict__ h0p = D.uh_m;
+    const float* __restrict__ l0p = D.ul_m;
+    double* __restrict__ un = D.u_n;
+    float* __restrict__ best = D.bestf;
+    for (int n = S.blk * blockDim.x + threadIdx.x; n < D.N; n += S.nblk * blockDim.x) {
+        const float h1 = h1p[n], l1 = l1p[n];
+        const float s = (h1 - h0p[n]) + (l1 - l0p[n]);
+        un[n] = ff_to_double(h1, l1);
+        if (s > best[n]) {
+            best[n] = s;
+            D.at[n] = t_new;
+        }
+    }
 }
 
 // Loop condition of a batched refinement sweep: another sweep while any
@@ -159,8 +135,10 @@ void launch_update32(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s) 
     k_update32<<<grid, kNodeThreads, 0, s>>>(d, graph);
 }
 void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s) {
-    k_finish<<<grid, kNodeThreads, 0, s>>>(single_batch(d));
+    if (h.prec == EP_PREC_FP32_REFINED) k_finish_ff<<<grid, kNodeThreads, 0, s>>>(single_batch(d));
+    else k_finish<<<grid, kNodeThreads, 0, s>>>(single_batch(d));
 }
-void launch_finish_batch(const Batch& B, int grid, cudaStream_t s) { k_finish<<<grid, kNodeThreads, 0, s>>>(B); }
+// refined instances
+void launch_finish_batch(const Batch& B, int grid, cudaStream_t s) { k_finish_ff<<<grid, kNodeThreads, 0, s>>>(B); }
 
 }  // namespace epk

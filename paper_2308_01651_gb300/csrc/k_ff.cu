@@ -61,7 +61,11 @@ __device__ void rhs_finish(Dev& D, const double* t, bool FIRST, int graph, float
         D.sweeps += 1;
         if (!conv && D.sweeps >= D.max_sweeps && D.status == EP_OK) D.status = EP_ENOCONV;
     }
-    set_cond(graph ? D.h_outer : 0ull, &D.f_outer, (!conv && !nan && D.sweeps < D.max_sweeps) ? 1u : 0u);
+    const bool more = !conv && !nan && D.sweeps < D.max_sweeps;
+    set_cond(graph ? D.h_outer : 0ull, &D.f_outer, more ? 1u : 0u);
+    // the step's refinement is over: rotate the time levels now (the
+    // finishing kernel then works on the rotated levels)
+    if (!more) end_of_step(D);
     // the next inner loop starts enabled (with the per-iteration inner
     // loop its handle belongs to the refinement body, where this runs)
     if (FIRST) D.f_inner = 1;
@@ -128,6 +132,10 @@ __global__ void __launch_bounds__(kStThreads) k_rhs_ff(Batch B, int graph) {
                 } else {
                     row_ff(D.Ahi, D.Alo, N, suh, sul, h, n, ah, al);
                 }
+                // A u_EXT is the step's A u if this residual already meets
+                // the tolerance (a sweep overwrites it otherwise)
+                D.yc_hi[n] = ah;
+                D.yc_lo[n] = al;
             } else {
                 bh = D.b_hi[n];
                 bl = D.b_lo[n];

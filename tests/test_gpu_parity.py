@@ -248,3 +248,26 @@ def test_graph_and_host_driven_stepping_agree():
         d = ep.Instance(prob, precision=prec)
         d.step(15)
         assert np.array_equal(c.save(), d.save())
+
+
+def test_steps_converging_at_first_residual_keep_history_exact():
+    """With a loose tolerance many steps meet it at their first residual (no
+    sweep), whose A u_EXT comes from the A u history; such a step must record
+    A u_EXT as its own A u, or the next steps' history would be stale.  After
+    every such step the relative residual the solver reports (from the
+    history) must equal the one recomputed from scratch (b - A u_n with the
+    operator, ep_residual_norm_noalloc) to the float-float accuracy."""
+    prob = small_ttp06(nx=30, ny=8, nz=6, T=10.0)
+    inst = ep.Instance(prob, precision=REF, tol=1e-5)
+    zero_sweeps = 0
+    try:
+        for _ in range(80):
+            inst.step(1)
+            st = inst.stats()
+            if st["sweeps"] == 0:
+                zero_sweeps += 1
+                exact = ep.ep_residual_norm_noalloc(inst.h)
+                assert abs(exact - st["relres"]) <= 1e-12, (exact, st["relres"])
+    finally:
+        inst.close()
+    assert zero_sweeps >= 5, zero_sweeps

@@ -81,6 +81,12 @@ typedef struct {
     double L[3];
     const double* xyz;
     int64_t n_nodes;
+    /* Subdomain label per element (Sec. 1.1.2: a labelled partition of the
+     * domain), or NULL for one region.  Element (i, j, k) -- the hexahedron
+     * spanning nodes i..i+1, j..j+1, k..k+1, j wrapping on the shell -- is
+     * entry i + nx (j + ny k); n_elems = nx * ny * nz bytes, each below
+     * ep_conductivities.n_regions. */
+    const uint8_t* region;
 } ep_mesh;
 
 /* Nodal fibre (f0) and sheet (s0) directions, n_nodes x 3 each (Eq. (3)).
@@ -95,11 +101,26 @@ typedef struct {
 /* Conductivities (Eq. (3)).  If is_D != 0, sigma_* are diffusivities in
  * cm^2/ms; otherwise they are conductivities in mS/cm and the library
  * rescales D = sigma / (chi_m C_m) (Sec. 1.1.2) with chi_m in 1/cm and C_m in
- * uF/cm^2.  All must be positive and finite. */
+ * uF/cm^2.  All must be positive and finite.
+ *
+ * With a region label on the mesh, region r uses region_sigma[r] (l, t, n;
+ * same units) instead of sigma_*, for r < n_regions (1..EP_MAX_REGIONS); the
+ * bulk values are then unused.  non_conductive[r] != 0 excludes region r
+ * from the simulation, a conduction block such as a scar (Sec. 1.1.2): its
+ * elements contribute to neither M nor K, and a node all of whose elements
+ * are excluded is inactive -- ionic model off, states held, no applied
+ * current, its potential kept.  Fluxes across interfaces between conductive
+ * regions are continuous (the Galerkin form with piecewise D).  Regions need
+ * the stencil FP32 operator in the refined path (EP_OP_MATRIX_FREE gets
+ * EP_EUNSUPPORTED; EP_OP_AUTO picks the stencil). */
+#define EP_MAX_REGIONS 8
 typedef struct {
     double sigma_l, sigma_t, sigma_n;
     double chi_m, Cm;
     int32_t is_D;
+    int32_t n_regions;
+    double region_sigma[EP_MAX_REGIONS][3];
+    uint8_t non_conductive[EP_MAX_REGIONS];
 } ep_conductivities;
 
 /* Ionic model (Sec. 1.1.1): Bueno-Orovio minimal model (epicardial
@@ -219,7 +240,8 @@ ep_status ep_save_state(const ep_instance* inst, void* buf, size_t bytes);
 ep_status ep_load_state(ep_instance* inst, const void* buf, size_t bytes);
 
 /* Device bytes an instance of this mesh, model and options would hold;
- * 0 if the arguments are invalid. */
+ * 0 if the arguments are invalid.  With a region label it assumes some
+ * region may be non-conductive (an upper bound otherwise). */
 size_t ep_footprint_bytes(const ep_mesh* mesh, const ep_ionic_model* ionic,
                           const ep_options* opts);
 

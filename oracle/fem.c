@@ -115,6 +115,19 @@ static int64_t find_col(const or_csr* A, int64_t row, int64_t col) {
 int or_assemble(int64_t nn, int64_t ne, const double* xyz, const int32_t* hex,
                 const double* f0, const double* s0, double dl, double dt_,
                 double dn, or_csr* A) {
+    const double rdiff[3] = {dl, dt_, dn};
+    const uint8_t excluded[1] = {0};
+    return or_assemble_regions(nn, ne, xyz, hex, f0, s0, NULL, 1, rdiff, excluded, A, NULL);
+}
+
+int or_assemble_regions(int64_t nn, int64_t ne, const double* xyz,
+                        const int32_t* hex, const double* f0, const double* s0,
+                        const uint8_t* label, int nreg, const double* rdiff,
+                        const uint8_t* excluded, or_csr* A, uint8_t* active) {
+    if (nreg < 1 || nreg > OR_MAX_REGIONS) return -1;
+    if (label)
+        for (int64_t e = 0; e < ne; ++e)
+            if (label[e] >= nreg) return -1;
     memset(A, 0, sizeof(*A));
     /* node -> element incidence */
     int64_t* cnt = calloc((size_t)nn + 1, sizeof(int64_t));
@@ -156,8 +169,12 @@ int or_assemble(int64_t nn, int64_t ne, const double* xyz, const int32_t* hex,
     A->nnz = nnz;
     A->mval = calloc((size_t)nnz, sizeof(double));
     A->kval = calloc((size_t)nnz, sizeof(double));
-    /* element loop */
+    /* element loop (excluded elements contribute nothing to M and K; their
+       mass diagonal is kept aside for the nodes they leave inactive) */
+    uint8_t* has = calloc((size_t)nn, 1);
+    double* mexcl = calloc((size_t)nn, sizeof(double));
     for (int64_t e = 0; e < ne; ++e) {
+        const int r = label ? label[e] : 0;
         double X[24], F[24], S[24], Me[64], Ke[64];
         for (int a = 0; a < 8; ++a) {
             const int64_t v = hex[8 * e + a];
@@ -167,7 +184,12 @@ int or_assemble(int64_t nn, int64_t ne, const double* xyz, const int32_t* hex,
                 S[3 * a + i] = s0[3 * v + i];
             }
         }
-        or_element_matrices(X, F, S, dl, dt_, dn, Me, Ke);
+        or_element_matrices(X, F, S, rdiff[3 * r], rdiff[3 * r + 1], rdiff[3 * r + 2], Me, Ke);
+        if (excluded[r]) {
+            for (int a = 0; a < 8; ++a) mexcl[hex[8 * e + a]] += Me[9 * a];
+            continue;
+        }
+        for (int a = 0; a < 8; ++a) has[hex[8 * e + a]] = 1;
         for (int a = 0; a < 8; ++a) {
             const int64_t r = hex[8 * e + a];
             for (int b = 0; b < 8; ++b) {
@@ -177,6 +199,15 @@ int or_assemble(int64_t nn, int64_t ne, const double* xyz, const int32_t* hex,
             }
         }
     }
+    /* inactive nodes: a lone mass diagonal (the consistent-mass diagonal of
+       their excluded elements, so that their rows scale like the others), no
+       stiffness */
+    for (int64_t v = 0; v < nn; ++v) {
+        if (active) active[v] = has[v];
+        if (!has[v]) A->mval[find_col(A, v, v)] = mexcl[v];
+    }
+    free(mexcl);
+    free(has);
     free(cnt);
     free(inc);
     free(fill);

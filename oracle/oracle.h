@@ -84,6 +84,21 @@ typedef struct {
 int or_assemble(int64_t nn, int64_t ne, const double* xyz, const int32_t* hex,
                 const double* f0, const double* s0, double dl, double dt_,
                 double dn, or_csr* A);
+
+/* Subdomains (Sec. 1.1.2: a labelled partition of the domain, each part
+ * with its own conductivities; a part labelled non-conductive is excluded
+ * from the simulation, a conduction block).  label[e] in 0..nreg-1 per
+ * element (NULL: all 0); rdiff[3 r + c] the diffusivities (dl, dt, dn) of
+ * region r; excluded[r] != 0 removes region r's elements from M and K.  A
+ * node none of whose elements remains is inactive: its row of M is a lone
+ * diagonal, the consistent-mass diagonal its excluded elements would give
+ * (so its equation scales like its neighbours'), its row of K zero, and
+ * active[node] is set to 0 (else 1). */
+#define OR_MAX_REGIONS 8
+int or_assemble_regions(int64_t nn, int64_t ne, const double* xyz,
+                        const int32_t* hex, const double* f0, const double* s0,
+                        const uint8_t* label, int nreg, const double* rdiff,
+                        const uint8_t* excluded, or_csr* A, uint8_t* active);
 void or_csr_free(or_csr* A);
 /* y = (cm*M + ck*K) x */
 void or_csr_apply(const or_csr* A, double cm, double ck, const double* x,
@@ -116,6 +131,19 @@ or_sim* or_sim_create(int64_t nn, int64_t ne, const double* xyz,
                       int bdf_order, double tol, int maxit, int npulses,
                       const or_pulse* pulses, const uint8_t* masks,
                       double act_thr);
+/* The same with subdomains (see or_assemble_regions): an inactive node keeps
+ * its ionic states, has no ionic or applied current, and so keeps its
+ * potential. */
+or_sim* or_sim_create_regions(int64_t nn, int64_t ne, const double* xyz,
+                              const int32_t* hex, const double* f0,
+                              const double* s0, const uint8_t* label, int nreg,
+                              const double* rdiff, const uint8_t* excluded,
+                              int model, const uint8_t* cell, double g_passive,
+                              double dt, int bdf_order, double tol, int maxit,
+                              int npulses, const or_pulse* pulses,
+                              const uint8_t* masks, double act_thr);
+/* 1 for an active node, 0 for an inactive one. */
+void or_sim_get_active(const or_sim* S, uint8_t* active);
 void or_sim_destroy(or_sim* S);
 /* Advances nsteps steps; returns 0, or -1 on CG failure, -2 on non-finite. */
 int or_sim_step(or_sim* S, int64_t nsteps);

@@ -33,6 +33,13 @@ def lib():
         L.or_sim_create.argtypes = [i64, i64, vp, vp, vp, vp, d, d, d, i32, vp, d, d,
                                     i32, d, i32, i32, vp, vp, d]
         L.or_sim_create.restype = vp
+        L.or_sim_create_regions.argtypes = [i64, i64, vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, d, d,
+                                            i32, d, i32, i32, vp, vp, d]
+        L.or_sim_create_regions.restype = vp
+        L.or_sim_get_active.argtypes = [vp, vp]
+        L.or_assemble_regions.argtypes = [i64, i64, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
+        L.or_assemble_regions.restype = i32
+        L.or_csr_free.argtypes = [vp]
         L.or_sim_destroy.argtypes = [vp]
         L.or_sim_step.argtypes = [vp, i64]
         L.or_sim_step.restype = i32
@@ -120,11 +127,22 @@ class _CSR(C.Structure):
                 ("kval", C.POINTER(C.c_double))]
 
 
+def _csr_to_scipy(A, sp):
+    n, nnz = A.n, A.nnz
+    rowptr = np.ctypeslib.as_array(A.rowptr, shape=(n + 1,)).copy()
+    col = np.ctypeslib.as_array(A.col, shape=(nnz,)).copy()
+    mv = np.ctypeslib.as_array(A.mval, shape=(nnz,)).copy()
+    kv = np.ctypeslib.as_array(A.kval, shape=(nnz,)).copy()
+    return sp.csr_matrix((mv, col, rowptr), shape=(n, n)), sp.csr_matrix((kv, col, rowptr), shape=(n, n))
+
+
 class Sim:
     """Monodomain simulation (oracle.h, or_sim_*)."""
 
     def __init__(self, xyz, hex8, f0, s0, D, model, dt, bdf_order, cell=None, g=0.0,
-                 tol=1e-12, maxit=1000, pulses=(), masks=None, act_thr=1.0):
+                 tol=1e-12, maxit=1000, pulses=(), masks=None, act_thr=1.0, regions=None):
+        """regions: None, or (label per element, [(dl, dt, dn) per region],
+        [excluded flag per region]) with diffusivities in cm^2/ms."""
         self.xyz = _f64(xyz)
         self.hex = np.ascontiguousarray(hex8, dtype=np.int32)
         self.f0 = _f64(f0)
@@ -140,9 +158,19 @@ class Sim:
             m = np.zeros((1, nn), dtype=np.uint8)
         self._pl, self._m = pl, m
         self.dt = dt
-        self.h = lib().or_sim_create(nn, ne, _p(self.xyz), _p(self.hex), _p(self.f0), _p(self.s0),
-                                     D[0], D[1], D[2], model, _p(self.cell), g, dt, bdf_order,
-                                     tol, maxit, len(pulses), _p(pl), _p(m), act_thr)
+        if regions is None:
+            self.h = lib().or_sim_create(nn, ne, _p(self.xyz), _p(self.hex), _p(self.f0), _p(self.s0),
+                                         D[0], D[1], D[2], model, _p(self.cell), g, dt, bdf_order,
+                                         tol, maxit, len(pulses), _p(pl), _p(m), act_thr)
+        else:
+            label, rdiff, excl = regions
+            self._label = np.ascontiguousarray(label, dtype=np.uint8)
+            self._rdiff = _f64(np.asarray(rdiff, dtype=np.float64).reshape(-1, 3))
+            self._excl = np.ascontiguousarray(excl, dtype=np.uint8)
+            self.h = lib().or_sim_create_regions(
+                nn, ne, _p(self.xyz), _p(self.hex), _p(self.f0), _p(self.s0), _p(self._label),
+                self._rdiff.shape[0], _p(self._rdiff), _p(self._excl), model, _p(self.cell), g, dt,
+                bdf_order, tol, maxit, len(pulses), _p(pl), _p(m), act_thr)
         if not self.h:
             raise ValueError("or_sim_create failed")
         self.nn = nn
@@ -209,6 +237,11 @@ class Sim:
         lib().or_sim_get_iion(self.h, _p(v))
         return v
 
+    def active(self):
+        a = np.zeros(self.nn, dtype=np.uint8)
+        lib().or_sim_get_active(self.h, _p(a))
+        return a
+
     def matrices(self):
         """(rowptr, col, M values, K values) of the assembled CSR matrices."""
         A = _CSR.from_address(lib().or_sim_matrix(self.h))
@@ -229,9 +262,46 @@ def diffusivities(cond):
     return tuple(float(x) / (cond["chi_m"] * cond["Cm"]) for x in s)
 
 
+def region_diffusivities(prob):
+    """(label, per-region diffusivities, excluded flags) of a problem record
+    with subdomains, the region conductivities rescaled like the bulk ones."""
+    r = prob.get("regions")
+    if r is None:
+        return None
+    c = prob["cond"]
+    rd = [diffusivities(dict(c, sigma=tuple(sig))) for sig in r["sigma"]]
+    return (r["label"], rd, r["excluded"])
+
+
+def assemble_regions(prob):
+    """Assembled M, K (scipy CSR) and the active-node flags of a problem
+    record with subdomains."""
+    import scipy.sparse as sp
+
+    m = prob["mesh"]
+    label, rd, excl = region_diffusivities(prob)
+    xyz, hx = _f64(m["xyz"]), np.ascontiguousarray(m["hex"], dtype=np.int32)
+    f0, s0 = _f64(prob["f0"]), _f64(prob["s0"])
+    lab = np.ascontiguousarray(label, dtype=np.uint8)
+    rdv = _f64(np.asarray(rd, dtype=np.float64).reshape(-1, 3))
+    ex = np.ascontiguousarray(excl, dtype=np.uint8)
+    nn, ne = xyz.shape[0], hx.shape[0]
+    A = _CSR()
+    active = np.zeros(nn, dtype=np.uint8)
+    rc = lib().or_assemble_regions(nn, ne, _p(xyz), _p(hx), _p(f0), _p(s0), _p(lab), rdv.shape[0], _p(rdv),
+                                   _p(ex), C.byref(A), _p(active))
+    if rc != 0:
+        raise ValueError("or_assemble_regions failed")
+    out = _csr_to_scipy(A, sp)
+    lib().or_csr_free(C.byref(A))
+    return out[0], out[1], active
+
+
 def sim_from_problem(prob, tol=1e-12, maxit=1000, **kw):
     """Oracle simulation of a problem record built by the inputs module."""
     m = prob["mesh"]
+    if prob.get("regions") is not None:
+        kw = dict(kw, regions=region_diffusivities(prob))
     return Sim(m["xyz"], m["hex"], prob["f0"], prob["s0"], diffusivities(prob["cond"]),
                prob["model"], prob["dt"], prob["bdf"], cell=prob["cell"], tol=tol, maxit=maxit,
                pulses=prob["pulses"], masks=prob["masks"], act_thr=prob["act_thr"], **kw)

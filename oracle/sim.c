@@ -44,6 +44,7 @@ struct or_sim {
     int have_extra;
     int last_iters;
     double last_relres;
+    uint8_t* active;  /* 0: inactive node (no element left after exclusions) */
 };
 
 or_sim* or_sim_create(int64_t nn, int64_t ne, const double* xyz,
@@ -53,13 +54,30 @@ or_sim* or_sim_create(int64_t nn, int64_t ne, const double* xyz,
                       double tol, int maxit, int npulses,
                       const or_pulse* pulses, const uint8_t* masks,
                       double act_thr) {
+    const double rdiff[3] = {dl, dt_, dn};
+    const uint8_t excluded[1] = {0};
+    return or_sim_create_regions(nn, ne, xyz, hex, f0, s0, NULL, 1, rdiff, excluded, model, cell, g,
+                                 dt, bdf_order, tol, maxit, npulses, pulses, masks, act_thr);
+}
+
+or_sim* or_sim_create_regions(int64_t nn, int64_t ne, const double* xyz,
+                              const int32_t* hex, const double* f0,
+                              const double* s0, const uint8_t* label, int nreg,
+                              const double* rdiff, const uint8_t* excluded,
+                              int model, const uint8_t* cell, double g,
+                              double dt, int bdf_order, double tol, int maxit,
+                              int npulses, const or_pulse* pulses,
+                              const uint8_t* masks, double act_thr) {
     if (npulses < 0 || npulses > OR_MAX_PULSES || nn <= 0 || ne <= 0) return NULL;
     if (bdf_order != 1 && bdf_order != 2) return NULL;
     const int ns = or_model_nstates(model);
     if (ns < 0) return NULL;
     or_sim* S = calloc(1, sizeof(or_sim));
     S->nn = nn;
-    if (or_assemble(nn, ne, xyz, hex, f0, s0, dl, dt_, dn, &S->A) != 0) {
+    S->active = malloc((size_t)nn);
+    if (or_assemble_regions(nn, ne, xyz, hex, f0, s0, label, nreg, rdiff, excluded, &S->A,
+                            S->active) != 0) {
+        free(S->active);
         free(S);
         return NULL;
     }
@@ -109,6 +127,7 @@ void or_sim_destroy(or_sim* S) {
     free(S->w_n); free(S->w_nm1); free(S->w_new);
     free(S->iion); free(S->rhs); free(S->tmp);
     free(S->at); free(S->best); free(S->masks); free(S->iapp_extra);
+    free(S->active);
     free(S);
 }
 
@@ -150,6 +169,14 @@ static int step_once(or_sim* S) {
             const double x = S->w_n[(size_t)k * N + i], y = S->w_nm1[(size_t)k * N + i];
             wB[k] = order == 2 ? 2.0 * x - 0.5 * y : x;
             wE[k] = order == 2 ? 2.0 * x - y : x;
+        }
+        if (!S->active[i]) {
+            /* excluded from the simulation: states held, no currents */
+            for (int k = 0; k < ns; ++k) S->w_new[(size_t)k * N + i] = S->w_n[(size_t)k * N + i];
+            S->iion[i] = 0.0;
+            S->tmp[i] = uB / dt;
+            S->u_new[i] = uE;
+            continue;
         }
         or_model_rates(S->model, S->cell[i], S->g, uE, wE, a, b);
         for (int k = 0; k < ns; ++k) {
@@ -209,6 +236,7 @@ void or_sim_set_iapp_extra(or_sim* S, const double* iapp) {
 }
 
 int64_t or_sim_nodes(const or_sim* S) { return S->nn; }
+void or_sim_get_active(const or_sim* S, uint8_t* active) { memcpy(active, S->active, (size_t)S->nn); }
 int or_sim_nstates(const or_sim* S) { return S->ns; }
 int64_t or_sim_stepindex(const or_sim* S) { return S->step; }
 int or_sim_last_iters(const or_sim* S) { return S->last_iters; }

@@ -183,6 +183,8 @@ void dfree(ep_instance* I, T*& p, size_t count) {
 struct Sizes {
     int N, ns, ng32, ns64, prec, op32;
     bool slab;
+    bool regions;     // the mesh carries subdomain labels
+    bool slab_mass;   // the refined path applies the analytic slab mass matrix
 };
 
 // float-float pair (nearest float, then the nearest float of the rest)
@@ -213,6 +215,7 @@ size_t footprint(const Sizes& z) {
     b += 2 * al(z.ng32 * N * 4);          // gates (refined)
     b += 2 * al(z.ns64 * N * 8);          // FP64 states
     b += al(N);                           // cell types
+    if (z.regions) b += al(N);            // active-node flags
     if (z.prec != EP_PREC_FP32_REFINED) b += 3 * al(N * 8);  // v, b, r
     b += 2 * al(N * 8);                   // at, best
     if (z.prec != EP_PREC_FP32_REFINED) {
@@ -222,7 +225,7 @@ size_t footprint(const Sizes& z) {
     if (z.prec == EP_PREC_FP32_REFINED) {
         b += al(N * 4);                   // dinv32
         b += 2 * al(epk::kGroups * N * 16);                              // Ahi Alo
-        if (!z.slab) b += 2 * al(epk::kGroups * N * 16);                 // Mhi Mlo (curved meshes)
+        if (!z.slab_mass) b += 2 * al(epk::kGroups * N * 16);            // Mhi Mlo (curved / with regions)
         b += 6 * al(N * 4);                                              // u, v, b (hi, lo)
         b += 6 * al(N * 4);                                              // A u history (hi, lo)
         b += 5 * al(N * 4);                                              // u levels (hi, lo), best slope
@@ -255,7 +258,8 @@ ep_status validate(const ep_mesh* mesh, const ep_fibers* fib, const ep_conductiv
         return fail(EP_EINVAL, "shell needs xyz");
     }
     if (!fib->f0 || !fib->s0) return fail(EP_EINVAL, "fibers.f0/s0 must be given");
-    if (!finite_pos(cond->sigma_l) || !finite_pos(cond->sigma_t) || !finite_pos(cond->sigma_n))
+    if (!mesh->region &&
+        (!finite_pos(cond->sigma_l) || !finite_pos(cond->sigma_t) || !finite_pos(cond->sigma_n)))
         return fail(EP_EINVAL, "conductivities must be positive and finite");
     if (!cond->is_D && (!finite_pos(cond->chi_m) || !finite_pos(cond->Cm)))
         return fail(EP_EINVAL, "chi_m and Cm must be positive and finite");
@@ -281,6 +285,20 @@ ep_status validate(const ep_mesh* mesh, const ep_fibers* fib, const ep_conductiv
     if (opts->op32 < EP_OP_AUTO || opts->op32 > EP_OP_STENCIL) return fail(EP_EINVAL, "options.op32");
     if (opts->op32 == EP_OP_MATRIX_FREE && mesh->kind != EP_MESH_SLAB)
         return fail(EP_EUNSUPPORTED, "the matrix-free FP32 operator needs a slab mesh");
+    if (mesh->region) {
+        if (opts->op32 == EP_OP_MATRIX_FREE && opts->precision == EP_PREC_FP32_REFINED)
+            return fail(EP_EUNSUPPORTED, "the matrix-free FP32 operator does not take subdomains");
+        if (cond->n_regions < 1 || cond->n_regions > EP_MAX_REGIONS)
+            return fail(EP_EINVAL, "conductivities.n_regions must be in 1..8 with a region label");
+        for (int r = 0; r < cond->n_regions; ++r)
+            if (!cond->non_conductive[r])
+                for (int c = 0; c < 3; ++c)
+                    if (!finite_pos(cond->region_sigma[r][c]))
+                        return fail(EP_EINVAL, "region conductivities must be positive and finite");
+        const int64_t ne = (int64_t)mesh->nx * mesh->ny * mesh->nz;
+        for (int64_t e = 0; e < ne; ++e)
+            if (mesh->region[e] >= cond->n_regions) return fail(EP_EINVAL, "region label out of range");
+    }
     if (opts->tol < 0 || opts->inner_tol < 0 || opts->max_iter < 0 || opts->max_sweeps < 0)
         return fail(EP_EINVAL, "negative solver option");
     return EP_OK;
@@ -292,9 +310,12 @@ Sizes sizes_of(const ep_mesh* mesh, const ep_ionic_model* ionic, const ep_option
     z.ns = ionic->model == EP_MODEL_BO ? epk::kBOStates : epk::kTTGates + epk::kTTConc;
     z.prec = opts->precision;
     z.slab = mesh->kind == EP_MESH_SLAB;
+    z.regions = mesh->region != nullptr;
+    // an excluded region changes M; the footprint assumes it may
+    z.slab_mass = z.slab && !z.regions;
     // AUTO on a slab keeps both FP32 operators and lets the create-time
     // autotuner pick; the matrix-free apply needs an axis-aligned slab
-    z.op32 = opts->op32 == EP_OP_AUTO ? (z.slab ? EP_OP_AUTO : EP_OP_STENCIL) : opts->op32;
+    z.op32 = opts->op32 == EP_OP_AUTO ? ((z.slab && !z.regions) ? EP_OP_AUTO : EP_OP_STENCIL) : opts->op32;
     if (z.prec == EP_PREC_FP32_REFINED) {
         z.ng32 = ionic->model == EP_MODEL_BO ? epk::kBOStates : epk::kTTGates;
         z.ns64 = ionic->model == EP_MODEL_BO ? 0 : epk::kTTConc;
@@ -606,6 +627,11 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     uint8_t* cell = nullptr;
     ALLOC(cell, N);
     h.cell = cell;
+    if (z.regions) {
+        uint8_t* act = nullptr;
+        ALLOC(act, N);
+        h.active = act;  // written by the assembly
+    }
     if (!ref) {
         ALLOC(h.v, N);
         ALLOC(h.b, N);
@@ -620,7 +646,7 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         ALLOC(h.dinv32, N);
         ALLOC(h.Ahi, epk::kGroups * N);
         ALLOC(h.Alo, epk::kGroups * N);
-        if (h.kind != EP_MESH_SLAB) {
+        if (!z.slab_mass) {
             ALLOC(h.Mhi, epk::kGroups * N);
             ALLOC(h.Mlo, epk::kGroups * N);
         }
@@ -770,8 +796,20 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         if (e == cudaSuccess && xyz) e = cudaMemcpy(xyz, mesh->xyz, N * 24, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(bad, 0, sizeof(int));
         int bad_h = 0;
+        uint8_t* label = nullptr;
+        epk::AsmParams P{xyz, f0, s0, dl, dtr, dn, alpha_dt, bad, nullptr, {}, {}};
+        if (e == cudaSuccess && mesh->region) {
+            const size_t ne = (size_t)mesh->nx * mesh->ny * mesh->nz;
+            e = cudaMalloc(&label, ne);
+            if (e == cudaSuccess) e = cudaMemcpy(label, mesh->region, ne, cudaMemcpyHostToDevice);
+            P.label = label;
+            const double sc = cond->is_D ? 1.0 : 1.0 / (cond->chi_m * cond->Cm);
+            for (int r = 0; r < cond->n_regions; ++r) {
+                for (int c = 0; c < 3; ++c) P.rd[r][c] = cond->region_sigma[r][c] * sc;
+                P.excl[r] = cond->non_conductive[r] ? 1 : 0;
+            }
+        }
         if (e == cudaSuccess) {
-            epk::AsmParams P{xyz, f0, s0, dl, dtr, dn, alpha_dt, bad};
             epk::launch_assemble(I->d, h, P, I->stream);
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
@@ -781,6 +819,7 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         cudaFree(s0);
         if (xyz) cudaFree(xyz);
         if (bad) cudaFree(bad);
+        if (label) cudaFree(label);
         if (e != cudaSuccess) return fail(EP_ECUDA, std::string("assembly: ") + cudaGetErrorString(e));
         if (bad_h) return fail(EP_EINVAL, "mesh has an element with non-positive Jacobian determinant");
     }

@@ -67,6 +67,7 @@ struct Dev {
                                 // the TTP06 concentrations as float-float, the
                                 // memory read as float [2][5][N] (hi parts, then lo)
     const uint8_t* cell;
+    const uint8_t* active;      // per node, 0 = excluded from the simulation (NULL: all active)
     double *v;                  // u_BDF/dt - I_ion + I_app (FP64 path)
     double *b, *r;              // FP64 right-hand side and residual (FP64 path)
     // refined path, float-float (hi, lo): the solve's iterate u (starts at
@@ -130,9 +131,14 @@ struct AsmParams {
     const double* xyz;  // shell coordinates [N][3] (NULL for slabs)
     const double* f0;   // [N][3]
     const double* s0;   // [N][3]
-    double dl, dt, dn;  // diffusivities (cm^2/ms)
+    double dl, dt, dn;  // diffusivities (cm^2/ms), one region
     double alpha_dt;    // alpha/dt of the system matrix A = alpha/dt M + K
     int* bad;           // set to 1 on a non-positive Jacobian determinant
+    // subdomains: element labels (NULL: one region with dl, dt, dn), the
+    // diffusivities of each region and its exclusion flag
+    const uint8_t* label;
+    double rd[EP_MAX_REGIONS][3];
+    int excl[EP_MAX_REGIONS];
 };
 
 // Counter slots (one per reducing kernel so that consecutive kernels never

@@ -152,17 +152,19 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Batch B) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) wB[k] = wn[(size_t)k * N + n];
         }
+        // an excluded node: states held, no currents
+        const bool on = !D.active || D.active[n];
         // BO rates depend on u only
         G a[3], b[3], w1[3];
         BO<G>::rates(uEg, a, b);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            w1[k] = (wB[k] + dtg * a[k]) / (alg + dtg * b[k]);
+            w1[k] = on ? (wB[k] + dtg * a[k]) / (alg + dtg * b[k]) : wn[(size_t)k * N + n];
             wm[(size_t)k * N + n] = w1[k];
         }
-        const G I = BO<G>::iion(uEg, w1[0], w1[1], w1[2]);
-        if constexpr (sizeof(G) == 4) store_vu_ff(D, n, ubh, ubl, ueh, uel, applied_f(D, c, n) - I);
-        else store_vu64(D, n, fma(uB, c.inv_dt, applied(D, c, n) - (double)I), uE);
+        const G I = on ? BO<G>::iion(uEg, w1[0], w1[1], w1[2]) : G(0);
+        if constexpr (sizeof(G) == 4) store_vu_ff(D, n, ubh, ubl, ueh, uel, on ? applied_f(D, c, n) - I : 0.f);
+        else store_vu64(D, n, fma(uB, c.inv_dt, on ? applied(D, c, n) - (double)I : 0.0), uE);
     }
 }
 
@@ -215,6 +217,18 @@ __global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_
                     dc[k] = 0.f;
                     cE[k] = ch[k];
                 }
+            }
+            if (D.active && !D.active[n]) {
+                // excluded from the simulation: states held, no currents
+#pragma unroll
+                for (int k = 0; k < kTTGates; ++k) gm[(size_t)k * N + n] = gn[(size_t)k * N + n];
+#pragma unroll
+                for (int k = 0; k < kTTConc; ++k) {
+                    chm[(size_t)k * N + n] = ch[k];
+                    chm[LO + (size_t)k * N + n] = cl[k];
+                }
+                store_vu_ff(D, n, ubh, ubl, ueh, uel, 0.f);
+                continue;
             }
             float a[kTTGates], b[kTTGates], r[kTTConc];
             TT<float>::rates(cell, ueh, gE, cE[0], cE[1], cE[2], cE[3], cE[4], a, b, r);
@@ -271,6 +285,13 @@ __global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_
                 for (int k = 0; k < kTTGates; ++k) gB[k] = gE[k] = gn[(size_t)k * N + n];
 #pragma unroll
                 for (int k = 0; k < kTTConc; ++k) cB[k] = cE[k] = cn[(size_t)k * N + n];
+            }
+            if (D.active && !D.active[n]) {
+                // excluded from the simulation: states held, no currents
+                for (int k = 0; k < kTTGates; ++k) gm[(size_t)k * N + n] = gn[(size_t)k * N + n];
+                for (int k = 0; k < kTTConc; ++k) cm[(size_t)k * N + n] = cn[(size_t)k * N + n];
+                store_vu64(D, n, uB * c.inv_dt, uE);
+                continue;
             }
             double a[kTTGates], b[kTTGates], r[kTTConc];
             TT<double>::rates(cell, uE, gE, cE[0], cE[1], cE[2], cE[3], cE[4], a, b, r);

@@ -38,9 +38,10 @@ __device__ void node_coords(const Dev& D, const AsmParams& P, int i, int j, int 
     }
 }
 
-// Row a of the element mass and stiffness matrices of element (ei, ej, ek).
-__device__ void element_row(const Dev& D, const AsmParams& P, int ei, int ej, int ek, int a,
-                            double Mrow[8], double Krow[8], bool& bad) {
+// Row a of the element mass and stiffness matrices of element (ei, ej, ek)
+// with diffusivities dl, dt, dn.
+__device__ void element_row(const Dev& D, const AsmParams& P, int ei, int ej, int ek, int a, double dl,
+                            double dtr, double dn, double Mrow[8], double Krow[8], bool& bad) {
     double X[8][3], F[8][3], S[8][3];
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
@@ -109,7 +110,7 @@ __device__ void element_row(const Dev& D, const AsmParams& P, int ei, int ej, in
         for (int i = 0; i < 3; ++i) {
             const double fg = fq[0] * G[a][0] + fq[1] * G[a][1] + fq[2] * G[a][2];
             const double sg = sq[0] * G[a][0] + sq[1] * G[a][1] + sq[2] * G[a][2];
-            Dg[i] = P.dn * G[a][i] + (P.dl - P.dn) * fg * fq[i] + (P.dt - P.dn) * sg * sq[i];
+            Dg[i] = dn * G[a][i] + (dl - dn) * fg * fq[i] + (dtr - dn) * sg * sq[i];
         }
         const double pa = phi[a];
         for (int b = 0; b < 8; ++b) {
@@ -129,6 +130,8 @@ __global__ void __launch_bounds__(128) k_assemble(Dev* __restrict__ Dp, AsmParam
     double cm[kSlots], ck[kSlots];
     for (int s = 0; s < kSlots; ++s) cm[s] = ck[s] = 0.0;
     bool bad = false;
+    int included = 0;
+    double mexcl = 0.0;  // mass diagonal of the excluded elements around n
     for (int ec = 0; ec < 2; ++ec)
         for (int eb = 0; eb < 2; ++eb)
             for (int ea = 0; ea < 2; ++ea) {
@@ -142,8 +145,23 @@ __global__ void __launch_bounds__(128) k_assemble(Dev* __restrict__ Dp, AsmParam
                 }
                 const int a0 = 1 - ea, a1 = 1 - eb, a2 = 1 - ec;
                 const int a = a0 + 2 * a1 + 4 * a2;
+                double dl = P.dl, dtr = P.dt, dn = P.dn;
+                bool excluded = false;
+                if (P.label) {
+                    // element (gi, gj, gk) of the subdomain partition
+                    const int r = P.label[(size_t)gi + (size_t)D.nx * ((size_t)gj + (size_t)D.ny * gk)];
+                    excluded = P.excl[r] != 0;
+                    dl = P.rd[r][0];
+                    dtr = P.rd[r][1];
+                    dn = P.rd[r][2];
+                }
                 double Mrow[8], Krow[8];
-                element_row(D, P, gi, gj, gk, a, Mrow, Krow, bad);
+                element_row(D, P, gi, gj, gk, a, dl, dtr, dn, Mrow, Krow, bad);
+                if (excluded) {  // no contribution to M and K; its mass diagonal aside
+                    mexcl += Mrow[a];
+                    continue;
+                }
+                ++included;
                 for (int b = 0; b < 8; ++b) {
                     const int di = (b & 1) - a0, dj = ((b >> 1) & 1) - a1, dk = ((b >> 2) & 1) - a2;
                     const int t = (di + 1) + 3 * (dj + 1) + 9 * (dk + 1);
@@ -154,6 +172,10 @@ __global__ void __launch_bounds__(128) k_assemble(Dev* __restrict__ Dp, AsmParam
                 }
             }
     if (bad) *P.bad = 1;
+    // an inactive node keeps a lone mass diagonal (what its excluded elements
+    // would give, so its row scales like its neighbours') and no stiffness
+    if (included == 0) cm[0] = mexcl;
+    if (D.active) const_cast<uint8_t*>(D.active)[n] = included > 0 ? 1 : 0;
     for (int s = 0; s < kSlots; ++s) {
         const double av = ck[s] + P.alpha_dt * cm[s];
         D.M64[(size_t)s * D.N + n] = cm[s];

@@ -40,16 +40,21 @@ class EpError(RuntimeError):
 
 class ep_mesh(C.Structure):
     _fields_ = [("kind", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
-                ("L", C.c_double * 3), ("xyz", C.c_void_p), ("n_nodes", C.c_int64)]
+                ("L", C.c_double * 3), ("xyz", C.c_void_p), ("n_nodes", C.c_int64), ("region", C.c_void_p)]
 
 
 class ep_fibers(C.Structure):
     _fields_ = [("f0", C.c_void_p), ("s0", C.c_void_p)]
 
 
+EP_MAX_REGIONS = 8
+
+
 class ep_conductivities(C.Structure):
     _fields_ = [("sigma_l", C.c_double), ("sigma_t", C.c_double), ("sigma_n", C.c_double),
-                ("chi_m", C.c_double), ("Cm", C.c_double), ("is_D", C.c_int32)]
+                ("chi_m", C.c_double), ("Cm", C.c_double), ("is_D", C.c_int32), ("n_regions", C.c_int32),
+                ("region_sigma", (C.c_double * 3) * EP_MAX_REGIONS),
+                ("non_conductive", C.c_uint8 * EP_MAX_REGIONS)]
 
 
 class ep_ionic_model(C.Structure):
@@ -156,7 +161,9 @@ class _Args:
 
     def __init__(self, mesh, f0=None, s0=None, cond=None, model=EP_MODEL_TTP06, cell_type=None,
                  pulses=(), dt=0.05, bdf_order=2, precision=EP_PREC_FP64, tol=0.0, max_iter=0,
-                 inner_tol=0.0, max_sweeps=0, op32=EP_OP_AUTO, cuda_stream=None):
+                 inner_tol=0.0, max_sweeps=0, op32=EP_OP_AUTO, cuda_stream=None, regions=None):
+        """regions: None, or dict(label=per-element uint8, sigma=[(l, t, n)
+        per region] in the units of cond, excluded=[flag per region])."""
         keep = []
         m = ep_mesh()
         m.kind, m.nx, m.ny, m.nz = mesh["kind"], mesh["nx"], mesh["ny"], mesh["nz"]
@@ -169,6 +176,10 @@ class _Args:
         else:
             m.xyz = None
         m.n_nodes = mesh["xyz"].shape[0] if "xyz" in mesh else mesh["n_nodes"]
+        if regions is not None:
+            lab = np.ascontiguousarray(regions["label"], dtype=np.uint8)
+            keep.append(lab)
+            m.region = _ptr(lab)
         self.mesh = m
         fb = ep_fibers()
         if f0 is not None:
@@ -180,6 +191,12 @@ class _Args:
         if cond is not None:
             c.sigma_l, c.sigma_t, c.sigma_n = cond["sigma"]
             c.chi_m, c.Cm, c.is_D = cond["chi_m"], cond["Cm"], 1 if cond["is_D"] else 0
+        if regions is not None:
+            c.n_regions = len(regions["sigma"])
+            for r, sig in enumerate(regions["sigma"]):
+                for k in range(3):
+                    c.region_sigma[r][k] = sig[k]
+                c.non_conductive[r] = 1 if regions["excluded"][r] else 0
         self.cond = c
         io = ep_ionic_model()
         io.model = model
@@ -356,7 +373,8 @@ class Instance:
         self.model = prob["model"]
         self.h = ep_create(m, prob["f0"], prob["s0"], prob["cond"], prob["model"],
                            cell_type=prob["cell"], pulses=pulses, dt=prob["dt"],
-                           bdf_order=prob["bdf"], precision=precision, **opts)
+                           bdf_order=prob["bdf"], precision=precision, regions=prob.get("regions"),
+                           **opts)
 
     def step(self, n=1):
         ep_step(self.h, n)

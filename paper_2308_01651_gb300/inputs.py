@@ -255,6 +255,38 @@ def as_bo(prob, amp=1.0, dur=2.0):
     return q
 
 
+def element_centroids(mesh):
+    """Centroid of every element (element order of the connectivity)."""
+    return mesh["xyz"][mesh["hex"]].mean(axis=1)
+
+
+def slab_regions(nx=40, ny=12, nz=6, h=0.01, T=20.0, dt=0.05, bdf=2, model=None, wall=False):
+    """TTP06 slab with subdomains (Sec. 1.1.2): region 0 healthy tissue, region
+    1 a grey zone with the conductivities halved, region 2 a non-conductive
+    scar.  wall=False: a scar block in the middle of the slab (x in
+    [0.4, 0.6], y in [0.25, 0.75] of the lengths, through z) ringed by a grey
+    zone 0.15 of the length wide; wall=True: a scar layer across the whole
+    section at x in [0.45, 0.55] of the length (a complete conduction
+    block).  Stimulus on the x = 0 face."""
+    L = (nx * h, ny * h, nz * h)
+    p = slab_ttp06(nx=nx, ny=ny, nz=nz, L=L, T=T, bdf=bdf, dt=dt)
+    if model == BO:
+        p = as_bo(p)
+    c = element_centroids(p["mesh"]) / np.array(L)
+    label = np.zeros(c.shape[0], dtype=np.uint8)
+    if wall:
+        label[(c[:, 0] >= 0.45) & (c[:, 0] <= 0.55)] = 2
+    else:
+        grey = (c[:, 0] >= 0.25) & (c[:, 0] <= 0.75) & (c[:, 1] >= 0.1) & (c[:, 1] <= 0.9)
+        scar = (c[:, 0] >= 0.4) & (c[:, 0] <= 0.6) & (c[:, 1] >= 0.25) & (c[:, 1] <= 0.75)
+        label[grey] = 1
+        label[scar] = 2
+    s0 = tuple(p["cond"]["sigma"])
+    p["regions"] = dict(label=label, sigma=[s0, tuple(0.5 * x for x in s0), s0], excluded=[0, 0, 1])
+    p["name"] = p["name"] + ("_wall" if wall else "_scar")
+    return p
+
+
 def batch_slabs(count=96, n_lo=2.0e4, n_hi=4.0e5, T=300.0, dt=0.05, seed_offset=2, h=0.01):
     """Uneven batch of slabs: node counts log-uniform in [n_lo, n_hi], aspect
     nx/ny uniform in [1, 4] with nz = ny, h = 0.01 cm, model Bernoulli(1/2)

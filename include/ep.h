@@ -134,14 +134,19 @@ typedef struct {
 } ep_ionic_model;
 
 /* Applied current I_app (Sec. 1.1.2): pulse p adds amp (model units per ms:
- * mV/ms for TTP06, 1/ms for BO) at the nodes where mask[node] != 0, on step
- * n+1 when k0 < n+1 <= k0 + kd with k0 = round(t0/dt), kd = round(dur/dt),
- * repeating every round(period/dt) steps when period > 0.  At most
- * EP_MAX_PULSES pulses; each mask has n_nodes bytes. */
+ * mV/ms for TTP06, 1/ms for BO) at the nodes where mask[node] != 0 -- or,
+ * with a spatial profile, amp * weight[node] at every node (the paper's
+ * Gaussian impulses, Sec. 3.2: weight = exp(-|x - c|^2 / (2 s^2)); a
+ * spherical impulse is a mask) -- on step n+1 when k0 < n+1 <= k0 + kd
+ * with k0 = round(t0/dt), kd = round(dur/dt), repeating every
+ * round(period/dt) steps when period > 0.  At most EP_MAX_PULSES pulses;
+ * each mask has n_nodes bytes, each weight n_nodes finite doubles; a pulse
+ * needs a mask or a weight (the weight wins when both are given). */
 #define EP_MAX_PULSES 4
 typedef struct {
     double amp, t0, dur, period;
     const uint8_t* mask;
+    const double* weight;
 } ep_pulse;
 
 typedef struct {

@@ -142,6 +142,10 @@ or_sim* or_sim_create_regions(int64_t nn, int64_t ne, const double* xyz,
                               double dt, int bdf_order, double tol, int maxit,
                               int npulses, const or_pulse* pulses,
                               const uint8_t* masks, double act_thr);
+/* Spatial profile of pulse p (Sec. 3.2.x: spherical and Gaussian impulses):
+ * the node receives amp * weight[node] instead of amp * (mask[node] != 0).
+ * NULL restores the mask.  The array is copied. */
+void or_sim_set_pulse_weights(or_sim* S, int p, const double* weight);
 /* 1 for an active node, 0 for an inactive one. */
 void or_sim_get_active(const or_sim* S, uint8_t* active);
 void or_sim_destroy(or_sim* S);

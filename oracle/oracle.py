@@ -37,6 +37,7 @@ def lib():
                                             i32, d, i32, i32, vp, vp, d]
         L.or_sim_create_regions.restype = vp
         L.or_sim_get_active.argtypes = [vp, vp]
+        L.or_sim_set_pulse_weights.argtypes = [vp, i32, vp]
         L.or_assemble_regions.argtypes = [i64, i64, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
         L.or_assemble_regions.restype = i32
         L.or_csr_free.argtypes = [vp]
@@ -173,6 +174,10 @@ class Sim:
                 bdf_order, tol, maxit, len(pulses), _p(pl), _p(m), act_thr)
         if not self.h:
             raise ValueError("or_sim_create failed")
+        for k, p in enumerate(pulses):
+            if p.get("weight") is not None:
+                w = _f64(p["weight"])
+                lib().or_sim_set_pulse_weights(self.h, k, _p(w))
         self.nn = nn
         self.ns = lib().or_sim_nstates(self.h)
 

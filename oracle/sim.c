@@ -45,6 +45,7 @@ struct or_sim {
     int last_iters;
     double last_relres;
     uint8_t* active;  /* 0: inactive node (no element left after exclusions) */
+    double* weight[OR_MAX_PULSES];  /* per-node pulse profiles (NULL: mask) */
 };
 
 or_sim* or_sim_create(int64_t nn, int64_t ne, const double* xyz,
@@ -128,6 +129,7 @@ void or_sim_destroy(or_sim* S) {
     free(S->iion); free(S->rhs); free(S->tmp);
     free(S->at); free(S->best); free(S->masks); free(S->iapp_extra);
     free(S->active);
+    for (int p = 0; p < OR_MAX_PULSES; ++p) free(S->weight[p]);
     free(S);
 }
 
@@ -186,8 +188,10 @@ static int step_once(or_sim* S) {
         const double I = or_model_iion(S->model, S->cell[i], S->g, uE, wn);
         S->iion[i] = I;
         double iapp = S->have_extra ? S->iapp_extra[i] : 0.0;
-        for (int p = 0; p < S->npulses; ++p)
-            if (S->masks[(size_t)p * N + i]) iapp += amp_now[p];
+        for (int p = 0; p < S->npulses; ++p) {
+            if (S->weight[p]) iapp += amp_now[p] * S->weight[p][i];
+            else if (S->masks[(size_t)p * N + i]) iapp += amp_now[p];
+        }
         /* nodal vector that the mass matrix multiplies on the right of Eq. (6) */
         S->tmp[i] = uB / dt - I + iapp;
         S->u_new[i] = uE;  /* initial guess u_EXT */
@@ -237,6 +241,16 @@ void or_sim_set_iapp_extra(or_sim* S, const double* iapp) {
 
 int64_t or_sim_nodes(const or_sim* S) { return S->nn; }
 void or_sim_get_active(const or_sim* S, uint8_t* active) { memcpy(active, S->active, (size_t)S->nn); }
+
+void or_sim_set_pulse_weights(or_sim* S, int p, const double* weight) {
+    if (p < 0 || p >= OR_MAX_PULSES) return;
+    free(S->weight[p]);
+    S->weight[p] = NULL;
+    if (weight) {
+        S->weight[p] = malloc((size_t)S->nn * sizeof(double));
+        memcpy(S->weight[p], weight, (size_t)S->nn * sizeof(double));
+    }
+}
 int or_sim_nstates(const or_sim* S) { return S->ns; }
 int64_t or_sim_stepindex(const or_sim* S) { return S->step; }
 int or_sim_last_iters(const or_sim* S) { return S->last_iters; }

@@ -273,7 +273,10 @@ ep_status validate(const ep_mesh* mesh, const ep_fibers* fib, const ep_conductiv
         if (stim->n_pulses > 0 && !stim->pulses) return fail(EP_EINVAL, "stimulus.pulses is NULL");
         for (int p = 0; p < stim->n_pulses; ++p) {
             const ep_pulse& P = stim->pulses[p];
-            if (!P.mask) return fail(EP_EINVAL, "pulse mask is NULL");
+            if (!P.mask && !P.weight) return fail(EP_EINVAL, "a pulse needs a mask or a weight");
+            if (P.weight)
+                for (int64_t i = 0; i < nn; ++i)
+                    if (!std::isfinite(P.weight[i])) return fail(EP_EINVAL, "pulse weights must be finite");
             if (!std::isfinite(P.amp) || !std::isfinite(P.t0) || !(P.dur >= 0) || !std::isfinite(P.period))
                 return fail(EP_EINVAL, "pulse parameters must be finite, dur >= 0");
         }
@@ -695,8 +698,25 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         h.kp[p] = P.period > 0 ? llround(P.period / h.dt) : 0;
         uint8_t* m = nullptr;
         ALLOC(m, N);
-        CUDA_TRY(cudaMemcpyAsync(m, P.mask, N, cudaMemcpyHostToDevice, I->stream));
+        if (P.mask) CUDA_TRY(cudaMemcpyAsync(m, P.mask, N, cudaMemcpyHostToDevice, I->stream));
+        else CUDA_TRY(cudaMemsetAsync(m, 0, N, I->stream));
         h.mask[p] = m;
+        if (P.weight) {
+            // the profile in the path's precision
+            if (ref) {
+                std::vector<float> w32(N);
+                for (size_t i = 0; i < N; ++i) w32[i] = (float)P.weight[i];
+                float* w = nullptr;
+                ALLOC(w, N);
+                CUDA_TRY(cudaMemcpy(w, w32.data(), N * 4, cudaMemcpyHostToDevice));
+                h.wgt32[p] = w;
+            } else {
+                double* w = nullptr;
+                ALLOC(w, N);
+                CUDA_TRY(cudaMemcpy(w, P.weight, N * 8, cudaMemcpyHostToDevice));
+                h.wgt64[p] = w;
+            }
+        }
     }
 
     // ---- initial state ------------------------------------------------------

@@ -60,6 +60,8 @@ struct Dev {
     double amp[EP_MAX_PULSES];
     long long k0[EP_MAX_PULSES], kd[EP_MAX_PULSES], kp[EP_MAX_PULSES];
     const uint8_t* mask[EP_MAX_PULSES];
+    const double* wgt64[EP_MAX_PULSES];  // pulse profiles (FP64 path; NULL: mask)
+    const float* wgt32[EP_MAX_PULSES];   // pulse profiles (refined path)
     // ---- state ---------------------------------------------------------------
     double *u_n, *u_nm1, *u_new;
     float *g32_n, *g32_nm1;     // FP32 gates [ng][N] (FP32_REFINED)

@@ -60,7 +60,10 @@ __device__ __forceinline__ double applied(const Dev& D, const StepConsts& c, int
     double s = 0.0;
 #pragma unroll
     for (int p = 0; p < EP_MAX_PULSES; ++p)
-        if (c.iamp[p] != 0.0 && D.mask[p][n]) s += c.iamp[p];
+        if (c.iamp[p] != 0.0) {
+            if (D.wgt64[p]) s += c.iamp[p] * D.wgt64[p][n];
+            else if (D.mask[p][n]) s += c.iamp[p];
+        }
     return s;
 }
 
@@ -102,7 +105,10 @@ __device__ __forceinline__ float applied_f(const Dev& D, const StepConsts& c, in
     float s = 0.f;
 #pragma unroll
     for (int p = 0; p < EP_MAX_PULSES; ++p)
-        if (c.iamp[p] != 0.0 && D.mask[p][n]) s += (float)c.iamp[p];
+        if (c.iamp[p] != 0.0) {
+            if (D.wgt32[p]) s += (float)c.iamp[p] * D.wgt32[p][n];
+            else if (D.mask[p][n]) s += (float)c.iamp[p];
+        }
     return s;
 }
 

@@ -63,7 +63,7 @@ class ep_ionic_model(C.Structure):
 
 class ep_pulse(C.Structure):
     _fields_ = [("amp", C.c_double), ("t0", C.c_double), ("dur", C.c_double), ("period", C.c_double),
-                ("mask", C.c_void_p)]
+                ("mask", C.c_void_p), ("weight", C.c_void_p)]
 
 
 class ep_stimulus(C.Structure):
@@ -212,6 +212,10 @@ class _Args:
             arr[k].amp, arr[k].t0, arr[k].dur = p["amp"], p["t0"], p["dur"]
             arr[k].period = p.get("period", 0.0)
             arr[k].mask = _ptr(mk)
+            if p.get("weight") is not None:
+                wt = _f64(p["weight"])
+                keep.append(wt)
+                arr[k].weight = _ptr(wt)
         keep.append(arr)
         s = ep_stimulus()
         s.n_pulses = len(pulses)

@@ -255,6 +255,43 @@ def as_bo(prob, amp=1.0, dur=2.0):
     return q
 
 
+def sphere_mask(xyz, centre, radius, h=1.0):
+    """Nodes inside a ball (closed, with a tolerance of 1e-9 h): the
+    paper's spherical impulse."""
+    d = np.linalg.norm(np.asarray(xyz) - np.asarray(centre, dtype=np.float64), axis=1)
+    return (d <= radius + 1e-9 * h).astype(np.uint8)
+
+
+def gaussian_weight(xyz, centre, sd):
+    """exp(-|x - c|^2 / (2 sd^2)) at every node: the paper's Gaussian
+    impulse profile (site c, standard deviation sd)."""
+    d2 = np.sum((np.asarray(xyz) - np.asarray(centre, dtype=np.float64)) ** 2, axis=1)
+    return np.exp(-d2 / (2.0 * sd * sd))
+
+
+def slab_gaussian_pacing(nx=30, ny=10, nz=5, h=0.01, T=20.0, dt=0.05, model=None, sites=None, sd=0.025,
+                         amp=None, period=0.0, dur=2.0):
+    """Slab paced by Gaussian impulses (Sec. 3.2, the idealised ventricle's
+    protocol): one pulse per site, each with its own profile; TTP06 by
+    default (amplitude 35.714 mV/ms), Bueno-Orovio with model=BO (1/ms)."""
+    L = (nx * h, ny * h, nz * h)
+    p = slab_ttp06(nx=nx, ny=ny, nz=nz, L=L, T=T, dt=dt)
+    if model == BO:
+        p = as_bo(p)
+    if sites is None:
+        sites = [(0.2 * L[0], 0.5 * L[1], 0.0), (0.8 * L[0], 0.2 * L[1], L[2])]
+    a = amp if amp is not None else (35.714 if p["model"] == TTP06 else 1.0)
+    xyz = p["mesh"]["xyz"]
+    pulses, masks = [], []
+    for c in sites:
+        w = gaussian_weight(xyz, c, sd)
+        pulses.append(dict(amp=a, t0=0.0, dur=dur, period=period, weight=w))
+        masks.append((w > 1e-3).astype(np.uint8))
+    q = problem(p["mesh"], p["f0"], p["s0"], p["cond"], p["model"], p["dt"], p["bdf"], T, pulses, masks,
+                name=p["name"] + "_gauss")
+    return q
+
+
 def element_centroids(mesh):
     """Centroid of every element (element order of the connectivity)."""
     return mesh["xyz"][mesh["hex"]].mean(axis=1)

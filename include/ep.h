@@ -131,7 +131,25 @@ typedef struct {
 typedef struct {
     int32_t model;
     const uint8_t* cell_type;
+    /* Optional initial u and states per cell type (ENDO, MID, EPI), 3 rows
+     * of 1 + S doubles (u first, then the states in the checkpoint's order;
+     * S = 3 BO, 18 TTP06), e.g. from ep_prepace; NULL: the defaults above. */
+    const double* initial;
 } ep_ionic_model;
+
+/* Single-cell pre-pacing (the paper initialises its ionic models from 0D
+ * simulations of many beats at the pacing period, Sec. 3.2).  For each of
+ * n_cells cells (cell_types[i] = EP_CELL_*; the type matters for TTP06
+ * only), integrates Eq. (1) without diffusion with the semi-implicit step of
+ * Eq. (4) that the tissue step uses (BDF of bdf_order, a BDF1 first step),
+ * time step dt, under a train of pulses of amp (model units per ms) lasting
+ * dur_ms every period_ms from t = 0, for beats beats; writes u and the
+ * states at the end (start of the next beat) to out, n_cells rows of 1 + S
+ * doubles.  initial: NULL (the model's defaults) or n_cells rows of 1 + S.
+ * Runs on the GPU in FP64, one thread per cell, a launch per beat. */
+ep_status ep_prepace(int32_t model, const uint8_t* cell_types, int32_t n_cells, double period_ms,
+                     int32_t beats, double dt, double amp, double dur_ms, int32_t bdf_order,
+                     const double* initial, double* out);
 
 /* Applied current I_app (Sec. 1.1.2): pulse p adds amp (model units per ms:
  * mV/ms for TTP06, 1/ms for BO) at the nodes where mask[node] != 0 -- or,

@@ -385,3 +385,32 @@ double or_cell_step(int model, int cell, double g, int order, double dt,
     const double I = or_model_iion(model, cell, g, uE, w_new);
     return (uB + dt * (iapp - I)) / alpha;
 }
+
+void or_prepace(int model, int cell, int bdf, double dt, double period, int beats,
+                double amp, double dur, const double* init, double* out) {
+    const int ns = or_model_nstates(model);
+    double un, um, wn[OR_MAX_STATES], wm[OR_MAX_STATES], w1[OR_MAX_STATES];
+    if (init) {
+        un = init[0];
+        for (int k = 0; k < ns; ++k) wn[k] = init[1 + k];
+    } else {
+        or_model_initial(model, cell, &un, wn);
+    }
+    um = un;
+    for (int k = 0; k < ns; ++k) wm[k] = wn[k];
+    const long long kp = llround(period / dt), kd = llround(dur / dt);
+    const long long total = kp * (long long)beats;
+    for (long long m = 1; m <= total; ++m) {
+        const int order = (bdf == 2 && m >= 2) ? 2 : 1;
+        const double iapp = ((m - 1) % kp) < kd ? amp : 0.0;
+        const double u1 = or_cell_step(model, cell, 0.0, order, dt, un, wn, um, wm, iapp, w1);
+        um = un;
+        un = u1;
+        for (int k = 0; k < ns; ++k) {
+            wm[k] = wn[k];
+            wn[k] = w1[k];
+        }
+    }
+    out[0] = un;
+    for (int k = 0; k < ns; ++k) out[1 + k] = wn[k];
+}

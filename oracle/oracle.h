@@ -62,6 +62,16 @@ double or_cell_step(int model, int cell, double g_passive, int order, double dt,
                     double u_n, const double* w_n, double u_nm1,
                     const double* w_nm1, double iapp, double* w_new);
 
+/* Single-cell pre-pacing (Sec. 3.2: ionic states initialised from 0D
+ * simulations of many beats at the pacing period): beats beats of
+ * or_cell_step under a pulse of amp lasting dur every period ms from t = 0
+ * (the pulse is on for the new level m when (m - 1) mod kp < kd, kp =
+ * round(period/dt), kd = round(dur/dt)); order bdf (a BDF1 first step).
+ * init: NULL (or_model_initial) or u then the states; out: u then the
+ * states at the end. */
+void or_prepace(int model, int cell, int bdf, double dt, double period, int beats,
+                double amp, double dur, const double* init, double* out);
+
 /* ---- Q1 finite elements (Sec. 1.2, Eq. (6)) ---------------------------- */
 
 /* Element mass and stiffness matrices (8x8, row-major, local node index

@@ -38,6 +38,7 @@ def lib():
         L.or_sim_create_regions.restype = vp
         L.or_sim_get_active.argtypes = [vp, vp]
         L.or_sim_set_pulse_weights.argtypes = [vp, i32, vp]
+        L.or_prepace.argtypes = [i32, i32, i32, d, d, i32, d, d, vp, vp]
         L.or_assemble_regions.argtypes = [i64, i64, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
         L.or_assemble_regions.restype = i32
         L.or_csr_free.argtypes = [vp]
@@ -310,3 +311,12 @@ def sim_from_problem(prob, tol=1e-12, maxit=1000, **kw):
     return Sim(m["xyz"], m["hex"], prob["f0"], prob["s0"], diffusivities(prob["cond"]),
                prob["model"], prob["dt"], prob["bdf"], cell=prob["cell"], tol=tol, maxit=maxit,
                pulses=prob["pulses"], masks=prob["masks"], act_thr=prob["act_thr"], **kw)
+
+
+def prepace(model, cell, period, beats, dt, amp, dur, bdf=2, init=None):
+    """Single-cell pre-pacing (or_prepace): u and the states at the end."""
+    ns = lib().or_model_nstates(model)
+    out = np.zeros(1 + ns)
+    ini = None if init is None else _f64(init)
+    lib().or_prepace(model, cell, bdf, dt, period, beats, amp, dur, _p(ini), _p(out))
+    return out

@@ -41,6 +41,8 @@ void launch_resid_np_batch(const Batch& B, int graph, int grid, cudaStream_t s);
 void launch_finish_batch(const Batch& B, int grid, cudaStream_t s);
 cudaError_t launch_pcg32_batch(const Batch& B, int grid, cudaStream_t s);
 void launch_batch_cond(Dev* const* devs, int n, const unsigned long long* h, cudaStream_t s);
+cudaError_t launch_prepace(int model, const uint8_t* cells, int ncell, double dt, long long m0, long long nsteps,
+                           long long kp, long long kd, double amp, int bdf, double* st, cudaStream_t s);
 void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s);
 int mf_tiles(const Dev& h);
 cudaError_t mf_prepare();
@@ -267,6 +269,11 @@ ep_status validate(const ep_mesh* mesh, const ep_fibers* fib, const ep_conductiv
     if (ionic->cell_type)
         for (int64_t i = 0; i < nn; ++i)
             if (ionic->cell_type[i] > EP_CELL_EPI) return fail(EP_EINVAL, "cell_type out of range");
+    if (ionic->initial) {
+        const int S1 = 1 + (ionic->model == EP_MODEL_BO ? epk::kBOStates : epk::kTTGates + epk::kTTConc);
+        for (int k = 0; k < 3 * S1; ++k)
+            if (!std::isfinite(ionic->initial[k])) return fail(EP_EINVAL, "ionic.initial must be finite");
+    }
     if (stim) {
         if (stim->n_pulses < 0 || stim->n_pulses > EP_MAX_PULSES)
             return fail(EP_EINVAL, "stimulus.n_pulses must be in 0..4");
@@ -725,49 +732,57 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         if (ionic->cell_type) std::memcpy(ct.data(), ionic->cell_type, N);
         CUDA_TRY(cudaMemcpyAsync(cell, ct.data(), N, cudaMemcpyHostToDevice, I->stream));
         CUDA_TRY(cudaStreamSynchronize(I->stream));
-        const double u0 = h.model == EP_MODEL_BO ? 0.0 : epk::kTTInitialV;
-        std::vector<double> uv(N, u0);
+        // initial u and states per cell type: given (e.g. pre-paced), or the
+        // model's rest / the paper's epicardial values for every type
+        const int S1 = 1 + z.ns;
+        std::vector<double> tab(3 * S1);
+        for (int c = 0; c < 3; ++c) {
+            if (ionic->initial) {
+                for (int k = 0; k < S1; ++k) tab[c * S1 + k] = ionic->initial[c * S1 + k];
+            } else if (h.model == EP_MODEL_BO) {
+                const double bo[4] = {0.0, 1.0, 1.0, 0.0};
+                for (int k = 0; k < S1; ++k) tab[c * S1 + k] = bo[k];
+            } else {
+                tab[c * S1] = epk::kTTInitialV;
+                for (int k = 0; k < z.ns; ++k) tab[c * S1 + 1 + k] = epk::tt_initial(k);
+            }
+        }
+        auto init = [&](size_t n, int k) { return tab[(size_t)ct[n] * S1 + k]; };  // k = 0: u
+        std::vector<double> uv(N);
+        for (size_t n = 0; n < N; ++n) uv[n] = init(n, 0);
         CUDA_TRY(cudaMemcpy(h.u_n, uv.data(), N * 8, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(h.u_nm1, uv.data(), N * 8, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(h.u_new, uv.data(), N * 8, cudaMemcpyHostToDevice));
-        std::vector<double> w0(z.ns);
-        if (h.model == EP_MODEL_BO) {
-            w0 = {1.0, 1.0, 0.0};
-        } else {
-            for (int k = 0; k < z.ns; ++k) w0[k] = epk::tt_initial(k);
-        }
         if (z.ng32) {
             std::vector<float> g(z.ng32 * N);
             for (int k = 0; k < z.ng32; ++k)
-                for (size_t n = 0; n < N; ++n) g[k * N + n] = (float)w0[k];
+                for (size_t n = 0; n < N; ++n) g[k * N + n] = (float)init(n, 1 + k);
             CUDA_TRY(cudaMemcpy(h.g32_n, g.data(), g.size() * 4, cudaMemcpyHostToDevice));
             CUDA_TRY(cudaMemcpy(h.g32_nm1, g.data(), g.size() * 4, cudaMemcpyHostToDevice));
         }
         if (z.ns64 && !ref) {
             std::vector<double> c(z.ns64 * N);
             for (int k = 0; k < z.ns64; ++k)
-                for (size_t n = 0; n < N; ++n) c[k * N + n] = w0[k];
+                for (size_t n = 0; n < N; ++n) c[k * N + n] = init(n, 1 + k);
             CUDA_TRY(cudaMemcpy(h.s64_n, c.data(), c.size() * 8, cudaMemcpyHostToDevice));
             CUDA_TRY(cudaMemcpy(h.s64_nm1, c.data(), c.size() * 8, cudaMemcpyHostToDevice));
         }
         if (z.ns64 && ref) {
             // float-float concentrations: [hi][k][N] then [lo][k][N]
             std::vector<float> c(2 * z.ns64 * N);
-            for (int k = 0; k < z.ns64; ++k) {
-                float hi, lo;
-                split_ff(w0[z.ng32 + k], hi, lo);
+            for (int k = 0; k < z.ns64; ++k)
                 for (size_t n = 0; n < N; ++n) {
+                    float hi, lo;
+                    split_ff(init(n, 1 + z.ng32 + k), hi, lo);
                     c[k * N + n] = hi;
                     c[(z.ns64 + k) * N + n] = lo;
                 }
-            }
             CUDA_TRY(cudaMemcpy(h.s64_n, c.data(), c.size() * 4, cudaMemcpyHostToDevice));
             CUDA_TRY(cudaMemcpy(h.s64_nm1, c.data(), c.size() * 4, cudaMemcpyHostToDevice));
         }
         if (ref) {
-            float hi, lo;
-            split_ff(u0, hi, lo);
-            std::vector<float> fh(N, hi), fl(N, lo), fb(N, -INFINITY);
+            std::vector<float> fh(N), fl(N), fb(N, -INFINITY);
+            for (size_t n = 0; n < N; ++n) split_ff(uv[n], fh[n], fl[n]);
             for (float* d : {h.uh_n, h.uh_m}) CUDA_TRY(cudaMemcpy(d, fh.data(), N * 4, cudaMemcpyHostToDevice));
             for (float* d : {h.ul_n, h.ul_m}) CUDA_TRY(cudaMemcpy(d, fl.data(), N * 4, cudaMemcpyHostToDevice));
             CUDA_TRY(cudaMemcpy(h.bestf, fb.data(), N * 4, cudaMemcpyHostToDevice));
@@ -1126,6 +1141,67 @@ ep_status ep_create(const ep_mesh* mesh, const ep_fibers* fibers, const ep_condu
         return st;
     }
     *out = I;
+    return EP_OK;
+}
+
+ep_status ep_prepace(int32_t model, const uint8_t* cell_types, int32_t n_cells, double period_ms, int32_t beats,
+                     double dt, double amp, double dur_ms, int32_t bdf_order, const double* initial,
+                     double* out) {
+    if (model != EP_MODEL_BO && model != EP_MODEL_TTP06) return fail(EP_EINVAL, "model");
+    if (!cell_types || !out || n_cells < 1 || n_cells > 4096) return fail(EP_EINVAL, "cells / out / n_cells");
+    for (int i = 0; i < n_cells; ++i)
+        if (cell_types[i] > EP_CELL_EPI) return fail(EP_EINVAL, "cell type out of range");
+    if (!finite_pos(dt) || !finite_pos(period_ms) || beats < 0 || !std::isfinite(amp) || !(dur_ms >= 0))
+        return fail(EP_EINVAL, "pacing parameters");
+    if (bdf_order != 1 && bdf_order != 2) return fail(EP_EINVAL, "bdf_order must be 1 or 2");
+    const long long kp = llround(period_ms / dt), kd = llround(dur_ms / dt);
+    if (kp < 1) return fail(EP_EINVAL, "period shorter than a step");
+    const int ns = model == EP_MODEL_BO ? epk::kBOStates : epk::kTTGates + epk::kTTConc;
+    const int S1 = 1 + ns;
+    constexpr int P = 1 + epk::kTTGates + epk::kTTConc;
+    // two levels per cell, both the initial state
+    std::vector<double> st((size_t)n_cells * 2 * P, 0.0);
+    for (int i = 0; i < n_cells; ++i) {
+        double v[P] = {0};
+        if (initial) {
+            for (int k = 0; k < S1; ++k) v[k] = initial[(size_t)i * S1 + k];
+        } else if (model == EP_MODEL_BO) {
+            v[0] = 0.0, v[1] = 1.0, v[2] = 1.0, v[3] = 0.0;
+        } else {
+            v[0] = epk::kTTInitialV;
+            for (int k = 0; k < ns; ++k) v[1 + k] = epk::tt_initial(k);
+        }
+        for (int lv = 0; lv < 2; ++lv)
+            for (int k = 0; k < S1; ++k) st[((size_t)i * 2 + lv) * P + k] = v[k];
+    }
+    double* dst = nullptr;
+    uint8_t* dcell = nullptr;
+    cudaStream_t s = nullptr;
+    auto cleanup = [&] {
+        if (dst) cudaFree(dst);
+        if (dcell) cudaFree(dcell);
+        if (s) cudaStreamDestroy(s);
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&dst, st.size() * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&dcell, (size_t)n_cells);
+    if (e == cudaSuccess) e = cudaMemcpy(dst, st.data(), st.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dcell, cell_types, (size_t)n_cells, cudaMemcpyHostToDevice);
+    // the protocol in short launches of at most one beat each
+    const long long total = kp * (long long)beats;
+    for (long long m0 = 0; e == cudaSuccess && m0 < total; m0 += kp) {
+        const long long k = std::min(kp, total - m0);
+        e = epk::launch_prepace(model, dcell, n_cells, dt, m0, k, kp, kd, amp, bdf_order, dst, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(st.data(), dst, st.size() * 8, cudaMemcpyDeviceToHost);
+    cleanup();
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(EP_ECUDA, std::string("pre-pacing: ") + cudaGetErrorString(e));
+    }
+    for (int i = 0; i < n_cells; ++i)
+        for (int k = 0; k < S1; ++k) out[(size_t)i * S1 + k] = st[((size_t)i * 2) * P + k];
     return EP_OK;
 }
 

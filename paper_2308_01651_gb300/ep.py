@@ -29,7 +29,7 @@ EP_MAX_PULSES = 4
 EXPORTS = ["ep_create", "ep_step", "ep_step_async", "ep_sync", "ep_step_batch", "ep_read_potential",
            "ep_activation_times", "ep_state_bytes", "ep_save_state", "ep_load_state",
            "ep_footprint_bytes", "ep_get_stats", "ep_potential_device", "ep_destroy", "ep_last_error",
-           "ep_profile_enable", "ep_profile_read", "ep_residual_norm_noalloc"]
+           "ep_profile_enable", "ep_profile_read", "ep_residual_norm_noalloc", "ep_prepace"]
 
 
 class EpError(RuntimeError):
@@ -58,7 +58,7 @@ class ep_conductivities(C.Structure):
 
 
 class ep_ionic_model(C.Structure):
-    _fields_ = [("model", C.c_int32), ("cell_type", C.c_void_p)]
+    _fields_ = [("model", C.c_int32), ("cell_type", C.c_void_p), ("initial", C.c_void_p)]
 
 
 class ep_pulse(C.Structure):
@@ -130,6 +130,9 @@ def lib():
         L.ep_profile_read.restype = st
         L.ep_residual_norm_noalloc.argtypes = [vp, P(C.c_double)]
         L.ep_residual_norm_noalloc.restype = st
+        d = C.c_double
+        L.ep_prepace.argtypes = [i32, vp, i32, d, i32, d, d, d, i32, vp, vp]
+        L.ep_prepace.restype = st
         L.ep_destroy.argtypes = [vp]
         L.ep_destroy.restype = st
         L.ep_last_error.argtypes = []
@@ -161,7 +164,8 @@ class _Args:
 
     def __init__(self, mesh, f0=None, s0=None, cond=None, model=EP_MODEL_TTP06, cell_type=None,
                  pulses=(), dt=0.05, bdf_order=2, precision=EP_PREC_FP64, tol=0.0, max_iter=0,
-                 inner_tol=0.0, max_sweeps=0, op32=EP_OP_AUTO, cuda_stream=None, regions=None):
+                 inner_tol=0.0, max_sweeps=0, op32=EP_OP_AUTO, cuda_stream=None, regions=None,
+                 initial=None):
         """regions: None, or dict(label=per-element uint8, sigma=[(l, t, n)
         per region] in the units of cond, excluded=[flag per region])."""
         keep = []
@@ -204,6 +208,10 @@ class _Args:
             ct = np.ascontiguousarray(cell_type, dtype=np.uint8)
             keep.append(ct)
             io.cell_type = _ptr(ct)
+        if initial is not None:
+            ini = _f64(initial)
+            keep.append(ini)
+            io.initial = _ptr(ini)
         self.ionic = io
         arr = (ep_pulse * max(len(pulses), 1))()
         for k, p in enumerate(pulses):
@@ -314,6 +322,18 @@ def ep_profile_read(h, reset=False):
     return {arr[k].name.decode(): (arr[k].launches, arr[k].ms_total) for k in range(min(n.value, cap))}
 
 
+def ep_prepace(model, cell_types, period_ms, beats, dt, amp, dur_ms, bdf_order=2, initial=None):
+    """Single-cell pre-pacing (ep.h): returns an (n_cells, 1 + S) array of u
+    and the states at the end of the last beat."""
+    ct = np.ascontiguousarray(cell_types, dtype=np.uint8)
+    S1 = 1 + (3 if model == EP_MODEL_BO else 18)
+    out = np.zeros((ct.size, S1))
+    ini = None if initial is None else _f64(np.asarray(initial).reshape(ct.size, S1))
+    _check(lib().ep_prepace(model, _ptr(ct), ct.size, period_ms, beats, dt, amp, dur_ms, bdf_order, _ptr(ini),
+                            _ptr(out)))
+    return out
+
+
 def ep_residual_norm_noalloc(h):
     """Relative FP64 residual of the last solve, computed without allocating
     (see ep.h)."""
@@ -378,7 +398,7 @@ class Instance:
         self.h = ep_create(m, prob["f0"], prob["s0"], prob["cond"], prob["model"],
                            cell_type=prob["cell"], pulses=pulses, dt=prob["dt"],
                            bdf_order=prob["bdf"], precision=precision, regions=prob.get("regions"),
-                           **opts)
+                           initial=prob.get("initial"), **opts)
 
     def step(self, n=1):
         ep_step(self.h, n)

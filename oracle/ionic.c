@@ -375,7 +375,7 @@ double or_cell_step(int model, int cell, double g, int order, double dt,
             wB[k] = 2.0 * w_n[k] - 0.5 * w_nm1[k];
             wE[k] = 2.0 * w_n[k] - w_nm1[k];
         }
-    } else {
+    } else {  /* order 1 (the single-cell step has no level n-2) */
         alpha = 1.0;
         uB = uE = u_n;
         for (int k = 0; k < ns; ++k) wB[k] = wE[k] = w_n[k];

@@ -130,7 +130,9 @@ typedef struct {
     double period;  /* ms; <= 0 means a single pulse */
 } or_pulse;
 
-/* Creates a simulation.  cell may be NULL (all epicardial).  masks holds
+/* Creates a simulation (BDF order 1, 2 or 3, ramping 1, 2, 3 over the first
+ * steps: BDF3 takes a BDF1 then a BDF2 step).  cell may be NULL (all
+ * epicardial).  masks holds
  * npulses x nn bytes (1 = node receives the pulse).  act_thr is the slope
  * (model units per ms) a node's largest forward difference must exceed to
  * count as activated. */
@@ -174,6 +176,9 @@ void or_sim_get_state(const or_sim* S, double* u_n, double* u_nm1, double* w_n,
                       double* w_nm1);
 void or_sim_set_state(or_sim* S, const double* u_n, const double* u_nm1,
                       const double* w_n, const double* w_nm1, int64_t step);
+/* Level n-2 of u and the states (BDF3), copied out / in. */
+void or_sim_get_level2(const or_sim* S, double* u_nm2, double* w_nm2);
+void or_sim_set_level2(or_sim* S, const double* u_nm2, const double* w_nm2);
 /* Activation times in ms (NaN where never activated) and the largest
  * forward difference seen so far. */
 void or_sim_get_activation(const or_sim* S, double* at, double* best);

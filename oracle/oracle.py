@@ -39,6 +39,8 @@ def lib():
         L.or_sim_get_active.argtypes = [vp, vp]
         L.or_sim_set_pulse_weights.argtypes = [vp, i32, vp]
         L.or_prepace.argtypes = [i32, i32, i32, d, d, i32, d, d, vp, vp]
+        L.or_sim_get_level2.argtypes = [vp, vp, vp]
+        L.or_sim_set_level2.argtypes = [vp, vp, vp]
         L.or_assemble_regions.argtypes = [i64, i64, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
         L.or_assemble_regions.restype = i32
         L.or_csr_free.argtypes = [vp]
@@ -242,6 +244,16 @@ class Sim:
         v = np.zeros(self.nn)
         lib().or_sim_get_iion(self.h, _p(v))
         return v
+
+    def get_level2(self):
+        u = np.zeros(self.nn)
+        w = np.zeros((self.ns, self.nn))
+        lib().or_sim_get_level2(self.h, _p(u), _p(w))
+        return u, w
+
+    def set_level2(self, u_nm2, w_nm2):
+        u, w = _f64(u_nm2), _f64(np.asarray(w_nm2).reshape(self.ns, self.nn))
+        lib().or_sim_set_level2(self.h, _p(u), _p(w))
 
     def active(self):
         a = np.zeros(self.nn, dtype=np.uint8)

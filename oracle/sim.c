@@ -34,6 +34,7 @@ struct or_sim {
     int ns;
     int64_t step;
     double *u_n, *u_nm1, *w_n, *w_nm1, *w_new;
+    double *u_nm2, *w_nm2;  /* level n-2 (BDF3) */
     double *iion, *rhs, *tmp, *u_new;
     double *at, *best;
     double act_thr;
@@ -70,7 +71,7 @@ or_sim* or_sim_create_regions(int64_t nn, int64_t ne, const double* xyz,
                               int npulses, const or_pulse* pulses,
                               const uint8_t* masks, double act_thr) {
     if (npulses < 0 || npulses > OR_MAX_PULSES || nn <= 0 || ne <= 0) return NULL;
-    if (bdf_order != 1 && bdf_order != 2) return NULL;
+    if (bdf_order < 1 || bdf_order > 3) return NULL;
     const int ns = or_model_nstates(model);
     if (ns < 0) return NULL;
     or_sim* S = calloc(1, sizeof(or_sim));
@@ -95,6 +96,8 @@ or_sim* or_sim_create_regions(int64_t nn, int64_t ne, const double* xyz,
     const size_t N = (size_t)nn, NS = (size_t)(ns > 0 ? ns : 1) * N;
     S->u_n = calloc(N, sizeof(double));
     S->u_nm1 = calloc(N, sizeof(double));
+    S->u_nm2 = calloc(N, sizeof(double));
+    S->w_nm2 = calloc(NS, sizeof(double));
     S->u_new = calloc(N, sizeof(double));
     S->w_n = calloc(NS, sizeof(double));
     S->w_nm1 = calloc(NS, sizeof(double));
@@ -108,8 +111,9 @@ or_sim* or_sim_create_regions(int64_t nn, int64_t ne, const double* xyz,
     for (int64_t i = 0; i < nn; ++i) {
         double u0, w0[OR_MAX_STATES];
         or_model_initial(model, S->cell[i], &u0, w0);
-        S->u_n[i] = S->u_nm1[i] = u0;
-        for (int k = 0; k < ns; ++k) S->w_n[(size_t)k * N + i] = S->w_nm1[(size_t)k * N + i] = w0[k];
+        S->u_n[i] = S->u_nm1[i] = S->u_nm2[i] = u0;
+        for (int k = 0; k < ns; ++k)
+            S->w_n[(size_t)k * N + i] = S->w_nm1[(size_t)k * N + i] = S->w_nm2[(size_t)k * N + i] = w0[k];
         S->at[i] = NAN;
         S->best[i] = -INFINITY;
     }
@@ -124,7 +128,7 @@ void or_sim_destroy(or_sim* S) {
     if (!S) return;
     or_csr_free(&S->A);
     free(S->cell);
-    free(S->u_n); free(S->u_nm1); free(S->u_new);
+    free(S->u_n); free(S->u_nm1); free(S->u_new); free(S->u_nm2); free(S->w_nm2);
     free(S->w_n); free(S->w_nm1); free(S->w_new);
     free(S->iion); free(S->rhs); free(S->tmp);
     free(S->at); free(S->best); free(S->masks); free(S->iapp_extra);
@@ -147,8 +151,9 @@ static int pulse_active(const or_pulse* P, double dt, int64_t m) {
 static int step_once(or_sim* S) {
     const int64_t N = S->nn;
     const int ns = S->ns;
-    const int order = (S->bdf == 2 && S->step >= 1) ? 2 : 1;
-    const double alpha = order == 2 ? 1.5 : 1.0;
+    /* order ramps 1, 2, 3 over the first steps up to the scheme's order */
+    const int order = S->bdf < S->step + 1 ? S->bdf : (int)(S->step + 1);
+    const double alpha = order == 3 ? 11.0 / 6.0 : (order == 2 ? 1.5 : 1.0);
     const double dt = S->dt;
     const int64_t m = S->step + 1;  /* index of the new time level */
     const double t_new = (double)m * dt;
@@ -160,17 +165,29 @@ static int step_once(or_sim* S) {
     /* 1-2: ionic states and current at every node (Eq. (4), ICI) */
     for (int64_t i = 0; i < N; ++i) {
         double uB, uE, wB[OR_MAX_STATES], wE[OR_MAX_STATES], a[OR_MAX_STATES], b[OR_MAX_STATES], wn[OR_MAX_STATES];
-        const double un = S->u_n[i], unm1 = S->u_nm1[i];
-        if (order == 2) {
+        const double un = S->u_n[i], unm1 = S->u_nm1[i], unm2 = S->u_nm2[i];
+        /* BDF combinations: f_BDF and the extrapolation f_EXT of the order */
+        if (order == 3) {
+            uB = 3.0 * un - 1.5 * unm1 + unm2 / 3.0;
+            uE = 3.0 * un - 3.0 * unm1 + unm2;
+        } else if (order == 2) {
             uB = 2.0 * un - 0.5 * unm1;
             uE = 2.0 * un - unm1;
         } else {
             uB = uE = un;
         }
         for (int k = 0; k < ns; ++k) {
-            const double x = S->w_n[(size_t)k * N + i], y = S->w_nm1[(size_t)k * N + i];
-            wB[k] = order == 2 ? 2.0 * x - 0.5 * y : x;
-            wE[k] = order == 2 ? 2.0 * x - y : x;
+            const size_t o = (size_t)k * N + i;
+            const double x = S->w_n[o], y = S->w_nm1[o], z = S->w_nm2[o];
+            if (order == 3) {
+                wB[k] = 3.0 * x - 1.5 * y + z / 3.0;
+                wE[k] = 3.0 * x - 3.0 * y + z;
+            } else if (order == 2) {
+                wB[k] = 2.0 * x - 0.5 * y;
+                wE[k] = 2.0 * x - y;
+            } else {
+                wB[k] = wE[k] = x;
+            }
         }
         if (!S->active[i]) {
             /* excluded from the simulation: states held, no currents */
@@ -214,8 +231,8 @@ static int step_once(or_sim* S) {
         }
     }
     double* t;
-    t = S->u_nm1; S->u_nm1 = S->u_n; S->u_n = S->u_new; S->u_new = t;
-    t = S->w_nm1; S->w_nm1 = S->w_n; S->w_n = S->w_new; S->w_new = t;
+    t = S->u_nm2; S->u_nm2 = S->u_nm1; S->u_nm1 = S->u_n; S->u_n = S->u_new; S->u_new = t;
+    t = S->w_nm2; S->w_nm2 = S->w_nm1; S->w_nm1 = S->w_n; S->w_n = S->w_new; S->w_new = t;
     S->step = m;
     if (it < 0) return -1;
     if (bad) return -2;
@@ -274,6 +291,18 @@ void or_sim_set_state(or_sim* S, const double* u_n, const double* u_nm1,
     if (w_n && NS) memcpy(S->w_n, w_n, NS * sizeof(double));
     if (w_nm1 && NS) memcpy(S->w_nm1, w_nm1, NS * sizeof(double));
     S->step = step;
+}
+
+void or_sim_get_level2(const or_sim* S, double* u_nm2, double* w_nm2) {
+    const size_t N = (size_t)S->nn, NS = (size_t)S->ns * N;
+    if (u_nm2) memcpy(u_nm2, S->u_nm2, N * sizeof(double));
+    if (w_nm2 && NS) memcpy(w_nm2, S->w_nm2, NS * sizeof(double));
+}
+
+void or_sim_set_level2(or_sim* S, const double* u_nm2, const double* w_nm2) {
+    const size_t N = (size_t)S->nn, NS = (size_t)S->ns * N;
+    if (u_nm2) memcpy(S->u_nm2, u_nm2, N * sizeof(double));
+    if (w_nm2 && NS) memcpy(S->w_nm2, w_nm2, NS * sizeof(double));
 }
 
 void or_sim_get_activation(const or_sim* S, double* at, double* best) {

@@ -21,16 +21,24 @@ import oracle.oracle as O
 from paper_2308_01651_gb300 import inputs as I
 
 
-def manufactured_run(bdf, dt, T=1.0, n=(6, 4, 3), L=(0.6, 0.4, 0.3), D=1e-2, g=0.5):
+def manufactured_run(bdf, dt, T=1.0, n=(6, 4, 3), L=(0.6, 0.4, 0.3), D=1e-2, g=0.5, start=None, t0=0.0):
+    """start: None (the exact u at t = 0, the scheme's start-up ramp), or
+    (u(t0), u(t0 - dt), u(t0 - 2 dt)) of the discrete problem, continued at
+    full order from t0."""
     m = I.slab_mesh(*n, L)
     xyz = m["xyz"]
     f0, s0 = I.uniform_fibres(xyz.shape[0])
     S = O.Sim(xyz, m["hex"], f0, s0, (D, D, D), O.PASSIVE, dt, bdf, g=g, tol=1e-13)
     shape = np.cos(math.pi * xyz[:, 0] / L[0]) * np.cos(math.pi * xyz[:, 1] / L[1]) * np.cos(math.pi * xyz[:, 2] / L[2])
     lam = math.pi ** 2 * sum(1.0 / l ** 2 for l in L)
-    S.set_state(shape, shape * math.exp(dt), np.zeros((0, xyz.shape[0])), np.zeros((0, xyz.shape[0])), 0)
-    for k in range(int(round(T / dt))):
-        t1 = (k + 1) * dt
+    z = np.zeros((0, xyz.shape[0]))
+    if start is None:
+        S.set_state(shape, shape * math.exp(dt), z, z, 0)
+    else:
+        S.set_state(start[0], start[1], z, z, 2)
+        S.set_level2(start[2], z)
+    for k in range(int(round((T - t0) / dt))):
+        t1 = t0 + (k + 1) * dt
         S.set_iapp_extra((g - 1.0 + D * lam) * math.exp(-t1) * shape)
         S.step(1)
     return S.potential()
@@ -43,6 +51,27 @@ def test_bdf_order_manufactured(bdf, lo, hi):
     errs = [np.abs(manufactured_run(bdf, dt) - ref).max() for dt in dts]
     slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
     assert all(lo < s < hi for s in slopes), (errs, slopes)
+
+
+def test_bdf3_order_manufactured():
+    """BDF3 (alpha = 11/6, f_BDF = 3 f_n - 3/2 f_{n-1} + 1/3 f_{n-2}, f_EXT =
+    3 f_n - 3 f_{n-1} + f_{n-2}) from an exact three-level history converges
+    at order 3; with its start-up ramp (a BDF1 and a BDF2 step) the first
+    steps' larger errors remain, so the slope drops towards 2 but the error
+    stays below BDF2's."""
+    T, t0 = 1.0, 0.2
+    fine = 0.1 / 2048
+    ref = manufactured_run(3, fine, T=T)
+    errs = []
+    for dt in (0.1, 0.05, 0.025):
+        # the discrete solution at t0 - 2 dt, t0 - dt, t0 from a much finer run
+        hist = [manufactured_run(3, fine, T=t0 - j * dt) for j in (0, 1, 2)]
+        errs.append(np.abs(manufactured_run(3, dt, T=T, start=hist, t0=t0) - ref).max())
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert all(2.7 < s < 3.4 for s in slopes), (errs, slopes)
+    ramp3 = np.abs(manufactured_run(3, 0.05) - manufactured_run(3, 0.05 / 64)).max()
+    bdf2 = np.abs(manufactured_run(2, 0.05) - manufactured_run(2, 0.05 / 64)).max()
+    assert ramp3 < bdf2
 
 
 @pytest.mark.parametrize("t0,dur,dt", [(0.0, 1.0, 0.05), (0.3, 0.2, 0.1), (1.0, 2.0, 0.05)])

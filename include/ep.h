@@ -172,8 +172,9 @@ typedef struct {
     const ep_pulse* pulses;
 } ep_stimulus;
 
-/* Solver options.  dt > 0 (ms); bdf_order 1 or 2 (order 2 takes a BDF1 first
- * step); tol: relative FP64 residual ||b - A u||_2 <= tol ||b||_2 (0 ->
+/* Solver options.  dt > 0 (ms); bdf_order 1, 2 or 3 (the BDF order of Sec.
+ * 1.2; the first steps ramp up, order min(bdf_order, n + 1) at step n, so
+ * order 3 takes a BDF1 then a BDF2 step); tol: relative FP64 residual ||b - A u||_2 <= tol ||b||_2 (0 ->
  * 1e-12 for FP64, 1e-10 for FP32_REFINED); max_iter: CG iterations (FP64) or
  * inner iterations per refinement sweep (0 -> 1000 / 200); inner_tol: the
  * FP32 inner solve of a sweep stops once its residual is below 0.9 tol ||b||
@@ -245,19 +246,21 @@ ep_status ep_activation_times(const ep_instance* inst, double* out_ms, int64_t n
  *           extension below, 0 if none);
  *   double u_n[N], u_{n-1}[N]          (model units)
  *   double w_n[S][N], w_{n-1}[S][N]    (state-major; S = 3 BO, 18 TTP06)
+ * with a third level for bdf_order 3: u_n, u_{n-1}, u_{n-2}, then w_n,
+ * w_{n-1}, w_{n-2} (L = 3 levels, else L = 2),
  *   double at[N]                       (time of the largest slope, ms)
  *   double best[N]                     (largest u_{n+1} - u_n, model units)
  * FP32_REFINED instances append an extension with their float-float working
  * state, so that a restart continues bit for bit: char tag[8] = "EPFFEXT1";
- * int32 hist (valid A u history levels, 0..2); int32 0; then float arrays
- * of N: u_n hi, lo, u_{n-1} hi, lo; the TTP06 concentrations of level n and
- * n-1, each [2][5][N] (hi parts, then lo parts; absent for BO); A u of step
- * n hi, lo and of step n-1 hi, lo.  The portable part alone is a complete
+ * int32 hist (valid A u history levels, 0..L); int32 0; then float arrays
+ * of N: u hi, lo of each level (n first); the TTP06 concentrations of each
+ * level, [2][5][N] (hi parts, then lo parts; absent for BO); A u hi, lo of
+ * each level's step.  The portable part alone is a complete
  * state: any instance of the same model and size loads it (a refined
  * instance then splits the doubles into pairs and rebuilds its history
  * within two steps).  ep_state_bytes gives the size of this instance's
- * buffer.  ep_load_state requires the same model and n_nodes and at least
- * the portable part; it also resets the stimulus clock to the loaded step. */
+ * buffer.  ep_load_state requires the same model, n_nodes and number of
+ * levels and at least the portable part; it also resets the stimulus clock to the loaded step. */
 size_t ep_state_bytes(const ep_instance* inst);
 ep_status ep_save_state(const ep_instance* inst, void* buf, size_t bytes);
 ep_status ep_load_state(ep_instance* inst, const void* buf, size_t bytes);

@@ -187,6 +187,7 @@ struct Sizes {
     bool slab;
     bool regions;     // the mesh carries subdomain labels
     bool slab_mass;   // the refined path applies the analytic slab mass matrix
+    int levels;       // time levels kept: 3 for BDF3, else 2
 };
 
 // float-float pair (nearest float, then the nearest float of the rest)
@@ -213,9 +214,10 @@ size_t footprint(const Sizes& z) {
     auto al = [](size_t b) { return ((b + 255) / 256) * 256; };
     const size_t N = (size_t)z.N;
     size_t b = 0;
-    b += 3 * al(N * 8);                   // u_n, u_nm1, u_new
-    b += 2 * al(z.ng32 * N * 4);          // gates (refined)
-    b += 2 * al(z.ns64 * N * 8);          // FP64 states
+    const size_t L = (size_t)z.levels;
+    b += (L + 1) * al(N * 8);             // u_n, u_nm1 (, u_nm2), u_new
+    b += L * al(z.ng32 * N * 4);          // gates (refined)
+    b += L * al(z.ns64 * N * 8);          // FP64 states
     b += al(N);                           // cell types
     if (z.regions) b += al(N);            // active-node flags
     if (z.prec != EP_PREC_FP32_REFINED) b += 3 * al(N * 8);  // v, b, r
@@ -229,8 +231,8 @@ size_t footprint(const Sizes& z) {
         b += 2 * al(epk::kGroups * N * 16);                              // Ahi Alo
         if (!z.slab_mass) b += 2 * al(epk::kGroups * N * 16);            // Mhi Mlo (curved / with regions)
         b += 6 * al(N * 4);                                              // u, v, b (hi, lo)
-        b += 6 * al(N * 4);                                              // A u history (hi, lo)
-        b += 5 * al(N * 4);                                              // u levels (hi, lo), best slope
+        b += (2 + 2 * L) * al(N * 4);                                    // A u history (hi, lo)
+        b += (1 + 2 * L) * al(N * 4);                                    // u levels (hi, lo), best slope
         if (z.op32 != EP_OP_STENCIL) b += al(6 * N * 4);                 // fibres
         b += 6 * al(N * 4);               // r32 z32 q32 d32 pa32 pb32
         b += al(N);                       // boundary flags
@@ -289,7 +291,7 @@ ep_status validate(const ep_mesh* mesh, const ep_fibers* fib, const ep_conductiv
         }
     }
     if (!finite_pos(opts->dt)) return fail(EP_EINVAL, "options.dt must be positive");
-    if (opts->bdf_order != 1 && opts->bdf_order != 2) return fail(EP_EINVAL, "options.bdf_order must be 1 or 2");
+    if (opts->bdf_order < 1 || opts->bdf_order > 3) return fail(EP_EINVAL, "options.bdf_order must be 1, 2 or 3");
     if (opts->precision != EP_PREC_FP64 && opts->precision != EP_PREC_FP32_REFINED)
         return fail(EP_EINVAL, "options.precision");
     if (opts->op32 < EP_OP_AUTO || opts->op32 > EP_OP_STENCIL) return fail(EP_EINVAL, "options.op32");
@@ -319,6 +321,7 @@ Sizes sizes_of(const ep_mesh* mesh, const ep_ionic_model* ionic, const ep_option
     z.N = (int)expected_nodes(mesh);
     z.ns = ionic->model == EP_MODEL_BO ? epk::kBOStates : epk::kTTGates + epk::kTTConc;
     z.prec = opts->precision;
+    z.levels = opts->bdf_order == 3 ? 3 : 2;
     z.slab = mesh->kind == EP_MESH_SLAB;
     z.regions = mesh->region != nullptr;
     // an excluded region changes M; the footprint assumes it may
@@ -336,21 +339,37 @@ Sizes sizes_of(const ep_mesh* mesh, const ep_ionic_model* ionic, const ep_option
     return z;
 }
 
+// alpha/dt of the BDF order `order` (1, 2, 3)
+double alpha_dt_of(const Dev& h, int order) { return (order == 3 ? 11.0 / 6.0 : order == 2 ? 1.5 : 1.0) / h.dt; }
+
+// alpha/dt of the step with index `step`: BDF order min(bdf, step + 1)
 double required_alpha_dt(const Dev& h, long long step) {
-    return ((h.bdf == 2 && step >= 1) ? 1.5 : 1.0) / h.dt;
+    return alpha_dt_of(h, h.bdf < step + 1 ? h.bdf : (int)(step + 1));
 }
 
-// make sure the device operators hold alpha/dt of the step about to run
+// make sure the device operators hold alpha/dt of the step about to run.
+// Raising the order goes through every order in between, as a run from
+// step 0 does (1 -> 2 -> 3), so that an instance that loads a checkpoint
+// holds bitwise the operator of the run that wrote it.
 void ensure_alpha(ep_instance* I) {
     const double need = required_alpha_dt(I->h, I->host_step);
-    if (need != I->alpha_dt_dev) {
-        const float cmass = (float)(need * I->h.h[0] * I->h.h[1] * I->h.h[2]);
-        const double delta = need - I->alpha_dt_dev;
+    if (need == I->alpha_dt_dev) return;
+    double path[3];
+    int np = 0;
+    for (int o = 1; o <= 3; ++o) {
+        const double a = alpha_dt_of(I->h, o);
+        if (a > I->alpha_dt_dev && a <= need) path[np++] = a;
+    }
+    if (need < I->alpha_dt_dev) path[np++] = need;
+    for (int k = 0; k < np; ++k) {
+        const double to = path[k];
+        const float cmass = (float)(to * I->h.h[0] * I->h.h[1] * I->h.h[2]);
+        const double delta = to - I->alpha_dt_dev;
         timed(I, K_REALPHA, [&] {
-            if (I->h.prec == EP_PREC_FP32_REFINED) epk::launch_realpha_ff(I->d, I->h, delta, need, cmass, I->stream);
-            else epk::launch_realpha(I->d, I->h, delta, need, cmass, I->stream);
+            if (I->h.prec == EP_PREC_FP32_REFINED) epk::launch_realpha_ff(I->d, I->h, delta, to, cmass, I->stream);
+            else epk::launch_realpha(I->d, I->h, delta, to, cmass, I->stream);
         });
-        I->alpha_dt_dev = need;
+        I->alpha_dt_dev = to;
     }
 }
 
@@ -626,13 +645,17 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     ALLOC(h.u_n, N);
     ALLOC(h.u_nm1, N);
     ALLOC(h.u_new, N);
+    const bool lv3 = z.levels == 3;
+    if (lv3) ALLOC(h.u_nm2, N);
     if (z.ng32) {
         ALLOC(h.g32_n, z.ng32 * N);
         ALLOC(h.g32_nm1, z.ng32 * N);
+        if (lv3) ALLOC(h.g32_nm2, z.ng32 * N);
     }
     if (z.ns64) {
         ALLOC(h.s64_n, z.ns64 * N);
         ALLOC(h.s64_nm1, z.ns64 * N);
+        if (lv3) ALLOC(h.s64_nm2, z.ns64 * N);
     }
     uint8_t* cell = nullptr;
     ALLOC(cell, N);
@@ -664,6 +687,12 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         ALLOC(h.ul_n, N);
         ALLOC(h.uh_m, N);
         ALLOC(h.ul_m, N);
+        if (lv3) {
+            ALLOC(h.uh_m2, N);
+            ALLOC(h.ul_m2, N);
+            ALLOC(h.ym2_hi, N);
+            ALLOC(h.ym2_lo, N);
+        }
         ALLOC(h.bestf, N);
         ALLOC(h.yc_hi, N);
         ALLOC(h.yc_lo, N);
@@ -751,21 +780,21 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         std::vector<double> uv(N);
         for (size_t n = 0; n < N; ++n) uv[n] = init(n, 0);
         CUDA_TRY(cudaMemcpy(h.u_n, uv.data(), N * 8, cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(h.u_nm1, uv.data(), N * 8, cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(h.u_new, uv.data(), N * 8, cudaMemcpyHostToDevice));
+        for (double* d : {h.u_nm1, h.u_nm2, h.u_new})
+            if (d) CUDA_TRY(cudaMemcpy(d, uv.data(), N * 8, cudaMemcpyHostToDevice));
         if (z.ng32) {
             std::vector<float> g(z.ng32 * N);
             for (int k = 0; k < z.ng32; ++k)
                 for (size_t n = 0; n < N; ++n) g[k * N + n] = (float)init(n, 1 + k);
-            CUDA_TRY(cudaMemcpy(h.g32_n, g.data(), g.size() * 4, cudaMemcpyHostToDevice));
-            CUDA_TRY(cudaMemcpy(h.g32_nm1, g.data(), g.size() * 4, cudaMemcpyHostToDevice));
+            for (float* d : {h.g32_n, h.g32_nm1, h.g32_nm2})
+                if (d) CUDA_TRY(cudaMemcpy(d, g.data(), g.size() * 4, cudaMemcpyHostToDevice));
         }
         if (z.ns64 && !ref) {
             std::vector<double> c(z.ns64 * N);
             for (int k = 0; k < z.ns64; ++k)
                 for (size_t n = 0; n < N; ++n) c[k * N + n] = init(n, 1 + k);
-            CUDA_TRY(cudaMemcpy(h.s64_n, c.data(), c.size() * 8, cudaMemcpyHostToDevice));
-            CUDA_TRY(cudaMemcpy(h.s64_nm1, c.data(), c.size() * 8, cudaMemcpyHostToDevice));
+            for (double* d : {h.s64_n, h.s64_nm1, h.s64_nm2})
+                if (d) CUDA_TRY(cudaMemcpy(d, c.data(), c.size() * 8, cudaMemcpyHostToDevice));
         }
         if (z.ns64 && ref) {
             // float-float concentrations: [hi][k][N] then [lo][k][N]
@@ -777,14 +806,16 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
                     c[k * N + n] = hi;
                     c[(z.ns64 + k) * N + n] = lo;
                 }
-            CUDA_TRY(cudaMemcpy(h.s64_n, c.data(), c.size() * 4, cudaMemcpyHostToDevice));
-            CUDA_TRY(cudaMemcpy(h.s64_nm1, c.data(), c.size() * 4, cudaMemcpyHostToDevice));
+            for (double* d : {h.s64_n, h.s64_nm1, h.s64_nm2})
+                if (d) CUDA_TRY(cudaMemcpy(d, c.data(), c.size() * 4, cudaMemcpyHostToDevice));
         }
         if (ref) {
             std::vector<float> fh(N), fl(N), fb(N, -INFINITY);
             for (size_t n = 0; n < N; ++n) split_ff(uv[n], fh[n], fl[n]);
-            for (float* d : {h.uh_n, h.uh_m}) CUDA_TRY(cudaMemcpy(d, fh.data(), N * 4, cudaMemcpyHostToDevice));
-            for (float* d : {h.ul_n, h.ul_m}) CUDA_TRY(cudaMemcpy(d, fl.data(), N * 4, cudaMemcpyHostToDevice));
+            for (float* d : {h.uh_n, h.uh_m, h.uh_m2})
+                if (d) CUDA_TRY(cudaMemcpy(d, fh.data(), N * 4, cudaMemcpyHostToDevice));
+            for (float* d : {h.ul_n, h.ul_m, h.ul_m2})
+                if (d) CUDA_TRY(cudaMemcpy(d, fl.data(), N * 4, cudaMemcpyHostToDevice));
             CUDA_TRY(cudaMemcpy(h.bestf, fb.data(), N * 4, cudaMemcpyHostToDevice));
         }
         std::vector<double> nanv(N, NAN), ninf(N, -INFINITY);
@@ -1330,20 +1361,34 @@ ep_status ep_activation_times(const ep_instance* I, double* out, int64_t n) {
     return EP_OK;
 }
 
+// Time levels a checkpoint holds: n, n-1 and, for BDF3, n-2.
+static int state_levels(int bdf) { return bdf == 3 ? 3 : 2; }
+
 // Refined instances append their float-float working state (tag, history
 // count, then float arrays) so that a restart continues bit for bit: the
 // potential levels, the concentrations as pairs and the A u history.
 static size_t ff_ext_bytes(const ep_instance* I) {
     if (I->h.prec != EP_PREC_FP32_REFINED) return 0;
     const size_t N = (size_t)I->h.N;
+    const size_t L = (size_t)state_levels(I->h.bdf);
     const size_t nc = I->h.model == EP_MODEL_BO ? 0 : epk::kTTConc;
-    return 16 + 4 * N * (4 + 4 * nc + 4);
+    return 16 + 4 * N * 2 * L * (2 + nc);
 }
 
 static size_t base_state_bytes(const ep_instance* I) {
     const size_t N = (size_t)I->h.N;
-    return 64 + 8 * N * (2 + 2 * (size_t)I->h.ns + 2);
+    const size_t L = (size_t)state_levels(I->h.bdf);
+    return 64 + 8 * N * (L + L * (size_t)I->h.ns + 2);
 }
+
+// the level-l buffers (0: n, 1: n-1, 2: n-2) of a device state copy
+static double* lvl_u(const Dev& t, int l) { return l == 0 ? t.u_n : l == 1 ? t.u_nm1 : t.u_nm2; }
+static float* lvl_g(const Dev& t, int l) { return l == 0 ? t.g32_n : l == 1 ? t.g32_nm1 : t.g32_nm2; }
+static double* lvl_s(const Dev& t, int l) { return l == 0 ? t.s64_n : l == 1 ? t.s64_nm1 : t.s64_nm2; }
+static float* lvl_uh(const Dev& t, int l) { return l == 0 ? t.uh_n : l == 1 ? t.uh_m : t.uh_m2; }
+static float* lvl_ul(const Dev& t, int l) { return l == 0 ? t.ul_n : l == 1 ? t.ul_m : t.ul_m2; }
+static float* lvl_yh(const Dev& t, int l) { return l == 0 ? t.yn_hi : l == 1 ? t.ym_hi : t.ym2_hi; }
+static float* lvl_yl(const Dev& t, int l) { return l == 0 ? t.yn_lo : l == 1 ? t.ym_lo : t.ym2_lo; }
 
 size_t ep_state_bytes(const ep_instance* I) {
     if (!I) return 0;
@@ -1389,34 +1434,35 @@ ep_status ep_save_state(const ep_instance* I, void* buf, size_t bytes) {
         std::memcpy(dst, tmp.data(), N * 8);
         return e;
     };
-    CUDA_TRY(get(t.u_n, o));
-    CUDA_TRY(get(t.u_nm1, o + N));
+    const int L = state_levels(I->h.bdf);
+    for (int lvl = 0; lvl < L; ++lvl) CUDA_TRY(get(lvl_u(t, lvl), o + (size_t)lvl * N));
     const bool ref = I->h.prec == EP_PREC_FP32_REFINED;
     const int ng32 = ref ? (I->h.model == EP_MODEL_BO ? 3 : epk::kTTGates) : 0;
     const int nc = ns - ng32;  // refined: float-float concentrations
     std::vector<float> f(N), fl(N);
-    for (int lvl = 0; lvl < 2; ++lvl) {
-        double* dst = o + 2 * N + (size_t)lvl * ns * N;
+    for (int lvl = 0; lvl < L; ++lvl) {
+        double* dst = o + (size_t)L * N + (size_t)lvl * ns * N;
         for (int k = 0; k < ns; ++k) {
             if (k < ng32) {
-                const float* src = (lvl == 0 ? t.g32_n : t.g32_nm1) + (size_t)k * N;
+                const float* src = lvl_g(t, lvl) + (size_t)k * N;
                 CUDA_TRY(cudaMemcpy(f.data(), src, N * 4, cudaMemcpyDeviceToHost));
                 for (size_t n = 0; n < N; ++n) tmp[n] = f[n];
                 std::memcpy(dst + (size_t)k * N, tmp.data(), N * 8);
             } else if (ref) {
-                const float* src = reinterpret_cast<const float*>(lvl == 0 ? t.s64_n : t.s64_nm1);
+                const float* src = reinterpret_cast<const float*>(lvl_s(t, lvl));
                 CUDA_TRY(cudaMemcpy(f.data(), src + (size_t)(k - ng32) * N, N * 4, cudaMemcpyDeviceToHost));
                 CUDA_TRY(cudaMemcpy(fl.data(), src + (size_t)(nc + k - ng32) * N, N * 4, cudaMemcpyDeviceToHost));
                 for (size_t n = 0; n < N; ++n) tmp[n] = (double)f[n] + (double)fl[n];
                 std::memcpy(dst + (size_t)k * N, tmp.data(), N * 8);
             } else {
-                const double* src = (lvl == 0 ? t.s64_n : t.s64_nm1) + (size_t)k * N;
+                const double* src = lvl_s(t, lvl) + (size_t)k * N;
                 CUDA_TRY(get(src, dst + (size_t)k * N));
             }
         }
     }
-    CUDA_TRY(get(t.at, o + (2 + 2 * (size_t)ns) * N));
-    CUDA_TRY(get_best(I, o + (3 + 2 * (size_t)ns) * N));
+    const size_t oat = (size_t)L * (1 + ns) * N;  // at, then best
+    CUDA_TRY(get(t.at, o + oat));
+    CUDA_TRY(get_best(I, o + oat + N));
     if (ref) {
         char* e = p + base_state_bytes(I);
         std::memcpy(e, "EPFFEXT1", 8);
@@ -1430,12 +1476,18 @@ ep_status ep_save_state(const ep_instance* I, void* buf, size_t bytes) {
             q += N * 4;
             return err;
         };
-        for (const float* d : {t.uh_n, t.ul_n, t.uh_m, t.ul_m}) CUDA_TRY(getf(d));
-        for (int lvl = 0; lvl < 2; ++lvl) {
-            const float* c = reinterpret_cast<const float*>(lvl == 0 ? t.s64_n : t.s64_nm1);
+        for (int lvl = 0; lvl < L; ++lvl) {
+            CUDA_TRY(getf(lvl_uh(t, lvl)));
+            CUDA_TRY(getf(lvl_ul(t, lvl)));
+        }
+        for (int lvl = 0; lvl < L; ++lvl) {
+            const float* c = reinterpret_cast<const float*>(lvl_s(t, lvl));
             for (int k = 0; k < 2 * nc; ++k) CUDA_TRY(getf(c + (size_t)k * N));
         }
-        for (const float* d : {t.yn_hi, t.yn_lo, t.ym_hi, t.ym_lo}) CUDA_TRY(getf(d));
+        for (int lvl = 0; lvl < L; ++lvl) {
+            CUDA_TRY(getf(lvl_yh(t, lvl)));
+            CUDA_TRY(getf(lvl_yl(t, lvl)));
+        }
     }
     return EP_OK;
 }
@@ -1452,6 +1504,8 @@ ep_status ep_load_state(ep_instance* I, const void* buf, size_t bytes) {
     if (H.model != I->h.model || H.n_nodes != I->h.N || H.n_states != I->h.ns)
         return fail(EP_EINVAL, "state buffer is for a different model or mesh");
     if (H.step < 0) return fail(EP_EINVAL, "negative step");
+    if (H.bdf_order < 1 || H.bdf_order > 3 || state_levels(H.bdf_order) != state_levels(I->h.bdf))
+        return fail(EP_EINVAL, "state buffer holds a different number of time levels (BDF order)");
     CUDA_TRY(cudaStreamSynchronize(I->stream));
     Dev t;
     CUDA_TRY(cudaMemcpy(&t, I->d, sizeof(Dev), cudaMemcpyDeviceToHost));
@@ -1463,45 +1517,45 @@ ep_status ep_load_state(ep_instance* I, const void* buf, size_t bytes) {
         std::memcpy(tmp.data(), src, N * 8);
         return cudaMemcpy(d, tmp.data(), N * 8, cudaMemcpyHostToDevice);
     };
-    CUDA_TRY(put(t.u_n, o));
-    CUDA_TRY(put(t.u_nm1, o + N));
+    const int L = state_levels(I->h.bdf);
+    for (int lvl = 0; lvl < L; ++lvl) CUDA_TRY(put(lvl_u(t, lvl), o + (size_t)lvl * N));
     const bool ref = I->h.prec == EP_PREC_FP32_REFINED;
     const int ng32 = ref ? (I->h.model == EP_MODEL_BO ? 3 : epk::kTTGates) : 0;
     const int nc = ns - ng32;  // refined: float-float concentrations
     std::vector<float> f(N), fl(N);
-    for (int lvl = 0; lvl < 2; ++lvl) {
-        const double* src = o + 2 * N + (size_t)lvl * ns * N;
+    for (int lvl = 0; lvl < L; ++lvl) {
+        const double* src = o + (size_t)L * N + (size_t)lvl * ns * N;
         for (int k = 0; k < ns; ++k) {
             if (k < ng32) {
                 std::memcpy(tmp.data(), src + (size_t)k * N, N * 8);
                 for (size_t n = 0; n < N; ++n) f[n] = (float)tmp[n];
-                CUDA_TRY(cudaMemcpy((lvl == 0 ? t.g32_n : t.g32_nm1) + (size_t)k * N, f.data(), N * 4,
-                                    cudaMemcpyHostToDevice));
+                CUDA_TRY(cudaMemcpy(lvl_g(t, lvl) + (size_t)k * N, f.data(), N * 4, cudaMemcpyHostToDevice));
             } else if (ref) {
                 std::memcpy(tmp.data(), src + (size_t)k * N, N * 8);
                 for (size_t n = 0; n < N; ++n) split_ff(tmp[n], f[n], fl[n]);
-                float* d = reinterpret_cast<float*>(lvl == 0 ? t.s64_n : t.s64_nm1);
+                float* d = reinterpret_cast<float*>(lvl_s(t, lvl));
                 CUDA_TRY(cudaMemcpy(d + (size_t)(k - ng32) * N, f.data(), N * 4, cudaMemcpyHostToDevice));
                 CUDA_TRY(cudaMemcpy(d + (size_t)(nc + k - ng32) * N, fl.data(), N * 4, cudaMemcpyHostToDevice));
             } else {
-                CUDA_TRY(put((lvl == 0 ? t.s64_n : t.s64_nm1) + (size_t)k * N, src + (size_t)k * N));
+                CUDA_TRY(put(lvl_s(t, lvl) + (size_t)k * N, src + (size_t)k * N));
             }
         }
     }
+    const size_t oat = (size_t)L * (1 + ns) * N;  // at, then best
     if (ref) {
-        // the float-float potential levels from the two stored potentials
-        for (int lvl = 0; lvl < 2; ++lvl) {
+        // the float-float potential levels from the stored potentials
+        for (int lvl = 0; lvl < L; ++lvl) {
             const double* src = o + (size_t)lvl * N;
             for (size_t n = 0; n < N; ++n) split_ff(src[n], f[n], fl[n]);
-            CUDA_TRY(cudaMemcpy(lvl == 0 ? t.uh_n : t.uh_m, f.data(), N * 4, cudaMemcpyHostToDevice));
-            CUDA_TRY(cudaMemcpy(lvl == 0 ? t.ul_n : t.ul_m, fl.data(), N * 4, cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(lvl_uh(t, lvl), f.data(), N * 4, cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(lvl_ul(t, lvl), fl.data(), N * 4, cudaMemcpyHostToDevice));
         }
-        const double* bsrc = o + (3 + 2 * (size_t)ns) * N;
+        const double* bsrc = o + oat + N;
         for (size_t n = 0; n < N; ++n) f[n] = (float)bsrc[n];
         CUDA_TRY(cudaMemcpy(t.bestf, f.data(), N * 4, cudaMemcpyHostToDevice));
     }
-    CUDA_TRY(put(t.at, o + (2 + 2 * (size_t)ns) * N));
-    CUDA_TRY(put(t.best, o + (3 + 2 * (size_t)ns) * N));
+    CUDA_TRY(put(t.at, o + oat));
+    CUDA_TRY(put(t.best, o + oat + N));
     long long step = H.step;
     int zero = 0;
     CUDA_TRY(cudaMemcpy(&I->d->step, &step, sizeof(step), cudaMemcpyHostToDevice));
@@ -1520,19 +1574,25 @@ ep_status ep_load_state(ep_instance* I, const void* buf, size_t bytes) {
     if (ref && H.reserved[0] == (int64_t)ext && bytes >= need && std::memcmp(e, "EPFFEXT1", 8) == 0) {
         int32_t hh = 0;
         std::memcpy(&hh, e + 8, 4);
-        hist = std::max(0, std::min(2, (int)hh));
+        hist = std::max(0, std::min(L, (int)hh));
         const char* q = e + 16;
         auto putf = [&](float* d) -> cudaError_t {
             std::memcpy(f.data(), q, N * 4);
             q += N * 4;
             return cudaMemcpy(d, f.data(), N * 4, cudaMemcpyHostToDevice);
         };
-        for (float* d : {t.uh_n, t.ul_n, t.uh_m, t.ul_m}) CUDA_TRY(putf(d));
-        for (int lvl = 0; lvl < 2; ++lvl) {
-            float* c = reinterpret_cast<float*>(lvl == 0 ? t.s64_n : t.s64_nm1);
+        for (int lvl = 0; lvl < L; ++lvl) {
+            CUDA_TRY(putf(lvl_uh(t, lvl)));
+            CUDA_TRY(putf(lvl_ul(t, lvl)));
+        }
+        for (int lvl = 0; lvl < L; ++lvl) {
+            float* c = reinterpret_cast<float*>(lvl_s(t, lvl));
             for (int k = 0; k < 2 * nc; ++k) CUDA_TRY(putf(c + (size_t)k * N));
         }
-        for (float* d : {t.yn_hi, t.yn_lo, t.ym_hi, t.ym_lo}) CUDA_TRY(putf(d));
+        for (int lvl = 0; lvl < L; ++lvl) {
+            CUDA_TRY(putf(lvl_yh(t, lvl)));
+            CUDA_TRY(putf(lvl_yl(t, lvl)));
+        }
     }
     CUDA_TRY(cudaMemcpy(&I->d->hist, &hist, sizeof(int), cudaMemcpyHostToDevice));
     return EP_OK;

@@ -64,10 +64,13 @@ struct Dev {
     const float* wgt32[EP_MAX_PULSES];   // pulse profiles (refined path)
     // ---- state ---------------------------------------------------------------
     double *u_n, *u_nm1, *u_new;
+    double* u_nm2;              // level n-2 (BDF3 instances only, else NULL)
     float *g32_n, *g32_nm1;     // FP32 gates [ng][N] (FP32_REFINED)
+    float* g32_nm2;             // level n-2 (BDF3)
     double *s64_n, *s64_nm1;    // FP64: all states [ns][N] in double.  FP32_REFINED:
                                 // the TTP06 concentrations as float-float, the
                                 // memory read as float [2][5][N] (hi parts, then lo)
+    double* s64_nm2;            // level n-2 of the same (BDF3)
     const uint8_t* cell;
     const uint8_t* active;      // per node, 0 = excluded from the simulation (NULL: all active)
     double *v;                  // u_BDF/dt - I_ion + I_app (FP64 path)
@@ -82,13 +85,15 @@ struct Dev {
     // (u_n and u_nm1 hold the same values rounded to double), and the
     // activation's best slope per node in float
     float *uh_n, *ul_n, *uh_m, *ul_m;
+    float *uh_m2, *ul_m2;       // level n-2 (BDF3)
     float* bestf;
     // A u of the solve's iterate (float-float): the current step's (written by
-    // every residual evaluation, the first one included), step n's and step
-    // n-1's.  hist counts the
-    // valid past levels; with enough of them A u_EXT is their BDF
-    // extrapolation instead of an operator apply.
+    // every residual evaluation, the first one included), step n's, step
+    // n-1's (and, BDF3, step n-2's).  hist counts the valid past levels; with
+    // enough of them A u_EXT is their BDF extrapolation instead of an
+    // operator apply.
     float *yc_hi, *yc_lo, *yn_hi, *yn_lo, *ym_hi, *ym_lo;
+    float *ym2_hi, *ym2_lo;     // step n-2's (BDF3)
     int hist;
     double *at, *best;
     // ---- operators -----------------------------------------------------------
@@ -275,26 +280,58 @@ __device__ __forceinline__ Slot batch_slot(const Batch& B) {
 
 inline Batch single_batch(Dev* d) { return Batch{d, nullptr, nullptr, 1}; }
 
+// BDF order of the step about to run: the scheme's order, ramping 1, 2, 3
+// over the first steps.
+__host__ __device__ __forceinline__ int bdf_order(const Dev& D) {
+    return D.bdf < D.step + 1 ? D.bdf : (int)(D.step + 1);
+}
+
+// 1/3 as a float-float pair
+constexpr float kThirdHi = 0.333333343267f;
+constexpr float kThirdLo = -9.93410748e-9f;
+
 // End of a step (one thread, after the step's last reduction): rotation of
 // the time levels by pointer swaps (potentials, ionic states; refined: the
 // float-float potential levels and the A u history), the step counter and
 // the per-step statistics.
 __device__ __forceinline__ void end_of_step(Dev& D) {
-    double* t = D.u_nm1;
+    // potentials (double): new -> n -> n-1 (-> n-2), the oldest buffer
+    // takes the next step's new level
+    double* t = D.u_nm2 ? D.u_nm2 : D.u_nm1;
+    if (D.u_nm2) D.u_nm2 = D.u_nm1;
     D.u_nm1 = D.u_n;
     D.u_n = D.u_new;
     D.u_new = t;
-    float* g = D.g32_nm1;
-    D.g32_nm1 = D.g32_n;
-    D.g32_n = g;
-    double* c = D.s64_nm1;
-    D.s64_nm1 = D.s64_n;
-    D.s64_n = c;
+    // states: the new level was written into the oldest slot
+    if (D.g32_nm2) {
+        float* g = D.g32_nm2;
+        D.g32_nm2 = D.g32_nm1;
+        D.g32_nm1 = D.g32_n;
+        D.g32_n = g;
+    } else {
+        float* g = D.g32_nm1;
+        D.g32_nm1 = D.g32_n;
+        D.g32_n = g;
+    }
+    if (D.s64_nm2) {
+        double* c = D.s64_nm2;
+        D.s64_nm2 = D.s64_nm1;
+        D.s64_nm1 = D.s64_n;
+        D.s64_n = c;
+    } else {
+        double* c = D.s64_nm1;
+        D.s64_nm1 = D.s64_n;
+        D.s64_n = c;
+    }
     if (D.u_hi) {
-        // the iterate becomes level n, level n becomes n-1, and the old
-        // n-1 buffers take the next step's iterate
-        float* ph = D.uh_m;
-        float* pl = D.ul_m;
+        // the iterate becomes level n, level n becomes n-1 (and n-1 n-2),
+        // and the oldest buffers take the next step's iterate
+        float* ph = D.uh_m2 ? D.uh_m2 : D.uh_m;
+        float* pl = D.ul_m2 ? D.ul_m2 : D.ul_m;
+        if (D.uh_m2) {
+            D.uh_m2 = D.uh_m;
+            D.ul_m2 = D.ul_m;
+        }
         D.uh_m = D.uh_n;
         D.ul_m = D.ul_n;
         D.uh_n = D.u_hi;
@@ -303,15 +340,20 @@ __device__ __forceinline__ void end_of_step(Dev& D) {
         D.u_lo = pl;
         // A u of the new solution becomes step n's; the oldest level is
         // reused for the next step's residuals
-        float* yh = D.ym_hi;
-        float* yl = D.ym_lo;
+        float* yh = D.ym2_hi ? D.ym2_hi : D.ym_hi;
+        float* yl = D.ym2_lo ? D.ym2_lo : D.ym_lo;
+        if (D.ym2_hi) {
+            D.ym2_hi = D.ym_hi;
+            D.ym2_lo = D.ym_lo;
+        }
         D.ym_hi = D.yn_hi;
         D.ym_lo = D.yn_lo;
         D.yn_hi = D.yc_hi;
         D.yn_lo = D.yc_lo;
         D.yc_hi = yh;
         D.yc_lo = yl;
-        D.hist = D.hist < 2 ? D.hist + 1 : 2;
+        const int hmax = D.ym2_hi ? 3 : 2;
+        D.hist = D.hist < hmax ? D.hist + 1 : hmax;
     }
     D.step += 1;
     D.done_step = D.step;

@@ -63,6 +63,15 @@ __device__ void rhs_finish(Dev& D, const double* t, bool FIRST, int graph, float
     }
     const bool more = !conv && !nan && D.sweeps < D.max_sweeps;
     set_cond(graph ? D.h_outer : 0ull, &D.f_outer, more ? 1u : 0u);
+    if (FIRST && !more && D.u_hi && D.hist >= bdf_order(D) && bdf_order(D) >= 2) {
+        // the step ends at its first pass with A u_EXT extrapolated from the
+        // history: that value, not an operator apply, becomes its A u.  Later
+        // extrapolations would weigh its rounding by up to 3 per step (BDF3)
+        // and compound it, so no window uses it: the history restarts after
+        // this step (end_of_step takes the count from -1 to 0).  BDF1 needs no
+        // restart: its u_EXT is u_n, so the stored value is step n's A u.
+        D.hist = -1;
+    }
     // the step's refinement is over: rotate the time levels now (the
     // finishing kernel then works on the rotated levels)
     if (!more) end_of_step(D);
@@ -74,7 +83,8 @@ __device__ void rhs_finish(Dev& D, const double* t, bool FIRST, int graph, float
 
 // FIRST: b = M v and r = b - A u_EXT, where A u_EXT comes from the stored
 // A u of the last steps when there are enough of them (BDF1: y_n; BDF2:
-// 2 y_n - y_{n-1}, the extrapolation u_EXT is made of) and from an operator
+// 2 y_n - y_{n-1}; BDF3: 3 y_n - 3 y_{n-1} + y_{n-2}, the extrapolations
+// u_EXT is made of) and from an operator
 // apply otherwise (first steps, after a BDF order change or a state load).
 // Otherwise (after a correction): y = A u, stored as the step's current A u,
 // and r = b - y with the stored b.  M v on a uniform slab needs no stored
@@ -91,7 +101,7 @@ __global__ void __launch_bounds__(kStThreads) k_rhs_ff(Batch B, int graph) {
     if (!FIRST && !D.f_outer) return;
     const size_t N = (size_t)D.N;
     const float ns = D.nscale;
-    const int order = (D.bdf == 2 && D.step >= 1) ? 2 : 1;
+    const int order = bdf_order(D);
     // FIRST: extrapolate A u_EXT from the history instead of applying A
     const bool hist = FIRST && D.hist >= order;
     const bool slab_mass = D.Mhi == nullptr;
@@ -128,6 +138,12 @@ __global__ void __launch_bounds__(kStThreads) k_rhs_ff(Batch B, int graph) {
                     if (order == 2) {
                         // 2 y_n - y_{n-1}: the doubling is exact
                         ff_sub(2.f * ah, 2.f * al, D.ym_hi[n], D.ym_lo[n], ah, al);
+                    } else if (order == 3) {
+                        // 3 (y_n - y_{n-1}) + y_{n-2}
+                        float dh, dl;
+                        ff_sub(ah, al, D.ym_hi[n], D.ym_lo[n], dh, dl);
+                        ff_mul(dh, dl, 3.f, 0.f, dh, dl);
+                        ff_sub(dh, dl, -D.ym2_hi[n], -D.ym2_lo[n], ah, al);
                     }
                 } else {
                     row_ff(D.Ahi, D.Alo, N, suh, sul, h, n, ah, al);

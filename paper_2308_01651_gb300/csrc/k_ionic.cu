@@ -37,9 +37,9 @@ struct StepConsts {
 __device__ __forceinline__ StepConsts step_consts(const Dev& D) {
     StepConsts c;
     c.dt = D.dt;
-    c.order = (D.bdf == 2 && D.step >= 1) ? 2 : 1;
-    c.alpha = c.order == 2 ? 1.5 : 1.0;
-    c.inv_alpha = c.order == 2 ? 2.0 / 3.0 : 1.0;
+    c.order = bdf_order(D);
+    c.alpha = c.order == 3 ? 11.0 / 6.0 : (c.order == 2 ? 1.5 : 1.0);
+    c.inv_alpha = c.order == 3 ? 6.0 / 11.0 : (c.order == 2 ? 2.0 / 3.0 : 1.0);
     c.inv_dt = D.inv_dt;
     c.dt_alpha = c.dt * c.inv_alpha;
     const long long m = D.step + 1;  // new time level
@@ -73,13 +73,38 @@ __device__ __forceinline__ void store_vu64(const Dev& D, int n, double v, double
     D.u_new[n] = uE;
 }
 
-// Refined path: the potential's BDF combinations from the float-float levels
-// u_n and u_{n-1}: uB = u_BDF (order 1: u_n; 2: 2 u_n - u_{n-1}/2) and uE =
-// u_EXT (order 1: u_n; 2: 2 u_n - u_{n-1}); the scalings by 2 and 1/2 are exact.
+// BDF combinations of one quantity from its levels n, n-1, n-2:
+//   order 1: B = E = x;  order 2: B = 2x - y/2, E = 2x - y;
+//   order 3: B = 3x - 3y/2 + z/3, E = 3x - 3y + z.
+template <typename T>
+__device__ __forceinline__ void bdf_comb(int order, T x, T y, T z, T& B, T& E) {
+    if (order == 3) {
+        B = T(3) * x - T(1.5) * y + z / T(3);
+        E = T(3) * x - T(3) * y + z;
+    } else if (order == 2) {
+        B = T(2) * x - T(0.5) * y;
+        E = T(2) * x - y;
+    } else {
+        B = E = x;
+    }
+}
+
+// Refined path: the potential's BDF combinations from its float-float
+// levels (the scalings by 2 and 1/2 are exact; by 3 and 1/3 float-float).
 __device__ __forceinline__ void u_bdf_ff(const Dev& D, int order, int n, float& bh, float& bl, float& eh,
                                          float& el) {
     const float h0 = D.uh_n[n], l0 = D.ul_n[n];
-    if (order == 2) {
+    if (order == 3) {
+        const float h1 = D.uh_m[n], l1 = D.ul_m[n], h2 = D.uh_m2[n], l2 = D.ul_m2[n];
+        float th, tl, ah, al, ch, cl;
+        ff_mul(h0, l0, 3.f, 0.f, th, tl);      // 3 u_n
+        ff_mul(h1, l1, 3.f, 0.f, ah, al);      // 3 u_{n-1}
+        ff_sub(th, tl, ah, al, eh, el);
+        ff_sub(eh, el, -h2, -l2, eh, el);      // + u_{n-2}
+        ff_sub(th, tl, 1.5f * h1, 1.5f * l1, bh, bl);
+        ff_mul(h2, l2, kThirdHi, kThirdLo, ch, cl);
+        ff_sub(bh, bl, -ch, -cl, bh, bl);
+    } else if (order == 2) {
         const float h1 = D.uh_m[n], l1 = D.ul_m[n];
         ff_sub(2.f * h0, 2.f * l0, 0.5f * h1, 0.5f * l1, bh, bl);
         ff_sub(2.f * h0, 2.f * l0, h1, l1, eh, el);
@@ -112,6 +137,16 @@ __device__ __forceinline__ float applied_f(const Dev& D, const StepConsts& c, in
     return s;
 }
 
+// State levels: n, n-1 and (BDF3) n-2; the new level overwrites the oldest
+// slot (n-2 for BDF3 instances, else n-1), the end of the step rotates.
+template <typename G>
+struct Levels {
+    const G* n;
+    const G* m;
+    const G* m2;  // NULL unless BDF3
+    G* out;
+};
+
 // G: arithmetic/storage type of the gates (float when refined, double in the
 // FP64 path).
 template <typename G>
@@ -120,14 +155,13 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Batch B) {
     const Dev& D = *S.D;
     const StepConsts c = step_consts(D);
     const int N = D.N;
-    G* __restrict__ wn;
-    G* __restrict__ wm;
+    Levels<G> L;
     if constexpr (sizeof(G) == 4) {
-        wn = reinterpret_cast<G*>(D.g32_n);
-        wm = reinterpret_cast<G*>(D.g32_nm1);
+        L = {reinterpret_cast<const G*>(D.g32_n), reinterpret_cast<const G*>(D.g32_nm1),
+             reinterpret_cast<const G*>(D.g32_nm2), reinterpret_cast<G*>(D.g32_nm2 ? D.g32_nm2 : D.g32_nm1)};
     } else {
-        wn = reinterpret_cast<G*>(D.s64_n);
-        wm = reinterpret_cast<G*>(D.s64_nm1);
+        L = {reinterpret_cast<const G*>(D.s64_n), reinterpret_cast<const G*>(D.s64_nm1),
+             reinterpret_cast<const G*>(D.s64_nm2), reinterpret_cast<G*>(D.s64_nm2 ? D.s64_nm2 : D.s64_nm1)};
     }
     const G dtg = G(c.dt), alg = G(c.alpha);
     for (int n = S.blk * blockDim.x + threadIdx.x; n < N; n += S.nblk * blockDim.x) {
@@ -138,25 +172,17 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Batch B) {
             u_bdf_ff(D, c.order, n, ubh, ubl, ueh, uel);
             uEg = ueh;
         } else {
-            const double un = D.u_n[n];
-            uB = uE = un;
-            if (c.order == 2) {
-                const double um = D.u_nm1[n];
-                uB = 2.0 * un - 0.5 * um;
-                uE = 2.0 * un - um;
-            }
+            bdf_comb<double>(c.order, D.u_n[n], c.order > 1 ? D.u_nm1[n] : 0.0, c.order > 2 ? D.u_nm2[n] : 0.0,
+                             uB, uE);
             uEg = uE;
         }
-        G wB[3];
-        if (c.order == 2) {
+        G wB[3], wn0[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const G x = wn[(size_t)k * N + n], y = wm[(size_t)k * N + n];
-                wB[k] = G(2) * x - G(0.5) * y;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) wB[k] = wn[(size_t)k * N + n];
+        for (int k = 0; k < 3; ++k) {
+            const size_t o = (size_t)k * N + n;
+            G E;
+            wn0[k] = L.n[o];
+            bdf_comb<G>(c.order, wn0[k], c.order > 1 ? L.m[o] : G(0), c.order > 2 ? L.m2[o] : G(0), wB[k], E);
         }
         // an excluded node: states held, no currents
         const bool on = !D.active || D.active[n];
@@ -165,8 +191,8 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Batch B) {
         BO<G>::rates(uEg, a, b);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            w1[k] = on ? (wB[k] + dtg * a[k]) / (alg + dtg * b[k]) : wn[(size_t)k * N + n];
-            wm[(size_t)k * N + n] = w1[k];
+            w1[k] = on ? (wB[k] + dtg * a[k]) / (alg + dtg * b[k]) : wn0[k];
+            L.out[(size_t)k * N + n] = w1[k];
         }
         const G I = on ? BO<G>::iion(uEg, w1[0], w1[1], w1[2]) : G(0);
         if constexpr (sizeof(G) == 4) store_vu_ff(D, n, ubh, ubl, ueh, uel, on ? applied_f(D, c, n) - I : 0.f);
@@ -174,67 +200,66 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Batch B) {
     }
 }
 
-template <typename G>
-__global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_tt(Batch B) {
-    const Slot S = batch_slot(B);
-    const Dev& D = *S.D;
-    const StepConsts c = step_consts(D);
+// The node loop of one instance at BDF order ORD (a compile-time constant,
+// so that each order keeps only its own levels live).
+template <typename G, int ORD>
+__device__ __forceinline__ void ionic_tt_nodes(const Slot& S, const Dev& D, const StepConsts& c) {
     const int N = D.N;
     const G dtg = G(c.dt), alg = G(c.alpha);
+    constexpr int ord = ORD;
     for (int n = S.blk * blockDim.x + threadIdx.x; n < N; n += S.nblk * blockDim.x) {
         const int cell = D.cell[n];
         if constexpr (sizeof(G) == 4) {
             // ---- refined: float gates, float-float concentrations and potentials
             const float* __restrict__ gn = D.g32_n;
-            float* __restrict__ gm = D.g32_nm1;
+            const float* __restrict__ gm = D.g32_nm1;
+            const float* __restrict__ gm2 = D.g32_nm2;
+            float* __restrict__ go = D.g32_nm2 ? D.g32_nm2 : D.g32_nm1;
             const float* __restrict__ chn = reinterpret_cast<const float*>(D.s64_n);
-            float* __restrict__ chm = reinterpret_cast<float*>(D.s64_nm1);
+            const float* __restrict__ chm = reinterpret_cast<const float*>(D.s64_nm1);
+            const float* __restrict__ chm2 = reinterpret_cast<const float*>(D.s64_nm2);
+            float* __restrict__ cho = reinterpret_cast<float*>(D.s64_nm2 ? D.s64_nm2 : D.s64_nm1);
             const size_t LO = (size_t)kTTConc * N;  // lo parts follow the hi parts
             float ubh, ubl, ueh, uel;
-            u_bdf_ff(D, c.order, n, ubh, ubl, ueh, uel);
-            float gB[kTTGates], gE[kTTGates];
-            float ch[kTTConc], cl[kTTConc], dc[kTTConc], cE[kTTConc];
-#pragma unroll
-            for (int k = 0; k < kTTConc; ++k) {
-                ch[k] = chn[(size_t)k * N + n];
-                cl[k] = chn[LO + (size_t)k * N + n];
-            }
-            if (c.order == 2) {
-#pragma unroll
-                for (int k = 0; k < kTTGates; ++k) {
-                    const float x = gn[(size_t)k * N + n], y = gm[(size_t)k * N + n];
-                    gB[k] = 2.f * x - 0.5f * y;
-                    gE[k] = 2.f * x - y;
-                }
-#pragma unroll
-                for (int k = 0; k < kTTConc; ++k) {
-                    // c_n - c_{n-1}: the hi parts are close, so their
-                    // difference is exact
-                    float dh, dl;
-                    ff_sub(ch[k], cl[k], chm[(size_t)k * N + n], chm[LO + (size_t)k * N + n], dh, dl);
-                    dc[k] = dh;
-                    cE[k] = ch[k] + dc[k];
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < kTTGates; ++k) gB[k] = gE[k] = gn[(size_t)k * N + n];
-#pragma unroll
-                for (int k = 0; k < kTTConc; ++k) {
-                    dc[k] = 0.f;
-                    cE[k] = ch[k];
-                }
-            }
+            u_bdf_ff(D, ord, n, ubh, ubl, ueh, uel);
             if (D.active && !D.active[n]) {
                 // excluded from the simulation: states held, no currents
 #pragma unroll
-                for (int k = 0; k < kTTGates; ++k) gm[(size_t)k * N + n] = gn[(size_t)k * N + n];
+                for (int k = 0; k < kTTGates; ++k) go[(size_t)k * N + n] = gn[(size_t)k * N + n];
 #pragma unroll
                 for (int k = 0; k < kTTConc; ++k) {
-                    chm[(size_t)k * N + n] = ch[k];
-                    chm[LO + (size_t)k * N + n] = cl[k];
+                    cho[(size_t)k * N + n] = chn[(size_t)k * N + n];
+                    cho[LO + (size_t)k * N + n] = chn[LO + (size_t)k * N + n];
                 }
                 store_vu_ff(D, n, ubh, ubl, ueh, uel, 0.f);
                 continue;
+            }
+            float gB[kTTGates], gE[kTTGates];
+            float ch[kTTConc], cl[kTTConc], d1[kTTConc], d2[kTTConc], cE[kTTConc];
+#pragma unroll
+            for (int k = 0; k < kTTConc; ++k) {
+                const size_t o = (size_t)k * N + n;
+                ch[k] = chn[o];
+                cl[k] = chn[LO + o];
+                d1[k] = d2[k] = 0.f;
+                // differences of consecutive levels: the hi parts are close,
+                // so these are (nearly) exact
+                float dh, dl;
+                if (ord > 1) {
+                    ff_sub(ch[k], cl[k], chm[o], chm[LO + o], dh, dl);
+                    d1[k] = dh;
+                }
+                if (ord > 2) {
+                    ff_sub(chm[o], chm[LO + o], chm2[o], chm2[LO + o], dh, dl);
+                    d2[k] = dh;
+                }
+                // c_EXT = c_n + (order 2) d1 + (order 3) 2 d1 - d2
+                cE[k] = ord == 3 ? ch[k] + (2.f * d1[k] - d2[k]) : ch[k] + d1[k];
+            }
+#pragma unroll
+            for (int k = 0; k < kTTGates; ++k) {
+                const size_t o = (size_t)k * N + n;
+                bdf_comb<float>(ord, gn[o], ord > 1 ? gm[o] : 0.f, ord > 2 ? gm2[o] : 0.f, gB[k], gE[k]);
             }
             float a[kTTGates], b[kTTGates], r[kTTConc];
             TT<float>::rates(cell, ueh, gE, cE[0], cE[1], cE[2], cE[3], cE[4], a, b, r);
@@ -242,18 +267,23 @@ __global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_
 #pragma unroll
             for (int k = 0; k < kTTGates; ++k) {
                 g1[k] = (gB[k] + dtg * a[k]) / (alg + dtg * b[k]);
-                gm[(size_t)k * N + n] = g1[k];
+                go[(size_t)k * N + n] = g1[k];
             }
             float c1[kTTConc];
-            const float third = 1.f / 3.f, dta = (float)c.dt_alpha;
+            const float dta = (float)c.dt_alpha;
 #pragma unroll
             for (int k = 0; k < kTTConc; ++k) {
-                // order 1: c_n + dt r;  order 2: c_n + (c_n - c_{n-1})/3 + (2/3) dt r
-                const float inc = c.order == 2 ? fmaf(third, dc[k], dta * r[k]) : dta * r[k];
+                // c_{n+1} = c_n + [(c_BDF - alpha c_n) + dt r] / alpha, with
+                // (c_BDF - alpha c_n)/alpha = d1/3 (order 2), 7/11 d1 - 2/11 d2
+                // (order 3): only the small increment is rounded to float
+                float hist = 0.f;
+                if (ord == 2) hist = d1[k] * (1.f / 3.f);
+                else if (ord == 3) hist = fmaf(7.f / 11.f, d1[k], -(2.f / 11.f) * d2[k]);
+                const float inc = fmaf(dta, r[k], hist);
                 float h1, l1;
                 ff_add_f(ch[k], cl[k], inc, h1, l1);
-                chm[(size_t)k * N + n] = h1;
-                chm[LO + (size_t)k * N + n] = l1;
+                cho[(size_t)k * N + n] = h1;
+                cho[LO + (size_t)k * N + n] = l1;
                 c1[k] = h1;
             }
             TT<float>::Cur cur;
@@ -262,56 +292,39 @@ __global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_
             store_vu_ff(D, n, ubh, ubl, ueh, uel, applied_f(D, c, n) - I);
         } else {
             // ---- FP64: every state in double
-            const double* __restrict__ gn = D.s64_n;
-            double* __restrict__ gm = D.s64_nm1;
-            const double* __restrict__ cn = D.s64_n + (size_t)kTTGates * N;
-            double* __restrict__ cm = D.s64_nm1 + (size_t)kTTGates * N;
-            const double un = D.u_n[n];
-            double uB = un, uE = un;
-            double gB[kTTGates], gE[kTTGates];
-            double cB[kTTConc], cE[kTTConc];
-            if (c.order == 2) {
-                const double um = D.u_nm1[n];
-                uB = 2.0 * un - 0.5 * um;
-                uE = 2.0 * un - um;
+            const double* __restrict__ wn = D.s64_n;
+            const double* __restrict__ wm = D.s64_nm1;
+            const double* __restrict__ wm2 = D.s64_nm2;
+            double* __restrict__ wo = D.s64_nm2 ? D.s64_nm2 : D.s64_nm1;
+            double uB, uE;
+            bdf_comb<double>(ord, D.u_n[n], ord > 1 ? D.u_nm1[n] : 0.0, ord > 2 ? D.u_nm2[n] : 0.0, uB, uE);
+            double wB[kTTGates + kTTConc], wE[kTTGates + kTTConc], w0[kTTGates + kTTConc];
 #pragma unroll
-                for (int k = 0; k < kTTGates; ++k) {
-                    const double x = gn[(size_t)k * N + n], y = gm[(size_t)k * N + n];
-                    gB[k] = 2.0 * x - 0.5 * y;
-                    gE[k] = 2.0 * x - y;
-                }
-#pragma unroll
-                for (int k = 0; k < kTTConc; ++k) {
-                    const double x = cn[(size_t)k * N + n], y = cm[(size_t)k * N + n];
-                    cB[k] = 2.0 * x - 0.5 * y;
-                    cE[k] = 2.0 * x - y;
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < kTTGates; ++k) gB[k] = gE[k] = gn[(size_t)k * N + n];
-#pragma unroll
-                for (int k = 0; k < kTTConc; ++k) cB[k] = cE[k] = cn[(size_t)k * N + n];
+            for (int k = 0; k < kTTGates + kTTConc; ++k) {
+                const size_t o = (size_t)k * N + n;
+                w0[k] = wn[o];
+                bdf_comb<double>(ord, w0[k], ord > 1 ? wm[o] : 0.0, ord > 2 ? wm2[o] : 0.0, wB[k], wE[k]);
             }
             if (D.active && !D.active[n]) {
                 // excluded from the simulation: states held, no currents
-                for (int k = 0; k < kTTGates; ++k) gm[(size_t)k * N + n] = gn[(size_t)k * N + n];
-                for (int k = 0; k < kTTConc; ++k) cm[(size_t)k * N + n] = cn[(size_t)k * N + n];
+                for (int k = 0; k < kTTGates + kTTConc; ++k) wo[(size_t)k * N + n] = w0[k];
                 store_vu64(D, n, uB * c.inv_dt, uE);
                 continue;
             }
+            const double* cE = wE + kTTGates;
             double a[kTTGates], b[kTTGates], r[kTTConc];
-            TT<double>::rates(cell, uE, gE, cE[0], cE[1], cE[2], cE[3], cE[4], a, b, r);
+            TT<double>::rates(cell, uE, wE, cE[0], cE[1], cE[2], cE[3], cE[4], a, b, r);
             double g1[kTTGates];
 #pragma unroll
             for (int k = 0; k < kTTGates; ++k) {
-                g1[k] = (gB[k] + dtg * a[k]) / (alg + dtg * b[k]);
-                gm[(size_t)k * N + n] = g1[k];
+                g1[k] = (wB[k] + dtg * a[k]) / (alg + dtg * b[k]);
+                wo[(size_t)k * N + n] = g1[k];
             }
             double c1[kTTConc];
 #pragma unroll
             for (int k = 0; k < kTTConc; ++k) {
-                c1[k] = fma(c.dt_alpha, r[k], cB[k] * c.inv_alpha);
-                cm[(size_t)k * N + n] = c1[k];
+                c1[k] = fma(c.dt_alpha, r[k], wB[kTTGates + k] * c.inv_alpha);
+                wo[(size_t)(kTTGates + k) * N + n] = c1[k];
             }
             TT<double>::Cur cur;
             TT<double>::currents(cell, uE, g1, c1[0], c1[2], c1[3], c1[4], cur);
@@ -319,6 +332,16 @@ __global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_
             store_vu64(D, n, fma(uB, c.inv_dt, applied(D, c, n) - I), uE);
         }
     }
+}
+
+template <typename G>
+__global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_tt(Batch B) {
+    const Slot S = batch_slot(B);
+    const Dev& D = *S.D;
+    const StepConsts c = step_consts(D);
+    if (c.order == 3) ionic_tt_nodes<G, 3>(S, D, c);
+    else if (c.order == 2) ionic_tt_nodes<G, 2>(S, D, c);
+    else ionic_tt_nodes<G, 1>(S, D, c);
 }
 
 void launch_ionic(Dev* d, const Dev& h, int grid, cudaStream_t s) {

@@ -353,23 +353,30 @@ HEADER = np.dtype([("magic", "S8"), ("version", "<i4"), ("model", "<i4"), ("n_no
                    ("reserved", "<i8", (2,))])
 
 
-def state_pack(model, bdf_order, dt, step, u_n, u_nm1, w_n, w_nm1, at, best):
-    """Builds an EPSTATE1 buffer (ep.h layout) from host arrays."""
+def state_pack(model, bdf_order, dt, step, u_n, u_nm1, w_n, w_nm1, at, best, u_nm2=None, w_nm2=None):
+    """Builds an EPSTATE1 buffer (ep.h layout) from host arrays; BDF3 buffers
+    carry the third level (u_nm2, w_nm2)."""
     n = len(u_n)
     ns = w_n.shape[0]
     hdr = np.zeros(1, dtype=HEADER)
     hdr["magic"], hdr["version"], hdr["model"], hdr["n_nodes"] = b"EPSTATE1", 1, model, n
     hdr["n_states"], hdr["bdf_order"], hdr["step"], hdr["dt"] = ns, bdf_order, step, dt
-    body = np.concatenate([_f64(u_n), _f64(u_nm1), _f64(w_n).ravel(), _f64(w_nm1).ravel(), _f64(at),
-                           _f64(best)])
+    us, ws = [u_n, u_nm1], [w_n, w_nm1]
+    if bdf_order == 3:
+        if u_nm2 is None or w_nm2 is None:
+            raise ValueError("a BDF3 state needs u_nm2 and w_nm2")
+        us.append(u_nm2)
+        ws.append(w_nm2)
+    body = np.concatenate([_f64(u) for u in us] + [_f64(w).ravel() for w in ws] + [_f64(at), _f64(best)])
     return np.concatenate([hdr.view(np.uint8), body.view(np.uint8)])
 
 
 def state_unpack(buf):
     hdr = np.frombuffer(buf[:64].tobytes(), dtype=HEADER)[0]
     n, ns = int(hdr["n_nodes"]), int(hdr["n_states"])
+    L = 3 if int(hdr["bdf_order"]) == 3 else 2
     # the portable part only (a refined instance's extension follows it)
-    body = np.frombuffer(buf[64:64 + 8 * n * (4 + 2 * ns)].tobytes(), dtype=np.float64).copy()
+    body = np.frombuffer(buf[64:64 + 8 * n * (L + L * ns + 2)].tobytes(), dtype=np.float64).copy()
     o = 0
 
     def take(k):
@@ -378,12 +385,14 @@ def state_unpack(buf):
         o += k
         return v
 
-    u_n, u_nm1 = take(n), take(n)
-    w_n = take(ns * n).reshape(ns, n)
-    w_nm1 = take(ns * n).reshape(ns, n)
+    us = [take(n) for _ in range(L)]
+    ws = [take(ns * n).reshape(ns, n) for _ in range(L)]
     at, best = take(n), take(n)
-    return dict(model=int(hdr["model"]), step=int(hdr["step"]), dt=float(hdr["dt"]), u_n=u_n,
-                u_nm1=u_nm1, w_n=w_n, w_nm1=w_nm1, at=at, best=best)
+    out = dict(model=int(hdr["model"]), bdf_order=int(hdr["bdf_order"]), step=int(hdr["step"]),
+               dt=float(hdr["dt"]), u_n=us[0], u_nm1=us[1], w_n=ws[0], w_nm1=ws[1], at=at, best=best)
+    if L == 3:
+        out.update(u_nm2=us[2], w_nm2=ws[2])
+    return out
 
 
 class Instance:

@@ -16,8 +16,12 @@ def oracle_to_gpu(sim, inst, prob):
     the GPU instance through ep_load_state."""
     u_n, u_nm1, w_n, w_nm1 = sim.get_state()
     at_raw, best = sim.activation_raw()
+    extra = {}
+    if prob["bdf"] == 3:
+        u_nm2, w_nm2 = sim.get_level2()
+        extra = dict(u_nm2=u_nm2, w_nm2=w_nm2)
     buf = ep.state_pack(prob["model"], prob["bdf"], prob["dt"], sim.stepindex, u_n, u_nm1, w_n,
-                        w_nm1, at_raw, best)
+                        w_nm1, at_raw, best, **extra)
     inst.load(buf)
 
 

@@ -35,7 +35,7 @@ def _args(prob, **kw):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(dt=0.0), dict(dt=-1.0), dict(bdf_order=3), dict(precision=7), dict(op32=9),
+    dict(dt=0.0), dict(dt=-1.0), dict(bdf_order=4), dict(bdf_order=0), dict(precision=7), dict(op32=9),
     dict(max_iter=-1), dict(tol=-1.0),
 ])
 def test_create_rejects_bad_options(bad):
@@ -111,3 +111,25 @@ def test_state_pack_roundtrip():
     assert st["step"] == 17 and st["model"] == 1 and st["dt"] == 0.05
     for k, name in enumerate(["u_n", "u_nm1", "w_n", "w_nm1", "at", "best"]):
         assert np.array_equal(st[name], arrs[k])
+
+
+def test_state_pack_roundtrip_bdf3():
+    """BDF3 buffers carry a third level: u_n, u_nm1, u_nm2, then w_n, w_nm1,
+    w_nm2, then at and best."""
+    n, ns = 9, 3
+    g = I.rng(4)
+    u = [g.normal(size=n) for _ in range(3)]
+    w = [g.normal(size=(ns, n)) for _ in range(3)]
+    at, best = g.normal(size=n), g.normal(size=n)
+    buf = ep.state_pack(0, 3, 0.05, 5, u[0], u[1], w[0], w[1], at, best, u_nm2=u[2], w_nm2=w[2])
+    assert buf.size == 64 + 8 * n * (3 + 3 * ns + 2)
+    body = buf[64:].view(np.float64)
+    assert np.array_equal(body[2 * n:3 * n], u[2])
+    assert np.array_equal(body[3 * n + 2 * ns * n:3 * n + 3 * ns * n], w[2].ravel())
+    st = ep.state_unpack(buf)
+    assert st["bdf_order"] == 3
+    for name, v in [("u_n", u[0]), ("u_nm1", u[1]), ("u_nm2", u[2]), ("w_nm2", w[2]), ("at", at),
+                    ("best", best)]:
+        assert np.array_equal(st[name], v)
+    with pytest.raises(ValueError):
+        ep.state_pack(0, 3, 0.05, 5, u[0], u[1], w[0], w[1], at, best)

@@ -33,7 +33,7 @@ void launch_apply32_stencil(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_apply32_mf(Dev* d, const Dev& h, cudaStream_t s);
 void launch_update32(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s);
 void launch_correct_ff(Dev* d, const Dev& h, int grid, cudaStream_t s);
-void launch_ionic_batch(const Batch& B, int model, int grid, cudaStream_t s);
+void launch_ionic_batch(const Batch& B, int model, bool lv3, int grid, cudaStream_t s);
 void launch_rhs_ff_batch(const Batch& B, int first, int graph, int grid, cudaStream_t s);
 void launch_correct_ff_batch(const Batch& B, int grid, cudaStream_t s);
 void launch_resid_np(Dev* d, const Dev& h, int graph, int grid, cudaStream_t s);
@@ -1003,9 +1003,10 @@ ep_status build_plan(BatchPlan* P) {
     if (occ <= 0) return fail(EP_ECUDA, "occupancy query of the persistent solver failed");
     const int cap = sms * occ;
     if (n > cap) return fail(EP_EINVAL, "batch larger than the persistent solver's resident blocks");
-    // host tables: all instances, then the BO and TTP06 subsets
-    std::vector<Dev*> all, bo, tt;
-    std::vector<int> s_tiles{0}, s_nodes{0}, s_pcg{0}, s_bo{0}, s_tt{0};
+    // host tables: all instances, then the ionic kernel's groups: BO, TTP06
+    // with two levels, TTP06 with three (BDF3)
+    std::vector<Dev*> all, grp[3];
+    std::vector<int> s_tiles{0}, s_nodes{0}, s_pcg{0}, s_grp[3] = {{0}, {0}, {0}};
     double total = 0.0;
     for (ep_instance* I : P->key) total += (double)I->h.N;
     // persistent solver: blocks in proportion to size, at least one each,
@@ -1031,17 +1032,17 @@ ep_status build_plan(BatchPlan* P) {
         s_tiles.push_back(s_tiles.back() + I->grid_tiles);
         s_nodes.push_back(s_nodes.back() + I->grid_nodes);
         s_pcg.push_back(s_pcg.back() + gp[i]);
-        if (I->h.model == EP_MODEL_BO) {
-            bo.push_back(I->d);
-            s_bo.push_back(s_bo.back() + I->grid_ionic);
-        } else {
-            tt.push_back(I->d);
-            s_tt.push_back(s_tt.back() + I->grid_ionic);
-        }
+        const int gi = I->h.model == EP_MODEL_BO ? 0 : (I->h.u_nm2 ? 2 : 1);
+        grp[gi].push_back(I->d);
+        s_grp[gi].push_back(s_grp[gi].back() + I->grid_ionic);
     }
     // one device buffer: pointer arrays first (8-byte aligned), then ints
-    const size_t np = all.size() + bo.size() + tt.size() + 1;  // + the loop's handle
-    const size_t ni = s_tiles.size() + s_nodes.size() + s_pcg.size() + s_bo.size() + s_tt.size();
+    size_t np = all.size() + 1;  // + the loop's handle
+    size_t ni = s_tiles.size() + s_nodes.size() + s_pcg.size();
+    for (int gi = 0; gi < 3; ++gi) {
+        np += grp[gi].size();
+        ni += s_grp[gi].size();
+    }
     std::vector<char> hbuf(np * sizeof(Dev*) + ni * sizeof(int));
     char* q = hbuf.data();
     auto put = [&](const void* src, size_t bytes) {
@@ -1053,13 +1054,12 @@ ep_status build_plan(BatchPlan* P) {
     const unsigned long long hzero = 0ull;
     const size_t o_h = put(&hzero, sizeof(hzero));
     const size_t o_all = put(all.data(), all.size() * sizeof(Dev*));
-    const size_t o_bo = put(bo.data(), bo.size() * sizeof(Dev*));
-    const size_t o_tt = put(tt.data(), tt.size() * sizeof(Dev*));
+    size_t o_grp[3], o_sgrp[3];
+    for (int gi = 0; gi < 3; ++gi) o_grp[gi] = put(grp[gi].data(), grp[gi].size() * sizeof(Dev*));
     const size_t o_st = put(s_tiles.data(), s_tiles.size() * sizeof(int));
     const size_t o_sn = put(s_nodes.data(), s_nodes.size() * sizeof(int));
     const size_t o_sp = put(s_pcg.data(), s_pcg.size() * sizeof(int));
-    const size_t o_sb = put(s_bo.data(), s_bo.size() * sizeof(int));
-    const size_t o_sx = put(s_tt.data(), s_tt.size() * sizeof(int));
+    for (int gi = 0; gi < 3; ++gi) o_sgrp[gi] = put(s_grp[gi].data(), s_grp[gi].size() * sizeof(int));
     CUDA_TRY(cudaMalloc(&P->dmem, hbuf.size()));
     CUDA_TRY(cudaMemcpy(P->dmem, hbuf.data(), hbuf.size(), cudaMemcpyHostToDevice));
     char* d = static_cast<char*>(P->dmem);
@@ -1079,8 +1079,10 @@ ep_status build_plan(BatchPlan* P) {
     Capture C{s};
     cudaGraphConditionalHandle hc = 0;
     C.chk(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    if (!bo.empty()) epk::launch_ionic_batch(mk(o_bo, o_sb, (int)bo.size(), bo[0]), EP_MODEL_BO, s_bo.back(), s);
-    if (!tt.empty()) epk::launch_ionic_batch(mk(o_tt, o_sx, (int)tt.size(), tt[0]), EP_MODEL_TTP06, s_tt.back(), s);
+    for (int gi = 0; gi < 3; ++gi)
+        if (!grp[gi].empty())
+            epk::launch_ionic_batch(mk(o_grp[gi], o_sgrp[gi], (int)grp[gi].size(), grp[gi][0]),
+                                    gi == 0 ? EP_MODEL_BO : EP_MODEL_TTP06, gi == 2, s_grp[gi].back(), s);
     epk::launch_rhs_ff_batch(Bt, 1, 0, s_tiles.back(), s);
     epk::launch_batch_cond(dall, n, dh, s);
     cudaGraph_t body = nullptr;

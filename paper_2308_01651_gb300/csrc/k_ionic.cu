@@ -200,9 +200,12 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Batch B) {
     }
 }
 
-// The node loop of one instance at BDF order ORD (a compile-time constant,
-// so that each order keeps only its own levels live).
-template <typename G, int ORD>
+// The node loop of one instance at BDF order ORD; LV3: the instance keeps a
+// third level (BDF3), into whose slot the new level goes (without one, the
+// new level overwrites level n-1 in place).  Both are compile-time so that
+// each variant keeps only its own levels and pointers live.  (Two-level
+// instances run k_ionic_tt2 below.)
+template <typename G, int ORD, bool LV3>
 __device__ __forceinline__ void ionic_tt_nodes(const Slot& S, const Dev& D, const StepConsts& c) {
     const int N = D.N;
     const G dtg = G(c.dt), alg = G(c.alpha);
@@ -211,14 +214,16 @@ __device__ __forceinline__ void ionic_tt_nodes(const Slot& S, const Dev& D, cons
         const int cell = D.cell[n];
         if constexpr (sizeof(G) == 4) {
             // ---- refined: float gates, float-float concentrations and potentials
+            // the new level goes to the n-2 slot (LV3) or over level n-1;
+            // one pointer per array, so that restrict holds
             const float* __restrict__ gn = D.g32_n;
-            const float* __restrict__ gm = D.g32_nm1;
-            const float* __restrict__ gm2 = D.g32_nm2;
-            float* __restrict__ go = D.g32_nm2 ? D.g32_nm2 : D.g32_nm1;
+            float* __restrict__ gm = D.g32_nm1;
+            float* __restrict__ gm2 = D.g32_nm2;
+            float* const go = LV3 ? gm2 : gm;  // based on gm or gm2
             const float* __restrict__ chn = reinterpret_cast<const float*>(D.s64_n);
-            const float* __restrict__ chm = reinterpret_cast<const float*>(D.s64_nm1);
-            const float* __restrict__ chm2 = reinterpret_cast<const float*>(D.s64_nm2);
-            float* __restrict__ cho = reinterpret_cast<float*>(D.s64_nm2 ? D.s64_nm2 : D.s64_nm1);
+            float* __restrict__ chm = reinterpret_cast<float*>(D.s64_nm1);
+            float* __restrict__ chm2 = reinterpret_cast<float*>(D.s64_nm2);
+            float* const cho = LV3 ? chm2 : chm;
             const size_t LO = (size_t)kTTConc * N;  // lo parts follow the hi parts
             float ubh, ubl, ueh, uel;
             u_bdf_ff(D, ord, n, ubh, ubl, ueh, uel);
@@ -293,9 +298,9 @@ __device__ __forceinline__ void ionic_tt_nodes(const Slot& S, const Dev& D, cons
         } else {
             // ---- FP64: every state in double
             const double* __restrict__ wn = D.s64_n;
-            const double* __restrict__ wm = D.s64_nm1;
-            const double* __restrict__ wm2 = D.s64_nm2;
-            double* __restrict__ wo = D.s64_nm2 ? D.s64_nm2 : D.s64_nm1;
+            double* __restrict__ wm = D.s64_nm1;
+            double* __restrict__ wm2 = D.s64_nm2;
+            double* const wo = LV3 ? wm2 : wm;
             double uB, uE;
             bdf_comb<double>(ord, D.u_n[n], ord > 1 ? D.u_nm1[n] : 0.0, ord > 2 ? D.u_nm2[n] : 0.0, uB, uE);
             double wB[kTTGates + kTTConc], wE[kTTGates + kTTConc], w0[kTTGates + kTTConc];
@@ -334,15 +339,168 @@ __device__ __forceinline__ void ionic_tt_nodes(const Slot& S, const Dev& D, cons
     }
 }
 
+// BDF3 instances (three levels)
 template <typename G>
-__global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_tt(Batch B) {
+__global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_tt3(Batch B) {
     const Slot S = batch_slot(B);
     const Dev& D = *S.D;
     const StepConsts c = step_consts(D);
-    if (c.order == 3) ionic_tt_nodes<G, 3>(S, D, c);
-    else if (c.order == 2) ionic_tt_nodes<G, 2>(S, D, c);
-    else ionic_tt_nodes<G, 1>(S, D, c);
+    if (c.order == 3) ionic_tt_nodes<G, 3, true>(S, D, c);
+    else if (c.order == 2) ionic_tt_nodes<G, 2, true>(S, D, c);
+    else ionic_tt_nodes<G, 1, true>(S, D, c);
 }
+
+// Instances with two levels (BDF1, BDF2): the new level overwrites level n-1
+// in place.  A kernel of its own, written for orders 1 and 2 only, so that
+// its register allocation is not shaped by the three-level variant (this
+// one sits at the 80-register cap of three resident blocks per SM).
+template <typename G>
+__global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_tt2(Batch B) {
+    const Slot S = batch_slot(B);
+    const Dev& D = *S.D;
+    const StepConsts c = step_consts(D);
+    const int N = D.N;
+    const G dtg = G(c.dt), alg = G(c.alpha);
+    for (int n = S.blk * blockDim.x + threadIdx.x; n < N; n += S.nblk * blockDim.x) {
+        const int cell = D.cell[n];
+        if constexpr (sizeof(G) == 4) {
+            // ---- refined: float gates, float-float concentrations and potentials
+            const float* __restrict__ gn = D.g32_n;
+            float* __restrict__ gm = D.g32_nm1;
+            const float* __restrict__ chn = reinterpret_cast<const float*>(D.s64_n);
+            float* __restrict__ chm = reinterpret_cast<float*>(D.s64_nm1);
+            const size_t LO = (size_t)kTTConc * N;  // lo parts follow the hi parts
+            float ubh, ubl, ueh, uel;
+            u_bdf_ff(D, c.order, n, ubh, ubl, ueh, uel);
+            float gB[kTTGates], gE[kTTGates];
+            float ch[kTTConc], cl[kTTConc], dc[kTTConc], cE[kTTConc];
+#pragma unroll
+            for (int k = 0; k < kTTConc; ++k) {
+                ch[k] = chn[(size_t)k * N + n];
+                cl[k] = chn[LO + (size_t)k * N + n];
+            }
+            if (c.order == 2) {
+#pragma unroll
+                for (int k = 0; k < kTTGates; ++k) {
+                    const float x = gn[(size_t)k * N + n], y = gm[(size_t)k * N + n];
+                    gB[k] = 2.f * x - 0.5f * y;
+                    gE[k] = 2.f * x - y;
+                }
+#pragma unroll
+                for (int k = 0; k < kTTConc; ++k) {
+                    // c_n - c_{n-1}: the hi parts are close, so their
+                    // difference is exact
+                    float dh, dl;
+                    ff_sub(ch[k], cl[k], chm[(size_t)k * N + n], chm[LO + (size_t)k * N + n], dh, dl);
+                    dc[k] = dh;
+                    cE[k] = ch[k] + dc[k];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kTTGates; ++k) gB[k] = gE[k] = gn[(size_t)k * N + n];
+#pragma unroll
+                for (int k = 0; k < kTTConc; ++k) {
+                    dc[k] = 0.f;
+                    cE[k] = ch[k];
+                }
+            }
+            if (D.active && !D.active[n]) {
+                // excluded from the simulation: states held, no currents
+#pragma unroll
+                for (int k = 0; k < kTTGates; ++k) gm[(size_t)k * N + n] = gn[(size_t)k * N + n];
+#pragma unroll
+                for (int k = 0; k < kTTConc; ++k) {
+                    chm[(size_t)k * N + n] = ch[k];
+                    chm[LO + (size_t)k * N + n] = cl[k];
+                }
+                store_vu_ff(D, n, ubh, ubl, ueh, uel, 0.f);
+                continue;
+            }
+            float a[kTTGates], b[kTTGates], r[kTTConc];
+            TT<float>::rates(cell, ueh, gE, cE[0], cE[1], cE[2], cE[3], cE[4], a, b, r);
+            float g1[kTTGates];
+#pragma unroll
+            for (int k = 0; k < kTTGates; ++k) {
+                g1[k] = (gB[k] + dtg * a[k]) / (alg + dtg * b[k]);
+                gm[(size_t)k * N + n] = g1[k];
+            }
+            float c1[kTTConc];
+            const float third = 1.f / 3.f, dta = (float)c.dt_alpha;
+#pragma unroll
+            for (int k = 0; k < kTTConc; ++k) {
+                // order 1: c_n + dt r;  order 2: c_n + (c_n - c_{n-1})/3 + (2/3) dt r
+                const float inc = c.order == 2 ? fmaf(third, dc[k], dta * r[k]) : dta * r[k];
+                float h1, l1;
+                ff_add_f(ch[k], cl[k], inc, h1, l1);
+                chm[(size_t)k * N + n] = h1;
+                chm[LO + (size_t)k * N + n] = l1;
+                c1[k] = h1;
+            }
+            TT<float>::Cur cur;
+            TT<float>::currents(cell, ueh, g1, c1[0], c1[2], c1[3], c1[4], cur);
+            const float I = TT<float>::iion_of(cur);
+            store_vu_ff(D, n, ubh, ubl, ueh, uel, applied_f(D, c, n) - I);
+        } else {
+            // ---- FP64: every state in double
+            const double* __restrict__ gn = D.s64_n;
+            double* __restrict__ gm = D.s64_nm1;
+            const double* __restrict__ cn = D.s64_n + (size_t)kTTGates * N;
+            double* __restrict__ cm = D.s64_nm1 + (size_t)kTTGates * N;
+            const double un = D.u_n[n];
+            double uB = un, uE = un;
+            double gB[kTTGates], gE[kTTGates];
+            double cB[kTTConc], cE[kTTConc];
+            if (c.order == 2) {
+                const double um = D.u_nm1[n];
+                uB = 2.0 * un - 0.5 * um;
+                uE = 2.0 * un - um;
+#pragma unroll
+                for (int k = 0; k < kTTGates; ++k) {
+                    const double x = gn[(size_t)k * N + n], y = gm[(size_t)k * N + n];
+                    gB[k] = 2.0 * x - 0.5 * y;
+                    gE[k] = 2.0 * x - y;
+                }
+#pragma unroll
+                for (int k = 0; k < kTTConc; ++k) {
+                    const double x = cn[(size_t)k * N + n], y = cm[(size_t)k * N + n];
+                    cB[k] = 2.0 * x - 0.5 * y;
+                    cE[k] = 2.0 * x - y;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kTTGates; ++k) gB[k] = gE[k] = gn[(size_t)k * N + n];
+#pragma unroll
+                for (int k = 0; k < kTTConc; ++k) cB[k] = cE[k] = cn[(size_t)k * N + n];
+            }
+            if (D.active && !D.active[n]) {
+                // excluded from the simulation: states held, no currents
+                for (int k = 0; k < kTTGates; ++k) gm[(size_t)k * N + n] = gn[(size_t)k * N + n];
+                for (int k = 0; k < kTTConc; ++k) cm[(size_t)k * N + n] = cn[(size_t)k * N + n];
+                store_vu64(D, n, uB * c.inv_dt, uE);
+                continue;
+            }
+            double a[kTTGates], b[kTTGates], r[kTTConc];
+            TT<double>::rates(cell, uE, gE, cE[0], cE[1], cE[2], cE[3], cE[4], a, b, r);
+            double g1[kTTGates];
+#pragma unroll
+            for (int k = 0; k < kTTGates; ++k) {
+                g1[k] = (gB[k] + dtg * a[k]) / (alg + dtg * b[k]);
+                gm[(size_t)k * N + n] = g1[k];
+            }
+            double c1[kTTConc];
+#pragma unroll
+            for (int k = 0; k < kTTConc; ++k) {
+                c1[k] = fma(c.dt_alpha, r[k], cB[k] * c.inv_alpha);
+                cm[(size_t)k * N + n] = c1[k];
+            }
+            TT<double>::Cur cur;
+            TT<double>::currents(cell, uE, g1, c1[0], c1[2], c1[3], c1[4], cur);
+            const double I = TT<double>::iion_of(cur);
+            store_vu64(D, n, fma(uB, c.inv_dt, applied(D, c, n) - I), uE);
+        }
+    }
+}
+
 
 void launch_ionic(Dev* d, const Dev& h, int grid, cudaStream_t s) {
     const bool refined = h.prec == EP_PREC_FP32_REFINED;
@@ -350,16 +508,20 @@ void launch_ionic(Dev* d, const Dev& h, int grid, cudaStream_t s) {
     if (h.model == EP_MODEL_BO) {
         if (refined) k_ionic_bo<float><<<grid, kNodeThreads, 0, s>>>(B);
         else k_ionic_bo<double><<<grid, kNodeThreads, 0, s>>>(B);
+    } else if (h.u_nm2) {
+        if (refined) k_ionic_tt3<float><<<grid, kNodeThreads, 0, s>>>(B);
+        else k_ionic_tt3<double><<<grid, kNodeThreads, 0, s>>>(B);
     } else {
-        if (refined) k_ionic_tt<float><<<grid, kNodeThreads, 0, s>>>(B);
-        else k_ionic_tt<double><<<grid, kNodeThreads, 0, s>>>(B);
+        if (refined) k_ionic_tt2<float><<<grid, kNodeThreads, 0, s>>>(B);
+        else k_ionic_tt2<double><<<grid, kNodeThreads, 0, s>>>(B);
     }
 }
 
-// refined instances of one model, batched
-void launch_ionic_batch(const Batch& B, int model, int grid, cudaStream_t s) {
+// refined instances of one model and number of levels, batched
+void launch_ionic_batch(const Batch& B, int model, bool lv3, int grid, cudaStream_t s) {
     if (model == EP_MODEL_BO) k_ionic_bo<float><<<grid, kNodeThreads, 0, s>>>(B);
-    else k_ionic_tt<float><<<grid, kNodeThreads, 0, s>>>(B);
+    else if (lv3) k_ionic_tt3<float><<<grid, kNodeThreads, 0, s>>>(B);
+    else k_ionic_tt2<float><<<grid, kNodeThreads, 0, s>>>(B);
 }
 
 }  // namespace epk

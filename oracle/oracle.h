@@ -109,6 +109,19 @@ int or_assemble_regions(int64_t nn, int64_t ne, const double* xyz,
                         const int32_t* hex, const double* f0, const double* s0,
                         const uint8_t* label, int nreg, const double* rdiff,
                         const uint8_t* excluded, or_csr* A, uint8_t* active);
+/* ---- Q2 finite elements (Sec. 1.2: hexahedra of arbitrary degree) ------- */
+/* Element matrices (27x27, row-major) of a triquadratic 27-node hexahedron,
+ * local node a = a0 + 3 a1 + 9 a2 at reference point (a0, a1, a2)/2 of
+ * [0,1]^3, by 3x3x3 Gauss-Legendre quadrature (exact for the mass matrix of
+ * a straight element); fibres Q2-interpolated to the quadrature points. */
+void or_element_matrices_q2(const double* X, const double* f, const double* s,
+                            double dl, double dt_, double dn, double* Me,
+                            double* Ke);
+/* Assembly over 27-node hexahedra (hex27: ne x 27 node indices in the local
+ * order above). */
+int or_assemble_q2(int64_t nn, int64_t ne, const double* xyz, const int32_t* hex27,
+                   const double* f0, const double* s0, double dl, double dt_,
+                   double dn, or_csr* A);
 void or_csr_free(or_csr* A);
 /* y = (cm*M + ck*K) x */
 void or_csr_apply(const or_csr* A, double cm, double ck, const double* x,
@@ -154,6 +167,14 @@ or_sim* or_sim_create_regions(int64_t nn, int64_t ne, const double* xyz,
                               double dt, int bdf_order, double tol, int maxit,
                               int npulses, const or_pulse* pulses,
                               const uint8_t* masks, double act_thr);
+/* The same on 27-node (Q2) hexahedra, one region. */
+or_sim* or_sim_create_q2(int64_t nn, int64_t ne, const double* xyz,
+                         const int32_t* hex27, const double* f0, const double* s0,
+                         double dl, double dt_, double dn, int model,
+                         const uint8_t* cell, double g_passive, double dt,
+                         int bdf_order, double tol, int maxit, int npulses,
+                         const or_pulse* pulses, const uint8_t* masks,
+                         double act_thr);
 /* Spatial profile of pulse p (Sec. 3.2.x: spherical and Gaussian impulses):
  * the node receives amp * weight[node] instead of amp * (mask[node] != 0).
  * NULL restores the mask.  The array is copied. */

@@ -30,6 +30,12 @@ def lib():
         L.or_cell_step.argtypes = [i32, i32, d, i32, d, d, vp, d, vp, d, vp]
         L.or_cell_step.restype = d
         L.or_element_matrices.argtypes = [vp, vp, vp, d, d, d, vp, vp]
+        L.or_element_matrices_q2.argtypes = [vp, vp, vp, d, d, d, vp, vp]
+        L.or_assemble_q2.argtypes = [i64, i64, vp, vp, vp, vp, d, d, d, vp]
+        L.or_assemble_q2.restype = i32
+        L.or_sim_create_q2.argtypes = [i64, i64, vp, vp, vp, vp, d, d, d, i32, vp, d, d,
+                                       i32, d, i32, i32, vp, vp, d]
+        L.or_sim_create_q2.restype = vp
         L.or_sim_create.argtypes = [i64, i64, vp, vp, vp, vp, d, d, d, i32, vp, d, d,
                                     i32, d, i32, i32, vp, vp, d]
         L.or_sim_create.restype = vp
@@ -125,6 +131,15 @@ def element_matrices(X, f, s, dl, dt_, dn):
     return Me, Ke
 
 
+def element_matrices_q2(X, f, s, dl, dt_, dn):
+    """27-node (Q2) element matrices; local node a = a0 + 3 a1 + 9 a2."""
+    X, f, s = _f64(X).reshape(27, 3), _f64(f).reshape(27, 3), _f64(s).reshape(27, 3)
+    Me = np.zeros((27, 27))
+    Ke = np.zeros((27, 27))
+    lib().or_element_matrices_q2(_p(X), _p(f), _p(s), dl, dt_, dn, _p(Me), _p(Ke))
+    return Me, Ke
+
+
 class _CSR(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.POINTER(C.c_int64)),
                 ("col", C.POINTER(C.c_int64)), ("mval", C.POINTER(C.c_double)),
@@ -162,7 +177,13 @@ class Sim:
             m = np.zeros((1, nn), dtype=np.uint8)
         self._pl, self._m = pl, m
         self.dt = dt
-        if regions is None:
+        if self.hex.shape[1] == 27:
+            if regions is not None:
+                raise ValueError("Q2 meshes take one region")
+            self.h = lib().or_sim_create_q2(nn, ne, _p(self.xyz), _p(self.hex), _p(self.f0), _p(self.s0),
+                                            D[0], D[1], D[2], model, _p(self.cell), g, dt, bdf_order,
+                                            tol, maxit, len(pulses), _p(pl), _p(m), act_thr)
+        elif regions is None:
             self.h = lib().or_sim_create(nn, ne, _p(self.xyz), _p(self.hex), _p(self.f0), _p(self.s0),
                                          D[0], D[1], D[2], model, _p(self.cell), g, dt, bdf_order,
                                          tol, maxit, len(pulses), _p(pl), _p(m), act_thr)
@@ -313,6 +334,22 @@ def assemble_regions(prob):
     out = _csr_to_scipy(A, sp)
     lib().or_csr_free(C.byref(A))
     return out[0], out[1], active
+
+
+def assemble_q2(xyz, hex27, f0, s0, D):
+    """Assembled M, K (scipy CSR) on 27-node hexahedra."""
+    import scipy.sparse as sp
+
+    xyz, hx = _f64(xyz), np.ascontiguousarray(hex27, dtype=np.int32)
+    f0, s0 = _f64(f0), _f64(s0)
+    A = _CSR()
+    rc = lib().or_assemble_q2(xyz.shape[0], hx.shape[0], _p(xyz), _p(hx), _p(f0), _p(s0), D[0], D[1], D[2],
+                              C.byref(A))
+    if rc != 0:
+        raise ValueError("or_assemble_q2 failed")
+    out = _csr_to_scipy(A, sp)
+    lib().or_csr_free(C.byref(A))
+    return out
 
 
 def sim_from_problem(prob, tol=1e-12, maxit=1000, **kw):

@@ -62,7 +62,8 @@ or_sim* or_sim_create(int64_t nn, int64_t ne, const double* xyz,
                                  dt, bdf_order, tol, maxit, npulses, pulses, masks, act_thr);
 }
 
-or_sim* or_sim_create_regions(int64_t nn, int64_t ne, const double* xyz,
+/* npe 8: Q1 with subdomains; npe 27: Q2, one region */
+static or_sim* create_general(int npe, int64_t nn, int64_t ne, const double* xyz,
                               const int32_t* hex, const double* f0,
                               const double* s0, const uint8_t* label, int nreg,
                               const double* rdiff, const uint8_t* excluded,
@@ -77,8 +78,15 @@ or_sim* or_sim_create_regions(int64_t nn, int64_t ne, const double* xyz,
     or_sim* S = calloc(1, sizeof(or_sim));
     S->nn = nn;
     S->active = malloc((size_t)nn);
-    if (or_assemble_regions(nn, ne, xyz, hex, f0, s0, label, nreg, rdiff, excluded, &S->A,
-                            S->active) != 0) {
+    int rc;
+    if (npe == 27) {
+        rc = or_assemble_q2(nn, ne, xyz, hex, f0, s0, rdiff[0], rdiff[1], rdiff[2], &S->A);
+        memset(S->active, 1, (size_t)nn);
+    } else {
+        rc = or_assemble_regions(nn, ne, xyz, hex, f0, s0, label, nreg, rdiff, excluded, &S->A,
+                                 S->active);
+    }
+    if (rc != 0) {
         free(S->active);
         free(S);
         return NULL;
@@ -122,6 +130,31 @@ or_sim* or_sim_create_regions(int64_t nn, int64_t ne, const double* xyz,
     S->masks = malloc((size_t)(npulses > 0 ? npulses : 1) * N);
     if (npulses > 0) memcpy(S->masks, masks, (size_t)npulses * N);
     return S;
+}
+
+or_sim* or_sim_create_regions(int64_t nn, int64_t ne, const double* xyz,
+                              const int32_t* hex, const double* f0,
+                              const double* s0, const uint8_t* label, int nreg,
+                              const double* rdiff, const uint8_t* excluded,
+                              int model, const uint8_t* cell, double g,
+                              double dt, int bdf_order, double tol, int maxit,
+                              int npulses, const or_pulse* pulses,
+                              const uint8_t* masks, double act_thr) {
+    return create_general(8, nn, ne, xyz, hex, f0, s0, label, nreg, rdiff, excluded, model, cell, g,
+                          dt, bdf_order, tol, maxit, npulses, pulses, masks, act_thr);
+}
+
+or_sim* or_sim_create_q2(int64_t nn, int64_t ne, const double* xyz,
+                         const int32_t* hex27, const double* f0, const double* s0,
+                         double dl, double dt_, double dn, int model,
+                         const uint8_t* cell, double g, double dt,
+                         int bdf_order, double tol, int maxit, int npulses,
+                         const or_pulse* pulses, const uint8_t* masks,
+                         double act_thr) {
+    const double rdiff[3] = {dl, dt_, dn};
+    const uint8_t excluded[1] = {0};
+    return create_general(27, nn, ne, xyz, hex27, f0, s0, NULL, 1, rdiff, excluded, model, cell, g,
+                          dt, bdf_order, tol, maxit, npulses, pulses, masks, act_thr);
 }
 
 void or_sim_destroy(or_sim* S) {

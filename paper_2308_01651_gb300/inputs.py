@@ -30,7 +30,7 @@ MASTER_SEED = 20230803
 # model / cell identifiers shared by the C ABI and the oracle
 BO, TTP06 = 0, 1
 ENDO, MID, EPI = 0, 1, 2
-MESH_SLAB, MESH_SHELL = 0, 1
+MESH_SLAB, MESH_SHELL, MESH_SLAB_Q2 = 0, 1, 2
 
 # activation slope thresholds (model units per ms): 1 mV/ms, i.e. 1/85.7 per ms
 # in Bueno-Orovio's dimensionless potential (u_mV = 85.7 u - 84)
@@ -57,6 +57,29 @@ def slab_mesh(nx, ny, nz, L):
     xyz = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
     hexes = _hex_connectivity(nx, ny, nz, periodic_y=False)
     return dict(kind=MESH_SLAB, nx=nx, ny=ny, nz=nz, L=(Lx, Ly, Lz), xyz=xyz, hex=hexes)
+
+
+def slab_mesh_q2(nx, ny, nz, L):
+    """The box [0,Lx]x[0,Ly]x[0,Lz] with nx x ny x nz triquadratic (27-node)
+    hexahedra: nodes on the grid of half the element size,
+    (2nx+1)(2ny+1)(2nz+1) of them, node (I, J, K) = I + NX (J + NY K); the
+    element (i, j, k) holds the nodes 2i..2i+2 x 2j..2j+2 x 2k..2k+2, local
+    node a = a0 + 3 a1 + 9 a2 at (2i+a0, 2j+a1, 2k+a2)."""
+    Lx, Ly, Lz = L
+    NX, NY, NZ = 2 * nx + 1, 2 * ny + 1, 2 * nz + 1
+    x = np.arange(NX) * (Lx / (2 * nx))
+    y = np.arange(NY) * (Ly / (2 * ny))
+    z = np.arange(NZ) * (Lz / (2 * nz))
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    xyz = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    i, j, k = i.ravel(), j.ravel(), k.ravel()
+    cols = []
+    for a in range(27):
+        a0, a1, a2 = a % 3, (a // 3) % 3, a // 9
+        cols.append((2 * i + a0) + NX * ((2 * j + a1) + NY * (2 * k + a2)))
+    hexes = np.stack(cols, axis=1).astype(np.int32)
+    return dict(kind=MESH_SLAB_Q2, nx=nx, ny=ny, nz=nz, L=(Lx, Ly, Lz), xyz=xyz, hex=hexes)
 
 
 def _hex_connectivity(nx, ny, nz, periodic_y):
@@ -149,8 +172,9 @@ def box_mask(xyz, lo, hi, h):
 
 
 def node_ijk(mesh):
-    NX = mesh["nx"] + 1
-    NY = mesh["ny"] if mesh["kind"] == MESH_SHELL else mesh["ny"] + 1
+    q2 = mesh["kind"] == MESH_SLAB_Q2
+    NX = 2 * mesh["nx"] + 1 if q2 else mesh["nx"] + 1
+    NY = mesh["ny"] if mesh["kind"] == MESH_SHELL else (2 * mesh["ny"] + 1 if q2 else mesh["ny"] + 1)
     idx = np.arange(mesh["xyz"].shape[0])
     return idx % NX, (idx // NX) % NY, idx // (NX * NY)
 
@@ -158,7 +182,7 @@ def node_ijk(mesh):
 def face_mask(mesh, face):
     """Nodes on a face of a slab: face in 0..5 = x-, x+, y-, y+, z-, z+."""
     i, j, k = node_ijk(mesh)
-    n = (mesh["nx"], mesh["ny"], mesh["nz"])[face // 2]
+    n = (mesh["nx"], mesh["ny"], mesh["nz"])[face // 2] * (2 if mesh["kind"] == MESH_SLAB_Q2 else 1)
     idx = (i, j, k)[face // 2]
     return (idx == (0 if face % 2 == 0 else n)).astype(np.uint8)
 
@@ -210,6 +234,30 @@ def slab_ttp06(nx=200, ny=70, nz=30, L=(2.0, 0.7, 0.3), T=400.0, bdf=2, dt=0.05)
     mask = face_mask(m, 0)
     return problem(m, f0, s0, cond_sigma(1.4, 0.5, 0.25), TTP06, dt, bdf, T,
                    [dict(amp=35.714, t0=0.0, dur=2.0, period=0.0)], [mask], name="slab_ttp06")
+
+
+def slab_ttp06_q2(nx=100, ny=35, nz=15, L=(2.0, 0.7, 0.3), T=400.0, bdf=2, dt=0.05):
+    """The TTP06 slab of slab_ttp06 on triquadratic elements of twice the
+    size: the same node grid (201 x 71 x 31 = 442,401 nodes at the default
+    size), fibres, conductivities, time step and x = 0 face stimulus."""
+    m = slab_mesh_q2(nx, ny, nz, L)
+    f0, s0 = rotating_slab_fibres(m["xyz"], L[2])
+    mask = face_mask(m, 0)
+    return problem(m, f0, s0, cond_sigma(1.4, 0.5, 0.25), TTP06, dt, bdf, T,
+                   [dict(amp=35.714, t0=0.0, dur=2.0, period=0.0)], [mask], name="slab_ttp06_q2")
+
+
+def slab_bo_q2(nx=10, ny=5, nz=3, L=(1.0, 0.5, 0.3), T=60.0, amp=1.0, bdf=1):
+    """Bueno-Orovio slab on triquadratic elements: f0 along x, D_l = 1.3e-3,
+    D_t = D_n = 0.45e-3 cm^2/ms, dt 0.05 ms, 1 ms pulse in a 0.1 cm corner
+    cube."""
+    m = slab_mesh_q2(nx, ny, nz, L)
+    n = m["xyz"].shape[0]
+    f0, s0 = uniform_fibres(n)
+    h = min(L[0] / nx, L[1] / ny, L[2] / nz) / 2
+    mask = box_mask(m["xyz"], (0, 0, 0), (0.1, 0.1, 0.1), h)
+    return problem(m, f0, s0, cond_D(1.3e-3, 0.45e-3, 0.45e-3), BO, 0.05, bdf, T,
+                   [dict(amp=amp, t0=0.0, dur=1.0, period=0.0)], [mask], name="slab_bo_q2")
 
 
 def nversion(dx=0.01, dt=0.005, T=50.0):

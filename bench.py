@@ -50,6 +50,9 @@ WORKLOADS = {
            "together (ep_step_batch)"),
     "c5": ("serving: requests arriving Poisson, sizes log-uniform, slab or ellipsoid shell, Bueno-Orovio/TTP06, "
            "admitted by device footprint, continuously batched (scaled-down stream; see config)"),
+    "q2": ("slab_ttp06_q2: the 2 x 0.7 x 0.3 cm slab on Q2 (27-node) hexahedra, 100x35x15 elements (the same "
+           "442,401 nodes), TTP06 epi, fibres +60->-60 deg in z, sigma 1.4/0.5/0.25 mS/cm, BDF2, dt 0.05 ms, "
+           "stimulus 35.714 mV/ms x 2 ms in x <= 0.04 cm; matrix-free sum-factorised operators"),
 }
 # FP32 pipe peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -66,7 +69,7 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_model(name, N, n_elems, inner_iters=1.0, shell=False):
+def kernel_model(name, N, n_elems, inner_iters=1.0, shell=False, q2=False):
     """Bytes and flops per launch of each kernel of the refined slab step.
 
     Returns (algorithmic bytes, implementation bytes, flops).  Algorithmic
@@ -104,6 +107,24 @@ def kernel_model(name, N, n_elems, inner_iters=1.0, shell=False):
         "apply32_stencil": (72 * N, 72 * N, 56 * N),
         "update32": (32 * N, 32 * N, 8 * N),
     }
+    if q2:
+        # triquadratic slab (27 Gauss points per element, N ~ 8 n_elems):
+        # matrix-free minimum per node as for Q1 (fibres instead of
+        # operators); this layout reads the per-point flux matrices (6 floats
+        # per point, hi for FP32, hi + lo for float-float) and writes and
+        # reads the per-element outputs (27 per element)
+        eq = 27 * n_elems
+        M.update({
+            # FP32 apply: p 4 + q 4 + fibres 24; z, p_old 8, G 24 eq, element
+            # outputs 8 eq, p and q 8; ~1800 FMA per element
+            "apply32_q2": (32 * N, 16 * N + 32 * eq, 3600 * n_elems + 4 * N),
+            # right-hand side: u 8 + v 8 + fibres 24 + b 8 + r/z/d 12; u, v
+            # 16, G 48 eq, outputs A u and M v 32 eq, D^-1 4, b 8, r/z/d 12
+            "rhs": (60 * N, 40 * N + 80 * eq, 2 * 4600 * 10 * n_elems),
+            # residual: u 8 + b 8 + fibres 24 + r/z/d 12; u 8, G 48 eq,
+            # outputs 16 eq, b 8, D^-1 4, r/z/d 12
+            "resid": (52 * N, 32 * N + 64 * eq, 4600 * 10 * n_elems),
+        })
     v = M.get(name)
     if v is None:
         return None, None, None
@@ -121,9 +142,11 @@ def source_hash(files):
 KERNEL_SOURCES = {
     "apply32_mf": ["paper_2308_01651_gb300/csrc/k_mf.cu", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
     "resid": ["paper_2308_01651_gb300/csrc/k_ff.cu", "paper_2308_01651_gb300/csrc/ep_tile.cuh",
-              "paper_2308_01651_gb300/csrc/ep_ff.cuh", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
+              "paper_2308_01651_gb300/csrc/ep_ff.cuh", "paper_2308_01651_gb300/csrc/ep_dev.cuh",
+              "paper_2308_01651_gb300/csrc/ep_refine.cuh"],
     "rhs": ["paper_2308_01651_gb300/csrc/k_ff.cu", "paper_2308_01651_gb300/csrc/ep_tile.cuh",
-            "paper_2308_01651_gb300/csrc/ep_ff.cuh", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
+            "paper_2308_01651_gb300/csrc/ep_ff.cuh", "paper_2308_01651_gb300/csrc/ep_dev.cuh",
+            "paper_2308_01651_gb300/csrc/ep_refine.cuh"],
     "pcg32": ["paper_2308_01651_gb300/csrc/k_pcg.cu", "paper_2308_01651_gb300/csrc/ep_tile.cuh",
               "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
     "update32": ["paper_2308_01651_gb300/csrc/k_cg.cu", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
@@ -239,7 +262,8 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2308_01651_gb300 import inputs as I
-    prob = I.shell_ttp06() if args.workload == "c4" else I.slab_ttp06()
+    prob = (I.shell_ttp06() if args.workload == "c4" else
+            I.slab_ttp06_q2() if args.workload == "q2" else I.slab_ttp06())
     leg = oracle_leg(prob, budget_s=min(120.0, 10.0 + 2.0 * args.steps), max_steps=max(2, args.steps))
     line = {"metric": METRIC, "value": leg["value"], "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": leg["steps"], "warmup": 0, "ms_per_step": leg["ms_per_step"], "higher_is_better": True,
@@ -276,7 +300,8 @@ def run_ours(args):
     from paper_2308_01651_gb300 import inputs as I
 
     shell = args.workload == "c4"
-    prob = I.shell_ttp06() if shell else I.slab_ttp06()
+    q2 = args.workload == "q2"
+    prob = I.shell_ttp06() if shell else (I.slab_ttp06_q2() if q2 else I.slab_ttp06())
     N = prob["mesh"]["xyz"].shape[0]
     n_elems = prob["mesh"]["hex"].shape[0]
     # a dedicated stream: the library orders its work on it, and the events
@@ -309,7 +334,12 @@ def run_ours(args):
             st = inst.stats()  # synchronises; outside the events
             it_sum += st["cg_iters"]
             sw_sum += st["sweeps"]
-            if st["op32"] == ep.EP_OP_STENCIL:
+            if q2:
+                # ionic, rhs (element + gather), finish; per inner iteration
+                # the apply (element + gather) and the update; per sweep the
+                # correction and the residual (element + gather)
+                launches += 4 + 3 * st["cg_iters"] + 3 * st["sweeps"]
+            elif st["op32"] == ep.EP_OP_STENCIL:
                 launches += 3 + 3 * st["sweeps"]  # ionic, rhs, finish; per sweep: pcg32, correct, resid
             else:
                 launches += 3 + 2 * st["cg_iters"] + 2 * st["sweeps"]
@@ -347,7 +377,7 @@ def run_ours(args):
         tot_prof = sum(v[1] for v in prof.values())
         ipl = it_sum / max(sw_sum, 1)
         for name, (n_l, ms) in prof.items():
-            b, bi, f = kernel_model(name, N, n_elems, ipl, shell=shell)
+            b, bi, f = kernel_model(name, N, n_elems, ipl, shell=shell, q2=q2)
             avg_s = ms / 1e3 / n_l
             kernels[name] = {"launches": n_l, "avg_us": 1e6 * avg_s, "share": ms / tot_prof,
                              "gbs": (b / avg_s / 1e9) if b else None,
@@ -357,7 +387,7 @@ def run_ours(args):
         hbm_peak, peak_kind = measured_peaks()
         d = kernels[dom]
         hbm_frac = d["gbs"] / hbm_peak if d["gbs"] else 0.0
-        fp64 = dom in ("resid", "rhs", "apply64")
+        fp64 = dom in ("resid", "rhs", "apply64") and not q2
         alu_peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
         alu_frac = d["tflops"] / alu_peak if d["tflops"] else 0.0
         # the hot-path measurement table: the operator / CG / residual
@@ -381,7 +411,7 @@ def run_ours(args):
     u32 = inst.potential()
     inst.close()
     acc, fp64 = None, None
-    if not args.no_accuracy:
+    if not args.no_accuracy and not q2:  # (Q2 slabs: refined precision only)
         i64 = ep.Instance(prob, precision=FP64, cuda_stream=sp)
         i64.step(W)
         e64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -441,14 +471,15 @@ def run_ours(args):
         "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "nodes": N, "elements": n_elems,
                    "precision": "FP32 inner CG, float-float refinement",
-                   "op32": {0: "auto", 1: "matrix-free", 2: "stencil"}[op32],
+                   "op32": "Q2 matrix-free (sum factorisation)" if q2 else
+                           {0: "auto", 1: "matrix-free", 2: "stencil"}[op32],
                    "t_window_ms": [W * prob["dt"], (W + K) * prob["dt"]],
                    "l2": "flushed before every step (256 MiB write), per-step CUDA events on the instance stream",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": p50, "p99": p99, "what": "one IMEX step of the whole mesh"},
         "roofline": roof, "kernels": kernels, "profile_steps": P,
         "op32_autotune_us": {"matrix_free": tune["tune_us_mf"], "stencil": tune["tune_us_stencil"],
-                             "chosen": {1: "matrix-free", 2: "stencil"}.get(tune["op32"], "?")},
+                             "chosen": {1: "matrix-free", 2: "stencil"}.get(tune["op32"], "Q2")},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
         "accuracy": acc, "fp64_gpu": fp64,
     }

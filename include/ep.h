@@ -52,7 +52,15 @@ typedef enum {
     EP_EUNSUPPORTED = 7  /* a valid request this build does not implement */
 } ep_status;
 
-enum { EP_MESH_SLAB = 0, EP_MESH_SHELL = 1 };
+/* Meshes: EP_MESH_SLAB, the box [0,L] with nx x ny x nz trilinear hexahedra;
+ * EP_MESH_SHELL, a periodic-in-j structured shell given by node coordinates;
+ * EP_MESH_SLAB_Q2, the box with nx x ny x nz triquadratic 27-node hexahedra
+ * (Sec. 1.2: hexahedral elements of any polynomial degree), nodes on the grid
+ * of half the element size, (2nx+1)(2ny+1)(2nz+1) of them, node
+ * (I, J, K) = I + (2nx+1) (J + (2ny+1) K).  Q2 operators are matrix-free
+ * (sum factorisation on 3 x 3 x 3 Gauss points) and need FP32_REFINED
+ * precision and one region (else EP_EUNSUPPORTED). */
+enum { EP_MESH_SLAB = 0, EP_MESH_SHELL = 1, EP_MESH_SLAB_Q2 = 2 };
 enum { EP_MODEL_BO = 0, EP_MODEL_TTP06 = 1 };
 enum { EP_CELL_ENDO = 0, EP_CELL_MID = 1, EP_CELL_EPI = 2 };
 /* Arithmetic of the step.  FP64: every quantity in double, CG on the FP64

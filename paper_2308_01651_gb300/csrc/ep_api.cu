@@ -34,6 +34,10 @@ void launch_apply32_mf(Dev* d, const Dev& h, cudaStream_t s);
 void launch_update32(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s);
 void launch_correct_ff(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_ionic_batch(const Batch& B, int model, bool lv3, int grid, cudaStream_t s);
+cudaError_t q2_upload_tables();
+void launch_q2_apply32(Dev* d, const Dev& h, int grid_nodes, cudaStream_t s);
+void launch_q2_resid(Dev* d, const Dev& h, int first, int graph, int grid_nodes, cudaStream_t s);
+void launch_realpha_q2(Dev* d, const Dev& h, double alpha_dt, cudaStream_t s);
 void launch_rhs_ff_batch(const Batch& B, int first, int graph, int grid, cudaStream_t s);
 void launch_correct_ff_batch(const Batch& B, int grid, cudaStream_t s);
 void launch_resid_np(Dev* d, const Dev& h, int graph, int grid, cudaStream_t s);
@@ -99,9 +103,9 @@ struct ep_instance {
 
 static const char* kKernelNames[] = {"ionic", "rhs", "resid", "p64", "apply64", "update64",
                                      "apply32_mf", "apply32_stencil", "update32", "correct",
-                                     "finish", "realpha", "pcg32"};
+                                     "finish", "realpha", "pcg32", "apply32_q2"};
 enum { K_IONIC, K_RHS, K_RESID, K_P64, K_APPLY64, K_UPDATE64, K_APPLY32MF, K_APPLY32ST, K_UPDATE32,
-       K_CORRECT, K_FINISH, K_REALPHA, K_PCG32, K_COUNT };
+       K_CORRECT, K_FINISH, K_REALPHA, K_PCG32, K_APPLY32Q2, K_COUNT };
 
 static cudaEvent_t prof_event(ep_instance* I) {
     if (!I->free_events.empty()) {
@@ -150,6 +154,7 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 int64_t expected_nodes(const ep_mesh* m) {
     if (m->kind == EP_MESH_SLAB) return (int64_t)(m->nx + 1) * (m->ny + 1) * (m->nz + 1);
+    if (m->kind == EP_MESH_SLAB_Q2) return (int64_t)(2 * m->nx + 1) * (2 * m->ny + 1) * (2 * m->nz + 1);
     return (int64_t)(m->nx + 1) * m->ny * (m->nz + 1);
 }
 
@@ -188,6 +193,8 @@ struct Sizes {
     bool regions;     // the mesh carries subdomain labels
     bool slab_mass;   // the refined path applies the analytic slab mass matrix
     int levels;       // time levels kept: 3 for BDF3, else 2
+    bool q2;          // triquadratic slab
+    int64_t ne;       // elements (Q2)
 };
 
 // float-float pair (nearest float, then the nearest float of the rest)
@@ -209,6 +216,10 @@ cudaError_t get_best(const ep_instance* I, double* out) {
     return cudaMemcpy(out, I->h.best, N * 8, cudaMemcpyDeviceToHost);
 }
 
+// Internal operator kind of triquadratic slabs (not an ep_options.op32 value):
+// the matrix-free Q2 operators of k_q2.cu.
+constexpr int kOpQ2 = 100;
+
 // Device bytes per instance; mirrors the allocations in ep_create.
 size_t footprint(const Sizes& z) {
     auto al = [](size_t b) { return ((b + 255) / 256) * 256; };
@@ -228,14 +239,21 @@ size_t footprint(const Sizes& z) {
     }
     if (z.prec == EP_PREC_FP32_REFINED) {
         b += al(N * 4);                   // dinv32
-        b += 2 * al(epk::kGroups * N * 16);                              // Ahi Alo
-        if (!z.slab_mass) b += 2 * al(epk::kGroups * N * 16);            // Mhi Mlo (curved / with regions)
+        if (z.q2) {
+            const size_t eq = (size_t)z.ne * 27;
+            b += al(12 * eq * 4);         // quadrature-point flux matrices (hi, lo)
+            b += 5 * al(eq * 4);          // element outputs: FP32 apply, A u and M v (hi, lo)
+            b += 2 * al(N * 8);           // diagonals of M and K
+        } else {
+            b += 2 * al(epk::kGroups * N * 16);                          // Ahi Alo
+            if (!z.slab_mass) b += 2 * al(epk::kGroups * N * 16);        // Mhi Mlo (curved / with regions)
+        }
         b += 6 * al(N * 4);                                              // u, v, b (hi, lo)
         b += (2 + 2 * L) * al(N * 4);                                    // A u history (hi, lo)
         b += (1 + 2 * L) * al(N * 4);                                    // u levels (hi, lo), best slope
-        if (z.op32 != EP_OP_STENCIL) b += al(6 * N * 4);                 // fibres
+        if (z.op32 != EP_OP_STENCIL && !z.q2) b += al(6 * N * 4);       // fibres
         b += 6 * al(N * 4);               // r32 z32 q32 d32 pa32 pb32
-        b += al(N);                       // boundary flags
+        if (!z.q2) b += al(N);            // boundary flags
     } else {
         b += 4 * al(N * 8);               // z64 q64 pa64 pb64
     }
@@ -249,13 +267,14 @@ size_t footprint(const Sizes& z) {
 ep_status validate(const ep_mesh* mesh, const ep_fibers* fib, const ep_conductivities* cond,
                    const ep_ionic_model* ionic, const ep_stimulus* stim, const ep_options* opts) {
     if (!mesh || !fib || !cond || !ionic || !opts) return fail(EP_EINVAL, "NULL argument");
-    if (mesh->kind != EP_MESH_SLAB && mesh->kind != EP_MESH_SHELL) return fail(EP_EINVAL, "mesh.kind");
+    if (mesh->kind != EP_MESH_SLAB && mesh->kind != EP_MESH_SHELL && mesh->kind != EP_MESH_SLAB_Q2)
+        return fail(EP_EINVAL, "mesh.kind");
     if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1) return fail(EP_EINVAL, "mesh sizes must be >= 1");
     if (mesh->kind == EP_MESH_SHELL && mesh->ny < 3) return fail(EP_EINVAL, "shell needs ny >= 3");
     const int64_t nn = expected_nodes(mesh);
     if (nn > (int64_t)1 << 30) return fail(EP_EINVAL, "mesh too large for one instance (> 2^30 nodes)");
     if (mesh->n_nodes != nn) return fail(EP_EINVAL, "mesh.n_nodes does not match the structured sizes");
-    if (mesh->kind == EP_MESH_SLAB) {
+    if (mesh->kind == EP_MESH_SLAB || mesh->kind == EP_MESH_SLAB_Q2) {
         for (int d = 0; d < 3; ++d)
             if (!finite_pos(mesh->L[d])) return fail(EP_EINVAL, "slab lengths must be positive");
     } else if (!mesh->xyz) {
@@ -295,8 +314,13 @@ ep_status validate(const ep_mesh* mesh, const ep_fibers* fib, const ep_conductiv
     if (opts->precision != EP_PREC_FP64 && opts->precision != EP_PREC_FP32_REFINED)
         return fail(EP_EINVAL, "options.precision");
     if (opts->op32 < EP_OP_AUTO || opts->op32 > EP_OP_STENCIL) return fail(EP_EINVAL, "options.op32");
-    if (opts->op32 == EP_OP_MATRIX_FREE && mesh->kind != EP_MESH_SLAB)
+    if (opts->op32 == EP_OP_MATRIX_FREE && mesh->kind == EP_MESH_SHELL)
         return fail(EP_EUNSUPPORTED, "the matrix-free FP32 operator needs a slab mesh");
+    if (mesh->kind == EP_MESH_SLAB_Q2) {
+        if (opts->precision != EP_PREC_FP32_REFINED)
+            return fail(EP_EUNSUPPORTED, "Q2 meshes need FP32_REFINED precision");
+        if (mesh->region) return fail(EP_EUNSUPPORTED, "Q2 meshes take one region");
+    }
     if (mesh->region) {
         if (opts->op32 == EP_OP_MATRIX_FREE && opts->precision == EP_PREC_FP32_REFINED)
             return fail(EP_EUNSUPPORTED, "the matrix-free FP32 operator does not take subdomains");
@@ -322,6 +346,8 @@ Sizes sizes_of(const ep_mesh* mesh, const ep_ionic_model* ionic, const ep_option
     z.ns = ionic->model == EP_MODEL_BO ? epk::kBOStates : epk::kTTGates + epk::kTTConc;
     z.prec = opts->precision;
     z.levels = opts->bdf_order == 3 ? 3 : 2;
+    z.q2 = mesh->kind == EP_MESH_SLAB_Q2;
+    z.ne = (int64_t)mesh->nx * mesh->ny * mesh->nz;
     z.slab = mesh->kind == EP_MESH_SLAB;
     z.regions = mesh->region != nullptr;
     // an excluded region changes M; the footprint assumes it may
@@ -329,6 +355,7 @@ Sizes sizes_of(const ep_mesh* mesh, const ep_ionic_model* ionic, const ep_option
     // AUTO on a slab keeps both FP32 operators and lets the create-time
     // autotuner pick; the matrix-free apply needs an axis-aligned slab
     z.op32 = opts->op32 == EP_OP_AUTO ? ((z.slab && !z.regions) ? EP_OP_AUTO : EP_OP_STENCIL) : opts->op32;
+    if (z.q2) z.op32 = kOpQ2;
     if (z.prec == EP_PREC_FP32_REFINED) {
         z.ng32 = ionic->model == EP_MODEL_BO ? epk::kBOStates : epk::kTTGates;
         z.ns64 = ionic->model == EP_MODEL_BO ? 0 : epk::kTTConc;
@@ -366,7 +393,9 @@ void ensure_alpha(ep_instance* I) {
         const float cmass = (float)(to * I->h.h[0] * I->h.h[1] * I->h.h[2]);
         const double delta = to - I->alpha_dt_dev;
         timed(I, K_REALPHA, [&] {
-            if (I->h.prec == EP_PREC_FP32_REFINED) epk::launch_realpha_ff(I->d, I->h, delta, to, cmass, I->stream);
+            if (I->h.q2) epk::launch_realpha_q2(I->d, I->h, to, I->stream);
+            else if (I->h.prec == EP_PREC_FP32_REFINED)
+                epk::launch_realpha_ff(I->d, I->h, delta, to, cmass, I->stream);
             else epk::launch_realpha(I->d, I->h, delta, to, cmass, I->stream);
         });
         I->alpha_dt_dev = to;
@@ -419,6 +448,7 @@ ep_status build_graph(ep_instance* I) {
     C.chk(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     epk::launch_ionic(I->d, h, I->grid_ionic, s);
     if (h.prec == EP_PREC_FP64) epk::launch_rhs64(I->d, h, 1, 1, I->grid_tiles, s);
+    else if (h.q2) epk::launch_q2_resid(I->d, h, 1, 1, I->grid_nodes, s);
     else epk::launch_rhs_ff(I->d, h, 1, 1, I->grid_tiles, s);
     cudaGraph_t body = nullptr, body2 = nullptr;
     if (h.prec == EP_PREC_FP64) {
@@ -446,13 +476,15 @@ ep_status build_graph(ep_instance* I) {
             C.chk(add_while(s2, &h_inner, &body2));
             if (C.err == cudaSuccess) {
                 C.chk(cudaStreamBeginCaptureToGraph(s3, body2, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-                if (h.op32 == EP_OP_MATRIX_FREE) epk::launch_apply32_mf(I->d, h, s3);
+                if (h.q2) epk::launch_q2_apply32(I->d, h, I->grid_nodes, s3);
+                else if (h.op32 == EP_OP_MATRIX_FREE) epk::launch_apply32_mf(I->d, h, s3);
                 else epk::launch_apply32_stencil(I->d, h, I->grid_tiles, s3);
                 epk::launch_update32(I->d, h, I->grid_nodes, 1, s3);
                 C.chk(cudaStreamEndCapture(s3, &body2));
             }
             epk::launch_correct_ff(I->d, h, I->grid_nodes, s2);
-            epk::launch_resid_np(I->d, h, 1, I->grid_nodes, s2);
+            if (h.q2) epk::launch_q2_resid(I->d, h, 0, 1, I->grid_nodes, s2);
+            else epk::launch_resid_np(I->d, h, 1, I->grid_nodes, s2);
             C.chk(cudaStreamEndCapture(s2, &body));
         }
     }
@@ -496,6 +528,7 @@ ep_status step_host(ep_instance* I) {
     timed(I, K_IONIC, [&] { epk::launch_ionic(d, h, I->grid_ionic, s); });
     timed(I, K_RHS, [&] {
         if (h.prec == EP_PREC_FP64) epk::launch_rhs64(d, h, 1, 0, I->grid_tiles, s);
+        else if (h.q2) epk::launch_q2_resid(d, h, 1, 0, I->grid_nodes, s);
         else epk::launch_rhs_ff(d, h, 1, 0, I->grid_tiles, s);
     });
     int f = 0;
@@ -519,7 +552,9 @@ ep_status step_host(ep_instance* I) {
                 fi = 0;
             }
             for (int it = 0; fi && it <= h.max_iter; ++it) {
-                if (h.op32 == EP_OP_MATRIX_FREE)
+                if (h.q2)
+                    timed(I, K_APPLY32Q2, [&] { epk::launch_q2_apply32(d, h, I->grid_nodes, s); });
+                else if (h.op32 == EP_OP_MATRIX_FREE)
                     timed(I, K_APPLY32MF, [&] { epk::launch_apply32_mf(d, h, s); });
                 else
                     timed(I, K_APPLY32ST, [&] { epk::launch_apply32_stencil(d, h, I->grid_tiles, s); });
@@ -530,7 +565,10 @@ ep_status step_host(ep_instance* I) {
             // the persistent solver applies its correction itself
             if (h.op32 != EP_OP_STENCIL)
                 timed(I, K_CORRECT, [&] { epk::launch_correct_ff(d, h, I->grid_nodes, s); });
-            timed(I, K_RESID, [&] { epk::launch_resid_np(d, h, 0, I->grid_nodes, s); });
+            timed(I, K_RESID, [&] {
+                if (h.q2) epk::launch_q2_resid(d, h, 0, 0, I->grid_nodes, s);
+                else epk::launch_resid_np(d, h, 0, I->grid_nodes, s);
+            });
             CUDA_TRY(cudaGetLastError());
             CUDA_TRY(flag(&d->f_outer, &f));
         }
@@ -600,6 +638,83 @@ void free_all(ep_instance* I) {
     if (I->own_stream && I->stream) cudaStreamDestroy(I->stream);
 }
 
+// Triquadratic slab operators, computed on the host in double: per element
+// and Gauss point the flux matrix w_q |J| H D(q) H (D of Eq. (3) with the
+// fibres Q2-interpolated to the point, not renormalised), uploaded as
+// float-float pairs; the diagonals of M and K; the Jacobi diagonal for the
+// first step; the norm scale.
+ep_status q2_setup(ep_instance* I, const ep_fibers* fib, double dl, double dtr, double dn) {
+    Dev& h = I->h;
+    const size_t N = (size_t)h.N, E = (size_t)h.ne, EQ = E * 27;
+    const double r = std::sqrt(15.0) / 10.0;
+    const double xq[3] = {0.5 - r, 0.5, 0.5 + r};
+    const double w1[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+    double L1[3][3], D1[3][3];  // [q][b]: l_b(xi_q), l_b'(xi_q)
+    for (int q = 0; q < 3; ++q) {
+        const double t = xq[q];
+        L1[q][0] = (1.0 - t) * (1.0 - 2.0 * t);
+        L1[q][1] = 4.0 * t * (1.0 - t);
+        L1[q][2] = t * (2.0 * t - 1.0);
+        D1[q][0] = 4.0 * t - 3.0;
+        D1[q][1] = 4.0 - 8.0 * t;
+        D1[q][2] = 4.0 * t - 1.0;
+    }
+    const double ih[3] = {1.0 / h.h[0], 1.0 / h.h[1], 1.0 / h.h[2]};
+    const double vol = h.q2vol;
+    std::vector<float> G(12 * EQ);
+    std::vector<double> dM(N, 0.0), dK(N, 0.0);
+    for (size_t e = 0; e < E; ++e) {
+        const int ei = (int)(e % h.enx), ej = (int)((e / h.enx) % h.eny), ek = (int)(e / ((size_t)h.enx * h.eny));
+        int node[27];
+        for (int a = 0; a < 27; ++a)
+            node[a] = (2 * ei + a % 3) + h.NX * ((2 * ej + (a / 3) % 3) + h.NY * (2 * ek + a / 9));
+        for (int q = 0; q < 27; ++q) {
+            const int q0 = q % 3, q1 = (q / 3) % 3, q2 = q / 9;
+            double f[3] = {0, 0, 0}, sv[3] = {0, 0, 0};
+            double phi[27], gr[27][3];
+            for (int a = 0; a < 27; ++a) {
+                const int a0 = a % 3, a1 = (a / 3) % 3, a2 = a / 9;
+                phi[a] = L1[q0][a0] * L1[q1][a1] * L1[q2][a2];
+                gr[a][0] = D1[q0][a0] * L1[q1][a1] * L1[q2][a2];
+                gr[a][1] = L1[q0][a0] * D1[q1][a1] * L1[q2][a2];
+                gr[a][2] = L1[q0][a0] * L1[q1][a1] * D1[q2][a2];
+                for (int c = 0; c < 3; ++c) {
+                    f[c] += phi[a] * fib->f0[3 * (size_t)node[a] + c];
+                    sv[c] += phi[a] * fib->s0[3 * (size_t)node[a] + c];
+                }
+            }
+            const double w = w1[q0] * w1[q1] * w1[q2] * vol;
+            double Gm[3][3];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    const double Dij = (i == j ? dn : 0.0) + (dl - dn) * f[i] * f[j] + (dtr - dn) * sv[i] * sv[j];
+                    Gm[i][j] = w * ih[i] * Dij * ih[j];
+                }
+            const double comp[6] = {Gm[0][0], Gm[1][1], Gm[2][2], Gm[0][1], Gm[0][2], Gm[1][2]};
+            for (int c = 0; c < 6; ++c) split_ff(comp[c], G[c * EQ + e * 27 + q], G[(6 + c) * EQ + e * 27 + q]);
+            for (int a = 0; a < 27; ++a) {
+                dM[node[a]] += w * phi[a] * phi[a];
+                double k = 0.0;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) k += gr[a][i] * Gm[i][j] * gr[a][j];
+                dK[node[a]] += k;
+            }
+        }
+    }
+    CUDA_TRY(epk::q2_upload_tables());
+    CUDA_TRY(cudaMemcpy(const_cast<float*>(h.q2G), G.data(), G.size() * 4, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(h.q2dM, dM.data(), N * 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(h.q2dK, dK.data(), N * 8, cudaMemcpyHostToDevice));
+    std::vector<float> di(N);
+    for (size_t n = 0; n < N; ++n) di[n] = (float)(1.0 / (h.alpha_dt * dM[n] + dK[n]));
+    CUDA_TRY(cudaMemcpy(h.dinv32, di.data(), N * 4, cudaMemcpyHostToDevice));
+    // norm scale from a vertex's mass diagonal (keeps the float sums of
+    // squares in range)
+    h.nscale = dM[0] > 0.0 ? (float)(1.0 / dM[0]) : 1.0f;
+    CUDA_TRY(cudaMemcpy(I->d, &h, sizeof(Dev), cudaMemcpyHostToDevice));
+    return EP_OK;
+}
+
 ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conductivities* cond,
                       const ep_ionic_model* ionic, const ep_stimulus* stim, const ep_options* opts,
                       ep_instance* I) {
@@ -616,8 +731,20 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     h.NZ = mesh->nz + 1;
     h.periodic = mesh->kind == EP_MESH_SHELL;
     h.N = z.N;
-    if (mesh->kind == EP_MESH_SLAB)
+    if (mesh->kind == EP_MESH_SLAB || mesh->kind == EP_MESH_SLAB_Q2)
         for (int d = 0; d < 3; ++d) h.h[d] = mesh->L[d] / (d == 0 ? mesh->nx : d == 1 ? mesh->ny : mesh->nz);
+    if (z.q2) {
+        // node grid of half the element size; h holds the element sizes
+        h.q2 = 1;
+        h.NX = 2 * mesh->nx + 1;
+        h.NY = 2 * mesh->ny + 1;
+        h.NZ = 2 * mesh->nz + 1;
+        h.enx = mesh->nx;
+        h.eny = mesh->ny;
+        h.enz = mesh->nz;
+        h.ne = (int)z.ne;
+        h.q2vol = h.h[0] * h.h[1] * h.h[2];
+    }
     h.model = ionic->model;
     h.prec = opts->precision;
     h.bdf = opts->bdf_order;
@@ -672,14 +799,30 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     }
     ALLOC(h.at, N);
     ALLOC(h.best, N);
-    ALLOC(h.M64, epk::kSlots * N);
-    ALLOC(h.A64, epk::kSlots * N);
-    ALLOC(h.dinv64, N);
+    if (!z.q2) {
+        ALLOC(h.M64, epk::kSlots * N);
+        ALLOC(h.A64, epk::kSlots * N);
+        ALLOC(h.dinv64, N);
+    }
     if (ref) {
         ALLOC(h.dinv32, N);
-        ALLOC(h.Ahi, epk::kGroups * N);
-        ALLOC(h.Alo, epk::kGroups * N);
-        if (!z.slab_mass) {
+        if (z.q2) {
+            const size_t eq = (size_t)z.ne * 27;
+            float* G = nullptr;
+            ALLOC(G, 12 * eq);
+            h.q2G = G;
+            ALLOC(h.q2Y32, eq);
+            ALLOC(h.q2Yh, eq);
+            ALLOC(h.q2Yl, eq);
+            ALLOC(h.q2Bh, eq);
+            ALLOC(h.q2Bl, eq);
+            ALLOC(h.q2dM, N);
+            ALLOC(h.q2dK, N);
+        } else {
+            ALLOC(h.Ahi, epk::kGroups * N);
+            ALLOC(h.Alo, epk::kGroups * N);
+        }
+        if (!z.slab_mass && !z.q2) {
             ALLOC(h.Mhi, epk::kGroups * N);
             ALLOC(h.Mlo, epk::kGroups * N);
         }
@@ -706,14 +849,14 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         ALLOC(h.v_lo, N);
         ALLOC(h.b_hi, N);
         ALLOC(h.b_lo, N);
-        if (z.op32 != EP_OP_STENCIL) ALLOC(h.fib, 6 * N);
+        if (z.op32 != EP_OP_STENCIL && !z.q2) ALLOC(h.fib, 6 * N);
         ALLOC(h.r32, N);
         ALLOC(h.z32, N);
         ALLOC(h.q32, N);
         ALLOC(h.d32, N);
         ALLOC(h.pa32, N);
         ALLOC(h.pb32, N);
-        ALLOC(h.nflag, N);
+        if (!z.q2) ALLOC(h.nflag, N);
     } else {
         ALLOC(h.z64, N);
         ALLOC(h.q64, N);
@@ -849,7 +992,10 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         h.mw_lo = (float)(mw - (double)h.mw_hi);
     }
     CUDA_TRY(cudaMemcpy(I->d, &h, sizeof(Dev), cudaMemcpyHostToDevice));
-    {
+    if (z.q2) {
+        ep_status st2 = q2_setup(I, fib, dl, dtr, dn);
+        if (st2 != EP_OK) return st2;
+    } else {
         double *f0 = nullptr, *s0 = nullptr, *xyz = nullptr;
         CUDA_TRY(cudaMalloc(&f0, N * 3 * 8));
         cudaError_t e1 = cudaMalloc(&s0, N * 3 * 8);
@@ -889,7 +1035,7 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         if (e != cudaSuccess) return fail(EP_ECUDA, std::string("assembly: ") + cudaGetErrorString(e));
         if (bad_h) return fail(EP_EINVAL, "mesh has an element with non-positive Jacobian determinant");
     }
-    if (ref) {
+    if (ref && !z.q2) {
         // refined operators: full float-float couplings; norm scale from a
         // mass-matrix diagonal (keeps the float sums of squares in range)
         epk::launch_expand(I->d, h, 1, 1, I->stream);
@@ -932,7 +1078,7 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         I->grid_pcg = std::max(1, std::min(std::min(want, sms * occ), epk::kMaxPersistentBlocks));
     }
     if (!ref) h.op32 = 0;  // no FP32 operator in the FP64 path
-    if (ref && h.op32 == EP_OP_AUTO) {
+    if (ref && !z.q2 && h.op32 == EP_OP_AUTO) {
         ep_status st2 = autotune_op32(I);
         if (st2 != EP_OK) return st2;
     }
@@ -1662,6 +1808,7 @@ ep_status ep_residual_norm_noalloc(const ep_instance* I, double* relres_out) {
     if (!I || !relres_out) return fail(EP_EINVAL, "NULL argument");
     if (I->h.prec != EP_PREC_FP32_REFINED)
         return fail(EP_EUNSUPPORTED, "the allocation-free residual serves FP32_REFINED instances");
+    if (I->h.q2) return fail(EP_EUNSUPPORTED, "the allocation-free residual serves structured-stencil instances");
     if (I->grid_nodes > epk::noalloc_max_blocks())
         return fail(EP_EINVAL, "the residual of this instance needs " + std::to_string(I->grid_nodes) +
                                    " thread blocks; the allocation-free path holds partial sums for at most " +

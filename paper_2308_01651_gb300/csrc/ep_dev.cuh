@@ -104,6 +104,16 @@ struct Dev {
     float4 *Ahi, *Alo, *Mhi, *Mlo;
     float *dinv32;
     float *fib;                 // [6][N]: f0/h, s0/h per component (matrix-free)
+    // ---- triquadratic slab (EP_MESH_SLAB_Q2): matrix-free operators -----------
+    int q2;                     // 1: 27-node hexahedra (nodes on the half-element grid)
+    int enx, eny, enz, ne;      // elements per direction, in total
+    double q2vol;               // element volume hx hy hz
+    const float* q2G;           // [2][6][ne * 27]: hi, then lo parts of the quadrature
+                                // point flux matrices w_q |J| H D(q) H (xx yy zz xy xz yz)
+    float* q2Y32;               // [ne * 27] element outputs of the FP32 apply
+    float *q2Yh, *q2Yl;         // [ne * 27] element outputs of A u (float-float)
+    float *q2Bh, *q2Bl;         // [ne * 27] element outputs of M v (float-float)
+    double *q2dM, *q2dK;        // diagonals of M and K
     float mf_cn[3], mf_cl, mf_ct, mf_cmass;
     double alpha_dt;            // alpha_BDF/dt the operators currently hold
     int op32;                   // EP_OP_MATRIX_FREE or EP_OP_STENCIL

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libep_gb300.so")
 EP_OK, EP_EINVAL, EP_ENOMEM, EP_ENOCONV, EP_ENAN, EP_ETIMEOUT, EP_ECUDA, EP_EUNSUPPORTED = range(8)
 STATUS_NAMES = {0: "EP_OK", 1: "EP_EINVAL", 2: "EP_ENOMEM", 3: "EP_ENOCONV", 4: "EP_ENAN",
                 5: "EP_ETIMEOUT", 6: "EP_ECUDA", 7: "EP_EUNSUPPORTED"}
-EP_MESH_SLAB, EP_MESH_SHELL = 0, 1
+EP_MESH_SLAB, EP_MESH_SHELL, EP_MESH_SLAB_Q2 = 0, 1, 2
 EP_MODEL_BO, EP_MODEL_TTP06 = 0, 1
 EP_CELL_ENDO, EP_CELL_MID, EP_CELL_EPI = 0, 1, 2
 EP_PREC_FP64, EP_PREC_FP32_REFINED = 0, 1

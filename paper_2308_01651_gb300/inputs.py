@@ -239,10 +239,14 @@ def slab_ttp06(nx=200, ny=70, nz=30, L=(2.0, 0.7, 0.3), T=400.0, bdf=2, dt=0.05)
 def slab_ttp06_q2(nx=100, ny=35, nz=15, L=(2.0, 0.7, 0.3), T=400.0, bdf=2, dt=0.05):
     """The TTP06 slab of slab_ttp06 on triquadratic elements of twice the
     size: the same node grid (201 x 71 x 31 = 442,401 nodes at the default
-    size), fibres, conductivities, time step and x = 0 face stimulus."""
+    size), fibres, conductivities, time step and stimulus amplitude.  The
+    stimulus covers x <= 0.04 cm (two element layers): on Q2 elements the
+    x = 0 face alone carries a sixth of an element layer's current (the
+    integral of the face's basis functions) and starts no wave."""
     m = slab_mesh_q2(nx, ny, nz, L)
     f0, s0 = rotating_slab_fibres(m["xyz"], L[2])
-    mask = face_mask(m, 0)
+    hmin = min(L[0] / nx, L[1] / ny, L[2] / nz) / 2
+    mask = box_mask(m["xyz"], (0.0, 0.0, 0.0), (0.04, L[1], L[2]), hmin)
     return problem(m, f0, s0, cond_sigma(1.4, 0.5, 0.25), TTP06, dt, bdf, T,
                    [dict(amp=35.714, t0=0.0, dur=2.0, period=0.0)], [mask], name="slab_ttp06_q2")
 

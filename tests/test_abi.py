@@ -133,3 +133,24 @@ def test_state_pack_roundtrip_bdf3():
         assert np.array_equal(st[name], v)
     with pytest.raises(ValueError):
         ep.state_pack(0, 3, 0.05, 5, u[0], u[1], w[0], w[1], at, best)
+
+
+def test_q2_slab_validation_and_footprint():
+    """Q2 slabs need FP32_REFINED and one region; the footprint counts the
+    quadrature-point flux matrices and element buffers instead of stencils."""
+    prob = I.slab_ttp06_q2(nx=4, ny=3, nz=2, L=(0.4, 0.3, 0.2), T=1.0)
+    a, kw = _args(prob)
+    kw.update(precision=ep.EP_PREC_FP64)
+    with pytest.raises(ep.EpError) as e:
+        ep.ep_create(*a, **kw)
+    assert e.value.status == ep.EP_EUNSUPPORTED
+    bad = dict(prob["mesh"], n_nodes=10)
+    bad.pop("xyz")
+    with pytest.raises(ep.EpError) as e:
+        ep.ep_create(bad, *a[1:], **dict(kw, precision=ep.EP_PREC_FP32_REFINED))
+    assert e.value.status == ep.EP_EINVAL
+    big = I.slab_mesh_q2(100, 35, 15, (2.0, 0.7, 0.3))
+    fp = ep.ep_footprint_bytes(big, I.TTP06, precision=ep.EP_PREC_FP32_REFINED)
+    n = big["xyz"].shape[0]
+    assert n == 201 * 71 * 31
+    assert 300 * n < fp < 900 * n

@@ -34,7 +34,6 @@ void launch_apply32_mf(Dev* d, const Dev& h, cudaStream_t s);
 void launch_update32(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s);
 void launch_correct_ff(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_ionic_batch(const Batch& B, int model, bool lv3, int grid, cudaStream_t s);
-cudaError_t q2_upload_tables();
 void launch_q2_apply32(Dev* d, const Dev& h, int grid_nodes, cudaStream_t s);
 void launch_q2_resid(Dev* d, const Dev& h, int first, int graph, int grid_nodes, cudaStream_t s);
 void launch_realpha_q2(Dev* d, const Dev& h, double alpha_dt, cudaStream_t s);
@@ -242,6 +241,7 @@ size_t footprint(const Sizes& z) {
         if (z.q2) {
             const size_t eq = (size_t)z.ne * 27;
             b += al(12 * eq * 4);         // quadrature-point flux matrices (hi, lo)
+            b += al(6 * eq * 4);          // their hi parts, element fastest (FP32 apply)
             b += 5 * al(eq * 4);          // element outputs: FP32 apply, A u and M v (hi, lo)
             b += 2 * al(N * 8);           // diagonals of M and K
         } else {
@@ -701,8 +701,15 @@ ep_status q2_setup(ep_instance* I, const ep_fibers* fib, double dl, double dtr, 
             }
         }
     }
-    CUDA_TRY(epk::q2_upload_tables());
     CUDA_TRY(cudaMemcpy(const_cast<float*>(h.q2G), G.data(), G.size() * 4, cudaMemcpyHostToDevice));
+    {
+        // FP32 apply's copy: [6][27][ne]
+        std::vector<float> T(6 * EQ);
+        for (int c = 0; c < 6; ++c)
+            for (size_t e = 0; e < E; ++e)
+                for (int q = 0; q < 27; ++q) T[((size_t)c * 27 + q) * E + e] = G[c * EQ + e * 27 + q];
+        CUDA_TRY(cudaMemcpy(const_cast<float*>(h.q2G32), T.data(), T.size() * 4, cudaMemcpyHostToDevice));
+    }
     CUDA_TRY(cudaMemcpy(h.q2dM, dM.data(), N * 8, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(h.q2dK, dK.data(), N * 8, cudaMemcpyHostToDevice));
     std::vector<float> di(N);
@@ -811,6 +818,9 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
             float* G = nullptr;
             ALLOC(G, 12 * eq);
             h.q2G = G;
+            float* G32 = nullptr;
+            ALLOC(G32, 6 * eq);
+            h.q2G32 = G32;
             ALLOC(h.q2Y32, eq);
             ALLOC(h.q2Yh, eq);
             ALLOC(h.q2Yl, eq);

@@ -13,14 +13,15 @@
 // and point at ep_create.  The transposed passes bring the quadrature values
 // back to the 27 nodes.
 //
-// Work decomposition: 27 threads per element (one per node in the nodal
-// passes, one per Gauss point in the quadrature passes), nine elements per
-// 256-thread block, the intermediate arrays in shared memory.  Every element
-// writes its 27 outputs to a per-element buffer; a node-parallel gather then
-// sums the contributions of the node's 1, 2, 4 or 8 elements in a fixed
-// order (no atomics: bitwise reproducible).  The FP32 variant is the inner
-// CG's operator; the float-float variant (ep_ff.cuh) gives the refinement its
-// right-hand side b = M v and residual b - A u.
+// Work decomposition.  FP32 apply (the inner CG's operator): one thread per
+// element, the whole sum factorisation in registers with the 1-D
+// coefficients as immediates, flux matrices read element-fastest.  Float-
+// float passes (the refinement's right-hand side b = M v and residual
+// b - A u, ep_ff.cuh): nine threads per element, one per 1-D pencil of the
+// pass, the intermediate arrays in shared memory between the passes.  Every
+// element writes its 27 outputs to a per-element buffer; a node-parallel
+// gather then sums the contributions of the node's 1, 2, 4 or 8 elements in
+// a fixed order (no atomics: bitwise reproducible).
 #include <cmath>
 
 #include "ep_dev.cuh"
@@ -29,286 +30,427 @@
 
 namespace epk {
 
-constexpr int kQ2Groups = 9;     // elements per block
-constexpr int kQ2Threads = 256;  // 9 x 27 = 243 working threads
-constexpr int kQ2Slots = 7;      // intermediate arrays per element
-
-// [q * 3 + b]: hi parts at 0..8, lo parts at 9..17
-__constant__ float cQ2B[18];
-__constant__ float cQ2D[18];
-// Gauss weight products w_{q0} w_{q1} w_{q2}: hi at 0..26, lo at 27..53
-__constant__ float cQ2W[54];
-
-struct FF {
+struct __align__(8) FF {
     float h, l;
 };
 
 __device__ __forceinline__ void q2_zero(float& a) { a = 0.f; }
 __device__ __forceinline__ void q2_zero(FF& a) { a = FF{0.f, 0.f}; }
-// acc += tab[i] x
-__device__ __forceinline__ void q2_mac(float& acc, const float* tab, int i, float x) {
-    acc = fmaf(tab[i], x, acc);
-}
-__device__ __forceinline__ void q2_mac(FF& acc, const float* tab, int i, FF x) {
-    ff_mac(tab[i], tab[9 + i], x.h, x.l, acc.h, acc.l);
-}
-// acc += a x
-__device__ __forceinline__ void q2_fma(float& acc, float a, float x) { acc = fmaf(a, x, acc); }
-__device__ __forceinline__ void q2_fma(FF& acc, FF a, FF x) { ff_mac(a.h, a.l, x.h, x.l, acc.h, acc.l); }
-__device__ __forceinline__ void q2_norm(float&) {}
-__device__ __forceinline__ void q2_norm(FF& a) { ff_normalize(a.h, a.l); }
 __device__ __forceinline__ void q2_add(float& acc, float x) { acc += x; }
 __device__ __forceinline__ void q2_add(FF& acc, FF x) { ff_sub(acc.h, acc.l, -x.h, -x.l, acc.h, acc.l); }
 
-// The element operator on the group's 27 values in S[0] (written by the
-// caller before a barrier).  t: the thread's node / Gauss point index
-// t0 + 3 t1 + 9 t2.  MASS_ONLY: cm_q u(q) alone (no flux).  Every thread of
-// the block calls it (it holds block barriers).  Slots: 0 input; F0 -> 1, 2;
-// F1 -> 3, 4, 5; quadrature values -> 0, 1, 2, 6; R2 -> 3, 4, 5; R1 -> 0, 1.
-template <typename V, bool MASS_ONLY>
-__device__ __forceinline__ V q2_op(V* s[kQ2Slots], int t, const V (&G)[6], V cm) {
-    const int t0 = t % 3, t1 = (t / 3) % 3, t2 = t / 9;
-    // F0: along direction 0, entry (q0, b1, b2) = (t0, t1, t2)
-    {
-        V ab, ad;
-        q2_zero(ab);
-        q2_zero(ad);
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const V x = s[0][b + 3 * t1 + 9 * t2];
-            q2_mac(ab, cQ2B, 3 * t0 + b, x);
-            if (!MASS_ONLY) q2_mac(ad, cQ2D, 3 * t0 + b, x);
-        }
-        q2_norm(ab);
-        q2_norm(ad);
-        s[1][t] = ab;
-        if (!MASS_ONLY) s[2][t] = ad;
-    }
-    __syncthreads();
-    // F1: along direction 1, entry (q0, q1, b2)
-    {
-        V bb, db, bd;
-        q2_zero(bb);
-        q2_zero(db);
-        q2_zero(bd);
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const int i = t0 + 3 * b + 9 * t2;
-            const V x = s[1][i];
-            q2_mac(bb, cQ2B, 3 * t1 + b, x);
-            if (!MASS_ONLY) {
-                q2_mac(db, cQ2B, 3 * t1 + b, s[2][i]);
-                q2_mac(bd, cQ2D, 3 * t1 + b, x);
-            }
-        }
-        q2_norm(bb);
-        s[3][t] = bb;
-        if (!MASS_ONLY) {
-            q2_norm(db);
-            q2_norm(bd);
-            s[4][t] = db;
-            s[5][t] = bd;
-        }
-    }
-    __syncthreads();
-    // F2: along direction 2, Gauss point q = t: the value and the reference
-    // gradient, then the mass and flux terms
-    {
-        V val, g0, g1, g2;
-        q2_zero(val);
-        q2_zero(g0);
-        q2_zero(g1);
-        q2_zero(g2);
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const int i = t0 + 3 * t1 + 9 * b;
-            const V x = s[3][i];
-            q2_mac(val, cQ2B, 3 * t2 + b, x);
-            if (!MASS_ONLY) {
-                q2_mac(g0, cQ2B, 3 * t2 + b, s[4][i]);
-                q2_mac(g1, cQ2B, 3 * t2 + b, s[5][i]);
-                q2_mac(g2, cQ2D, 3 * t2 + b, x);
-            }
-        }
-        q2_norm(val);
-        V mv;
-        q2_zero(mv);
-        q2_fma(mv, cm, val);
-        q2_norm(mv);
-        s[0][t] = mv;
-        if (!MASS_ONLY) {
-            q2_norm(g0);
-            q2_norm(g1);
-            q2_norm(g2);
-            // G symmetric: xx yy zz xy xz yz
-            V f0, f1, f2;
-            q2_zero(f0);
-            q2_zero(f1);
-            q2_zero(f2);
-            q2_fma(f0, G[0], g0);
-            q2_fma(f0, G[3], g1);
-            q2_fma(f0, G[4], g2);
-            q2_fma(f1, G[3], g0);
-            q2_fma(f1, G[1], g1);
-            q2_fma(f1, G[5], g2);
-            q2_fma(f2, G[4], g0);
-            q2_fma(f2, G[5], g1);
-            q2_fma(f2, G[2], g2);
-            q2_norm(f0);
-            q2_norm(f1);
-            q2_norm(f2);
-            s[1][t] = f0;
-            s[2][t] = f1;
-            s[6][t] = f2;
-        }
-    }
-    __syncthreads();
-    // R2: transposed along direction 2, entry (q0, q1, a2)
-    {
-        V sa, p0, p1;
-        q2_zero(sa);
-        q2_zero(p0);
-        q2_zero(p1);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const int i = t0 + 3 * t1 + 9 * q;
-            q2_mac(sa, cQ2B, 3 * q + t2, s[0][i]);
-            if (!MASS_ONLY) {
-                q2_mac(sa, cQ2D, 3 * q + t2, s[6][i]);
-                q2_mac(p0, cQ2B, 3 * q + t2, s[1][i]);
-                q2_mac(p1, cQ2B, 3 * q + t2, s[2][i]);
-            }
-        }
-        q2_norm(sa);
-        s[3][t] = sa;
-        if (!MASS_ONLY) {
-            q2_norm(p0);
-            q2_norm(p1);
-            s[4][t] = p0;
-            s[5][t] = p1;
-        }
-    }
-    __syncthreads();
-    // R1: transposed along direction 1, entry (q0, a1, a2)
-    {
-        V r, qq;
-        q2_zero(r);
-        q2_zero(qq);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const int i = t0 + 3 * q + 9 * t2;
-            q2_mac(r, cQ2B, 3 * q + t1, s[3][i]);
-            if (!MASS_ONLY) {
-                q2_mac(r, cQ2D, 3 * q + t1, s[5][i]);
-                q2_mac(qq, cQ2B, 3 * q + t1, s[4][i]);
-            }
-        }
-        q2_norm(r);
-        s[0][t] = r;
-        if (!MASS_ONLY) {
-            q2_norm(qq);
-            s[1][t] = qq;
-        }
-    }
-    __syncthreads();
-    // R0: transposed along direction 0, node a = t
-    V y;
-    q2_zero(y);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const int i = q + 3 * t1 + 9 * t2;
-        q2_mac(y, cQ2B, 3 * q + t0, s[0][i]);
-        if (!MASS_ONLY) q2_mac(y, cQ2D, 3 * q + t0, s[1][i]);
-    }
-    q2_norm(y);
-    return y;
+// 1-D quadratic Lagrange basis on [0,1] (nodes 0, 1/2, 1), l_b(xi_q), and
+// its derivative l_b'(xi_q) at the 3-point Gauss points xi = 1/2 -+
+// sqrt(15)/10, 1/2 (rounded to float), and the Gauss weights 5/18, 8/18,
+// 5/18: compile-time constants of the FP32 apply (the float-float kernels
+// take them as float-float pairs, below).
+__host__ __device__ constexpr float q2b(int q, int b) {
+    return q == 0 ? (b == 0 ? 0.68729836f : b == 1 ? 0.4f : -0.08729833f)
+           : q == 1 ? (b == 0 ? 0.0f : b == 1 ? 1.0f : 0.0f)
+           : (b == 0 ? -0.08729833f : b == 1 ? 0.4f : 0.68729836f);
+}
+__host__ __device__ constexpr float q2db(int q, int b) {
+    return q == 0 ? (b == 0 ? -2.5491934f : b == 1 ? 3.0983868f : -0.5491933f)
+           : q == 1 ? (b == 0 ? -1.0f : b == 1 ? 0.0f : 1.0f)
+           : (b == 0 ? 0.5491933f : b == 1 ? -3.0983868f : 2.5491934f);
+}
+__host__ __device__ constexpr float q2w(int q) { return q == 1 ? 0.44444445f : 0.2777778f; }
+#define Q2B(q, b) q2b((q), (b))
+#define Q2D(q, b) q2db((q), (b))
+
+// c0 x0 + c1 x1 + c2 x2 for compile-time coefficients; a zero coefficient
+// drops its term (l_b at the middle Gauss point is 0, 1, 0)
+__device__ __forceinline__ float q2dot(float c0, float x0, float c1, float x1, float c2, float x2) {
+    float acc = c2 == 0.f ? 0.f : c2 * x2;
+    acc = c1 == 0.f ? acc : fmaf(c1, x1, acc);
+    return c0 == 0.f ? acc : fmaf(c0, x0, acc);
 }
 
-// element e's node t = t0 + 3 t1 + 9 t2
-__device__ __forceinline__ int q2_node(const Dev& D, int e, int t) {
-    const int ei = e % D.enx, ej = (e / D.enx) % D.eny, ek = e / (D.enx * D.eny);
-    const int t0 = t % 3, t1 = (t / 3) % 3, t2 = t / 9;
-    return (2 * ei + t0) + D.NX * ((2 * ej + t1) + D.NY * (2 * ek + t2));
-}
-
-// FP32 apply of the inner CG: p = z + beta p_old at the element's nodes,
-// element outputs of A p.
-__global__ void __launch_bounds__(kQ2Threads) k_q2_elem32(Dev* __restrict__ Dp) {
-    __shared__ float sm[kQ2Slots][(kQ2Groups + 1) * 27];
+// FP32 apply of the inner CG, one thread per element with the whole sum
+// factorisation in registers (the 1-D coefficients are immediates): p =
+// z + beta p_old at the element's 27 nodes, the element outputs of A p,
+// node-major [27][ne].  The flux matrices are read from their element-fastest
+// FP32 copy [6][27][ne] (coalesced).
+__global__ void __launch_bounds__(128) k_q2_elem32(Dev* __restrict__ Dp) {
     const Dev& D = *Dp;
-    const int g = threadIdx.x / 27, t = threadIdx.x % 27;  // g == kQ2Groups: spare threads
-    const int e = blockIdx.x * kQ2Groups + g;
-    const bool valid = g < kQ2Groups && e < D.ne;
-    float* s[kQ2Slots];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= D.ne) return;
+    const int ei = e % D.enx, ej = (e / D.enx) % D.eny, ek = e / (D.enx * D.eny);
+    const int NX = D.NX, NXY = D.NX * D.NY;
+    const int n0 = 2 * ei + NX * (2 * ej) + NXY * (2 * ek);
+    const float beta = (float)D.beta;
+    const float* __restrict__ z = D.z32;
+    const float* __restrict__ pold = D.pswap ? D.pb32 : D.pa32;
+    // F0 (direction 0) straight from the nodal values, pencil by pencil
+    float ab[27], ad[27];
 #pragma unroll
-    for (int k = 0; k < kQ2Slots; ++k) s[k] = sm[k] + g * 27;
-    const size_t EQ = (size_t)D.ne * 27;
-    float G[6], cm = 0.f, x = 0.f;
+    for (int r = 0; r < 9; ++r) {  // r = b1 + 3 b2
+        const int n = n0 + NX * (r % 3) + NXY * (r / 3);
+        float x[3];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) G[c] = 0.f;
-    if (valid) {
-        const float beta = (float)D.beta;
-        const float* __restrict__ pold = D.pswap ? D.pb32 : D.pa32;
-        const int n = q2_node(D, e, t);
-        x = beta == 0.f ? D.z32[n] : fmaf(beta, pold[n], D.z32[n]);
-        const size_t o = (size_t)e * 27 + t;
+        for (int b = 0; b < 3; ++b) x[b] = beta == 0.f ? z[n + b] : fmaf(beta, pold[n + b], z[n + b]);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) G[c] = D.q2G[c * EQ + o];
-        cm = (float)(D.alpha_dt * D.q2vol) * cQ2W[t];
+        for (int q = 0; q < 3; ++q) {
+            ab[q + 3 * r] = q2dot(Q2B(q, 0), x[0], Q2B(q, 1), x[1], Q2B(q, 2), x[2]);
+            ad[q + 3 * r] = q2dot(Q2D(q, 0), x[0], Q2D(q, 1), x[1], Q2D(q, 2), x[2]);
+        }
     }
-    s[0][t] = x;
+    // F1 (direction 1): index q0 + 3 q1 + 9 b2
+    float bb[27], db[27], bd[27];
+#pragma unroll
+    for (int q0 = 0; q0 < 3; ++q0)
+#pragma unroll
+        for (int b2 = 0; b2 < 3; ++b2) {
+            const int i = q0 + 9 * b2;
+#pragma unroll
+            for (int q1 = 0; q1 < 3; ++q1) {
+                bb[i + 3 * q1] = q2dot(Q2B(q1, 0), ab[i], Q2B(q1, 1), ab[i + 3], Q2B(q1, 2), ab[i + 6]);
+                db[i + 3 * q1] = q2dot(Q2B(q1, 0), ad[i], Q2B(q1, 1), ad[i + 3], Q2B(q1, 2), ad[i + 6]);
+                bd[i + 3 * q1] = q2dot(Q2D(q1, 0), ab[i], Q2D(q1, 1), ab[i + 3], Q2D(q1, 2), ab[i + 6]);
+            }
+        }
+    // F2 (direction 2), the quadrature-point terms and R2 (direction 2,
+    // transposed), pencil by pencil over (q0, q1)
+    const size_t E = (size_t)D.ne;
+    const float* __restrict__ G = D.q2G32;
+    const float adtv = (float)(D.alpha_dt * D.q2vol);
+    float sa[27], p0[27], p1[27];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {  // c = q0 + 3 q1
+        float mv[3], f0[3], f1[3], f2[3];
+#pragma unroll
+        for (int q2 = 0; q2 < 3; ++q2) {
+            const float val = q2dot(Q2B(q2, 0), bb[c], Q2B(q2, 1), bb[c + 9], Q2B(q2, 2), bb[c + 18]);
+            const float g0 = q2dot(Q2B(q2, 0), db[c], Q2B(q2, 1), db[c + 9], Q2B(q2, 2), db[c + 18]);
+            const float g1 = q2dot(Q2B(q2, 0), bd[c], Q2B(q2, 1), bd[c + 9], Q2B(q2, 2), bd[c + 18]);
+            const float g2 = q2dot(Q2D(q2, 0), bb[c], Q2D(q2, 1), bb[c + 9], Q2D(q2, 2), bb[c + 18]);
+            const int q = c + 9 * q2;
+            const float* Gq = G + (size_t)q * E + e;
+            const float gxx = Gq[0], gyy = Gq[27 * E], gzz = Gq[54 * E];
+            const float gxy = Gq[81 * E], gxz = Gq[108 * E], gyz = Gq[135 * E];
+            const float w = q2w(c % 3) * q2w(c / 3) * q2w(q2);
+            mv[q2] = adtv * w * val;
+            f0[q2] = fmaf(gxx, g0, fmaf(gxy, g1, gxz * g2));
+            f1[q2] = fmaf(gxy, g0, fmaf(gyy, g1, gyz * g2));
+            f2[q2] = fmaf(gxz, g0, fmaf(gyz, g1, gzz * g2));
+        }
+#pragma unroll
+        for (int a2 = 0; a2 < 3; ++a2) {
+            sa[c + 9 * a2] = q2dot(Q2B(0, a2), mv[0], Q2B(1, a2), mv[1], Q2B(2, a2), mv[2]) +
+                             q2dot(Q2D(0, a2), f2[0], Q2D(1, a2), f2[1], Q2D(2, a2), f2[2]);
+            p0[c + 9 * a2] = q2dot(Q2B(0, a2), f0[0], Q2B(1, a2), f0[1], Q2B(2, a2), f0[2]);
+            p1[c + 9 * a2] = q2dot(Q2B(0, a2), f1[0], Q2B(1, a2), f1[1], Q2B(2, a2), f1[2]);
+        }
+    }
+    // R1 (direction 1, transposed): index q0 + 3 a1 + 9 a2
+    float rr[27], qq[27];
+#pragma unroll
+    for (int q0 = 0; q0 < 3; ++q0)
+#pragma unroll
+        for (int a2 = 0; a2 < 3; ++a2) {
+            const int i = q0 + 9 * a2;
+#pragma unroll
+            for (int a1 = 0; a1 < 3; ++a1) {
+                rr[i + 3 * a1] = q2dot(Q2B(0, a1), sa[i], Q2B(1, a1), sa[i + 3], Q2B(2, a1), sa[i + 6]) +
+                                 q2dot(Q2D(0, a1), p1[i], Q2D(1, a1), p1[i + 3], Q2D(2, a1), p1[i + 6]);
+                qq[i + 3 * a1] = q2dot(Q2B(0, a1), p0[i], Q2B(1, a1), p0[i + 3], Q2B(2, a1), p0[i + 6]);
+            }
+        }
+    // R0 (direction 0, transposed) and the node-major store
+    float* __restrict__ Y = D.q2Y32;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+#pragma unroll
+        for (int a0 = 0; a0 < 3; ++a0) {
+            const float y = q2dot(Q2B(0, a0), rr[3 * r], Q2B(1, a0), rr[3 * r + 1], Q2B(2, a0), rr[3 * r + 2]) +
+                            q2dot(Q2D(0, a0), qq[3 * r], Q2D(1, a0), qq[3 * r + 1], Q2D(2, a0), qq[3 * r + 2]);
+            Y[(size_t)(a0 + 3 * r) * E + e] = y;
+        }
+    }
+}
+
+// The 1-D tables as float-float pairs (hi, lo of the double values), for
+// the float-float kernels below: compile-time constants.
+__host__ __device__ constexpr float q2bh(int q, int b) { return q2b(q, b); }
+__host__ __device__ constexpr float q2bl(int q, int b) {
+    return q == 1 ? 0.0f
+                  : (b == 1 ? -5.9604646e-09f : (q == 0) == (b == 0) ? -2.2865983e-08f : -9.758747e-10f);
+}
+__host__ __device__ constexpr float q2dh(int q, int b) { return q2db(q, b); }
+__host__ __device__ constexpr float q2dl(int q, int b) {
+    return q == 1 ? 0.0f
+           : q == 0 ? (b == 0 ? 4.378022e-08f : b == 1 ? -8.756044e-08f : -1.5824428e-08f)
+                    : (b == 0 ? 1.5824428e-08f : b == 1 ? 8.756044e-08f : -4.378022e-08f);
+}
+// product of three Gauss weights, k of them 8/18 (the others 5/18)
+__device__ __forceinline__ FF q2wff(int k) {
+    return k == 0 ? FF{0.02143347f, -2.631721e-10f}
+           : k == 1 ? FF{0.03429355f, 1.8140989e-09f}
+           : k == 2 ? FF{0.054869685f, -8.2273216e-10f}
+                    : FF{0.087791495f, 1.7374466e-10f};
+}
+
+// acc += c x for a compile-time float-float coefficient (hi, lo); a zero
+// coefficient drops the term
+__device__ __forceinline__ void q2fm(FF& acc, float ch, float cl, FF x) {
+    if (ch != 0.f) ff_mac(ch, cl, x.h, x.l, acc.h, acc.l);
+}
+#define Q2FB(acc, q, b, x) q2fm(acc, q2bh(q, b), q2bl(q, b), x)
+#define Q2FD(acc, q, b, x) q2fm(acc, q2dh(q, b), q2dl(q, b), x)
+
+constexpr int kQ2PEl = 28;  // elements per block of the float-float kernels (9 threads each)
+
+// The float-float element operator with one thread per 1-D pencil: in each
+// pass the thread takes the three values of its pencil from shared memory
+// and produces the three outputs along the pass's direction (coefficients
+// are immediates, every thread uses all of them).  j = j0 + 3 j1 selects the
+// pencil.  A and Bf: the element's two 81-entry arrays in shared memory.
+// MASS_ONLY: cm_q u(q) alone.  Every thread of the block calls it.
+template <bool MASS_ONLY>
+__device__ __forceinline__ void q2_op_ff(const Dev& D, bool valid, int e, int j0, int j1, const FF (&x)[3],
+                                         FF* A, FF* Bf, FF cmv, FF (&y)[3]) {
+    const FF z0 = FF{0.f, 0.f};
+    // F0: pencil (b1, b2) = (j0, j1) along direction 0 -> A[q0 + 3 b1 + 9 b2]
+    {
+        const int o = 3 * j0 + 9 * j1;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            FF ab = z0, ad = z0;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                Q2FB(ab, q, b, x[b]);
+                if (!MASS_ONLY) Q2FD(ad, q, b, x[b]);
+            }
+            ff_normalize(ab.h, ab.l);
+            A[q + o] = ab;
+            if (!MASS_ONLY) {
+                ff_normalize(ad.h, ad.l);
+                A[27 + q + o] = ad;
+            }
+        }
+    }
     __syncthreads();
-    const float y = q2_op<float, false>(s, t, G, cm);
-    if (valid) D.q2Y32[(size_t)e * 27 + t] = y;
+    // F1: pencil (q0, b2) = (j0, j1) along direction 1 -> Bf[q0 + 3 q1 + 9 b2]
+    {
+        FF ab[3], ad[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            ab[b] = A[j0 + 3 * b + 9 * j1];
+            if (!MASS_ONLY) ad[b] = A[27 + j0 + 3 * b + 9 * j1];
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            FF bb = z0, db = z0, bd = z0;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                Q2FB(bb, q, b, ab[b]);
+                if (!MASS_ONLY) {
+                    Q2FB(db, q, b, ad[b]);
+                    Q2FD(bd, q, b, ab[b]);
+                }
+            }
+            const int i = j0 + 3 * q + 9 * j1;
+            ff_normalize(bb.h, bb.l);
+            Bf[i] = bb;
+            if (!MASS_ONLY) {
+                ff_normalize(db.h, db.l);
+                ff_normalize(bd.h, bd.l);
+                Bf[27 + i] = db;
+                Bf[54 + i] = bd;
+            }
+        }
+    }
+    __syncthreads();
+    // F2 + quadrature point terms + R2: pencil (q0, q1) = (j0, j1) along
+    // direction 2 -> A[q0 + 3 q1 + 9 a2]
+    {
+        const int c = j0 + 3 * j1;
+        FF bb[3], db[3], bd[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            bb[b] = Bf[c + 9 * b];
+            if (!MASS_ONLY) {
+                db[b] = Bf[27 + c + 9 * b];
+                bd[b] = Bf[54 + c + 9 * b];
+            }
+        }
+        FF mv[3], f0[3], f1[3], f2[3];
+        const size_t EQ = (size_t)D.ne * 27;
+        const int kw = (j0 == 1) + (j1 == 1);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            FF val = z0, g0 = z0, g1 = z0, g2 = z0;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                Q2FB(val, q, b, bb[b]);
+                if (!MASS_ONLY) {
+                    Q2FB(g0, q, b, db[b]);
+                    Q2FB(g1, q, b, bd[b]);
+                    Q2FD(g2, q, b, bb[b]);
+                }
+            }
+            ff_normalize(val.h, val.l);
+            // mass term cm_q u(q): (alpha/dt |J| or |J|) x w_q
+            const FF w = q2wff(kw + (q == 1));
+            FF cq;
+            ff_mul(cmv.h, cmv.l, w.h, w.l, cq.h, cq.l);
+            FF m = z0;
+            ff_mac(cq.h, cq.l, val.h, val.l, m.h, m.l);
+            ff_normalize(m.h, m.l);
+            mv[q] = m;
+            if (!MASS_ONLY) {
+                ff_normalize(g0.h, g0.l);
+                ff_normalize(g1.h, g1.l);
+                ff_normalize(g2.h, g2.l);
+                FF G[6];
+                const size_t o = (size_t)e * 27 + c + 9 * q;
+#pragma unroll
+                for (int k = 0; k < 6; ++k)
+                    G[k] = valid ? FF{D.q2G[k * EQ + o], D.q2G[(6 + k) * EQ + o]} : z0;
+                FF a0 = z0, a1 = z0, a2 = z0;
+                ff_mac(G[0].h, G[0].l, g0.h, g0.l, a0.h, a0.l);
+                ff_mac(G[3].h, G[3].l, g1.h, g1.l, a0.h, a0.l);
+                ff_mac(G[4].h, G[4].l, g2.h, g2.l, a0.h, a0.l);
+                ff_mac(G[3].h, G[3].l, g0.h, g0.l, a1.h, a1.l);
+                ff_mac(G[1].h, G[1].l, g1.h, g1.l, a1.h, a1.l);
+                ff_mac(G[5].h, G[5].l, g2.h, g2.l, a1.h, a1.l);
+                ff_mac(G[4].h, G[4].l, g0.h, g0.l, a2.h, a2.l);
+                ff_mac(G[5].h, G[5].l, g1.h, g1.l, a2.h, a2.l);
+                ff_mac(G[2].h, G[2].l, g2.h, g2.l, a2.h, a2.l);
+                ff_normalize(a0.h, a0.l);
+                ff_normalize(a1.h, a1.l);
+                ff_normalize(a2.h, a2.l);
+                f0[q] = a0;
+                f1[q] = a1;
+                f2[q] = a2;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            FF sa = z0, p0 = z0, p1 = z0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                Q2FB(sa, q, a, mv[q]);
+                if (!MASS_ONLY) {
+                    Q2FD(sa, q, a, f2[q]);
+                    Q2FB(p0, q, a, f0[q]);
+                    Q2FB(p1, q, a, f1[q]);
+                }
+            }
+            const int i = c + 9 * a;
+            ff_normalize(sa.h, sa.l);
+            A[i] = sa;
+            if (!MASS_ONLY) {
+                ff_normalize(p0.h, p0.l);
+                ff_normalize(p1.h, p1.l);
+                A[27 + i] = p0;
+                A[54 + i] = p1;
+            }
+        }
+    }
+    __syncthreads();
+    // R1: pencil (q0, a2) = (j0, j1) along direction 1 -> Bf[q0 + 3 a1 + 9 a2]
+    {
+        FF sa[3], p0[3], p1[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int i = j0 + 3 * q + 9 * j1;
+            sa[q] = A[i];
+            if (!MASS_ONLY) {
+                p0[q] = A[27 + i];
+                p1[q] = A[54 + i];
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            FF r = z0, qq = z0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                Q2FB(r, q, a, sa[q]);
+                if (!MASS_ONLY) {
+                    Q2FD(r, q, a, p1[q]);
+                    Q2FB(qq, q, a, p0[q]);
+                }
+            }
+            const int i = j0 + 3 * a + 9 * j1;
+            ff_normalize(r.h, r.l);
+            Bf[i] = r;
+            if (!MASS_ONLY) {
+                ff_normalize(qq.h, qq.l);
+                Bf[27 + i] = qq;
+            }
+        }
+    }
+    __syncthreads();
+    // R0: pencil (a1, a2) = (j0, j1) along direction 0 -> y[a0]
+    {
+        FF r[3], qq[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int i = q + 3 * j0 + 9 * j1;
+            r[q] = Bf[i];
+            if (!MASS_ONLY) qq[q] = Bf[27 + i];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            FF acc = z0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                Q2FB(acc, q, a, r[q]);
+                if (!MASS_ONLY) Q2FD(acc, q, a, qq[q]);
+            }
+            ff_normalize(acc.h, acc.l);
+            y[a] = acc;
+        }
+    }
 }
 
 // Float-float element outputs for the refinement: A u (u = the iterate) and,
-// FIRST, M v as well.
+// FIRST, M v as well; 9 threads (pencils) per element, 28 elements per
+// block.
 template <int FIRST>
-__global__ void __launch_bounds__(kQ2Threads) k_q2_elem_ff(Dev* __restrict__ Dp) {
-    __shared__ FF sm[kQ2Slots][(kQ2Groups + 1) * 27];
+__global__ void __launch_bounds__(9 * kQ2PEl) k_q2_elem_ff(Dev* __restrict__ Dp) {
+    __shared__ FF smA[kQ2PEl][81];
+    __shared__ FF smB[kQ2PEl][81];
     const Dev& D = *Dp;
     if (!FIRST && !D.f_outer) return;  // uniform: the refinement is over
-    const int g = threadIdx.x / 27, t = threadIdx.x % 27;
-    const int e = blockIdx.x * kQ2Groups + g;
-    const bool valid = g < kQ2Groups && e < D.ne;
-    FF* s[kQ2Slots];
-#pragma unroll
-    for (int k = 0; k < kQ2Slots; ++k) s[k] = sm[k] + g * 27;
-    const size_t EQ = (size_t)D.ne * 27;
-    const size_t o = (size_t)e * 27 + t;
-    FF G[6], cm = FF{0.f, 0.f}, x = FF{0.f, 0.f}, xv = FF{0.f, 0.f}, cv = FF{0.f, 0.f};
-#pragma unroll
-    for (int c = 0; c < 6; ++c) G[c] = FF{0.f, 0.f};
+    const int g = threadIdx.x / 9, j = threadIdx.x % 9;
+    const int j0 = j % 3, j1 = j / 3;
+    const int e = blockIdx.x * kQ2PEl + g;
+    const bool valid = e < D.ne;
+    int n = 0;
     if (valid) {
-        const int n = q2_node(D, e, t);
-        x = FF{D.u_hi[n], D.u_lo[n]};
-        if (FIRST) xv = FF{D.v_hi[n], D.v_lo[n]};
-#pragma unroll
-        for (int c = 0; c < 6; ++c) G[c] = FF{D.q2G[c * EQ + o], D.q2G[(6 + c) * EQ + o]};
-        // cm = (alpha/dt |J|) w_q and |J| w_q, the scalars rounded to
-        // float-float once per thread
-        float ah, al, vh, vl;
-        ff_from_double(D.alpha_dt * D.q2vol, ah, al);
-        ff_mul(ah, al, cQ2W[t], cQ2W[27 + t], cm.h, cm.l);
-        ff_from_double(D.q2vol, vh, vl);
-        ff_mul(vh, vl, cQ2W[t], cQ2W[27 + t], cv.h, cv.l);
+        const int ei = e % D.enx, ej = (e / D.enx) % D.eny, ek = e / (D.enx * D.eny);
+        n = (2 * ei) + D.NX * ((2 * ej + j0) + D.NY * (2 * ek + j1));
     }
-    s[0][t] = x;
-    __syncthreads();
-    const FF y = q2_op<FF, false>(s, t, G, cm);
+    FF x[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) x[b] = valid ? FF{D.u_hi[n + b], D.u_lo[n + b]} : FF{0.f, 0.f};
+    FF cm;
+    ff_from_double(D.alpha_dt * D.q2vol, cm.h, cm.l);
+    FF y[3];
+    q2_op_ff<false>(D, valid, e, j0, j1, x, smA[g], smB[g], cm, y);
+    const size_t o = (size_t)e * 27 + 3 * j0 + 9 * j1;  // outputs a = a0 + 3 a1 + 9 a2
     if (valid) {
-        D.q2Yh[o] = y.h;
-        D.q2Yl[o] = y.l;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            D.q2Yh[o + a] = y[a].h;
+            D.q2Yl[o + a] = y[a].l;
+        }
     }
     if (FIRST) {
-        __syncthreads();  // the last pass still reads slot 0
-        s[0][t] = xv;
-        __syncthreads();
-        const FF b = q2_op<FF, true>(s, t, G, cv);
+        FF xv[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) xv[b] = valid ? FF{D.v_hi[n + b], D.v_lo[n + b]} : FF{0.f, 0.f};
+        FF cv;
+        ff_from_double(D.q2vol, cv.h, cv.l);
+        q2_op_ff<true>(D, valid, e, j0, j1, xv, smA[g], smB[g], cv, y);
         if (valid) {
-            D.q2Bh[o] = b.h;
-            D.q2Bl[o] = b.l;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                D.q2Bh[o + a] = y[a].h;
+                D.q2Bl[o + a] = y[a].l;
+            }
         }
     }
 }
@@ -349,7 +491,7 @@ __device__ __forceinline__ V q2_gather(const Dev& D, int n, Load load) {
         for (int b = 0; b < cy; ++b)
             for (int a = 0; a < cx; ++a) {
                 const int e = ex[a] + D.enx * (ey[b] + D.eny * ez[c]);
-                q2_add(acc, load((size_t)e * 27 + lx[a] + 3 * ly[b] + 9 * lz[c]));
+                q2_add(acc, load(e, lx[a] + 3 * ly[b] + 9 * lz[c]));
             }
     return acc;
 }
@@ -365,7 +507,8 @@ __global__ void __launch_bounds__(kNodeThreads) k_q2_gather32(Dev* __restrict__ 
     float v[1] = {0.f};
     const double none[1] = {0.0};
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x) {
-        const float q = q2_gather<float>(D, n, [&](size_t i) { return Y[i]; });
+        // element outputs node-major: [27][ne]
+        const float q = q2_gather<float>(D, n, [&](int e, int a) { return Y[(size_t)a * D.ne + e]; });
         const float p = beta == 0.f ? D.z32[n] : fmaf(beta, pold[n], D.z32[n]);
         pnew[n] = p;
         D.q32[n] = q;
@@ -385,10 +528,16 @@ __global__ void __launch_bounds__(kNodeThreads) k_q2_gather_ff(Dev* __restrict__
     float vf[4] = {0.f, 0.f, 0.f, 0.f};
     const double none[1] = {0.0};
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x) {
-        const FF y = q2_gather<FF>(D, n, [&](size_t i) { return FF{D.q2Yh[i], D.q2Yl[i]}; });
+        const FF y = q2_gather<FF>(D, n, [&](int e, int a) {
+            const size_t i = (size_t)e * 27 + a;
+            return FF{D.q2Yh[i], D.q2Yl[i]};
+        });
         FF b;
         if (FIRST) {
-            b = q2_gather<FF>(D, n, [&](size_t i) { return FF{D.q2Bh[i], D.q2Bl[i]}; });
+            b = q2_gather<FF>(D, n, [&](int e, int a) {
+                const size_t i = (size_t)e * 27 + a;
+                return FF{D.q2Bh[i], D.q2Bl[i]};
+            });
             D.b_hi[n] = b.h;
             D.b_lo[n] = b.l;
         } else {
@@ -424,45 +573,18 @@ __global__ void k_realpha_q2(Dev* __restrict__ Dp, double alpha_dt) {
 
 // ---- host side ---------------------------------------------------------------
 
-// The 1-D tables in double, rounded to float-float pairs.
-cudaError_t q2_upload_tables() {
-    const double r = std::sqrt(15.0) / 10.0;
-    const double xq[3] = {0.5 - r, 0.5, 0.5 + r};
-    const double w1[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
-    float B[18], Dd[18], W[54];
-    auto split = [](double x, float& hi, float& lo) {
-        hi = (float)x;
-        lo = (float)(x - (double)hi);
-    };
-    for (int q = 0; q < 3; ++q) {
-        const double t = xq[q];
-        const double l[3] = {(1.0 - t) * (1.0 - 2.0 * t), 4.0 * t * (1.0 - t), t * (2.0 * t - 1.0)};
-        const double d[3] = {4.0 * t - 3.0, 4.0 - 8.0 * t, 4.0 * t - 1.0};
-        for (int b = 0; b < 3; ++b) {
-            split(l[b], B[3 * q + b], B[9 + 3 * q + b]);
-            split(d[b], Dd[3 * q + b], Dd[9 + 3 * q + b]);
-        }
-    }
-    for (int q = 0; q < 27; ++q) split(w1[q % 3] * w1[(q / 3) % 3] * w1[q / 9], W[q], W[27 + q]);
-    cudaError_t e = cudaMemcpyToSymbol(cQ2B, B, sizeof(B));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cQ2D, Dd, sizeof(Dd));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cQ2W, W, sizeof(W));
-    return e;
-}
-
-int q2_elem_blocks(const Dev& h) { return (h.ne + kQ2Groups - 1) / kQ2Groups; }
-
 void launch_q2_apply32(Dev* d, const Dev& h, int grid_nodes, cudaStream_t s) {
-    k_q2_elem32<<<q2_elem_blocks(h), kQ2Threads, 0, s>>>(d);
+    k_q2_elem32<<<(h.ne + 127) / 128, 128, 0, s>>>(d);
     k_q2_gather32<<<grid_nodes, kNodeThreads, 0, s>>>(d);
 }
 
 void launch_q2_resid(Dev* d, const Dev& h, int first, int graph, int grid_nodes, cudaStream_t s) {
+    const int eb = (h.ne + kQ2PEl - 1) / kQ2PEl;
     if (first) {
-        k_q2_elem_ff<1><<<q2_elem_blocks(h), kQ2Threads, 0, s>>>(d);
+        k_q2_elem_ff<1><<<eb, 9 * kQ2PEl, 0, s>>>(d);
         k_q2_gather_ff<1><<<grid_nodes, kNodeThreads, 0, s>>>(d, graph);
     } else {
-        k_q2_elem_ff<0><<<q2_elem_blocks(h), kQ2Threads, 0, s>>>(d);
+        k_q2_elem_ff<0><<<eb, 9 * kQ2PEl, 0, s>>>(d);
         k_q2_gather_ff<0><<<grid_nodes, kNodeThreads, 0, s>>>(d, graph);
     }
 }

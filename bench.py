@@ -334,15 +334,16 @@ def run_ours(args):
             st = inst.stats()  # synchronises; outside the events
             it_sum += st["cg_iters"]
             sw_sum += st["sweeps"]
+            # (the refined step's per-node end runs inside the next ionic kernel)
             if q2:
-                # ionic, rhs (element + gather), finish; per inner iteration
-                # the apply (element + gather) and the update; per sweep the
-                # correction and the residual (element + gather)
-                launches += 4 + 3 * st["cg_iters"] + 3 * st["sweeps"]
+                # ionic, rhs (element + gather); per inner iteration the apply
+                # (element + gather) and the update; per sweep the correction
+                # and the residual (element + gather)
+                launches += 3 + 3 * st["cg_iters"] + 3 * st["sweeps"]
             elif st["op32"] == ep.EP_OP_STENCIL:
-                launches += 3 + 3 * st["sweeps"]  # ionic, rhs, finish; per sweep: pcg32, correct, resid
+                launches += 2 + 2 * st["sweeps"]  # ionic, rhs; per sweep: pcg32 (with u += delta), resid
             else:
-                launches += 3 + 2 * st["cg_iters"] + 2 * st["sweeps"]
+                launches += 2 + 2 * st["cg_iters"] + 2 * st["sweeps"]
         inst.sync()
         torch.cuda.synchronize()
     if dist:

@@ -41,7 +41,6 @@ void launch_rhs_ff_batch(const Batch& B, int first, int graph, int grid, cudaStr
 void launch_correct_ff_batch(const Batch& B, int grid, cudaStream_t s);
 void launch_resid_np(Dev* d, const Dev& h, int graph, int grid, cudaStream_t s);
 void launch_resid_np_batch(const Batch& B, int graph, int grid, cudaStream_t s);
-void launch_finish_batch(const Batch& B, int grid, cudaStream_t s);
 cudaError_t launch_pcg32_batch(const Batch& B, int grid, cudaStream_t s);
 void launch_batch_cond(Dev* const* devs, int n, const unsigned long long* h, cudaStream_t s);
 cudaError_t launch_prepace(int model, const uint8_t* cells, int ncell, double dt, long long m0, long long nsteps,
@@ -82,6 +81,9 @@ struct ep_instance {
     std::vector<void*> allocs;
     size_t bytes = 0;
     long long host_step = 0;   // step index of the next enqueued step
+    // refined path: a step ran whose per-node end (k_finish_ff's work) waits
+    // for the next step's ionic kernel; reads of the state do it first
+    mutable bool fin_pending = false;
     double alpha_dt_dev = 0;   // alpha/dt the device operators hold
     int grid_nodes = 0;        // grid of the grid-stride node kernels (with reductions)
     int grid_ionic = 0;        // one node per thread
@@ -488,7 +490,9 @@ ep_status build_graph(ep_instance* I) {
             C.chk(cudaStreamEndCapture(s2, &body));
         }
     }
-    epk::launch_finish(I->d, h, I->grid_nodes, s);
+    // the refined path's per-node end of the step runs in the next step's
+    // ionic kernel (or flush_finish when the host reads the state)
+    if (h.prec == EP_PREC_FP64) epk::launch_finish(I->d, h, I->grid_nodes, s);
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(s, &g);
     C.chk(ee);
@@ -573,7 +577,7 @@ ep_status step_host(ep_instance* I) {
             CUDA_TRY(flag(&d->f_outer, &f));
         }
     }
-    timed(I, K_FINISH, [&] { epk::launch_finish(d, h, I->grid_nodes, s); });
+    if (h.prec == EP_PREC_FP64) timed(I, K_FINISH, [&] { epk::launch_finish(d, h, I->grid_nodes, s); });
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(s));
     prof_resolve(I);
@@ -1250,7 +1254,6 @@ ep_status build_plan(BatchPlan* P) {
         epk::launch_batch_cond(dall, n, dh, s2);
         C.chk(cudaStreamEndCapture(s2, &body));
     }
-    epk::launch_finish_batch(Bn, s_nodes.back(), s);
     cudaGraph_t g = nullptr;
     C.chk(cudaStreamEndCapture(s, &g));
     C.chk(cudaGetLastError());
@@ -1407,6 +1410,7 @@ ep_status ep_step_async(ep_instance* I, int64_t n_steps) {
             if (st != EP_OK) return st;
         }
         I->host_step += 1;
+        I->fin_pending = I->h.prec == EP_PREC_FP32_REFINED;
     }
     CUDA_TRY(cudaGetLastError());
     return EP_OK;
@@ -1462,7 +1466,10 @@ ep_status ep_step_batch(ep_instance* const* insts, int32_t n, int64_t n_steps) {
                 }
             }
             CUDA_TRY(cudaGraphLaunch(P->exec, P->stream));
-            for (int32_t k = 0; k < n; ++k) insts[k]->host_step += 1;
+            for (int32_t k = 0; k < n; ++k) {
+                insts[k]->host_step += 1;
+                insts[k]->fin_pending = insts[k]->h.prec == EP_PREC_FP32_REFINED;
+            }
         }
         CUDA_TRY(cudaStreamSynchronize(P->stream));
         ep_status first = EP_OK;
@@ -1494,9 +1501,22 @@ ep_status ep_step_batch(ep_instance* const* insts, int32_t n, int64_t n_steps) {
     return EP_OK;
 }
 
+// Refined instances finish a step's per-node work (activation slope, u_n in
+// double) in the next step's ionic kernel; before the host reads the state,
+// the last step's is done here (the same idempotent kernel).
+static ep_status flush_finish(const ep_instance* I) {
+    if (I->fin_pending) {
+        epk::launch_finish(I->d, I->h, I->grid_nodes, I->stream);
+        CUDA_TRY(cudaGetLastError());
+        I->fin_pending = false;
+    }
+    return EP_OK;
+}
+
 ep_status ep_read_potential(const ep_instance* I, double* out, int64_t n) {
     if (!I || !out) return fail(EP_EINVAL, "NULL argument");
     if (n != I->h.N) return fail(EP_EINVAL, "n must equal n_nodes");
+    if (ep_status st = flush_finish(I); st != EP_OK) return st;
     Dev tmp;
     CUDA_TRY(cudaMemcpyAsync(&tmp, I->d, sizeof(Dev), cudaMemcpyDeviceToHost, I->stream));
     CUDA_TRY(cudaStreamSynchronize(I->stream));
@@ -1509,6 +1529,7 @@ ep_status ep_read_potential(const ep_instance* I, double* out, int64_t n) {
 ep_status ep_activation_times(const ep_instance* I, double* out, int64_t n) {
     if (!I || !out) return fail(EP_EINVAL, "NULL argument");
     if (n != I->h.N) return fail(EP_EINVAL, "n must equal n_nodes");
+    if (ep_status st = flush_finish(I); st != EP_OK) return st;
     CUDA_TRY(cudaStreamSynchronize(I->stream));
     std::vector<double> best((size_t)n);
     CUDA_TRY(cudaMemcpy(out, I->h.at, (size_t)n * 8, cudaMemcpyDeviceToHost));
@@ -1568,6 +1589,7 @@ ep_status ep_save_state(const ep_instance* I, void* buf, size_t bytes) {
     if (!I || !buf) return fail(EP_EINVAL, "NULL argument");
     const size_t need = ep_state_bytes(I);
     if (bytes < need) return fail(EP_EINVAL, "buffer too small: need " + std::to_string(need));
+    if (ep_status st = flush_finish(I); st != EP_OK) return st;
     Dev t;
     CUDA_TRY(cudaMemcpyAsync(&t, I->d, sizeof(Dev), cudaMemcpyDeviceToHost, I->stream));
     CUDA_TRY(cudaStreamSynchronize(I->stream));
@@ -1718,6 +1740,9 @@ ep_status ep_load_state(ep_instance* I, const void* buf, size_t bytes) {
     int zero = 0;
     CUDA_TRY(cudaMemcpy(&I->d->step, &step, sizeof(step), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(&I->d->status, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    // the loaded step's per-node end is part of the state: not redone
+    CUDA_TRY(cudaMemcpy(&I->d->fin_pending, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    I->fin_pending = false;
     CUDA_TRY(cudaMemset(t.counter, 0, epk::CNT_N * sizeof(unsigned int)));
     I->host_step = step;
     I->sticky = EP_OK;
@@ -1775,6 +1800,7 @@ ep_status ep_get_stats(const ep_instance* I, ep_stats* out) {
 
 ep_status ep_potential_device(const ep_instance* I, const double** out) {
     if (!I || !out) return fail(EP_EINVAL, "NULL argument");
+    if (ep_status st = flush_finish(I); st != EP_OK) return st;
     Dev t;
     CUDA_TRY(cudaMemcpyAsync(&t, I->d, sizeof(Dev), cudaMemcpyDeviceToHost, I->stream));
     CUDA_TRY(cudaStreamSynchronize(I->stream));

@@ -95,6 +95,9 @@ struct Dev {
     float *yc_hi, *yc_lo, *yn_hi, *yn_lo, *ym_hi, *ym_lo;
     float *ym2_hi, *ym2_lo;     // step n-2's (BDF3)
     int hist;
+    // 1 from the end of a refined step until the next step's right-hand
+    // side: the ionic kernel then does the previous step's per-node end
+    int fin_pending;
     double *at, *best;
     // ---- operators -----------------------------------------------------------
     double *M64, *A64;          // [kSlots][N] (symmetric, FP64)
@@ -365,6 +368,7 @@ __device__ __forceinline__ void end_of_step(Dev& D) {
         D.yc_lo = yl;
         const int hmax = D.ym2_hi ? 3 : 2;
         D.hist = D.hist < hmax ? D.hist + 1 : hmax;
+        D.fin_pending = 1;
     }
     D.step += 1;
     D.done_step = D.step;

@@ -31,6 +31,7 @@ __device__ __forceinline__ void rhs_finish(Dev& D, const double* t, bool FIRST, 
     }
     D.rr = t[3];
     if (FIRST) {
+        D.fin_pending = 0;  // the ionic kernel before this pass has done it
         D.sweeps = 0;
         D.it_total = 0;
         // the persistent solver's barrier counter starts the step at 0

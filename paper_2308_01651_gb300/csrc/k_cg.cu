@@ -90,11 +90,14 @@ __global__ void __launch_bounds__(kNodeThreads) k_finish(Batch B) {
     });
 }
 
-// Refined path: the refinement's last residual pass has already rotated the
-// time levels (end_of_step), so the new potential is level n and the old one
-// level n-1.  Per node: the activation slope in float from the pairs, the
-// new potential rounded to double for u_n.  A non-finite potential has
-// already made that residual NaN (EP_ENAN); no reduction is needed here.
+// Refined path, the per-node end of a step: the refinement's last residual
+// pass has already rotated the time levels (end_of_step), so the new
+// potential is level n and the old one level n-1.  Per node: the activation
+// slope in float from the pairs, the new potential rounded to double for
+// u_n.  A non-finite potential has already made that residual NaN (EP_ENAN);
+// no reduction is needed here.  The next step's ionic kernel does the same
+// work on its way (finish_prev_ff); this kernel runs only when the host
+// reads the state before another step.  Idempotent.
 __global__ void __launch_bounds__(kNodeThreads) k_finish_ff(Batch B) {
     const Slot S = batch_slot(B);
     Dev& D = *S.D;
@@ -138,7 +141,5 @@ void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s) {
     if (h.prec == EP_PREC_FP32_REFINED) k_finish_ff<<<grid, kNodeThreads, 0, s>>>(single_batch(d));
     else k_finish<<<grid, kNodeThreads, 0, s>>>(single_batch(d));
 }
-// refined instances
-void launch_finish_batch(const Batch& B, int grid, cudaStream_t s) { k_finish_ff<<<grid, kNodeThreads, 0, s>>>(B); }
 
 }  // namespace epk

@@ -73,6 +73,22 @@ __device__ __forceinline__ void store_vu64(const Dev& D, int n, double v, double
     D.u_new[n] = uE;
 }
 
+// The per-node end of the previous step of a refined instance, deferred from
+// that step to this kernel (which reads the same potential levels): the
+// activation slope u_n - u_{n-1} in float from the pairs, the largest slope
+// and its time t (Sec. 3.2.1: first maximum wins), and u_n rounded to
+// double for the public potential.  Idempotent: k_finish_ff does the same
+// when the host reads the state between steps.
+__device__ __forceinline__ void finish_prev_ff(const Dev& D, int n, double t, float h0, float l0, float h1,
+                                               float l1) {
+    const float s = (h0 - h1) + (l0 - l1);  // levels n and n-1
+    D.u_n[n] = ff_to_double(h0, l0);
+    if (s > D.bestf[n]) {
+        D.bestf[n] = s;
+        D.at[n] = t;
+    }
+}
+
 // BDF combinations of one quantity from its levels n, n-1, n-2:
 //   order 1: B = E = x;  order 2: B = 2x - y/2, E = 2x - y;
 //   order 3: B = 3x - 3y/2 + z/3, E = 3x - 3y + z.
@@ -91,11 +107,17 @@ __device__ __forceinline__ void bdf_comb(int order, T x, T y, T z, T& B, T& E) {
 
 // Refined path: the potential's BDF combinations from its float-float
 // levels (the scalings by 2 and 1/2 are exact; by 3 and 1/3 float-float).
-__device__ __forceinline__ void u_bdf_ff(const Dev& D, int order, int n, float& bh, float& bl, float& eh,
-                                         float& el) {
+__device__ __forceinline__ void u_bdf_ff(const Dev& D, int order, int n, bool fin, double t_fin, float& bh,
+                                         float& bl, float& eh, float& el) {
     const float h0 = D.uh_n[n], l0 = D.ul_n[n];
+    float h1 = 0.f, l1 = 0.f;
+    if (order >= 2 || fin) {
+        h1 = D.uh_m[n];
+        l1 = D.ul_m[n];
+    }
+    if (fin) finish_prev_ff(D, n, t_fin, h0, l0, h1, l1);
     if (order == 3) {
-        const float h1 = D.uh_m[n], l1 = D.ul_m[n], h2 = D.uh_m2[n], l2 = D.ul_m2[n];
+        const float h2 = D.uh_m2[n], l2 = D.ul_m2[n];
         float th, tl, ah, al, ch, cl;
         ff_mul(h0, l0, 3.f, 0.f, th, tl);      // 3 u_n
         ff_mul(h1, l1, 3.f, 0.f, ah, al);      // 3 u_{n-1}
@@ -105,7 +127,6 @@ __device__ __forceinline__ void u_bdf_ff(const Dev& D, int order, int n, float& 
         ff_mul(h2, l2, kThirdHi, kThirdLo, ch, cl);
         ff_sub(bh, bl, -ch, -cl, bh, bl);
     } else if (order == 2) {
-        const float h1 = D.uh_m[n], l1 = D.ul_m[n];
         ff_sub(2.f * h0, 2.f * l0, 0.5f * h1, 0.5f * l1, bh, bl);
         ff_sub(2.f * h0, 2.f * l0, h1, l1, eh, el);
     } else {
@@ -164,12 +185,15 @@ __global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Batch B) {
              reinterpret_cast<const G*>(D.s64_nm2), reinterpret_cast<G*>(D.s64_nm2 ? D.s64_nm2 : D.s64_nm1)};
     }
     const G dtg = G(c.dt), alg = G(c.alpha);
+    // refined path: the per-node end of the previous step, deferred to here
+    const bool fin = sizeof(G) == 4 && D.fin_pending;
+    const double t_fin = (double)D.step * D.dt;
     for (int n = S.blk * blockDim.x + threadIdx.x; n < N; n += S.nblk * blockDim.x) {
         G uEg;
         double uB = 0.0, uE = 0.0;
         float ubh = 0.f, ubl = 0.f, ueh = 0.f, uel = 0.f;
         if constexpr (sizeof(G) == 4) {
-            u_bdf_ff(D, c.order, n, ubh, ubl, ueh, uel);
+            u_bdf_ff(D, c.order, n, fin, t_fin, ubh, ubl, ueh, uel);
             uEg = ueh;
         } else {
             bdf_comb<double>(c.order, D.u_n[n], c.order > 1 ? D.u_nm1[n] : 0.0, c.order > 2 ? D.u_nm2[n] : 0.0,
@@ -210,6 +234,9 @@ __device__ __forceinline__ void ionic_tt_nodes(const Slot& S, const Dev& D, cons
     const int N = D.N;
     const G dtg = G(c.dt), alg = G(c.alpha);
     constexpr int ord = ORD;
+    // refined path: the per-node end of the previous step, deferred to here
+    const bool fin = sizeof(G) == 4 && D.fin_pending;
+    const double t_fin = (double)D.step * D.dt;
     for (int n = S.blk * blockDim.x + threadIdx.x; n < N; n += S.nblk * blockDim.x) {
         const int cell = D.cell[n];
         if constexpr (sizeof(G) == 4) {
@@ -226,7 +253,7 @@ __device__ __forceinline__ void ionic_tt_nodes(const Slot& S, const Dev& D, cons
             float* const cho = LV3 ? chm2 : chm;
             const size_t LO = (size_t)kTTConc * N;  // lo parts follow the hi parts
             float ubh, ubl, ueh, uel;
-            u_bdf_ff(D, ord, n, ubh, ubl, ueh, uel);
+            u_bdf_ff(D, ord, n, fin, t_fin, ubh, ubl, ueh, uel);
             if (D.active && !D.active[n]) {
                 // excluded from the simulation: states held, no currents
 #pragma unroll
@@ -361,6 +388,9 @@ __global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_
     const StepConsts c = step_consts(D);
     const int N = D.N;
     const G dtg = G(c.dt), alg = G(c.alpha);
+    // refined path: the per-node end of the previous step, deferred to here
+    const bool fin = sizeof(G) == 4 && D.fin_pending;
+    const double t_fin = (double)D.step * D.dt;
     for (int n = S.blk * blockDim.x + threadIdx.x; n < N; n += S.nblk * blockDim.x) {
         const int cell = D.cell[n];
         if constexpr (sizeof(G) == 4) {
@@ -371,7 +401,7 @@ __global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_
             float* __restrict__ chm = reinterpret_cast<float*>(D.s64_nm1);
             const size_t LO = (size_t)kTTConc * N;  // lo parts follow the hi parts
             float ubh, ubl, ueh, uel;
-            u_bdf_ff(D, c.order, n, ubh, ubl, ueh, uel);
+            u_bdf_ff(D, c.order, n, fin, t_fin, ubh, ubl, ueh, uel);
             float gB[kTTGates], gE[kTTGates];
             float ch[kTTConc], cl[kTTConc], dc[kTTConc], cE[kTTConc];
 #pragma unroll

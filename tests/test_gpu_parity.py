@@ -230,7 +230,8 @@ def test_graph_and_host_driven_stepping_agree():
     ep.ep_profile_enable(b.h, False)
     b.step(10)
     assert np.array_equal(a.save(), b.save())
-    assert prof["ionic"][0] == 10 and prof["finish"][0] == 10
+    # the refined step's per-node end runs inside the next ionic kernel
+    assert prof["ionic"][0] == 10 and "finish" not in prof
     if "pcg32" in prof:  # persistent inner solver: one launch per refinement sweep,
         # which applies its own correction; a residual after each
         assert prof["pcg32"][0] == prof["resid"][0] > 0 and "correct" not in prof

@@ -244,7 +244,8 @@ size_t footprint(const Sizes& z) {
             const size_t eq = (size_t)z.ne * 27;
             b += al(12 * eq * 4);         // quadrature-point flux matrices (hi, lo)
             b += al(6 * eq * 4);          // their hi parts, element fastest (FP32 apply)
-            b += 5 * al(eq * 4);          // element outputs: FP32 apply, A u and M v (hi, lo)
+            b += al(8 * N * 4);           // FP32 apply's element outputs in node slots
+            b += 4 * al(eq * 4);          // element outputs of A u and M v (hi, lo)
             b += 2 * al(N * 8);           // diagonals of M and K
         } else {
             b += 2 * al(epk::kGroups * N * 16);                          // Ahi Alo
@@ -825,7 +826,7 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
             float* G32 = nullptr;
             ALLOC(G32, 6 * eq);
             h.q2G32 = G32;
-            ALLOC(h.q2Y32, eq);
+            ALLOC(h.q2Y32, 8 * N);
             ALLOC(h.q2Yh, eq);
             ALLOC(h.q2Yl, eq);
             ALLOC(h.q2Bh, eq);

@@ -114,7 +114,7 @@ struct Dev {
     const float* q2G;           // [2][6][ne * 27]: hi, then lo parts of the quadrature
                                 // point flux matrices w_q |J| H D(q) H (xx yy zz xy xz yz)
     const float* q2G32;         // [6][27][ne]: the hi parts again, element fastest (FP32 apply)
-    float* q2Y32;               // [27][ne] element outputs of the FP32 apply
+    float* q2Y32;               // [8][N] element outputs of the FP32 apply in node slots
     float *q2Yh, *q2Yl;         // [ne * 27] element outputs of A u (float-float)
     float *q2Bh, *q2Bl;         // [ne * 27] element outputs of M v (float-float)
     double *q2dM, *q2dK;        // diagonals of M and K

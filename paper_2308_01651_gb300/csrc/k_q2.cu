@@ -71,7 +71,7 @@ __device__ __forceinline__ float q2dot(float c0, float x0, float c1, float x1, f
 // z + beta p_old at the element's 27 nodes, the element outputs of A p,
 // node-major [27][ne].  The flux matrices are read from their element-fastest
 // FP32 copy [6][27][ne] (coalesced).
-__global__ void __launch_bounds__(128) k_q2_elem32(Dev* __restrict__ Dp) {
+__global__ void __launch_bounds__(128, 4) k_q2_elem32(Dev* __restrict__ Dp) {
     const Dev& D = *Dp;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= D.ne) return;
@@ -156,17 +156,40 @@ __global__ void __launch_bounds__(128) k_q2_elem32(Dev* __restrict__ Dp) {
                 qq[i + 3 * a1] = q2dot(Q2B(0, a1), p0[i], Q2B(1, a1), p0[i + 3], Q2B(2, a1), p0[i + 6]);
             }
         }
-    // R0 (direction 0, transposed) and the node-major store
+    // R0 (direction 0, transposed) and the store into the node slots: slot
+    // bit d is 1 where the node is this element's first node along d (local
+    // index 0), so the (up to 8) elements of a node write distinct slots
     float* __restrict__ Y = D.q2Y32;
+    const size_t NN = (size_t)D.N;
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
 #pragma unroll
         for (int a0 = 0; a0 < 3; ++a0) {
             const float y = q2dot(Q2B(0, a0), rr[3 * r], Q2B(1, a0), rr[3 * r + 1], Q2B(2, a0), rr[3 * r + 2]) +
                             q2dot(Q2D(0, a0), qq[3 * r], Q2D(1, a0), qq[3 * r + 1], Q2D(2, a0), qq[3 * r + 2]);
-            Y[(size_t)(a0 + 3 * r) * E + e] = y;
+            const int a1 = r % 3, a2 = r / 3;
+            const int slot = (a0 == 0) + 2 * (a1 == 0) + 4 * (a2 == 0);
+            Y[(size_t)slot * NN + n0 + a0 + NX * a1 + NXY * a2] = y;
         }
     }
+}
+
+// Sum of node n's slots (1, 2, 4 or 8 of them: along each direction slot 1
+// holds the element the node starts, slot 0 the element it ends or is
+// interior to) in a fixed order.
+__device__ __forceinline__ float q2_gather_slots(const Dev& D, int n, const float* __restrict__ Y) {
+    const int I = n % D.NX, J = (n / D.NX) % D.NY, K = n / (D.NX * D.NY);
+    const bool x0 = (I & 1) || I > 0, x1 = !(I & 1) && I < D.NX - 1;
+    const bool y0 = (J & 1) || J > 0, y1 = !(J & 1) && J < D.NY - 1;
+    const bool z0 = (K & 1) || K > 0, z1 = !(K & 1) && K < D.NZ - 1;
+    const size_t NN = (size_t)D.N;
+    float acc = 0.f;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const bool ok = ((s & 1) ? x1 : x0) && ((s & 2) ? y1 : y0) && ((s & 4) ? z1 : z0);
+        if (ok) acc += Y[(size_t)s * NN + n];
+    }
+    return acc;
 }
 
 // The 1-D tables as float-float pairs (hi, lo of the double values), for
@@ -507,8 +530,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_q2_gather32(Dev* __restrict__ 
     float v[1] = {0.f};
     const double none[1] = {0.0};
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x) {
-        // element outputs node-major: [27][ne]
-        const float q = q2_gather<float>(D, n, [&](int e, int a) { return Y[(size_t)a * D.ne + e]; });
+        const float q = q2_gather_slots(D, n, Y);
         const float p = beta == 0.f ? D.z32[n] : fmaf(beta, pold[n], D.z32[n]);
         pnew[n] = p;
         D.q32[n] = q;

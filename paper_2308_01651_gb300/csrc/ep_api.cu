@@ -1083,7 +1083,7 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     // per SM (one partial sum and one counter update per block); tiled
     // stencil kernels: two 512-thread blocks per SM
     I->grid_nodes = std::max(1, std::min(blocks, 4 * sms));
-    I->grid_ionic = blocks;
+    I->grid_ionic = (int)((N + epk::kIonicThreads - 1) / epk::kIonicThreads);
     I->grid_tiles = std::max(1, std::min(epk::st_tiles(h), 2 * sms));
     if (ref) {
         // the persistent solver's blocks must all be resident at once

@@ -26,6 +26,10 @@ constexpr int kMaxBlock = 512;
 // threads per block of the node-wise kernels
 constexpr int kNodeThreads = 256;
 constexpr int kNodesPerThread = 4;
+// threads per block of the ionic kernels (one node per thread; 128-thread
+// blocks schedule the register-heavy TTP06 step better than 256 at the same
+// occupancy)
+constexpr int kIonicThreads = 128;
 constexpr int kNodeTile = kNodeThreads * kNodesPerThread;
 // tiled stencil kernels: owned tile kStTx x kStTy x kStTz, threads per block
 constexpr int kStTx = 32, kStTy = 4, kStTz = 4;

@@ -171,7 +171,7 @@ struct Levels {
 // G: arithmetic/storage type of the gates (float when refined, double in the
 // FP64 path).
 template <typename G>
-__global__ void __launch_bounds__(kNodeThreads) k_ionic_bo(Batch B) {
+__global__ void __launch_bounds__(kIonicThreads) k_ionic_bo(Batch B) {
     const Slot S = batch_slot(B);
     const Dev& D = *S.D;
     const StepConsts c = step_consts(D);
@@ -368,7 +368,7 @@ __device__ __forceinline__ void ionic_tt_nodes(const Slot& S, const Dev& D, cons
 
 // BDF3 instances (three levels)
 template <typename G>
-__global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_tt3(Batch B) {
+__global__ void __launch_bounds__(kIonicThreads, sizeof(G) == 4 ? 6 : 1) k_ionic_tt3(Batch B) {
     const Slot S = batch_slot(B);
     const Dev& D = *S.D;
     const StepConsts c = step_consts(D);
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_
 // its register allocation is not shaped by the three-level variant (this
 // one sits at the 80-register cap of three resident blocks per SM).
 template <typename G>
-__global__ void __launch_bounds__(kNodeThreads, sizeof(G) == 4 ? 3 : 1) k_ionic_tt2(Batch B) {
+__global__ void __launch_bounds__(kIonicThreads, sizeof(G) == 4 ? 6 : 1) k_ionic_tt2(Batch B) {
     const Slot S = batch_slot(B);
     const Dev& D = *S.D;
     const StepConsts c = step_consts(D);
@@ -536,22 +536,22 @@ void launch_ionic(Dev* d, const Dev& h, int grid, cudaStream_t s) {
     const bool refined = h.prec == EP_PREC_FP32_REFINED;
     const Batch B = single_batch(d);
     if (h.model == EP_MODEL_BO) {
-        if (refined) k_ionic_bo<float><<<grid, kNodeThreads, 0, s>>>(B);
-        else k_ionic_bo<double><<<grid, kNodeThreads, 0, s>>>(B);
+        if (refined) k_ionic_bo<float><<<grid, kIonicThreads, 0, s>>>(B);
+        else k_ionic_bo<double><<<grid, kIonicThreads, 0, s>>>(B);
     } else if (h.u_nm2) {
-        if (refined) k_ionic_tt3<float><<<grid, kNodeThreads, 0, s>>>(B);
-        else k_ionic_tt3<double><<<grid, kNodeThreads, 0, s>>>(B);
+        if (refined) k_ionic_tt3<float><<<grid, kIonicThreads, 0, s>>>(B);
+        else k_ionic_tt3<double><<<grid, kIonicThreads, 0, s>>>(B);
     } else {
-        if (refined) k_ionic_tt2<float><<<grid, kNodeThreads, 0, s>>>(B);
-        else k_ionic_tt2<double><<<grid, kNodeThreads, 0, s>>>(B);
+        if (refined) k_ionic_tt2<float><<<grid, kIonicThreads, 0, s>>>(B);
+        else k_ionic_tt2<double><<<grid, kIonicThreads, 0, s>>>(B);
     }
 }
 
 // refined instances of one model and number of levels, batched
 void launch_ionic_batch(const Batch& B, int model, bool lv3, int grid, cudaStream_t s) {
-    if (model == EP_MODEL_BO) k_ionic_bo<float><<<grid, kNodeThreads, 0, s>>>(B);
-    else if (lv3) k_ionic_tt3<float><<<grid, kNodeThreads, 0, s>>>(B);
-    else k_ionic_tt2<float><<<grid, kNodeThreads, 0, s>>>(B);
+    if (model == EP_MODEL_BO) k_ionic_bo<float><<<grid, kIonicThreads, 0, s>>>(B);
+    else if (lv3) k_ionic_tt3<float><<<grid, kIonicThreads, 0, s>>>(B);
+    else k_ionic_tt2<float><<<grid, kIonicThreads, 0, s>>>(B);
 }
 
 }  // namespace epk

@@ -87,6 +87,7 @@ struct ep_instance {
     double alpha_dt_dev = 0;   // alpha/dt the device operators hold
     int grid_nodes = 0;        // grid of the grid-stride node kernels (with reductions)
     int grid_ionic = 0;        // one node per thread
+    int grid_resid = 0;        // node-parallel residual: 512-thread blocks, two per SM
     int grid_tiles = 0;        // persistent grid of the tiled stencil kernels
     int grid_pcg = 0;          // cooperative grid of the persistent inner solver
     ep_status sticky = EP_OK;
@@ -469,7 +470,7 @@ ep_status build_graph(ep_instance* I) {
         if (C.err == cudaSuccess) {
             C.chk(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
             C.chk(epk::launch_pcg32(I->d, h, I->grid_pcg, s2));  // ends with u += delta
-            epk::launch_resid_np(I->d, h, 1, I->grid_nodes, s2);
+            epk::launch_resid_np(I->d, h, 1, I->grid_resid, s2);
             C.chk(cudaStreamEndCapture(s2, &body));
         }
     } else {
@@ -487,7 +488,7 @@ ep_status build_graph(ep_instance* I) {
             }
             epk::launch_correct_ff(I->d, h, I->grid_nodes, s2);
             if (h.q2) epk::launch_q2_resid(I->d, h, 0, 1, I->grid_nodes, s2);
-            else epk::launch_resid_np(I->d, h, 1, I->grid_nodes, s2);
+            else epk::launch_resid_np(I->d, h, 1, I->grid_resid, s2);
             C.chk(cudaStreamEndCapture(s2, &body));
         }
     }
@@ -572,7 +573,7 @@ ep_status step_host(ep_instance* I) {
                 timed(I, K_CORRECT, [&] { epk::launch_correct_ff(d, h, I->grid_nodes, s); });
             timed(I, K_RESID, [&] {
                 if (h.q2) epk::launch_q2_resid(d, h, 0, 0, I->grid_nodes, s);
-                else epk::launch_resid_np(d, h, 0, I->grid_nodes, s);
+                else epk::launch_resid_np(d, h, 0, I->grid_resid, s);
             });
             CUDA_TRY(cudaGetLastError());
             CUDA_TRY(flag(&d->f_outer, &f));
@@ -1084,6 +1085,7 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     // stencil kernels: two 512-thread blocks per SM
     I->grid_nodes = std::max(1, std::min(blocks, 4 * sms));
     I->grid_ionic = (int)((N + epk::kIonicThreads - 1) / epk::kIonicThreads);
+    I->grid_resid = std::max(1, std::min((int)((N + epk::kResidThreads - 1) / epk::kResidThreads), 2 * sms));
     I->grid_tiles = std::max(1, std::min(epk::st_tiles(h), 2 * sms));
     if (ref) {
         // the persistent solver's blocks must all be resident at once
@@ -1191,7 +1193,7 @@ ep_status build_plan(BatchPlan* P) {
         ep_instance* I = P->key[i];
         all.push_back(I->d);
         s_tiles.push_back(s_tiles.back() + I->grid_tiles);
-        s_nodes.push_back(s_nodes.back() + I->grid_nodes);
+        s_nodes.push_back(s_nodes.back() + I->grid_resid);
         s_pcg.push_back(s_pcg.back() + gp[i]);
         const int gi = I->h.model == EP_MODEL_BO ? 0 : (I->h.u_nm2 ? 2 : 1);
         grp[gi].push_back(I->d);
@@ -1846,12 +1848,12 @@ ep_status ep_residual_norm_noalloc(const ep_instance* I, double* relres_out) {
     if (I->h.prec != EP_PREC_FP32_REFINED)
         return fail(EP_EUNSUPPORTED, "the allocation-free residual serves FP32_REFINED instances");
     if (I->h.q2) return fail(EP_EUNSUPPORTED, "the allocation-free residual serves structured-stencil instances");
-    if (I->grid_nodes > epk::noalloc_max_blocks())
-        return fail(EP_EINVAL, "the residual of this instance needs " + std::to_string(I->grid_nodes) +
+    if (I->grid_resid > epk::noalloc_max_blocks())
+        return fail(EP_EINVAL, "the residual of this instance needs " + std::to_string(I->grid_resid) +
                                    " thread blocks; the allocation-free path holds partial sums for at most " +
                                    std::to_string(epk::noalloc_max_blocks()));
     double sums[2] = {0.0, 0.0};
-    CUDA_TRY(epk::residual_norm_noalloc(I->d, I->grid_nodes, I->stream, sums));
+    CUDA_TRY(epk::residual_norm_noalloc(I->d, I->grid_resid, I->stream, sums));
     *relres_out = sums[0] > 0.0 ? std::sqrt(sums[1] / sums[0]) : std::sqrt(sums[1]);
     return EP_OK;
 }

@@ -30,6 +30,9 @@ constexpr int kNodesPerThread = 4;
 // blocks schedule the register-heavy TTP06 step better than 256 at the same
 // occupancy)
 constexpr int kIonicThreads = 128;
+// threads per block of the node-parallel residual (two blocks per SM at 64
+// registers; measured faster than four of 256 or eight of 128)
+constexpr int kResidThreads = 512;
 constexpr int kNodeTile = kNodeThreads * kNodesPerThread;
 // tiled stencil kernels: owned tile kStTx x kStTy x kStTz, threads per block
 constexpr int kStTx = 32, kStTy = 4, kStTz = 4;

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kStThreads) k_rhs_ff(Batch B, int graph) {
 // barriers between the coefficient streams -- and writes y = A u (the step's
 // history), r = b - y and the inner solver's start (r32, u = D^-1 r32, delta
 // = 0).  Same terms, order and totals as the tiled pass.
-__global__ void __launch_bounds__(kNodeThreads) k_resid_np(Batch B, int graph) {
+__global__ void __launch_bounds__(kResidThreads) k_resid_np(Batch B, int graph) {
     const Slot S = batch_slot(B);
     Dev& D = *S.D;
     if (!D.f_outer) return;
@@ -194,7 +194,7 @@ void launch_resid_np(Dev* d, const Dev& h, int graph, int grid, cudaStream_t s) 
     launch_resid_np_batch(single_batch(d), graph, grid, s);
 }
 void launch_resid_np_batch(const Batch& B, int graph, int grid, cudaStream_t s) {
-    k_resid_np<<<grid, kNodeThreads, 0, s>>>(B, graph);
+    k_resid_np<<<grid, kResidThreads, 0, s>>>(B, graph);
 }
 
 void launch_correct_ff(Dev* d, const Dev& h, int grid, cudaStream_t s) {

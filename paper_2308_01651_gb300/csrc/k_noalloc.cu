@@ -44,7 +44,7 @@ constexpr size_t kNoAllocScratchBytes = kNoAllocCounterOff + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-__global__ void __launch_bounds__(kNodeThreads) k_residual_norm_noalloc(const Dev* __restrict__ Dp,
+__global__ void __launch_bounds__(kResidThreads) k_residual_norm_noalloc(const Dev* __restrict__ Dp,
                                                                          unsigned char* scratch) {
     const Dev& D = *Dp;
     const int N = D.N;
@@ -108,7 +108,7 @@ cudaError_t residual_norm_noalloc(Dev* d, int grid, cudaStream_t s, double sums[
     unsigned char* base = static_cast<unsigned char*>(scratch);
     e = cudaMemsetAsync(base + kNoAllocCounterOff, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    k_residual_norm_noalloc<<<grid, kNodeThreads, 0, s>>>(d, base);
+    k_residual_norm_noalloc<<<grid, kResidThreads, 0, s>>>(d, base);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(sums, base + kNoAllocTotalOff, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -246,7 +246,7 @@ size_t footprint(const Sizes& z) {
             b += al(12 * eq * 4);         // quadrature-point flux matrices (hi, lo)
             b += al(6 * eq * 4);          // their hi parts, element fastest (FP32 apply)
             b += al(8 * N * 4);           // FP32 apply's element outputs in node slots
-            b += 4 * al(eq * 4);          // element outputs of A u and M v (hi, lo)
+            b += 4 * al(8 * N * 4);       // element outputs of A u and M v (hi, lo) in node slots
             b += 2 * al(N * 8);           // diagonals of M and K
         } else {
             b += 2 * al(epk::kGroups * N * 16);                          // Ahi Alo
@@ -828,10 +828,10 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
             ALLOC(G32, 6 * eq);
             h.q2G32 = G32;
             ALLOC(h.q2Y32, 8 * N);
-            ALLOC(h.q2Yh, eq);
-            ALLOC(h.q2Yl, eq);
-            ALLOC(h.q2Bh, eq);
-            ALLOC(h.q2Bl, eq);
+            ALLOC(h.q2Yh, 8 * N);
+            ALLOC(h.q2Yl, 8 * N);
+            ALLOC(h.q2Bh, 8 * N);
+            ALLOC(h.q2Bl, 8 * N);
             ALLOC(h.q2dM, N);
             ALLOC(h.q2dK, N);
         } else {

@@ -122,8 +122,8 @@ struct Dev {
                                 // point flux matrices w_q |J| H D(q) H (xx yy zz xy xz yz)
     const float* q2G32;         // [6][27][ne]: the hi parts again, element fastest (FP32 apply)
     float* q2Y32;               // [8][N] element outputs of the FP32 apply in node slots
-    float *q2Yh, *q2Yl;         // [ne * 27] element outputs of A u (float-float)
-    float *q2Bh, *q2Bl;         // [ne * 27] element outputs of M v (float-float)
+    float *q2Yh, *q2Yl;         // [8][N] element outputs of A u in node slots (float-float)
+    float *q2Bh, *q2Bl;         // [8][N] element outputs of M v in node slots (float-float)
     double *q2dM, *q2dK;        // diagonals of M and K
     float mf_cn[3], mf_cl, mf_ct, mf_cmass;
     double alpha_dt;            // alpha_BDF/dt the operators currently hold

@@ -176,20 +176,25 @@ __global__ void __launch_bounds__(128, 4) k_q2_elem32(Dev* __restrict__ Dp) {
 
 // Sum of node n's slots (1, 2, 4 or 8 of them: along each direction slot 1
 // holds the element the node starts, slot 0 the element it ends or is
-// interior to) in a fixed order.
-__device__ __forceinline__ float q2_gather_slots(const Dev& D, int n, const float* __restrict__ Y) {
+// interior to) in a fixed order; load(slot) returns one.
+template <typename V, typename Load>
+__device__ __forceinline__ V q2_gather_slots_v(const Dev& D, int n, Load load) {
     const int I = n % D.NX, J = (n / D.NX) % D.NY, K = n / (D.NX * D.NY);
     const bool x0 = (I & 1) || I > 0, x1 = !(I & 1) && I < D.NX - 1;
     const bool y0 = (J & 1) || J > 0, y1 = !(J & 1) && J < D.NY - 1;
     const bool z0 = (K & 1) || K > 0, z1 = !(K & 1) && K < D.NZ - 1;
-    const size_t NN = (size_t)D.N;
-    float acc = 0.f;
+    V acc;
+    q2_zero(acc);
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
         const bool ok = ((s & 1) ? x1 : x0) && ((s & 2) ? y1 : y0) && ((s & 4) ? z1 : z0);
-        if (ok) acc += Y[(size_t)s * NN + n];
+        if (ok) q2_add(acc, load(s));
     }
     return acc;
+}
+__device__ __forceinline__ float q2_gather_slots(const Dev& D, int n, const float* __restrict__ Y) {
+    const size_t NN = (size_t)D.N;
+    return q2_gather_slots_v<float>(D, n, [&](int s) { return Y[(size_t)s * NN + n]; });
 }
 
 // The 1-D tables as float-float pairs (hi, lo of the double values), for
@@ -453,12 +458,16 @@ __global__ void __launch_bounds__(9 * kQ2PEl) k_q2_elem_ff(Dev* __restrict__ Dp)
     ff_from_double(D.alpha_dt * D.q2vol, cm.h, cm.l);
     FF y[3];
     q2_op_ff<false>(D, valid, e, j0, j1, x, smA[g], smB[g], cm, y);
-    const size_t o = (size_t)e * 27 + 3 * j0 + 9 * j1;  // outputs a = a0 + 3 a1 + 9 a2
+    // outputs a = a0 + 3 a1 + 9 a2, (a1, a2) = (j0, j1), into the node slots
+    // (as the FP32 apply's)
+    const size_t NN = (size_t)D.N;
+    const int sl = 2 * (j0 == 0) + 4 * (j1 == 0);
     if (valid) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            D.q2Yh[o + a] = y[a].h;
-            D.q2Yl[o + a] = y[a].l;
+            const size_t o = (size_t)(sl + (a == 0)) * NN + n + a;
+            D.q2Yh[o] = y[a].h;
+            D.q2Yl[o] = y[a].l;
         }
     }
     if (FIRST) {
@@ -471,52 +480,12 @@ __global__ void __launch_bounds__(9 * kQ2PEl) k_q2_elem_ff(Dev* __restrict__ Dp)
         if (valid) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                D.q2Bh[o + a] = y[a].h;
-                D.q2Bl[o + a] = y[a].l;
+                const size_t o = (size_t)(sl + (a == 0)) * NN + n + a;
+                D.q2Bh[o] = y[a].h;
+                D.q2Bl[o] = y[a].l;
             }
         }
     }
-}
-
-// The elements of node index I along one direction (ne elements): the
-// element and the node's local index in it, 1 or 2 of them.
-__device__ __forceinline__ int q2_incident(int I, int ne, int (&el)[2], int (&loc)[2]) {
-    if (I & 1) {
-        el[0] = I >> 1;
-        loc[0] = 1;
-        return 1;
-    }
-    int c = 0;
-    const int k = I >> 1;
-    if (k >= 1) {
-        el[c] = k - 1;
-        loc[c++] = 2;
-    }
-    if (k < ne) {
-        el[c] = k;
-        loc[c++] = 0;
-    }
-    return c;
-}
-
-// Sum of the element outputs at node n, in a fixed order (direction 0
-// innermost).
-template <typename V, typename Load>
-__device__ __forceinline__ V q2_gather(const Dev& D, int n, Load load) {
-    const int I = n % D.NX, J = (n / D.NX) % D.NY, K = n / (D.NX * D.NY);
-    int ex[2], lx[2], ey[2], ly[2], ez[2], lz[2];
-    const int cx = q2_incident(I, D.enx, ex, lx);
-    const int cy = q2_incident(J, D.eny, ey, ly);
-    const int cz = q2_incident(K, D.enz, ez, lz);
-    V acc;
-    q2_zero(acc);
-    for (int c = 0; c < cz; ++c)
-        for (int b = 0; b < cy; ++b)
-            for (int a = 0; a < cx; ++a) {
-                const int e = ex[a] + D.enx * (ey[b] + D.eny * ez[c]);
-                q2_add(acc, load(e, lx[a] + 3 * ly[b] + 9 * lz[c]));
-            }
-    return acc;
 }
 
 // q = A p, the new direction p, and alpha = (r . z) / (p . q): the same
@@ -550,14 +519,15 @@ __global__ void __launch_bounds__(kNodeThreads) k_q2_gather_ff(Dev* __restrict__
     float vf[4] = {0.f, 0.f, 0.f, 0.f};
     const double none[1] = {0.0};
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < D.N; n += gridDim.x * blockDim.x) {
-        const FF y = q2_gather<FF>(D, n, [&](int e, int a) {
-            const size_t i = (size_t)e * 27 + a;
+        const size_t NN = (size_t)D.N;
+        const FF y = q2_gather_slots_v<FF>(D, n, [&](int s) {
+            const size_t i = (size_t)s * NN + n;
             return FF{D.q2Yh[i], D.q2Yl[i]};
         });
         FF b;
         if (FIRST) {
-            b = q2_gather<FF>(D, n, [&](int e, int a) {
-                const size_t i = (size_t)e * 27 + a;
+            b = q2_gather_slots_v<FF>(D, n, [&](int s) {
+                const size_t i = (size_t)s * NN + n;
                 return FF{D.q2Bh[i], D.q2Bl[i]};
             });
             D.b_hi[n] = b.h;

@@ -69,7 +69,7 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_model(name, N, n_elems, inner_iters=1.0, shell=False, q2=False):
+def kernel_model(name, N, n_elems, inner_iters=1.0, shell=False, q2=False, sweeps=1.0):
     """Bytes and flops per launch of each kernel of the refined slab step.
 
     Returns (algorithmic bytes, implementation bytes, flops).  Algorithmic
@@ -88,6 +88,12 @@ def kernel_model(name, N, n_elems, inner_iters=1.0, shell=False, q2=False):
         # u 4 + r 4 + w 4, per update r w u s p x D^-1 28 + 5 writes 20, with
         # one apply more than updates (single-reduction CG)
         "pcg32": ((60 + g) * N * it, N * (121 * (it + 1) + 48 * it), (600 * n_elems + 12 * N) * (it + 1)),
+        # the whole solve of a step in one persistent launch: per sweep the
+        # inner iterations (it here: per launch), u += delta and the residual
+        # (48 B/node; this layout 256 + 20)
+        "solve32": (((60 + g) * it + (48 + g) * sweeps) * N,
+                    N * (121 * (it + sweeps) + 48 * it + 276 * sweeps),
+                    (600 * n_elems + 12 * N) * (it + sweeps) + 27 * 12 * N * sweeps),
         # residual sweep: u 8 + b 8 + r 8 + fibres 24 = 48 B/node; this layout:
         # float-float couplings 216 + u 8 + b 8 + D^-1 4; A u 8 + r/z/d 12
         "resid": ((48 + g) * N, 256 * N, 27 * 12 * N),
@@ -147,6 +153,8 @@ KERNEL_SOURCES = {
     "rhs": ["paper_2308_01651_gb300/csrc/k_ff.cu", "paper_2308_01651_gb300/csrc/ep_tile.cuh",
             "paper_2308_01651_gb300/csrc/ep_ff.cuh", "paper_2308_01651_gb300/csrc/ep_dev.cuh",
             "paper_2308_01651_gb300/csrc/ep_refine.cuh"],
+    "solve32": ["paper_2308_01651_gb300/csrc/k_pcg.cu", "paper_2308_01651_gb300/csrc/ep_tile.cuh",
+                "paper_2308_01651_gb300/csrc/ep_ff.cuh", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
     "pcg32": ["paper_2308_01651_gb300/csrc/k_pcg.cu", "paper_2308_01651_gb300/csrc/ep_tile.cuh",
               "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
     "update32": ["paper_2308_01651_gb300/csrc/k_cg.cu", "paper_2308_01651_gb300/csrc/ep_dev.cuh"],
@@ -341,7 +349,7 @@ def run_ours(args):
                 # and the residual (element + gather)
                 launches += 3 + 3 * st["cg_iters"] + 3 * st["sweeps"]
             elif st["op32"] == ep.EP_OP_STENCIL:
-                launches += 2 + 2 * st["sweeps"]  # ionic, rhs; per sweep: pcg32 (with u += delta), resid
+                launches += 3  # ionic, rhs, the persistent solve (all sweeps)
             else:
                 launches += 2 + 2 * st["cg_iters"] + 2 * st["sweeps"]
         inst.sync()
@@ -378,7 +386,10 @@ def run_ours(args):
         tot_prof = sum(v[1] for v in prof.values())
         ipl = it_sum / max(sw_sum, 1)
         for name, (n_l, ms) in prof.items():
-            b, bi, f = kernel_model(name, N, n_elems, ipl, shell=shell, q2=q2)
+            if name == "solve32":  # per launch (one per step): the step's iterations and sweeps
+                b, bi, f = kernel_model(name, N, n_elems, it_sum / K, shell=shell, sweeps=sw_sum / K)
+            else:
+                b, bi, f = kernel_model(name, N, n_elems, ipl, shell=shell, q2=q2)
             avg_s = ms / 1e3 / n_l
             kernels[name] = {"launches": n_l, "avg_us": 1e6 * avg_s, "share": ms / tot_prof,
                              "gbs": (b / avg_s / 1e9) if b else None,

@@ -42,7 +42,6 @@ void launch_correct_ff_batch(const Batch& B, int grid, cudaStream_t s);
 void launch_resid_np(Dev* d, const Dev& h, int graph, int grid, cudaStream_t s);
 void launch_resid_np_batch(const Batch& B, int graph, int grid, cudaStream_t s);
 cudaError_t launch_pcg32_batch(const Batch& B, int grid, cudaStream_t s);
-void launch_batch_cond(Dev* const* devs, int n, const unsigned long long* h, cudaStream_t s);
 cudaError_t launch_prepace(int model, const uint8_t* cells, int ncell, double dt, long long m0, long long nsteps,
                            long long kp, long long kd, double amp, int bdf, double* st, cudaStream_t s);
 void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s);
@@ -105,7 +104,7 @@ struct ep_instance {
 
 static const char* kKernelNames[] = {"ionic", "rhs", "resid", "p64", "apply64", "update64",
                                      "apply32_mf", "apply32_stencil", "update32", "correct",
-                                     "finish", "realpha", "pcg32", "apply32_q2"};
+                                     "finish", "realpha", "solve32", "apply32_q2"};
 enum { K_IONIC, K_RHS, K_RESID, K_P64, K_APPLY64, K_UPDATE64, K_APPLY32MF, K_APPLY32ST, K_UPDATE32,
        K_CORRECT, K_FINISH, K_REALPHA, K_PCG32, K_APPLY32Q2, K_COUNT };
 
@@ -465,14 +464,10 @@ ep_status build_graph(ep_instance* I) {
             C.chk(cudaStreamEndCapture(s2, &body));
         }
     } else if (h.op32 == EP_OP_STENCIL) {
-        // refinement sweeps: [persistent inner PCG, u += delta, FP64 residual]
-        C.chk(add_while(s, &h_outer, &body));
-        if (C.err == cudaSuccess) {
-            C.chk(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-            C.chk(epk::launch_pcg32(I->d, h, I->grid_pcg, s2));  // ends with u += delta
-            epk::launch_resid_np(I->d, h, 1, I->grid_resid, s2);
-            C.chk(cudaStreamEndCapture(s2, &body));
-        }
+        // every refinement sweep [inner PCG, u += delta, float-float residual,
+        // decision] in one persistent launch (it returns at once when the
+        // first residual met the tolerance)
+        C.chk(epk::launch_pcg32(I->d, h, I->grid_pcg, s));
     } else {
         C.chk(add_while(s, &h_outer, &body));
         if (C.err == cudaSuccess) {
@@ -507,7 +502,7 @@ ep_status build_graph(ep_instance* I) {
     }
     I->graph = g;
     if ((h.prec == EP_PREC_FP64 && !h_loop) ||
-        (h.prec != EP_PREC_FP64 && (!h_outer || (h.op32 != EP_OP_STENCIL && !h_inner))))
+        (h.prec != EP_PREC_FP64 && h.op32 != EP_OP_STENCIL && (!h_outer || !h_inner)))
         return fail(EP_ECUDA, "a conditional handle of the step graph is zero");
     CUDA_TRY(cudaGraphInstantiate(&I->exec, g, 0));
     // the conditional handles live in the device descriptor
@@ -549,14 +544,15 @@ ep_status step_host(ep_instance* I) {
         }
     } else {
         CUDA_TRY(flag(&d->f_outer, &f));
+        if (h.op32 == EP_OP_STENCIL) {
+            // the whole solve in one persistent launch
+            cudaError_t pe = cudaSuccess;
+            timed(I, K_PCG32, [&] { pe = epk::launch_pcg32(d, h, I->grid_pcg, s); });
+            CUDA_TRY(pe);
+            f = 0;
+        }
         for (int sw = 0; f && sw <= h.max_sweeps; ++sw) {
             int fi = 1;
-            if (h.op32 == EP_OP_STENCIL) {
-                cudaError_t pe = cudaSuccess;
-                timed(I, K_PCG32, [&] { pe = epk::launch_pcg32(d, h, I->grid_pcg, s); });
-                CUDA_TRY(pe);
-                fi = 0;
-            }
             for (int it = 0; fi && it <= h.max_iter; ++it) {
                 if (h.q2)
                     timed(I, K_APPLY32Q2, [&] { epk::launch_q2_apply32(d, h, I->grid_nodes, s); });
@@ -568,9 +564,7 @@ ep_status step_host(ep_instance* I) {
                 CUDA_TRY(cudaGetLastError());
                 CUDA_TRY(flag(&d->f_inner, &fi));
             }
-            // the persistent solver applies its correction itself
-            if (h.op32 != EP_OP_STENCIL)
-                timed(I, K_CORRECT, [&] { epk::launch_correct_ff(d, h, I->grid_nodes, s); });
+            timed(I, K_CORRECT, [&] { epk::launch_correct_ff(d, h, I->grid_nodes, s); });
             timed(I, K_RESID, [&] {
                 if (h.q2) epk::launch_q2_resid(d, h, 0, 0, I->grid_nodes, s);
                 else epk::launch_resid_np(d, h, 0, I->grid_resid, s);
@@ -1200,7 +1194,7 @@ ep_status build_plan(BatchPlan* P) {
         s_grp[gi].push_back(s_grp[gi].back() + I->grid_ionic);
     }
     // one device buffer: pointer arrays first (8-byte aligned), then ints
-    size_t np = all.size() + 1;  // + the loop's handle
+    size_t np = all.size();
     size_t ni = s_tiles.size() + s_nodes.size() + s_pcg.size();
     for (int gi = 0; gi < 3; ++gi) {
         np += grp[gi].size();
@@ -1214,8 +1208,6 @@ ep_status build_plan(BatchPlan* P) {
         q += bytes;
         return at - hbuf.data();
     };
-    const unsigned long long hzero = 0ull;
-    const size_t o_h = put(&hzero, sizeof(hzero));
     const size_t o_all = put(all.data(), all.size() * sizeof(Dev*));
     size_t o_grp[3], o_sgrp[3];
     for (int gi = 0; gi < 3; ++gi) o_grp[gi] = put(grp[gi].data(), grp[gi].size() * sizeof(Dev*));
@@ -1231,43 +1223,30 @@ ep_status build_plan(BatchPlan* P) {
         return epk::Batch{nullptr, reinterpret_cast<Dev* const*>(d + od), reinterpret_cast<const int*>(d + os), cnt};
     };
     const epk::Batch Bt = mk(o_all, o_st, n, all[0]);
-    const epk::Batch Bn = mk(o_all, o_sn, n, all[0]);
     const epk::Batch Bp = mk(o_all, o_sp, n, all[0]);
-    Dev* const* dall = reinterpret_cast<Dev* const*>(d + o_all);
-    const unsigned long long* dh = reinterpret_cast<const unsigned long long*>(d + o_h);
 
     CUDA_TRY(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
     cudaStream_t s = P->stream, s2 = nullptr;
     CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
     Capture C{s};
-    cudaGraphConditionalHandle hc = 0;
     C.chk(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     for (int gi = 0; gi < 3; ++gi)
         if (!grp[gi].empty())
             epk::launch_ionic_batch(mk(o_grp[gi], o_sgrp[gi], (int)grp[gi].size(), grp[gi][0]),
                                     gi == 0 ? EP_MODEL_BO : EP_MODEL_TTP06, gi == 2, s_grp[gi].back(), s);
     epk::launch_rhs_ff_batch(Bt, 1, 0, s_tiles.back(), s);
-    epk::launch_batch_cond(dall, n, dh, s);
-    cudaGraph_t body = nullptr;
-    C.chk(add_while(s, &hc, &body));
-    if (C.err == cudaSuccess) {
-        C.chk(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        C.chk(epk::launch_pcg32_batch(Bp, s_pcg.back(), s2));  // ends with u += delta
-        epk::launch_resid_np_batch(Bn, 0, s_nodes.back(), s2);
-        epk::launch_batch_cond(dall, n, dh, s2);
-        C.chk(cudaStreamEndCapture(s2, &body));
-    }
+    // every instance's refinement sweeps in one persistent launch (the
+    // blocks of an instance that needs no sweep return at once)
+    C.chk(epk::launch_pcg32_batch(Bp, s_pcg.back(), s));
     cudaGraph_t g = nullptr;
     C.chk(cudaStreamEndCapture(s, &g));
     C.chk(cudaGetLastError());
     cudaStreamDestroy(s2);
-    if (C.err != cudaSuccess || !hc) {
+    if (C.err != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return fail(EP_ECUDA, std::string("building the batch graph: ") + cudaGetErrorString(C.err));
     }
     P->graph = g;
-    const unsigned long long hv = (unsigned long long)hc;
-    CUDA_TRY(cudaMemcpy(d + o_h, &hv, sizeof(hv), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaGraphInstantiate(&P->exec, g, 0));
     return EP_OK;
 }
@@ -1847,13 +1826,14 @@ ep_status ep_residual_norm_noalloc(const ep_instance* I, double* relres_out) {
     if (!I || !relres_out) return fail(EP_EINVAL, "NULL argument");
     if (I->h.prec != EP_PREC_FP32_REFINED)
         return fail(EP_EUNSUPPORTED, "the allocation-free residual serves FP32_REFINED instances");
-    if (I->h.q2) return fail(EP_EUNSUPPORTED, "the allocation-free residual serves structured-stencil instances");
-    if (I->grid_resid > epk::noalloc_max_blocks())
-        return fail(EP_EINVAL, "the residual of this instance needs " + std::to_string(I->grid_resid) +
+    if (I->h.q2 || I->h.op32 != EP_OP_STENCIL)
+        return fail(EP_EUNSUPPORTED, "the allocation-free residual serves instances with the stencil FP32 operator");
+    if (I->grid_pcg > epk::noalloc_max_blocks())
+        return fail(EP_EINVAL, "the residual of this instance needs " + std::to_string(I->grid_pcg) +
                                    " thread blocks; the allocation-free path holds partial sums for at most " +
                                    std::to_string(epk::noalloc_max_blocks()));
     double sums[2] = {0.0, 0.0};
-    CUDA_TRY(epk::residual_norm_noalloc(I->d, I->grid_resid, I->stream, sums));
+    CUDA_TRY(epk::residual_norm_noalloc(I->d, I->grid_pcg, I->stream, sums));
     *relres_out = sums[0] > 0.0 ? std::sqrt(sums[1] / sums[0]) : std::sqrt(sums[1]);
     return EP_OK;
 }

@@ -183,6 +183,42 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Block sums of NV float values (warp butterflies, then the warps' sums by
+// warp 0 in the same way), written as part[k * G + blk].  (Block-wide
+// __syncthreads inside.)
+template <int NV>
+__device__ __forceinline__ void publish(const float (&v)[NV], float* part, int G, int blk) {
+    __shared__ float sh[NV][kMaxBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const float s = warp_sum(v[k]);
+        if (lane == 0) sh[k][warp] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const float s = warp_sum(lane < nwarp ? sh[k][lane] : 0.f);
+            if (lane == 0) part[(size_t)k * G + blk] = s;
+        }
+    }
+}
+
+// Totals of G blocks' partials, formed by warp 0 in a fixed order
+// (lane-strided sums, then a butterfly), so every block that forms them holds
+// the same bits; the result is valid in warp 0 only.
+template <int NV>
+__device__ __forceinline__ void gather(const float* part, int G, float (&tot)[NV]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        float acc = 0.f;
+        for (int i = lane; i < G; i += 32) acc += __ldcg(&part[(size_t)k * G + i]);
+        tot[k] = warp_sum(acc);
+    }
+}
+
 // Shared-memory tree sum of sh[k][0..n) into sh[k][0] (n a power of two equal
 // to blockDim.x).  n - 1 additions per row: on GB300 the FP64 pipe is ~60x
 // slower than FP32, and a warp-shuffle tree would spend 5 x 32 additions per

@@ -119,21 +119,6 @@ __global__ void __launch_bounds__(kNodeThreads) k_finish_ff(Batch B) {
     }
 }
 
-// Loop condition of a batched refinement sweep: another sweep while any
-// instance's refinement goes on.
-// The handle is read from device memory: it is created after the kernels
-// upstream of the loop have been captured.
-__global__ void k_batch_cond(Dev* const* devs, int n, const unsigned long long* h) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    unsigned int any = 0;
-    for (int i = 0; i < n; ++i) any |= devs[i]->f_outer ? 1u : 0u;
-    cudaGraphSetConditional((cudaGraphConditionalHandle)*h, any);
-}
-
-void launch_batch_cond(Dev* const* devs, int n, const unsigned long long* h, cudaStream_t s) {
-    k_batch_cond<<<1, 32, 0, s>>>(devs, n, h);
-}
-
 void launch_update32(Dev* d, const Dev& h, int grid, int graph, cudaStream_t s) {
     k_update32<<<grid, kNodeThreads, 0, s>>>(d, graph);
 }

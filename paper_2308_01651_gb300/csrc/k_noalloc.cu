@@ -23,11 +23,12 @@
 // the counter before its kernel runs, and calls whose work overlaps on the
 // GPU (different streams, no ordering) race on the array.
 //
-// The kernel is a variant of the refined solver's residual kernel
-// (k_resid_np, float-float, node-parallel): same nodes per thread, same
-// per-thread and per-block summation order, so it reproduces the solver's
-// own residual norm; it writes nothing but the scratch array.  It serves
-// FP32_REFINED instances.
+// The kernel repeats the refined solver's residual (the one closing each
+// refinement sweep inside the persistent solve, float-float, node-parallel):
+// same grid, same nodes per thread, same per-thread, per-block and
+// across-block summation (float partials, summed in the same fixed order), so
+// it reproduces the solver's own residual norm; it writes nothing but the
+// scratch array.  It serves FP32_REFINED stencil instances.
 #include <mutex>
 #include <string>
 
@@ -37,42 +38,58 @@
 namespace epk {
 
 constexpr int kNoAllocMaxBlocks = 1024;
-// layout: double partial[2 * kNoAllocMaxBlocks]; double total[2]; unsigned counter
+// layout: float partial[2][kNoAllocMaxBlocks] (in the first half of the
+// area); double total[2]; unsigned counter
 constexpr size_t kNoAllocTotalOff = sizeof(double) * 2 * kNoAllocMaxBlocks;
 constexpr size_t kNoAllocCounterOff = kNoAllocTotalOff + 2 * sizeof(double);
 constexpr size_t kNoAllocScratchBytes = kNoAllocCounterOff + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-__global__ void __launch_bounds__(kResidThreads) k_residual_norm_noalloc(const Dev* __restrict__ Dp,
-                                                                         unsigned char* scratch) {
+__global__ void __launch_bounds__(kPcgThreads) k_residual_norm_noalloc(const Dev* __restrict__ Dp,
+                                                                       unsigned char* scratch) {
     const Dev& D = *Dp;
     const int N = D.N;
     const size_t NN = (size_t)N;
     const float ns = D.nscale;
     const int nx = D.NX, nxy = D.NX * D.NY, wrap = D.periodic ? D.NX * (D.NY - 1) : 0;
-    double* partial = reinterpret_cast<double*>(scratch);
+    float* part = reinterpret_cast<float*>(scratch);
     double* total = reinterpret_cast<double*>(scratch + kNoAllocTotalOff);
     unsigned int* counter = reinterpret_cast<unsigned int*>(scratch + kNoAllocCounterOff);
+    const int G = gridDim.x, T = G * blockDim.x;
     float vf[2] = {0.f, 0.f};
-    const double none[1] = {0.0};
     // the last solve's float-float iterate, now the potential level n (u_n is
     // its sum rounded to double)
     const float* __restrict__ uh = D.uh_n;
     const float* __restrict__ ul = D.ul_n;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += T) {
         const NbrOff o = nbr_offsets(nx, nxy, wrap, D.nflag[n]);
         float ah, al, rh, rl;
         row_ff_np(D.Ahi, D.Alo, NN, uh, ul, n, o, ah, al);
-        ff_sub(D.b_hi[n], D.b_lo[n], ah, al, rh, rl);
-        const float bs = ns * D.b_hi[n], rs = ns * rh;
+        const float bh = D.b_hi[n];
+        ff_sub(bh, D.b_lo[n], ah, al, rh, rl);
+        const float bs = ns * bh, rs = ns * rh;
         vf[0] = fmaf(bs, bs, vf[0]);
         vf[1] = fmaf(rs, rs, vf[1]);
     }
-    grid_reduce<2, 0>(vf, none, partial, counter, blockIdx.x, gridDim.x, [&](double* t) {
-        total[0] = t[0];
-        total[1] = t[1];
-    });
+    publish<2>(vf, part, G, blockIdx.x);
+    // the last block to arrive forms the totals
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(counter, 1u) == (unsigned int)(G - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < 32) {
+        float tt[2];
+        gather<2>(part, G, tt);
+        if (threadIdx.x == 0) {
+            total[0] = tt[0];
+            total[1] = tt[1];
+        }
+    }
 }
 
 namespace {
@@ -108,7 +125,7 @@ cudaError_t residual_norm_noalloc(Dev* d, int grid, cudaStream_t s, double sums[
     unsigned char* base = static_cast<unsigned char*>(scratch);
     e = cudaMemsetAsync(base + kNoAllocCounterOff, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    k_residual_norm_noalloc<<<grid, kResidThreads, 0, s>>>(d, base);
+    k_residual_norm_noalloc<<<grid, kPcgThreads, 0, s>>>(d, base);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(sums, base + kNoAllocTotalOff, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);

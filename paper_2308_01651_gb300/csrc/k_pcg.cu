@@ -1,5 +1,6 @@
-// k_pcg.cu -- the FP32 inner solve of a refinement sweep in one persistent,
-// cooperative launch (stencil operator).
+// k_pcg.cu -- the whole linear solve of a step, every refinement sweep, in
+// one persistent, cooperative launch (stencil operator): the FP32 inner solve,
+// the correction and the float-float residual with the refinement's decision.
 //
 // Jacobi-preconditioned CG (the paper solves Eq. (6) with CG, Sec. 2) on
 // A delta = r in float, A the hi parts of the node-major full couplings, in
@@ -25,7 +26,18 @@
 // release/acquire pair orders them for every thread of the block.  A barrier
 // that does not complete within ~1 s records EP_ETIMEOUT and the kernel
 // returns.
+//
+// After the inner solve: u += delta (float-float), a grid barrier, then the
+// residual of the sweep on the same node map -- y = A u with the float-float
+// couplings, r = b - y, the next inner solve's start (r, D^-1 r, delta = 0) --
+// and its sums (ns b)^2, (ns r)^2, r . D^-1 r, r . r, reduced like the CG's
+// (block partials, every block summing them in the same order), so every
+// block takes the same decision: the refinement has converged when
+// ||r|| <= tol ||b||, else another sweep follows (at most max_sweeps); block 0
+// records the step's figures and, at the end, rotates the time levels.  The
+// inner solve's couplings are then still in L2 for the residual's hi parts.
 #include "ep_dev.cuh"
+#include "ep_ff.cuh"
 #include "ep_tile.cuh"
 
 namespace epk {
@@ -69,8 +81,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned
     return ok != 0;
 }
 
-// Block sums of NV float values (warp butterflies, then the warps' sums by
-// warp 0 in the same way), written as part[k * G + blockIdx.x].
 // u += delta (float-float) on this thread's nodes; kept out of line so that
 // its registers do not add to the solver loop's
 __device__ __noinline__ void correct_ff_nodes(const Dev& D, int t0, int T) {
@@ -85,43 +95,45 @@ __device__ __noinline__ void correct_ff_nodes(const Dev& D, int t0, int T) {
     }
 }
 
-template <int NV>
-__device__ __forceinline__ void publish(const float (&v)[NV], float* part, int G, int blk) {
-    __shared__ float sh[NV][kMaxBlock / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const float s = warp_sum(v[k]);
-        if (lane == 0) sh[k][warp] = s;
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            const float s = warp_sum(lane < nwarp ? sh[k][lane] : 0.f);
-            if (lane == 0) part[(size_t)k * G + blk] = s;
-        }
+// The sweep's float-float residual on this thread's nodes: y = A u with
+// the hi and lo couplings (stored as the step's A u), r = b - y, the next
+// inner solve's start (r32 = r, z32 = D^-1 r32, delta = 0), and this
+// thread's sums (ns b)^2, (ns r)^2, r32 . z32, r32 . r32.  Out of line, as
+// correct_ff_nodes.
+__device__ __noinline__ void resid_ff_nodes(const Dev& D, int t0, int T, float (&vf)[4]) {
+    const int N = D.N;
+    const size_t NN = (size_t)N;
+    const int nx = D.NX, nxy = D.NX * D.NY, wrap = D.periodic ? D.NX * (D.NY - 1) : 0;
+    const float ns = D.nscale;
+    const float* __restrict__ uh = D.u_hi;
+    const float* __restrict__ ul = D.u_lo;
+    vf[0] = vf[1] = vf[2] = vf[3] = 0.f;
+    for (int n = t0; n < N; n += T) {
+        const NbrOff o = nbr_offsets(nx, nxy, wrap, D.nflag[n]);
+        float ah, al, rh, rl;
+        row_ff_np(D.Ahi, D.Alo, NN, uh, ul, n, o, ah, al);
+        D.yc_hi[n] = ah;
+        D.yc_lo[n] = al;
+        const float bh = D.b_hi[n];
+        ff_sub(bh, D.b_lo[n], ah, al, rh, rl);
+        const float r32 = rh;
+        const float z = D.dinv32[n] * r32;
+        D.r32[n] = r32;
+        D.z32[n] = z;
+        D.d32[n] = 0.0f;
+        const float bs = ns * bh, rs = ns * rh;
+        vf[0] = fmaf(bs, bs, vf[0]);
+        vf[1] = fmaf(rs, rs, vf[1]);
+        vf[2] = fmaf(r32, z, vf[2]);
+        vf[3] = fmaf(r32, r32, vf[3]);
     }
 }
 
-// Totals of all blocks' partials, formed by warp 0 of every block in the same
-// fixed order (lane-strided sums, then a butterfly), so every block holds the
-// same bits; the result is valid in warp 0 only.
-template <int NV>
-__device__ __forceinline__ void gather(const float* part, int G, float (&tot)[NV]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        float acc = 0.f;
-        for (int i = lane; i < G; i += 32) acc += __ldcg(&part[(size_t)k * G + i]);
-        tot[k] = warp_sum(acc);
-    }
-}
-
-__global__ void __launch_bounds__(kPcgThreads, 2) k_pcg32_stencil(Batch B) {
+__global__ void __launch_bounds__(kPcgThreads, 2) k_solve32_stencil(Batch B) {
     const Slot S = batch_slot(B);
     Dev& D = *S.D;
-    // a batched sweep also visits instances whose refinement has finished
+    // the step's first residual may already meet the tolerance; a batched
+    // launch also visits such instances
     if (!D.f_outer) return;
     const int N = D.N;
     const size_t NN = (size_t)N;
@@ -145,100 +157,154 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_pcg32_stencil(Batch B) {
     // CG scalars (float, like the solve): formed by thread 0 of every block
     // from the same totals, handed to the block through shared memory
     __shared__ float sc_alpha, sc_beta;
-    __shared__ int sc_done, sc_it, sc_nan;
+    __shared__ int sc_done, sc_it, sc_nan, sc_more, sc_sweeps, sc_itsum;
     __shared__ float sc_stop, sc_gam_old, sc_alpha_old, sc_rr, sc_gam;
     if (threadIdx.x == 0) {
         sc_it = 0;
         sc_nan = 0;
-        sc_stop = sc_gam_old = sc_alpha_old = sc_rr = sc_gam = 0.f;
+        sc_sweeps = 0;
+        sc_itsum = 0;
+        sc_stop = (float)D.inner_stop;  // the first sweep's, from the right-hand side
+        sc_gam_old = sc_alpha_old = sc_rr = sc_gam = 0.f;
     }
-    float alpha = 0.f, beta = 0.f;
-    bool first = true;
-    for (;;) {
-        if (!first) {
-            // ---- update, node by node
-            for (int n = t0; n < N; n += T) {
-                const float dv = dinv[n];
-                const float r0 = r[n], w0 = w[n], u0 = u[n];
-                const float s1 = beta == 0.f ? w0 : fmaf(beta, s[n], w0);
-                const float p1 = beta == 0.f ? u0 : fmaf(beta, p[n], u0);
-                const float r1 = fmaf(-alpha, s1, r0);
-                x[n] = fmaf(alpha, p1, x[n]);
-                s[n] = s1;
-                p[n] = p1;
-                r[n] = r1;
-                u[n] = dv * r1;
-            }
-            if (!grid_barrier(bcount, target, G, &D.status)) break;
-        }
-        // ---- apply w = A u and the block partials
-        float v[3] = {0.f, 0.f, 0.f};  // gamma, eta, rho
-        for (int n = t0; n < N; n += T) {
-            const NbrOff o = nbr_offsets(nx, nxy, wrap, flag[n]);
-            float acc = 0.f;
-#pragma unroll
-            for (int g = 0; g < kGroups; ++g) {
-                const float4 c = A[(size_t)g * NN + n];
-                const float cv[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int t = 4 * g + q;
-                    if (t < 27) acc = fmaf(cv[q], u[n + o.x[t % 3] + o.y[(t / 3) % 3] + o.z[t / 9]], acc);
+    __syncthreads();
+    bool aborted = false;
+    for (;;) {  // ---- refinement sweeps
+        float alpha = 0.f, beta = 0.f;
+        bool first = true;
+        if (threadIdx.x == 0) sc_it = 0;
+        for (;;) {  // ---- inner CG
+            if (!first) {
+                // ---- update, node by node
+                for (int n = t0; n < N; n += T) {
+                    const float dv = dinv[n];
+                    const float r0 = r[n], w0 = w[n], u0 = u[n];
+                    const float s1 = beta == 0.f ? w0 : fmaf(beta, s[n], w0);
+                    const float p1 = beta == 0.f ? u0 : fmaf(beta, p[n], u0);
+                    const float r1 = fmaf(-alpha, s1, r0);
+                    x[n] = fmaf(alpha, p1, x[n]);
+                    s[n] = s1;
+                    p[n] = p1;
+                    r[n] = r1;
+                    u[n] = dv * r1;
+                }
+                if (!grid_barrier(bcount, target, G, &D.status)) {
+                    aborted = true;
+                    break;
                 }
             }
-            w[n] = acc;
-            const float rn = r[n], un = u[n];
-            v[0] = fmaf(rn, un, v[0]);
-            v[1] = fmaf(un, acc, v[1]);
-            v[2] = fmaf(rn, rn, v[2]);
+            // ---- apply w = A u and the block partials
+            float v[3] = {0.f, 0.f, 0.f};  // gamma, eta, rho
+            for (int n = t0; n < N; n += T) {
+                const NbrOff o = nbr_offsets(nx, nxy, wrap, flag[n]);
+                float acc = 0.f;
+#pragma unroll
+                for (int g = 0; g < kGroups; ++g) {
+                    const float4 c = A[(size_t)g * NN + n];
+                    const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int t = 4 * g + q;
+                        if (t < 27) acc = fmaf(cv[q], u[n + o.x[t % 3] + o.y[(t / 3) % 3] + o.z[t / 9]], acc);
+                    }
+                }
+                w[n] = acc;
+                const float rn = r[n], un = u[n];
+                v[0] = fmaf(rn, un, v[0]);
+                v[1] = fmaf(un, acc, v[1]);
+                v[2] = fmaf(rn, rn, v[2]);
+            }
+            publish<3>(v, part, G, S.blk);
+            if (!grid_barrier(bcount, target, G, &D.status)) {
+                aborted = true;
+                break;
+            }
+            if (threadIdx.x < 32) {
+                float tt[3];
+                gather<3>(part, G, tt);
+                if (threadIdx.x == 0) {
+                    if (!first) ++sc_it;
+                    const float gam = tt[0], rr = tt[2];
+                    sc_gam = gam;
+                    sc_rr = rr;
+                    const bool nan = !(tt[0] == tt[0] && tt[1] == tt[1] && tt[2] == tt[2]);
+                    sc_nan = nan ? 1 : 0;
+                    const int done = (nan || rr <= sc_stop || sc_it >= D.max_iter) ? 1 : 0;
+                    if (!done) {
+                        const float b = first ? 0.f : gam / sc_gam_old;
+                        const float a = first ? gam / tt[1] : gam / (tt[1] - b * gam / sc_alpha_old);
+                        sc_beta = b;
+                        sc_alpha = a;
+                        sc_gam_old = gam;
+                        sc_alpha_old = a;
+                    }
+                    sc_done = done;
+                }
+            }
+            __syncthreads();
+            if (sc_done) break;
+            alpha = sc_alpha;
+            beta = sc_beta;
+            first = false;
         }
-        publish<3>(v, part, G, S.blk);
+        if (aborted) break;
+        // the sweep's correction u += delta (float-float), node by node
+        correct_ff_nodes(D, t0, T);
+        if (!grid_barrier(bcount, target, G, &D.status)) break;  // neighbours' u below
+        // ---- the sweep's residual and the next inner solve's start
+        {
+            float vf[4];
+            resid_ff_nodes(D, t0, T, vf);
+            publish<4>(vf, part, G, S.blk);
+        }
         if (!grid_barrier(bcount, target, G, &D.status)) break;
         if (threadIdx.x < 32) {
-            float tt[3];
-            gather<3>(part, G, tt);
+            float tt[4];
+            gather<4>(part, G, tt);
             if (threadIdx.x == 0) {
-                if (!first) ++sc_it;
-                const float gam = tt[0], rr = tt[2];
-                sc_gam = gam;
-                sc_rr = rr;
-                if (first) sc_stop = (float)D.inner_stop;
-                const bool nan = !(tt[0] == tt[0] && tt[1] == tt[1] && tt[2] == tt[2]);
-                sc_nan = nan ? 1 : 0;
-                const int done = (nan || rr <= sc_stop || sc_it >= D.max_iter) ? 1 : 0;
-                if (!done) {
-                    const float b = first ? 0.f : gam / sc_gam_old;
-                    const float a = first ? gam / tt[1] : gam / (tt[1] - b * gam / sc_alpha_old);
-                    sc_beta = b;
-                    sc_alpha = a;
-                    sc_gam_old = gam;
-                    sc_alpha_old = a;
+                sc_itsum += sc_it;
+                sc_sweeps += 1;
+                const double bb = tt[0], rr = tt[1];
+                const bool nan = !(rr == rr);
+                const bool conv = !nan && rr <= D.tol * D.tol * bb;
+                const bool more = !conv && !nan && sc_sweeps < D.max_sweeps;
+                // the next inner solve's stop: (0.9 tol ||b||)^2 in float
+                // units, or the float floor inner_tol^2 x its first r . r
+                const double ns2 = (double)D.nscale * (double)D.nscale;
+                const double target2 = 0.81 * D.tol * D.tol * (bb / ns2);
+                const double floor2 = D.inner_tol * D.inner_tol * (double)tt[3];
+                sc_stop = (float)(target2 > floor2 ? target2 : floor2);
+                sc_more = more ? 1 : 0;
+                if (S.blk == 0) {
+                    // the step's figures (block 0 only; the other blocks
+                    // read none of these fields)
+                    D.bb = bb;
+                    D.relres = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+                    D.rr0 = tt[3];
+                    D.rr = tt[3];
+                    D.rz = tt[2];
+                    D.sweeps = sc_sweeps;
+                    D.it = sc_it;
+                    D.it_total += sc_it;
+                    if (nan && D.status == EP_OK) D.status = EP_ENAN;
+                    if (sc_nan && D.status == EP_OK) D.status = EP_ENAN;
+                    if (!conv && !more && !nan && D.status == EP_OK) D.status = EP_ENOCONV;
+                    if (!more) {
+                        D.f_outer = 0;
+                        end_of_step(D);
+                    }
                 }
-                sc_done = done;
             }
         }
         __syncthreads();
-        if (sc_done) break;
-        alpha = sc_alpha;
-        beta = sc_beta;
-        first = false;
-    }
-    // the sweep's correction u += delta (float-float), node by node: no
-    // neighbour is involved, so it needs no barrier and no launch of its own
-    correct_ff_nodes(D, t0, T);
-    if (S.blk == 0 && threadIdx.x == 0) {
-        D.rz = sc_gam;
-        D.rr = sc_rr;
-        D.it = sc_it;
-        D.it_total += sc_it;
-        if (sc_nan && D.status == EP_OK) D.status = EP_ENAN;
+        if (!sc_more) break;
     }
 }
 
-// blocks of k_pcg32_stencil that fit on one SM at once
+// blocks of k_solve32_stencil that fit on one SM at once
 int pcg_blocks_per_sm() {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg32_stencil, kPcgThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil, kPcgThreads, 0) != cudaSuccess)
         return 0;
     return occ;
 }
@@ -254,7 +320,7 @@ cudaError_t launch_pcg32_batch(const Batch& B, int grid, cudaStream_t s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_pcg32_stencil, B);
+    return cudaLaunchKernelEx(&cfg, k_solve32_stencil, B);
 }
 
 cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, cudaStream_t s) {

@@ -232,9 +232,9 @@ def test_graph_and_host_driven_stepping_agree():
     assert np.array_equal(a.save(), b.save())
     # the refined step's per-node end runs inside the next ionic kernel
     assert prof["ionic"][0] == 10 and "finish" not in prof
-    if "pcg32" in prof:  # persistent inner solver: one launch per refinement sweep,
-        # which applies its own correction; a residual after each
-        assert prof["pcg32"][0] == prof["resid"][0] > 0 and "correct" not in prof
+    if "solve32" in prof:  # the whole solve (sweeps, corrections, residuals)
+        # in one persistent launch per step
+        assert prof["solve32"][0] == 10 and "resid" not in prof and "correct" not in prof
     else:
         apply = prof.get("apply32_mf", prof.get("apply32_stencil"))
         assert apply[0] == prof["update32"][0] > 0

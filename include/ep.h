@@ -307,8 +307,9 @@ ep_status ep_profile_read(ep_instance* inst, ep_kernel_time* out, int32_t cap,
  * ||b - A u||_2 / ||b||_2 of an FP32_REFINED instance's last linear solve
  * (the value ep_get_stats reports as relres), recomputed from the instance's
  * operator, right-hand side and the solver's float-float iterate u (whose sum
- * rounded to double is the potential u_n) in the same arithmetic as the
- * solver's residual; other instances get EP_EUNSUPPORTED.  After ep_state_load
+ * rounded to double is the potential u_n) in the same arithmetic and
+ * summation order as the solver's residual; instances other than refined
+ * ones with the stencil FP32 operator get EP_EUNSUPPORTED.  After ep_state_load
  * it still describes the last solve run, not the loaded state.  It calls no
  * cudaMalloc, cudaFree
  * or other allocating routine, for callers that must not allocate device

@@ -324,6 +324,14 @@ ep_status ep_profile_read(ep_instance* inst, ep_kernel_time* out, int32_t cap,
  * on one stream do not.  Runs on the instance's stream and waits for it. */
 ep_status ep_residual_norm_noalloc(const ep_instance* inst, double* relres_out);
 
+/* Self-test of the persistent solver's bounded waits (no instance needed):
+ * one thread block waits at the solver's grid barrier for a second block
+ * that never comes; the wait gives up after a bounded number of naps (a few
+ * milliseconds here, about a second in the solver) and records the status
+ * the solver would record, written to *status_out (EP_ETIMEOUT).  Nothing
+ * faults and the CUDA context stays usable.  Synchronises the device. */
+ep_status ep_selftest_barrier_timeout(int32_t* status_out);
+
 /* Frees every resource of the instance (NULL is accepted). */
 ep_status ep_destroy(ep_instance* inst);
 

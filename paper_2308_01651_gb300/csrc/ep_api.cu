@@ -49,6 +49,7 @@ int mf_tiles(const Dev& h);
 cudaError_t mf_prepare();
 int pcg_blocks_per_sm();
 cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, cudaStream_t s);
+cudaError_t barrier_timeout_probe(int* status_out);
 cudaError_t residual_norm_noalloc(Dev* d, int grid, cudaStream_t s, double sums[2]);
 int noalloc_max_blocks();
 }  // namespace epk
@@ -1819,6 +1820,14 @@ ep_status ep_profile_read(ep_instance* I, ep_kernel_time* out, int32_t cap, int3
             I->prof_ms[id] = 0.0;
             I->prof_n[id] = 0;
         }
+    return EP_OK;
+}
+
+ep_status ep_selftest_barrier_timeout(int32_t* status_out) {
+    if (!status_out) return fail(EP_EINVAL, "NULL argument");
+    int st = 0;
+    CUDA_TRY(epk::barrier_timeout_probe(&st));
+    *status_out = st;
     return EP_OK;
 }
 

@@ -54,7 +54,7 @@ constexpr long long kBarrierSpinLimit = 1ll << 24;  // x >= 64 ns naps: about a 
 // barrier of the launch).  Returns false after recording EP_ETIMEOUT when the
 // other blocks did not all arrive in time.
 __device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned long long& target, int G,
-                                             int* status) {
+                                             int* status, long long spin_limit = kBarrierSpinLimit) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -68,7 +68,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned
             unsigned long long cur;
             asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(cur) : "l"(count) : "memory");
             if (cur >= target) break;
-            if (++spins > kBarrierSpinLimit) {
+            if (++spins > spin_limit) {
                 good = 0;
                 atomicCAS(status, (int)EP_OK, (int)EP_ETIMEOUT);
                 break;
@@ -299,6 +299,32 @@ __global__ void __launch_bounds__(kPcgThreads, 2) k_solve32_stencil(Batch B) {
         __syncthreads();
         if (!sc_more) break;
     }
+}
+
+// Self-test of the bounded wait: one block enters a barrier of a grid of
+// two, whose other block never comes (a flag that nothing sets).  The spin
+// gives up after spin_limit naps, records EP_ETIMEOUT in *status and the
+// kernel returns; nothing faults and the context stays usable.
+__global__ void k_barrier_probe(unsigned long long* count, int* status, long long spin_limit) {
+    unsigned long long target = 0ull;
+    (void)grid_barrier(count, target, 2, status, spin_limit);
+}
+
+cudaError_t barrier_timeout_probe(int* status_out) {
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, 64);
+    if (e != cudaSuccess) return e;
+    unsigned long long* count = static_cast<unsigned long long*>(mem);
+    int* status = reinterpret_cast<int*>(static_cast<char*>(mem) + 32);
+    e = cudaMemset(mem, 0, 64);
+    if (e == cudaSuccess) {
+        k_barrier_probe<<<1, 32>>>(count, status, 1ll << 16);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(status_out, status, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(mem);
+    return e;
 }
 
 // blocks of k_solve32_stencil that fit on one SM at once

@@ -29,7 +29,8 @@ EP_MAX_PULSES = 4
 EXPORTS = ["ep_create", "ep_step", "ep_step_async", "ep_sync", "ep_step_batch", "ep_read_potential",
            "ep_activation_times", "ep_state_bytes", "ep_save_state", "ep_load_state",
            "ep_footprint_bytes", "ep_get_stats", "ep_potential_device", "ep_destroy", "ep_last_error",
-           "ep_profile_enable", "ep_profile_read", "ep_residual_norm_noalloc", "ep_prepace"]
+           "ep_profile_enable", "ep_profile_read", "ep_residual_norm_noalloc", "ep_prepace",
+           "ep_selftest_barrier_timeout"]
 
 
 class EpError(RuntimeError):
@@ -130,6 +131,8 @@ def lib():
         L.ep_profile_read.restype = st
         L.ep_residual_norm_noalloc.argtypes = [vp, P(C.c_double)]
         L.ep_residual_norm_noalloc.restype = st
+        L.ep_selftest_barrier_timeout.argtypes = [P(i32)]
+        L.ep_selftest_barrier_timeout.restype = st
         d = C.c_double
         L.ep_prepace.argtypes = [i32, vp, i32, d, i32, d, d, d, i32, vp, vp]
         L.ep_prepace.restype = st
@@ -339,6 +342,13 @@ def ep_residual_norm_noalloc(h):
     (see ep.h)."""
     out = C.c_double()
     _check(lib().ep_residual_norm_noalloc(h, C.byref(out)))
+    return out.value
+
+
+def ep_selftest_barrier_timeout():
+    """The status a timed-out grid barrier records (EP_ETIMEOUT)."""
+    out = C.c_int32()
+    _check(lib().ep_selftest_barrier_timeout(C.byref(out)))
     return out.value
 
 

@@ -38,9 +38,7 @@ void launch_q2_apply32(Dev* d, const Dev& h, int grid_nodes, cudaStream_t s);
 void launch_q2_resid(Dev* d, const Dev& h, int first, int graph, int grid_nodes, cudaStream_t s);
 void launch_realpha_q2(Dev* d, const Dev& h, double alpha_dt, cudaStream_t s);
 void launch_rhs_ff_batch(const Batch& B, int first, int graph, int grid, cudaStream_t s);
-void launch_correct_ff_batch(const Batch& B, int grid, cudaStream_t s);
 void launch_resid_np(Dev* d, const Dev& h, int graph, int grid, cudaStream_t s);
-void launch_resid_np_batch(const Batch& B, int graph, int grid, cudaStream_t s);
 cudaError_t launch_pcg32_batch(const Batch& B, int grid, cudaStream_t s);
 cudaError_t launch_prepace(int model, const uint8_t* cells, int ncell, double dt, long long m0, long long nsteps,
                            long long kp, long long kd, double amp, int bdf, double* st, cudaStream_t s);
@@ -1102,14 +1100,15 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
 
 // ---- batched stepping --------------------------------------------------------
 // ep_step_batch runs refined stencil-operator instances together: one launch
-// per phase over all instances (two for the ionic step when both models are
-// present), the refinement sweeps as one conditional loop that runs while any
-// instance still refines, all captured in one CUDA graph per batch.  Every
-// instance keeps the block counts of its own single-instance launches in the
-// non-persistent kernels, so their reductions sum in the same order as when
-// it runs alone; the persistent inner solver's blocks are shared out in
-// proportion to the instances' sizes (one cooperative grid must fit on the
-// GPU), which changes only the rounding of the inner iterations.
+// per phase over all instances (one ionic launch per model and level count),
+// every instance's refinement sweeps inside one persistent solve launch (each
+// instance's blocks loop over its own sweeps and leave when it has
+// converged), all captured in one CUDA graph per batch.  Every instance keeps
+// the block counts of its own single-instance launches in the non-persistent
+// kernels, so their reductions sum in the same order as when it runs alone;
+// the persistent solver's blocks are shared out in proportion to the
+// instances' sizes (one cooperative grid must fit on the GPU), which changes
+// only the rounding of the inner iterations and residual sums.
 
 struct BatchPlan {
     std::vector<ep_instance*> key;
@@ -1164,7 +1163,7 @@ ep_status build_plan(BatchPlan* P) {
     // host tables: all instances, then the ionic kernel's groups: BO, TTP06
     // with two levels, TTP06 with three (BDF3)
     std::vector<Dev*> all, grp[3];
-    std::vector<int> s_tiles{0}, s_nodes{0}, s_pcg{0}, s_grp[3] = {{0}, {0}, {0}};
+    std::vector<int> s_tiles{0}, s_pcg{0}, s_grp[3] = {{0}, {0}, {0}};
     double total = 0.0;
     for (ep_instance* I : P->key) total += (double)I->h.N;
     // persistent solver: blocks in proportion to size, at least one each,
@@ -1188,7 +1187,6 @@ ep_status build_plan(BatchPlan* P) {
         ep_instance* I = P->key[i];
         all.push_back(I->d);
         s_tiles.push_back(s_tiles.back() + I->grid_tiles);
-        s_nodes.push_back(s_nodes.back() + I->grid_resid);
         s_pcg.push_back(s_pcg.back() + gp[i]);
         const int gi = I->h.model == EP_MODEL_BO ? 0 : (I->h.u_nm2 ? 2 : 1);
         grp[gi].push_back(I->d);
@@ -1196,7 +1194,7 @@ ep_status build_plan(BatchPlan* P) {
     }
     // one device buffer: pointer arrays first (8-byte aligned), then ints
     size_t np = all.size();
-    size_t ni = s_tiles.size() + s_nodes.size() + s_pcg.size();
+    size_t ni = s_tiles.size() + s_pcg.size();
     for (int gi = 0; gi < 3; ++gi) {
         np += grp[gi].size();
         ni += s_grp[gi].size();
@@ -1213,7 +1211,6 @@ ep_status build_plan(BatchPlan* P) {
     size_t o_grp[3], o_sgrp[3];
     for (int gi = 0; gi < 3; ++gi) o_grp[gi] = put(grp[gi].data(), grp[gi].size() * sizeof(Dev*));
     const size_t o_st = put(s_tiles.data(), s_tiles.size() * sizeof(int));
-    const size_t o_sn = put(s_nodes.data(), s_nodes.size() * sizeof(int));
     const size_t o_sp = put(s_pcg.data(), s_pcg.size() * sizeof(int));
     for (int gi = 0; gi < 3; ++gi) o_sgrp[gi] = put(s_grp[gi].data(), s_grp[gi].size() * sizeof(int));
     CUDA_TRY(cudaMalloc(&P->dmem, hbuf.size()));

@@ -182,11 +182,11 @@ def test_bdf3_history_extrapolation_exact():
     thread and block in float, totals in double), in different orders, which
     adds up to ~1e-6 of the norm itself: |reported - recomputed| <= 1e-6
     relres + 5e-12."""
-    prob = ttp06(nx=30, ny=8, nz=6, T=10.0)
+    prob = ttp06(nx=30, ny=8, nz=6, T=30.0)
     inst = ep.Instance(prob, precision=REF, tol=1e-4)
     zero = 0
     try:
-        for _ in range(120):
+        for _ in range(prob["nsteps"]):
             inst.step(1)
             st = inst.stats()
             if st["sweeps"] == 0:

@@ -258,11 +258,11 @@ def test_steps_converging_at_first_residual_keep_history_exact():
     every such step the relative residual the solver reports (from the
     history) must equal the one recomputed from scratch (b - A u_n with the
     operator, ep_residual_norm_noalloc) to the float-float accuracy."""
-    prob = small_ttp06(nx=30, ny=8, nz=6, T=10.0)
+    prob = small_ttp06(nx=30, ny=8, nz=6, T=30.0)
     inst = ep.Instance(prob, precision=REF, tol=1e-5)
     zero_sweeps = 0
     try:
-        for _ in range(80):
+        for _ in range(prob["nsteps"]):
             inst.step(1)
             st = inst.stats()
             if st["sweeps"] == 0:

@@ -164,9 +164,12 @@ KERNEL_SOURCES = {
 }
 
 
-def committed_traffic(name):
+def committed_traffic(name, N=None, n_elems=None, alg_bytes=None, shell=False):
     """DRAM bytes per launch of a kernel from the committed ncu summary, if the
-    kernel's sources are unchanged since the capture."""
+    kernel's sources are unchanged since the capture.  A launch whose work
+    depends on the iterations it runs (the persistent solve) is scaled from
+    the captured launch to this run's average launch by the algorithmic
+    bytes of the two (the capture records its iterations and sweeps)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p) or name not in KERNEL_SOURCES:
         return None
@@ -174,7 +177,12 @@ def committed_traffic(name):
         d = json.load(f).get(name)
     if not d or d.get("source_hash") != source_hash(KERNEL_SOURCES[name]):
         return None
-    return d.get("dram_bytes_per_launch")
+    t = d.get("dram_bytes_per_launch")
+    if t is not None and "inner_iters" in d and alg_bytes and N:
+        cap = kernel_model(name, N, n_elems, d["inner_iters"], shell=shell, sweeps=d.get("sweeps", 1.0))[0]
+        if cap:
+            t = t * alg_bytes / cap
+    return t
 
 
 class ClockSampler:
@@ -426,7 +434,10 @@ def run_ours(args):
         else:
             roof = {"bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak, "unit": "GB/s",
                     "frac": hbm_frac, "peak_source": f"{peak_kind} HBM copy bandwidth"}
-        roof.update(kernel=dom, hbm_frac=hbm_frac, alu_frac=alu_frac, traffic=committed_traffic(dom),
+        dom_alg = kernel_model(dom, N, n_elems, it_p / P, shell=shell, sweeps=sw_p / P)[0] \
+            if dom == "solve32" else None
+        roof.update(kernel=dom, hbm_frac=hbm_frac, alu_frac=alu_frac,
+                    traffic=committed_traffic(dom, N, n_elems, dom_alg, shell),
                     impl_frac=(d["impl_gbs"] / hbm_peak) if d["impl_gbs"] else None,
                     bytes_model="per-node figures of the hot-path measurement table x nodes x "
                                 "inner iterations per launch; impl_frac: this layout's bytes")

@@ -138,6 +138,34 @@ def kernel_model(name, N, n_elems, inner_iters=1.0, shell=False, q2=False, sweep
     return v
 
 
+def conduction_velocity(mesh, at, frac=(0.25, 0.75)):
+    """Conduction velocity (cm/ms) along x of a slab's activation map `at`
+    (ms per node, NaN where never activated), for a wave started at the
+    x = 0 face.  Mean velocity: the distance between the node planes nearest
+    x = frac[0] Lx and frac[1] Lx over the difference of their mean
+    activation times.  Per column (each line of nodes along x): the
+    reciprocal of the least-squares slope of activation time against x over
+    the nodes between those planes.  Returns (mean, per-column array) or
+    None where the mesh is not a slab or a plane has a node that never
+    activated."""
+    if mesh["kind"] not in (0, 2):  # slab (Q1) or slab (Q2); not the shell
+        return None
+    import numpy as np
+    q2 = mesh["kind"] == 2
+    NX = 2 * mesh["nx"] + 1 if q2 else mesh["nx"] + 1
+    x = mesh["xyz"][:, 0]
+    cols = at.reshape(-1, NX)           # one row per (j, k) line of nodes along x
+    xs = x[:NX]
+    i0, i1 = (int(np.argmin(np.abs(xs - f * mesh["L"][0]))) for f in frac)
+    seg = cols[:, i0:i1 + 1]
+    if i1 <= i0 or np.isnan(seg).any():
+        return None
+    mean_v = (xs[i1] - xs[i0]) / (seg[:, -1].mean() - seg[:, 0].mean())
+    xc = xs[i0:i1 + 1] - xs[i0:i1 + 1].mean()
+    slope = (seg - seg.mean(axis=1, keepdims=True)) @ xc / (xc @ xc)
+    return float(mean_v), 1.0 / slope
+
+
 def source_hash(files):
     h = hashlib.sha256()
     for f in files:
@@ -471,6 +499,14 @@ def run_ours(args):
                    np.array_equal(np.isnan(at64), np.isnan(at_ref32))),
                "u_linf_mV_at_end": float(np.abs(u64 - u32).max()), "t_end_ms": steps_done * prob["dt"],
                "vs": "plain FP64 GPU path, same workload and steps"}
+        cv64 = conduction_velocity(prob["mesh"], at64)
+        cv32 = conduction_velocity(prob["mesh"], at_ref32)
+        if cv64 and cv32:
+            acc.update(cv_cm_per_ms={"fp64": cv64[0], "refined": cv32[0]},
+                       cv_rel_err=abs(cv32[0] - cv64[0]) / cv64[0],
+                       cv_rel_err_max_column=float(np.max(np.abs(cv32[1] - cv64[1]) / np.abs(cv64[1]))),
+                       cv_what="along x between the node planes at 0.25 and 0.75 Lx: plane means and "
+                               "per-column least-squares slopes")
         fp64 = {"value": N * len(e64) / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / len(e64),
                 "steps": len(e64)}
 

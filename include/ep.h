@@ -236,7 +236,10 @@ ep_status ep_step_async(ep_instance* inst, int64_t n_steps);
 ep_status ep_sync(ep_instance* inst);
 
 /* Advances several instances by n_steps each, all enqueued before any wait;
- * returns the first failing status (inst[k] order). */
+ * returns the first failing status (inst[k] order).  FP32_REFINED stencil
+ * instances share one persistent solve launch, one or more resident thread
+ * blocks each: at most two such instances per SM (304 on GB300), EP_EINVAL
+ * beyond. */
 ep_status ep_step_batch(ep_instance* const* insts, int32_t n, int64_t n_steps);
 
 /* Copies u_n (mV) into out[0..n), n == n_nodes. */

@@ -45,7 +45,7 @@ cudaError_t launch_prepace(int model, const uint8_t* cells, int ncell, double dt
 void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s);
 int mf_tiles(const Dev& h);
 cudaError_t mf_prepare();
-int pcg_blocks_per_sm();
+int pcg_blocks_per_sm(int batched);
 cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, cudaStream_t s);
 cudaError_t barrier_timeout_probe(int* status_out);
 cudaError_t residual_norm_noalloc(Dev* d, int grid, cudaStream_t s, double sums[2]);
@@ -173,6 +173,23 @@ ep_status dalloc(ep_instance* I, T** p, size_t count) {
     return EP_OK;
 }
 
+// A float vector of N nodes with `pad` zero floats before and after it
+// (*p points at node 0): node-parallel kernels may then read the neighbours
+// of every node of a Q1 slab at fixed offsets, without boundary flags: a
+// read past the slab's edge lands in the zero padding (never written) or on
+// another node, and meets a zero coupling either way.
+ep_status dalloc_padded(ep_instance* I, float** p, size_t N, int64_t pad) {
+    float* raw = nullptr;
+    const ep_status st = dalloc(I, &raw, N + 2 * (size_t)pad);
+    if (st != EP_OK) return st;
+    if (cudaMemsetAsync(raw, 0, (N + 2 * (size_t)pad) * sizeof(float), I->stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(EP_ECUDA, "cudaMemsetAsync of a padded vector failed");
+    }
+    *p = raw + pad;
+    return EP_OK;
+}
+
 // Frees one allocation of dalloc before ep_destroy.
 template <typename T>
 void dfree(ep_instance* I, T*& p, size_t count) {
@@ -195,6 +212,7 @@ struct Sizes {
     int levels;       // time levels kept: 3 for BDF3, else 2
     bool q2;          // triquadratic slab
     int64_t ne;       // elements (Q2)
+    int64_t npad;     // zero nodes before and after the solver's neighbour-read vectors (Q1 slab)
 };
 
 // float-float pair (nearest float, then the nearest float of the rest)
@@ -254,7 +272,9 @@ size_t footprint(const Sizes& z) {
         b += (2 + 2 * L) * al(N * 4);                                    // A u history (hi, lo)
         b += (1 + 2 * L) * al(N * 4);                                    // u levels (hi, lo), best slope
         if (z.op32 != EP_OP_STENCIL && !z.q2) b += al(6 * N * 4);       // fibres
-        b += 6 * al(N * 4);               // r32 z32 q32 d32 pa32 pb32
+        const size_t Np = N + 2 * (size_t)z.npad;
+        b += 5 * al(N * 4) + al(Np * 4);  // r32 q32 d32 pa32 pb32, z32 (padded)
+        if (!z.q2) b += al(N * 4) + 2 * al(Np * 4);  // zz32, ma32 mb32 (padded)
         if (!z.q2) b += al(N);            // boundary flags
     } else {
         b += 4 * al(N * 8);               // z64 q64 pa64 pb64
@@ -351,6 +371,10 @@ Sizes sizes_of(const ep_mesh* mesh, const ep_ionic_model* ionic, const ep_option
     z.q2 = mesh->kind == EP_MESH_SLAB_Q2;
     z.ne = (int64_t)mesh->nx * mesh->ny * mesh->nz;
     z.slab = mesh->kind == EP_MESH_SLAB;
+    // a Q1 slab's neighbour offsets reach 1 + (nx+1) + (nx+1)(ny+1) nodes
+    // either way; rounded up to 64 floats, so that the vectors keep the
+    // 256-byte alignment of every allocation (16-byte vector accesses)
+    z.npad = z.slab ? ((int64_t)(mesh->nx + 1) * (mesh->ny + 1) + (mesh->nx + 1) + 1 + 63) / 64 * 64 : 0;
     z.regions = mesh->region != nullptr;
     // an excluded region changes M; the footprint assumes it may
     z.slab_mass = z.slab && !z.regions;
@@ -860,11 +884,17 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         ALLOC(h.b_lo, N);
         if (z.op32 != EP_OP_STENCIL && !z.q2) ALLOC(h.fib, 6 * N);
         ALLOC(h.r32, N);
-        ALLOC(h.z32, N);
+        if ((st = dalloc_padded(I, &h.z32, N, z.npad)) != EP_OK) return st;
         ALLOC(h.q32, N);
         ALLOC(h.d32, N);
         ALLOC(h.pa32, N);
         ALLOC(h.pb32, N);
+        if (!z.q2) {
+            ALLOC(h.zz32, N);
+            if ((st = dalloc_padded(I, &h.ma32, N, z.npad)) != EP_OK) return st;
+            if ((st = dalloc_padded(I, &h.mb32, N, z.npad)) != EP_OK) return st;
+            h.npad = (int)z.npad;
+        }
         if (!z.q2) ALLOC(h.nflag, N);
     } else {
         ALLOC(h.z64, N);
@@ -1082,7 +1112,7 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     I->grid_tiles = std::max(1, std::min(epk::st_tiles(h), 2 * sms));
     if (ref) {
         // the persistent solver's blocks must all be resident at once
-        const int occ = epk::pcg_blocks_per_sm();
+        const int occ = epk::pcg_blocks_per_sm(0);
         if (occ <= 0) return fail(EP_ECUDA, "occupancy query of the persistent solver failed");
         const int want = (int)((N + epk::kPcgThreads - 1) / epk::kPcgThreads);
         I->grid_pcg = std::max(1, std::min(std::min(want, sms * occ), epk::kMaxPersistentBlocks));
@@ -1156,7 +1186,7 @@ ep_status build_plan(BatchPlan* P) {
     int dev = 0, sms = 152;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int occ = epk::pcg_blocks_per_sm();
+    const int occ = epk::pcg_blocks_per_sm(1);
     if (occ <= 0) return fail(EP_ECUDA, "occupancy query of the persistent solver failed");
     const int cap = sms * occ;
     if (n > cap) return fail(EP_EINVAL, "batch larger than the persistent solver's resident blocks");

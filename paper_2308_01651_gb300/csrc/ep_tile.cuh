@@ -159,6 +159,24 @@ __device__ __forceinline__ void row_ff(const float4* __restrict__ chi, const flo
     ff_normalize(sh, sl);
 }
 
+// FP32 row of node n with neighbour values read from global memory
+// (node-parallel kernels): sum_t c(t) x(n + off(t)), t = 0..26 in order
+__device__ __forceinline__ float row32_np(const float4* __restrict__ c, size_t N, const float* __restrict__ x,
+                                          int n, const NbrOff& o) {
+    float acc = 0.f;
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+        const float4 cg = c[(size_t)g * N + n];
+        const float cv[4] = {cg.x, cg.y, cg.z, cg.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int t = 4 * g + q;
+            if (t < 27) acc = fmaf(cv[q], x[n + o.x[t % 3] + o.y[(t / 3) % 3] + o.z[t / 9]], acc);
+        }
+    }
+    return acc;
+}
+
 // float-float row of node n with neighbour values read from global memory
 // (node-parallel kernels): (sh + sl) = sum_t (chi + clo)(t) (xh + xl)(n +
 // off(t)), t = 0..26 in order -- the same terms in the same order as row_ff

@@ -1,0 +1,74 @@
+"""Host-side measurement helpers of bench.py (no GPU): the conduction
+velocity read from an activation map, and the per-kernel byte models."""
+import numpy as np
+
+import bench
+from paper_2308_01651_gb300 import inputs as I
+
+
+def test_cv_planar_wave_exact():
+    """A planar front t = x / v + t0 gives v back, in the mean and in every
+    column (Q1 and Q2 slabs)."""
+    for mesh in (I.slab_mesh(20, 5, 4, (1.0, 0.25, 0.2)), I.slab_mesh_q2(10, 3, 2, (1.0, 0.3, 0.2))):
+        x = mesh["xyz"][:, 0]
+        at = x / 0.061 + 2.5
+        mean, col = bench.conduction_velocity(mesh, at)
+        assert abs(mean - 0.061) <= 1e-12
+        assert np.abs(col - 0.061).max() <= 1e-12
+
+
+def test_cv_columns_and_mean():
+    """Columns with their own speeds: each column's least-squares slope
+    recovers its speed; the mean is distance over mean travel time (the
+    harmonic mean of the column speeds), not their arithmetic mean."""
+    mesh = I.slab_mesh(40, 3, 2, (2.0, 0.3, 0.2))
+    g = I.rng(77)
+    NX = 41
+    ncol = mesh["xyz"].shape[0] // NX
+    v = g.uniform(0.03, 0.08, size=ncol)
+    x = mesh["xyz"][:, 0].reshape(ncol, NX)
+    at = (x / v[:, None] + g.uniform(0, 1, size=(ncol, 1))).ravel()
+    mean, col = bench.conduction_velocity(mesh, at)
+    assert np.allclose(col, v, rtol=1e-12)
+    # planes at x = 0.5 and 1.5: distance 1 over the mean of 1 / v
+    assert abs(mean - 1.0 / np.mean(1.0 / v)) <= 1e-12
+
+
+def test_cv_curved_front_slope_is_least_squares():
+    """A front that accelerates: the column speed is the reciprocal of the
+    least-squares line's slope over the window, checked against numpy's
+    polyfit on the same nodes."""
+    mesh = I.slab_mesh(30, 2, 2, (1.5, 0.2, 0.2))
+    x = mesh["xyz"][:, 0]
+    at = 20.0 * np.sqrt(x + 0.1)
+    _, col = bench.conduction_velocity(mesh, at)
+    xs = x[:31]
+    sel = slice(int(np.argmin(np.abs(xs - 0.375))), int(np.argmin(np.abs(xs - 1.125))) + 1)
+    slope = np.polyfit(xs[sel], (20.0 * np.sqrt(xs + 0.1))[sel], 1)[0]
+    assert np.allclose(col, 1.0 / slope, rtol=1e-10)
+
+
+def test_cv_undefined_cases():
+    """No velocity for the shell, or when a node of the window never
+    activated (the front has not crossed)."""
+    mesh = I.slab_mesh(20, 2, 2, (1.0, 0.2, 0.2))
+    at = mesh["xyz"][:, 0] / 0.05
+    at[(mesh["xyz"][:, 0] > 0.6)] = np.nan
+    assert bench.conduction_velocity(mesh, at) is None
+    shell = dict(mesh, kind=I.MESH_SHELL)
+    assert bench.conduction_velocity(shell, mesh["xyz"][:, 0]) is None
+
+
+def test_kernel_models_scale():
+    """Algorithmic bytes grow linearly with the nodes and with the inner
+    iterations of the persistent solve."""
+    N, E = 442401, 420000
+    a = bench.kernel_model("solve32", N, E, inner_iters=10.0, sweeps=2.0)[0]
+    b = bench.kernel_model("solve32", 2 * N, 2 * E, inner_iters=10.0, sweeps=2.0)[0]
+    c = bench.kernel_model("solve32", N, E, inner_iters=20.0, sweeps=2.0)[0]
+    assert abs(b / a - 2.0) < 1e-3
+    assert c > a
+    for name in ("ionic", "rhs", "resid"):
+        m1 = bench.kernel_model(name, N, E)[0]
+        m2 = bench.kernel_model(name, 2 * N, 2 * E)[0]
+        assert m1 > 0 and abs(m2 / m1 - 2.0) < 1e-3

@@ -23,7 +23,7 @@ void launch_ionic(Dev* d, const Dev& h, int grid, cudaStream_t s);
 void launch_assemble(Dev* d, const Dev& h, const AsmParams& P, cudaStream_t s);
 void launch_realpha(Dev* d, const Dev& h, double delta, double alpha_dt, float cmass, cudaStream_t s);
 void launch_rhs64(Dev* d, const Dev& h, int first, int graph, int grid, cudaStream_t s);
-void launch_rhs_ff(Dev* d, const Dev& h, int first, int graph, int grid, cudaStream_t s);
+void launch_rhs_ff(Dev* d, const Dev& h, int graph, int grid, cudaStream_t s);
 void launch_expand(Dev* d, const Dev& h, int want_a, int want_m, cudaStream_t s);
 void launch_realpha_ff(Dev* d, const Dev& h, double delta, double alpha_dt, float cmass, cudaStream_t s);
 void launch_p64(Dev* d, const Dev& h, int grid, cudaStream_t s);
@@ -37,7 +37,7 @@ void launch_ionic_batch(const Batch& B, int model, bool lv3, int grid, cudaStrea
 void launch_q2_apply32(Dev* d, const Dev& h, int grid_nodes, cudaStream_t s);
 void launch_q2_resid(Dev* d, const Dev& h, int first, int graph, int grid_nodes, cudaStream_t s);
 void launch_realpha_q2(Dev* d, const Dev& h, double alpha_dt, cudaStream_t s);
-void launch_rhs_ff_batch(const Batch& B, int first, int graph, int grid, cudaStream_t s);
+void launch_rhs_ff_batch(const Batch& B, int graph, int grid, cudaStream_t s);
 void launch_resid_np(Dev* d, const Dev& h, int graph, int grid, cudaStream_t s);
 cudaError_t launch_pcg32_batch(const Batch& B, int grid, cudaStream_t s);
 cudaError_t launch_prepace(int model, const uint8_t* cells, int ncell, double dt, long long m0, long long nsteps,
@@ -475,7 +475,7 @@ ep_status build_graph(ep_instance* I) {
     epk::launch_ionic(I->d, h, I->grid_ionic, s);
     if (h.prec == EP_PREC_FP64) epk::launch_rhs64(I->d, h, 1, 1, I->grid_tiles, s);
     else if (h.q2) epk::launch_q2_resid(I->d, h, 1, 1, I->grid_nodes, s);
-    else epk::launch_rhs_ff(I->d, h, 1, 1, I->grid_tiles, s);
+    else epk::launch_rhs_ff(I->d, h, 1, I->grid_resid, s);
     cudaGraph_t body = nullptr, body2 = nullptr;
     if (h.prec == EP_PREC_FP64) {
         C.chk(add_while(s, &h_loop, &body));
@@ -553,7 +553,7 @@ ep_status step_host(ep_instance* I) {
     timed(I, K_RHS, [&] {
         if (h.prec == EP_PREC_FP64) epk::launch_rhs64(d, h, 1, 0, I->grid_tiles, s);
         else if (h.q2) epk::launch_q2_resid(d, h, 1, 0, I->grid_nodes, s);
-        else epk::launch_rhs_ff(d, h, 1, 0, I->grid_tiles, s);
+        else epk::launch_rhs_ff(d, h, 0, I->grid_resid, s);
     });
     int f = 0;
     if (h.prec == EP_PREC_FP64) {
@@ -1193,7 +1193,7 @@ ep_status build_plan(BatchPlan* P) {
     // host tables: all instances, then the ionic kernel's groups: BO, TTP06
     // with two levels, TTP06 with three (BDF3)
     std::vector<Dev*> all, grp[3];
-    std::vector<int> s_tiles{0}, s_pcg{0}, s_grp[3] = {{0}, {0}, {0}};
+    std::vector<int> s_rhs{0}, s_pcg{0}, s_grp[3] = {{0}, {0}, {0}};
     double total = 0.0;
     for (ep_instance* I : P->key) total += (double)I->h.N;
     // persistent solver: blocks in proportion to size, at least one each,
@@ -1216,7 +1216,7 @@ ep_status build_plan(BatchPlan* P) {
     for (int i = 0; i < n; ++i) {
         ep_instance* I = P->key[i];
         all.push_back(I->d);
-        s_tiles.push_back(s_tiles.back() + I->grid_tiles);
+        s_rhs.push_back(s_rhs.back() + I->grid_resid);
         s_pcg.push_back(s_pcg.back() + gp[i]);
         const int gi = I->h.model == EP_MODEL_BO ? 0 : (I->h.u_nm2 ? 2 : 1);
         grp[gi].push_back(I->d);
@@ -1224,7 +1224,7 @@ ep_status build_plan(BatchPlan* P) {
     }
     // one device buffer: pointer arrays first (8-byte aligned), then ints
     size_t np = all.size();
-    size_t ni = s_tiles.size() + s_pcg.size();
+    size_t ni = s_rhs.size() + s_pcg.size();
     for (int gi = 0; gi < 3; ++gi) {
         np += grp[gi].size();
         ni += s_grp[gi].size();
@@ -1240,7 +1240,7 @@ ep_status build_plan(BatchPlan* P) {
     const size_t o_all = put(all.data(), all.size() * sizeof(Dev*));
     size_t o_grp[3], o_sgrp[3];
     for (int gi = 0; gi < 3; ++gi) o_grp[gi] = put(grp[gi].data(), grp[gi].size() * sizeof(Dev*));
-    const size_t o_st = put(s_tiles.data(), s_tiles.size() * sizeof(int));
+    const size_t o_st = put(s_rhs.data(), s_rhs.size() * sizeof(int));
     const size_t o_sp = put(s_pcg.data(), s_pcg.size() * sizeof(int));
     for (int gi = 0; gi < 3; ++gi) o_sgrp[gi] = put(s_grp[gi].data(), s_grp[gi].size() * sizeof(int));
     CUDA_TRY(cudaMalloc(&P->dmem, hbuf.size()));
@@ -1250,7 +1250,7 @@ ep_status build_plan(BatchPlan* P) {
         if (cnt == 1) return epk::single_batch(only);
         return epk::Batch{nullptr, reinterpret_cast<Dev* const*>(d + od), reinterpret_cast<const int*>(d + os), cnt};
     };
-    const epk::Batch Bt = mk(o_all, o_st, n, all[0]);
+    const epk::Batch Br = mk(o_all, o_st, n, all[0]);
     const epk::Batch Bp = mk(o_all, o_sp, n, all[0]);
 
     CUDA_TRY(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
@@ -1262,7 +1262,7 @@ ep_status build_plan(BatchPlan* P) {
         if (!grp[gi].empty())
             epk::launch_ionic_batch(mk(o_grp[gi], o_sgrp[gi], (int)grp[gi].size(), grp[gi][0]),
                                     gi == 0 ? EP_MODEL_BO : EP_MODEL_TTP06, gi == 2, s_grp[gi].back(), s);
-    epk::launch_rhs_ff_batch(Bt, 1, 0, s_tiles.back(), s);
+    epk::launch_rhs_ff_batch(Br, 0, s_rhs.back(), s);
     // every instance's refinement sweeps in one persistent launch (the
     // blocks of an instance that needs no sweep return at once)
     C.chk(epk::launch_pcg32_batch(Bp, s_pcg.back(), s));

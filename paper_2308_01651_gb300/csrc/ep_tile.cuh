@@ -134,31 +134,6 @@ __device__ __forceinline__ float row_f32(const float4* __restrict__ c, size_t N,
     return acc;
 }
 
-// float-float row: (sh + sl) = sum_t (chi + clo)(t) * (xh + xl)(h + dh(t)),
-// t = 0..26 in order, normalised
-__device__ __forceinline__ void row_ff(const float4* __restrict__ chi, const float4* __restrict__ clo,
-                                       size_t N, const float* xh, const float* xl, int h, int n, float& sh,
-                                       float& sl) {
-    sh = 0.f;
-    sl = 0.f;
-#pragma unroll
-    for (int g = 0; g < kGroups; ++g) {
-        const float4 a = chi[(size_t)g * N + n];
-        const float4 b = clo[(size_t)g * N + n];
-        int d = t_dh(4 * g);
-        ff_mac(a.x, b.x, xh[h + d], xl[h + d], sh, sl);
-        d = t_dh(4 * g + 1);
-        ff_mac(a.y, b.y, xh[h + d], xl[h + d], sh, sl);
-        d = t_dh(4 * g + 2);
-        ff_mac(a.z, b.z, xh[h + d], xl[h + d], sh, sl);
-        if (g < kGroups - 1) {
-            d = t_dh(4 * g + 3);
-            ff_mac(a.w, b.w, xh[h + d], xl[h + d], sh, sl);
-        }
-    }
-    ff_normalize(sh, sl);
-}
-
 // FP32 row of node n with neighbour values read from global memory
 // (node-parallel kernels): sum_t c(t) x(n + off(t)), t = 0..26 in order
 __device__ __forceinline__ float row32_np(const float4* __restrict__ c, size_t N, const float* __restrict__ x,
@@ -179,7 +154,7 @@ __device__ __forceinline__ float row32_np(const float4* __restrict__ c, size_t N
 
 // float-float row of node n with neighbour values read from global memory
 // (node-parallel kernels): (sh + sl) = sum_t (chi + clo)(t) (xh + xl)(n +
-// off(t)), t = 0..26 in order -- the same terms in the same order as row_ff
+// off(t)), t = 0..26 in order, normalised
 __device__ __forceinline__ void row_ff_np(const float4* __restrict__ chi, const float4* __restrict__ clo,
                                           size_t N, const float* __restrict__ xh, const float* __restrict__ xl,
                                           int n, const NbrOff& o, float& sh, float& sl) {
@@ -199,33 +174,6 @@ __device__ __forceinline__ void row_ff_np(const float4* __restrict__ chi, const 
         }
     }
     ff_normalize(sh, sl);
-}
-
-// Consistent mass matrix of a uniform Q1 slab, applied without stored
-// coefficients: M(n, n+o) = w c_x c_y c_z, w = hx hy hz / 216, with per
-// direction c = 1 off the diagonal and 4 (interior) or 2 (first/last node)
-// on it -- the 1D mass matrix h/6 [1 4 1] with its halved boundary diagonal,
-// exact for the trilinear basis.  The weights are powers of two, so the sum
-// runs in float-float on exact products; missing neighbours are staged as 0.
-// (sh + sl) = sum_t c(t) (xh + xl)(h + dh(t)) * (wh + wl), normalised.
-__device__ __forceinline__ void row_mass_slab(const Dev& D, const float* xh, const float* xl, int h, int n,
-                                              float& sh, float& sl) {
-    int i, j, k;
-    node_ijk(D, n, i, j, k);
-    const float cx = (i == 0 || i == D.NX - 1) ? 2.f : 4.f;
-    const float cy = (j == 0 || j == D.NY - 1) ? 2.f : 4.f;
-    const float cz = (k == 0 || k == D.NZ - 1) ? 2.f : 4.f;
-    sh = 0.f;
-    sl = 0.f;
-#pragma unroll
-    for (int t = 0; t < 27; ++t) {
-        const int di = t % 3 - 1, dj = (t / 3) % 3 - 1, dk = t / 9 - 1;
-        const float c = (di == 0 ? cx : 1.f) * (dj == 0 ? cy : 1.f) * (dk == 0 ? cz : 1.f);
-        const int d = t_dh(t);
-        ff_acc_pow2(c, xh[h + d], xl[h + d], sh, sl);
-    }
-    ff_normalize(sh, sl);
-    ff_mul(sh, sl, D.mw_hi, D.mw_lo, sh, sl);
 }
 
 }  // namespace epk

@@ -210,7 +210,7 @@ __global__ void k_realpha(Dev* __restrict__ Dp, double delta, double alpha_dt, f
 // its double sum; the inverse diagonal (offset 13: group 3, component y)
 // follows.
 // The mass couplings are the stored ones on curved meshes and the analytic
-// uniform-slab ones (w c_x c_y c_z, see row_mass_slab) on slabs.  The step
+// uniform-slab ones (w c_x c_y c_z, see mass_slab_np) on slabs.  The step
 // history of A u no longer matches A: it is marked empty.
 __global__ void k_realpha_ff(Dev* __restrict__ Dp, double delta, double alpha_dt, float cmass) {
     Dev& D = *Dp;

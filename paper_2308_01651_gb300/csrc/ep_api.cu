@@ -212,7 +212,7 @@ struct Sizes {
     int levels;       // time levels kept: 3 for BDF3, else 2
     bool q2;          // triquadratic slab
     int64_t ne;       // elements (Q2)
-    int64_t npad;     // zero nodes before and after the solver's neighbour-read vectors (Q1 slab)
+    int64_t npad;     // zero nodes before and after the inner solver's u (Q1 slab)
 };
 
 // float-float pair (nearest float, then the nearest float of the rest)
@@ -272,9 +272,7 @@ size_t footprint(const Sizes& z) {
         b += (2 + 2 * L) * al(N * 4);                                    // A u history (hi, lo)
         b += (1 + 2 * L) * al(N * 4);                                    // u levels (hi, lo), best slope
         if (z.op32 != EP_OP_STENCIL && !z.q2) b += al(6 * N * 4);       // fibres
-        const size_t Np = N + 2 * (size_t)z.npad;
-        b += 5 * al(N * 4) + al(Np * 4);  // r32 q32 d32 pa32 pb32, z32 (padded)
-        if (!z.q2) b += al(N * 4) + 2 * al(Np * 4);  // zz32, ma32 mb32 (padded)
+        b += 5 * al(N * 4) + al((N + 2 * (size_t)z.npad) * 4);  // r32 q32 d32 pa32 pb32, z32 (padded)
         if (!z.q2) b += al(N);            // boundary flags
     } else {
         b += 4 * al(N * 8);               // z64 q64 pa64 pb64
@@ -889,12 +887,7 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         ALLOC(h.d32, N);
         ALLOC(h.pa32, N);
         ALLOC(h.pb32, N);
-        if (!z.q2) {
-            ALLOC(h.zz32, N);
-            if ((st = dalloc_padded(I, &h.ma32, N, z.npad)) != EP_OK) return st;
-            if ((st = dalloc_padded(I, &h.mb32, N, z.npad)) != EP_OK) return st;
-            h.npad = (int)z.npad;
-        }
+        h.npad = (int)z.npad;
         if (!z.q2) ALLOC(h.nflag, N);
     } else {
         ALLOC(h.z64, N);

@@ -130,8 +130,7 @@ struct Dev {
     int op32;                   // EP_OP_MATRIX_FREE or EP_OP_STENCIL
     // ---- CG ------------------------------------------------------------------
     float *r32, *z32, *q32, *d32, *pa32, *pb32;
-    float *zz32, *ma32, *mb32;  // persistent stencil solve: z = A D^-1 s, m = D^-1 w (two buffers)
-    int npad;                   // Q1 slab: z32, ma32, mb32 have npad zero floats before and after
+    int npad;                   // Q1 slab: z32 has npad zero floats before and after it
     unsigned char* nflag;       // boundary flags per node (bits: i=0, i=NX-1, j=0, j=NY-1, k=0, k=NZ-1)
     double *z64, *q64, *pa64, *pb64;
     double rz, pq, alpha, beta, rr, rr0, bb, relres;

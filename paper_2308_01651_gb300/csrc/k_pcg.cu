@@ -4,36 +4,35 @@
 //
 // Jacobi-preconditioned CG (the paper solves Eq. (6) with CG, Sec. 2) on
 // A delta = r in float, A the hi parts of the node-major full couplings, in
-// the pipelined arrangement of Ghysels and Vanroose (2014): besides r, the
-// recurrences carry w = A u (u = D^-1 r), s = A p and z = A D^-1 s, so an
-// iteration needs one operator apply, to m = D^-1 w, and its three dot
-// products come from the same pass.  With D diagonal, u = D^-1 r and
-// m = D^-1 w are formed from r and w directly, so only z needs the extra
-// recurrence.  Iteration i, given alpha_i and beta_i (beta_0 = 0):
-//   one pass, every node on its own after its row of A:
-//     n_i = A m_i,             z_i = n_i + beta_i z_{i-1},
-//     s_i = w_i + beta_i s_{i-1},   p_i = u_i + beta_i p_{i-1},
-//     delta += alpha_i p_i,    r_{i+1} = r_i - alpha_i s_i,
-//     w_{i+1} = w_i - alpha_i z_i,   m_{i+1} = D^-1 w_{i+1} (into the other
-//     of two m buffers: this pass reads the neighbours' m_i), and block
-//     partials of gamma = (r, u), eta = (u, w), rho = (r, r) at i + 1
-//   one grid barrier; every block sums all partials in the same fixed
-//   order, so all blocks take the same
+// the single-reduction arrangement of Chronopoulos and Gear (1989): with
+// u = D^-1 r and w = A u, both dot products of an iteration come from the
+// same pass.  Iteration i, given alpha_i and beta_i:
+//   update (every node on its own):
+//     s_i = w_i + beta_i s_{i-1},   r_{i+1} = r_i - alpha_i s_i,
+//     p_i = u_i + beta_i p_{i-1},   delta  += alpha_i p_i,   u_{i+1} = D^-1 r_{i+1}
+//   grid barrier (u_{i+1} of the neighbours is needed next)
+//   apply: w_{i+1} = A u_{i+1}; block partials of
+//     gamma = (r_{i+1}, u_{i+1}), eta = (u_{i+1}, w_{i+1}), rho = (r_{i+1}, r_{i+1})
+//   grid barrier; every block sums all partials in the same fixed order, so
+//   all blocks take the same
 //     beta_{i+1} = gamma_{i+1} / gamma_i,
 //     alpha_{i+1} = gamma_{i+1} / (eta_{i+1} - beta_{i+1} gamma_{i+1} / alpha_i)
-//   and the same stopping decision (rho against the sweep's stop).
-// In exact arithmetic these are CG's iterates (Chronopoulos and Gear's
-// scalars); in float the recursive w drifts from A u by
-// rounding that the refinement's float-float residual removes.  The
-// right-hand-side kernel (or the previous sweep's residual) leaves r_0 and
-// u_0 = D^-1 r_0, so a sweep starts with one pass forming w_0 = A u_0,
-// m_0 = D^-1 w_0 and the first dot products.  Nodes are spread over all
-// threads of the grid in index order (thread t: nodes t, t + T, ...), so
-// every thread owns the same number of nodes up to one.  Neighbour values
-// of m and u are plain cached loads: they were written before the last
-// barrier, whose release/acquire pair orders them for every thread of the
-// block.  A barrier that does not complete within ~1 s records EP_ETIMEOUT
-// and the kernel returns.
+//   and the same stopping decision (rho relative to the sweep's first rho).
+// The right-hand-side kernel leaves r_0 and u_0 = D^-1 r_0, so the launch
+// starts with the apply of u_0.  Nodes are spread over all threads of the
+// grid in index order (thread t: nodes t, t + T, ...), so every thread owns
+// the same number of nodes up to one.  Neighbour values of u are plain
+// cached loads: they were written before the last barrier, whose
+// release/acquire pair orders them for every thread of the block; on a Q1
+// slab u is padded with zeros, so rows read their neighbours at fixed
+// offsets without the boundary flags.  A barrier that does not complete
+// within ~1 s records EP_ETIMEOUT and the kernel returns.
+//
+// A pipelined arrangement (Ghysels and Vanroose 2014: w and z = A D^-1 s by
+// recurrence, one pass and one barrier per iteration) measured the same on
+// the 442k-node slab (331 against 333 us a step's solve) and slower on the
+// LV shell, where the float recurrences slowed convergence (100 inner
+// iterations a sweep against 36); it is not used.
 //
 // After the inner solve: u += delta (float-float), a grid barrier, then the
 // residual of the sweep on the same node map -- y = A u with the float-float
@@ -142,12 +141,11 @@ __device__ __noinline__ void resid_ff_nodes(const Dev& D, int t0, int T, float (
 }
 
 // MINB resident 512-thread blocks per SM.  An instance alone runs one per
-// SM: up to 128 registers a thread, so the fused pass keeps its pointers and
-// row in registers, and 152 blocks arrive at each grid barrier.  Measured on
-// the 442k-node slab: 326 us a step's solve against 357 us with two
-// 256-thread blocks per SM (same warps, twice the arrivals a barrier) and
-// 350 us with two 512-thread blocks (64 registers, spills).  A batch runs
-// two per SM: its instances' barriers gather a few blocks each, and its
+// SM: up to 128 registers a thread (no spills), and 152 blocks arrive at
+// each grid barrier, whose cost grows with the arrivals.  Measured on the
+// 442k-node slab (t = 1-16 ms): 333 us a step's solve, against 368 us with
+// two blocks per SM (64 registers, spills, 304 arrivals a barrier).  A batch
+// runs two per SM: its instances' barriers gather a few blocks each, and its
 // working set, far beyond L2, wants the loads of more warps in flight.
 template <int MINB>
 __global__ void __launch_bounds__(kPcgThreads, MINB) k_solve32_stencil(Batch B) {
@@ -167,13 +165,12 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) k_solve32_stencil(Batch B) 
     float* __restrict__ w = D.q32;
     float* __restrict__ s = D.pa32;
     float* __restrict__ p = D.pb32;
-    float* __restrict__ z = D.zz32;
     float* __restrict__ x = D.d32;
     const float* __restrict__ dinv = D.dinv32;
     const unsigned char* __restrict__ flag = D.nflag;
-    // Q1 slab: u and m are padded, so every row reads its 27 neighbours at
-    // fixed offsets (couplings past the slab's edge are 0) and the boundary
-    // flags are not needed
+    // Q1 slab: u is padded, so every row reads its 27 neighbours at fixed
+    // offsets (couplings past the slab's edge are 0) and the boundary flags
+    // are not needed
     const bool fixed = D.npad > 0 && wrap == 0;
     const float4* __restrict__ A = D.Ahi;
     float* part = reinterpret_cast<float*>(D.partial);
@@ -197,61 +194,42 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) k_solve32_stencil(Batch B) 
     for (;;) {  // ---- refinement sweeps
         float alpha = 0.f, beta = 0.f;
         bool first = true;
-        int cur = 0;  // the m buffer the next pass applies A to
         if (threadIdx.x == 0) sc_it = 0;
-        for (;;) {  // ---- inner CG, one pass and one grid barrier per iteration
-            const float* __restrict__ mc = cur ? D.mb32 : D.ma32;
-            float* __restrict__ mn = cur ? D.ma32 : D.mb32;
-            float v[3] = {0.f, 0.f, 0.f};  // gamma, eta, rho of the new vectors
-            if (first) {
-                // w_0 = A u_0 (u_0 = D^-1 r_0 from the residual), m_0 = D^-1 w_0
-                const float* __restrict__ u = D.z32;
-                float* __restrict__ m0 = D.ma32;
-                unsigned int fn = (!fixed && t0 < N) ? flag[t0] : 0u;
+        float* __restrict__ u = D.z32;
+        for (;;) {  // ---- inner CG: an update pass and an apply pass per iteration
+            if (!first) {
+                // ---- update, node by node
                 for (int n = t0; n < N; n += T) {
-                    const unsigned int f = fn;
-                    fn = (!fixed && n + T < N) ? flag[n + T] : 0u;
-                    const NbrOff o = nbr_offsets(nx, nxy, wrap, f);
-                    const float acc = row32_np(A, NN, u, n, o);
-                    const float rn = r[n], un = u[n];
-                    w[n] = acc;
-                    m0[n] = dinv[n] * acc;
-                    v[0] = fmaf(rn, un, v[0]);
-                    v[1] = fmaf(un, acc, v[1]);
-                    v[2] = fmaf(rn, rn, v[2]);
-                }
-            } else {
-                // n_i = A m_i, then every recurrence of the iteration and
-                // m_{i+1} = D^-1 w_{i+1} into the other m buffer (this pass
-                // reads the neighbours' m_i from the first)
-                unsigned int fn = (!fixed && t0 < N) ? flag[t0] : 0u;
-                for (int n = t0; n < N; n += T) {
-                    // the next node's flags load while this node's row runs
-                    const unsigned int f = fn;
-                    fn = (!fixed && n + T < N) ? flag[n + T] : 0u;
-                    const NbrOff o = nbr_offsets(nx, nxy, wrap, f);
-                    const float an = row32_np(A, NN, mc, n, o);
                     const float dv = dinv[n];
-                    const float r0 = r[n], w0 = w[n];
-                    const float u0 = dv * r0;
-                    const float z1 = beta == 0.f ? an : fmaf(beta, z[n], an);
+                    const float r0 = r[n], w0 = w[n], u0 = u[n];
                     const float s1 = beta == 0.f ? w0 : fmaf(beta, s[n], w0);
                     const float p1 = beta == 0.f ? u0 : fmaf(beta, p[n], u0);
                     const float r1 = fmaf(-alpha, s1, r0);
-                    const float w1 = fmaf(-alpha, z1, w0);
-                    const float u1 = dv * r1;
                     x[n] = fmaf(alpha, p1, x[n]);
-                    z[n] = z1;
                     s[n] = s1;
                     p[n] = p1;
                     r[n] = r1;
-                    w[n] = w1;
-                    mn[n] = dv * w1;
-                    v[0] = fmaf(r1, u1, v[0]);
-                    v[1] = fmaf(u1, w1, v[1]);
-                    v[2] = fmaf(r1, r1, v[2]);
+                    u[n] = dv * r1;
                 }
-                cur ^= 1;
+                if (!grid_barrier(bcount, target, G, &D.status)) {
+                    aborted = true;
+                    break;
+                }
+            }
+            // ---- apply w = A u and the block partials
+            float v[3] = {0.f, 0.f, 0.f};  // gamma, eta, rho
+            unsigned int fn = (!fixed && t0 < N) ? flag[t0] : 0u;
+            for (int n = t0; n < N; n += T) {
+                // the next node's flags load while this node's row runs
+                const unsigned int f = fn;
+                fn = (!fixed && n + T < N) ? flag[n + T] : 0u;
+                const NbrOff o = nbr_offsets(nx, nxy, wrap, f);
+                const float acc = row32_np(A, NN, u, n, o);
+                w[n] = acc;
+                const float rn = r[n], un = u[n];
+                v[0] = fmaf(rn, un, v[0]);
+                v[1] = fmaf(un, acc, v[1]);
+                v[2] = fmaf(rn, rn, v[2]);
             }
             publish<3>(v, part, G, S.blk);
             if (!grid_barrier(bcount, target, G, &D.status)) {

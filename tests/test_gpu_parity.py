@@ -257,7 +257,9 @@ def test_steps_converging_at_first_residual_keep_history_exact():
     A u_EXT as its own A u, or the next steps' history would be stale.  After
     every such step the relative residual the solver reports (from the
     history) must equal the one recomputed from scratch (b - A u_n with the
-    operator, ep_residual_norm_noalloc) to the float-float accuracy."""
+    operator, ep_residual_norm_noalloc): both residuals are float-float, but
+    their norms are float sums taken over different thread grids, so they
+    agree to ~1e-7 relative (a stale history would be off by O(1))."""
     prob = small_ttp06(nx=30, ny=8, nz=6, T=30.0)
     inst = ep.Instance(prob, precision=REF, tol=1e-5)
     zero_sweeps = 0
@@ -268,7 +270,7 @@ def test_steps_converging_at_first_residual_keep_history_exact():
             if st["sweeps"] == 0:
                 zero_sweeps += 1
                 exact = ep.ep_residual_norm_noalloc(inst.h)
-                assert abs(exact - st["relres"]) <= 1e-12, (exact, st["relres"])
+                assert abs(exact - st["relres"]) <= 1e-6 * exact, (exact, st["relres"])
     finally:
         inst.close()
     assert zero_sweeps >= 5, zero_sweeps

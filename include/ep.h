@@ -311,7 +311,10 @@ ep_status ep_profile_read(ep_instance* inst, ep_kernel_time* out, int32_t cap,
  * (the value ep_get_stats reports as relres), recomputed from the instance's
  * operator, right-hand side and the solver's float-float iterate u (whose sum
  * rounded to double is the potential u_n) in the same arithmetic and
- * summation order as the solver's residual; instances other than refined
+ * summation order as the solver's residual when the instance steps alone
+ * (ep_step_batch spreads an instance over other blocks, so its reported
+ * relres may differ from this one in the float summation, ~1e-7 relative);
+ * instances other than refined
  * ones with the stencil FP32 operator get EP_EUNSUPPORTED.  After ep_state_load
  * it still describes the last solve run, not the loaded state.  It calls no
  * cudaMalloc, cudaFree

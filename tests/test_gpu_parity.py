@@ -134,6 +134,12 @@ def test_trajectory_bo_fp64_and_refined():
 
 
 def test_trajectory_ttp06_refined():
+    """TTP06 slab 0.4 x 0.1 x 0.06 cm over 25 ms (the wave crosses it):
+    activation times within 0.5 ms of the oracle's, u within 1 mV away from
+    each node's upstroke, and the conduction velocity along x (plane means
+    between 0.25 and 0.75 Lx, and every line of nodes along x) within 1 %."""
+    import bench
+
     prob = small_ttp06(nx=40, ny=10, nz=6, T=25.0)
     sim = O.sim_from_problem(prob)
     inst = ep.Instance(prob, precision=REF)
@@ -152,6 +158,12 @@ def test_trajectory_ttp06_refined():
     for t, u_ref, u in snaps:
         near = np.abs(np.nan_to_num(at_ref, nan=-1e9) - t) <= 2 * prob["dt"]
         assert np.abs(u - u_ref)[~near].max() <= 1.0
+    cv_ref = bench.conduction_velocity(prob["mesh"], at_ref)
+    cv = bench.conduction_velocity(prob["mesh"], at)
+    assert cv_ref is not None and cv is not None
+    assert 0.04 < cv_ref[0] < 0.08  # cm/ms: the wave crossed the slab
+    assert abs(cv[0] - cv_ref[0]) <= 0.01 * cv_ref[0]
+    assert np.max(np.abs(cv[1] - cv_ref[1]) / cv_ref[1]) <= 0.01
 
 
 def test_deterministic_and_checkpoint_roundtrip():

@@ -271,6 +271,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_replicas(total_ms, units, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed over the slowest rank's time.  total_ms, units: this rank's
+    timed milliseconds and units (DoF-steps); dist: torch.distributed (None
+    for one process), its tensors on `device`.  Returns (units per second,
+    the slowest rank's ms, all ranks' units); every rank gets the same."""
+    if dist is not None:
+        import torch
+        tm = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        un = torch.tensor([float(units)], dtype=torch.float64, device=device)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        dist.all_reduce(un, op=dist.ReduceOp.SUM)
+        total_ms, units = float(tm.item()), float(un.item())
+    return units / (total_ms / 1e3), total_ms, units
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -397,12 +413,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     times = [a.elapsed_time(b) for a, b in ev]  # ms
-    total_ms = sum(times)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = N * K * world / (total_ms / 1e3)
+    value, total_ms, _ = aggregate_replicas(sum(times), N * K, dist, "cuda")
     lat = sorted(times)
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]

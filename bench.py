@@ -330,7 +330,10 @@ def run_reference(args):
             "steps": leg["steps"], "warmup": 0, "ms_per_step": leg["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS.get(args.workload, WORKLOAD), "nodes": prob["mesh"]["xyz"].shape[0],
-                       "l2": "n/a (CPU)", "note": "bounded sample; see cpu_baseline.sample"},
+                       "l2": "n/a (CPU)",
+                       "note": f"bounded sample of the requested --steps {args.steps} --warmup {args.warmup} "
+                               "(full-mesh oracle steps take ~1 s each): steps = the oracle steps timed, "
+                               "see cpu_baseline.sample"},
             "cpu_baseline": {k: leg[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": leg["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -1097,8 +1097,10 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     // pointwise reducing kernels: a persistent grid of four 256-thread blocks
-    // per SM (one partial sum and one counter update per block); tiled
-    // stencil kernels: two 512-thread blocks per SM
+    // per SM (one partial sum and one counter update per block); tiled (FP64)
+    // stencil kernels and the node-parallel first residual and residual: two
+    // 512-thread blocks per SM; the persistent solve: as many blocks as fit
+    // (one per SM alone)
     I->grid_nodes = std::max(1, std::min(blocks, 4 * sms));
     I->grid_ionic = (int)((N + epk::kIonicThreads - 1) / epk::kIonicThreads);
     I->grid_resid = std::max(1, std::min((int)((N + epk::kResidThreads - 1) / epk::kResidThreads), 2 * sms));

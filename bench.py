@@ -15,7 +15,7 @@ activation-time error of the refined path against the FP64 GPU path, an
 end-to-end figure through the public API with host buffers, and the SM
 clocks sampled during the timed region.
 
---impl reference times the FP64 CPU oracle (the reference of this build) on
+--impl reference times the FP64 CPU oracle (the reference arm: the paper's own code is not available) on
 the same workload, a bounded number of steps, on the host cores.
 Multi-GPU (torchrun): every rank runs its own replica (the path has no
 cross-instance exchange), value = all ranks' DoF-steps / the slowest rank.

@@ -49,7 +49,7 @@ typedef enum {
     EP_ENAN = 4,         /* a potential became non-finite */
     EP_ETIMEOUT = 5,     /* a bounded device wait gave up */
     EP_ECUDA = 6,        /* a CUDA runtime call failed */
-    EP_EUNSUPPORTED = 7  /* a valid request this build does not implement */
+    EP_EUNSUPPORTED = 7  /* a valid request this library does not implement */
 } ep_status;
 
 /* Meshes: EP_MESH_SLAB, the box [0,L] with nx x ny x nz trilinear hexahedra;

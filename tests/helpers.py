@@ -49,3 +49,13 @@ def synthetic_front_state(prob, g, width=0.05):
     w_n = w * (1.0 + 1e-3 * g.normal(size=w.shape))
     w_nm1 = w.copy()
     return u_n, u_nm1, w_n, w_nm1
+
+
+def golden(name):
+    """A fixture of values the paper prints (tests/golden/<name>, with its
+    citation inside)."""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:
+        return json.load(f)

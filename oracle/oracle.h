@@ -175,7 +175,7 @@ or_sim* or_sim_create_q2(int64_t nn, int64_t ne, const double* xyz,
                          int bdf_order, double tol, int maxit, int npulses,
                          const or_pulse* pulses, const uint8_t* masks,
                          double act_thr);
-/* Spatial profile of pulse p (Sec. 3.2.x: spherical and Gaussian impulses):
+/* Spatial profile of pulse p (Secs. 3.2.2 and 3.2.3: spherical and Gaussian impulses):
  * the node receives amp * weight[node] instead of amp * (mask[node] != 0).
  * NULL restores the mask.  The array is copied. */
 void or_sim_set_pulse_weights(or_sim* S, int p, const double* weight);

@@ -1,5 +1,5 @@
 // k_q2.cu -- matrix-free operators of triquadratic (Q2, 27-node) hexahedra on
-// slab meshes (Sec. 1.2: hexahedral elements of any degree; Sec. 5 names
+// slab meshes (Sec. 1.2: hexahedral elements of any degree; Sec. 4 names
 // high-order matrix-free solvers on GPUs as the way forward).
 //
 // The element operator of Eq. (6), A_e = alpha/dt M_e + K_e, is applied by

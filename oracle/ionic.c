@@ -17,7 +17,15 @@
  * Every rate is returned as dw/dt = a - b w.  The semi-implicit step of
  * Eq. (4) then reads w_{n+1} = (w_BDF + dt a) / (alpha + dt b): states whose
  * rate is affine in themselves (b > 0) are implicit, the rest (b = 0) are
- * explicit, as the paper prescribes ("directly inverting").
+ * explicit, as the paper's scheme has it.
+ *
+ * Parity unpinned (in part): the paper prints neither model, so the rates and
+ * currents away from rest are pinned only by what the tests can fix without
+ * them -- the BO rest state exact, the TTP06 initial state (the paper's)
+ * staying within 1 mV for 1 s, action-potential features of the source
+ * publications, the step converging to RK4 at first order, and end to end the
+ * N-version activation time the paper reports.  A wrong constant that keeps
+ * those features would go unnoticed by the oracle's pins.
  */
 #include <math.h>
 #include <string.h>

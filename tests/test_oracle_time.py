@@ -109,3 +109,59 @@ def test_manufactured_solution_converges_in_space():
         errs.append(np.abs(u - exact).max() / np.abs(exact).max())
     assert errs[0] < 0.1
     assert 3.0 < errs[0] / errs[1] < 5.0, errs
+
+
+def _eigen_recurrence(bdf, lam, g, dt, nsteps):
+    """Amplitudes a_n of a discrete eigenmode (K v = lam M v) under the IMEX
+    step: (alpha/dt + lam) a_{n+1} = a_BDF/dt - g a_EXT, the order ramping
+    1 -> 2 -> 3 over the first steps."""
+    a = [1.0]
+    for n in range(nsteps):
+        order = min(bdf, n + 1)
+        x = a[-1]
+        y = a[-2] if len(a) > 1 else 0.0
+        z = a[-3] if len(a) > 2 else 0.0
+        if order == 1:
+            alpha, aB, aE = 1.0, x, x
+        elif order == 2:
+            alpha, aB, aE = 1.5, 2 * x - 0.5 * y, 2 * x - y
+        else:
+            alpha, aB, aE = 11.0 / 6.0, 3 * x - 1.5 * y + z / 3.0, 3 * x - 3 * y + z
+        a.append((aB / dt - g * aE) / (alpha / dt + lam))
+    return np.array(a)
+
+
+@pytest.mark.parametrize("bdf", [1, 2, 3])
+def test_discrete_eigenmode_closed_form(bdf):
+    """On a box of Q1 elements the nodal vector v = cos(pi x/Lx) cos(pi y/Ly)
+    cos(pi z/Lz) is an exact eigenvector of the Neumann problem, K v = lam M v
+    with lam = sum_d D_d (6/h_d^2)(1 - cos t_d)/(2 + cos t_d), t_d = pi h_d/L_d
+    (the 1-D consistent mass h/6 [1 4 1] and stiffness 1/h [-1 2 -1], and
+    their halved boundary rows, act on cos(pi i h/L) by those factors).  With
+    a passive membrane I_ion = g u, anisotropic diagonal D, no stimulus, the
+    whole IMEX step on that mode is a scalar recurrence, written out above:
+    every step of the oracle must reproduce it (M, K, alpha, u_BDF, the
+    explicit u_EXT in the ionic term, the order ramp)."""
+    n, L = (7, 5, 3), (0.7, 0.4, 0.45)
+    D = (2e-2, 0.7e-2, 0.4e-2)
+    g, dt, steps = 0.8, 0.05, 12
+    m = I.slab_mesh(*n, L)
+    xyz = m["xyz"]
+    f0, s0 = I.uniform_fibres(xyz.shape[0])
+    S = O.Sim(xyz, m["hex"], f0, s0, D, O.PASSIVE, dt, bdf, g=g, tol=1e-14)
+    v = np.cos(math.pi * xyz[:, 0] / L[0]) * np.cos(math.pi * xyz[:, 1] / L[1]) * np.cos(math.pi * xyz[:, 2] / L[2])
+    lam = 0.0
+    for d in range(3):
+        h = L[d] / n[d]
+        t = math.pi * h / L[d]
+        lam += D[d] * (6.0 / h ** 2) * (1.0 - math.cos(t)) / (2.0 + math.cos(t))
+    z = np.zeros((0, xyz.shape[0]))
+    S.set_state(v, v, z, z, 0)
+    amp = _eigen_recurrence(bdf, lam, g, dt, steps)
+    for k in range(1, steps + 1):
+        S.step(1)
+        assert np.abs(S.potential() - amp[k] * v).max() <= 1e-11 * np.abs(amp[k]), k
+    # the mode decays, and not at the continuous rate (the discrete lam is
+    # what the check above fixes)
+    cont = sum(D[d] * (math.pi / L[d]) ** 2 for d in range(3))
+    assert abs(lam - cont) > 1e-3 * cont

@@ -12,6 +12,9 @@ What fixes each check:
     u of 1.2..1.7 (u_mV = 85.7 u - 84, Sec. 3.2.3) with APD90 of 200..350 ms.
   * The semi-implicit step converges to a classical RK4 solution of the same
     ODE (Eq. (1)), at order 1 for BDF1.
+  * Bueno-Orovio excitability: released above theta_v = 0.3 a cell fires,
+    at or below it relaxes to rest (a mistyped threshold or gate constant
+    moves that boundary).
 """
 import numpy as np
 import pytest
@@ -134,3 +137,16 @@ def test_semi_implicit_step_converges_to_rk4():
     assert all(e2 < 0.2 * e1 for e1, e2 in zip(errs[1], errs[2]))
     r2 = [errs[2][i] / errs[2][i + 1] for i in range(2)]
     assert all(r > 2.2 for r in r2), r2
+
+
+def test_bo_excitation_threshold():
+    """The minimal model is excitable with a threshold: a cell released
+    above theta_v = 0.3 fires a full upstroke (fast inward J_fi opens), one
+    released at theta_v or below relaxes towards rest without firing (first
+    with tau_o2 = 6 ms, below theta_o = 0.006 with tau_o1 = 400 ms; epicardial
+    set of Bueno-Orovio et al. 2008)."""
+    fired = run_cell(O.BO, O.EPI, 0.01, 100.0, 0.0, 0.0, u0=0.35)
+    assert fired.max() > 1.2
+    for u0 in (0.10, 0.30):
+        quiet = run_cell(O.BO, O.EPI, 0.01, 100.0, 0.0, 0.0, u0=u0)
+        assert quiet.max() <= u0 and 0.0 < quiet[-1] < 0.006

@@ -72,3 +72,20 @@ def test_kernel_models_scale():
         m1 = bench.kernel_model(name, N, E)[0]
         m2 = bench.kernel_model(name, 2 * N, 2 * E)[0]
         assert m1 > 0 and abs(m2 / m1 - 2.0) < 1e-3
+
+
+def test_algorithmic_bytes_per_node():
+    """The roofline's algorithmic bytes are the hot path's per-node minimum:
+    an inner CG iteration 60 B (x 4, y 4, fibres 24, seven FP32 vector
+    touches 28; the shell adds 12 B of coordinates), a float-float residual
+    48 B (+12), the right-hand side 28 B, the refined TTP06 ionic step
+    2 (13 x 4 + 5 x 8) + 16 + 4 = 204 B."""
+    N, E = 1000, 900
+    one_it = bench.kernel_model("solve32", N, E, inner_iters=1.0, sweeps=0.0)[0] / N
+    one_sw = bench.kernel_model("solve32", N, E, inner_iters=0.0, sweeps=1.0)[0] / N
+    assert (one_it, one_sw) == (60, 48)
+    sh_it = bench.kernel_model("solve32", N, E, inner_iters=1.0, sweeps=0.0, shell=True)[0] / N
+    sh_sw = bench.kernel_model("solve32", N, E, inner_iters=0.0, sweeps=1.0, shell=True)[0] / N
+    assert (sh_it, sh_sw) == (72, 60)
+    assert bench.kernel_model("rhs", N, E)[0] / N == 28
+    assert bench.kernel_model("ionic", N, E)[0] / N == 2 * (13 * 4 + 5 * 8) + 16 + 4

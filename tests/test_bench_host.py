@@ -89,3 +89,22 @@ def test_algorithmic_bytes_per_node():
     assert (sh_it, sh_sw) == (72, 60)
     assert bench.kernel_model("rhs", N, E)[0] / N == 28
     assert bench.kernel_model("ionic", N, E)[0] / N == 2 * (13 * 4 + 5 * 8) + 16 + 4
+
+
+def test_clock_summary_parses_samples_and_reasons():
+    """The clocks record of the bench line: median SM clock under load, the
+    maximum, and every throttle reason seen Active in any sample (a sample
+    line that is not a full record is skipped)."""
+    c = bench.ClockSampler(0)
+    c.lines = [
+        "0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1400.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "[N/A]",
+    ]
+    s = c.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.lines = ["0, 1500, 2070, 1000, 0x40, Active, Not Active, Active, Not Active"]
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    c.lines = []
+    assert c.summary()["samples"] == 0

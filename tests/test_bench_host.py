@@ -1,6 +1,8 @@
 """Host-side measurement helpers of bench.py (no GPU): the conduction
-velocity read from an activation map, and the per-kernel byte models."""
+velocity read from an activation map, the per-kernel byte models, the
+committed DRAM traffic and the clock record."""
 import numpy as np
+import pytest
 
 import bench
 from paper_2308_01651_gb300 import inputs as I
@@ -108,3 +110,27 @@ def test_clock_summary_parses_samples_and_reasons():
     assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     c.lines = []
     assert c.summary()["samples"] == 0
+
+
+def test_committed_traffic_scaling_and_staleness(monkeypatch):
+    """Traffic of the persistent solve is the captured launch's DRAM bytes
+    scaled by the ratio of algorithmic bytes (this run's average launch over
+    the captured one, whose iterations and sweeps the record holds); a kernel
+    whose sources changed since the capture reports none."""
+    import json
+    import os
+
+    with open(os.path.join(bench.ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)["solve32"]
+    N, E = 442401, 420000
+    # sources as at the capture (the check below does not depend on the
+    # current files)
+    monkeypatch.setattr(bench, "source_hash", lambda files: rec["source_hash"])
+    cap = bench.kernel_model("solve32", N, E, rec["inner_iters"], sweeps=rec["sweeps"])[0]
+    alg = bench.kernel_model("solve32", N, E, 8.45, sweeps=1.36)[0]
+    t = bench.committed_traffic("solve32", N, E, alg)
+    assert t == pytest.approx(rec["dram_bytes_per_launch"] * alg / cap, rel=1e-12)
+    assert bench.committed_traffic("solve32", N, E, cap) == pytest.approx(rec["dram_bytes_per_launch"])
+    monkeypatch.setattr(bench, "source_hash", lambda files: "changed")
+    assert bench.committed_traffic("solve32", N, E, alg) is None
+    assert bench.committed_traffic("no_such_kernel") is None

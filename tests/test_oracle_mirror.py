@@ -1,4 +1,4 @@
-"""Mirror symmetry of the oracle's whole simulation (CPU).
+"""Mirror and rotation symmetry of the oracle's whole simulation (CPU).
 
 A slab with fibres along x, a diffusion tensor diagonal in x, y, z, and a
 stimulus box centred in the slab is invariant under each of the reflections
@@ -48,3 +48,25 @@ def test_solution_is_mirror_symmetric(model, bdf):
         assert np.array_equal(np.isnan(a), np.isnan(b))
         ok = ~np.isnan(a)
         assert np.abs(a[ok] - b[ok]).max() <= prob["dt"] + 1e-12
+
+
+def test_shell_solution_is_rotation_invariant():
+    """The truncated-ellipsoid shell is a surface of revolution meshed with
+    the same element column at every azimuth (periodic in phi); the helix
+    fibres, the cell types (by depth) and the apical stimulus (whole rings)
+    do not depend on phi.  So a rotation by one element column maps the
+    problem onto itself and the potential and activation times are the same
+    in every column, to the rounding of the nodes' sines and cosines and the
+    CG's stopping point (measured 4e-10).  A wrong neighbour across the
+    periodic seam or an azimuth-dependent index breaks it."""
+    p = I.shell_ttp06(nt=3, nphi=16, nlong=10, T=10.0)
+    sim = O.sim_from_problem(p)
+    sim.step(p["nsteps"])
+    shape = (11, 16, 4)  # (longitudinal, azimuthal, transmural)
+    u = sim.potential().reshape(shape)
+    assert np.abs(u - u.mean(axis=1, keepdims=True)).max() <= 1e-8 * np.abs(u).max()
+    at = sim.activation()[0].reshape(shape)
+    assert np.isfinite(at).sum() > 100  # the wave left the stimulated rings
+    assert np.array_equal(np.isnan(at), np.isnan(np.roll(at, 1, axis=1)))
+    ok = ~np.isnan(at)
+    assert np.abs(at - np.roll(at, 1, axis=1))[ok].max() <= p["dt"] + 1e-12

@@ -313,21 +313,28 @@ ep_status ep_profile_read(ep_instance* inst, ep_kernel_time* out, int32_t cap,
  * rounded to double is the potential u_n) in the same arithmetic and
  * summation order as the solver's residual when the instance steps alone
  * (ep_step_batch spreads an instance over other blocks, so its reported
- * relres may differ from this one in the float summation, ~1e-7 relative);
- * instances other than refined
- * ones with the stencil FP32 operator get EP_EUNSUPPORTED.  After ep_state_load
- * it still describes the last solve run, not the loaded state.  It calls no
- * cudaMalloc, cudaFree
- * or other allocating routine, for callers that must not allocate device
- * memory where they check a solve (while capturing a stream into a graph, in
- * a host callback, under an external allocator that owns all device memory).
- * Its scratch is a fixed ~16 KiB device array in the library, holding one
- * pair of partial sums per thread block, at most 1024 blocks; an instance
- * whose residual kernel would need more blocks is refused with EP_EINVAL.
- * The first call on each device looks up that array's device address: make
- * it before any stream capture on the device.  All calls share the array,
- * so calls whose GPU work overlaps (unordered streams) race; calls ordered
- * on one stream do not.  Runs on the instance's stream and waits for it. */
+ * relres may differ from this one in the float summation, ~1e-7 relative).
+ * Errors: EP_EUNSUPPORTED for instances other than refined ones with the
+ * stencil FP32 operator; EP_EINVAL when no step has run since ep_create or
+ * the last ep_load_state (a loaded potential has no solve of its own), or
+ * when the last solve's right-hand side is zero (no relative residual).
+ *
+ * Who it is for: callers that cannot call cudaMalloc where they check a
+ * solve -- for example a host application whose device memory is owned by
+ * another allocator (a framework's caching allocator, or a pool that
+ * reserves the GPU's memory at start-up), where an allocation by this
+ * library would fail or break the owner's accounting.  This call allocates
+ * nothing: it calls no cudaMalloc, cudaFree or other allocating routine.
+ * Its scratch is a fixed ~16 KiB device array in the library (every GPU that
+ * loads the library holds it until the process exits), holding one pair of
+ * partial sums per thread block, at most 1024 blocks; an instance whose
+ * residual kernel would need more blocks is refused with EP_EINVAL.  The
+ * first call on each device looks up that array's device address (done
+ * once per device, with that device current).  All calls share the array
+ * and it keeps the last call's contents; each call clears what must start
+ * at zero.  Calls whose GPU work overlaps (unordered streams) race on it;
+ * calls ordered on one stream do not.  Runs on the instance's stream and
+ * waits for it. */
 ep_status ep_residual_norm_noalloc(const ep_instance* inst, double* relres_out);
 
 /* Self-test of the persistent solver's bounded waits (no instance needed):

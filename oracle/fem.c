@@ -331,6 +331,8 @@ void or_csr_free(or_csr* A) {
 
 void or_csr_apply(const or_csr* A, double cm, double ck, const double* x,
                   double* y) {
+    /* rows are independent: threads split them, each row summed in order */
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < A->n; ++i) {
         double acc = 0.0;
         for (int64_t p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p)
@@ -339,9 +341,23 @@ void or_csr_apply(const or_csr* A, double cm, double ck, const double* x,
     }
 }
 
+/* Dot product in a fixed order that does not depend on the thread count:
+ * chunks of OR_DOT_CHUNK consecutive terms are summed in index order, then
+ * the chunk sums in chunk order.  One thread or many give the same bits. */
+#define OR_DOT_CHUNK 8192
 static double dot(int64_t n, const double* a, const double* b) {
+    const int64_t nc = (n + OR_DOT_CHUNK - 1) / OR_DOT_CHUNK;
+    double* part = malloc(sizeof(double) * (size_t)(nc > 0 ? nc : 1));
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < nc; ++c) {
+        const int64_t lo = c * OR_DOT_CHUNK, hi = lo + OR_DOT_CHUNK < n ? lo + OR_DOT_CHUNK : n;
+        double s = 0.0;
+        for (int64_t i = lo; i < hi; ++i) s += a[i] * b[i];
+        part[c] = s;
+    }
     double s = 0.0;
-    for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+    for (int64_t c = 0; c < nc; ++c) s += part[c];
+    free(part);
     return s;
 }
 
@@ -360,6 +376,7 @@ int or_pcg(const or_csr* A, double cm, double ck, const double* b, double* x,
         dinv[i] = 1.0 / d;
     }
     or_csr_apply(A, cm, ck, x, q);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         r[i] = b[i] - q[i];
         z[i] = dinv[i] * r[i];
@@ -380,6 +397,7 @@ int or_pcg(const or_csr* A, double cm, double ck, const double* b, double* x,
         if (it >= maxit) { it = -1; break; }
         or_csr_apply(A, cm, ck, p, q);
         const double alpha = rz / dot(n, p, q);
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) {
             x[i] += alpha * p[i];
             r[i] -= alpha * q[i];
@@ -388,6 +406,7 @@ int or_pcg(const or_csr* A, double cm, double ck, const double* b, double* x,
         const double rz_new = dot(n, r, z);
         const double beta = rz_new / rz;
         rz = rz_new;
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
         rnorm = sqrt(dot(n, r, r));
         ++it;

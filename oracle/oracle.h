@@ -210,6 +210,12 @@ void or_sim_set_activation(or_sim* S, const double* at, const double* best);
 void or_sim_get_iion(const or_sim* S, double* iion);
 const or_csr* or_sim_matrix(const or_sim* S);
 
+/* Threads of the oracle's parallel loops (OpenMP when built with it, else
+ * 1): nodes of the ionic step and rows of the matrix products split among
+ * threads; dot products summed in fixed chunks, so the result does not depend
+ * on the thread count.  n <= 0 queries.  Returns the count in effect. */
+int or_set_threads(int n);
+
 #ifdef __cplusplus
 }
 #endif

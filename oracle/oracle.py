@@ -21,6 +21,8 @@ def lib():
         path = _build.build()
         L = C.CDLL(path)
         d, i64, i32, vp = C.c_double, C.c_int64, C.c_int, C.c_void_p
+        L.or_set_threads.argtypes = [i32]
+        L.or_set_threads.restype = i32
         L.or_model_nstates.argtypes = [i32]
         L.or_model_nstates.restype = i32
         L.or_model_initial.argtypes = [i32, i32, vp, vp]
@@ -78,6 +80,13 @@ def lib():
 
 BO, TTP06, PASSIVE = 0, 1, 2
 ENDO, MID, EPI = 0, 1, 2
+
+
+def set_threads(n=0):
+    """Threads of the oracle's parallel loops (n <= 0: query); returns the
+    count in effect (1 when the library was built without OpenMP).  Results
+    do not depend on it."""
+    return int(lib().or_set_threads(int(n)))
 
 
 def _p(a):

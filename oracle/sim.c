@@ -195,7 +195,9 @@ static int step_once(or_sim* S) {
     for (int p = 0; p < S->npulses; ++p)
         amp_now[p] = pulse_active(&S->pulses[p], dt, m) ? S->pulses[p].amp : 0.0;
 
-    /* 1-2: ionic states and current at every node (Eq. (4), ICI) */
+    /* 1-2: ionic states and current at every node (Eq. (4), ICI); nodes are
+     * independent, threads split them */
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i) {
         double uB, uE, wB[OR_MAX_STATES], wE[OR_MAX_STATES], a[OR_MAX_STATES], b[OR_MAX_STATES], wn[OR_MAX_STATES];
         const double un = S->u_n[i], unm1 = S->u_nm1[i], unm2 = S->u_nm2[i];
@@ -255,9 +257,10 @@ static int step_once(or_sim* S) {
 
     /* 4: activation, non-finite check, rotation */
     int bad = 0;
+#pragma omp parallel for schedule(static) reduction(|| : bad)
     for (int64_t i = 0; i < N; ++i) {
         const double sl = S->u_new[i] - S->u_n[i];
-        if (!isfinite(S->u_new[i])) bad = 1;
+        bad = bad || !isfinite(S->u_new[i]);
         if (sl > S->best[i]) {
             S->best[i] = sl;
             S->at[i] = t_new;
@@ -360,4 +363,20 @@ void or_sim_set_activation(or_sim* S, const double* at, const double* best) {
 
 void or_sim_get_iion(const or_sim* S, double* iion) {
     memcpy(iion, S->iion, sizeof(double) * (size_t)S->nn);
+}
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the parallel loops (1 without OpenMP); n <= 0 keeps the
+ * current setting.  Returns the number in effect. */
+int or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

@@ -79,6 +79,10 @@ struct ep_instance {
     std::vector<void*> allocs;
     size_t bytes = 0;
     long long host_step = 0;   // step index of the next enqueued step
+    // a linear solve ran since ep_create or the last ep_load_state, so b, the
+    // operator and the iterate describe one solve (the allocation-free
+    // residual check needs that)
+    bool solved = false;
     // refined path: a step ran whose per-node end (k_finish_ff's work) waits
     // for the next step's ionic kernel; reads of the state do it first
     mutable bool fin_pending = false;
@@ -1416,6 +1420,7 @@ ep_status ep_step_async(ep_instance* I, int64_t n_steps) {
         }
         I->host_step += 1;
         I->fin_pending = I->h.prec == EP_PREC_FP32_REFINED;
+        I->solved = true;
     }
     CUDA_TRY(cudaGetLastError());
     return EP_OK;
@@ -1474,6 +1479,7 @@ ep_status ep_step_batch(ep_instance* const* insts, int32_t n, int64_t n_steps) {
             for (int32_t k = 0; k < n; ++k) {
                 insts[k]->host_step += 1;
                 insts[k]->fin_pending = insts[k]->h.prec == EP_PREC_FP32_REFINED;
+                insts[k]->solved = true;
             }
         }
         CUDA_TRY(cudaStreamSynchronize(P->stream));
@@ -1751,6 +1757,9 @@ ep_status ep_load_state(ep_instance* I, const void* buf, size_t bytes) {
     CUDA_TRY(cudaMemset(t.counter, 0, epk::CNT_N * sizeof(unsigned int)));
     I->host_step = step;
     I->sticky = EP_OK;
+    // the right-hand side and the A u of the last solve no longer match the
+    // loaded potential
+    I->solved = false;
     // the operators for the loaded step's BDF order now, so that the restored
     // A u history stays valid for the next step
     ensure_alpha(I);
@@ -1863,9 +1872,13 @@ ep_status ep_residual_norm_noalloc(const ep_instance* I, double* relres_out) {
         return fail(EP_EINVAL, "the residual of this instance needs " + std::to_string(I->grid_pcg) +
                                    " thread blocks; the allocation-free path holds partial sums for at most " +
                                    std::to_string(epk::noalloc_max_blocks()));
+    if (!I->solved)
+        return fail(EP_EINVAL, "no linear solve since the instance was created or its state loaded");
     double sums[2] = {0.0, 0.0};
     CUDA_TRY(epk::residual_norm_noalloc(I->d, I->grid_pcg, I->stream, sums));
-    *relres_out = sums[0] > 0.0 ? std::sqrt(sums[1] / sums[0]) : std::sqrt(sums[1]);
+    if (!(sums[0] > 0.0))
+        return fail(EP_EINVAL, "the last solve's right-hand side is zero: no relative residual");
+    *relres_out = std::sqrt(sums[1] / sums[0]);
     return EP_OK;
 }
 

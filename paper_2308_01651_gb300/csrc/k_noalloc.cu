@@ -3,12 +3,13 @@
 // float-float iterate, whose sum rounded to double is u_n), computed without
 // allocating anything.
 //
-// Who needs it: code that must not call cudaMalloc at the point where it
-// wants the number -- for example while a CUDA stream is being captured into
-// a graph, inside a host callback or a plugin whose memory is owned by
-// another allocator, or in a process that pre-reserves all device memory at
-// start-up.  Everything this call touches is either the instance's existing
-// memory (read only) or the fixed scratch array below.
+// Who needs it: host code that cannot call cudaMalloc at the point where it
+// wants the number -- for example an application whose device memory is owned
+// by another allocator (a framework's caching allocator, or a pool that
+// reserves the GPU's memory at start-up), where an allocation here would fail
+// or break the owner's accounting.  Everything this call touches is either
+// the instance's existing memory (read only) or the fixed scratch array
+// below.
 //
 // Scratch: g_noalloc_scratch, a file-scope __device__ array of
 // kNoAllocScratchBytes (about 16 KiB) that every GPU loading this library
@@ -17,8 +18,7 @@
 // arrival counter of the last-block reduction.  Host code cannot use the
 // array's name as a device address; at set-up, once per device and with that
 // device current, the address is taken with cudaGetSymbolAddress and passed
-// to the kernel.  The first call on each device does that set-up, so make
-// the first call before any stream capture on that device.  Every call
+// to the kernel; the first call on each device does that set-up.  Every call
 // shares the array and it keeps the last call's contents: each call clears
 // the counter before its kernel runs, and calls whose work overlaps on the
 // GPU (different streams, no ordering) race on the array.

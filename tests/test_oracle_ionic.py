@@ -150,3 +150,25 @@ def test_bo_excitation_threshold():
     for u0 in (0.10, 0.30):
         quiet = run_cell(O.BO, O.EPI, 0.01, 100.0, 0.0, 0.0, u0=u0)
         assert quiet.max() <= u0 and 0.0 < quiet[-1] < 0.006
+
+
+# The fast TTP06 gates of the paper's epicardial initial state (Sec. 3.2.1)
+# are at their voltage steady states: with time constants of 0.001-9 ms at
+# -85.23 mV they have relaxed long before any state is recorded.  So the
+# oracle's steady-state value a/b of each of them at the printed potential
+# must reproduce the printed value to its last digit (one unit of it).  h
+# (tau 8 ms) and j (76 ms) are still recovering from the last beat and are
+# left out, like the slow gates and the concentrations.
+FAST_GATES_LAST_DIGIT = {"m": 1e-5, "xr2": 1e-4, "s": 1e-6, "r": 1e-10, "d": 1e-8}
+
+
+def test_ttp06_fast_gates_of_the_papers_initial_state_are_steady():
+    from .helpers import golden
+    g = golden("ttp06_epi_initial_state.json")
+    order = g["state_order"]
+    w = np.array([g["states"][k] for k in order])
+    a, b = O.rates(O.TTP06, g["V_mV"], w, cell=O.EPI)
+    for name, unit in FAST_GATES_LAST_DIGIT.items():
+        k = order.index(name)
+        assert 1.0 / b[k] < 10.0, name  # a fast gate: time constant below 10 ms
+        assert abs(a[k] / b[k] - g["states"][name]) <= unit, (name, a[k] / b[k], g["states"][name])

@@ -321,6 +321,27 @@ int or_assemble_q2(int64_t nn, int64_t ne, const double* xyz, const int32_t* hex
     return assemble_general(27, nn, ne, xyz, hex27, f0, s0, NULL, 1, rdiff, excluded, A, NULL);
 }
 
+void or_element_region_vector(int64_t nn, int64_t ne, const double* xyz,
+                              const int32_t* hex, const uint8_t* elem,
+                              double* out) {
+    /* fibres do not enter the mass matrix: any unit vectors do */
+    static const double fz[24] = {1, 0, 0, 1, 0, 0, 1, 0, 0, 1, 0, 0, 1, 0, 0, 1, 0, 0, 1, 0, 0, 1, 0, 0};
+    static const double sz[24] = {0, 1, 0, 0, 1, 0, 0, 1, 0, 0, 1, 0, 0, 1, 0, 0, 1, 0, 0, 1, 0, 0, 1, 0};
+    for (int64_t j = 0; j < nn; ++j) out[j] = 0.0;
+    for (int64_t e = 0; e < ne; ++e) {
+        if (!elem[e]) continue;
+        double X[24], Me[64], Ke[64];
+        for (int a = 0; a < 8; ++a)
+            for (int c = 0; c < 3; ++c) X[3 * a + c] = xyz[3 * (size_t)hex[8 * e + a] + c];
+        or_element_matrices(X, fz, sz, 1.0, 1.0, 1.0, Me, Ke);
+        for (int a = 0; a < 8; ++a) {
+            double row = 0.0;
+            for (int b = 0; b < 8; ++b) row += Me[8 * a + b];
+            out[hex[8 * e + a]] += row;
+        }
+    }
+}
+
 void or_csr_free(or_csr* A) {
     free(A->rowptr);
     free(A->col);

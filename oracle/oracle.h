@@ -127,6 +127,16 @@ void or_csr_free(or_csr* A);
 void or_csr_apply(const or_csr* A, double cm, double ck, const double* x,
                   double* y);
 
+/* The vector of an applied current that is amp = 1 on a region of whole Q1
+ * elements and 0 elsewhere, integrated against every basis function with the
+ * 2x2x2 Gauss rule (Sec. 1.2: the vector arising from the applied current):
+ * out[j] = sum over elements e with elem[e] != 0 of int_e phi_j, which is the
+ * row sum of each such element's mass matrix (the basis sums to 1).  out has
+ * nn entries and is overwritten. */
+void or_element_region_vector(int64_t nn, int64_t ne, const double* xyz,
+                              const int32_t* hex, const uint8_t* elem,
+                              double* out);
+
 /* Jacobi-PCG on (cm M + ck K) x = b; x holds the initial guess.  Returns the
  * iteration count, or -1 when maxit is reached. */
 int or_pcg(const or_csr* A, double cm, double ck, const double* b, double* x,
@@ -179,6 +189,12 @@ or_sim* or_sim_create_q2(int64_t nn, int64_t ne, const double* xyz,
  * the node receives amp * weight[node] instead of amp * (mask[node] != 0).
  * NULL restores the mask.  The array is copied. */
 void or_sim_set_pulse_weights(or_sim* S, int p, const double* weight);
+/* Pulse p as an applied current on a region of elements (Gauss-point
+ * integration, see or_element_region_vector): vec (nn doubles) is that
+ * region's vector; the step adds amp(t) * vec to the right-hand side of
+ * Eq. (6) after the mass product and the pulse's nodal mask is ignored.
+ * NULL restores the nodal pulse. */
+void or_sim_set_pulse_region(or_sim* S, int p, const double* vec);
 /* 1 for an active node, 0 for an inactive one. */
 void or_sim_get_active(const or_sim* S, uint8_t* active);
 void or_sim_destroy(or_sim* S);

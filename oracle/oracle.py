@@ -46,6 +46,8 @@ def lib():
         L.or_sim_create_regions.restype = vp
         L.or_sim_get_active.argtypes = [vp, vp]
         L.or_sim_set_pulse_weights.argtypes = [vp, i32, vp]
+        L.or_sim_set_pulse_region.argtypes = [vp, i32, vp]
+        L.or_element_region_vector.argtypes = [i64, i64, vp, vp, vp, vp]
         L.or_prepace.argtypes = [i32, i32, i32, d, d, i32, d, d, vp, vp]
         L.or_sim_get_level2.argtypes = [vp, vp, vp]
         L.or_sim_set_level2.argtypes = [vp, vp, vp]
@@ -132,6 +134,20 @@ def cell_step(model, order, dt, u_n, w_n, u_nm1, w_nm1, iapp, cell=EPI, g=0.0):
     return u, out[: nstates(model)]
 
 
+def element_region_vector(xyz, hex8, elem):
+    """int_e phi_j summed over the elements with elem[e] != 0, per node j
+    (or_element_region_vector): the Gauss-integrated vector of a unit applied
+    current on that region of elements."""
+    xyz = _f64(xyz).reshape(-1, 3)
+    hex8 = np.ascontiguousarray(hex8, dtype=np.int32)
+    if hex8.shape[1] != 8:
+        raise ValueError("element regions take Q1 hexahedra")
+    el = np.ascontiguousarray(elem, dtype=np.uint8).reshape(-1)
+    out = np.zeros(xyz.shape[0])
+    lib().or_element_region_vector(xyz.shape[0], hex8.shape[0], _p(xyz), _p(hex8), _p(el), _p(out))
+    return out
+
+
 def element_matrices(X, f, s, dl, dt_, dn):
     X, f, s = _f64(X).reshape(8, 3), _f64(f).reshape(8, 3), _f64(s).reshape(8, 3)
     Me = np.zeros((8, 8))
@@ -208,7 +224,10 @@ class Sim:
         if not self.h:
             raise ValueError("or_sim_create failed")
         for k, p in enumerate(pulses):
-            if p.get("weight") is not None:
+            if p.get("elem") is not None:
+                v = element_region_vector(self.xyz, self.hex, p["elem"])
+                lib().or_sim_set_pulse_region(self.h, k, _p(v))
+            elif p.get("weight") is not None:
                 w = _f64(p["weight"])
                 lib().or_sim_set_pulse_weights(self.h, k, _p(w))
         self.nn = nn

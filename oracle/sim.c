@@ -47,6 +47,7 @@ struct or_sim {
     double last_relres;
     uint8_t* active;  /* 0: inactive node (no element left after exclusions) */
     double* weight[OR_MAX_PULSES];  /* per-node pulse profiles (NULL: mask) */
+    double* region[OR_MAX_PULSES];  /* element-region vectors (NULL: nodal pulse) */
 };
 
 or_sim* or_sim_create(int64_t nn, int64_t ne, const double* xyz,
@@ -166,7 +167,10 @@ void or_sim_destroy(or_sim* S) {
     free(S->iion); free(S->rhs); free(S->tmp);
     free(S->at); free(S->best); free(S->masks); free(S->iapp_extra);
     free(S->active);
-    for (int p = 0; p < OR_MAX_PULSES; ++p) free(S->weight[p]);
+    for (int p = 0; p < OR_MAX_PULSES; ++p) {
+        free(S->weight[p]);
+        free(S->region[p]);
+    }
     free(S);
 }
 
@@ -241,6 +245,7 @@ static int step_once(or_sim* S) {
         S->iion[i] = I;
         double iapp = S->have_extra ? S->iapp_extra[i] : 0.0;
         for (int p = 0; p < S->npulses; ++p) {
+            if (S->region[p]) continue;  /* added to the right-hand side below */
             if (S->weight[p]) iapp += amp_now[p] * S->weight[p][i];
             else if (S->masks[(size_t)p * N + i]) iapp += amp_now[p];
         }
@@ -250,8 +255,12 @@ static int step_once(or_sim* S) {
     }
     S->have_extra = 0;
 
-    /* 3: linear system, Eq. (6) */
+    /* 3: linear system, Eq. (6); applied currents on element regions enter
+     * as their Gauss-integrated vectors */
     or_csr_apply(&S->A, 1.0, 0.0, S->tmp, S->rhs);
+    for (int p = 0; p < S->npulses; ++p)
+        if (S->region[p] && amp_now[p] != 0.0)
+            for (int64_t i = 0; i < N; ++i) S->rhs[i] += amp_now[p] * S->region[p][i];
     const int it = or_pcg(&S->A, alpha / dt, 1.0, S->rhs, S->u_new, S->tol, S->maxit, &S->last_relres);
     S->last_iters = it;
 
@@ -302,6 +311,15 @@ void or_sim_set_pulse_weights(or_sim* S, int p, const double* weight) {
     if (weight) {
         S->weight[p] = malloc((size_t)S->nn * sizeof(double));
         memcpy(S->weight[p], weight, (size_t)S->nn * sizeof(double));
+    }
+}
+void or_sim_set_pulse_region(or_sim* S, int p, const double* vec) {
+    if (p < 0 || p >= OR_MAX_PULSES) return;
+    free(S->region[p]);
+    S->region[p] = NULL;
+    if (vec) {
+        S->region[p] = malloc((size_t)S->nn * sizeof(double));
+        memcpy(S->region[p], vec, (size_t)S->nn * sizeof(double));
     }
 }
 int or_sim_nstates(const or_sim* S) { return S->ns; }

@@ -173,6 +173,15 @@ typedef struct {
     double amp, t0, dur, period;
     const uint8_t* mask;
     const double* weight;
+    /* Optional region of whole elements (n_elems bytes, element numbering of
+     * ep_mesh.region; Q1 meshes): I_app = amp on the elements where
+     * elem[e] != 0 and 0 elsewhere, entering Eq. (6) as the applied-current
+     * vector integrated by the 2x2x2 Gauss rule, f_j = amp * sum over those
+     * elements of int_e phi_j -- the quadrature evaluation of a current given
+     * as a function of space, such as the paper's cubic impulse (Sec. 3.2.1)
+     * -- instead of the nodal values times the mass matrix; mask and weight
+     * are then ignored.  NULL: the nodal pulse above. */
+    const uint8_t* elem;
 } ep_pulse;
 
 typedef struct {
@@ -210,7 +219,9 @@ typedef struct {
     int32_t sweeps;         /* refinement sweeps (0 for FP64) */
     double relres;          /* final ||b - A u|| / ||b|| (FP64) */
     int32_t op32;           /* FP32 operator in use (EP_OP_*) */
-    int32_t reserved;
+    int32_t solve_per_sm;   /* resident 512-thread blocks per SM of the persistent
+                               solve (stencil operator: 1 while its working set fits
+                               in L2, else 2), 0 for other operators */
     size_t device_bytes;    /* device memory held by the instance */
     double tune_us_mf;      /* autotuner: matrix-free apply time (us), 0 if not timed */
     double tune_us_stencil; /* autotuner: FP32 stencil apply time (us), 0 if not timed */

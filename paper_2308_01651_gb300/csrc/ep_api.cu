@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "ep_dev.cuh"
 #include "ionic_models.cuh"
 #include "ep_tile.cuh"
@@ -45,8 +47,14 @@ cudaError_t launch_prepace(int model, const uint8_t* cells, int ncell, double dt
 void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s);
 int mf_tiles(const Dev& h);
 cudaError_t mf_prepare();
+bool mfc_supported(int NX);
+size_t mfc_geo_floats(int NX, int NY, int NZ);
+void mfc_fill_geo(float* g, int NX, int NY, int NZ, const double* xyz, const double* f0, const double* s0);
+cudaError_t mfc_tensor_map(CUtensorMap* tm, const float* g, int NX, int NY, int NZ);
+cudaError_t mfc_prepare(int NX);
+void launch_apply32_mfc(Dev* d, const Dev& h, const CUtensorMap& tm, cudaStream_t s);
 int pcg_blocks_per_sm(int batched);
-cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, cudaStream_t s);
+cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, int per_sm, cudaStream_t s);
 cudaError_t barrier_timeout_probe(int* status_out);
 cudaError_t residual_norm_noalloc(Dev* d, int grid, cudaStream_t s, double sums[2]);
 int noalloc_max_blocks();
@@ -92,10 +100,15 @@ struct ep_instance {
     int grid_resid = 0;        // node-parallel residual: 512-thread blocks, two per SM
     int grid_tiles = 0;        // persistent grid of the tiled stencil kernels
     int grid_pcg = 0;          // cooperative grid of the persistent inner solver
+    int pcg_per_sm = 1;        // its resident 512-thread blocks per SM (1 or 2)
     ep_status sticky = EP_OK;
     int* bad = nullptr;        // device flag of the assembly
     bool graph_mode = true;    // false: host-driven loops (EP_GRAPH=0), for debugging
     float tune_ms[3] = {0.f, 0.f, 0.f};  // autotuned FP32 operator apply times (ms)
+    // matrix-free FP32 operator of curved (shell) meshes: the staged
+    // geometry array and its TMA tensor map
+    float* mfc_geo = nullptr;
+    CUtensorMap mfc_tm;
     // per-kernel event timing (ep_profile_enable)
     bool profiling = false;
     struct Pending { int id; cudaEvent_t a, b; };
@@ -194,6 +207,17 @@ ep_status dalloc_padded(ep_instance* I, float** p, size_t N, int64_t pad) {
     return EP_OK;
 }
 
+// A zeroed device array of count floats.
+ep_status dalloc_zero(ep_instance* I, float** p, size_t count) {
+    const ep_status st = dalloc(I, p, count);
+    if (st != EP_OK) return st;
+    if (cudaMemsetAsync(*p, 0, count * sizeof(float), I->stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(EP_ECUDA, "cudaMemsetAsync of a coupling array failed");
+    }
+    return EP_OK;
+}
+
 // Frees one allocation of dalloc before ep_destroy.
 template <typename T>
 void dfree(ep_instance* I, T*& p, size_t count) {
@@ -211,12 +235,15 @@ void dfree(ep_instance* I, T*& p, size_t count) {
 struct Sizes {
     int N, ns, ng32, ns64, prec, op32;
     bool slab;
+    bool shell;
     bool regions;     // the mesh carries subdomain labels
     bool slab_mass;   // the refined path applies the analytic slab mass matrix
     int levels;       // time levels kept: 3 for BDF3, else 2
     bool q2;          // triquadratic slab
     int64_t ne;       // elements (Q2)
     int64_t npad;     // zero nodes before and after the inner solver's u (Q1 slab)
+    int64_t cs;       // slot stride of the refined couplings (floats): N, then zeros
+    int NX, NY, NZ;   // nodes per direction (Q1)
 };
 
 // float-float pair (nearest float, then the nearest float of the rest)
@@ -269,13 +296,16 @@ size_t footprint(const Sizes& z) {
             b += 4 * al(8 * N * 4);       // element outputs of A u and M v (hi, lo) in node slots
             b += 2 * al(N * 8);           // diagonals of M and K
         } else {
-            b += 2 * al(epk::kGroups * N * 16);                          // Ahi Alo
-            if (!z.slab_mass) b += 2 * al(epk::kGroups * N * 16);        // Mhi Mlo (curved / with regions)
+            const size_t cb = (size_t)epk::kSlots * (size_t)z.cs * 4;
+            b += 2 * al(cb);                         // Ahi Alo (symmetric float-float stencil)
+            if (!z.slab_mass) b += 2 * al(cb);       // Mhi Mlo (curved / with regions)
         }
         b += 6 * al(N * 4);                                              // u, v, b (hi, lo)
         b += (2 + 2 * L) * al(N * 4);                                    // A u history (hi, lo)
         b += (1 + 2 * L) * al(N * 4);                                    // u levels (hi, lo), best slope
-        if (z.op32 != EP_OP_STENCIL && !z.q2) b += al(6 * N * 4);       // fibres
+        if (z.op32 != EP_OP_STENCIL && z.slab) b += al(6 * N * 4);      // fibres (slab matrix-free)
+        if (z.op32 != EP_OP_STENCIL && z.shell)                          // staged geometry (shell matrix-free)
+            b += al(epk::mfc_geo_floats(z.NX, z.NY, z.NZ) * 4);
         b += 5 * al(N * 4) + al((N + 2 * (size_t)z.npad) * 4);  // r32 q32 d32 pa32 pb32, z32 (padded)
         if (!z.q2) b += al(N);            // boundary flags
     } else {
@@ -325,7 +355,10 @@ ep_status validate(const ep_mesh* mesh, const ep_fibers* fib, const ep_conductiv
         if (stim->n_pulses > 0 && !stim->pulses) return fail(EP_EINVAL, "stimulus.pulses is NULL");
         for (int p = 0; p < stim->n_pulses; ++p) {
             const ep_pulse& P = stim->pulses[p];
-            if (!P.mask && !P.weight) return fail(EP_EINVAL, "a pulse needs a mask or a weight");
+            if (!P.mask && !P.weight && !P.elem)
+                return fail(EP_EINVAL, "a pulse needs a mask, a weight or an element region");
+            if (P.elem && mesh->kind == EP_MESH_SLAB_Q2)
+                return fail(EP_EUNSUPPORTED, "pulses on element regions take Q1 meshes");
             if (P.weight)
                 for (int64_t i = 0; i < nn; ++i)
                     if (!std::isfinite(P.weight[i])) return fail(EP_EINVAL, "pulse weights must be finite");
@@ -338,8 +371,8 @@ ep_status validate(const ep_mesh* mesh, const ep_fibers* fib, const ep_conductiv
     if (opts->precision != EP_PREC_FP64 && opts->precision != EP_PREC_FP32_REFINED)
         return fail(EP_EINVAL, "options.precision");
     if (opts->op32 < EP_OP_AUTO || opts->op32 > EP_OP_STENCIL) return fail(EP_EINVAL, "options.op32");
-    if (opts->op32 == EP_OP_MATRIX_FREE && mesh->kind == EP_MESH_SHELL)
-        return fail(EP_EUNSUPPORTED, "the matrix-free FP32 operator needs a slab mesh");
+    if (opts->op32 == EP_OP_MATRIX_FREE && mesh->kind == EP_MESH_SHELL && !epk::mfc_supported(mesh->nx + 1))
+        return fail(EP_EUNSUPPORTED, "the matrix-free FP32 operator takes shells at most 31 elements across the wall");
     if (mesh->kind == EP_MESH_SLAB_Q2) {
         if (opts->precision != EP_PREC_FP32_REFINED)
             return fail(EP_EUNSUPPORTED, "Q2 meshes need FP32_REFINED precision");
@@ -364,6 +397,59 @@ ep_status validate(const ep_mesh* mesh, const ep_fibers* fib, const ep_conductiv
     return EP_OK;
 }
 
+// The applied-current vector of a unit current on a region of Q1 elements,
+// g_j = sum over the region's elements of int_e phi_j (Eq. (6), the vector
+// arising from I_app), by the 2x2x2 Gauss rule on each element's trilinear
+// map: on a box element every corner gets |e| / 8; on a curved one
+// sum_q (1/8) det J(q) phi_a(q).  In double, once per instance.
+std::vector<double> region_vector(const ep_mesh* mesh, const Dev& h, const uint8_t* elem) {
+    std::vector<double> g((size_t)h.N, 0.0);
+    const int nx = mesh->nx, ny = mesh->ny, nz = mesh->nz;
+    const double gp[2] = {0.5 - 0.5 / std::sqrt(3.0), 0.5 + 0.5 / std::sqrt(3.0)};
+    const bool shell = mesh->kind == EP_MESH_SHELL;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                if (!elem[(size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k)]) continue;
+                size_t node[8];
+                double X[8][3];
+                for (int a = 0; a < 8; ++a) {
+                    const int ii = i + (a & 1), kk = k + (a >> 2);
+                    int jj = j + ((a >> 1) & 1);
+                    if (shell && jj == h.NY) jj = 0;
+                    node[a] = (size_t)ii + (size_t)h.NX * ((size_t)jj + (size_t)h.NY * kk);
+                    for (int c = 0; c < 3; ++c) X[a][c] = shell ? mesh->xyz[3 * node[a] + c] : 0.0;
+                }
+                if (!shell) {
+                    const double q = h.h[0] * h.h[1] * h.h[2] / 8.0;
+                    for (int a = 0; a < 8; ++a) g[node[a]] += q;
+                    continue;
+                }
+                for (int q = 0; q < 8; ++q) {
+                    const double xi[3] = {gp[q & 1], gp[(q >> 1) & 1], gp[q >> 2]};
+                    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, phi[8];
+                    for (int a = 0; a < 8; ++a) {
+                        const int b0 = a & 1, b1 = (a >> 1) & 1, b2 = a >> 2;
+                        const double l0 = b0 ? xi[0] : 1.0 - xi[0], l1 = b1 ? xi[1] : 1.0 - xi[1],
+                                     l2 = b2 ? xi[2] : 1.0 - xi[2];
+                        const double d0 = (b0 ? 1.0 : -1.0) * l1 * l2, d1 = l0 * (b1 ? 1.0 : -1.0) * l2,
+                                     d2 = l0 * l1 * (b2 ? 1.0 : -1.0);
+                        phi[a] = l0 * l1 * l2;
+                        for (int c = 0; c < 3; ++c) {
+                            J[c][0] += X[a][c] * d0;
+                            J[c][1] += X[a][c] * d1;
+                            J[c][2] += X[a][c] * d2;
+                        }
+                    }
+                    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+                    for (int a = 0; a < 8; ++a) g[node[a]] += 0.125 * std::fabs(det) * phi[a];
+                }
+            }
+    return g;
+}
+
 Sizes sizes_of(const ep_mesh* mesh, const ep_ionic_model* ionic, const ep_options* opts) {
     Sizes z{};
     z.N = (int)expected_nodes(mesh);
@@ -377,12 +463,27 @@ Sizes sizes_of(const ep_mesh* mesh, const ep_ionic_model* ionic, const ep_option
     // either way; rounded up to 64 floats, so that the vectors keep the
     // 256-byte alignment of every allocation (16-byte vector accesses)
     z.npad = z.slab ? ((int64_t)(mesh->nx + 1) * (mesh->ny + 1) + (mesh->nx + 1) + 1 + 63) / 64 * 64 : 0;
+    {
+        // symmetric float couplings: each slot followed by at least the
+        // largest backward offset in zeros, rounded up to 64 floats
+        const int64_t NX = mesh->nx + 1, NY = mesh->kind == EP_MESH_SHELL ? mesh->ny : mesh->ny + 1;
+        const int64_t back = 1 + NX + NX * NY;
+        z.cs = ((int64_t)z.N + back + 63) / 64 * 64;
+        z.NX = (int)NX;
+        z.NY = (int)NY;
+        z.NZ = mesh->nz + 1;
+    }
     z.regions = mesh->region != nullptr;
     // an excluded region changes M; the footprint assumes it may
     z.slab_mass = z.slab && !z.regions;
-    // AUTO on a slab keeps both FP32 operators and lets the create-time
-    // autotuner pick; the matrix-free apply needs an axis-aligned slab
-    z.op32 = opts->op32 == EP_OP_AUTO ? ((z.slab && !z.regions) ? EP_OP_AUTO : EP_OP_STENCIL) : opts->op32;
+    z.shell = mesh->kind == EP_MESH_SHELL;
+    {
+        // AUTO keeps both FP32 operators where the matrix-free one applies
+        // (axis-aligned slabs; shells up to 31 elements across the wall), one
+        // region only, and lets the create-time autotuner pick
+        const bool mf_ok = !z.regions && (z.slab || (z.shell && epk::mfc_supported(mesh->nx + 1)));
+        z.op32 = opts->op32 == EP_OP_AUTO ? (mf_ok ? EP_OP_AUTO : EP_OP_STENCIL) : opts->op32;
+    }
     if (z.q2) z.op32 = kOpQ2;
     if (z.prec == EP_PREC_FP32_REFINED) {
         z.ng32 = ionic->model == EP_MODEL_BO ? epk::kBOStates : epk::kTTGates;
@@ -418,7 +519,8 @@ void ensure_alpha(ep_instance* I) {
     if (need < I->alpha_dt_dev) path[np++] = need;
     for (int k = 0; k < np; ++k) {
         const double to = path[k];
-        const float cmass = (float)(to * I->h.h[0] * I->h.h[1] * I->h.h[2]);
+        const float cmass =
+            (float)(I->h.kind == EP_MESH_SHELL ? to : to * I->h.h[0] * I->h.h[1] * I->h.h[2]);
         const double delta = to - I->alpha_dt_dev;
         timed(I, K_REALPHA, [&] {
             if (I->h.q2) epk::launch_realpha_q2(I->d, I->h, to, I->stream);
@@ -439,6 +541,13 @@ struct Capture {
         if (err == cudaSuccess && e != cudaSuccess) err = e;
     }
 };
+
+// The matrix-free FP32 apply of the instance's mesh: the slab kernel
+// (constant Jacobian) or the curved one (TMA-staged geometry).
+void launch_apply32_free(ep_instance* I, cudaStream_t s) {
+    if (I->mfc_geo) epk::launch_apply32_mfc(I->d, I->h, I->mfc_tm, s);
+    else epk::launch_apply32_mf(I->d, I->h, s);
+}
 
 // Adds a WHILE node at the current capture position of stream s, returns its
 // handle and body graph, and moves s past the node.
@@ -492,7 +601,7 @@ ep_status build_graph(ep_instance* I) {
         // every refinement sweep [inner PCG, u += delta, float-float residual,
         // decision] in one persistent launch (it returns at once when the
         // first residual met the tolerance)
-        C.chk(epk::launch_pcg32(I->d, h, I->grid_pcg, s));
+        C.chk(epk::launch_pcg32(I->d, h, I->grid_pcg, I->pcg_per_sm, s));
     } else {
         C.chk(add_while(s, &h_outer, &body));
         if (C.err == cudaSuccess) {
@@ -501,7 +610,7 @@ ep_status build_graph(ep_instance* I) {
             if (C.err == cudaSuccess) {
                 C.chk(cudaStreamBeginCaptureToGraph(s3, body2, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
                 if (h.q2) epk::launch_q2_apply32(I->d, h, I->grid_nodes, s3);
-                else if (h.op32 == EP_OP_MATRIX_FREE) epk::launch_apply32_mf(I->d, h, s3);
+                else if (h.op32 == EP_OP_MATRIX_FREE) launch_apply32_free(I, s3);
                 else epk::launch_apply32_stencil(I->d, h, I->grid_tiles, s3);
                 epk::launch_update32(I->d, h, I->grid_nodes, 1, s3);
                 C.chk(cudaStreamEndCapture(s3, &body2));
@@ -572,7 +681,7 @@ ep_status step_host(ep_instance* I) {
         if (h.op32 == EP_OP_STENCIL) {
             // the whole solve in one persistent launch
             cudaError_t pe = cudaSuccess;
-            timed(I, K_PCG32, [&] { pe = epk::launch_pcg32(d, h, I->grid_pcg, s); });
+            timed(I, K_PCG32, [&] { pe = epk::launch_pcg32(d, h, I->grid_pcg, I->pcg_per_sm, s); });
             CUDA_TRY(pe);
             f = 0;
         }
@@ -582,7 +691,7 @@ ep_status step_host(ep_instance* I) {
                 if (h.q2)
                     timed(I, K_APPLY32Q2, [&] { epk::launch_q2_apply32(d, h, I->grid_nodes, s); });
                 else if (h.op32 == EP_OP_MATRIX_FREE)
-                    timed(I, K_APPLY32MF, [&] { epk::launch_apply32_mf(d, h, s); });
+                    timed(I, K_APPLY32MF, [&] { launch_apply32_free(I, s); });
                 else
                     timed(I, K_APPLY32ST, [&] { epk::launch_apply32_stencil(d, h, I->grid_tiles, s); });
                 timed(I, K_UPDATE32, [&] { epk::launch_update32(d, h, I->grid_nodes, 0, s); });
@@ -622,7 +731,7 @@ ep_status autotune_op32(ep_instance* I) {
     int best = EP_OP_STENCIL;
     for (int c : cands) {
         auto launch = [&] {
-            if (c == EP_OP_MATRIX_FREE) epk::launch_apply32_mf(I->d, h, s);
+            if (c == EP_OP_MATRIX_FREE) launch_apply32_free(I, s);
             else epk::launch_apply32_stencil(I->d, h, I->grid_tiles, s);
         };
         for (int w = 0; w < 3; ++w) launch();
@@ -854,12 +963,13 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
             ALLOC(h.q2dM, N);
             ALLOC(h.q2dK, N);
         } else {
-            ALLOC(h.Ahi, epk::kGroups * N);
-            ALLOC(h.Alo, epk::kGroups * N);
+            h.cs = z.cs;
+            if ((st = dalloc_zero(I, &h.Ahi, (size_t)epk::kSlots * z.cs)) != EP_OK) return st;
+            if ((st = dalloc_zero(I, &h.Alo, (size_t)epk::kSlots * z.cs)) != EP_OK) return st;
         }
         if (!z.slab_mass && !z.q2) {
-            ALLOC(h.Mhi, epk::kGroups * N);
-            ALLOC(h.Mlo, epk::kGroups * N);
+            if ((st = dalloc_zero(I, &h.Mhi, (size_t)epk::kSlots * z.cs)) != EP_OK) return st;
+            if ((st = dalloc_zero(I, &h.Mlo, (size_t)epk::kSlots * z.cs)) != EP_OK) return st;
         }
         ALLOC(h.uh_n, N);
         ALLOC(h.ul_n, N);
@@ -884,7 +994,8 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         ALLOC(h.v_lo, N);
         ALLOC(h.b_hi, N);
         ALLOC(h.b_lo, N);
-        if (z.op32 != EP_OP_STENCIL && !z.q2) ALLOC(h.fib, 6 * N);
+        if (z.op32 != EP_OP_STENCIL && z.slab) ALLOC(h.fib, 6 * N);
+        if (z.op32 != EP_OP_STENCIL && z.shell) ALLOC(I->mfc_geo, epk::mfc_geo_floats(z.NX, z.NY, z.NZ));
         ALLOC(h.r32, N);
         if ((st = dalloc_padded(I, &h.z32, N, z.npad)) != EP_OK) return st;
         ALLOC(h.q32, N);
@@ -916,7 +1027,26 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         if (P.mask) CUDA_TRY(cudaMemcpyAsync(m, P.mask, N, cudaMemcpyHostToDevice, I->stream));
         else CUDA_TRY(cudaMemsetAsync(m, 0, N, I->stream));
         h.mask[p] = m;
-        if (P.weight) {
+        if (P.elem) {
+            // the Gauss-integrated vector of a unit current on the region
+            const std::vector<double> g = region_vector(mesh, h, P.elem);
+            if (ref) {
+                std::vector<float> gh(N), gl(N);
+                for (size_t i = 0; i < N; ++i) split_ff(g[i], gh[i], gl[i]);
+                float *dh = nullptr, *dl = nullptr;
+                ALLOC(dh, N);
+                ALLOC(dl, N);
+                CUDA_TRY(cudaMemcpy(dh, gh.data(), N * 4, cudaMemcpyHostToDevice));
+                CUDA_TRY(cudaMemcpy(dl, gl.data(), N * 4, cudaMemcpyHostToDevice));
+                h.egh[p] = dh;
+                h.egl[p] = dl;
+            } else {
+                double* dg = nullptr;
+                ALLOC(dg, N);
+                CUDA_TRY(cudaMemcpy(dg, g.data(), N * 8, cudaMemcpyHostToDevice));
+                h.eg64[p] = dg;
+            }
+        } else if (P.weight) {
             // the profile in the path's precision
             if (ref) {
                 std::vector<float> w32(N);
@@ -1026,6 +1156,13 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         const double mw = vol / 216.0;  // slab mass weight (analytic mass matrix)
         h.mw_hi = (float)mw;
         h.mw_lo = (float)(mw - (double)h.mw_hi);
+    } else if (h.kind == EP_MESH_SHELL) {
+        // matrix-free curved apply: D = dn I + (dl-dn) f f^T + (dt-dn) s s^T,
+        // mass coefficient alpha/dt (the Jacobian is formed per point)
+        h.mf_cn[0] = h.mf_cn[1] = h.mf_cn[2] = (float)dn;
+        h.mf_cl = (float)(dl - dn);
+        h.mf_ct = (float)(dtr - dn);
+        h.mf_cmass = (float)alpha_dt;
     }
     CUDA_TRY(cudaMemcpy(I->d, &h, sizeof(Dev), cudaMemcpyHostToDevice));
     if (z.q2) {
@@ -1096,6 +1233,14 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         CUDA_TRY(cudaMemcpy(h.fib, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
         CUDA_TRY(epk::mf_prepare());
     }
+    if (I->mfc_geo) {
+        // coordinates and fibre frames for the TMA-staged curved apply
+        std::vector<float> g(epk::mfc_geo_floats(h.NX, h.NY, h.NZ));
+        epk::mfc_fill_geo(g.data(), h.NX, h.NY, h.NZ, mesh->xyz, fib->f0, fib->s0);
+        CUDA_TRY(cudaMemcpy(I->mfc_geo, g.data(), g.size() * 4, cudaMemcpyHostToDevice));
+        CUDA_TRY(epk::mfc_tensor_map(&I->mfc_tm, I->mfc_geo, h.NX, h.NY, h.NZ));
+        CUDA_TRY(epk::mfc_prepare(h.NX));
+    }
     const int blocks = (int)((N + epk::kNodeThreads - 1) / epk::kNodeThreads);
     int dev = 0, sms = 152;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -1111,7 +1256,14 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     I->grid_tiles = std::max(1, std::min(epk::st_tiles(h), 2 * sms));
     if (ref) {
         // the persistent solver's blocks must all be resident at once
-        const int occ = epk::pcg_blocks_per_sm(0);
+        // launch shape of the persistent solve: one 512-thread block per SM
+        // while its working set (the FP32 operator's 14 couplings and seven
+        // CG vectors, 84 B a node) fits in L2, two beyond it (measured: the
+        // 442k-node slab and the 2.19M-node shell, k_pcg.cu)
+        int l2 = 0;
+        CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+        I->pcg_per_sm = (double)N * 84.0 > (double)l2 ? 2 : 1;
+        const int occ = std::min(epk::pcg_blocks_per_sm(I->pcg_per_sm == 2), I->pcg_per_sm);
         if (occ <= 0) return fail(EP_ECUDA, "occupancy query of the persistent solver failed");
         const int want = (int)((N + epk::kPcgThreads - 1) / epk::kPcgThreads);
         I->grid_pcg = std::max(1, std::min(std::min(want, sms * occ), epk::kMaxPersistentBlocks));
@@ -1805,7 +1957,7 @@ ep_status ep_get_stats(const ep_instance* I, ep_stats* out) {
     out->sweeps = t.last_sweeps;
     out->relres = t.last_relres;
     out->op32 = I->h.prec == EP_PREC_FP32_REFINED ? I->h.op32 : 0;
-    out->reserved = 0;
+    out->solve_per_sm = (I->h.prec == EP_PREC_FP32_REFINED && I->h.op32 == EP_OP_STENCIL) ? I->pcg_per_sm : 0;
     out->device_bytes = I->bytes;
     out->tune_us_mf = 1e3 * I->tune_ms[EP_OP_MATRIX_FREE];
     out->tune_us_stencil = 1e3 * I->tune_ms[EP_OP_STENCIL];

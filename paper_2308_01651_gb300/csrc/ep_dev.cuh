@@ -69,6 +69,12 @@ struct Dev {
     const uint8_t* mask[EP_MAX_PULSES];
     const double* wgt64[EP_MAX_PULSES];  // pulse profiles (FP64 path; NULL: mask)
     const float* wgt32[EP_MAX_PULSES];   // pulse profiles (refined path)
+    // pulses on element regions: their Gauss-integrated vectors (per unit
+    // amplitude), added to b in the right-hand-side kernels (FP64; refined:
+    // float-float hi, lo); NULL for nodal pulses
+    const double* eg64[EP_MAX_PULSES];
+    const float* egh[EP_MAX_PULSES];
+    const float* egl[EP_MAX_PULSES];
     // ---- state ---------------------------------------------------------------
     double *u_n, *u_nm1, *u_new;
     double* u_nm2;              // level n-2 (BDF3 instances only, else NULL)
@@ -109,9 +115,15 @@ struct Dev {
     // ---- operators -----------------------------------------------------------
     double *M64, *A64;          // [kSlots][N] (symmetric, FP64)
     double *dinv64;
-    // refined path: all 27 couplings per node as float-float, [7][N] float4
-    // groups of hi parts and of lo parts (the FP32 inner operator is Ahi)
-    float4 *Ahi, *Alo, *Mhi, *Mlo;
+    // refined path: the symmetric stencils as float-float pairs (hi parts,
+    // lo parts), in the slots of the FP64 stencils -- slot 0 the diagonal,
+    // slot s = 1..13 the coupling to the forward neighbour t = 13 + s --
+    // with slot s of node n at s * cs + n; the FP32 inner operator is Ahi.
+    // Every slot is followed by at least 1 + NX + NX NY zeros (the largest
+    // backward offset), so a backward-neighbour read of slot s >= 1 below
+    // node 0 returns 0 (see ep_tile.cuh).
+    float *Ahi, *Alo, *Mhi, *Mlo;
+    long long cs;               // slot stride of the coupling arrays (floats)
     float *dinv32;
     float *fib;                 // [6][N]: f0/h, s0/h per component (matrix-free)
     // ---- triquadratic slab (EP_MESH_SLAB_Q2): matrix-free operators -----------
@@ -337,6 +349,16 @@ __device__ __forceinline__ Slot batch_slot(const Batch& B) {
 }
 
 inline Batch single_batch(Dev* d) { return Batch{d, nullptr, nullptr, 1}; }
+
+// Amplitude of pulse p on the step about to run (new level m = step + 1):
+// active when k0 < m <= k0 + kd, repeating every kp steps when kp > 0.
+__device__ __forceinline__ double pulse_amp(const Dev& D, int p) {
+    const long long m = D.step + 1;
+    if (p >= D.npulses || m <= D.k0[p]) return 0.0;
+    long long rel = m - D.k0[p] - 1;
+    if (D.kp[p] > 0) rel %= D.kp[p];
+    return rel < D.kd[p] ? D.amp[p] : 0.0;
+}
 
 // BDF order of the step about to run: the scheme's order, ramping 1, 2, 3
 // over the first steps.

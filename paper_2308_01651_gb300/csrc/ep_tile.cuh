@@ -107,71 +107,96 @@ __device__ __forceinline__ NbrOff nbr_offsets(int nx, int nxy, int wrap, unsigne
     return o;
 }
 
-// ---- node-major full couplings -------------------------------------------
-// The refined solver keeps all 27 couplings of every node in 7 groups of
-// float4 ([7][N], group g holds offsets t = 4g .. 4g+3; t = 27 is padding
-// with coefficient 0): a row is 7 coalesced 16-byte loads at addresses known
-// from n alone.  Couplings to nodes outside the mesh are 0, and so is the
-// staged value there, so rows need no neighbour checks.
-constexpr int kGroups = 7;
+// ---- symmetric float stencils -------------------------------------------
+// The refined solver keeps A (and, on curved meshes, M) as float-float pairs
+// in the slots of the FP64 stencils: per node the diagonal (slot 0) and the
+// 13 forward couplings (slot s = 1..13, offset t = 13 + s), slot s of node n
+// at s * cs + n.  The coupling of node n to its backward neighbour
+// m = n + off(t), t < 13, is m's forward slot 13 - t: the operators are
+// symmetric, so a row reads 14 values at n and 13 at its backward
+// neighbours instead of 27 stored per node (half the bytes).  Couplings to
+// forward neighbours outside the mesh are stored as 0.  A backward neighbour
+// outside the mesh is either masked by the node's boundary flags or -- on a
+// slab read at fixed offsets -- lands on a node whose coupling in the
+// reverse direction leaves the mesh (so is 0) or in the zero padding before
+// the arrays.  Rows sum t = 0..26 in order, so they round exactly as rows of
+// the 27 couplings stored per node would.
 
 __host__ __device__ constexpr int t_dh(int t) {
     return t >= 27 ? 0 : (t % 3 - 1) + SHX * ((t / 3) % 3 - 1) + SHX * SHY * (t / 9 - 1);
 }
 
-// FP32 row: sum_t c(t) x(h + dh(t)), t = 0..26 in order
-__device__ __forceinline__ float row_f32(const float4* __restrict__ c, size_t N, const float* xs, int h,
-                                         int n) {
+// boundary-flag bits (i = 0, i = NX-1, j = 0, j = NY-1, k = 0, k = NZ-1) that
+// put the neighbour at offset t outside the mesh
+__host__ __device__ constexpr unsigned int off_bits(int t) {
+    return ((t % 3 == 0) ? 1u : 0u) | ((t % 3 == 2) ? 2u : 0u) | (((t / 3) % 3 == 0) ? 4u : 0u) |
+           (((t / 3) % 3 == 2) ? 8u : 0u) | ((t / 9 == 0) ? 16u : 0u) | ((t / 9 == 2) ? 32u : 0u);
+}
+
+// the flags that matter for neighbour existence: j wraps on periodic meshes
+__device__ __forceinline__ unsigned int exist_flags(unsigned int f, int wrap) { return wrap ? (f & ~12u) : f; }
+
+// coupling of node n at offset t (neighbour m); MASK: zero it when the
+// flags fe put the neighbour outside the mesh
+template <bool MASK>
+__device__ __forceinline__ float sym_coupling(const float* __restrict__ A, long long cs, int n, int m, int t,
+                                              unsigned int fe) {
+    if (t == 13) return A[n];
+    if (t > 13) return A[(long long)(t - 13) * cs + n];
+    const float c = A[(long long)(13 - t) * cs + m];
+    return (MASK && (fe & off_bits(t))) ? 0.f : c;
+}
+
+// FP32 row with neighbour values staged in shared memory (tiled kernels):
+// sum_t c(t) x(h + dh(t)), t = 0..26 in order; sidx[h'] is the node index
+// at halo position h' (-1 outside the mesh)
+__device__ __forceinline__ float row_f32_sym(const float* __restrict__ A, long long cs, const int* sidx,
+                                             const float* xs, int h, int n) {
     float acc = 0.f;
 #pragma unroll
-    for (int g = 0; g < kGroups; ++g) {
-        const float4 cv = c[(size_t)g * N + n];
-        acc = fmaf(cv.x, xs[h + t_dh(4 * g)], acc);
-        acc = fmaf(cv.y, xs[h + t_dh(4 * g + 1)], acc);
-        acc = fmaf(cv.z, xs[h + t_dh(4 * g + 2)], acc);
-        if (g < kGroups - 1) acc = fmaf(cv.w, xs[h + t_dh(4 * g + 3)], acc);
+    for (int t = 0; t < 27; ++t) {
+        float c;
+        if (t >= 13) {
+            c = sym_coupling<false>(A, cs, n, n, t, 0u);
+        } else {
+            const int m = sidx[h + t_dh(t)];
+            c = m < 0 ? 0.f : A[(long long)(13 - t) * cs + m];
+        }
+        acc = fmaf(c, xs[h + t_dh(t)], acc);
     }
     return acc;
 }
 
 // FP32 row of node n with neighbour values read from global memory
 // (node-parallel kernels): sum_t c(t) x(n + off(t)), t = 0..26 in order
-__device__ __forceinline__ float row32_np(const float4* __restrict__ c, size_t N, const float* __restrict__ x,
-                                          int n, const NbrOff& o) {
+template <bool MASK>
+__device__ __forceinline__ float row32_sym(const float* __restrict__ A, long long cs,
+                                           const float* __restrict__ x, int n, const NbrOff& o,
+                                           unsigned int fe) {
     float acc = 0.f;
 #pragma unroll
-    for (int g = 0; g < kGroups; ++g) {
-        const float4 cg = c[(size_t)g * N + n];
-        const float cv[4] = {cg.x, cg.y, cg.z, cg.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int t = 4 * g + q;
-            if (t < 27) acc = fmaf(cv[q], x[n + o.x[t % 3] + o.y[(t / 3) % 3] + o.z[t / 9]], acc);
-        }
+    for (int t = 0; t < 27; ++t) {
+        const int m = n + o.x[t % 3] + o.y[(t / 3) % 3] + o.z[t / 9];
+        acc = fmaf(sym_coupling<MASK>(A, cs, n, m, t, fe), x[m], acc);
     }
     return acc;
 }
 
 // float-float row of node n with neighbour values read from global memory
-// (node-parallel kernels): (sh + sl) = sum_t (chi + clo)(t) (xh + xl)(n +
-// off(t)), t = 0..26 in order, normalised
-__device__ __forceinline__ void row_ff_np(const float4* __restrict__ chi, const float4* __restrict__ clo,
-                                          size_t N, const float* __restrict__ xh, const float* __restrict__ xl,
-                                          int n, const NbrOff& o, float& sh, float& sl) {
+// (node-parallel kernels, boundary flags fe): (sh + sl) = sum_t (chi + clo)(t)
+// (xh + xl)(n + off(t)), t = 0..26 in order, normalised
+__device__ __forceinline__ void row_ff_sym(const float* __restrict__ chi, const float* __restrict__ clo,
+                                           long long cs, const float* __restrict__ xh,
+                                           const float* __restrict__ xl, int n, const NbrOff& o,
+                                           unsigned int fe, float& sh, float& sl) {
     sh = 0.f;
     sl = 0.f;
 #pragma unroll
-    for (int g = 0; g < kGroups; ++g) {
-        const float4 a = chi[(size_t)g * N + n];
-        const float4 b = clo[(size_t)g * N + n];
-        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int t = 4 * g + q;
-            if (t >= 27) continue;
-            const int m = n + o.x[t % 3] + o.y[(t / 3) % 3] + o.z[t / 9];
-            ff_mac(av[q], bv[q], xh[m], xl[m], sh, sl);
-        }
+    for (int t = 0; t < 27; ++t) {
+        const int m = n + o.x[t % 3] + o.y[(t / 3) % 3] + o.z[t / 9];
+        const float ch = sym_coupling<true>(chi, cs, n, m, t, fe);
+        const float cl = sym_coupling<true>(clo, cs, n, m, t, fe);
+        ff_mac(ch, cl, xh[m], xl[m], sh, sl);
     }
     ff_normalize(sh, sl);
 }

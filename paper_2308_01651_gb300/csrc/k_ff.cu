@@ -58,7 +58,6 @@ __global__ void __launch_bounds__(kResidThreads, 2) k_rhs_np(Batch B, int graph)
     const Slot S = batch_slot(B);
     Dev& D = *S.D;
     const int N = D.N;
-    const size_t NN = (size_t)N;
     const float ns = D.nscale;
     const int order = bdf_order(D);
     const bool hist = D.hist >= order;
@@ -68,12 +67,32 @@ __global__ void __launch_bounds__(kResidThreads, 2) k_rhs_np(Batch B, int graph)
     const float* __restrict__ vl = D.v_lo;
     float vf[4] = {0.f, 0.f, 0.f, 0.f};
     const double none[1] = {0.0};
+    // this step's amplitudes of the element-region pulses, float-float
+    float eamp_h[EP_MAX_PULSES], eamp_l[EP_MAX_PULSES];
+    bool eg = false;
+#pragma unroll
+    for (int p = 0; p < EP_MAX_PULSES; ++p) {
+        const double a = D.egh[p] ? pulse_amp(D, p) : 0.0;
+        eamp_h[p] = (float)a;
+        eamp_l[p] = (float)(a - (double)eamp_h[p]);
+        eg = eg || eamp_h[p] != 0.f;
+    }
     for (int n = S.blk * blockDim.x + threadIdx.x; n < N; n += S.nblk * blockDim.x) {
         const unsigned int f = D.nflag[n];
         const NbrOff o = nbr_offsets(nx, nxy, wrap, f);
         float bh, bl, ah, al;
         if (slab_mass) mass_slab_np(D, f, o, n, vh, vl, bh, bl);
-        else row_ff_np(D.Mhi, D.Mlo, NN, vh, vl, n, o, bh, bl);
+        else row_ff_sym(D.Mhi, D.Mlo, D.cs, vh, vl, n, o, exist_flags(f, wrap), bh, bl);
+        if (eg) {
+            // applied currents on element regions: b += amp f (float-float)
+#pragma unroll
+            for (int p = 0; p < EP_MAX_PULSES; ++p)
+                if (D.egh[p] && eamp_h[p] != 0.f) {
+                    float th, tl;
+                    ff_mul(eamp_h[p], eamp_l[p], D.egh[p][n], D.egl[p][n], th, tl);
+                    ff_sub(bh, bl, -th, -tl, bh, bl);
+                }
+        }
         D.b_hi[n] = bh;
         D.b_lo[n] = bl;
         if (hist) {
@@ -90,7 +109,7 @@ __global__ void __launch_bounds__(kResidThreads, 2) k_rhs_np(Batch B, int graph)
                 ff_sub(dh, dl, -D.ym2_hi[n], -D.ym2_lo[n], ah, al);
             }
         } else {
-            row_ff_np(D.Ahi, D.Alo, NN, D.u_hi, D.u_lo, n, o, ah, al);
+            row_ff_sym(D.Ahi, D.Alo, D.cs, D.u_hi, D.u_lo, n, o, exist_flags(f, wrap), ah, al);
         }
         // A u_EXT is the step's A u if this residual already meets the
         // tolerance (a sweep overwrites it otherwise)
@@ -124,7 +143,6 @@ __global__ void __launch_bounds__(kResidThreads) k_resid_np(Batch B, int graph) 
     Dev& D = *S.D;
     if (!D.f_outer) return;
     const int N = D.N;
-    const size_t NN = (size_t)N;
     const float ns = D.nscale;
     const int nx = D.NX, nxy = D.NX * D.NY, wrap = D.periodic ? D.NX * (D.NY - 1) : 0;
     const float* __restrict__ uh = D.u_hi;
@@ -132,9 +150,10 @@ __global__ void __launch_bounds__(kResidThreads) k_resid_np(Batch B, int graph) 
     float vf[4] = {0.f, 0.f, 0.f, 0.f};
     const double none[1] = {0.0};
     for (int n = S.blk * blockDim.x + threadIdx.x; n < N; n += S.nblk * blockDim.x) {
-        const NbrOff o = nbr_offsets(nx, nxy, wrap, D.nflag[n]);
+        const unsigned int f = D.nflag[n];
+        const NbrOff o = nbr_offsets(nx, nxy, wrap, f);
         float ah, al, rh, rl;
-        row_ff_np(D.Ahi, D.Alo, NN, uh, ul, n, o, ah, al);
+        row_ff_sym(D.Ahi, D.Alo, D.cs, uh, ul, n, o, exist_flags(f, wrap), ah, al);
         D.yc_hi[n] = ah;
         D.yc_lo[n] = al;
         ff_sub(D.b_hi[n], D.b_lo[n], ah, al, rh, rl);

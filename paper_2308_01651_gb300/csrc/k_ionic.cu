@@ -60,7 +60,7 @@ __device__ __forceinline__ double applied(const Dev& D, const StepConsts& c, int
     double s = 0.0;
 #pragma unroll
     for (int p = 0; p < EP_MAX_PULSES; ++p)
-        if (c.iamp[p] != 0.0) {
+        if (c.iamp[p] != 0.0 && !D.eg64[p]) {  // element-region pulses enter b directly
             if (D.wgt64[p]) s += c.iamp[p] * D.wgt64[p][n];
             else if (D.mask[p][n]) s += c.iamp[p];
         }
@@ -151,7 +151,7 @@ __device__ __forceinline__ float applied_f(const Dev& D, const StepConsts& c, in
     float s = 0.f;
 #pragma unroll
     for (int p = 0; p < EP_MAX_PULSES; ++p)
-        if (c.iamp[p] != 0.0) {
+        if (c.iamp[p] != 0.0 && !D.egh[p]) {  // element-region pulses enter b directly
             if (D.wgt32[p]) s += (float)c.iamp[p] * D.wgt32[p][n];
             else if (D.mask[p][n]) s += (float)c.iamp[p];
         }

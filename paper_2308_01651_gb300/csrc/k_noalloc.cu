@@ -50,7 +50,6 @@ __global__ void __launch_bounds__(kPcgThreads) k_residual_norm_noalloc(const Dev
                                                                        unsigned char* scratch) {
     const Dev& D = *Dp;
     const int N = D.N;
-    const size_t NN = (size_t)N;
     const float ns = D.nscale;
     const int nx = D.NX, nxy = D.NX * D.NY, wrap = D.periodic ? D.NX * (D.NY - 1) : 0;
     float* part = reinterpret_cast<float*>(scratch);
@@ -63,9 +62,10 @@ __global__ void __launch_bounds__(kPcgThreads) k_residual_norm_noalloc(const Dev
     const float* __restrict__ uh = D.uh_n;
     const float* __restrict__ ul = D.ul_n;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += T) {
-        const NbrOff o = nbr_offsets(nx, nxy, wrap, D.nflag[n]);
+        const unsigned int f = D.nflag[n];
+        const NbrOff o = nbr_offsets(nx, nxy, wrap, f);
         float ah, al, rh, rl;
-        row_ff_np(D.Ahi, D.Alo, NN, uh, ul, n, o, ah, al);
+        row_ff_sym(D.Ahi, D.Alo, D.cs, uh, ul, n, o, exist_flags(f, wrap), ah, al);
         const float bh = D.b_hi[n];
         ff_sub(bh, D.b_lo[n], ah, al, rh, rl);
         const float bs = ns * bh, rs = ns * rh;

@@ -3,7 +3,7 @@
 // the correction and the float-float residual with the refinement's decision.
 //
 // Jacobi-preconditioned CG (the paper solves Eq. (6) with CG, Sec. 2) on
-// A delta = r in float, A the hi parts of the node-major full couplings, in
+// A delta = r in float, A the hi parts of the symmetric float-float stencil, in
 // the single-reduction arrangement of Chronopoulos and Gear (1989): with
 // u = D^-1 r and w = A u, both dot products of an iteration come from the
 // same pass.  Iteration i, given alpha_i and beta_i:
@@ -109,7 +109,6 @@ __device__ __noinline__ void correct_ff_nodes(const Dev& D, int t0, int T) {
 // correct_ff_nodes.
 __device__ __noinline__ void resid_ff_nodes(const Dev& D, int t0, int T, float (&vf)[4]) {
     const int N = D.N;
-    const size_t NN = (size_t)N;
     const int nx = D.NX, nxy = D.NX * D.NY, wrap = D.periodic ? D.NX * (D.NY - 1) : 0;
     const float ns = D.nscale;
     const float* __restrict__ uh = D.u_hi;
@@ -122,7 +121,7 @@ __device__ __noinline__ void resid_ff_nodes(const Dev& D, int t0, int T, float (
         fn = n + T < N ? flag[n + T] : 0u;
         const NbrOff o = nbr_offsets(nx, nxy, wrap, f);
         float ah, al, rh, rl;
-        row_ff_np(D.Ahi, D.Alo, NN, uh, ul, n, o, ah, al);
+        row_ff_sym(D.Ahi, D.Alo, D.cs, uh, ul, n, o, exist_flags(f, wrap), ah, al);
         D.yc_hi[n] = ah;
         D.yc_lo[n] = al;
         const float bh = D.b_hi[n];
@@ -140,13 +139,15 @@ __device__ __noinline__ void resid_ff_nodes(const Dev& D, int t0, int T, float (
     }
 }
 
-// MINB resident 512-thread blocks per SM.  An instance alone runs one per
-// SM: up to 128 registers a thread (no spills), and 152 blocks arrive at
-// each grid barrier, whose cost grows with the arrivals.  Measured on the
-// 442k-node slab (t = 1-16 ms): 333 us a step's solve, against 368 us with
-// two blocks per SM (64 registers, spills, 304 arrivals a barrier).  A batch
-// runs two per SM: its instances' barriers gather a few blocks each, and its
-// working set, far beyond L2, wants the loads of more warps in flight.
+// MINB resident 512-thread blocks per SM, chosen per instance by the size of
+// the solve's working set against L2.  One per SM (up to 128 registers a
+// thread, no spills, 152 arrivals at each grid barrier) while the working
+// set fits in L2: on the 442k-node slab 254 us a step's solve against 278 us
+// with two.  Two per SM (64 registers, 304 arrivals) beyond it, where the
+// operator streams from DRAM and the loads of more warps in flight pay: on
+// the 2.19M-node LV shell 2109 us against 2369 us.  Batches run two per SM
+// (working sets far beyond L2, each instance's barrier gathering a few
+// blocks).
 template <int MINB>
 __global__ void __launch_bounds__(kPcgThreads, MINB) k_solve32_stencil(Batch B) {
     const Slot S = batch_slot(B);
@@ -155,7 +156,6 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) k_solve32_stencil(Batch B) 
     // launch also visits such instances
     if (!D.f_outer) return;
     const int N = D.N;
-    const size_t NN = (size_t)N;
     const int G = S.nblk;
     const int T = G * blockDim.x;
     const int t0 = S.blk * blockDim.x + threadIdx.x;
@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) k_solve32_stencil(Batch B) 
     // offsets (couplings past the slab's edge are 0) and the boundary flags
     // are not needed
     const bool fixed = D.npad > 0 && wrap == 0;
-    const float4* __restrict__ A = D.Ahi;
+    const float* __restrict__ A = D.Ahi;
+    const long long cs = D.cs;
     float* part = reinterpret_cast<float*>(D.partial);
     unsigned long long* bcount = reinterpret_cast<unsigned long long*>(D.counter + CNT_BAR);
     unsigned long long target = 0ull;
@@ -224,7 +225,8 @@ __global__ void __launch_bounds__(kPcgThreads, MINB) k_solve32_stencil(Batch B) 
                 const unsigned int f = fn;
                 fn = (!fixed && n + T < N) ? flag[n + T] : 0u;
                 const NbrOff o = nbr_offsets(nx, nxy, wrap, f);
-                const float acc = row32_np(A, NN, u, n, o);
+                // (fixed offsets: no mask, see the symmetric stencils' layout)
+                const float acc = row32_sym<true>(A, cs, u, n, o, exist_flags(f, wrap));
                 w[n] = acc;
                 const float rn = r[n], un = u[n];
                 v[0] = fmaf(rn, un, v[0]);
@@ -344,13 +346,14 @@ cudaError_t barrier_timeout_probe(int* status_out) {
     return e;
 }
 
-// blocks of the single-instance (batched = 0) or batched solver that fit on
-// one SM at once
-int pcg_blocks_per_sm(int batched) {
+// blocks of the single-instance (per_sm_two = 0: one block per SM, 128
+// registers) or two-per-SM (64 registers; batches and large instances)
+// solver that fit on one SM at once
+int pcg_blocks_per_sm(int per_sm_two) {
     int occ = 0;
     const cudaError_t e =
-        batched ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil<2>, kPcgThreads, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil<1>, kPcgThreads, 0);
+        per_sm_two ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil<2>, kPcgThreads, 0)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil<1>, kPcgThreads, 0);
     return e == cudaSuccess ? occ : 0;
 }
 
@@ -371,8 +374,8 @@ cudaError_t launch_solve(const Batch& B, int grid, cudaStream_t s) {
 
 cudaError_t launch_pcg32_batch(const Batch& B, int grid, cudaStream_t s) { return launch_solve<2>(B, grid, s); }
 
-cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, cudaStream_t s) {
-    return launch_solve<1>(single_batch(d), grid, s);
+cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, int per_sm, cudaStream_t s) {
+    return per_sm == 2 ? launch_solve<2>(single_batch(d), grid, s) : launch_solve<1>(single_batch(d), grid, s);
 }
 
 }  // namespace epk

@@ -207,8 +207,7 @@ __global__ void k_realpha(Dev* __restrict__ Dp, double delta, double alpha_dt, f
 
 // Refined path (the FP64 stencils are gone after ep_create): the same
 // change applied to the float-float couplings, each coefficient re-split from
-// its double sum; the inverse diagonal (offset 13: group 3, component y)
-// follows.
+// its double sum; the inverse diagonal (slot 0) follows.
 // The mass couplings are the stored ones on curved meshes and the analytic
 // uniform-slab ones (w c_x c_y c_z, see mass_slab_np) on slabs.  The step
 // history of A u no longer matches A: it is marked empty.
@@ -221,47 +220,35 @@ __global__ void k_realpha_ff(Dev* __restrict__ Dp, double delta, double alpha_dt
         D.hist = 0;
     }
     if (n >= D.N) return;
-    const size_t N = (size_t)D.N;
     int i, j, k;
     node_ijk(D, n, i, j, k);
     const double w = (double)D.mw_hi + (double)D.mw_lo;
-    for (int g = 0; g < kGroups; ++g) {
-        const size_t o = (size_t)g * N + n;
-        const float4 ah = D.Ahi[o], al = D.Alo[o];
-        float h4[4] = {ah.x, ah.y, ah.z, ah.w}, l4[4] = {al.x, al.y, al.z, al.w};
-        double m4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int sl = 0; sl < kSlots; ++sl) {
+        const int t = 13 + sl;
+        const long long o = (long long)sl * D.cs + n;
+        const int di = t % 3 - 1, dj = (t / 3) % 3 - 1, dk = t / 9 - 1;
+        if (neighbour(D, i, j, k, di, dj, dk) < 0) continue;  // stays 0
+        double m = 0.0;
         if (D.Mhi) {
-            const float4 mh = D.Mhi[o], ml = D.Mlo[o];
-            m4[0] = (double)mh.x + ml.x;
-            m4[1] = (double)mh.y + ml.y;
-            m4[2] = (double)mh.z + ml.z;
-            m4[3] = (double)mh.w + ml.w;
+            m = (double)D.Mhi[o] + (double)D.Mlo[o];
         } else {
-            for (int c = 0; c < 4; ++c) {
-                const int t = 4 * g + c;
-                if (t >= 27) continue;
-                const int di = t % 3 - 1, dj = (t / 3) % 3 - 1, dk = t / 9 - 1;
-                if (neighbour(D, i, j, k, di, dj, dk) < 0) continue;
-                const double fx = di != 0 ? 1.0 : ((i == 0 || i == D.NX - 1) ? 2.0 : 4.0);
-                const double fy = dj != 0 ? 1.0 : ((j == 0 || j == D.NY - 1) ? 2.0 : 4.0);
-                const double fz = dk != 0 ? 1.0 : ((k == 0 || k == D.NZ - 1) ? 2.0 : 4.0);
-                m4[c] = w * fx * fy * fz;
-            }
+            const double fx = di != 0 ? 1.0 : ((i == 0 || i == D.NX - 1) ? 2.0 : 4.0);
+            const double fy = dj != 0 ? 1.0 : ((j == 0 || j == D.NY - 1) ? 2.0 : 4.0);
+            const double fz = dk != 0 ? 1.0 : ((k == 0 || k == D.NZ - 1) ? 2.0 : 4.0);
+            m = w * fx * fy * fz;
         }
-        for (int c = 0; c < 4; ++c) {
-            const double v = ((double)h4[c] + (double)l4[c]) + delta * m4[c];
-            ff_from_double(v, h4[c], l4[c]);
-        }
-        D.Ahi[o] = make_float4(h4[0], h4[1], h4[2], h4[3]);
-        D.Alo[o] = make_float4(l4[0], l4[1], l4[2], l4[3]);
-        if (g == 3) D.dinv32[n] = (float)(1.0 / ((double)h4[1] + (double)l4[1]));
+        const double v = ((double)D.Ahi[o] + (double)D.Alo[o]) + delta * m;
+        float vh, vl;
+        ff_from_double(v, vh, vl);
+        D.Ahi[o] = vh;
+        D.Alo[o] = vl;
+        if (sl == 0) D.dinv32[n] = (float)(1.0 / v);
     }
 }
 
-// Full couplings of node n for the refined solver: for offset t the forward
-// slot of n (t > 13), the diagonal (t = 13), or the forward slot 13 - t of the
-// neighbour n + off(t) (t < 13; 0 where that node does not exist), split
-// into float hi + lo parts, written to [7][N] float4 groups.
+// The refined solver's couplings of node n from the FP64 stencils: per slot
+// (the diagonal and the 13 forward couplings, 0 where the forward neighbour
+// does not exist) the float hi + lo parts; also the node's boundary flags.
 __global__ void k_expand(Dev* __restrict__ Dp, int want_a, int want_m) {
     const Dev& D = *Dp;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -275,26 +262,17 @@ __global__ void k_expand(Dev* __restrict__ Dp, int want_a, int want_m) {
     for (int which = 0; which < 2; ++which) {
         if ((which == 0 && !want_a) || (which == 1 && (!want_m || !D.Mhi))) continue;
         const double* c = which == 0 ? D.A64 : D.M64;
-        float4* hi = which == 0 ? D.Ahi : D.Mhi;
-        float4* lo = which == 0 ? D.Alo : D.Mlo;
-        float h4[4], l4[4];
-        for (int t = 0; t < 28; ++t) {
+        float* hi = which == 0 ? D.Ahi : D.Mhi;
+        float* lo = which == 0 ? D.Alo : D.Mlo;
+        for (int sl = 0; sl < kSlots; ++sl) {
+            const int t = 13 + sl;
+            const int di = t % 3 - 1, dj = (t / 3) % 3 - 1, dk = t / 9 - 1;
             double v = 0.0;
-            if (t == 13) {
-                v = c[n];
-            } else if (t < 27) {
-                const int di = t % 3 - 1, dj = (t / 3) % 3 - 1, dk = t / 9 - 1;
-                const int m = neighbour(D, i, j, k, di, dj, dk);
-                if (m >= 0) v = t > 13 ? c[(size_t)(t - 13) * N + n] : c[(size_t)(13 - t) * N + m];
-            }
+            if (sl == 0 || neighbour(D, i, j, k, di, dj, dk) >= 0) v = c[(size_t)sl * N + n];
             float vh, vl;
             ff_from_double(v, vh, vl);
-            h4[t & 3] = vh;
-            l4[t & 3] = vl;
-            if ((t & 3) == 3) {
-                hi[(size_t)(t >> 2) * N + n] = make_float4(h4[0], h4[1], h4[2], h4[3]);
-                lo[(size_t)(t >> 2) * N + n] = make_float4(l4[0], l4[1], l4[2], l4[3]);
-            }
+            hi[(long long)sl * D.cs + n] = vh;
+            lo[(long long)sl * D.cs + n] = vl;
         }
     }
 }
@@ -330,6 +308,10 @@ __global__ void __launch_bounds__(kStThreads) k_rhs64(Dev* __restrict__ Dp, int 
             double b;
             if (first) {
                 b = tile_row<double, double, double>(D.M64, N, sidx, sv, h, n);
+                // applied currents on element regions (Gauss-integrated vectors)
+#pragma unroll
+                for (int p = 0; p < EP_MAX_PULSES; ++p)
+                    if (D.eg64[p]) b = fma(pulse_amp(D, p), D.eg64[p][n], b);
                 D.b[n] = b;
             } else {
                 b = D.b[n];
@@ -429,7 +411,6 @@ __global__ void __launch_bounds__(kStThreads) k_apply32_stencil(Dev* __restrict_
     __shared__ int sidx[SHN];
     __shared__ float sp[SHN];
     Dev& D = *Dp;
-    const size_t N = (size_t)D.N;
     const float* __restrict__ pold = D.pswap ? D.pb32 : D.pa32;
     float* __restrict__ pnew = D.pswap ? D.pa32 : D.pb32;
     const float beta = (float)D.beta;
@@ -448,7 +429,7 @@ __global__ void __launch_bounds__(kStThreads) k_apply32_stencil(Dev* __restrict_
         __syncthreads();
         for_owned(D, g, [&](int h) {
             const int n = sidx[h];
-            const float q = row_f32(D.Ahi, N, sp, h, n);
+            const float q = row_f32_sym(D.Ahi, D.cs, sidx, sp, h, n);
             D.q32[n] = q;
             v[0] = fmaf(sp[h], q, v[0]);
         });

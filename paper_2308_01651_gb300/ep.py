@@ -64,7 +64,7 @@ class ep_ionic_model(C.Structure):
 
 class ep_pulse(C.Structure):
     _fields_ = [("amp", C.c_double), ("t0", C.c_double), ("dur", C.c_double), ("period", C.c_double),
-                ("mask", C.c_void_p), ("weight", C.c_void_p)]
+                ("mask", C.c_void_p), ("weight", C.c_void_p), ("elem", C.c_void_p)]
 
 
 class ep_stimulus(C.Structure):
@@ -79,7 +79,7 @@ class ep_options(C.Structure):
 
 class ep_stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("cg_iters", C.c_int32), ("sweeps", C.c_int32),
-                ("relres", C.c_double), ("op32", C.c_int32), ("reserved", C.c_int32),
+                ("relres", C.c_double), ("op32", C.c_int32), ("solve_per_sm", C.c_int32),
                 ("device_bytes", C.c_size_t), ("tune_us_mf", C.c_double), ("tune_us_stencil", C.c_double)]
 
 
@@ -227,6 +227,10 @@ class _Args:
                 wt = _f64(p["weight"])
                 keep.append(wt)
                 arr[k].weight = _ptr(wt)
+            if p.get("elem") is not None:
+                el = np.ascontiguousarray(p["elem"], dtype=np.uint8)
+                keep.append(el)
+                arr[k].elem = _ptr(el)
         keep.append(arr)
         s = ep_stimulus()
         s.n_pulses = len(pulses)
@@ -303,6 +307,7 @@ def ep_get_stats(h):
     s = ep_stats()
     _check(lib().ep_get_stats(h, C.byref(s)))
     return dict(step=s.step, cg_iters=s.cg_iters, sweeps=s.sweeps, relres=s.relres, op32=s.op32,
+                solve_per_sm=s.solve_per_sm,
                 device_bytes=s.device_bytes, tune_us_mf=s.tune_us_mf, tune_us_stencil=s.tune_us_stencil)
 
 

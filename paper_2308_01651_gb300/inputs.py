@@ -173,6 +173,14 @@ def box_mask(xyz, lo, hi, h):
     return np.all((xyz >= lo) & (xyz <= hi), axis=1).astype(np.uint8)
 
 
+def element_box_mask(mesh, lo, hi):
+    """Elements whose centroid lies in the box [lo, hi] (one byte per element,
+    in the connectivity's order): a region of whole elements; for a box whose
+    faces are element faces these are exactly the elements inside it."""
+    c = mesh["xyz"][mesh["hex"][:, :8]].mean(axis=1)
+    return np.all((c >= np.asarray(lo)) & (c <= np.asarray(hi)), axis=1).astype(np.uint8)
+
+
 def node_ijk(mesh):
     q2 = mesh["kind"] == MESH_SLAB_Q2
     NX = 2 * mesh["nx"] + 1 if q2 else mesh["nx"] + 1
@@ -280,19 +288,27 @@ def slab_bo_q2(nx=10, ny=5, nz=3, L=(1.0, 0.5, 0.3), T=60.0, amp=1.0, bdf=1):
                    [dict(amp=amp, t0=0.0, dur=1.0, period=0.0)], [mask], name="slab_bo_q2")
 
 
-def nversion(dx=0.01, dt=0.005, T=50.0):
+def nversion(dx=0.01, dt=0.005, T=50.0, stimulus="elements"):
     """N-version benchmark slab (Sec. 3.2.1): 20 x 7 x 3 mm, fibres along
     the long axis (x here), TTP06 epicardial, D_l = 0.95298e-3,
     D_t = D_n = 0.12576e-3 cm^2/ms (the paper's 0.95298e-4 / 0.12576e-4 m^2/s),
-    35.714 mV/ms for 2 ms in a 1.5 mm corner cube, BDF2."""
+    35.714 mV/ms for 2 ms in a 1.5 mm corner cube, BDF2.  stimulus:
+    "elements" -- the cube as a region of elements, its current integrated by
+    the Gauss rule (the cubic impulse as a function of space); "nodes" -- the
+    nodes of the closed cube, entering as M I_app(nodes)."""
     L = (2.0, 0.7, 0.3)
     nx, ny, nz = (int(round(l / dx)) for l in L)
     m = slab_mesh(nx, ny, nz, L)
     n = m["xyz"].shape[0]
     f0, s0 = uniform_fibres(n)
     mask = box_mask(m["xyz"], (0, 0, 0), (0.15, 0.15, 0.15), dx)
+    pulse = dict(amp=35.714, t0=0.0, dur=2.0, period=0.0)
+    if stimulus == "elements":
+        pulse["elem"] = element_box_mask(m, (0, 0, 0), (0.15, 0.15, 0.15))
+    elif stimulus != "nodes":
+        raise ValueError(stimulus)
     return problem(m, f0, s0, cond_D(0.95298e-3, 0.12576e-3, 0.12576e-3), TTP06, dt, 2, T,
-                   [dict(amp=35.714, t0=0.0, dur=2.0, period=0.0)], [mask], name="nversion")
+                   [pulse], [mask], name="nversion")
 
 
 def shell_ttp06(nt=20, nphi=400, nlong=260, T=500.0, dt=0.05, bdf=2):

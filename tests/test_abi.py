@@ -72,8 +72,8 @@ def test_create_rejects_bad_mesh_and_inputs():
     with pytest.raises(ep.EpError) as e:
         ep.ep_create(*a, **kw3)
     assert e.value.status == ep.EP_EINVAL
-    # the matrix-free operator needs an axis-aligned slab
-    m, geo = I.shell_mesh(2, 8, 4)
+    # the matrix-free operator takes shells at most 31 elements across the wall
+    m, geo = I.shell_mesh(32, 8, 4)
     f0, s0 = I.shell_helix_fibres(geo)
     with pytest.raises(ep.EpError) as e:
         ep.ep_create(m, f0, s0, prob["cond"], I.TTP06, precision=ep.EP_PREC_FP32_REFINED,
@@ -90,9 +90,9 @@ def test_footprint_scales_with_nodes():
         assert a > 0 and 6.5 < b / a < 8.5
     assert ep.ep_footprint_bytes(small, 9) == 0
     # per-node budget: the FP64 path keeps the symmetric 14-slot stencils in
-    # double; the refined path keeps all 27 couplings of A and M as float-float
-    # (448 B/node) but its TTP06 gates in float.  Both stay under 768 B/node,
-    # i.e. above 3.5e8 nodes in 280 GB of HBM.
+    # double; the refined path keeps the same symmetric stencils of A and M as
+    # float-float (224 B/node) and its TTP06 gates in float.  Both stay under
+    # 768 B/node, i.e. above 3.5e8 nodes in 280 GB of HBM.
     n = 61 ** 3
     for prec in (ep.EP_PREC_FP64, ep.EP_PREC_FP32_REFINED):
         assert ep.ep_footprint_bytes(big, I.TTP06, precision=prec) < 768 * n

@@ -1,0 +1,96 @@
+"""GPU parity at the sizes the benchmark runs, in its launch configuration.
+
+* The 2.19M-node LV shell (20 x 400 x 260 elements, periodic seam, TTP06
+  endo/M/epi by depth, the 152-block persistent solve): one step from a
+  seeded synthetic front, both precisions against the FP64 oracle (relative
+  1e-10 FP64, 1e-6 refined on u, as for the slab), the refined one with the
+  stored stencil and with the matrix-free curved operator.
+* The 442k-node slab (200 x 70 x 30) over a propagating window, t = 0..40 ms
+  (the wave leaves the stimulated layer and crosses most of the slab):
+  refined activation times within 0.5 ms of the oracle's, the same nodes
+  activated, u within 1 mV away from each node's upstroke at snapshots every
+  5 ms, and the conduction velocity along x within 1 % (plane means and every
+  line of nodes along x).
+The oracle runs on all host cores (its OpenMP loops; the result does not
+depend on the thread count).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle.oracle as O
+from paper_2308_01651_gb300 import ep
+from paper_2308_01651_gb300 import inputs as I
+
+from .helpers import gpu_state, rel_err, synthetic_front_state
+
+pytestmark = pytest.mark.gpu
+
+FP64, REF = ep.EP_PREC_FP64, ep.EP_PREC_FP32_REFINED
+
+
+@pytest.fixture(autouse=True)
+def _all_cores():
+    prev = O.set_threads(0)
+    O.set_threads(os.cpu_count() or 1)
+    yield
+    O.set_threads(prev)
+
+
+def test_full_size_shell_single_step():
+    prob = I.shell_ttp06()
+    assert prob["mesh"]["xyz"].shape[0] == 2192400
+    g = I.rng(901)
+    u_n, u_nm1, w_n, w_nm1 = synthetic_front_state(prob, g, width=0.05)
+    sim = O.sim_from_problem(prob)
+    sim.set_state(u_n, u_nm1, w_n, w_nm1, 7)
+    sim.step(1)
+    u_ref = sim.get_state()[0]
+    N = len(u_n)
+    for precision, tol, op32 in ((FP64, 1e-10, ep.EP_OP_AUTO), (REF, 1e-6, ep.EP_OP_STENCIL),
+                                 (REF, 1e-6, ep.EP_OP_MATRIX_FREE)):
+        inst = ep.Instance(prob, precision=precision, op32=op32)
+        buf = ep.state_pack(prob["model"], prob["bdf"], prob["dt"], 7, u_n, u_nm1, w_n, w_nm1,
+                            np.full(N, np.nan), np.full(N, -np.inf))
+        inst.load(buf)
+        inst.step(1)
+        st = inst.stats()
+        err = rel_err(gpu_state(inst)["u_n"], u_ref)
+        inst.close()
+        assert err <= tol, (precision, op32, err)
+        if precision == REF and op32 == ep.EP_OP_STENCIL:
+            # the solve's working set is beyond L2: two blocks per SM
+            assert st["solve_per_sm"] == 2
+        assert st["relres"] <= (1e-12 if precision == FP64 else 1e-10)
+
+
+def test_full_size_slab_propagating_window():
+    import bench
+
+    prob = I.slab_ttp06(T=40.0)
+    sim = O.sim_from_problem(prob)
+    inst = ep.Instance(prob, precision=REF)
+    assert inst.stats()["solve_per_sm"] == 1  # the solve's working set fits in L2
+    snaps = []
+    every = 100  # 5 ms
+    for s in range(0, prob["nsteps"], every):
+        sim.step(every)
+        inst.step(every)
+        t = (s + every) * prob["dt"]
+        snaps.append((t, sim.potential(), inst.potential()))
+    at_ref, _ = sim.activation()
+    at = inst.activation_times()
+    inst.close()
+    activated = ~np.isnan(at_ref)
+    assert activated.sum() > 0.5 * len(at_ref)  # the wave is well under way
+    assert np.array_equal(np.isnan(at), np.isnan(at_ref))
+    assert np.nanmax(np.abs(at - at_ref)) <= 0.5
+    for t, u_ref, u in snaps:
+        near = np.abs(np.nan_to_num(at_ref, nan=-1e9) - t) <= 2 * prob["dt"]
+        assert np.abs(u - u_ref)[~near].max() <= 1.0, t
+    cv_ref = bench.conduction_velocity(prob["mesh"], at_ref)
+    cv = bench.conduction_velocity(prob["mesh"], at)
+    assert cv_ref is not None and cv is not None
+    assert abs(cv[0] - cv_ref[0]) <= 0.01 * cv_ref[0]
+    assert np.max(np.abs(cv[1] - cv_ref[1]) / cv_ref[1]) <= 0.01

@@ -2,18 +2,23 @@
 
 The paper rebuilds the Niederer et al. benchmark: a 20 x 7 x 3 mm slab of
 TTP06 epicardial tissue, fibres along the long axis, a 1.5 mm corner cube
-stimulated with 35.714 V/s for 2 ms, BDF2.  It reports the latest activation
-time -- at P8, the corner opposite the stimulus -- as 42.0 ms on its finest
-hexahedral grid (dx = 0.05 mm, dt = 0.001 ms) and 42-43 ms at dx = 0.1 mm,
-dt = 0.005 ms.
+stimulated with 35.714 V/s for 2 ms (a "Cubic" impulse: a current given as a
+function of space), BDF2.  It reports the latest activation time -- at P8,
+the corner opposite the stimulus -- as 42.0 ms on its finest hexahedral grid
+(dx = 0.05 mm, dt = 0.001 ms) and, at dx = 0.1 mm and dt = 0.005 ms, in
+excellent agreement with the benchmark's converged 42-43 ms.
 
-Here the stimulus enters as M I_app(nodes) with the closed-cube node mask
-(ionic-current-interpolation treatment of I_app), which spreads it half an
-element beyond the cube; the activation time converges in h from below
-(measured: 41.14 ms at 0.1 mm, 41.79 ms at 0.05 mm, time-converged at
-dt = 0.005 ms).  So the finest grid is pinned to the paper's converged
-42.0 ms within 0.5 ms, and the 0.1 mm grid to the paper's 42-43 ms widened by
-1 ms on the early side for that half-element stimulus spread.
+Here the cube enters as a region of whole elements whose current is
+integrated by the Gauss rule (the applied-current vector of Eq. (6)); the
+nodal reading (M I_app(nodes) with the closed cube's node mask) spreads it
+half an element beyond the cube and activates P8 earlier.
+
+Measured on GB300: P8 = 41.895 ms on the paper's finest grid and time step
+(0.105 ms from the paper's 42.0), 41.375 ms at dx = 0.1 mm (the nodal
+reading: 41.14 ms).  The activation time converges in h from below here and
+from above in the paper's figure, so the 0.1 mm grid lands 0.6 ms under the
+paper's band: that test is kept as the paper states it and marked as a known
+deviation (xfail), not widened.
 """
 import numpy as np
 import pytest
@@ -26,8 +31,8 @@ from .helpers import golden, gpu_state
 pytestmark = pytest.mark.gpu
 
 
-def p8_activation(dx, dt, precision):
-    prob = I.nversion(dx=dx, dt=dt, T=50.0)
+def p8_activation(dx, dt, precision, stimulus="elements"):
+    prob = I.nversion(dx=dx, dt=dt, T=50.0, stimulus=stimulus)
     m = prob["mesh"]
     inst = ep.Instance(prob, precision=precision)
     inst.step(prob["nsteps"])
@@ -39,16 +44,39 @@ def p8_activation(dx, dt, precision):
     return at[far]
 
 
+@pytest.mark.xfail(strict=True, reason="known deviation: P8 = 41.375 ms at dx = 0.1 mm (measured), 0.6 ms "
+                                      "under the paper's 42-43 ms; this discretisation converges from below")
 @pytest.mark.parametrize("precision", [ep.EP_PREC_FP32_REFINED, ep.EP_PREC_FP64])
-def test_nversion_dx01_dt0005(precision):
+def test_nversion_dx01_dt0005_in_papers_band(precision):
     lo, hi = golden("nversion_slab.json")["p8_activation_ms_at_dx_1e-4_m_dt_5e-6_s"]
     t = p8_activation(0.01, 0.005, precision)
-    assert lo - 1.0 <= t <= hi, t
+    assert lo <= t <= hi, t
+
+
+@pytest.mark.parametrize("precision", [ep.EP_PREC_FP32_REFINED, ep.EP_PREC_FP64])
+def test_nversion_dx01_dt0005_measured(precision):
+    """The 0.1 mm grid's P8 as measured, the same in both precisions."""
+    t = p8_activation(0.01, 0.005, precision)
+    assert abs(t - 41.375) <= 0.05, t
 
 
 def test_nversion_finest_grid_converged_value():
-    t = p8_activation(0.005, 0.005, ep.EP_PREC_FP32_REFINED)
-    assert abs(t - golden("nversion_slab.json")["latest_activation_ms_converged_hexahedra"]) <= 0.5, t
+    """The paper's finest grid and time step (dx = 0.05 mm, dt = 0.001 ms)."""
+    g = golden("nversion_slab.json")
+    assert g["converged_grid"] == {"dx_m": 5e-5, "dt_s": 1e-6}
+    t = p8_activation(0.005, 0.001, ep.EP_PREC_FP32_REFINED)
+    assert abs(t - g["latest_activation_ms_converged_hexahedra"]) <= 0.25, t
+
+
+def test_stimulus_reading_and_grid_move_p8():
+    """The reading of the cubic impulse: the nodal one (half an element of
+    spread) activates P8 0.2-0.3 ms earlier at dx = 0.1 mm; halving dx moves
+    P8 later (convergence from below)."""
+    t_el = p8_activation(0.01, 0.005, ep.EP_PREC_FP32_REFINED)
+    t_nd = p8_activation(0.01, 0.005, ep.EP_PREC_FP32_REFINED, stimulus="nodes")
+    assert 0.15 <= t_el - t_nd <= 0.35, (t_el, t_nd)
+    t_fine = p8_activation(0.005, 0.005, ep.EP_PREC_FP32_REFINED)
+    assert t_fine > t_el + 0.3, (t_fine, t_el)
 
 
 @pytest.mark.parametrize("precision,rtol", [(ep.EP_PREC_FP64, 0.0), (ep.EP_PREC_FP32_REFINED, 6e-8)])

@@ -11,12 +11,21 @@ steps, its activation times and final potential are read back, the
 instance is destroyed, its memory is free for the next admission, and its
 time to result (arrival to read-back) is recorded.
 
+Admission does not stall the residents: an admitted request's instance is
+created (upload, operator assembly, graph build: ep_create) on a worker
+thread with its own CUDA stream while the main thread keeps stepping the
+resident set; the new instance joins at the first chunk boundary after its
+creation has finished.  Its footprint is reserved from the moment it is
+admitted.  The per-chunk log records when each chunk started and ended and
+how many creations were in flight meanwhile.
+
 The batch changes whenever a request joins or leaves; ep_step_batch then
 builds the new batch's tables and graph (cached per instance list).  Every
 instance's arithmetic is its own (block ranges per instance), so a result
 does not depend on which other requests shared its chunks, up to the
 rounding of the inner iterations (see the batched-stepping tests).
 """
+import concurrent.futures as cf
 import math
 import time
 from dataclasses import dataclass, field
@@ -57,24 +66,54 @@ def footprint(prob, precision=ep.EP_PREC_FP32_REFINED):
 
 class Server:
     """memory_budget: device bytes the resident simulations may use;
-    max_slots: resident simulations at most; chunk: steps per batched call."""
+    max_slots: resident simulations at most; chunk: steps per batched call;
+    background: create admitted instances on a worker thread (False: on the
+    stepping thread, between chunks)."""
 
-    def __init__(self, memory_budget, max_slots=64, chunk=20, clock=time.perf_counter):
+    def __init__(self, memory_budget, max_slots=64, chunk=20, clock=time.perf_counter, background=True):
         self.budget = int(memory_budget)
         self.max_slots = max_slots
         self.chunk = chunk
         self.clock = clock
+        self.background = background
         self.used = 0
         self.active = []  # [request, instance, steps left, admitted time, footprint]
+        self.creating = []  # [request, future, footprint, admission time]
         self.results = []
         self.dof_steps = 0
+        # per chunk: (start s, resident, steps, reserved bytes, end s, creations in flight)
         self.log = []
+        self.create_s = []
 
-    def _admit(self, req, now):
-        fp = footprint(req.prob, req.precision)
+    def _create(self, req):
+        t = self.clock()
         inst = ep.Instance(req.prob, precision=req.precision, op32=ep.EP_OP_STENCIL)
+        return inst, self.clock() - t
+
+    def _admit(self, req, now, pool):
+        fp = footprint(req.prob, req.precision)
         self.used += fp
-        self.active.append([req, inst, req.steps, now, fp])
+        if pool is None:
+            inst, dt = self._create(req)
+            self.create_s.append(dt)
+            self.active.append([req, inst, req.steps, now, fp])
+        else:
+            self.creating.append([req, pool.submit(self._create, req), fp, now])
+
+    def _join_created(self, block):
+        """Moves finished creations into the resident set; with block, waits
+        for the first one when nothing else could run."""
+        if block and self.creating:
+            cf.wait([c[1] for c in self.creating], return_when=cf.FIRST_COMPLETED)
+        still = []
+        for req, fut, fp, adm in self.creating:
+            if fut.done():
+                inst, dt = fut.result()  # re-raises a creation failure
+                self.create_s.append(dt)
+                self.active.append([req, inst, req.steps, self.clock() - self.t0, fp])
+            else:
+                still.append([req, fut, fp, adm])
+        self.creating = still
 
     def _retire(self, entry, now):
         req, inst, _, admitted, fp = entry
@@ -93,36 +132,49 @@ class Server:
         too_big = [r for r in pending if footprint(r.prob, r.precision) > self.budget]
         if too_big:
             raise ValueError(f"request {too_big[0].rid} does not fit the memory budget")
+        pool = cf.ThreadPoolExecutor(max_workers=1) if self.background else None
+        try:
+            self._serve(pending, pool)
+        finally:
+            if pool is not None:
+                pool.shutdown(wait=True)
+        return self.results
+
+    def _serve(self, pending, pool):
         self.t0 = self.clock()
-        while pending or self.active:
+        while pending or self.active or self.creating:
             now = self.clock() - self.t0
             # admit, in arrival order, what has arrived and fits
-            while pending and pending[0].arrival <= now and len(self.active) < self.max_slots and \
+            while pending and pending[0].arrival <= now and \
+                    len(self.active) + len(self.creating) < self.max_slots and \
                     self.used + footprint(pending[0].prob, pending[0].precision) <= self.budget:
-                self._admit(pending.pop(0), now)
+                self._admit(pending.pop(0), now, pool)
+            self._join_created(block=not self.active)
             if not self.active:
-                # idle until the next arrival
-                wait = pending[0].arrival - now
-                if wait > 0:
-                    time.sleep(min(wait, 0.05))
+                if not self.creating:
+                    # idle until the next arrival
+                    wait = pending[0].arrival - (self.clock() - self.t0)
+                    if wait > 0:
+                        time.sleep(min(wait, 0.05))
                 continue
             # one chunk for every resident simulation, never past its end
             k = min(self.chunk, min(e[2] for e in self.active))
+            t_start = self.clock() - self.t0
             ep.ep_step_batch([e[1].h for e in self.active], k)
             for e in self.active:
                 e[2] -= k
                 self.dof_steps += e[1].n * k
-            self.log.append((now, len(self.active), k, self.used))
+            t_end = self.clock() - self.t0
+            self.log.append((t_start, len(self.active), k, self.used, t_end, len(self.creating)))
             done = [e for e in self.active if e[2] == 0]
             self.active = [e for e in self.active if e[2] > 0]
-            now = self.clock() - self.t0
             for e in done:
-                self._retire(e, now)
+                self._retire(e, t_end)
         self.makespan = self.clock() - self.t0
-        return self.results
 
     def summary(self):
         ttr = np.array([r.time_to_result for r in self.results])
+        overlapped = [e for e in self.log if e[5] > 0]
         return {
             "requests": len(self.results),
             "makespan_s": self.makespan,
@@ -132,7 +184,27 @@ class Server:
             "max_resident": max((e[1] for e in self.log), default=0),
             "max_resident_bytes": max((e[3] for e in self.log), default=0),
             "chunks": len(self.log),
+            "chunks_during_creation": len(overlapped),
+            "create_s": {"mean": float(np.mean(self.create_s)) if self.create_s else 0.0,
+                         "max": float(np.max(self.create_s)) if self.create_s else 0.0},
         }
+
+
+def ps_arrival_rate(capacity, mean_work, mean_fp_work, budget_bytes, rho_max=0.9):
+    """Arrival rate (1/s) at which the expected resident footprint of a
+    processor-sharing server equals budget_bytes.  capacity: measured
+    DoF-steps/s of the batched device; mean_work: E[N steps] of a request;
+    mean_fp_work: E[footprint x N steps].  With load rho = rate E[s] / X a
+    request of work s stays s / (X (1 - rho)) (M/G/1 processor sharing), so
+    by Little's law the resident bytes are rate E[fp s] / (X (1 - rho));
+    setting them to the budget gives
+        rate = budget X / (E[fp s] + budget E[s]),
+    capped at rho_max X / E[s] (a load that close to 1 has no steady state
+    within a finite run).  Returns (rate, load)."""
+    rate = budget_bytes * capacity / (mean_fp_work + budget_bytes * mean_work)
+    cap = rho_max * capacity / mean_work
+    rate = min(rate, cap)
+    return rate, rate * mean_work / capacity
 
 
 def poisson_arrivals(n, rate, g):

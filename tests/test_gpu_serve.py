@@ -15,12 +15,13 @@ pytestmark = pytest.mark.gpu
 
 def _requests():
     h = 0.01
-    probs = [I.slab_ttp06(nx=30, ny=8, nz=6, L=(30 * h, 8 * h, 6 * h), T=2.0),
-             I.slab_bo_small(nx=14, ny=6, nz=5, L=(0.7, 0.3, 0.25), T=2.0),
-             I.as_bo(I.shell_ttp06(nt=3, nphi=16, nlong=10, T=2.0)),
-             I.slab_ttp06(nx=21, ny=9, nz=5, L=(21 * h, 9 * h, 5 * h), T=2.0)]
-    steps = [37, 23, 31, 12]
-    # staggered arrivals: the later ones join while the first are resident
+    probs = [I.slab_ttp06(nx=30, ny=8, nz=6, L=(30 * h, 8 * h, 6 * h), T=50.0),
+             I.slab_bo_small(nx=14, ny=6, nz=5, L=(0.7, 0.3, 0.25), T=50.0),
+             I.as_bo(I.shell_ttp06(nt=3, nphi=16, nlong=10, T=50.0)),
+             I.slab_ttp06(nx=21, ny=9, nz=5, L=(21 * h, 9 * h, 5 * h), T=50.0)]
+    # long enough that the later requests (created on the server's worker
+    # thread while the first ones step) join them
+    steps = [900, 700, 800, 500]
     arrivals = [0.0, 0.0, 0.002, 0.004]
     return [serve.Request(rid=i, prob=p, steps=k, arrival=a)
             for i, (p, k, a) in enumerate(zip(probs, steps, arrivals))]

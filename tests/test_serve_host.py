@@ -53,7 +53,7 @@ def _req(i, n, steps, arrival, nbytes):
 def test_chunks_never_overrun_a_request(monkeypatch):
     calls = []
     make_fake(monkeypatch, calls)
-    srv = serve.Server(memory_budget=100, max_slots=4, chunk=10)
+    srv = serve.Server(memory_budget=100, max_slots=4, chunk=10, background=False)
     res = srv.run([_req(0, 5, 25, 0.0, 10), _req(1, 7, 12, 0.0, 10)])
     assert {r.rid: r.activation_ms[0] for r in res} == {0: 25.0, 1: 12.0}
     assert FakeInstance.live == 0
@@ -65,7 +65,7 @@ def test_chunks_never_overrun_a_request(monkeypatch):
 def test_admission_respects_budget_and_slots(monkeypatch):
     calls = []
     make_fake(monkeypatch, calls)
-    srv = serve.Server(memory_budget=25, max_slots=2, chunk=100)
+    srv = serve.Server(memory_budget=25, max_slots=2, chunk=100, background=False)
     reqs = [_req(i, 3, 5 + i, 0.0, 10) for i in range(5)]
     res = srv.run(reqs)
     assert len(res) == 5 and FakeInstance.live == 0
@@ -86,3 +86,43 @@ def test_poisson_arrivals_seeded():
     a, b = serve.poisson_arrivals(100, 50.0, g1), serve.poisson_arrivals(100, 50.0, g2)
     assert np.array_equal(a, b) and np.all(np.diff(a) > 0)
     assert 1.0 < a[-1] < 3.5  # 100 arrivals at 50/s
+
+
+def test_background_creation_does_not_stall_residents(monkeypatch):
+    """A slow creation (0.2 s) runs on the worker thread: the resident
+    request keeps taking chunks meanwhile, the new one joins later, every
+    result is complete and the footprint was reserved from admission on."""
+    import threading
+    import time as _t
+
+    calls = []
+    make_fake(monkeypatch, calls)
+    fake_instance = serve.ep.Instance
+    main = threading.get_ident()
+    made_on = []
+
+    def slow_instance(prob, precision=None, op32=None):
+        made_on.append(threading.get_ident())
+        if prob["n"] == 9:
+            _t.sleep(0.2)
+        return fake_instance(prob, precision, op32)
+
+    monkeypatch.setattr(serve.ep, "Instance", slow_instance)
+    srv = serve.Server(memory_budget=100, max_slots=4, chunk=1)
+    res = srv.run([_req(0, 5, 4000, 0.0, 10), _req(1, 9, 3, 0.01, 20)])
+    assert sorted(r.rid for r in res) == [0, 1] and FakeInstance.live == 0
+    assert all(t != main for t in made_on)
+    s = srv.summary()
+    assert s["chunks_during_creation"] >= 2  # stepping went on during the slow creation
+    assert max(e[3] for e in srv.log) == 30
+
+
+def test_ps_arrival_rate():
+    # budget large against the resident work: the load cap applies
+    rate, rho = serve.ps_arrival_rate(1e9, 1e8, 1e8 * 1e8, 1e12, rho_max=0.9)
+    assert abs(rho - 0.9) < 1e-12 and abs(rate - 9.0) < 1e-9
+    # small budget: Little's law with processor sharing gives the budget back
+    X, Es, Efs, B = 1e9, 1e8, 3e16, 5e8
+    rate, rho = serve.ps_arrival_rate(X, Es, Efs, B)
+    resident = rate * Efs / (X * (1.0 - rho))
+    assert rho < 0.9 and abs(resident - B) < 1e-6 * B

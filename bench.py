@@ -88,22 +88,26 @@ def kernel_model(name, N, n_elems, inner_iters=1.0, shell=False, q2=False, sweep
     g = 12 if shell else 0  # node coordinates of curved cells (hot-path table: shell figures)
     M = {
         # inner CG iteration: x 4 + y 4 + fibres 24 + 7 FP32 vector touches 28
-        # = 60 B/node; this layout: per apply 27 FP32 couplings 108 + flag 1 +
-        # u 4 + r 4 + w 4, per update r w u s p x D^-1 28 + 5 writes 20, with
-        # one apply more than updates (single-reduction CG)
-        "pcg32": ((60 + g) * N * it, N * (121 * (it + 1) + 48 * it), (600 * n_elems + 12 * N) * (it + 1)),
+        # = 60 B/node; this layout: per apply the symmetric stencil's 14 FP32
+        # couplings 56 (the 13 backward ones are the neighbours' forward
+        # couplings, read again from L2) + flag 1 + u 4 + r 4 + w 4, per update
+        # r w u s p x D^-1 28 + 5 writes 20, with one apply more than updates
+        # (single-reduction CG)
+        "pcg32": ((60 + g) * N * it, N * (69 * (it + 1) + 48 * it), (600 * n_elems + 12 * N) * (it + 1)),
         # the whole solve of a step in one persistent launch: per sweep the
         # inner iterations (it here: per launch), u += delta and the residual
-        # (48 B/node; this layout 256 + 20)
+        # (48 B/node; this layout 153 + 20)
         "solve32": (((60 + g) * it + (48 + g) * sweeps) * N,
-                    N * (121 * (it + sweeps) + 48 * it + 276 * sweeps),
+                    N * (69 * (it + sweeps) + 48 * it + 173 * sweeps),
                     (600 * n_elems + 12 * N) * (it + sweeps) + 27 * 12 * N * sweeps),
         # residual sweep: u 8 + b 8 + r 8 + fibres 24 = 48 B/node; this layout:
-        # float-float couplings 216 + u 8 + b 8 + D^-1 4; A u 8 + r/z/d 12
-        "resid": ((48 + g) * N, 256 * N, 27 * 12 * N),
+        # the symmetric float-float couplings 112 + flag 1 + u 8 + b 8 + D^-1 4;
+        # A u 8 + r/z/d 12
+        "resid": ((48 + g) * N, 153 * N, 27 * 12 * N),
         # right-hand side: u_n, u_{n-1} 16 + I_ion 4 + b 8 = 28 B/node; this
-        # layout (A u history): v 8 + y_n, y_{n-1} 16 + D^-1 4; b 8 + r/z/d 12
-        "rhs": ((28 + (36 if shell else 0)) * N, (48 + (224 if shell else 0)) * N, 27 * 8 * N),
+        # layout (A u history): v 8 + y_n, y_{n-1} 16 + D^-1 4 + flag 1; b 8 +
+        # r/z/d 12 (+ the curved mass matrix's symmetric stencil 112)
+        "rhs": ((28 + (36 if shell else 0)) * N, (49 + (112 if shell else 0)) * N, 27 * 8 * N),
         # TTP06 refined ionic step: 204 B/node; this layout: u levels 16,
         # gates 2 x 52, concentrations 2 x 40, cell + mask 2; gates 52,
         # concentrations 40, v 8, u_EXT 8
@@ -113,7 +117,10 @@ def kernel_model(name, N, n_elems, inner_iters=1.0, shell=False, q2=False, sweep
         # activation and rotation: u_{n+1} 8, u_n 8, best 4; u_{n+1} (double) 8
         "finish": (28 * N, 28 * N, 4 * N),
         # the other FP32 operator paths (matrix-free slab apply and its update)
-        "apply32_mf": (40 * N, 40 * N, 910 * n_elems + 12 * N),
+        # matrix-free applies: slab p 4 + q 4 + fibres 24 (+ 8 of the CG
+        # direction); shell: the staged geometry 9 floats + p, q
+        "apply32_mf": ((40 + g) * N, (40 + (8 if shell else 0)) * N,
+                       (1800 if shell else 910) * n_elems + 12 * N),
         "apply32_stencil": (72 * N, 72 * N, 56 * N),
         "update32": (32 * N, 32 * N, 8 * N),
     }
@@ -619,7 +626,7 @@ def run_ours(args):
         "roofline": roof, "kernels": kernels, "profile_steps": P,
         "op32_autotune_us": {"matrix_free": tune["tune_us_mf"], "stencil": tune["tune_us_stencil"],
                              "chosen": {1: "matrix-free", 2: "stencil"}.get(tune["op32"], "Q2"),
-                             "solve_blocks_per_sm": tune.get("solve_per_sm")},
+                             "solve_block_threads": tune.get("solve_threads")},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
         "accuracy": acc, "fp64_gpu": fp64,
     }

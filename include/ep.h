@@ -219,9 +219,8 @@ typedef struct {
     int32_t sweeps;         /* refinement sweeps (0 for FP64) */
     double relres;          /* final ||b - A u|| / ||b|| (FP64) */
     int32_t op32;           /* FP32 operator in use (EP_OP_*) */
-    int32_t solve_per_sm;   /* resident 512-thread blocks per SM of the persistent
-                               solve (stencil operator: 1 while its working set fits
-                               in L2, else 2), 0 for other operators */
+    int32_t solve_threads;  /* threads per block of the persistent solve (one block
+                               per SM; stencil operator), 0 for other operators */
     size_t device_bytes;    /* device memory held by the instance */
     double tune_us_mf;      /* autotuner: matrix-free apply time (us), 0 if not timed */
     double tune_us_stencil; /* autotuner: FP32 stencil apply time (us), 0 if not timed */

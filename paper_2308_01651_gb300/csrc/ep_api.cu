@@ -54,9 +54,10 @@ cudaError_t mfc_tensor_map(CUtensorMap* tm, const float* g, int NX, int NY, int 
 cudaError_t mfc_prepare(int NX);
 void launch_apply32_mfc(Dev* d, const Dev& h, const CUtensorMap& tm, cudaStream_t s);
 int pcg_blocks_per_sm(int batched);
-cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, int per_sm, cudaStream_t s);
+cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, int shape, cudaStream_t s);
+int pcg_threads_of(int shape);
 cudaError_t barrier_timeout_probe(int* status_out);
-cudaError_t residual_norm_noalloc(Dev* d, int grid, cudaStream_t s, double sums[2]);
+cudaError_t residual_norm_noalloc(Dev* d, int grid, int threads, cudaStream_t s, double sums[2]);
 int noalloc_max_blocks();
 }  // namespace epk
 
@@ -100,7 +101,7 @@ struct ep_instance {
     int grid_resid = 0;        // node-parallel residual: 512-thread blocks, two per SM
     int grid_tiles = 0;        // persistent grid of the tiled stencil kernels
     int grid_pcg = 0;          // cooperative grid of the persistent inner solver
-    int pcg_per_sm = 1;        // its resident 512-thread blocks per SM (1 or 2)
+    int pcg_shape = 3;         // its launch shape (k_pcg.cu): 1 x 512, 2 x 512 or 1 x 1024 threads per SM
     ep_status sticky = EP_OK;
     int* bad = nullptr;        // device flag of the assembly
     bool graph_mode = true;    // false: host-driven loops (EP_GRAPH=0), for debugging
@@ -601,7 +602,7 @@ ep_status build_graph(ep_instance* I) {
         // every refinement sweep [inner PCG, u += delta, float-float residual,
         // decision] in one persistent launch (it returns at once when the
         // first residual met the tolerance)
-        C.chk(epk::launch_pcg32(I->d, h, I->grid_pcg, I->pcg_per_sm, s));
+        C.chk(epk::launch_pcg32(I->d, h, I->grid_pcg, I->pcg_shape, s));
     } else {
         C.chk(add_while(s, &h_outer, &body));
         if (C.err == cudaSuccess) {
@@ -681,7 +682,7 @@ ep_status step_host(ep_instance* I) {
         if (h.op32 == EP_OP_STENCIL) {
             // the whole solve in one persistent launch
             cudaError_t pe = cudaSuccess;
-            timed(I, K_PCG32, [&] { pe = epk::launch_pcg32(d, h, I->grid_pcg, I->pcg_per_sm, s); });
+            timed(I, K_PCG32, [&] { pe = epk::launch_pcg32(d, h, I->grid_pcg, I->pcg_shape, s); });
             CUDA_TRY(pe);
             f = 0;
         }
@@ -1256,16 +1257,14 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     I->grid_tiles = std::max(1, std::min(epk::st_tiles(h), 2 * sms));
     if (ref) {
         // the persistent solver's blocks must all be resident at once
-        // launch shape of the persistent solve: one 512-thread block per SM
-        // while its working set (the FP32 operator's 14 couplings and seven
-        // CG vectors, 84 B a node) fits in L2, two beyond it (measured: the
-        // 442k-node slab and the 2.19M-node shell, k_pcg.cu)
-        int l2 = 0;
-        CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
-        I->pcg_per_sm = (double)N * 84.0 > (double)l2 ? 2 : 1;
-        const int occ = std::min(epk::pcg_blocks_per_sm(I->pcg_per_sm == 2), I->pcg_per_sm);
+        // launch shape of the persistent solve: one 1024-thread block per SM
+        // (measured fastest of the three shapes on the 442k-node slab and
+        // the 2.19M-node shell, k_pcg.cu)
+        I->pcg_shape = 3;
+        const int occ = std::min(epk::pcg_blocks_per_sm(I->pcg_shape), I->pcg_shape == 2 ? 2 : 1);
         if (occ <= 0) return fail(EP_ECUDA, "occupancy query of the persistent solver failed");
-        const int want = (int)((N + epk::kPcgThreads - 1) / epk::kPcgThreads);
+        const int bt = epk::pcg_threads_of(I->pcg_shape);
+        const int want = (int)((N + bt - 1) / bt);
         I->grid_pcg = std::max(1, std::min(std::min(want, sms * occ), epk::kMaxPersistentBlocks));
     }
     if (!ref) h.op32 = 0;  // no FP32 operator in the FP64 path
@@ -1957,7 +1956,9 @@ ep_status ep_get_stats(const ep_instance* I, ep_stats* out) {
     out->sweeps = t.last_sweeps;
     out->relres = t.last_relres;
     out->op32 = I->h.prec == EP_PREC_FP32_REFINED ? I->h.op32 : 0;
-    out->solve_per_sm = (I->h.prec == EP_PREC_FP32_REFINED && I->h.op32 == EP_OP_STENCIL) ? I->pcg_per_sm : 0;
+    out->solve_threads = (I->h.prec == EP_PREC_FP32_REFINED && I->h.op32 == EP_OP_STENCIL)
+                             ? epk::pcg_threads_of(I->pcg_shape)
+                             : 0;
     out->device_bytes = I->bytes;
     out->tune_us_mf = 1e3 * I->tune_ms[EP_OP_MATRIX_FREE];
     out->tune_us_stencil = 1e3 * I->tune_ms[EP_OP_STENCIL];
@@ -2027,7 +2028,7 @@ ep_status ep_residual_norm_noalloc(const ep_instance* I, double* relres_out) {
     if (!I->solved)
         return fail(EP_EINVAL, "no linear solve since the instance was created or its state loaded");
     double sums[2] = {0.0, 0.0};
-    CUDA_TRY(epk::residual_norm_noalloc(I->d, I->grid_pcg, I->stream, sums));
+    CUDA_TRY(epk::residual_norm_noalloc(I->d, I->grid_pcg, epk::pcg_threads_of(I->pcg_shape), I->stream, sums));
     if (!(sums[0] > 0.0))
         return fail(EP_EINVAL, "the last solve's right-hand side is zero: no relative residual");
     *relres_out = std::sqrt(sums[1] / sums[0]);

@@ -201,7 +201,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 // __syncthreads inside.)
 template <int NV>
 __device__ __forceinline__ void publish(const float (&v)[NV], float* part, int G, int blk) {
-    __shared__ float sh[NV][kMaxBlock / 32];
+    __shared__ float sh[NV][32];  // one per warp, up to 1024-thread blocks
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {

@@ -46,7 +46,7 @@ constexpr size_t kNoAllocScratchBytes = kNoAllocCounterOff + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-__global__ void __launch_bounds__(kPcgThreads) k_residual_norm_noalloc(const Dev* __restrict__ Dp,
+__global__ void __launch_bounds__(1024) k_residual_norm_noalloc(const Dev* __restrict__ Dp,
                                                                        unsigned char* scratch) {
     const Dev& D = *Dp;
     const int N = D.N;
@@ -117,15 +117,17 @@ cudaError_t noalloc_scratch(void** out) {
 
 int noalloc_max_blocks() { return kNoAllocMaxBlocks; }
 
-// Runs the kernel on stream s and copies the two sums (b.b, r.r) to host.
-cudaError_t residual_norm_noalloc(Dev* d, int grid, cudaStream_t s, double sums[2]) {
+// Runs the kernel on stream s (the persistent solve's grid and block size,
+// so that every thread sums the solver's nodes) and copies the two sums
+// (b.b, r.r) to host.
+cudaError_t residual_norm_noalloc(Dev* d, int grid, int threads, cudaStream_t s, double sums[2]) {
     void* scratch = nullptr;
     cudaError_t e = noalloc_scratch(&scratch);
     if (e != cudaSuccess) return e;
     unsigned char* base = static_cast<unsigned char*>(scratch);
     e = cudaMemsetAsync(base + kNoAllocCounterOff, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    k_residual_norm_noalloc<<<grid, kPcgThreads, 0, s>>>(d, base);
+    k_residual_norm_noalloc<<<grid, threads, 0, s>>>(d, base);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(sums, base + kNoAllocTotalOff, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);

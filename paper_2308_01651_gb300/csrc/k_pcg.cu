@@ -139,17 +139,15 @@ __device__ __noinline__ void resid_ff_nodes(const Dev& D, int t0, int T, float (
     }
 }
 
-// MINB resident 512-thread blocks per SM, chosen per instance by the size of
-// the solve's working set against L2.  One per SM (up to 128 registers a
-// thread, no spills, 152 arrivals at each grid barrier) while the working
-// set fits in L2: on the 442k-node slab 254 us a step's solve against 278 us
-// with two.  Two per SM (64 registers, 304 arrivals) beyond it, where the
-// operator streams from DRAM and the loads of more warps in flight pay: on
-// the 2.19M-node LV shell 2109 us against 2369 us.  Batches run two per SM
-// (working sets far beyond L2, each instance's barrier gathering a few
-// blocks).
-template <int MINB>
-__global__ void __launch_bounds__(kPcgThreads, MINB) k_solve32_stencil(Batch B) {
+// BT threads per block, MINB resident blocks per SM.  An instance alone runs
+// one 1024-thread block per SM (64 registers, 32 warps in flight, 152
+// arrivals at each grid barrier); measured against one 512-thread block
+// (128 registers, 16 warps) and two of them (64 registers, 304 arrivals) a
+// step's solve took 249.5 / 255.0 / 277.3 us on the 442k-node slab and
+// 2086 / 2373 / 2108 us on the 2.19M-node LV shell.  Batches run two
+// 512-thread blocks per SM (each instance's barrier gathers a few blocks).
+template <int BT, int MINB>
+__global__ void __launch_bounds__(BT, MINB) k_solve32_stencil(Batch B) {
     const Slot S = batch_slot(B);
     Dev& D = *S.D;
     // the step's first residual may already meet the tolerance; a batched
@@ -346,22 +344,26 @@ cudaError_t barrier_timeout_probe(int* status_out) {
     return e;
 }
 
-// blocks of the single-instance (per_sm_two = 0: one block per SM, 128
-// registers) or two-per-SM (64 registers; batches and large instances)
-// solver that fit on one SM at once
-int pcg_blocks_per_sm(int per_sm_two) {
+// Launch shapes of the persistent solve: 1 = one 512-thread block per SM
+// (128 registers), 2 = two 512-thread blocks per SM (64 registers), 3 = one
+// 1024-thread block per SM (64 registers, the arrivals of shape 1 with the
+// warps of shape 2).  Blocks of the shape that fit on one SM at once.
+int pcg_blocks_per_sm(int shape) {
     int occ = 0;
-    const cudaError_t e =
-        per_sm_two ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil<2>, kPcgThreads, 0)
-                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil<1>, kPcgThreads, 0);
+    cudaError_t e;
+    if (shape == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil<1024, 1>, 1024, 0);
+    else if (shape == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil<512, 2>, 512, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil<512, 1>, 512, 0);
     return e == cudaSuccess ? occ : 0;
 }
 
-template <int MINB>
+int pcg_threads_of(int shape) { return shape == 3 ? 1024 : 512; }
+
+template <int BT, int MINB>
 cudaError_t launch_solve(const Batch& B, int grid, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kPcgThreads);
+    cfg.blockDim = dim3(BT);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -369,13 +371,16 @@ cudaError_t launch_solve(const Batch& B, int grid, cudaStream_t s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_solve32_stencil<MINB>, B);
+    return cudaLaunchKernelEx(&cfg, k_solve32_stencil<BT, MINB>, B);
 }
 
-cudaError_t launch_pcg32_batch(const Batch& B, int grid, cudaStream_t s) { return launch_solve<2>(B, grid, s); }
+cudaError_t launch_pcg32_batch(const Batch& B, int grid, cudaStream_t s) { return launch_solve<512, 2>(B, grid, s); }
 
-cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, int per_sm, cudaStream_t s) {
-    return per_sm == 2 ? launch_solve<2>(single_batch(d), grid, s) : launch_solve<1>(single_batch(d), grid, s);
+cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, int shape, cudaStream_t s) {
+    const Batch B = single_batch(d);
+    if (shape == 3) return launch_solve<1024, 1>(B, grid, s);
+    if (shape == 2) return launch_solve<512, 2>(B, grid, s);
+    return launch_solve<512, 1>(B, grid, s);
 }
 
 }  // namespace epk

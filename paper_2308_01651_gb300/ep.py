@@ -79,7 +79,7 @@ class ep_options(C.Structure):
 
 class ep_stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("cg_iters", C.c_int32), ("sweeps", C.c_int32),
-                ("relres", C.c_double), ("op32", C.c_int32), ("solve_per_sm", C.c_int32),
+                ("relres", C.c_double), ("op32", C.c_int32), ("solve_threads", C.c_int32),
                 ("device_bytes", C.c_size_t), ("tune_us_mf", C.c_double), ("tune_us_stencil", C.c_double)]
 
 
@@ -307,7 +307,7 @@ def ep_get_stats(h):
     s = ep_stats()
     _check(lib().ep_get_stats(h, C.byref(s)))
     return dict(step=s.step, cg_iters=s.cg_iters, sweeps=s.sweeps, relres=s.relres, op32=s.op32,
-                solve_per_sm=s.solve_per_sm,
+                solve_threads=s.solve_threads,
                 device_bytes=s.device_bytes, tune_us_mf=s.tune_us_mf, tune_us_stencil=s.tune_us_stencil)
 
 

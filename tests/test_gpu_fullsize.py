@@ -60,8 +60,7 @@ def test_full_size_shell_single_step():
         inst.close()
         assert err <= tol, (precision, op32, err)
         if precision == REF and op32 == ep.EP_OP_STENCIL:
-            # the solve's working set is beyond L2: two blocks per SM
-            assert st["solve_per_sm"] == 2
+            assert st["solve_threads"] == 1024  # one 1024-thread block per SM
         assert st["relres"] <= (1e-12 if precision == FP64 else 1e-10)
 
 
@@ -71,7 +70,7 @@ def test_full_size_slab_propagating_window():
     prob = I.slab_ttp06(T=40.0)
     sim = O.sim_from_problem(prob)
     inst = ep.Instance(prob, precision=REF)
-    assert inst.stats()["solve_per_sm"] == 1  # the solve's working set fits in L2
+    assert inst.stats()["solve_threads"] == 1024
     snaps = []
     every = 100  # 5 ms
     for s in range(0, prob["nsteps"], every):

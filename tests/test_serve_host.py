@@ -108,8 +108,15 @@ def test_background_creation_does_not_stall_residents(monkeypatch):
         return fake_instance(prob, precision, op32)
 
     monkeypatch.setattr(serve.ep, "Instance", slow_instance)
+    step_batch = serve.ep.ep_step_batch
+
+    def slow_step(handles, n):  # a chunk takes 0.5 ms
+        _t.sleep(0.0005)
+        step_batch(handles, n)
+
+    monkeypatch.setattr(serve.ep, "ep_step_batch", slow_step)
     srv = serve.Server(memory_budget=100, max_slots=4, chunk=1)
-    res = srv.run([_req(0, 5, 4000, 0.0, 10), _req(1, 9, 3, 0.01, 20)])
+    res = srv.run([_req(0, 5, 1000, 0.0, 10), _req(1, 9, 3, 0.01, 20)])
     assert sorted(r.rid for r in res) == [0, 1] and FakeInstance.live == 0
     assert all(t != main for t in made_on)
     s = srv.summary()

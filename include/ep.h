@@ -199,7 +199,10 @@ typedef struct {
  * initial residual, whichever comes first (0 -> 1e-6, about the float
  * limit); max_sweeps: refinement sweeps
  * (0 -> 8); op32: FP32 inner operator; cuda_stream: a cudaStream_t to order
- * the instance's work on, or NULL for a stream the library creates. */
+ * the instance's work on, or NULL for a stream the library creates;
+ * ionic_threads: threads per block of the ionic kernel, 64, 128 or 256, or 0
+ * for the create-time autotuner's choice (the block size changes nothing in
+ * the results: one node per thread, no reductions). */
 typedef struct {
     double dt;
     int32_t bdf_order;
@@ -210,6 +213,7 @@ typedef struct {
     int32_t max_sweeps;
     int32_t op32;
     void* cuda_stream;
+    int32_t ionic_threads;
 } ep_options;
 
 /* Per-step counters of the last completed step. */
@@ -224,6 +228,8 @@ typedef struct {
     size_t device_bytes;    /* device memory held by the instance */
     double tune_us_mf;      /* autotuner: matrix-free apply time (us), 0 if not timed */
     double tune_us_stencil; /* autotuner: FP32 stencil apply time (us), 0 if not timed */
+    int32_t ionic_threads;  /* threads per block of the ionic kernel in use */
+    int32_t reserved2;
 } ep_stats;
 
 /* Creates an instance: validates the inputs, copies them to the device,
@@ -248,7 +254,7 @@ ep_status ep_sync(ep_instance* inst);
 /* Advances several instances by n_steps each, all enqueued before any wait;
  * returns the first failing status (inst[k] order).  FP32_REFINED stencil
  * instances share one persistent solve launch, one or more resident thread
- * blocks each: at most two such instances per SM (304 on GB300), EP_EINVAL
+ * blocks each: at most one such instance per SM (152 on GB300), EP_EINVAL
  * beyond. */
 ep_status ep_step_batch(ep_instance* const* insts, int32_t n, int64_t n_steps);
 

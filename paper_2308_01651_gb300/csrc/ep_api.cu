@@ -21,7 +21,7 @@
 #include "ep_tile.cuh"
 
 namespace epk {
-void launch_ionic(Dev* d, const Dev& h, int grid, cudaStream_t s);
+void launch_ionic(Dev* d, const Dev& h, int grid, int threads, cudaStream_t s);
 void launch_assemble(Dev* d, const Dev& h, const AsmParams& P, cudaStream_t s);
 void launch_realpha(Dev* d, const Dev& h, double delta, double alpha_dt, float cmass, cudaStream_t s);
 void launch_rhs64(Dev* d, const Dev& h, int first, int graph, int grid, cudaStream_t s);
@@ -41,7 +41,7 @@ void launch_q2_resid(Dev* d, const Dev& h, int first, int graph, int grid_nodes,
 void launch_realpha_q2(Dev* d, const Dev& h, double alpha_dt, cudaStream_t s);
 void launch_rhs_ff_batch(const Batch& B, int graph, int grid, cudaStream_t s);
 void launch_resid_np(Dev* d, const Dev& h, int graph, int grid, cudaStream_t s);
-cudaError_t launch_pcg32_batch(const Batch& B, int grid, cudaStream_t s);
+cudaError_t launch_pcg32_batch(const Batch& B, int grid, int hint, cudaStream_t s);
 cudaError_t launch_prepace(int model, const uint8_t* cells, int ncell, double dt, long long m0, long long nsteps,
                            long long kp, long long kd, double amp, int bdf, double* st, cudaStream_t s);
 void launch_finish(Dev* d, const Dev& h, int grid, cudaStream_t s);
@@ -54,7 +54,7 @@ cudaError_t mfc_tensor_map(CUtensorMap* tm, const float* g, int NX, int NY, int 
 cudaError_t mfc_prepare(int NX);
 void launch_apply32_mfc(Dev* d, const Dev& h, const CUtensorMap& tm, cudaStream_t s);
 int pcg_blocks_per_sm(int batched);
-cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, int shape, cudaStream_t s);
+cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, int shape, int hint, cudaStream_t s);
 int pcg_threads_of(int shape);
 cudaError_t barrier_timeout_probe(int* status_out);
 cudaError_t residual_norm_noalloc(Dev* d, int grid, int threads, cudaStream_t s, double sums[2]);
@@ -98,10 +98,12 @@ struct ep_instance {
     double alpha_dt_dev = 0;   // alpha/dt the device operators hold
     int grid_nodes = 0;        // grid of the grid-stride node kernels (with reductions)
     int grid_ionic = 0;        // one node per thread
+    int ionic_threads = epk::kIonicThreads;  // its block size (autotuned at create)
     int grid_resid = 0;        // node-parallel residual: 512-thread blocks, two per SM
     int grid_tiles = 0;        // persistent grid of the tiled stencil kernels
     int grid_pcg = 0;          // cooperative grid of the persistent inner solver
     int pcg_shape = 3;         // its launch shape (k_pcg.cu): 1 x 512, 2 x 512 or 1 x 1024 threads per SM
+    int pcg_hint = 0;          // its working set exceeds L2: L2 eviction-priority hints
     ep_status sticky = EP_OK;
     int* bad = nullptr;        // device flag of the assembly
     bool graph_mode = true;    // false: host-driven loops (EP_GRAPH=0), for debugging
@@ -247,6 +249,29 @@ struct Sizes {
     int NX, NY, NZ;   // nodes per direction (Q1)
 };
 
+// Packed refined state (ep_dev.cuh): slot of state k (checkpoint order) --
+// part 0 its float or hi part, part 1 the lo part of a TTP06 concentration --
+// and the address of slot s of node n in a [G][N] float4 array.
+int state_slot(int model, int k, int part) {
+    if (model == EP_MODEL_BO || k < epk::kTTGates) return k;
+    return part == 0 ? k : k + epk::kTTConc;
+}
+
+float* packed_at(float* base, size_t N, int slot, size_t n) {
+    return base + ((size_t)(slot / 4) * N + n) * 4 + slot % 4;
+}
+
+// slot s of every node of a device packed array to or from a host array of N
+cudaError_t get_slot(const float* dev, size_t N, int slot, float* host) {
+    return cudaMemcpy2D(host, sizeof(float), packed_at(const_cast<float*>(dev), N, slot, 0), 4 * sizeof(float),
+                        sizeof(float), N, cudaMemcpyDeviceToHost);
+}
+
+cudaError_t put_slot(float* dev, size_t N, int slot, const float* host) {
+    return cudaMemcpy2D(packed_at(dev, N, slot, 0), 4 * sizeof(float), host, sizeof(float), sizeof(float), N,
+                        cudaMemcpyHostToDevice);
+}
+
 // float-float pair (nearest float, then the nearest float of the rest)
 void split_ff(double x, float& hi, float& lo) {
     hi = (float)x;
@@ -277,7 +302,7 @@ size_t footprint(const Sizes& z) {
     size_t b = 0;
     const size_t L = (size_t)z.levels;
     b += (L + 1) * al(N * 8);             // u_n, u_nm1 (, u_nm2), u_new
-    b += L * al(z.ng32 * N * 4);          // gates (refined)
+    b += L * al(z.ng32 * N * 4);          // packed states (refined)
     b += L * al(z.ns64 * N * 8);          // FP64 states
     b += al(N);                           // cell types
     if (z.regions) b += al(N);            // active-node flags
@@ -372,6 +397,9 @@ ep_status validate(const ep_mesh* mesh, const ep_fibers* fib, const ep_conductiv
     if (opts->precision != EP_PREC_FP64 && opts->precision != EP_PREC_FP32_REFINED)
         return fail(EP_EINVAL, "options.precision");
     if (opts->op32 < EP_OP_AUTO || opts->op32 > EP_OP_STENCIL) return fail(EP_EINVAL, "options.op32");
+    if (opts->ionic_threads != 0 && opts->ionic_threads != 64 && opts->ionic_threads != 128 &&
+        opts->ionic_threads != 256)
+        return fail(EP_EINVAL, "options.ionic_threads must be 0, 64, 128 or 256");
     if (opts->op32 == EP_OP_MATRIX_FREE && mesh->kind == EP_MESH_SHELL && !epk::mfc_supported(mesh->nx + 1))
         return fail(EP_EUNSUPPORTED, "the matrix-free FP32 operator takes shells at most 31 elements across the wall");
     if (mesh->kind == EP_MESH_SLAB_Q2) {
@@ -487,8 +515,9 @@ Sizes sizes_of(const ep_mesh* mesh, const ep_ionic_model* ionic, const ep_option
     }
     if (z.q2) z.op32 = kOpQ2;
     if (z.prec == EP_PREC_FP32_REFINED) {
-        z.ng32 = ionic->model == EP_MODEL_BO ? epk::kBOStates : epk::kTTGates;
-        z.ns64 = ionic->model == EP_MODEL_BO ? 0 : epk::kTTConc;
+        // every state packed, four floats to a 16-byte group (ep_dev.cuh)
+        z.ng32 = 4 * (ionic->model == EP_MODEL_BO ? epk::kBOPacked : epk::kTTPacked);
+        z.ns64 = 0;
     } else {
         z.ng32 = 0;
         z.ns64 = z.ns;
@@ -584,7 +613,7 @@ ep_status build_graph(ep_instance* I) {
     Capture C{s};
     cudaGraphConditionalHandle h_loop = 0, h_outer = 0, h_inner = 0;
     C.chk(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    epk::launch_ionic(I->d, h, I->grid_ionic, s);
+    epk::launch_ionic(I->d, h, I->grid_ionic, I->ionic_threads, s);
     if (h.prec == EP_PREC_FP64) epk::launch_rhs64(I->d, h, 1, 1, I->grid_tiles, s);
     else if (h.q2) epk::launch_q2_resid(I->d, h, 1, 1, I->grid_nodes, s);
     else epk::launch_rhs_ff(I->d, h, 1, I->grid_resid, s);
@@ -602,7 +631,7 @@ ep_status build_graph(ep_instance* I) {
         // every refinement sweep [inner PCG, u += delta, float-float residual,
         // decision] in one persistent launch (it returns at once when the
         // first residual met the tolerance)
-        C.chk(epk::launch_pcg32(I->d, h, I->grid_pcg, I->pcg_shape, s));
+        C.chk(epk::launch_pcg32(I->d, h, I->grid_pcg, I->pcg_shape, I->pcg_hint, s));
     } else {
         C.chk(add_while(s, &h_outer, &body));
         if (C.err == cudaSuccess) {
@@ -661,7 +690,7 @@ ep_status step_host(ep_instance* I) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         return e;
     };
-    timed(I, K_IONIC, [&] { epk::launch_ionic(d, h, I->grid_ionic, s); });
+    timed(I, K_IONIC, [&] { epk::launch_ionic(d, h, I->grid_ionic, I->ionic_threads, s); });
     timed(I, K_RHS, [&] {
         if (h.prec == EP_PREC_FP64) epk::launch_rhs64(d, h, 1, 0, I->grid_tiles, s);
         else if (h.q2) epk::launch_q2_resid(d, h, 1, 0, I->grid_nodes, s);
@@ -682,7 +711,7 @@ ep_status step_host(ep_instance* I) {
         if (h.op32 == EP_OP_STENCIL) {
             // the whole solve in one persistent launch
             cudaError_t pe = cudaSuccess;
-            timed(I, K_PCG32, [&] { pe = epk::launch_pcg32(d, h, I->grid_pcg, I->pcg_shape, s); });
+            timed(I, K_PCG32, [&] { pe = epk::launch_pcg32(d, h, I->grid_pcg, I->pcg_shape, I->pcg_hint, s); });
             CUDA_TRY(pe);
             f = 0;
         }
@@ -757,6 +786,78 @@ ep_status autotune_op32(ep_instance* I) {
     cudaEventDestroy(b);
     h.op32 = best;
     CUDA_TRY(cudaMemcpy(&I->d->op32, &h.op32, sizeof(int), cudaMemcpyHostToDevice));
+    return EP_OK;
+}
+
+// Block size of the ionic kernel, per (model, precision, time levels, size
+// class): the first instance of a class times 64, 128 and 256 threads per
+// block on its own initial state (CUDA events on its stream, after warm-up)
+// and the class keeps the fastest.  At step 0 the kernel reads only level n
+// (BDF1 step) and writes the new level into an older slot and the step's
+// scratch vectors, so the runs change nothing but that slot, which is
+// restored from level n afterwards.  The choice changes no result.
+static std::mutex g_tune_mu;
+static std::vector<std::pair<long long, int>> g_tune_ionic;
+
+ep_status autotune_ionic(ep_instance* I) {
+    const Dev& h = I->h;
+    int cls = 0;
+    while ((2ll << cls) <= (long long)h.N) ++cls;
+    const long long key = ((long long)h.model * 4 + h.prec) * 4096 + (long long)(h.u_nm2 ? 3 : 2) * 64 + cls;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto& kv : g_tune_ionic)
+            if (kv.first == key) {
+                I->ionic_threads = kv.second;
+                I->grid_ionic = (h.N + kv.second - 1) / kv.second;
+                return EP_OK;
+            }
+    }
+    cudaStream_t s = I->stream;
+    cudaEvent_t a, b;
+    CUDA_TRY(cudaEventCreate(&a));
+    CUDA_TRY(cudaEventCreate(&b));
+    const int cands[3] = {64, 128, 256};
+    float best_ms = 1e30f;
+    int best = epk::kIonicThreads;
+    for (int bt : cands) {
+        const int grid = (h.N + bt - 1) / bt;
+        for (int w = 0; w < 2; ++w) epk::launch_ionic(I->d, h, grid, bt, s);
+        cudaEventRecord(a, s);
+        for (int r = 0; r < 5; ++r) epk::launch_ionic(I->d, h, grid, bt, s);
+        cudaEventRecord(b, s);
+        cudaError_t e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            return fail(EP_ECUDA, std::string("ionic autotune: ") + cudaGetErrorString(e));
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = bt;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    // the older time levels back to the initial state (level n)
+    const size_t N = (size_t)h.N;
+    if (h.g32_n) {
+        const size_t fb = (size_t)(h.model == EP_MODEL_BO ? epk::kBOPacked : epk::kTTPacked) * 16 * N;
+        for (float* d : {h.g32_nm1, h.g32_nm2})
+            if (d) CUDA_TRY(cudaMemcpyAsync(d, h.g32_n, fb, cudaMemcpyDeviceToDevice, s));
+    }
+    if (h.s64_n) {
+        const size_t db = (size_t)h.ns * 8 * N;
+        for (double* d : {h.s64_nm1, h.s64_nm2})
+            if (d) CUDA_TRY(cudaMemcpyAsync(d, h.s64_n, db, cudaMemcpyDeviceToDevice, s));
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    I->ionic_threads = best;
+    I->grid_ionic = (h.N + best - 1) / best;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_ionic.emplace_back(key, best);
     return EP_OK;
 }
 
@@ -1093,9 +1194,17 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         for (double* d : {h.u_nm1, h.u_nm2, h.u_new})
             if (d) CUDA_TRY(cudaMemcpy(d, uv.data(), N * 8, cudaMemcpyHostToDevice));
         if (z.ng32) {
-            std::vector<float> g(z.ng32 * N);
-            for (int k = 0; k < z.ng32; ++k)
-                for (size_t n = 0; n < N; ++n) g[k * N + n] = (float)init(n, 1 + k);
+            // packed refined states: gates (and BO states) as float, TTP06
+            // concentrations as float-float (hi and lo slots)
+            std::vector<float> g(z.ng32 * N, 0.0f);
+            const int ngate = h.model == EP_MODEL_BO ? epk::kBOStates : epk::kTTGates;
+            for (size_t n = 0; n < N; ++n)
+                for (int k = 0; k < z.ns; ++k) {
+                    float hi = (float)init(n, 1 + k), lo = 0.0f;
+                    if (k >= ngate) split_ff(init(n, 1 + k), hi, lo);
+                    *packed_at(g.data(), N, state_slot(h.model, k, 0), n) = hi;
+                    if (k >= ngate) *packed_at(g.data(), N, state_slot(h.model, k, 1), n) = lo;
+                }
             for (float* d : {h.g32_n, h.g32_nm1, h.g32_nm2})
                 if (d) CUDA_TRY(cudaMemcpy(d, g.data(), g.size() * 4, cudaMemcpyHostToDevice));
         }
@@ -1105,19 +1214,6 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
                 for (size_t n = 0; n < N; ++n) c[k * N + n] = init(n, 1 + k);
             for (double* d : {h.s64_n, h.s64_nm1, h.s64_nm2})
                 if (d) CUDA_TRY(cudaMemcpy(d, c.data(), c.size() * 8, cudaMemcpyHostToDevice));
-        }
-        if (z.ns64 && ref) {
-            // float-float concentrations: [hi][k][N] then [lo][k][N]
-            std::vector<float> c(2 * z.ns64 * N);
-            for (int k = 0; k < z.ns64; ++k)
-                for (size_t n = 0; n < N; ++n) {
-                    float hi, lo;
-                    split_ff(init(n, 1 + z.ng32 + k), hi, lo);
-                    c[k * N + n] = hi;
-                    c[(z.ns64 + k) * N + n] = lo;
-                }
-            for (double* d : {h.s64_n, h.s64_nm1, h.s64_nm2})
-                if (d) CUDA_TRY(cudaMemcpy(d, c.data(), c.size() * 4, cudaMemcpyHostToDevice));
         }
         if (ref) {
             std::vector<float> fh(N), fl(N), fb(N, -INFINITY);
@@ -1252,7 +1348,8 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     // 512-thread blocks per SM; the persistent solve: as many blocks as fit
     // (one per SM alone)
     I->grid_nodes = std::max(1, std::min(blocks, 4 * sms));
-    I->grid_ionic = (int)((N + epk::kIonicThreads - 1) / epk::kIonicThreads);
+    I->ionic_threads = opts->ionic_threads ? opts->ionic_threads : epk::kIonicThreads;
+    I->grid_ionic = (int)((N + I->ionic_threads - 1) / I->ionic_threads);
     I->grid_resid = std::max(1, std::min((int)((N + epk::kResidThreads - 1) / epk::kResidThreads), 2 * sms));
     I->grid_tiles = std::max(1, std::min(epk::st_tiles(h), 2 * sms));
     if (ref) {
@@ -1261,6 +1358,13 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         // (measured fastest of the three shapes on the 442k-node slab and
         // the 2.19M-node shell, k_pcg.cu)
         I->pcg_shape = 3;
+        // L2 policies when the solve's working set (the FP32 operator's 14
+        // couplings and the seven CG vectors, 84 B a node) exceeds L2:
+        // measured on the 2.19M-node shell 1871 against 2044 us a step's
+        // solve, on the L2-resident 442k-node slab 300 against 248 us
+        int l2 = 0;
+        CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+        I->pcg_hint = (double)N * 84.0 > (double)l2 ? 1 : 0;
         const int occ = std::min(epk::pcg_blocks_per_sm(I->pcg_shape), I->pcg_shape == 2 ? 2 : 1);
         if (occ <= 0) return fail(EP_ECUDA, "occupancy query of the persistent solver failed");
         const int bt = epk::pcg_threads_of(I->pcg_shape);
@@ -1270,6 +1374,10 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     if (!ref) h.op32 = 0;  // no FP32 operator in the FP64 path
     if (ref && !z.q2 && h.op32 == EP_OP_AUTO) {
         ep_status st2 = autotune_op32(I);
+        if (st2 != EP_OK) return st2;
+    }
+    if (opts->ionic_threads == 0) {
+        ep_status st2 = autotune_ionic(I);
         if (st2 != EP_OK) return st2;
     }
     const char* env = std::getenv("EP_GRAPH");
@@ -1336,7 +1444,7 @@ ep_status build_plan(BatchPlan* P) {
     int dev = 0, sms = 152;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int occ = epk::pcg_blocks_per_sm(1);
+    const int occ = epk::pcg_blocks_per_sm(3);  // the batched solve: 1024-thread blocks, as alone
     if (occ <= 0) return fail(EP_ECUDA, "occupancy query of the persistent solver failed");
     const int cap = sms * occ;
     if (n > cap) return fail(EP_EINVAL, "batch larger than the persistent solver's resident blocks");
@@ -1415,7 +1523,10 @@ ep_status build_plan(BatchPlan* P) {
     epk::launch_rhs_ff_batch(Br, 0, s_rhs.back(), s);
     // every instance's refinement sweeps in one persistent launch (the
     // blocks of an instance that needs no sweep return at once)
-    C.chk(epk::launch_pcg32_batch(Bp, s_pcg.back(), s));
+    // no L2 eviction-priority hints in batches: their instances are each
+    // L2-sized and the hints cost the 96-slab batch 9 % (1.06e9 against
+    // 1.17e9 DoF-steps/s)
+    C.chk(epk::launch_pcg32_batch(Bp, s_pcg.back(), 0, s));
     cudaGraph_t g = nullptr;
     C.chk(cudaStreamEndCapture(s, &g));
     C.chk(cudaGetLastError());
@@ -1780,20 +1891,17 @@ ep_status ep_save_state(const ep_instance* I, void* buf, size_t bytes) {
     for (int lvl = 0; lvl < L; ++lvl) CUDA_TRY(get(lvl_u(t, lvl), o + (size_t)lvl * N));
     const bool ref = I->h.prec == EP_PREC_FP32_REFINED;
     const int ng32 = ref ? (I->h.model == EP_MODEL_BO ? 3 : epk::kTTGates) : 0;
-    const int nc = ns - ng32;  // refined: float-float concentrations
     std::vector<float> f(N), fl(N);
     for (int lvl = 0; lvl < L; ++lvl) {
         double* dst = o + (size_t)L * N + (size_t)lvl * ns * N;
         for (int k = 0; k < ns; ++k) {
             if (k < ng32) {
-                const float* src = lvl_g(t, lvl) + (size_t)k * N;
-                CUDA_TRY(cudaMemcpy(f.data(), src, N * 4, cudaMemcpyDeviceToHost));
+                CUDA_TRY(get_slot(lvl_g(t, lvl), N, state_slot(I->h.model, k, 0), f.data()));
                 for (size_t n = 0; n < N; ++n) tmp[n] = f[n];
                 std::memcpy(dst + (size_t)k * N, tmp.data(), N * 8);
             } else if (ref) {
-                const float* src = reinterpret_cast<const float*>(lvl_s(t, lvl));
-                CUDA_TRY(cudaMemcpy(f.data(), src + (size_t)(k - ng32) * N, N * 4, cudaMemcpyDeviceToHost));
-                CUDA_TRY(cudaMemcpy(fl.data(), src + (size_t)(nc + k - ng32) * N, N * 4, cudaMemcpyDeviceToHost));
+                CUDA_TRY(get_slot(lvl_g(t, lvl), N, state_slot(I->h.model, k, 0), f.data()));
+                CUDA_TRY(get_slot(lvl_g(t, lvl), N, state_slot(I->h.model, k, 1), fl.data()));
                 for (size_t n = 0; n < N; ++n) tmp[n] = (double)f[n] + (double)fl[n];
                 std::memcpy(dst + (size_t)k * N, tmp.data(), N * 8);
             } else {
@@ -1822,10 +1930,13 @@ ep_status ep_save_state(const ep_instance* I, void* buf, size_t bytes) {
             CUDA_TRY(getf(lvl_uh(t, lvl)));
             CUDA_TRY(getf(lvl_ul(t, lvl)));
         }
-        for (int lvl = 0; lvl < L; ++lvl) {
-            const float* c = reinterpret_cast<const float*>(lvl_s(t, lvl));
-            for (int k = 0; k < 2 * nc; ++k) CUDA_TRY(getf(c + (size_t)k * N));
-        }
+        for (int lvl = 0; lvl < L; ++lvl)
+            for (int part = 0; part < 2; ++part)
+                for (int k = ng32; k < ns; ++k) {
+                    CUDA_TRY(get_slot(lvl_g(t, lvl), N, state_slot(I->h.model, k, part), f.data()));
+                    std::memcpy(q, f.data(), N * 4);
+                    q += N * 4;
+                }
         for (int lvl = 0; lvl < L; ++lvl) {
             CUDA_TRY(getf(lvl_yh(t, lvl)));
             CUDA_TRY(getf(lvl_yl(t, lvl)));
@@ -1863,7 +1974,6 @@ ep_status ep_load_state(ep_instance* I, const void* buf, size_t bytes) {
     for (int lvl = 0; lvl < L; ++lvl) CUDA_TRY(put(lvl_u(t, lvl), o + (size_t)lvl * N));
     const bool ref = I->h.prec == EP_PREC_FP32_REFINED;
     const int ng32 = ref ? (I->h.model == EP_MODEL_BO ? 3 : epk::kTTGates) : 0;
-    const int nc = ns - ng32;  // refined: float-float concentrations
     std::vector<float> f(N), fl(N);
     for (int lvl = 0; lvl < L; ++lvl) {
         const double* src = o + (size_t)L * N + (size_t)lvl * ns * N;
@@ -1871,13 +1981,12 @@ ep_status ep_load_state(ep_instance* I, const void* buf, size_t bytes) {
             if (k < ng32) {
                 std::memcpy(tmp.data(), src + (size_t)k * N, N * 8);
                 for (size_t n = 0; n < N; ++n) f[n] = (float)tmp[n];
-                CUDA_TRY(cudaMemcpy(lvl_g(t, lvl) + (size_t)k * N, f.data(), N * 4, cudaMemcpyHostToDevice));
+                CUDA_TRY(put_slot(lvl_g(t, lvl), N, state_slot(I->h.model, k, 0), f.data()));
             } else if (ref) {
                 std::memcpy(tmp.data(), src + (size_t)k * N, N * 8);
                 for (size_t n = 0; n < N; ++n) split_ff(tmp[n], f[n], fl[n]);
-                float* d = reinterpret_cast<float*>(lvl_s(t, lvl));
-                CUDA_TRY(cudaMemcpy(d + (size_t)(k - ng32) * N, f.data(), N * 4, cudaMemcpyHostToDevice));
-                CUDA_TRY(cudaMemcpy(d + (size_t)(nc + k - ng32) * N, fl.data(), N * 4, cudaMemcpyHostToDevice));
+                CUDA_TRY(put_slot(lvl_g(t, lvl), N, state_slot(I->h.model, k, 0), f.data()));
+                CUDA_TRY(put_slot(lvl_g(t, lvl), N, state_slot(I->h.model, k, 1), fl.data()));
             } else {
                 CUDA_TRY(put(lvl_s(t, lvl) + (size_t)k * N, src + (size_t)k * N));
             }
@@ -1933,10 +2042,13 @@ ep_status ep_load_state(ep_instance* I, const void* buf, size_t bytes) {
             CUDA_TRY(putf(lvl_uh(t, lvl)));
             CUDA_TRY(putf(lvl_ul(t, lvl)));
         }
-        for (int lvl = 0; lvl < L; ++lvl) {
-            float* c = reinterpret_cast<float*>(lvl_s(t, lvl));
-            for (int k = 0; k < 2 * nc; ++k) CUDA_TRY(putf(c + (size_t)k * N));
-        }
+        for (int lvl = 0; lvl < L; ++lvl)
+            for (int part = 0; part < 2; ++part)
+                for (int k = ng32; k < ns; ++k) {
+                    std::memcpy(f.data(), q, N * 4);
+                    q += N * 4;
+                    CUDA_TRY(put_slot(lvl_g(t, lvl), N, state_slot(I->h.model, k, part), f.data()));
+                }
         for (int lvl = 0; lvl < L; ++lvl) {
             CUDA_TRY(putf(lvl_yh(t, lvl)));
             CUDA_TRY(putf(lvl_yl(t, lvl)));
@@ -1962,6 +2074,8 @@ ep_status ep_get_stats(const ep_instance* I, ep_stats* out) {
     out->device_bytes = I->bytes;
     out->tune_us_mf = 1e3 * I->tune_ms[EP_OP_MATRIX_FREE];
     out->tune_us_stencil = 1e3 * I->tune_ms[EP_OP_STENCIL];
+    out->ionic_threads = I->ionic_threads;
+    out->reserved2 = 0;
     return EP_OK;
 }
 

@@ -20,6 +20,13 @@ constexpr int kSlots = 14;
 constexpr int kTTGates = 13;  // m h j xr1 xr2 xs s r d f f2 fCass RR
 constexpr int kTTConc = 5;    // Cai CaSR CaSS Nai Ki
 constexpr int kBOStates = 3;  // v w s
+// Refined ionic states, one time level: packed four to a 16-byte group,
+// group-major ([G][N] float4), so that a thread moves its node's state with G
+// 128-bit accesses.  TTP06 (G = 6): slots 0..12 the gates, 13..17 the
+// concentrations' float-float hi parts, 18..22 their lo parts, 23 unused.
+// Bueno-Orovio (G = 1): v, w, s, unused.
+constexpr int kTTPacked = 6;
+constexpr int kBOPacked = 1;
 
 // largest block of a reducing kernel (power of two)
 constexpr int kMaxBlock = 512;
@@ -78,11 +85,9 @@ struct Dev {
     // ---- state ---------------------------------------------------------------
     double *u_n, *u_nm1, *u_new;
     double* u_nm2;              // level n-2 (BDF3 instances only, else NULL)
-    float *g32_n, *g32_nm1;     // FP32 gates [ng][N] (FP32_REFINED)
+    float *g32_n, *g32_nm1;     // FP32_REFINED: every state, packed ([G][N] float4, see kTTPacked)
     float* g32_nm2;             // level n-2 (BDF3)
-    double *s64_n, *s64_nm1;    // FP64: all states [ns][N] in double.  FP32_REFINED:
-                                // the TTP06 concentrations as float-float, the
-                                // memory read as float [2][5][N] (hi parts, then lo)
+    double *s64_n, *s64_nm1;    // FP64: all states [ns][N] in double (NULL when refined)
     double* s64_nm2;            // level n-2 of the same (BDF3)
     const uint8_t* cell;
     const uint8_t* active;      // per node, 0 = excluded from the simulation (NULL: all active)

@@ -147,6 +147,53 @@ __device__ __forceinline__ float sym_coupling(const float* __restrict__ A, long 
     return (MASK && (fe & off_bits(t))) ? 0.f : c;
 }
 
+// ---- L2 eviction-priority hints -------------------------------------------
+// An access policy (createpolicy) attached to loads and stores: lines fetched
+// under evict_last are kept in L2 in preference to others, evict_first lines
+// are dropped first.  The persistent solve streams the operator's couplings
+// (read once per pass) under evict_first and keeps its CG vectors under
+// evict_last, so that the vectors of an instance whose whole working set
+// exceeds L2 stay resident across passes.
+__device__ __forceinline__ unsigned long long l2_policy_evict_last() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ unsigned long long l2_policy_evict_first() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ float ld_pol(const float* a, unsigned long long pol) {
+    float v;
+    asm("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ void st_pol(float* a, float v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+}
+
+// FP32 row of node n as row32_sym, couplings read under policy pa and the
+// vector under pv
+__device__ __forceinline__ float row32_sym_pol(const float* __restrict__ A, long long cs,
+                                               const float* __restrict__ x, int n, const NbrOff& o,
+                                               unsigned int fe, unsigned long long pa, unsigned long long pv) {
+    float acc = 0.f;
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+        const int m = n + o.x[t % 3] + o.y[(t / 3) % 3] + o.z[t / 9];
+        float c;
+        if (t == 13) c = ld_pol(A + n, pa);
+        else if (t > 13) c = ld_pol(A + (long long)(t - 13) * cs + n, pa);
+        else c = (fe & off_bits(t)) ? 0.f : ld_pol(A + (long long)(13 - t) * cs + m, pa);
+        acc = fmaf(c, ld_pol(x + m, pv), acc);
+    }
+    return acc;
+}
+
 // FP32 row with neighbour values staged in shared memory (tiled kernels):
 // sum_t c(t) x(h + dh(t)), t = 0..26 in order; sidx[h'] is the node index
 // at halo position h' (-1 outside the mesh)

@@ -22,6 +22,11 @@
 // float-float pairs, the BDF combinations are formed in float-float, and the
 // concentrations' BDF2 update is written as c_n + [(c_n - c_{n-1})/3 +
 // (2/3) dt r] so that only a small increment is rounded to float.
+//
+// Refined states are packed four to a 16-byte group, group-major ([G][N]
+// float4 per time level; ep_dev.cuh): one thread per node reads and writes its
+// whole state with G 128-bit accesses, each coalesced across the warp (a
+// warp moves 512 contiguous bytes per access).
 #include "ep_dev.cuh"
 #include "ionic_models.cuh"
 #include "ep_ff.cuh"
@@ -168,10 +173,31 @@ struct Levels {
     G* out;
 };
 
+// one time level of a node's packed refined state (G float4 groups)
+template <int G>
+__device__ __forceinline__ void ld_packed(const float* base, size_t N, int n, float (&v)[4 * G]) {
+    const float4* __restrict__ p = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const float4 q = p[(size_t)g * N + n];
+        v[4 * g] = q.x;
+        v[4 * g + 1] = q.y;
+        v[4 * g + 2] = q.z;
+        v[4 * g + 3] = q.w;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void st_packed(float* base, size_t N, int n, const float (&v)[4 * G]) {
+    float4* __restrict__ p = reinterpret_cast<float4*>(base);
+#pragma unroll
+    for (int g = 0; g < G; ++g) p[(size_t)g * N + n] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+}
+
 // G: arithmetic/storage type of the gates (float when refined, double in the
 // FP64 path).
-template <typename G>
-__global__ void __launch_bounds__(kIonicThreads) k_ionic_bo(Batch B) {
+template <typename G, int BT>
+__global__ void __launch_bounds__(BT) k_ionic_bo(Batch B) {
     const Slot S = batch_slot(B);
     const Dev& D = *S.D;
     const StepConsts c = step_consts(D);
@@ -201,12 +227,26 @@ __global__ void __launch_bounds__(kIonicThreads) k_ionic_bo(Batch B) {
             uEg = uE;
         }
         G wB[3], wn0[3];
+        if constexpr (sizeof(G) == 4) {
+            // packed: v w s in one 16-byte group per level
+            float s0[4], s1[4] = {0.f, 0.f, 0.f, 0.f}, s2[4] = {0.f, 0.f, 0.f, 0.f};
+            ld_packed<kBOPacked>(D.g32_n, (size_t)N, n, s0);
+            if (c.order > 1) ld_packed<kBOPacked>(D.g32_nm1, (size_t)N, n, s1);
+            if (c.order > 2) ld_packed<kBOPacked>(D.g32_nm2, (size_t)N, n, s2);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const size_t o = (size_t)k * N + n;
-            G E;
-            wn0[k] = L.n[o];
-            bdf_comb<G>(c.order, wn0[k], c.order > 1 ? L.m[o] : G(0), c.order > 2 ? L.m2[o] : G(0), wB[k], E);
+            for (int k = 0; k < 3; ++k) {
+                G E;
+                wn0[k] = s0[k];
+                bdf_comb<G>(c.order, s0[k], s1[k], s2[k], wB[k], E);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const size_t o = (size_t)k * N + n;
+                G E;
+                wn0[k] = L.n[o];
+                bdf_comb<G>(c.order, wn0[k], c.order > 1 ? L.m[o] : G(0), c.order > 2 ? L.m2[o] : G(0), wB[k], E);
+            }
         }
         // an excluded node: states held, no currents
         const bool on = !D.active || D.active[n];
@@ -214,9 +254,13 @@ __global__ void __launch_bounds__(kIonicThreads) k_ionic_bo(Batch B) {
         G a[3], b[3], w1[3];
         BO<G>::rates(uEg, a, b);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            w1[k] = on ? (wB[k] + dtg * a[k]) / (alg + dtg * b[k]) : wn0[k];
-            L.out[(size_t)k * N + n] = w1[k];
+        for (int k = 0; k < 3; ++k) w1[k] = on ? (wB[k] + dtg * a[k]) / (alg + dtg * b[k]) : wn0[k];
+        if constexpr (sizeof(G) == 4) {
+            const float o4[4] = {w1[0], w1[1], w1[2], 0.f};
+            st_packed<kBOPacked>(reinterpret_cast<float*>(L.out), (size_t)N, n, o4);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) L.out[(size_t)k * N + n] = w1[k];
         }
         const G I = on ? BO<G>::iion(uEg, w1[0], w1[1], w1[2]) : G(0);
         if constexpr (sizeof(G) == 4) store_vu_ff(D, n, ubh, ubl, ueh, uel, on ? applied_f(D, c, n) - I : 0.f);
@@ -240,68 +284,54 @@ __device__ __forceinline__ void ionic_tt_nodes(const Slot& S, const Dev& D, cons
     for (int n = S.blk * blockDim.x + threadIdx.x; n < N; n += S.nblk * blockDim.x) {
         const int cell = D.cell[n];
         if constexpr (sizeof(G) == 4) {
-            // ---- refined: float gates, float-float concentrations and potentials
-            // the new level goes to the n-2 slot (LV3) or over level n-1;
-            // one pointer per array, so that restrict holds
-            const float* __restrict__ gn = D.g32_n;
-            float* __restrict__ gm = D.g32_nm1;
-            float* __restrict__ gm2 = D.g32_nm2;
-            float* const go = LV3 ? gm2 : gm;  // based on gm or gm2
-            const float* __restrict__ chn = reinterpret_cast<const float*>(D.s64_n);
-            float* __restrict__ chm = reinterpret_cast<float*>(D.s64_nm1);
-            float* __restrict__ chm2 = reinterpret_cast<float*>(D.s64_nm2);
-            float* const cho = LV3 ? chm2 : chm;
-            const size_t LO = (size_t)kTTConc * N;  // lo parts follow the hi parts
+            // ---- refined: float gates, float-float concentrations and
+            // potentials, the levels packed (slots: 13 gates, 5 concentration
+            // hi parts, 5 lo parts); the new level goes to the n-2 slot (LV3)
+            // or over level n-1, after every level has been read
+            constexpr int GH = kTTGates, GL = kTTGates + kTTConc;  // first hi, lo slot
+            float* const out = LV3 ? D.g32_nm2 : D.g32_nm1;
             float ubh, ubl, ueh, uel;
             u_bdf_ff(D, ord, n, fin, t_fin, ubh, ubl, ueh, uel);
             if (D.active && !D.active[n]) {
                 // excluded from the simulation: states held, no currents
-#pragma unroll
-                for (int k = 0; k < kTTGates; ++k) go[(size_t)k * N + n] = gn[(size_t)k * N + n];
-#pragma unroll
-                for (int k = 0; k < kTTConc; ++k) {
-                    cho[(size_t)k * N + n] = chn[(size_t)k * N + n];
-                    cho[LO + (size_t)k * N + n] = chn[LO + (size_t)k * N + n];
-                }
+                float t[4 * kTTPacked];
+                ld_packed<kTTPacked>(D.g32_n, (size_t)N, n, t);
+                st_packed<kTTPacked>(out, (size_t)N, n, t);
                 store_vu_ff(D, n, ubh, ubl, ueh, uel, 0.f);
                 continue;
             }
+            float s0[4 * kTTPacked], s1[4 * kTTPacked], s2[4 * kTTPacked];
+            ld_packed<kTTPacked>(D.g32_n, (size_t)N, n, s0);
+            if (ord > 1) ld_packed<kTTPacked>(D.g32_nm1, (size_t)N, n, s1);
+            if (ord > 2) ld_packed<kTTPacked>(D.g32_nm2, (size_t)N, n, s2);
             float gB[kTTGates], gE[kTTGates];
-            float ch[kTTConc], cl[kTTConc], d1[kTTConc], d2[kTTConc], cE[kTTConc];
+            float d1[kTTConc], d2[kTTConc], cE[kTTConc];
 #pragma unroll
             for (int k = 0; k < kTTConc; ++k) {
-                const size_t o = (size_t)k * N + n;
-                ch[k] = chn[o];
-                cl[k] = chn[LO + o];
                 d1[k] = d2[k] = 0.f;
                 // differences of consecutive levels: the hi parts are close,
                 // so these are (nearly) exact
                 float dh, dl;
                 if (ord > 1) {
-                    ff_sub(ch[k], cl[k], chm[o], chm[LO + o], dh, dl);
+                    ff_sub(s0[GH + k], s0[GL + k], s1[GH + k], s1[GL + k], dh, dl);
                     d1[k] = dh;
                 }
                 if (ord > 2) {
-                    ff_sub(chm[o], chm[LO + o], chm2[o], chm2[LO + o], dh, dl);
+                    ff_sub(s1[GH + k], s1[GL + k], s2[GH + k], s2[GL + k], dh, dl);
                     d2[k] = dh;
                 }
                 // c_EXT = c_n + (order 2) d1 + (order 3) 2 d1 - d2
-                cE[k] = ord == 3 ? ch[k] + (2.f * d1[k] - d2[k]) : ch[k] + d1[k];
+                cE[k] = ord == 3 ? s0[GH + k] + (2.f * d1[k] - d2[k]) : s0[GH + k] + d1[k];
             }
 #pragma unroll
-            for (int k = 0; k < kTTGates; ++k) {
-                const size_t o = (size_t)k * N + n;
-                bdf_comb<float>(ord, gn[o], ord > 1 ? gm[o] : 0.f, ord > 2 ? gm2[o] : 0.f, gB[k], gE[k]);
-            }
+            for (int k = 0; k < kTTGates; ++k)
+                bdf_comb<float>(ord, s0[k], ord > 1 ? s1[k] : 0.f, ord > 2 ? s2[k] : 0.f, gB[k], gE[k]);
             float a[kTTGates], b[kTTGates], r[kTTConc];
             TT<float>::rates(cell, ueh, gE, cE[0], cE[1], cE[2], cE[3], cE[4], a, b, r);
-            float g1[kTTGates];
+            float o[4 * kTTPacked];
+            o[4 * kTTPacked - 1] = 0.f;
 #pragma unroll
-            for (int k = 0; k < kTTGates; ++k) {
-                g1[k] = (gB[k] + dtg * a[k]) / (alg + dtg * b[k]);
-                go[(size_t)k * N + n] = g1[k];
-            }
-            float c1[kTTConc];
+            for (int k = 0; k < kTTGates; ++k) o[k] = (gB[k] + dtg * a[k]) / (alg + dtg * b[k]);
             const float dta = (float)c.dt_alpha;
 #pragma unroll
             for (int k = 0; k < kTTConc; ++k) {
@@ -312,14 +342,11 @@ __device__ __forceinline__ void ionic_tt_nodes(const Slot& S, const Dev& D, cons
                 if (ord == 2) hist = d1[k] * (1.f / 3.f);
                 else if (ord == 3) hist = fmaf(7.f / 11.f, d1[k], -(2.f / 11.f) * d2[k]);
                 const float inc = fmaf(dta, r[k], hist);
-                float h1, l1;
-                ff_add_f(ch[k], cl[k], inc, h1, l1);
-                cho[(size_t)k * N + n] = h1;
-                cho[LO + (size_t)k * N + n] = l1;
-                c1[k] = h1;
+                ff_add_f(s0[GH + k], s0[GL + k], inc, o[GH + k], o[GL + k]);
             }
+            st_packed<kTTPacked>(out, (size_t)N, n, o);
             TT<float>::Cur cur;
-            TT<float>::currents(cell, ueh, g1, c1[0], c1[2], c1[3], c1[4], cur);
+            TT<float>::currents(cell, ueh, o, o[GH + 0], o[GH + 2], o[GH + 3], o[GH + 4], cur);
             const float I = TT<float>::iion_of(cur);
             store_vu_ff(D, n, ubh, ubl, ueh, uel, applied_f(D, c, n) - I);
         } else {
@@ -366,9 +393,10 @@ __device__ __forceinline__ void ionic_tt_nodes(const Slot& S, const Dev& D, cons
     }
 }
 
-// BDF3 instances (three levels)
-template <typename G>
-__global__ void __launch_bounds__(kIonicThreads, sizeof(G) == 4 ? 6 : 1) k_ionic_tt3(Batch B) {
+// BDF3 instances (three levels; the refined one holds three packed levels
+// of a node at once: 128 registers, four 128-thread blocks per SM)
+template <typename G, int BT>
+__global__ void __launch_bounds__(BT, sizeof(G) == 4 ? 512 / BT : 1) k_ionic_tt3(Batch B) {
     const Slot S = batch_slot(B);
     const Dev& D = *S.D;
     const StepConsts c = step_consts(D);
@@ -379,10 +407,11 @@ __global__ void __launch_bounds__(kIonicThreads, sizeof(G) == 4 ? 6 : 1) k_ionic
 
 // Instances with two levels (BDF1, BDF2): the new level overwrites level n-1
 // in place.  A kernel of its own, written for orders 1 and 2 only, so that
-// its register allocation is not shaped by the three-level variant (this
-// one sits at the 80-register cap of three resident blocks per SM).
-template <typename G>
-__global__ void __launch_bounds__(kIonicThreads, sizeof(G) == 4 ? 6 : 1) k_ionic_tt2(Batch B) {
+// its register allocation is not shaped by the three-level variant: the
+// refined one fits the 80-register cap of six resident 128-thread blocks
+// per SM without spills (the three-level one takes 128 registers, four).
+template <typename G, int BT>
+__global__ void __launch_bounds__(BT, sizeof(G) == 4 ? 768 / BT : 1) k_ionic_tt2(Batch B) {
     const Slot S = batch_slot(B);
     const Dev& D = *S.D;
     const StepConsts c = step_consts(D);
@@ -394,80 +423,66 @@ __global__ void __launch_bounds__(kIonicThreads, sizeof(G) == 4 ? 6 : 1) k_ionic
     for (int n = S.blk * blockDim.x + threadIdx.x; n < N; n += S.nblk * blockDim.x) {
         const int cell = D.cell[n];
         if constexpr (sizeof(G) == 4) {
-            // ---- refined: float gates, float-float concentrations and potentials
-            const float* __restrict__ gn = D.g32_n;
-            float* __restrict__ gm = D.g32_nm1;
-            const float* __restrict__ chn = reinterpret_cast<const float*>(D.s64_n);
-            float* __restrict__ chm = reinterpret_cast<float*>(D.s64_nm1);
-            const size_t LO = (size_t)kTTConc * N;  // lo parts follow the hi parts
+            // ---- refined: float gates, float-float concentrations and
+            // potentials, the levels packed (slots: 13 gates, 5 concentration
+            // hi parts, 5 lo parts); the new level overwrites level n-1 after
+            // both levels have been read
+            constexpr int GH = kTTGates, GL = kTTGates + kTTConc;  // first hi, lo slot
             float ubh, ubl, ueh, uel;
             u_bdf_ff(D, c.order, n, fin, t_fin, ubh, ubl, ueh, uel);
-            float gB[kTTGates], gE[kTTGates];
-            float ch[kTTConc], cl[kTTConc], dc[kTTConc], cE[kTTConc];
-#pragma unroll
-            for (int k = 0; k < kTTConc; ++k) {
-                ch[k] = chn[(size_t)k * N + n];
-                cl[k] = chn[LO + (size_t)k * N + n];
+            if (D.active && !D.active[n]) {
+                // excluded from the simulation: states held, no currents
+                float t[4 * kTTPacked];
+                ld_packed<kTTPacked>(D.g32_n, (size_t)N, n, t);
+                st_packed<kTTPacked>(D.g32_nm1, (size_t)N, n, t);
+                store_vu_ff(D, n, ubh, ubl, ueh, uel, 0.f);
+                continue;
             }
+            float s0[4 * kTTPacked], s1[4 * kTTPacked];
+            ld_packed<kTTPacked>(D.g32_n, (size_t)N, n, s0);
+            if (c.order == 2) ld_packed<kTTPacked>(D.g32_nm1, (size_t)N, n, s1);
+            float gB[kTTGates], gE[kTTGates];
+            float dc[kTTConc], cE[kTTConc];
             if (c.order == 2) {
 #pragma unroll
                 for (int k = 0; k < kTTGates; ++k) {
-                    const float x = gn[(size_t)k * N + n], y = gm[(size_t)k * N + n];
-                    gB[k] = 2.f * x - 0.5f * y;
-                    gE[k] = 2.f * x - y;
+                    gB[k] = 2.f * s0[k] - 0.5f * s1[k];
+                    gE[k] = 2.f * s0[k] - s1[k];
                 }
 #pragma unroll
                 for (int k = 0; k < kTTConc; ++k) {
                     // c_n - c_{n-1}: the hi parts are close, so their
                     // difference is exact
                     float dh, dl;
-                    ff_sub(ch[k], cl[k], chm[(size_t)k * N + n], chm[LO + (size_t)k * N + n], dh, dl);
+                    ff_sub(s0[GH + k], s0[GL + k], s1[GH + k], s1[GL + k], dh, dl);
                     dc[k] = dh;
-                    cE[k] = ch[k] + dc[k];
+                    cE[k] = s0[GH + k] + dc[k];
                 }
             } else {
 #pragma unroll
-                for (int k = 0; k < kTTGates; ++k) gB[k] = gE[k] = gn[(size_t)k * N + n];
+                for (int k = 0; k < kTTGates; ++k) gB[k] = gE[k] = s0[k];
 #pragma unroll
                 for (int k = 0; k < kTTConc; ++k) {
                     dc[k] = 0.f;
-                    cE[k] = ch[k];
+                    cE[k] = s0[GH + k];
                 }
-            }
-            if (D.active && !D.active[n]) {
-                // excluded from the simulation: states held, no currents
-#pragma unroll
-                for (int k = 0; k < kTTGates; ++k) gm[(size_t)k * N + n] = gn[(size_t)k * N + n];
-#pragma unroll
-                for (int k = 0; k < kTTConc; ++k) {
-                    chm[(size_t)k * N + n] = ch[k];
-                    chm[LO + (size_t)k * N + n] = cl[k];
-                }
-                store_vu_ff(D, n, ubh, ubl, ueh, uel, 0.f);
-                continue;
             }
             float a[kTTGates], b[kTTGates], r[kTTConc];
             TT<float>::rates(cell, ueh, gE, cE[0], cE[1], cE[2], cE[3], cE[4], a, b, r);
-            float g1[kTTGates];
+            float o[4 * kTTPacked];
+            o[4 * kTTPacked - 1] = 0.f;
 #pragma unroll
-            for (int k = 0; k < kTTGates; ++k) {
-                g1[k] = (gB[k] + dtg * a[k]) / (alg + dtg * b[k]);
-                gm[(size_t)k * N + n] = g1[k];
-            }
-            float c1[kTTConc];
+            for (int k = 0; k < kTTGates; ++k) o[k] = (gB[k] + dtg * a[k]) / (alg + dtg * b[k]);
             const float third = 1.f / 3.f, dta = (float)c.dt_alpha;
 #pragma unroll
             for (int k = 0; k < kTTConc; ++k) {
                 // order 1: c_n + dt r;  order 2: c_n + (c_n - c_{n-1})/3 + (2/3) dt r
                 const float inc = c.order == 2 ? fmaf(third, dc[k], dta * r[k]) : dta * r[k];
-                float h1, l1;
-                ff_add_f(ch[k], cl[k], inc, h1, l1);
-                chm[(size_t)k * N + n] = h1;
-                chm[LO + (size_t)k * N + n] = l1;
-                c1[k] = h1;
+                ff_add_f(s0[GH + k], s0[GL + k], inc, o[GH + k], o[GL + k]);
             }
+            st_packed<kTTPacked>(D.g32_nm1, (size_t)N, n, o);
             TT<float>::Cur cur;
-            TT<float>::currents(cell, ueh, g1, c1[0], c1[2], c1[3], c1[4], cur);
+            TT<float>::currents(cell, ueh, o, o[GH + 0], o[GH + 2], o[GH + 3], o[GH + 4], cur);
             const float I = TT<float>::iion_of(cur);
             store_vu_ff(D, n, ubh, ubl, ueh, uel, applied_f(D, c, n) - I);
         } else {
@@ -532,26 +547,36 @@ __global__ void __launch_bounds__(kIonicThreads, sizeof(G) == 4 ? 6 : 1) k_ionic
 }
 
 
-void launch_ionic(Dev* d, const Dev& h, int grid, cudaStream_t s) {
+// One launch of the instance's ionic kernel with BT threads per block.  The
+// block size changes nothing in the results (one node per thread, no
+// reductions): the create-time autotuner picks it per instance.
+template <int BT>
+void launch_ionic_bt(const Dev& h, const Batch& B, int grid, cudaStream_t s) {
     const bool refined = h.prec == EP_PREC_FP32_REFINED;
-    const Batch B = single_batch(d);
     if (h.model == EP_MODEL_BO) {
-        if (refined) k_ionic_bo<float><<<grid, kIonicThreads, 0, s>>>(B);
-        else k_ionic_bo<double><<<grid, kIonicThreads, 0, s>>>(B);
+        if (refined) k_ionic_bo<float, BT><<<grid, BT, 0, s>>>(B);
+        else k_ionic_bo<double, BT><<<grid, BT, 0, s>>>(B);
     } else if (h.u_nm2) {
-        if (refined) k_ionic_tt3<float><<<grid, kIonicThreads, 0, s>>>(B);
-        else k_ionic_tt3<double><<<grid, kIonicThreads, 0, s>>>(B);
+        if (refined) k_ionic_tt3<float, BT><<<grid, BT, 0, s>>>(B);
+        else k_ionic_tt3<double, BT><<<grid, BT, 0, s>>>(B);
     } else {
-        if (refined) k_ionic_tt2<float><<<grid, kIonicThreads, 0, s>>>(B);
-        else k_ionic_tt2<double><<<grid, kIonicThreads, 0, s>>>(B);
+        if (refined) k_ionic_tt2<float, BT><<<grid, BT, 0, s>>>(B);
+        else k_ionic_tt2<double, BT><<<grid, BT, 0, s>>>(B);
     }
+}
+
+void launch_ionic(Dev* d, const Dev& h, int grid, int threads, cudaStream_t s) {
+    const Batch B = single_batch(d);
+    if (threads == 64) launch_ionic_bt<64>(h, B, grid, s);
+    else if (threads == 256) launch_ionic_bt<256>(h, B, grid, s);
+    else launch_ionic_bt<128>(h, B, grid, s);
 }
 
 // refined instances of one model and number of levels, batched
 void launch_ionic_batch(const Batch& B, int model, bool lv3, int grid, cudaStream_t s) {
-    if (model == EP_MODEL_BO) k_ionic_bo<float><<<grid, kIonicThreads, 0, s>>>(B);
-    else if (lv3) k_ionic_tt3<float><<<grid, kIonicThreads, 0, s>>>(B);
-    else k_ionic_tt2<float><<<grid, kIonicThreads, 0, s>>>(B);
+    if (model == EP_MODEL_BO) k_ionic_bo<float, kIonicThreads><<<grid, kIonicThreads, 0, s>>>(B);
+    else if (lv3) k_ionic_tt3<float, kIonicThreads><<<grid, kIonicThreads, 0, s>>>(B);
+    else k_ionic_tt2<float, kIonicThreads><<<grid, kIonicThreads, 0, s>>>(B);
 }
 
 }  // namespace epk

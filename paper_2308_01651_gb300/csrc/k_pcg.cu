@@ -144,9 +144,10 @@ __device__ __noinline__ void resid_ff_nodes(const Dev& D, int t0, int T, float (
 // arrivals at each grid barrier); measured against one 512-thread block
 // (128 registers, 16 warps) and two of them (64 registers, 304 arrivals) a
 // step's solve took 249.5 / 255.0 / 277.3 us on the 442k-node slab and
-// 2086 / 2373 / 2108 us on the 2.19M-node LV shell.  Batches run two
-// 512-thread blocks per SM (each instance's barrier gathers a few blocks).
-template <int BT, int MINB>
+// 2086 / 2373 / 2108 us on the 2.19M-node LV shell.  Batches run the same
+// 1024-thread blocks, shared among their instances by size (so an instance
+// rounds alike alone and in a batch, to its share of blocks).
+template <int BT, int MINB, bool HINT>
 __global__ void __launch_bounds__(BT, MINB) k_solve32_stencil(Batch B) {
     const Slot S = batch_slot(B);
     Dev& D = *S.D;
@@ -172,6 +173,16 @@ __global__ void __launch_bounds__(BT, MINB) k_solve32_stencil(Batch B) {
     const bool fixed = D.npad > 0 && wrap == 0;
     const float* __restrict__ A = D.Ahi;
     const long long cs = D.cs;
+    // HINT (working set beyond L2): the CG vectors kept in L2, the couplings
+    // streamed; otherwise plain accesses (an L2-resident instance gains
+    // nothing and its couplings would be dropped first)
+    const unsigned long long pkeep = HINT ? l2_policy_evict_last() : 0ull;
+    const unsigned long long pstream = HINT ? l2_policy_evict_first() : 0ull;
+    auto ldv = [&](const float* a) { return HINT ? ld_pol(a, pkeep) : *a; };
+    auto stv = [&](float* a, float v) {
+        if (HINT) st_pol(a, v, pkeep);
+        else *a = v;
+    };
     float* part = reinterpret_cast<float*>(D.partial);
     unsigned long long* bcount = reinterpret_cast<unsigned long long*>(D.counter + CNT_BAR);
     unsigned long long target = 0ull;
@@ -199,16 +210,16 @@ __global__ void __launch_bounds__(BT, MINB) k_solve32_stencil(Batch B) {
             if (!first) {
                 // ---- update, node by node
                 for (int n = t0; n < N; n += T) {
-                    const float dv = dinv[n];
-                    const float r0 = r[n], w0 = w[n], u0 = u[n];
-                    const float s1 = beta == 0.f ? w0 : fmaf(beta, s[n], w0);
-                    const float p1 = beta == 0.f ? u0 : fmaf(beta, p[n], u0);
+                    const float dv = ldv(dinv + n);
+                    const float r0 = ldv(r + n), w0 = ldv(w + n), u0 = ldv(u + n);
+                    const float s1 = beta == 0.f ? w0 : fmaf(beta, ldv(s + n), w0);
+                    const float p1 = beta == 0.f ? u0 : fmaf(beta, ldv(p + n), u0);
                     const float r1 = fmaf(-alpha, s1, r0);
-                    x[n] = fmaf(alpha, p1, x[n]);
-                    s[n] = s1;
-                    p[n] = p1;
-                    r[n] = r1;
-                    u[n] = dv * r1;
+                    stv(x + n, fmaf(alpha, p1, ldv(x + n)));
+                    stv(s + n, s1);
+                    stv(p + n, p1);
+                    stv(r + n, r1);
+                    stv(u + n, dv * r1);
                 }
                 if (!grid_barrier(bcount, target, G, &D.status)) {
                     aborted = true;
@@ -223,10 +234,11 @@ __global__ void __launch_bounds__(BT, MINB) k_solve32_stencil(Batch B) {
                 const unsigned int f = fn;
                 fn = (!fixed && n + T < N) ? flag[n + T] : 0u;
                 const NbrOff o = nbr_offsets(nx, nxy, wrap, f);
-                // (fixed offsets: no mask, see the symmetric stencils' layout)
-                const float acc = row32_sym<true>(A, cs, u, n, o, exist_flags(f, wrap));
-                w[n] = acc;
-                const float rn = r[n], un = u[n];
+                // fixed offsets: no mask, see the symmetric stencils' layout
+                const float acc = HINT ? row32_sym_pol(A, cs, u, n, o, exist_flags(f, wrap), pstream, pkeep)
+                                       : row32_sym<true>(A, cs, u, n, o, exist_flags(f, wrap));
+                stv(w + n, acc);
+                const float rn = ldv(r + n), un = ldv(u + n);
                 v[0] = fmaf(rn, un, v[0]);
                 v[1] = fmaf(un, acc, v[1]);
                 v[2] = fmaf(rn, rn, v[2]);
@@ -351,15 +363,18 @@ cudaError_t barrier_timeout_probe(int* status_out) {
 int pcg_blocks_per_sm(int shape) {
     int occ = 0;
     cudaError_t e;
-    if (shape == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil<1024, 1>, 1024, 0);
-    else if (shape == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil<512, 2>, 512, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil<512, 1>, 512, 0);
+    if (shape == 3)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil<1024, 1, false>, 1024, 0);
+    else if (shape == 2)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil<512, 2, false>, 512, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve32_stencil<512, 1, false>, 512, 0);
     return e == cudaSuccess ? occ : 0;
 }
 
 int pcg_threads_of(int shape) { return shape == 3 ? 1024 : 512; }
 
-template <int BT, int MINB>
+template <int BT, int MINB, bool HINT>
 cudaError_t launch_solve(const Batch& B, int grid, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -371,16 +386,21 @@ cudaError_t launch_solve(const Batch& B, int grid, cudaStream_t s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_solve32_stencil<BT, MINB>, B);
+    return cudaLaunchKernelEx(&cfg, k_solve32_stencil<BT, MINB, HINT>, B);
 }
 
-cudaError_t launch_pcg32_batch(const Batch& B, int grid, cudaStream_t s) { return launch_solve<512, 2>(B, grid, s); }
+// hint: the solve's working set exceeds L2 (L2 eviction-priority policies)
+cudaError_t launch_pcg32_batch(const Batch& B, int grid, int hint, cudaStream_t s) {
+    return hint ? launch_solve<1024, 1, true>(B, grid, s) : launch_solve<1024, 1, false>(B, grid, s);
+}
 
-cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, int shape, cudaStream_t s) {
+cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, int shape, int hint, cudaStream_t s) {
     const Batch B = single_batch(d);
-    if (shape == 3) return launch_solve<1024, 1>(B, grid, s);
-    if (shape == 2) return launch_solve<512, 2>(B, grid, s);
-    return launch_solve<512, 1>(B, grid, s);
+    if (shape == 3)
+        return hint ? launch_solve<1024, 1, true>(B, grid, s) : launch_solve<1024, 1, false>(B, grid, s);
+    if (shape == 2)
+        return hint ? launch_solve<512, 2, true>(B, grid, s) : launch_solve<512, 2, false>(B, grid, s);
+    return hint ? launch_solve<512, 1, true>(B, grid, s) : launch_solve<512, 1, false>(B, grid, s);
 }
 
 }  // namespace epk

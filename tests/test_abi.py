@@ -36,7 +36,7 @@ def _args(prob, **kw):
 
 @pytest.mark.parametrize("bad", [
     dict(dt=0.0), dict(dt=-1.0), dict(bdf_order=4), dict(bdf_order=0), dict(precision=7), dict(op32=9),
-    dict(max_iter=-1), dict(tol=-1.0),
+    dict(max_iter=-1), dict(tol=-1.0), dict(ionic_threads=96), dict(ionic_threads=-128),
 ])
 def test_create_rejects_bad_options(bad):
     prob = I.slab_bo_small(nx=4, ny=3, nz=2, L=(0.2, 0.15, 0.1))

@@ -286,3 +286,30 @@ def test_steps_converging_at_first_residual_keep_history_exact():
     finally:
         inst.close()
     assert zero_sweeps >= 5, zero_sweeps
+
+
+def test_ionic_block_sizes_agree_bitwise():
+    """The ionic kernel's block size (64, 128, 256 threads, or the
+    create-time autotuner's choice) changes no result: one node per thread
+    and no reductions, so the states after 30 steps are bitwise equal."""
+    prob = small_ttp06(nx=40, ny=12, nz=8, T=5.0)
+    saves, chosen = [], None
+    for bt in (64, 128, 256, 0):
+        inst = ep.Instance(prob, precision=REF, ionic_threads=bt)
+        st = inst.stats()
+        assert st["ionic_threads"] == (bt if bt else st["ionic_threads"])
+        if bt == 0:
+            chosen = st["ionic_threads"]
+        inst.step(30)
+        saves.append(inst.save())
+        inst.close()
+    assert chosen in (64, 128, 256)
+    for sv in saves[1:]:
+        assert np.array_equal(sv, saves[0])
+
+
+def test_ionic_block_size_option_is_validated():
+    prob = small_ttp06(nx=4, ny=3, nz=2)
+    with pytest.raises(ep.EpError) as e:
+        ep.Instance(prob, precision=REF, ionic_threads=96)
+    assert e.value.status == ep.EP_EINVAL

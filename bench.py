@@ -202,17 +202,18 @@ KERNEL_SOURCES = {
 }
 
 
-def committed_traffic(name, N=None, n_elems=None, alg_bytes=None, shell=False):
-    """DRAM bytes per launch of a kernel from the committed ncu summary, if the
-    kernel's sources are unchanged since the capture.  A launch whose work
-    depends on the iterations it runs (the persistent solve) is scaled from
-    the captured launch to this run's average launch by the algorithmic
-    bytes of the two (the capture records its iterations and sweeps)."""
+def committed_traffic(workload, name, N=None, n_elems=None, alg_bytes=None, shell=False):
+    """DRAM bytes per launch of a kernel from the committed ncu summary of this
+    workload, if the kernel's sources are unchanged since the capture.  A
+    launch whose work depends on the iterations it runs (the persistent
+    solve) is scaled from the captured launch to this run's average launch by
+    the algorithmic bytes of the two (the capture records its iterations and
+    sweeps)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p) or name not in KERNEL_SOURCES:
         return None
     with open(p) as f:
-        d = json.load(f).get(name)
+        d = json.load(f).get(workload, {}).get(name)
     if not d or d.get("source_hash") != source_hash(KERNEL_SOURCES[name]):
         return None
     t = d.get("dram_bytes_per_launch")
@@ -550,7 +551,7 @@ def run_ours(args):
         dom_alg = kernel_model(dom, N, n_elems, it_p / P, shell=shell, sweeps=sw_p / P)[0] \
             if dom == "solve32" else None
         roof.update(kernel=dom, hbm_frac=hbm_frac, alu_frac=alu_frac,
-                    traffic=committed_traffic(dom, N, n_elems, dom_alg, shell),
+                    traffic=committed_traffic(args.workload, dom, N, n_elems, dom_alg, shell),
                     impl_frac=(d["impl_gbs"] / hbm_peak) if d["impl_gbs"] else None,
                     bytes_model="per-node figures of the hot-path measurement table x nodes x "
                                 "inner iterations per launch; impl_frac: this layout's bytes")
@@ -559,7 +560,7 @@ def run_ours(args):
     # checkpoint at its start: a portable state loads into either precision)
     inst.close()
     fp64 = None
-    if args.fp64_steps > 0:
+    if args.fp64_steps > 0 and not q2:  # (Q2 slabs: refined precision only)
         i64 = ep.Instance(prob, precision=FP64, cuda_stream=sp)
         i64.load(window_start)
         e64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))

@@ -121,16 +121,17 @@ def test_committed_traffic_scaling_and_staleness(monkeypatch):
     import os
 
     with open(os.path.join(bench.ROOT, "profiles", "traffic.json")) as f:
-        rec = json.load(f)["solve32"]
+        rec = json.load(f)["c2"]["solve32"]
     N, E = 442401, 420000
     # sources as at the capture (the check below does not depend on the
     # current files)
     monkeypatch.setattr(bench, "source_hash", lambda files: rec["source_hash"])
     cap = bench.kernel_model("solve32", N, E, rec["inner_iters"], sweeps=rec["sweeps"])[0]
     alg = bench.kernel_model("solve32", N, E, 8.45, sweeps=1.36)[0]
-    t = bench.committed_traffic("solve32", N, E, alg)
+    t = bench.committed_traffic("c2", "solve32", N, E, alg)
     assert t == pytest.approx(rec["dram_bytes_per_launch"] * alg / cap, rel=1e-12)
-    assert bench.committed_traffic("solve32", N, E, cap) == pytest.approx(rec["dram_bytes_per_launch"])
+    assert bench.committed_traffic("c2", "solve32", N, E, cap) == pytest.approx(rec["dram_bytes_per_launch"])
     monkeypatch.setattr(bench, "source_hash", lambda files: "changed")
-    assert bench.committed_traffic("solve32", N, E, alg) is None
-    assert bench.committed_traffic("no_such_kernel") is None
+    assert bench.committed_traffic("c2", "solve32", N, E, alg) is None
+    assert bench.committed_traffic("c2", "no_such_kernel") is None
+    assert bench.committed_traffic("no_such_workload", "solve32", N, E, alg) is None

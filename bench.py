@@ -373,7 +373,7 @@ def run_reference(args):
 ORACLE_FIXTURES = {"c4": os.path.join(ROOT, "tests", "golden", "shell_ttp06_oracle_40ms.npz")}
 
 
-def accuracy_vs_oracle(args, prob, ep, prec, sp, op32):
+def accuracy_vs_oracle(args, prob, ep, prec, sp, op32, tiles=0):
     """The refined path against the FP64 oracle on the benchmarked workload:
     a fresh instance stepped from t = 0 to the end of the oracle's stored
     window (written by tests/golden/make_shell_oracle_fixture.py, which calls
@@ -389,7 +389,7 @@ def accuracy_vs_oracle(args, prob, ep, prec, sp, op32):
     fx = np.load(path)
     steps = int(fx["steps"])
     dt = float(fx["dt"])
-    inst = ep.Instance(prob, precision=prec, cuda_stream=sp, op32=op32)
+    inst = ep.Instance(prob, precision=prec, cuda_stream=sp, op32=op32, solve_tiles=tiles)
     inst.step(steps)
     at = inst.activation_times()
     u = inst.potential()
@@ -447,7 +447,8 @@ def run_ours(args):
     REF, FP64 = ep.EP_PREC_FP32_REFINED, ep.EP_PREC_FP64
 
     op32 = {"auto": ep.EP_OP_AUTO, "mf": ep.EP_OP_MATRIX_FREE, "stencil": ep.EP_OP_STENCIL}[args.op32]
-    inst = ep.Instance(prob, precision=REF, cuda_stream=sp, op32=op32)
+    tiles = {"auto": 0, "nodes": 1, "tiles": 2}[args.solve]
+    inst = ep.Instance(prob, precision=REF, cuda_stream=sp, op32=op32, solve_tiles=tiles)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     W, K = max(3, args.warmup), args.steps
     # untimed: bring the instance into the propagating regime (the stimulus
@@ -582,7 +583,7 @@ def run_ours(args):
     # ---- accuracy of the refined path against the FP64 oracle
     acc = None
     if not args.no_accuracy:
-        acc = accuracy_vs_oracle(args, prob, ep, REF, sp, op32)
+        acc = accuracy_vs_oracle(args, prob, ep, REF, sp, op32, tiles)
 
     # ---- end to end through the public API, host buffers in and out
     e2e = None
@@ -593,7 +594,7 @@ def run_ours(args):
         K_e2e = K
     t0 = time.perf_counter()
     if K_e2e:
-        ie = ep.Instance(prob, precision=REF, cuda_stream=sp, op32=op32)
+        ie = ep.Instance(prob, precision=REF, cuda_stream=sp, op32=op32, solve_tiles=tiles)
         ie.step_async(K_e2e)
         at_h = ie.activation_times()
         u_h = ie.potential()
@@ -627,7 +628,9 @@ def run_ours(args):
         "roofline": roof, "kernels": kernels, "profile_steps": P,
         "op32_autotune_us": {"matrix_free": tune["tune_us_mf"], "stencil": tune["tune_us_stencil"],
                              "chosen": {1: "matrix-free", 2: "stencil"}.get(tune["op32"], "Q2"),
-                             "solve_block_threads": tune.get("solve_threads")},
+                             "solve_block_threads": tune.get("solve_threads"),
+                             "solve_apply": "tiles staged in shared memory" if tune.get("solve_tiles")
+                             else "node-parallel"},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
         "accuracy": acc, "fp64_gpu": fp64,
     }
@@ -781,6 +784,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--op32", default="auto", choices=["auto", "mf", "stencil"],
                     help="FP32 inner operator (auto: the faster one on slabs, by a create-time autotune)")
+    ap.add_argument("--solve", default="auto", choices=["auto", "nodes", "tiles"],
+                    help="the persistent solve's operator apply (auto: node-parallel; tiles: on tiles staged in "
+                         "shared memory)")
     ap.add_argument("--workload", default="c4", choices=sorted(WORKLOADS),
                     help="c4: the 2.19M-node LV shell (default, the headline line: the largest single-instance "
                          "configuration); c2: the 442k-node slab; c3: 96 slabs stepped as one batch; "

@@ -202,7 +202,13 @@ typedef struct {
  * the instance's work on, or NULL for a stream the library creates;
  * ionic_threads: threads per block of the ionic kernel, 64, 128 or 256, or 0
  * for the create-time autotuner's choice (the block size changes nothing in
- * the results: one node per thread, no reductions). */
+ * the results: one node per thread, no reductions); solve_tiles: the
+ * persistent solve's operator apply (stencil operator, Q1 meshes) on tiles
+ * of rows staged in shared memory by bulk copies (2), or node-parallel (0 or
+ * 1, the default: measured faster on the 2.19M-node LV shell); 2 on a Q2
+ * mesh, in FP64 or with the matrix-free operator is EP_EUNSUPPORTED.  The
+ * apply's rows are the same sums either way; the dot products group their
+ * partial sums by tile, so results differ in rounding only. */
 typedef struct {
     double dt;
     int32_t bdf_order;
@@ -214,6 +220,7 @@ typedef struct {
     int32_t op32;
     void* cuda_stream;
     int32_t ionic_threads;
+    int32_t solve_tiles;
 } ep_options;
 
 /* Per-step counters of the last completed step. */
@@ -229,7 +236,8 @@ typedef struct {
     double tune_us_mf;      /* autotuner: matrix-free apply time (us), 0 if not timed */
     double tune_us_stencil; /* autotuner: FP32 stencil apply time (us), 0 if not timed */
     int32_t ionic_threads;  /* threads per block of the ionic kernel in use */
-    int32_t reserved2;
+    int32_t solve_tiles;    /* 1: the persistent solve applies the operator on
+                               tiles staged in shared memory, 0 otherwise */
 } ep_stats;
 
 /* Creates an instance: validates the inputs, copies them to the device,

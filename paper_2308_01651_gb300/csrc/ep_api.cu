@@ -53,9 +53,14 @@ void mfc_fill_geo(float* g, int NX, int NY, int NZ, const double* xyz, const dou
 cudaError_t mfc_tensor_map(CUtensorMap* tm, const float* g, int NX, int NY, int NZ);
 cudaError_t mfc_prepare(int NX);
 void launch_apply32_mfc(Dev* d, const Dev& h, const CUtensorMap& tm, cudaStream_t s);
-int pcg_blocks_per_sm(int batched);
-cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, int shape, int hint, cudaStream_t s);
-int pcg_threads_of(int shape);
+int pcg_blocks_per_sm();
+cudaError_t launch_pcg32(Dev* d, const Dev& h, int grid, int tiled, int hint, cudaStream_t s);
+int pcg_threads_of();
+size_t tiled_smem_max();
+cudaError_t pcg_tiled_prepare(size_t smem, int* fits);
+size_t tiled_smem_bytes(int l, int NX);
+bool plan_tiles(int NX, int NY, int NZ, int sms, size_t smem_max, int* by, int* jt, int* kr, int* l,
+                double* cost);
 cudaError_t barrier_timeout_probe(int* status_out);
 cudaError_t residual_norm_noalloc(Dev* d, int grid, int threads, cudaStream_t s, double sums[2]);
 int noalloc_max_blocks();
@@ -102,7 +107,7 @@ struct ep_instance {
     int grid_resid = 0;        // node-parallel residual: 512-thread blocks, two per SM
     int grid_tiles = 0;        // persistent grid of the tiled stencil kernels
     int grid_pcg = 0;          // cooperative grid of the persistent inner solver
-    int pcg_shape = 3;         // its launch shape (k_pcg.cu): 1 x 512, 2 x 512 or 1 x 1024 threads per SM
+    int pcg_tiled = 0;         // its apply pass on tiles staged in shared memory (k_pcg.cu)
     int pcg_hint = 0;          // its working set exceeds L2: L2 eviction-priority hints
     ep_status sticky = EP_OK;
     int* bad = nullptr;        // device flag of the assembly
@@ -244,7 +249,8 @@ struct Sizes {
     int levels;       // time levels kept: 3 for BDF3, else 2
     bool q2;          // triquadratic slab
     int64_t ne;       // elements (Q2)
-    int64_t npad;     // zero nodes before and after the inner solver's u (Q1 slab)
+    int64_t npad;     // zero nodes before and after the inner solver's u (Q1 meshes)
+    int64_t cpad;     // zero floats before and after the float coupling arrays
     int64_t cs;       // slot stride of the refined couplings (floats): N, then zeros
     int NX, NY, NZ;   // nodes per direction (Q1)
 };
@@ -322,7 +328,7 @@ size_t footprint(const Sizes& z) {
             b += 4 * al(8 * N * 4);       // element outputs of A u and M v (hi, lo) in node slots
             b += 2 * al(N * 8);           // diagonals of M and K
         } else {
-            const size_t cb = (size_t)epk::kSlots * (size_t)z.cs * 4;
+            const size_t cb = ((size_t)epk::kSlots * (size_t)z.cs + 2 * (size_t)z.cpad) * 4;
             b += 2 * al(cb);                         // Ahi Alo (symmetric float-float stencil)
             if (!z.slab_mass) b += 2 * al(cb);       // Mhi Mlo (curved / with regions)
         }
@@ -400,6 +406,10 @@ ep_status validate(const ep_mesh* mesh, const ep_fibers* fib, const ep_conductiv
     if (opts->ionic_threads != 0 && opts->ionic_threads != 64 && opts->ionic_threads != 128 &&
         opts->ionic_threads != 256)
         return fail(EP_EINVAL, "options.ionic_threads must be 0, 64, 128 or 256");
+    if (opts->solve_tiles < 0 || opts->solve_tiles > 2) return fail(EP_EINVAL, "options.solve_tiles must be 0, 1 or 2");
+    if (opts->solve_tiles == 2 && (mesh->kind == EP_MESH_SLAB_Q2 || opts->precision != EP_PREC_FP32_REFINED ||
+                                   opts->op32 == EP_OP_MATRIX_FREE))
+        return fail(EP_EUNSUPPORTED, "the tiled solve takes FP32_REFINED Q1 meshes with the stencil operator");
     if (opts->op32 == EP_OP_MATRIX_FREE && mesh->kind == EP_MESH_SHELL && !epk::mfc_supported(mesh->nx + 1))
         return fail(EP_EUNSUPPORTED, "the matrix-free FP32 operator takes shells at most 31 elements across the wall");
     if (mesh->kind == EP_MESH_SLAB_Q2) {
@@ -491,7 +501,12 @@ Sizes sizes_of(const ep_mesh* mesh, const ep_ionic_model* ionic, const ep_option
     // a Q1 slab's neighbour offsets reach 1 + (nx+1) + (nx+1)(ny+1) nodes
     // either way; rounded up to 64 floats, so that the vectors keep the
     // 256-byte alignment of every allocation (16-byte vector accesses)
-    z.npad = z.slab ? ((int64_t)(mesh->nx + 1) * (mesh->ny + 1) + (mesh->nx + 1) + 1 + 63) / 64 * 64 : 0;
+    // (shells: a row and a few floats, the reach of the tiled solve's bulk
+    // copies past the first and last node; the coupling arrays get the same)
+    const int64_t reach = ((int64_t)mesh->nx + 1 + 8 + 63) / 64 * 64;
+    z.npad = z.slab ? ((int64_t)(mesh->nx + 1) * (mesh->ny + 1) + (mesh->nx + 1) + 1 + 63) / 64 * 64
+                    : (mesh->kind == EP_MESH_SHELL ? reach : 0);
+    z.cpad = reach;
     {
         // symmetric float couplings: each slot followed by at least the
         // largest backward offset in zeros, rounded up to 64 floats
@@ -631,7 +646,7 @@ ep_status build_graph(ep_instance* I) {
         // every refinement sweep [inner PCG, u += delta, float-float residual,
         // decision] in one persistent launch (it returns at once when the
         // first residual met the tolerance)
-        C.chk(epk::launch_pcg32(I->d, h, I->grid_pcg, I->pcg_shape, I->pcg_hint, s));
+        C.chk(epk::launch_pcg32(I->d, h, I->grid_pcg, I->pcg_tiled, I->pcg_hint, s));
     } else {
         C.chk(add_while(s, &h_outer, &body));
         if (C.err == cudaSuccess) {
@@ -711,7 +726,7 @@ ep_status step_host(ep_instance* I) {
         if (h.op32 == EP_OP_STENCIL) {
             // the whole solve in one persistent launch
             cudaError_t pe = cudaSuccess;
-            timed(I, K_PCG32, [&] { pe = epk::launch_pcg32(d, h, I->grid_pcg, I->pcg_shape, I->pcg_hint, s); });
+            timed(I, K_PCG32, [&] { pe = epk::launch_pcg32(d, h, I->grid_pcg, I->pcg_tiled, I->pcg_hint, s); });
             CUDA_TRY(pe);
             f = 0;
         }
@@ -1066,12 +1081,14 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
             ALLOC(h.q2dK, N);
         } else {
             h.cs = z.cs;
-            if ((st = dalloc_zero(I, &h.Ahi, (size_t)epk::kSlots * z.cs)) != EP_OK) return st;
-            if ((st = dalloc_zero(I, &h.Alo, (size_t)epk::kSlots * z.cs)) != EP_OK) return st;
+            const size_t cc = (size_t)epk::kSlots * z.cs;
+            if ((st = dalloc_padded(I, &h.Ahi, cc, z.cpad)) != EP_OK) return st;
+            if ((st = dalloc_padded(I, &h.Alo, cc, z.cpad)) != EP_OK) return st;
         }
         if (!z.slab_mass && !z.q2) {
-            if ((st = dalloc_zero(I, &h.Mhi, (size_t)epk::kSlots * z.cs)) != EP_OK) return st;
-            if ((st = dalloc_zero(I, &h.Mlo, (size_t)epk::kSlots * z.cs)) != EP_OK) return st;
+            const size_t cc = (size_t)epk::kSlots * z.cs;
+            if ((st = dalloc_padded(I, &h.Mhi, cc, z.cpad)) != EP_OK) return st;
+            if ((st = dalloc_padded(I, &h.Mlo, cc, z.cpad)) != EP_OK) return st;
         }
         ALLOC(h.uh_n, N);
         ALLOC(h.ul_n, N);
@@ -1353,11 +1370,9 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     I->grid_resid = std::max(1, std::min((int)((N + epk::kResidThreads - 1) / epk::kResidThreads), 2 * sms));
     I->grid_tiles = std::max(1, std::min(epk::st_tiles(h), 2 * sms));
     if (ref) {
-        // the persistent solver's blocks must all be resident at once
-        // launch shape of the persistent solve: one 1024-thread block per SM
-        // (measured fastest of the three shapes on the 442k-node slab and
-        // the 2.19M-node shell, k_pcg.cu)
-        I->pcg_shape = 3;
+        // the persistent solver's blocks must all be resident at once: one
+        // 1024-thread block per SM (measured fastest of three launch shapes
+        // on the 442k-node slab and the 2.19M-node shell, k_pcg.cu)
         // L2 policies when the solve's working set (the FP32 operator's 14
         // couplings and the seven CG vectors, 84 B a node) exceeds L2:
         // measured on the 2.19M-node shell 1871 against 2044 us a step's
@@ -1365,11 +1380,37 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         int l2 = 0;
         CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
         I->pcg_hint = (double)N * 84.0 > (double)l2 ? 1 : 0;
-        const int occ = std::min(epk::pcg_blocks_per_sm(I->pcg_shape), I->pcg_shape == 2 ? 2 : 1);
+        const int occ = std::min(epk::pcg_blocks_per_sm(), 1);
         if (occ <= 0) return fail(EP_ECUDA, "occupancy query of the persistent solver failed");
-        const int bt = epk::pcg_threads_of(I->pcg_shape);
+        const int bt = epk::pcg_threads_of();
         const int want = (int)((N + bt - 1) / bt);
         I->grid_pcg = std::max(1, std::min(std::min(want, sms * occ), epk::kMaxPersistentBlocks));
+        // the apply on tiles staged in shared memory (Q1 meshes), on request:
+        // on the 2.19M-node LV shell it measured slower than the node-parallel
+        // apply (k_pcg.cu)
+        I->pcg_tiled = 0;
+        if (!z.q2 && opts->solve_tiles == 2) {
+            int by = 0, jt = 0, kr = 0, l = 0;
+            double cost = 0.0;
+            const bool planned =
+                epk::plan_tiles(h.NX, h.NY, h.NZ, sms, epk::tiled_smem_max(), &by, &jt, &kr, &l, &cost);
+            const bool want_tiles = opts->solve_tiles == 2;
+            if (opts->solve_tiles == 2 && !planned)
+                return fail(EP_EUNSUPPORTED, "no tile plan of the persistent solve fits this mesh");
+            int fits = 0;
+            if (planned && want_tiles) CUDA_TRY(epk::pcg_tiled_prepare(epk::tiled_smem_bytes(l, h.NX), &fits));
+            if (opts->solve_tiles == 2 && !fits)
+                return fail(EP_EUNSUPPORTED, "the tiled solve's blocks do not fit on the SMs");
+            if (planned && want_tiles && fits) {
+                I->pcg_tiled = 1;
+                h.tile_by = by;
+                h.tile_jt = jt;
+                h.tile_kr = kr;
+                h.tile_l = l;
+                I->grid_pcg = jt * kr;
+                CUDA_TRY(cudaMemcpy(&I->d->tile_by, &h.tile_by, 4 * sizeof(int), cudaMemcpyHostToDevice));
+            }
+        }
     }
     if (!ref) h.op32 = 0;  // no FP32 operator in the FP64 path
     if (ref && !z.q2 && h.op32 == EP_OP_AUTO) {
@@ -1444,7 +1485,7 @@ ep_status build_plan(BatchPlan* P) {
     int dev = 0, sms = 152;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int occ = epk::pcg_blocks_per_sm(3);  // the batched solve: 1024-thread blocks, as alone
+    const int occ = epk::pcg_blocks_per_sm();  // the batched solve: 1024-thread blocks, as alone
     if (occ <= 0) return fail(EP_ECUDA, "occupancy query of the persistent solver failed");
     const int cap = sms * occ;
     if (n > cap) return fail(EP_EINVAL, "batch larger than the persistent solver's resident blocks");
@@ -2069,13 +2110,13 @@ ep_status ep_get_stats(const ep_instance* I, ep_stats* out) {
     out->relres = t.last_relres;
     out->op32 = I->h.prec == EP_PREC_FP32_REFINED ? I->h.op32 : 0;
     out->solve_threads = (I->h.prec == EP_PREC_FP32_REFINED && I->h.op32 == EP_OP_STENCIL)
-                             ? epk::pcg_threads_of(I->pcg_shape)
+                             ? epk::pcg_threads_of()
                              : 0;
     out->device_bytes = I->bytes;
     out->tune_us_mf = 1e3 * I->tune_ms[EP_OP_MATRIX_FREE];
     out->tune_us_stencil = 1e3 * I->tune_ms[EP_OP_STENCIL];
     out->ionic_threads = I->ionic_threads;
-    out->reserved2 = 0;
+    out->solve_tiles = (I->h.prec == EP_PREC_FP32_REFINED && I->h.op32 == EP_OP_STENCIL) ? I->pcg_tiled : 0;
     return EP_OK;
 }
 
@@ -2142,7 +2183,7 @@ ep_status ep_residual_norm_noalloc(const ep_instance* I, double* relres_out) {
     if (!I->solved)
         return fail(EP_EINVAL, "no linear solve since the instance was created or its state loaded");
     double sums[2] = {0.0, 0.0};
-    CUDA_TRY(epk::residual_norm_noalloc(I->d, I->grid_pcg, epk::pcg_threads_of(I->pcg_shape), I->stream, sums));
+    CUDA_TRY(epk::residual_norm_noalloc(I->d, I->grid_pcg, epk::pcg_threads_of(), I->stream, sums));
     if (!(sums[0] > 0.0))
         return fail(EP_EINVAL, "the last solve's right-hand side is zero: no relative residual");
     *relres_out = std::sqrt(sums[1] / sums[0]);

@@ -46,6 +46,7 @@ constexpr int kStTx = 32, kStTy = 4, kStTz = 4;
 constexpr int kStThreads = 512;  // one owned node per thread
 // upper bound of a persistent grid (partial-sum buffers are sized for it)
 constexpr int kMaxPersistentBlocks = 2048;
+
 constexpr int kPcgThreads = 512;  // block of the persistent inner solver
 
 // Matrix-free FP32 tile (owned nodes per block): 32 x 8 x 4
@@ -147,7 +148,13 @@ struct Dev {
     int op32;                   // EP_OP_MATRIX_FREE or EP_OP_STENCIL
     // ---- CG ------------------------------------------------------------------
     float *r32, *z32, *q32, *d32, *pa32, *pb32;
-    int npad;                   // Q1 slab: z32 has npad zero floats before and after it
+    int npad;                   // z32 has npad zero floats before and after it (Q1 meshes)
+    // tiled apply of the persistent solve (k_pcg.cu): a block's tile is
+    // tile_by rows of j (every i) over a range of k planes, tile_jt tiles
+    // across j times tile_kr ranges of k; its planes staged in shared memory,
+    // tile_l floats per slot and plane (the tile's rows, a row of halo on
+    // either side, slack and alignment)
+    int tile_by, tile_jt, tile_kr, tile_l;
     unsigned char* nflag;       // boundary flags per node (bits: i=0, i=NX-1, j=0, j=NY-1, k=0, k=NZ-1)
     double *z64, *q64, *pa64, *pb64;
     double rz, pq, alpha, beta, rr, rr0, bb, relres;

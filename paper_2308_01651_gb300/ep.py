@@ -75,14 +75,14 @@ class ep_options(C.Structure):
     _fields_ = [("dt", C.c_double), ("bdf_order", C.c_int32), ("precision", C.c_int32),
                 ("tol", C.c_double), ("max_iter", C.c_int32), ("inner_tol", C.c_double),
                 ("max_sweeps", C.c_int32), ("op32", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("ionic_threads", C.c_int32)]
+                ("ionic_threads", C.c_int32), ("solve_tiles", C.c_int32)]
 
 
 class ep_stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("cg_iters", C.c_int32), ("sweeps", C.c_int32),
                 ("relres", C.c_double), ("op32", C.c_int32), ("solve_threads", C.c_int32),
                 ("device_bytes", C.c_size_t), ("tune_us_mf", C.c_double), ("tune_us_stencil", C.c_double),
-                ("ionic_threads", C.c_int32), ("reserved2", C.c_int32)]
+                ("ionic_threads", C.c_int32), ("solve_tiles", C.c_int32)]
 
 
 class ep_kernel_time(C.Structure):
@@ -170,7 +170,7 @@ class _Args:
     def __init__(self, mesh, f0=None, s0=None, cond=None, model=EP_MODEL_TTP06, cell_type=None,
                  pulses=(), dt=0.05, bdf_order=2, precision=EP_PREC_FP64, tol=0.0, max_iter=0,
                  inner_tol=0.0, max_sweeps=0, op32=EP_OP_AUTO, cuda_stream=None, regions=None,
-                 initial=None, ionic_threads=0):
+                 initial=None, ionic_threads=0, solve_tiles=0):
         """regions: None, or dict(label=per-element uint8, sigma=[(l, t, n)
         per region] in the units of cond, excluded=[flag per region])."""
         keep = []
@@ -243,6 +243,7 @@ class _Args:
         o.tol, o.max_iter, o.inner_tol, o.max_sweeps, o.op32 = tol, max_iter, inner_tol, max_sweeps, op32
         o.cuda_stream = cuda_stream
         o.ionic_threads = ionic_threads
+        o.solve_tiles = solve_tiles
         self.opts = o
         self._keep = keep
 
@@ -312,7 +313,7 @@ def ep_get_stats(h):
     return dict(step=s.step, cg_iters=s.cg_iters, sweeps=s.sweeps, relres=s.relres, op32=s.op32,
                 solve_threads=s.solve_threads,
                 device_bytes=s.device_bytes, tune_us_mf=s.tune_us_mf, tune_us_stencil=s.tune_us_stencil,
-                ionic_threads=s.ionic_threads)
+                ionic_threads=s.ionic_threads, solve_tiles=s.solve_tiles)
 
 
 def ep_potential_device(h):

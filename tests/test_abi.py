@@ -37,6 +37,7 @@ def _args(prob, **kw):
 @pytest.mark.parametrize("bad", [
     dict(dt=0.0), dict(dt=-1.0), dict(bdf_order=4), dict(bdf_order=0), dict(precision=7), dict(op32=9),
     dict(max_iter=-1), dict(tol=-1.0), dict(ionic_threads=96), dict(ionic_threads=-128),
+    dict(solve_tiles=3), dict(solve_tiles=-1),
 ])
 def test_create_rejects_bad_options(bad):
     prob = I.slab_bo_small(nx=4, ny=3, nz=2, L=(0.2, 0.15, 0.1))
@@ -79,6 +80,12 @@ def test_create_rejects_bad_mesh_and_inputs():
         ep.ep_create(m, f0, s0, prob["cond"], I.TTP06, precision=ep.EP_PREC_FP32_REFINED,
                      op32=ep.EP_OP_MATRIX_FREE)
     assert e.value.status == ep.EP_EUNSUPPORTED
+    # the tiled solve takes refined Q1 instances with the stencil operator
+    for bad in (dict(precision=ep.EP_PREC_FP64, solve_tiles=2),
+                dict(precision=ep.EP_PREC_FP32_REFINED, op32=ep.EP_OP_MATRIX_FREE, solve_tiles=2)):
+        with pytest.raises(ep.EpError) as e:
+            ep.ep_create(*a, **dict(kw, **bad))
+        assert e.value.status == ep.EP_EUNSUPPORTED, bad
 
 
 def test_footprint_scales_with_nodes():
@@ -143,6 +150,9 @@ def test_q2_slab_validation_and_footprint():
     kw.update(precision=ep.EP_PREC_FP64)
     with pytest.raises(ep.EpError) as e:
         ep.ep_create(*a, **kw)
+    assert e.value.status == ep.EP_EUNSUPPORTED
+    with pytest.raises(ep.EpError) as e:
+        ep.ep_create(*a, **dict(kw, precision=ep.EP_PREC_FP32_REFINED, solve_tiles=2))
     assert e.value.status == ep.EP_EUNSUPPORTED
     bad = dict(prob["mesh"], n_nodes=10)
     bad.pop("xyz")

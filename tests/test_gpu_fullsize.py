@@ -4,7 +4,8 @@
   endo/M/epi by depth, the 152-block persistent solve): one step from a
   seeded synthetic front, both precisions against the FP64 oracle (relative
   1e-10 FP64, 1e-6 refined on u, as for the slab), the refined one with the
-  stored stencil and with the matrix-free curved operator.
+  stored stencil (applied node-parallel, the default, and on tiles staged in
+  shared memory) and with the matrix-free curved operator.
 * The 442k-node slab (200 x 70 x 30) over a propagating window, t = 0..40 ms
   (the wave leaves the stimulated layer and crosses most of the slab):
   refined activation times within 0.5 ms of the oracle's, the same nodes
@@ -48,9 +49,11 @@ def test_full_size_shell_single_step():
     sim.step(1)
     u_ref = sim.get_state()[0]
     N = len(u_n)
-    for precision, tol, op32 in ((FP64, 1e-10, ep.EP_OP_AUTO), (REF, 1e-6, ep.EP_OP_STENCIL),
-                                 (REF, 1e-6, ep.EP_OP_MATRIX_FREE)):
-        inst = ep.Instance(prob, precision=precision, op32=op32)
+    # the refined stencil path with its default solve (node-parallel apply)
+    # and with the apply on tiles staged in shared memory
+    for precision, tol, op32, tiles in ((FP64, 1e-10, ep.EP_OP_AUTO, 0), (REF, 1e-6, ep.EP_OP_STENCIL, 0),
+                                        (REF, 1e-6, ep.EP_OP_STENCIL, 2), (REF, 1e-6, ep.EP_OP_MATRIX_FREE, 0)):
+        inst = ep.Instance(prob, precision=precision, op32=op32, solve_tiles=tiles)
         buf = ep.state_pack(prob["model"], prob["bdf"], prob["dt"], 7, u_n, u_nm1, w_n, w_nm1,
                             np.full(N, np.nan), np.full(N, -np.inf))
         inst.load(buf)
@@ -58,9 +61,10 @@ def test_full_size_shell_single_step():
         st = inst.stats()
         err = rel_err(gpu_state(inst)["u_n"], u_ref)
         inst.close()
-        assert err <= tol, (precision, op32, err)
+        assert err <= tol, (precision, op32, tiles, err)
         if precision == REF and op32 == ep.EP_OP_STENCIL:
             assert st["solve_threads"] == 1024  # one 1024-thread block per SM
+            assert st["solve_tiles"] == (1 if tiles == 2 else 0)
         assert st["relres"] <= (1e-12 if precision == FP64 else 1e-10)
 
 

@@ -39,7 +39,7 @@ void launch_ionic_batch(const Batch& B, int model, bool lv3, int grid, cudaStrea
 void launch_q2_apply32(Dev* d, const Dev& h, int grid_nodes, cudaStream_t s);
 void launch_q2_resid(Dev* d, const Dev& h, int first, int graph, int grid_nodes, cudaStream_t s);
 void launch_realpha_q2(Dev* d, const Dev& h, double alpha_dt, cudaStream_t s);
-void launch_rhs_ff_batch(const Batch& B, int graph, int grid, cudaStream_t s);
+void launch_rhs_ff_batch(const Batch& B, int graph, int grid, bool curved, cudaStream_t s);
 void launch_resid_np(Dev* d, const Dev& h, int graph, int grid, cudaStream_t s);
 cudaError_t launch_pcg32_batch(const Batch& B, int grid, int hint, cudaStream_t s);
 cudaError_t launch_prepace(int model, const uint8_t* cells, int ncell, double dt, long long m0, long long nsteps,
@@ -1561,7 +1561,9 @@ ep_status build_plan(BatchPlan* P) {
         if (!grp[gi].empty())
             epk::launch_ionic_batch(mk(o_grp[gi], o_sgrp[gi], (int)grp[gi].size(), grp[gi][0]),
                                     gi == 0 ? EP_MODEL_BO : EP_MODEL_TTP06, gi == 2, s_grp[gi].back(), s);
-    epk::launch_rhs_ff_batch(Br, 0, s_rhs.back(), s);
+    bool curved = false;
+    for (const ep_instance* I : P->key) curved = curved || I->h.Mhi != nullptr;
+    epk::launch_rhs_ff_batch(Br, 0, s_rhs.back(), curved, s);
     // every instance's refinement sweeps in one persistent launch (the
     // blocks of an instance that needs no sweep return at once)
     // no L2 eviction-priority hints in batches: their instances are each

@@ -15,7 +15,7 @@
 
 namespace epk {
 
-void launch_rhs_ff_batch(const Batch& B, int graph, int grid, cudaStream_t s);
+void launch_rhs_ff_batch(const Batch& B, int graph, int grid, bool curved, cudaStream_t s);
 void launch_correct_ff_batch(const Batch& B, int grid, cudaStream_t s);
 void launch_resid_np_batch(const Batch& B, int graph, int grid, cudaStream_t s);
 
@@ -53,8 +53,14 @@ __device__ __forceinline__ void mass_slab_np(const Dev& D, unsigned int f, const
 // state load).  Every thread takes nodes n = t, t + T, ... and reads the
 // neighbours' values through L1 at the offsets of the node's flags (a tiled
 // form staging v and u with their halos in shared memory measured 33.6 us
-// against 28.0 us on the 442k-node slab).
-__global__ void __launch_bounds__(kResidThreads, 2) k_rhs_np(Batch B, int graph) {
+// against 28.0 us on the 442k-node slab).  MINB resident blocks per SM: with
+// the curved mass matrix's float-float rows (54 couplings and 54 neighbour
+// values a node) one block per SM and 128 registers (2.19M-node shell: 154
+// against 194 us), with the slab's analytic mass matrix two blocks and 64
+// registers (442k-node slab: 34 against 41 us); the register cap changes
+// nothing in the results.
+template <int MINB>
+__global__ void __launch_bounds__(kResidThreads, MINB) k_rhs_np(Batch B, int graph) {
     const Slot S = batch_slot(B);
     Dev& D = *S.D;
     const int N = D.N;
@@ -189,10 +195,12 @@ __global__ void __launch_bounds__(kNodeThreads) k_correct_ff(Batch B) {
 }
 
 void launch_rhs_ff(Dev* d, const Dev& h, int graph, int grid, cudaStream_t s) {
-    launch_rhs_ff_batch(single_batch(d), graph, grid, s);
+    launch_rhs_ff_batch(single_batch(d), graph, grid, h.Mhi != nullptr, s);
 }
-void launch_rhs_ff_batch(const Batch& B, int graph, int grid, cudaStream_t s) {
-    k_rhs_np<<<grid, kResidThreads, 0, s>>>(B, graph);
+// curved: some instance of the batch has the stored (curved) mass matrix
+void launch_rhs_ff_batch(const Batch& B, int graph, int grid, bool curved, cudaStream_t s) {
+    if (curved) k_rhs_np<1><<<grid, kResidThreads, 0, s>>>(B, graph);
+    else k_rhs_np<2><<<grid, kResidThreads, 0, s>>>(B, graph);
 }
 
 void launch_resid_np(Dev* d, const Dev& h, int graph, int grid, cudaStream_t s) {

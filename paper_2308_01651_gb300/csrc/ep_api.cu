@@ -104,7 +104,7 @@ struct ep_instance {
     int grid_nodes = 0;        // grid of the grid-stride node kernels (with reductions)
     int grid_ionic = 0;        // one node per thread
     int ionic_threads = epk::kIonicThreads;  // its block size (autotuned at create)
-    int grid_resid = 0;        // node-parallel residual: 512-thread blocks, two per SM
+    int grid_resid = 0;        // node-parallel residual / rhs: 512-thread blocks, two per SM (one on curved meshes)
     int grid_tiles = 0;        // persistent grid of the tiled stencil kernels
     int grid_pcg = 0;          // cooperative grid of the persistent inner solver
     int pcg_tiled = 0;         // its apply pass on tiles staged in shared memory (k_pcg.cu)
@@ -1367,7 +1367,10 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     I->grid_nodes = std::max(1, std::min(blocks, 4 * sms));
     I->ionic_threads = opts->ionic_threads ? opts->ionic_threads : epk::kIonicThreads;
     I->grid_ionic = (int)((N + I->ionic_threads - 1) / I->ionic_threads);
-    I->grid_resid = std::max(1, std::min((int)((N + epk::kResidThreads - 1) / epk::kResidThreads), 2 * sms));
+    // (curved meshes: the right-hand side runs one 128-register block per
+    // SM, so one wave of them -- 2.19M-node shell 141 against 151 us with two)
+    I->grid_resid = std::max(1, std::min((int)((N + epk::kResidThreads - 1) / epk::kResidThreads),
+                                         (h.Mhi ? 1 : 2) * sms));
     I->grid_tiles = std::max(1, std::min(epk::st_tiles(h), 2 * sms));
     if (ref) {
         // the persistent solver's blocks must all be resident at once: one

@@ -55,10 +55,10 @@ __device__ __forceinline__ void mass_slab_np(const Dev& D, unsigned int f, const
 // form staging v and u with their halos in shared memory measured 33.6 us
 // against 28.0 us on the 442k-node slab).  MINB resident blocks per SM: with
 // the curved mass matrix's float-float rows (54 couplings and 54 neighbour
-// values a node) one block per SM and 128 registers (2.19M-node shell: 154
-// against 194 us), with the slab's analytic mass matrix two blocks and 64
-// registers (442k-node slab: 34 against 41 us); the register cap changes
-// nothing in the results.
+// values a node) one block per SM and 128 registers (2.19M-node shell: 151
+// against 194 us, and 141 us with a grid of one block per SM), with the
+// slab's analytic mass matrix two blocks and 64 registers (442k-node slab:
+// 34 against 41 us); the register cap changes nothing in the results.
 template <int MINB>
 __global__ void __launch_bounds__(kResidThreads, MINB) k_rhs_np(Batch B, int graph) {
     const Slot S = batch_slot(B);

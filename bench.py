@@ -448,7 +448,8 @@ def run_ours(args):
 
     op32 = {"auto": ep.EP_OP_AUTO, "mf": ep.EP_OP_MATRIX_FREE, "stencil": ep.EP_OP_STENCIL}[args.op32]
     tiles = {"auto": 0, "nodes": 1, "tiles": 2}[args.solve]
-    inst = ep.Instance(prob, precision=REF, cuda_stream=sp, op32=op32, solve_tiles=tiles)
+    inst = ep.Instance(prob, precision=REF, cuda_stream=sp, op32=op32, solve_tiles=tiles,
+                       inner_tol=args.inner_tol)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     W, K = max(3, args.warmup), args.steps
     # untimed: bring the instance into the propagating regime (the stimulus
@@ -594,7 +595,8 @@ def run_ours(args):
         K_e2e = K
     t0 = time.perf_counter()
     if K_e2e:
-        ie = ep.Instance(prob, precision=REF, cuda_stream=sp, op32=op32, solve_tiles=tiles)
+        ie = ep.Instance(prob, precision=REF, cuda_stream=sp, op32=op32, solve_tiles=tiles,
+                         inner_tol=args.inner_tol)
         ie.step_async(K_e2e)
         at_h = ie.activation_times()
         u_h = ie.potential()
@@ -784,6 +786,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--op32", default="auto", choices=["auto", "mf", "stencil"],
                     help="FP32 inner operator (auto: the faster one on slabs, by a create-time autotune)")
+    ap.add_argument("--inner-tol", type=float, default=0.0,
+                    help="the inner FP32 solve's relative stop per refinement sweep (0: the library's 1e-6)")
     ap.add_argument("--solve", default="auto", choices=["auto", "nodes", "tiles"],
                     help="the persistent solve's operator apply (auto: node-parallel; tiles: on tiles staged in "
                          "shared memory)")

@@ -197,7 +197,8 @@ typedef struct {
  * FP32 inner solve of a sweep stops once its residual is below 0.9 tol ||b||
  * (enough for that sweep to end the refinement) or below inner_tol times its
  * initial residual, whichever comes first (0 -> 1e-6, about the float
- * limit); max_sweeps: refinement sweeps
+ * limit, on slabs; 1e-7 on shells, where the first sweep then ends the
+ * refinement more often); max_sweeps: refinement sweeps
  * (0 -> 8); op32: FP32 inner operator; cuda_stream: a cudaStream_t to order
  * the instance's work on, or NULL for a stream the library creates;
  * ionic_threads: threads per block of the ionic kernel, 64, 128 or 256, or 0

@@ -1014,7 +1014,14 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     h.op32 = z.op32;
     const bool ref = h.prec == EP_PREC_FP32_REFINED;
     h.tol = opts->tol > 0 ? opts->tol : (ref ? 1e-10 : 1e-12);
-    h.inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-6;
+    // the inner stop relative to the sweep's start: on the curved shell a
+    // tenth of the usual float floor lets the first sweep end the
+    // refinement more often (2.19M-node shell, t = 11-41 ms: 1.32 against
+    // 1.99 sweeps a step with the same inner iterations, 1749 against
+    // 1911 us a step's solve; over t = 11-111 ms 1.79 sweeps, 1835 against
+    // 1852 us); on slabs it only adds iterations (442k nodes: 347 against
+    // 339 us)
+    h.inner_tol = opts->inner_tol > 0 ? opts->inner_tol : (mesh->kind == EP_MESH_SHELL ? 1e-7 : 1e-6);
     h.max_iter = opts->max_iter > 0 ? opts->max_iter : (ref ? 200 : 1000);
     h.max_sweeps = opts->max_sweeps > 0 ? opts->max_sweeps : 8;
 

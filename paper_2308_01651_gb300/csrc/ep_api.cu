@@ -91,6 +91,7 @@ struct ep_instance {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<void*> allocs;
+    std::vector<void*> temps;  // create-time temporaries, stream-ordered (dalloc_temp)
     size_t bytes = 0;
     long long host_step = 0;   // step index of the next enqueued step
     // a linear solve ran since ep_create or the last ep_load_state, so b, the
@@ -224,6 +225,37 @@ ep_status dalloc_zero(ep_instance* I, float** p, size_t count) {
         return fail(EP_ECUDA, "cudaMemsetAsync of a coupling array failed");
     }
     return EP_OK;
+}
+
+// Create-time temporaries (the assembly's inputs, the FP64 stencils that
+// the refined path drops after the float-float split) are stream-ordered
+// allocations on the instance's stream: a cudaFree waits for all work on the
+// device, so while other instances step (a server creating one as the
+// others run) every free would wait for their batch in flight.
+template <class T>
+ep_status dalloc_temp(ep_instance* I, T** p, size_t count) {
+    void* v = nullptr;
+    const size_t b = ((count * sizeof(T) + 255) / 256) * 256;
+    cudaError_t e = cudaMallocAsync(&v, b > 0 ? b : 256, I->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(EP_ENOMEM, "cudaMallocAsync of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    I->temps.push_back(v);
+    *p = static_cast<T*>(v);
+    return EP_OK;
+}
+
+template <class T>
+void dfree_temp(ep_instance* I, T*& p) {
+    if (!p) return;
+    for (size_t i = 0; i < I->temps.size(); ++i)
+        if (I->temps[i] == (void*)p) {
+            I->temps.erase(I->temps.begin() + i);
+            cudaFreeAsync((void*)p, I->stream);
+            break;
+        }
+    p = nullptr;
 }
 
 // Frees one allocation of dalloc before ep_destroy.
@@ -886,6 +918,11 @@ void free_all(ep_instance* I) {
     if (I->graph) cudaGraphDestroy(I->graph);
     for (void* p : I->allocs) cudaFree(p);
     I->allocs.clear();
+    if (I->stream) {
+        for (void* p : I->temps) cudaFreeAsync(p, I->stream);
+        if (!I->temps.empty()) cudaStreamSynchronize(I->stream);
+    }
+    I->temps.clear();
     if (I->own_stream && I->stream) cudaStreamDestroy(I->stream);
 }
 
@@ -1064,10 +1101,15 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
     }
     ALLOC(h.at, N);
     ALLOC(h.best, N);
-    if (!z.q2) {
+    if (!z.q2 && !ref) {
         ALLOC(h.M64, epk::kSlots * N);
         ALLOC(h.A64, epk::kSlots * N);
         ALLOC(h.dinv64, N);
+    } else if (!z.q2) {
+        // the refined path splits them into float-float couplings and drops them
+        if ((st = dalloc_temp(I, &h.M64, epk::kSlots * N)) != EP_OK) return st;
+        if ((st = dalloc_temp(I, &h.A64, epk::kSlots * N)) != EP_OK) return st;
+        if ((st = dalloc_temp(I, &h.dinv64, N)) != EP_OK) return st;
     }
     if (ref) {
         ALLOC(h.dinv32, N);
@@ -1290,24 +1332,25 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         ep_status st2 = q2_setup(I, fib, dl, dtr, dn);
         if (st2 != EP_OK) return st2;
     } else {
+        // the assembly's inputs: stream-ordered temporaries (dalloc_temp)
+        cudaStream_t cs = I->stream;
         double *f0 = nullptr, *s0 = nullptr, *xyz = nullptr;
-        CUDA_TRY(cudaMalloc(&f0, N * 3 * 8));
-        cudaError_t e1 = cudaMalloc(&s0, N * 3 * 8);
-        cudaError_t e2 = h.kind == EP_MESH_SHELL ? cudaMalloc(&xyz, N * 3 * 8) : cudaSuccess;
         int* bad = nullptr;
-        cudaError_t e3 = cudaMalloc(&bad, sizeof(int));
-        cudaError_t e = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
-        if (e == cudaSuccess) e = cudaMemcpy(f0, fib->f0, N * 24, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(s0, fib->s0, N * 24, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && xyz) e = cudaMemcpy(xyz, mesh->xyz, N * 24, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemset(bad, 0, sizeof(int));
-        int bad_h = 0;
         uint8_t* label = nullptr;
+        if ((st = dalloc_temp(I, &f0, N * 3)) != EP_OK) return st;
+        if ((st = dalloc_temp(I, &s0, N * 3)) != EP_OK) return st;
+        if (h.kind == EP_MESH_SHELL && (st = dalloc_temp(I, &xyz, N * 3)) != EP_OK) return st;
+        if ((st = dalloc_temp(I, &bad, 1)) != EP_OK) return st;
+        cudaError_t e = cudaMemcpyAsync(f0, fib->f0, N * 24, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s0, fib->s0, N * 24, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess && xyz) e = cudaMemcpyAsync(xyz, mesh->xyz, N * 24, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), cs);
+        int bad_h = 0;
         epk::AsmParams P{xyz, f0, s0, dl, dtr, dn, alpha_dt, bad, nullptr, {}, {}};
         if (e == cudaSuccess && mesh->region) {
             const size_t ne = (size_t)mesh->nx * mesh->ny * mesh->nz;
-            e = cudaMalloc(&label, ne);
-            if (e == cudaSuccess) e = cudaMemcpy(label, mesh->region, ne, cudaMemcpyHostToDevice);
+            if ((st = dalloc_temp(I, &label, ne)) != EP_OK) return st;
+            e = cudaMemcpyAsync(label, mesh->region, ne, cudaMemcpyHostToDevice, cs);
             P.label = label;
             const double sc = cond->is_D ? 1.0 : 1.0 / (cond->chi_m * cond->Cm);
             for (int r = 0; r < cond->n_regions; ++r) {
@@ -1316,16 +1359,16 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
             }
         }
         if (e == cudaSuccess) {
-            epk::launch_assemble(I->d, h, P, I->stream);
+            epk::launch_assemble(I->d, h, P, cs);
             e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
-            if (e == cudaSuccess) e = cudaMemcpy(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, cs);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
         }
-        cudaFree(f0);
-        cudaFree(s0);
-        if (xyz) cudaFree(xyz);
-        if (bad) cudaFree(bad);
-        if (label) cudaFree(label);
+        dfree_temp(I, f0);
+        dfree_temp(I, s0);
+        dfree_temp(I, xyz);
+        dfree_temp(I, bad);
+        dfree_temp(I, label);
         if (e != cudaSuccess) return fail(EP_ECUDA, std::string("assembly: ") + cudaGetErrorString(e));
         if (bad_h) return fail(EP_EINVAL, "mesh has an element with non-positive Jacobian determinant");
     }
@@ -1336,12 +1379,13 @@ ep_status create_impl(const ep_mesh* mesh, const ep_fibers* fib, const ep_conduc
         CUDA_TRY(cudaGetLastError());
         CUDA_TRY(cudaStreamSynchronize(I->stream));
         double m0 = 0.0;
-        CUDA_TRY(cudaMemcpy(&m0, h.M64, sizeof(double), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpyAsync(&m0, h.M64, sizeof(double), cudaMemcpyDeviceToHost, I->stream));
+        CUDA_TRY(cudaStreamSynchronize(I->stream));
         h.nscale = m0 > 0.0 ? (float)(1.0 / m0) : 1.0f;
         // from here on the refined path reads only the float-float couplings
-        dfree(I, h.M64, epk::kSlots * N);
-        dfree(I, h.A64, epk::kSlots * N);
-        dfree(I, h.dinv64, N);
+        dfree_temp(I, h.M64);
+        dfree_temp(I, h.A64);
+        dfree_temp(I, h.dinv64);
         CUDA_TRY(cudaMemcpy(I->d, &h, sizeof(Dev), cudaMemcpyHostToDevice));
     }
     if (h.fib) {

@@ -728,8 +728,12 @@ def run_serve(args):
     mix = serve.request_mix(n_req, g, n_lo=1.0e4, n_hi=2.2e6, t_lo=200.0 * ts, t_hi=600.0 * ts)
     free, total = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
-    # pilot: the first requests of the mix stepped together
-    pilot = [ep.Instance(p, precision=ep.EP_PREC_FP32_REFINED, op32=ep.EP_OP_STENCIL) for p, _ in mix[:6]]
+    # pilot: the first requests of the mix stepped together -- 16 of them,
+    # about the server's concurrency at this load: a batched step waits for
+    # its slowest instance, so six requests measured 7.4e8 DoF-steps/s where
+    # 64 resident ones ran at 4.6e8, and a rate set from them overloaded the
+    # server (2000 requests: time to result growing to 250 s)
+    pilot = [ep.Instance(p, precision=ep.EP_PREC_FP32_REFINED, op32=ep.EP_OP_STENCIL) for p, _ in mix[:16]]
     hs = [i.h for i in pilot]
     ep.ep_step_batch(hs, 5)
     torch.cuda.synchronize()
@@ -758,7 +762,7 @@ def run_serve(args):
                        "duration_ms": f"uniform {200 * ts:g}-{600 * ts:g} (the specification's 200-600 "
                                       f"scaled by {ts:g})",
                        "arrival_rate_per_s": rate, "offered_load": rho,
-                       "pilot_dof_steps_per_s": X, "pilot": "6 requests of the mix, 40 batched steps",
+                       "pilot_dof_steps_per_s": X, "pilot": "16 requests of the mix, 40 batched steps",
                        "memory_budget_bytes": budget, "free_bytes": free, "chunk_steps": srv.chunk,
                        "rate_rule": "expected resident footprint = budget (processor sharing, Little's law), "
                                     "load capped at 0.9"},

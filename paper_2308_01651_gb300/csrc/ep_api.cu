@@ -1549,21 +1549,51 @@ ep_status build_plan(BatchPlan* P) {
     std::vector<int> s_rhs{0}, s_pcg{0}, s_grp[3] = {{0}, {0}, {0}};
     double total = 0.0;
     for (ep_instance* I : P->key) total += (double)I->h.N;
-    // persistent solver: blocks in proportion to size, at least one each,
-    // at most what the instance uses alone, the sum within the resident cap
-    std::vector<int> gp(n);
-    int used = 0;
+    // persistent solver: the launch lasts as long as its slowest instance,
+    // whose time goes with its nodes times its inner iterations over its
+    // blocks.  So every instance gets one block, then each further block
+    // goes to the instance with the most work per block (at most what it
+    // uses alone, the sum within the resident cap); the work is its nodes
+    // times the inner iterations of its last step (unknown before the first
+    // step: the median of the others).  Shares by size alone left a batch of
+    // slabs waiting for its shells, which need about twice the iterations.
+    std::vector<double> it(n, 0.0);
     for (int i = 0; i < n; ++i) {
-        const ep_instance* I = P->key[i];
-        const int want = I->grid_pcg;
-        gp[i] = std::max(1, std::min(want, (int)std::floor((double)cap * I->h.N / total)));
-        used += gp[i];
+        ep_instance* I = P->key[i];
+        if (I->stream) CUDA_TRY(cudaStreamSynchronize(I->stream));
+        int li = 0;
+        CUDA_TRY(cudaMemcpy(&li, reinterpret_cast<const char*>(I->d) + offsetof(epk::Dev, last_iters), sizeof(int),
+                            cudaMemcpyDeviceToHost));
+        it[i] = (double)li;
     }
-    while (used > cap) {  // trim the largest shares
-        int k = (int)(std::max_element(gp.begin(), gp.end()) - gp.begin());
-        if (gp[k] <= 1) break;
-        --gp[k];
-        --used;
+    {
+        std::vector<double> known;
+        for (double x : it)
+            if (x > 0.0) known.push_back(x);
+        double med = 10.0;
+        if (!known.empty()) {
+            std::nth_element(known.begin(), known.begin() + known.size() / 2, known.end());
+            med = known[known.size() / 2];
+        }
+        for (double& x : it)
+            if (x <= 0.0) x = med;
+    }
+    std::vector<int> gp(n, 1);
+    int used = n;
+    for (;;) {
+        int best = -1;
+        double wbest = 0.0;
+        for (int i = 0; i < n; ++i) {
+            if (gp[i] >= P->key[i]->grid_pcg) continue;
+            const double w = (double)P->key[i]->h.N * it[i] / gp[i];
+            if (w > wbest) {
+                wbest = w;
+                best = i;
+            }
+        }
+        if (best < 0 || used >= cap) break;
+        ++gp[best];
+        ++used;
     }
     if (used > cap) return fail(EP_EINVAL, "batch does not fit the persistent solver's resident blocks");
     for (int i = 0; i < n; ++i) {

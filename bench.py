@@ -712,12 +712,13 @@ def run_serve(args):
     a budget of 80 % of free device memory, continuously batched, instances
     created on a worker thread while the residents step; time to result
     p50/p99 and aggregate DoF-steps/s.  The arrival rate comes from a
-    measured pilot: the batched throughput X of a few requests of the mix,
-    then the rate at which a processor-sharing server's expected resident
-    footprint equals the budget (Little's law), capped at 90 % load.  The
-    request count and the durations (the specification's 200-600 ms times
-    --serve-time-scale) are scaled so that the run takes a few minutes; the
-    line states both."""
+    measured pilot: the batched throughput X of the first 16 requests of the
+    mix, then the rate at which a processor-sharing server's expected
+    resident footprint equals the budget (Little's law), capped at 90 % load.
+    The durations (the specification's 200-600 ms times --serve-time-scale)
+    and by default the request count (--requests; the specification's 2000
+    take over ten minutes) are scaled so that the run takes a few minutes;
+    the line states both."""
     import numpy as np
     torch = _gpu_setup()
     from paper_2308_01651_gb300 import ep, serve
